@@ -1,0 +1,209 @@
+/*
+ * lpsim.h -- C ABI of the GB300 (sm_103a) per-step vehicle update of
+ * "Large Scale Multi-GPU Based Parallel Traffic Simulation for Accelerated
+ * Traffic Assignment and Propagation" (Jiang, Sengupta, Demmel, Williams;
+ * arXiv 2406.08496).
+ *
+ * What the library computes.  One simulation step moves every vehicle on the
+ * network from its state at step k to step k+1 using only step-k state
+ * (eq. vehicle_dynamics, Sec. 3.1), following Algorithm 1 (Vehicle
+ * Propagation): departure when the first cell of the first edge is free,
+ * leader search within d_front = 2 dt v on a byte-per-metre lane map
+ * (Sec. 3.1, Lane Map: 255 = empty, 0..254 = speed of the occupying vehicle),
+ * IDM car following (eq. Car Following) or the free-flow speed, signal
+ * control at the stop line, mandatory lane change (eq. Lane Change) with gap
+ * acceptance (eq. Gap Acceptance), and entry to the next edge of the
+ * precomputed route when its first cell is free, one vehicle per cell
+ * (Sec. 3.1 Remark; Sec. 3.2).  Rules the paper names without a formula use
+ * the readings documented with the library: IDM with delta = 4; no-crash
+ * clamp at the standstill gap s0; lane-change probability 1 - x_rem/x0;
+ * critical gaps g + max(0, alpha_i v - alpha_a v_a) + eps; fixed-time
+ * signals (approach of phase j green iff (k / G) mod n_phases == j); several
+ * vehicles asking for one (edge, lane) entry: the lowest vehicle id wins.
+ * All vehicle state is IEEE binary32 and the results do not depend on
+ * launch configuration, sort period or processing order.
+ *
+ * Conventions.
+ *  - Every function returns an int status: LPSIM_OK (0) or a negative
+ *    LPSIM_E_* code; lpsim_last_error() gives a message for the calling
+ *    thread's last failure.  No C++ exception crosses this boundary.
+ *  - Every pointer argument that is an input is a HOST pointer to
+ *    caller-owned memory, read during the call and copied; nothing is
+ *    retained.  Every output is written into a caller-owned HOST buffer
+ *    whose size the caller states; a buffer that is too small gives
+ *    LPSIM_E_INVALID_ARG.
+ *  - Device memory is owned by the context and released by lpsim_destroy.
+ *    It comes from cudaMalloc unless lpsim_set_allocator installed a
+ *    callback pair (the Python binding routes it to PyTorch's caching
+ *    allocator).
+ *  - A context runs on the CUDA stream given to lpsim_load_network on the
+ *    device current at that call; NULL makes the library create its own
+ *    non-blocking stream (steps are captured into CUDA graphs, which the
+ *    legacy default stream cannot do).  Calls on one context must not
+ *    overlap.
+ */
+#ifndef LPSIM_H
+#define LPSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LPSIM_OK 0
+#define LPSIM_E_INVALID_ARG (-1) /* bad argument or input data (message says which) */
+#define LPSIM_E_OOM (-2)         /* device or host allocation failed */
+#define LPSIM_E_CUDA (-3)        /* a CUDA runtime call failed */
+#define LPSIM_E_STATE (-4)       /* call out of order (e.g. stepping before lpsim_load_demand) */
+#define LPSIM_E_TIMEOUT (-5)     /* a bounded device wait gave up */
+#define LPSIM_E_GRIDLOCK (-6)    /* vehicles active but none moved for the stated number of steps */
+#define LPSIM_E_INVARIANT (-7)   /* device check: a lane-map cell written twice in one step */
+
+#define LPSIM_F_NO_SORT 1u
+
+typedef struct lpsim_ctx lpsim_ctx;
+
+/* Model and run parameters.  Model fields mirror the symbols of Table 3. */
+typedef struct lpsim_params {
+    float dt;          /* time step Delta t, s (> 0) */
+    float a;           /* IDM acceleration potential, m/s^2 (> 0) */
+    float b;           /* IDM comfortable deceleration, m/s^2 (> 0) */
+    float s0;          /* standstill spacing, m (>= 0) */
+    float T;           /* desired time headway, s */
+    float x0;          /* distance to the edge end below which a mandatory lane change may start, m (> 0) */
+    float g_a, g_b;    /* desired lead / lag gaps, m */
+    float alpha_i, alpha_a, alpha_b; /* anticipation times of the changer, lead and lag vehicle, s */
+    float eps_amp;     /* random gap components eps ~ U(-eps_amp, eps_amp), m; 0 = none */
+    uint64_t seed;     /* seed of the lane-change draws (SplitMix64 of seed, vehicle id, step) */
+    uint32_t bin_steps;   /* steps per link-statistics bin (0 = no binned statistics) */
+    uint32_t n_bins;      /* bins kept per edge */
+    uint32_t sort_period; /* steps between re-sorts of the active vehicles by lane-map cell (0 = 64) */
+    uint32_t block_size;  /* threads per block of the step kernels: 128, 256, 512 or 0 (= 256) */
+    uint32_t blocks_per_sm; /* resident blocks per SM the step grids are sized for (0 = 4) */
+    uint32_t chunk_steps; /* steps captured in one CUDA graph launch (0 = 384); rounded up to a multiple
+                             of 2 sort periods and of 3 */
+    uint32_t gridlock_steps; /* lpsim_run fails with LPSIM_E_GRIDLOCK after this many steps with active
+                                vehicles and no departure, crossing or arrival (0 = never) */
+    uint32_t flags;       /* bit 0 (LPSIM_F_NO_SORT): compact without sorting; other bits must be 0 */
+} lpsim_params;
+
+/* Road network.  Edge e runs edge_src[e] -> edge_dst[e], is edge_len_m[e]
+ * metres long (stored as max(1, ceil(len)) one-metre cells per lane, at most
+ * 65535), has edge_lanes[e] in 1..4 lanes and speed limit edge_vmax[e] in
+ * (0, 254] m/s.  node_green_steps[i] is the green time per phase at node i in
+ * steps (0 = uncontrolled).  edge_approach_rank (nullable) is the signal
+ * phase of edge e at its downstream node, below that node's in-degree; NULL
+ * gives each incoming edge its own phase ranked by edge id.  At most 255
+ * incoming and 255 outgoing edges per node. */
+typedef struct lpsim_network {
+    uint32_t n_nodes, n_edges;
+    const uint32_t *edge_src, *edge_dst;
+    const float *edge_len_m;
+    const uint8_t *edge_lanes;
+    const float *edge_vmax;
+    const uint32_t *node_green_steps;
+    const uint8_t *edge_approach_rank;
+} lpsim_network;
+
+typedef struct lpsim_run_result {
+    uint64_t steps;     /* steps taken by this call */
+    uint64_t veh_steps; /* sum over those steps of the vehicles on the network (active vehicle-steps) */
+    uint64_t arrived;   /* trips arrived so far */
+    uint64_t active;    /* vehicles on the network now */
+    uint64_t waiting;   /* trips not yet departed */
+    uint64_t k;         /* current step */
+    double wall_ms;     /* host wall time of the call */
+} lpsim_run_result;
+
+typedef struct lpsim_link_stat {
+    uint64_t entries;  /* vehicles that entered the edge (departures included) */
+    uint64_t exits;    /* vehicles that left it (arrivals included) */
+    uint64_t tt_steps; /* sum over exits of the steps spent on the edge */
+} lpsim_link_stat;
+
+typedef struct lpsim_counters {
+    uint64_t k, veh_steps, arrived, active, waiting, lane_changes;
+    uint64_t slots;       /* vehicle slots in use (active plus not yet compacted) */
+    uint64_t launches;    /* kernel launches issued by this context */
+} lpsim_counters;
+
+/* Message of the calling thread's last failure ("" if none). */
+const char *lpsim_last_error(void);
+
+/* Library version string. */
+const char *lpsim_version(void);
+
+/* Route this process's device allocations of contexts created afterwards
+ * through alloc(size, user) / release(ptr, user); alloc must return memory
+ * usable on the current device and aligned to 256 bytes, or NULL.  Both NULL
+ * restores cudaMalloc / cudaFree. */
+int lpsim_set_allocator(void *(*alloc)(size_t size, void *user), void (*release)(void *ptr, void *user),
+                        void *user);
+
+/* Create a context and upload the network (Sec. 3.1, Network Data
+ * Information: per edge the lanes, its place in the lane map, upstream and
+ * downstream intersection).  stream: a cudaStream_t other than the legacy
+ * default stream, or NULL (the library then creates its own stream). */
+int lpsim_load_network(lpsim_ctx **out, const lpsim_network *net, const lpsim_params *p, void *stream);
+
+/* Upload the routed trips (Sec. 3.1, Vehicle Data Information: route and
+ * first edge "after the routing").  Trip j departs no earlier than step
+ * depart_step[j] and follows route_edges[route_off[j] .. route_off[j+1]), a
+ * non-empty sequence of edges where each edge starts at the node the previous
+ * one ends at.  route_off has n_trips + 1 entries starting at 0; the total
+ * route length must stay below 2^32.  Vehicle ids are the ranks of a stable
+ * sort of the trips by depart_step (the paper sorts by departure time,
+ * Sec. 4, Table 6); out_vehicle_id (nullable, n_trips entries) receives trip
+ * j's id.  Resets the step counter to 0.  Once per context. */
+int lpsim_load_demand(lpsim_ctx *ctx, uint64_t n_trips, const uint32_t *depart_step, const uint64_t *route_off,
+                      const uint32_t *route_edges, uint32_t *out_vehicle_id);
+
+/* Advance n_steps steps.  Returns after the steps have completed on the
+ * device and the device status word was read. */
+int lpsim_step(lpsim_ctx *ctx, uint32_t n_steps);
+
+/* Step until every trip has arrived or max_steps steps were taken; out
+ * (nullable) receives the totals of this call. */
+int lpsim_run(lpsim_ctx *ctx, uint32_t max_steps, lpsim_run_result *out);
+
+/* Back to step 0 with the same network and trips: empty lane maps, every
+ * trip waiting, statistics cleared.  No host-device transfer of inputs. */
+int lpsim_reset(lpsim_ctx *ctx);
+
+/* Link statistics.  out (nullable): n_edges records.  The binned arrays
+ * (each nullable, n_edges * n_bins u32, edge-major) receive per (edge, bin):
+ * inflow counted at entry step k+1 in bin (k+1)/bin_steps; steps spent and
+ * exit count of the vehicles that entered in that bin; the vehicles on the
+ * edge at the first step of the bin.  n_edges and n_bins must equal the
+ * context's. */
+int lpsim_link_stats(lpsim_ctx *ctx, lpsim_link_stat *out, uint64_t n_edges, uint32_t *bin_inflow,
+                     uint32_t *bin_tt_sum, uint32_t *bin_tt_cnt, uint32_t *bin_occ, uint32_t n_bins);
+
+/* Per vehicle id (n entries each, n = trips loaded): the step at which it
+ * entered the network (0xFFFFFFFF if not yet) and the step at which it
+ * arrived (0xFFFFFFFF if not yet).  Either pointer may be NULL. */
+int lpsim_get_trips(lpsim_ctx *ctx, uint64_t n, uint32_t *depart_actual, uint32_t *arrive_step);
+
+/* Per vehicle id (n entries each): position on the edge (m), speed (m/s),
+ * edge, lane, index in its route and status (0 waiting, 1 active, 2 arrived);
+ * non-active vehicles read x = v = 0, edge 0xFFFFFFFF, lane 0, index 0.  Any
+ * pointer may be NULL. */
+int lpsim_get_state(lpsim_ctx *ctx, uint64_t n, float *x, float *v, uint32_t *edge, uint8_t *lane,
+                    uint32_t *route_idx, uint8_t *status);
+
+/* Lane map at the current step in canonical layout: edges in id order, lanes
+ * in order, cells 0..len-1, no padding; size = lpsim_lane_map_size(). */
+uint64_t lpsim_lane_map_size(const lpsim_ctx *ctx);
+int lpsim_get_lane_map(lpsim_ctx *ctx, uint8_t *out, uint64_t size);
+
+int lpsim_get_counters(lpsim_ctx *ctx, lpsim_counters *out);
+
+/* Release every device and host resource of the context (NULL is a no-op). */
+void lpsim_destroy(lpsim_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,268 @@
+"""GB300-native per-step microsimulation of arXiv 2406.08496 (LPSim).
+
+Thin Python binding of the C ABI in include/lpsim.h (liblpsim.so, hand-written
+sm_103a CUDA).  This module only marshals arguments: every step of the
+simulation runs in the library's kernels.  PyTorch, when present, supplies
+device memory (caching allocator) and the stream.  There is no CPU fallback:
+importing the binding without the compiled library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from ._build import LIB as _LIB_PATH
+from ._build import build as _build_lib
+
+__all__ = ["Simulation", "LpsimError", "DEFAULT_PARAMS", "build", "load_library", "EXPORTED"]
+
+# Model readings (Table 3 lists the symbols without values): dt from the
+# workloads; IDM a, b, s0, T; lane-change horizon x0; critical-gap constants.
+DEFAULT_PARAMS = dict(dt=0.5, a=1.0, b=1.5, s0=2.0, T=1.5, x0=100.0, g_a=2.0, g_b=2.0,
+                      alpha_i=1.0, alpha_a=1.0, alpha_b=1.0, eps_amp=0.0, seed=12345,
+                      bin_steps=1800, n_bins=0, sort_period=64, block_size=256, blocks_per_sm=4,
+                      chunk_steps=384, gridlock_steps=0, flags=0)
+FLAG_NO_SORT = 1
+
+EXPORTED = ["lpsim_last_error", "lpsim_version", "lpsim_set_allocator", "lpsim_load_network",
+            "lpsim_load_demand", "lpsim_step", "lpsim_run", "lpsim_reset", "lpsim_link_stats",
+            "lpsim_get_trips", "lpsim_get_state", "lpsim_lane_map_size", "lpsim_get_lane_map",
+            "lpsim_get_counters", "lpsim_destroy"]
+
+STATUS = {0: "LPSIM_OK", -1: "LPSIM_E_INVALID_ARG", -2: "LPSIM_E_OOM", -3: "LPSIM_E_CUDA", -4: "LPSIM_E_STATE",
+          -5: "LPSIM_E_TIMEOUT", -6: "LPSIM_E_GRIDLOCK", -7: "LPSIM_E_INVARIANT"}
+
+
+class Params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_float) for n in ("dt", "a", "b", "s0", "T", "x0", "g_a", "g_b", "alpha_i",
+                                              "alpha_a", "alpha_b", "eps_amp")] + \
+               [("seed", ctypes.c_uint64)] + \
+               [(n, ctypes.c_uint32) for n in ("bin_steps", "n_bins", "sort_period", "block_size",
+                                               "blocks_per_sm", "chunk_steps", "gridlock_steps", "flags")]
+
+
+class Network(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_uint32), ("n_edges", ctypes.c_uint32),
+                ("edge_src", ctypes.c_void_p), ("edge_dst", ctypes.c_void_p), ("edge_len_m", ctypes.c_void_p),
+                ("edge_lanes", ctypes.c_void_p), ("edge_vmax", ctypes.c_void_p),
+                ("node_green_steps", ctypes.c_void_p), ("edge_approach_rank", ctypes.c_void_p)]
+
+
+class RunResult(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("steps", "veh_steps", "arrived", "active", "waiting", "k")] + \
+               [("wall_ms", ctypes.c_double)]
+
+
+class LinkStat(ctypes.Structure):
+    _fields_ = [("entries", ctypes.c_uint64), ("exits", ctypes.c_uint64), ("tt_steps", ctypes.c_uint64)]
+
+
+class Counters(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("k", "veh_steps", "arrived", "active", "waiting", "lane_changes",
+                                               "slots", "launches")]
+
+
+class LpsimError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+_alloc_cbs = None  # keeps the ctypes callbacks alive
+ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+def build(force: bool = False) -> str:
+    """Compile liblpsim.so for sm_103a (nvcc; works without a GPU)."""
+    return _build_lib(force=force)
+
+
+def load_library(path: str | None = None):
+    """Load liblpsim.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or _LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"liblpsim.so not found at {p}: run paper_2406_08496_gb300.build() first "
+                          "(the simulation has no CPU fallback)")
+    lib = ctypes.CDLL(p)
+    P = ctypes.c_void_p
+    lib.lpsim_last_error.restype = ctypes.c_char_p
+    lib.lpsim_version.restype = ctypes.c_char_p
+    lib.lpsim_set_allocator.argtypes = [ALLOC_T, FREE_T, P]
+    lib.lpsim_load_network.argtypes = [ctypes.POINTER(P), ctypes.POINTER(Network), ctypes.POINTER(Params), P]
+    lib.lpsim_load_demand.argtypes = [P, ctypes.c_uint64, P, P, P, P]
+    lib.lpsim_step.argtypes = [P, ctypes.c_uint32]
+    lib.lpsim_run.argtypes = [P, ctypes.c_uint32, ctypes.POINTER(RunResult)]
+    lib.lpsim_reset.argtypes = [P]
+    lib.lpsim_link_stats.argtypes = [P, P, ctypes.c_uint64, P, P, P, P, ctypes.c_uint32]
+    lib.lpsim_get_trips.argtypes = [P, ctypes.c_uint64, P, P]
+    lib.lpsim_get_state.argtypes = [P, ctypes.c_uint64, P, P, P, P, P, P]
+    lib.lpsim_lane_map_size.argtypes = [P]
+    lib.lpsim_lane_map_size.restype = ctypes.c_uint64
+    lib.lpsim_get_lane_map.argtypes = [P, P, ctypes.c_uint64]
+    lib.lpsim_get_counters.argtypes = [P, ctypes.POINTER(Counters)]
+    lib.lpsim_destroy.argtypes = [P]
+    lib.lpsim_destroy.restype = None
+    _lib = lib
+    return lib
+
+
+def _p(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def _check(lib, rc: int) -> None:
+    if rc != 0:
+        raise LpsimError(rc, lib.lpsim_last_error().decode(errors="replace"))
+
+
+def use_torch_allocator() -> bool:
+    """Route the library's device allocations through PyTorch's caching
+    allocator (contexts created afterwards).  Returns False without CUDA."""
+    global _alloc_cbs
+    lib = load_library()
+    try:
+        import torch
+    except ImportError:
+        return False
+    if not torch.cuda.is_available():
+        return False
+
+    def _alloc(size, user):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(size), stream=torch.cuda.current_stream()))
+        except Exception:
+            return None
+
+    def _free(ptr, user):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    cbs = (ALLOC_T(_alloc), FREE_T(_free))
+    _check(lib, lib.lpsim_set_allocator(cbs[0], cbs[1], None))
+    _alloc_cbs = cbs
+    return True
+
+
+def _current_stream():
+    """torch's current stream, or None for the library's own stream (the
+    legacy default stream cannot be captured into a CUDA graph)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            h = torch.cuda.current_stream().cuda_stream
+            return ctypes.c_void_p(h) if h else None
+    except ImportError:
+        pass
+    return None
+
+
+class Simulation:
+    """One network + demand on the GPU library.
+
+    net: dict with n_nodes, n_edges, edge_src, edge_dst, edge_len, edge_lanes,
+    edge_vmax, node_green and optionally edge_approach_rank (numpy arrays).
+    """
+
+    def __init__(self, net: dict, params: dict | None = None, stream=None):
+        self.lib = load_library()
+        self.params = dict(DEFAULT_PARAMS)
+        if params:
+            self.params.update(params)
+        self._p = Params(**self.params)
+        self._net = {
+            "edge_src": np.ascontiguousarray(net["edge_src"], dtype=np.uint32),
+            "edge_dst": np.ascontiguousarray(net["edge_dst"], dtype=np.uint32),
+            "edge_len": np.ascontiguousarray(net["edge_len"], dtype=np.float32),
+            "edge_lanes": np.ascontiguousarray(net["edge_lanes"], dtype=np.uint8),
+            "edge_vmax": np.ascontiguousarray(net["edge_vmax"], dtype=np.float32),
+            "node_green": np.ascontiguousarray(net["node_green"], dtype=np.uint32),
+        }
+        ar = net.get("edge_approach_rank")
+        self._net["edge_approach_rank"] = None if ar is None else np.ascontiguousarray(ar, dtype=np.uint8)
+        n = self._net
+        self.n_edges = int(net["n_edges"])
+        self.n_bins = int(self.params["n_bins"])
+        desc = Network(int(net["n_nodes"]), self.n_edges, _p(n["edge_src"]), _p(n["edge_dst"]), _p(n["edge_len"]),
+                       _p(n["edge_lanes"]), _p(n["edge_vmax"]), _p(n["node_green"]), _p(n["edge_approach_rank"]))
+        h = ctypes.c_void_p()
+        st = stream if stream is not None else _current_stream()
+        _check(self.lib, self.lib.lpsim_load_network(ctypes.byref(h), ctypes.byref(desc), ctypes.byref(self._p), st))
+        self.h = h
+        self.n = 0
+
+    def load_demand(self, dem: dict) -> np.ndarray:
+        dep = np.ascontiguousarray(dem["depart_step"], dtype=np.uint32)
+        off = np.ascontiguousarray(dem["route_off"], dtype=np.uint64)
+        edges = np.ascontiguousarray(dem["route_edges"], dtype=np.uint32)
+        vid = np.empty(len(dep), dtype=np.uint32)
+        _check(self.lib, self.lib.lpsim_load_demand(self.h, len(dep), _p(dep), _p(off), _p(edges), _p(vid)))
+        self.n = len(dep)
+        return vid
+
+    def step(self, n_steps: int = 1) -> None:
+        _check(self.lib, self.lib.lpsim_step(self.h, n_steps))
+
+    def run(self, max_steps: int) -> dict:
+        r = RunResult()
+        _check(self.lib, self.lib.lpsim_run(self.h, max_steps, ctypes.byref(r)))
+        return {f: getattr(r, f) for f, _ in RunResult._fields_}
+
+    def reset(self) -> None:
+        _check(self.lib, self.lib.lpsim_reset(self.h))
+
+    def counters(self) -> dict:
+        c = Counters()
+        _check(self.lib, self.lib.lpsim_get_counters(self.h, ctypes.byref(c)))
+        return {f: getattr(c, f) for f, _ in Counters._fields_}
+
+    def state(self) -> dict:
+        n = self.n
+        st = {"x": np.empty(n, np.float32), "v": np.empty(n, np.float32), "edge": np.empty(n, np.uint32),
+              "lane": np.empty(n, np.uint8), "ridx": np.empty(n, np.uint32), "status": np.empty(n, np.uint8)}
+        _check(self.lib, self.lib.lpsim_get_state(self.h, n, *(_p(st[k]) for k in
+                                                              ("x", "v", "edge", "lane", "ridx", "status"))))
+        return st
+
+    def trips(self) -> dict:
+        d = np.empty(self.n, np.uint32)
+        a = np.empty(self.n, np.uint32)
+        _check(self.lib, self.lib.lpsim_get_trips(self.h, self.n, _p(d), _p(a)))
+        return {"depart": d, "arrive": a}
+
+    def lane_map(self) -> np.ndarray:
+        m = np.empty(int(self.lib.lpsim_lane_map_size(self.h)), np.uint8)
+        _check(self.lib, self.lib.lpsim_get_lane_map(self.h, _p(m), m.size))
+        return m
+
+    def link_stats(self) -> dict:
+        ne, nb = self.n_edges, self.n_bins
+        pe = np.empty((ne, 3), np.uint64)
+        bins = {k: np.empty((ne, nb), np.uint32) for k in ("inflow", "tt_sum", "tt_cnt", "occ")}
+        _check(self.lib, self.lib.lpsim_link_stats(self.h, _p(pe), ne, *(_p(bins[k]) for k in
+                                                                         ("inflow", "tt_sum", "tt_cnt", "occ")), nb))
+        out = {"entries": pe[:, 0].copy(), "exits": pe[:, 1].copy(), "tt_steps": pe[:, 2].copy()}
+        out.update(bins)
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self.lib.lpsim_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

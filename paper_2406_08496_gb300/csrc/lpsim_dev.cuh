@@ -1,0 +1,129 @@
+// Internal device-side layout shared by the translation units of liblpsim.
+// Not part of the public ABI (include/lpsim.h).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lpsim {
+
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr uint8_t kEmpty = 0xFFu;
+
+// slot life cycle
+constexpr uint8_t kLive = 0;
+constexpr uint8_t kArrivedPending = 1;  // arrived this step: its cell is erased next step
+constexpr uint8_t kDead = 2;
+
+// per-step action of a live slot
+constexpr uint8_t kActStay = 0;
+constexpr uint8_t kActIntend = 1;
+constexpr uint8_t kActHold = 2;
+constexpr uint8_t kActCross = 3;
+constexpr uint8_t kActArrive = 4;
+
+// trip status (public)
+constexpr uint8_t kWaiting = 0;
+constexpr uint8_t kActive = 1;
+constexpr uint8_t kArrived = 2;
+
+// device error bits
+constexpr uint32_t kErrCellTaken = 1u;   // a lane-map cell written twice in one step
+constexpr uint32_t kErrSlotOverflow = 2u;
+
+// Edge record: one 16-byte load gives everything the car-following part needs.
+// Lane l, cell c of edge e lives at map[moff + l * stride(len) + c], stride =
+// len rounded up to 16 bytes so every lane row starts 16-byte aligned.
+struct __align__(16) EdgeRec {
+    uint32_t moff;   // lane-map byte offset of lane 0
+    uint16_t len;    // cells per lane
+    uint8_t lanes;   // 1..4
+    uint8_t arank;   // signal phase at the downstream node
+    float v0;        // speed limit (free-flow speed)
+    uint32_t dst;    // downstream node
+};
+
+struct __align__(8) NodeRec {
+    uint32_t green;  // green steps per phase (0 = uncontrolled)
+    uint8_t nphase;  // phases (1 + largest approach rank)
+    uint8_t nout;    // outgoing edges
+    uint16_t pad;
+};
+
+__host__ __device__ inline uint32_t row_stride(uint32_t len) { return (len + 15u) & ~15u; }
+
+struct Model {
+    float dt, a, s0, T, two_sqrt_ab, x0, g_a, g_b, alpha_i, alpha_a, alpha_b, eps_amp;
+    uint64_t seed;
+    uint32_t bin_steps, n_bins;
+};
+
+// Vehicle slots (structure of arrays).  x and v are double-buffered by step
+// parity: step k reads x[k&1] and writes x[(k+1)&1].
+struct Slots {
+    uint32_t *id, *e, *rpos, *rlast, *tent, *pcell, *imark;
+    uint8_t *lane, *flag, *act, *tl, *win;
+    float *x[2], *v[2];
+};
+
+struct Dev {
+    // network
+    const EdgeRec *edge;
+    const NodeRec *node;
+    const uint32_t *slot_off;  // first (edge, lane) claim slot of each edge
+    const uint8_t *orank;      // rank of the edge among the out-edges of its source
+    uint8_t *map[3];           // lane maps, step k reads map[k%3], writes map[(k+1)%3]
+    uint8_t *imap[2];          // lane-change intent marks of step k: imap[k&1]
+    uint32_t *claim;           // per (edge, lane): lowest id asking to enter this step
+    // trips, by vehicle id
+    const uint32_t *dep;       // departure step
+    const uint32_t *route;     // all routes, vehicle-id order
+    const uint32_t *roff;      // route start of vehicle id (n + 1 entries)
+    uint32_t *dep_act, *arr;
+    uint8_t *status;
+    // departure queues, one per origin edge
+    uint32_t n_org;
+    const uint32_t *org_edge, *org_qoff, *org_qend, *qid;
+    uint32_t *org_head;
+    uint8_t *dreq;             // requested lane this step (kEmpty = none)
+    // slots (current set: the host alternates two sets around each compaction)
+    Slots s;
+    uint32_t cap;              // slot capacity
+    // per-step lists, by step parity
+    uint32_t *cross_list[2], *intend_list[2];
+    uint32_t *counts;          // [0..1] cross count by parity, [2..3] intend count by parity
+    // statistics
+    unsigned long long *ent, *ext, *tts;
+    uint32_t *bin_in, *bin_tt, *bin_cnt, *bin_occ;
+    // run state
+    uint32_t *kbase;           // step of the first step of the current graph chunk
+    uint32_t *n_slots;         // slots in use
+    unsigned long long *ctr;   // [0] veh_steps, [1] arrived, [2] lane changes, [3] crossings + departures,
+                               // [4] departed
+    uint32_t *err;
+    Model m;
+};
+
+// kernels of a step; koff = offset of this step inside the chunk
+void launch_step(const Dev &d, uint32_t koff, int grid, int block, cudaStream_t st);
+void launch_chunk_end(const Dev &d, uint32_t steps, cudaStream_t st);
+
+// compaction (and optional sort by lane-map cell) of the slots after step k;
+// src/dst slot sets; writes *n_slots
+struct SortWork {
+    uint32_t *tile_cnt, *tile_off;   // per tile
+    uint32_t *key[2], *perm[2];      // radix sort ping-pong
+    uint32_t *hist;                  // 256 digits x tiles
+    uint32_t max_tiles;
+    uint32_t key_bits;
+};
+// returns the number of kernels launched
+int launch_compact(const Dev &d, const Slots &dst, const SortWork &w, uint32_t koff, bool sort, int grid,
+                   cudaStream_t st);
+uint32_t compact_tile();
+
+// helpers for the query functions
+void launch_state_scatter(const Dev &d, uint32_t k, float *x, float *v, uint32_t *edge, uint8_t *lane,
+                          uint32_t *ridx, cudaStream_t st);
+void launch_max_arrival(const Dev &d, uint64_t n, uint32_t *out, cudaStream_t st);
+
+}  // namespace lpsim

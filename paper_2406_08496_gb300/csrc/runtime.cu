@@ -1,0 +1,741 @@
+// Host runtime of liblpsim: the C ABI of include/lpsim.h.
+//
+// A context owns the device copy of the network (edge and node records,
+// three rotating lane maps, two intent maps, the per-(edge, lane) claim
+// slots), the trips in vehicle-id order (departure rank), the departure
+// queues of the origin edges, two sets of vehicle slots (the compaction
+// writes one set from the other), the link statistics and a few counters.
+// Steps run as CUDA-graph chunks of `chunk_steps` steps (three step kernels
+// per step plus a compaction, optionally a radix sort, every `sort_period`
+// steps); steps that do not fill an aligned chunk are launched one by one.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/lpsim.h"
+#include "lpsim_dev.cuh"
+
+using namespace lpsim;
+
+namespace {
+
+thread_local std::string g_last_error;
+std::mutex g_alloc_mu;
+void *(*g_alloc)(size_t, void *) = nullptr;
+void (*g_release)(void *, void *) = nullptr;
+void *g_alloc_user = nullptr;
+
+int fail(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+#define CU(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) return fail(LPSIM_E_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+}  // namespace
+
+struct lpsim_ctx {
+    int device = 0;
+    int n_sm = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    lpsim_params p{};
+    uint32_t n_nodes = 0, n_edges = 0;
+    // allocation
+    void *(*alloc)(size_t, void *) = nullptr;
+    void (*release)(void *, void *) = nullptr;
+    void *alloc_user = nullptr;
+    std::vector<void *> blocks;
+    // host mirror of the layout (queries)
+    std::vector<uint32_t> moff;
+    std::vector<uint16_t> len;
+    std::vector<uint8_t> lanes;
+    std::vector<uint32_t> src, dst;
+    uint64_t map_bytes = 0, canon_cells = 0, lane_slots = 0;
+    // device state
+    Dev d{};
+    Slots sets[2]{};
+    int cur = 0;
+    SortWork w{};
+    bool loaded = false;
+    uint64_t n_trips = 0;
+    uint32_t k = 0;
+    uint32_t R = 64, C = 384;
+    int grid = 0, block = 256;
+    bool sort = true;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    unsigned long long *h_ctr = nullptr;  // pinned: ctr[0..7], err, n_slots, ...
+    uint32_t *d_tmp = nullptr;
+    uint64_t launches = 0;
+    uint64_t stall_steps = 0;
+    unsigned long long last_progress = 0;
+
+    void *dalloc(size_t bytes) {
+        if (bytes == 0) bytes = 16;
+        bytes = (bytes + 255) & ~size_t(255);
+        void *ptr = nullptr;
+        if (alloc) {
+            ptr = alloc(bytes, alloc_user);
+        } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+            ptr = nullptr;
+        }
+        if (ptr) blocks.push_back(ptr);
+        return ptr;
+    }
+    ~lpsim_ctx() {
+        for (int i = 0; i < 2; i++)
+            if (graph[i]) cudaGraphExecDestroy(graph[i]);
+        if (stream) cudaStreamSynchronize(stream);
+        for (void *b : blocks) {
+            if (release) release(b, alloc_user);
+            else cudaFree(b);
+        }
+        if (h_ctr) cudaFreeHost(h_ctr);
+        if (own_stream) cudaStreamDestroy(stream);
+    }
+};
+
+namespace {
+
+template <class T>
+int dnew(lpsim_ctx *c, T *&out, size_t count) {
+    out = static_cast<T *>(c->dalloc(count * sizeof(T)));
+    if (!out) return fail(LPSIM_E_OOM, "device allocation of " + std::to_string(count * sizeof(T)) + " bytes failed");
+    return LPSIM_OK;
+}
+
+#define TRY(x)                 \
+    do {                       \
+        int rc_ = (x);         \
+        if (rc_ != LPSIM_OK) return rc_; \
+    } while (0)
+
+int check_params(const lpsim_params *p) {
+    if (!p) return fail(LPSIM_E_INVALID_ARG, "params is NULL");
+    if (!(p->dt > 0.0f) || !(p->a > 0.0f) || !(p->b > 0.0f) || !(p->s0 >= 0.0f) || !(p->x0 > 0.0f) ||
+        !std::isfinite(p->T) || !std::isfinite(p->g_a) || !std::isfinite(p->g_b) || !std::isfinite(p->alpha_i) ||
+        !std::isfinite(p->alpha_a) || !std::isfinite(p->alpha_b) || !(p->eps_amp >= 0.0f))
+        return fail(LPSIM_E_INVALID_ARG, "model parameter out of range");
+    if (p->bin_steps == 0 && p->n_bins != 0) return fail(LPSIM_E_INVALID_ARG, "n_bins without bin_steps");
+    if (p->block_size && p->block_size != 128 && p->block_size != 256 && p->block_size != 512)
+        return fail(LPSIM_E_INVALID_ARG, "block_size must be 0, 128, 256 or 512");
+    if (p->flags & ~1u) return fail(LPSIM_E_INVALID_ARG, "unknown flag bits");
+    return LPSIM_OK;
+}
+
+int upload(lpsim_ctx *c, void *dst, const void *src, size_t bytes) {
+    if (bytes) CU(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream));
+    return LPSIM_OK;
+}
+
+int alloc_slots(lpsim_ctx *c, Slots &s, uint32_t cap) {
+    TRY(dnew(c, s.id, cap));
+    TRY(dnew(c, s.e, cap));
+    TRY(dnew(c, s.rpos, cap));
+    TRY(dnew(c, s.rlast, cap));
+    TRY(dnew(c, s.tent, cap));
+    TRY(dnew(c, s.pcell, cap));
+    TRY(dnew(c, s.imark, cap));
+    TRY(dnew(c, s.lane, cap));
+    TRY(dnew(c, s.flag, cap));
+    TRY(dnew(c, s.act, cap));
+    TRY(dnew(c, s.tl, cap));
+    TRY(dnew(c, s.win, cap));
+    for (int i = 0; i < 2; i++) {
+        TRY(dnew(c, s.x[i], cap));
+        TRY(dnew(c, s.v[i], cap));
+    }
+    return LPSIM_OK;
+}
+
+// empty maps, waiting trips, cleared statistics, step 0
+int reset_state(lpsim_ctx *c) {
+    Dev &d = c->d;
+    cudaStream_t st = c->stream;
+    for (int i = 0; i < 3; i++) CU(cudaMemsetAsync(d.map[i], 0xFF, c->map_bytes, st));
+    for (int i = 0; i < 2; i++) CU(cudaMemsetAsync(d.imap[i], 0, c->map_bytes, st));
+    CU(cudaMemsetAsync(d.claim, 0xFF, c->lane_slots * 4, st));
+    CU(cudaMemsetAsync(d.ent, 0, c->n_edges * 8ull, st));
+    CU(cudaMemsetAsync(d.ext, 0, c->n_edges * 8ull, st));
+    CU(cudaMemsetAsync(d.tts, 0, c->n_edges * 8ull, st));
+    size_t nb = (size_t)c->n_edges * c->p.n_bins * 4;
+    if (nb) {
+        CU(cudaMemsetAsync(d.bin_in, 0, nb, st));
+        CU(cudaMemsetAsync(d.bin_tt, 0, nb, st));
+        CU(cudaMemsetAsync(d.bin_cnt, 0, nb, st));
+        CU(cudaMemsetAsync(d.bin_occ, 0, nb, st));
+    }
+    CU(cudaMemsetAsync(d.counts, 0, 4 * 4, st));
+    CU(cudaMemsetAsync(d.kbase, 0, 4, st));
+    CU(cudaMemsetAsync(d.n_slots, 0, 4, st));
+    CU(cudaMemsetAsync(d.ctr, 0, 8 * 8, st));
+    CU(cudaMemsetAsync(d.err, 0, 4, st));
+    if (c->loaded) {
+        CU(cudaMemsetAsync(d.dep_act, 0xFF, c->n_trips * 4, st));
+        CU(cudaMemsetAsync(d.arr, 0xFF, c->n_trips * 4, st));
+        CU(cudaMemsetAsync(d.status, 0, c->n_trips, st));
+        CU(cudaMemsetAsync(d.org_head, 0, (size_t)d.n_org * 4, st));
+    }
+    c->k = 0;
+    c->cur = 0;
+    c->d.s = c->sets[0];
+    c->stall_steps = 0;
+    c->last_progress = 0;
+    CU(cudaStreamSynchronize(st));
+    return LPSIM_OK;
+}
+
+int read_status(lpsim_ctx *c) {
+    // h_ctr: [0..7] counters, [8] err, [9] n_slots
+    CU(cudaMemcpyAsync(c->h_ctr, c->d.ctr, 8 * 8, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(c->h_ctr + 8, c->d.err, 4, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(c->h_ctr + 9, c->d.n_slots, 4, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    uint32_t err = (uint32_t)(c->h_ctr[8] & 0xFFFFFFFFull);
+    if (err & kErrCellTaken) return fail(LPSIM_E_INVARIANT, "two vehicles were written to one lane-map cell");
+    if (err & kErrSlotOverflow) return fail(LPSIM_E_INVARIANT, "vehicle slot capacity exceeded");
+    return LPSIM_OK;
+}
+
+// one step launched directly (kbase == k on entry; kbase == k+1 after)
+int direct_step(lpsim_ctx *c) {
+    Dev d = c->d;
+    d.s = c->sets[c->cur];
+    launch_step(d, 0, c->grid, c->block, c->stream);
+    c->launches += 3;
+    if ((c->k + 1) % c->R == 0) {
+        c->launches += launch_compact(d, c->sets[c->cur ^ 1], c->w, 0, c->sort, c->grid, c->stream);
+        c->cur ^= 1;
+    }
+    launch_chunk_end(d, 1, c->stream);
+    c->launches += 1;
+    CU(cudaGetLastError());
+    c->k += 1;
+    return LPSIM_OK;
+}
+
+int capture_chunk(lpsim_ctx *c, int start_set) {
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    int cur = start_set;
+    Dev d = c->d;
+    for (uint32_t koff = 0; koff < c->C; koff++) {
+        d.s = c->sets[cur];
+        launch_step(d, koff, c->grid, c->block, c->stream);
+        if ((koff + 1) % c->R == 0) {
+            launch_compact(d, c->sets[cur ^ 1], c->w, koff, c->sort, c->grid, c->stream);
+            cur ^= 1;
+        }
+    }
+    launch_chunk_end(d, c->C, c->stream);
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (e != cudaSuccess) return fail(LPSIM_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c->graph[start_set], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(LPSIM_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    if (cur != start_set) return fail(LPSIM_E_STATE, "chunk must hold an even number of compactions");
+    return LPSIM_OK;
+}
+
+// kernels per chunk (for the launch counter)
+uint64_t chunk_launches(const lpsim_ctx *c) {
+    uint64_t per_compact = 3;
+    if (c->sort) per_compact = 2 + 1 + 3ull * ((c->w.key_bits + 7) / 8) + 1;
+    return 3ull * c->C + (c->C / c->R) * per_compact + 1;
+}
+
+int chunk(lpsim_ctx *c) {
+    if (!c->graph[c->cur]) TRY(capture_chunk(c, c->cur));
+    CU(cudaGraphLaunch(c->graph[c->cur], c->stream));
+    c->launches += chunk_launches(c);
+    c->k += c->C;
+    return LPSIM_OK;
+}
+
+// Run up to n steps; stop early once every trip has arrived (if stop_done).
+// Returns steps actually taken in *taken.
+int run_steps(lpsim_ctx *c, uint64_t n, bool stop_done, uint64_t *taken) {
+    const uint32_t k0 = c->k;
+    uint64_t left = n;
+    while (left > 0) {
+        if (stop_done) {
+            TRY(read_status(c));
+            if (c->h_ctr[1] >= c->n_trips) break;
+        }
+        uint64_t before = c->k;
+        if (c->k % c->C == 0 && left >= c->C) {
+            TRY(chunk(c));
+        } else {
+            uint32_t todo = (uint32_t)std::min<uint64_t>(left, c->k % c->C == 0 ? left : c->C - c->k % c->C);
+            for (uint32_t j = 0; j < todo; j++) TRY(direct_step(c));
+        }
+        left -= c->k - before;
+        TRY(read_status(c));
+        // gridlock watch: vehicles on the network and no crossing, departure or arrival
+        unsigned long long prog = c->h_ctr[1] + c->h_ctr[3];
+        unsigned long long active = c->h_ctr[4] - c->h_ctr[1];
+        if (prog != c->last_progress || active == 0) {
+            c->last_progress = prog;
+            c->stall_steps = 0;
+        } else {
+            c->stall_steps += c->k - before;
+            if (c->p.gridlock_steps && c->stall_steps >= c->p.gridlock_steps)
+                return fail(LPSIM_E_GRIDLOCK, "no vehicle crossed, departed or arrived for " +
+                                                  std::to_string(c->stall_steps) + " steps");
+        }
+        if (stop_done && c->h_ctr[1] >= c->n_trips) break;
+    }
+    if (stop_done) {
+        TRY(read_status(c));
+        if (c->h_ctr[1] >= c->n_trips && c->n_trips > 0) {
+            // the last chunk may have run past the last arrival; nothing moves
+            // after it, so only the step counter needs to come back
+            CU(cudaMemsetAsync(c->d_tmp, 0, 4, c->stream));
+            launch_max_arrival(c->d, c->n_trips, c->d_tmp, c->stream);
+            uint32_t kfin = 0;
+            CU(cudaMemcpyAsync(&kfin, c->d_tmp, 4, cudaMemcpyDeviceToHost, c->stream));
+            CU(cudaStreamSynchronize(c->stream));
+            if (kfin < c->k && kfin >= k0) {
+                c->k = kfin;
+                CU(cudaMemcpyAsync(c->d.kbase, &c->k, 4, cudaMemcpyHostToDevice, c->stream));
+                CU(cudaStreamSynchronize(c->stream));
+            } else if (kfin < k0) {
+                c->k = std::max(c->k, k0);
+            }
+        }
+    }
+    *taken = c->k - k0;
+    return LPSIM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lpsim_last_error(void) { return g_last_error.c_str(); }
+
+const char *lpsim_version(void) { return "lpsim-gb300 1.0 (sm_103a)"; }
+
+int lpsim_set_allocator(void *(*alloc)(size_t, void *), void (*release)(void *, void *), void *user) {
+    if ((alloc == nullptr) != (release == nullptr)) return fail(LPSIM_E_INVALID_ARG, "give both callbacks or neither");
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc = alloc;
+    g_release = release;
+    g_alloc_user = user;
+    return LPSIM_OK;
+}
+
+int lpsim_load_network(lpsim_ctx **out, const lpsim_network *net, const lpsim_params *p, void *stream) {
+    if (!out) return fail(LPSIM_E_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    TRY(check_params(p));
+    if (!net || !net->edge_src || !net->edge_dst || !net->edge_len_m || !net->edge_lanes || !net->edge_vmax ||
+        !net->node_green_steps)
+        return fail(LPSIM_E_INVALID_ARG, "network array is NULL");
+    const uint32_t nn = net->n_nodes, ne = net->n_edges;
+    if (nn == 0 || ne == 0) return fail(LPSIM_E_INVALID_ARG, "empty network");
+    std::vector<uint32_t> n_in(nn, 0), n_out(nn, 0);
+    std::vector<uint8_t> orank(ne), arank(ne);
+    std::vector<EdgeRec> er(ne);
+    std::vector<uint32_t> slot_off(ne);
+    std::vector<uint16_t> lens(ne);
+    std::vector<uint32_t> moffs(ne);
+    uint64_t cells = 0, slots = 0, canon = 0;
+    for (uint32_t e = 0; e < ne; e++) {
+        if (net->edge_src[e] >= nn || net->edge_dst[e] >= nn)
+            return fail(LPSIM_E_INVALID_ARG, "edge " + std::to_string(e) + ": node id out of range");
+        if (net->edge_lanes[e] < 1 || net->edge_lanes[e] > 4)
+            return fail(LPSIM_E_INVALID_ARG, "edge " + std::to_string(e) + ": lanes must be 1..4");
+        float L = net->edge_len_m[e];
+        if (!(L > 0.0f) || !(L <= 65535.0f))
+            return fail(LPSIM_E_INVALID_ARG, "edge " + std::to_string(e) + ": length must be in (0, 65535] m");
+        float vm = net->edge_vmax[e];
+        if (!(vm > 0.0f) || !(vm <= 254.0f))
+            return fail(LPSIM_E_INVALID_ARG, "edge " + std::to_string(e) + ": speed limit must be in (0, 254] m/s");
+        uint32_t len = (uint32_t)std::ceil(L);
+        if (len < 1) len = 1;
+        orank[e] = (uint8_t)n_out[net->edge_src[e]];
+        if (++n_out[net->edge_src[e]] > 255) return fail(LPSIM_E_INVALID_ARG, "node with more than 255 out-edges");
+        uint32_t rank = n_in[net->edge_dst[e]];
+        if (++n_in[net->edge_dst[e]] > 255) return fail(LPSIM_E_INVALID_ARG, "node with more than 255 in-edges");
+        arank[e] = net->edge_approach_rank ? net->edge_approach_rank[e] : (uint8_t)rank;
+        lens[e] = (uint16_t)len;
+        moffs[e] = (uint32_t)cells;
+        er[e].moff = (uint32_t)cells;
+        er[e].len = (uint16_t)len;
+        er[e].lanes = net->edge_lanes[e];
+        er[e].v0 = vm;
+        er[e].dst = net->edge_dst[e];
+        cells += (uint64_t)row_stride(len) * net->edge_lanes[e];
+        canon += (uint64_t)len * net->edge_lanes[e];
+        slot_off[e] = (uint32_t)slots;
+        slots += net->edge_lanes[e];
+        if (cells >= 0xFFFFFFF0ull) return fail(LPSIM_E_INVALID_ARG, "lane map larger than 4 GiB");
+    }
+    std::vector<NodeRec> nr(nn);
+    for (uint32_t i = 0; i < nn; i++) {
+        nr[i].green = net->node_green_steps[i];
+        nr[i].nphase = 0;
+        nr[i].nout = (uint8_t)n_out[i];
+        nr[i].pad = 0;
+    }
+    for (uint32_t e = 0; e < ne; e++) {
+        uint32_t node = net->edge_dst[e];
+        if (arank[e] >= n_in[node])
+            return fail(LPSIM_E_INVALID_ARG, "edge " + std::to_string(e) + ": approach rank not below in-degree");
+        er[e].arank = arank[e];
+        if ((uint32_t)arank[e] + 1 > nr[node].nphase) nr[node].nphase = (uint8_t)(arank[e] + 1);
+    }
+
+    lpsim_ctx *c = new (std::nothrow) lpsim_ctx();
+    if (!c) return fail(LPSIM_E_OOM, "host allocation failed");
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        c->alloc = g_alloc;
+        c->release = g_release;
+        c->alloc_user = g_alloc_user;
+    }
+    auto bail = [&](int rc) {
+        delete c;
+        return rc;
+    };
+    if (cudaGetDevice(&c->device) != cudaSuccess) return bail(fail(LPSIM_E_CUDA, "no CUDA device"));
+    cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device);
+    c->stream = static_cast<cudaStream_t>(stream);
+    if (!c->stream) {
+        // graph capture needs a stream other than the legacy default stream
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(fail(LPSIM_E_CUDA, "cannot create a stream"));
+        c->own_stream = true;
+    }
+    c->p = *p;
+    c->n_nodes = nn;
+    c->n_edges = ne;
+    c->moff = moffs;
+    c->len = lens;
+    c->lanes.assign(net->edge_lanes, net->edge_lanes + ne);
+    c->src.assign(net->edge_src, net->edge_src + ne);
+    c->dst.assign(net->edge_dst, net->edge_dst + ne);
+    c->map_bytes = cells + 16;
+    c->canon_cells = canon;
+    c->lane_slots = slots;
+    c->R = p->sort_period ? p->sort_period : 64;
+    uint32_t base = 2 * c->R;
+    base = base % 3 == 0 ? base : base * 3;  // chunk = multiple of 2R and of 3 (lane-map rotation)
+    uint32_t want = p->chunk_steps ? p->chunk_steps : 384;
+    c->C = std::max(base, (want + base - 1) / base * base);
+    c->block = p->block_size ? (int)p->block_size : 256;
+    c->grid = c->n_sm * (int)(p->blocks_per_sm ? p->blocks_per_sm : 4) * 256 / c->block;
+    if (c->grid < 1) c->grid = 1;
+    c->sort = (p->flags & 1u) == 0;
+
+    Dev &d = c->d;
+    d.m.dt = p->dt;
+    d.m.a = p->a;
+    d.m.s0 = p->s0;
+    d.m.T = p->T;
+    d.m.two_sqrt_ab = (float)(2.0 * std::sqrt((double)p->a * (double)p->b));
+    d.m.x0 = p->x0;
+    d.m.g_a = p->g_a;
+    d.m.g_b = p->g_b;
+    d.m.alpha_i = p->alpha_i;
+    d.m.alpha_a = p->alpha_a;
+    d.m.alpha_b = p->alpha_b;
+    d.m.eps_amp = p->eps_amp;
+    d.m.seed = p->seed;
+    d.m.bin_steps = p->bin_steps;
+    d.m.n_bins = p->n_bins;
+
+    EdgeRec *edge = nullptr;
+    NodeRec *node = nullptr;
+    uint32_t *so = nullptr;
+    uint8_t *ork = nullptr;
+    int rc;
+    if ((rc = dnew(c, edge, ne)) || (rc = dnew(c, node, nn)) || (rc = dnew(c, so, ne)) || (rc = dnew(c, ork, ne)))
+        return bail(rc);
+    d.edge = edge;
+    d.node = node;
+    d.slot_off = so;
+    d.orank = ork;
+    for (int i = 0; i < 3; i++)
+        if ((rc = dnew(c, d.map[i], c->map_bytes))) return bail(rc);
+    for (int i = 0; i < 2; i++)
+        if ((rc = dnew(c, d.imap[i], c->map_bytes))) return bail(rc);
+    if ((rc = dnew(c, d.claim, slots)) || (rc = dnew(c, d.ent, ne)) || (rc = dnew(c, d.ext, ne)) ||
+        (rc = dnew(c, d.tts, ne)))
+        return bail(rc);
+    size_t nb = (size_t)ne * p->n_bins;
+    if ((rc = dnew(c, d.bin_in, nb)) || (rc = dnew(c, d.bin_tt, nb)) || (rc = dnew(c, d.bin_cnt, nb)) ||
+        (rc = dnew(c, d.bin_occ, nb)))
+        return bail(rc);
+    if ((rc = dnew(c, d.counts, 4)) || (rc = dnew(c, d.kbase, 1)) || (rc = dnew(c, d.n_slots, 1)) ||
+        (rc = dnew(c, d.ctr, 8)) || (rc = dnew(c, d.err, 1)) || (rc = dnew(c, c->d_tmp, 4)))
+        return bail(rc);
+    if (cudaMallocHost(&c->h_ctr, 16 * 8) != cudaSuccess) return bail(fail(LPSIM_E_OOM, "pinned allocation failed"));
+    if ((rc = upload(c, edge, er.data(), ne * sizeof(EdgeRec))) || (rc = upload(c, node, nr.data(), nn * sizeof(NodeRec))) ||
+        (rc = upload(c, so, slot_off.data(), ne * 4)) || (rc = upload(c, ork, orank.data(), ne)))
+        return bail(rc);
+    // key bits of the radix sort: enough for every lane-map cell index
+    uint32_t bits = 1;
+    while (bits < 32 && (1ull << bits) < c->map_bytes) bits++;
+    c->w.key_bits = bits;
+    if ((rc = reset_state(c))) return bail(rc);
+    *out = c;
+    return LPSIM_OK;
+}
+
+int lpsim_load_demand(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, const uint64_t *route_off,
+                      const uint32_t *route_edges, uint32_t *out_vid) {
+    if (!c) return fail(LPSIM_E_INVALID_ARG, "ctx is NULL");
+    if (c->loaded) return fail(LPSIM_E_STATE, "demand already loaded");
+    if (n == 0) return fail(LPSIM_E_INVALID_ARG, "no trips");
+    if (!depart_step || !route_off || !route_edges) return fail(LPSIM_E_INVALID_ARG, "trip array is NULL");
+    if (n >= 0xFFFFFFF0ull) return fail(LPSIM_E_INVALID_ARG, "too many trips");
+    if (route_off[0] != 0) return fail(LPSIM_E_INVALID_ARG, "route_off[0] must be 0");
+    for (uint64_t j = 0; j < n; j++)
+        if (route_off[j + 1] <= route_off[j])
+            return fail(LPSIM_E_INVALID_ARG, "trip " + std::to_string(j) + ": empty route or route_off not increasing");
+    const uint64_t total = route_off[n];
+    if (total >= 0xFFFFFFF0ull) return fail(LPSIM_E_INVALID_ARG, "total route length must stay below 2^32");
+    for (uint64_t j = 0; j < n; j++) {
+        for (uint64_t q = route_off[j]; q < route_off[j + 1]; q++) {
+            uint32_t e = route_edges[q];
+            if (e >= c->n_edges) return fail(LPSIM_E_INVALID_ARG, "trip " + std::to_string(j) + ": edge id out of range");
+            if (q > route_off[j] && c->dst[route_edges[q - 1]] != c->src[e])
+                return fail(LPSIM_E_INVALID_ARG, "trip " + std::to_string(j) + ": route edges are not contiguous");
+        }
+    }
+    // vehicle ids: stable sort by departure step
+    std::vector<uint32_t> order(n);
+    std::iota(order.begin(), order.end(), 0u);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](uint32_t a, uint32_t b) { return depart_step[a] < depart_step[b]; });
+    std::vector<uint32_t> dep(n), roff(n + 1), route(total ? total : 1);
+    roff[0] = 0;
+    for (uint64_t id = 0; id < n; id++) {
+        uint32_t j = order[id];
+        dep[id] = depart_step[j];
+        uint64_t L = route_off[j + 1] - route_off[j];
+        std::memcpy(route.data() + roff[id], route_edges + route_off[j], L * 4);
+        roff[id + 1] = (uint32_t)(roff[id] + L);
+        if (out_vid) out_vid[j] = (uint32_t)id;
+    }
+    // departure queues: ids grouped by first edge, ascending within a group
+    std::vector<uint32_t> cnt(c->n_edges + 1, 0);
+    for (uint64_t id = 0; id < n; id++) cnt[route[roff[id]] + 1]++;
+    std::vector<uint32_t> org_edge, org_qoff, org_qend;
+    for (uint32_t e = 0; e < c->n_edges; e++) {
+        if (cnt[e + 1]) {
+            org_edge.push_back(e);
+            org_qoff.push_back(cnt[e]);
+            org_qend.push_back(cnt[e] + cnt[e + 1]);
+        }
+        cnt[e + 1] += cnt[e];
+    }
+    std::vector<uint32_t> qid(n);
+    {
+        std::vector<uint32_t> fill(cnt.begin(), cnt.end() - 1);
+        for (uint64_t id = 0; id < n; id++) qid[fill[route[roff[id]]]++] = (uint32_t)id;
+    }
+    Dev &d = c->d;
+    const uint32_t norg = (uint32_t)org_edge.size();
+    uint32_t *ddep, *droute, *droff, *oe, *oq, *oqe, *dqid;
+    TRY(dnew(c, ddep, n));
+    TRY(dnew(c, droute, route.size()));
+    TRY(dnew(c, droff, n + 1));
+    TRY(dnew(c, d.dep_act, n));
+    TRY(dnew(c, d.arr, n));
+    TRY(dnew(c, d.status, n));
+    TRY(dnew(c, oe, norg));
+    TRY(dnew(c, oq, norg));
+    TRY(dnew(c, oqe, norg));
+    TRY(dnew(c, dqid, n));
+    TRY(dnew(c, d.org_head, norg));
+    TRY(dnew(c, d.dreq, norg));
+    const uint32_t cap = (uint32_t)n;
+    for (int i = 0; i < 2; i++) TRY(alloc_slots(c, c->sets[i], cap));
+    for (int i = 0; i < 2; i++) {
+        TRY(dnew(c, d.cross_list[i], cap));
+        TRY(dnew(c, d.intend_list[i], cap));
+    }
+    uint32_t max_tiles = (cap + compact_tile() - 1) / compact_tile() + 1;
+    c->w.max_tiles = max_tiles;
+    TRY(dnew(c, c->w.tile_cnt, max_tiles));
+    TRY(dnew(c, c->w.tile_off, max_tiles + 2));
+    TRY(dnew(c, c->w.hist, 256ull * max_tiles));
+    for (int i = 0; i < 2; i++) {
+        TRY(dnew(c, c->w.key[i], cap));
+        TRY(dnew(c, c->w.perm[i], cap));
+    }
+    TRY(upload(c, ddep, dep.data(), n * 4));
+    TRY(upload(c, droute, route.data(), route.size() * 4));
+    TRY(upload(c, droff, roff.data(), (n + 1) * 4));
+    TRY(upload(c, oe, org_edge.data(), norg * 4ull));
+    TRY(upload(c, oq, org_qoff.data(), norg * 4ull));
+    TRY(upload(c, oqe, org_qend.data(), norg * 4ull));
+    TRY(upload(c, dqid, qid.data(), n * 4));
+    d.dep = ddep;
+    d.route = droute;
+    d.roff = droff;
+    d.n_org = norg;
+    d.org_edge = oe;
+    d.org_qoff = oq;
+    d.org_qend = oqe;
+    d.qid = dqid;
+    d.cap = cap;
+    c->n_trips = n;
+    c->loaded = true;
+    TRY(reset_state(c));  // synchronises: the host vectors above may go away
+    return LPSIM_OK;
+}
+
+int lpsim_step(lpsim_ctx *c, uint32_t n_steps) {
+    if (!c) return fail(LPSIM_E_INVALID_ARG, "ctx is NULL");
+    if (!c->loaded) return fail(LPSIM_E_STATE, "lpsim_load_demand has not been called");
+    uint64_t taken = 0;
+    TRY(run_steps(c, n_steps, false, &taken));
+    return read_status(c);
+}
+
+int lpsim_run(lpsim_ctx *c, uint32_t max_steps, lpsim_run_result *out) {
+    if (!c) return fail(LPSIM_E_INVALID_ARG, "ctx is NULL");
+    if (!c->loaded) return fail(LPSIM_E_STATE, "lpsim_load_demand has not been called");
+    auto t0 = std::chrono::steady_clock::now();
+    TRY(read_status(c));
+    unsigned long long vs0 = c->h_ctr[0];
+    uint64_t taken = 0;
+    TRY(run_steps(c, max_steps, true, &taken));
+    TRY(read_status(c));
+    auto t1 = std::chrono::steady_clock::now();
+    if (out) {
+        out->steps = taken;
+        out->veh_steps = c->h_ctr[0] - vs0;
+        out->arrived = c->h_ctr[1];
+        out->active = c->h_ctr[4] - c->h_ctr[1];
+        out->waiting = c->n_trips - c->h_ctr[4];
+        out->k = c->k;
+        out->wall_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    }
+    return LPSIM_OK;
+}
+
+int lpsim_reset(lpsim_ctx *c) {
+    if (!c) return fail(LPSIM_E_INVALID_ARG, "ctx is NULL");
+    return reset_state(c);
+}
+
+int lpsim_link_stats(lpsim_ctx *c, lpsim_link_stat *out, uint64_t n_edges, uint32_t *bin_inflow, uint32_t *bin_tt_sum,
+                     uint32_t *bin_tt_cnt, uint32_t *bin_occ, uint32_t n_bins) {
+    if (!c) return fail(LPSIM_E_INVALID_ARG, "ctx is NULL");
+    if (n_edges != c->n_edges) return fail(LPSIM_E_INVALID_ARG, "n_edges does not match the network");
+    if ((bin_inflow || bin_tt_sum || bin_tt_cnt || bin_occ) && n_bins != c->p.n_bins)
+        return fail(LPSIM_E_INVALID_ARG, "n_bins does not match the context");
+    CU(cudaStreamSynchronize(c->stream));
+    if (out) {
+        std::vector<unsigned long long> a(c->n_edges), b(c->n_edges), t(c->n_edges);
+        CU(cudaMemcpy(a.data(), c->d.ent, c->n_edges * 8ull, cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(b.data(), c->d.ext, c->n_edges * 8ull, cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(t.data(), c->d.tts, c->n_edges * 8ull, cudaMemcpyDeviceToHost));
+        for (uint32_t e = 0; e < c->n_edges; e++) out[e] = lpsim_link_stat{a[e], b[e], t[e]};
+    }
+    size_t nb = (size_t)c->n_edges * c->p.n_bins * 4;
+    if (nb) {
+        if (bin_inflow) CU(cudaMemcpy(bin_inflow, c->d.bin_in, nb, cudaMemcpyDeviceToHost));
+        if (bin_tt_sum) CU(cudaMemcpy(bin_tt_sum, c->d.bin_tt, nb, cudaMemcpyDeviceToHost));
+        if (bin_tt_cnt) CU(cudaMemcpy(bin_tt_cnt, c->d.bin_cnt, nb, cudaMemcpyDeviceToHost));
+        if (bin_occ) CU(cudaMemcpy(bin_occ, c->d.bin_occ, nb, cudaMemcpyDeviceToHost));
+    }
+    return LPSIM_OK;
+}
+
+int lpsim_get_trips(lpsim_ctx *c, uint64_t n, uint32_t *depart_actual, uint32_t *arrive_step) {
+    if (!c) return fail(LPSIM_E_INVALID_ARG, "ctx is NULL");
+    if (!c->loaded) return fail(LPSIM_E_STATE, "lpsim_load_demand has not been called");
+    if (n != c->n_trips) return fail(LPSIM_E_INVALID_ARG, "n does not match the trips loaded");
+    CU(cudaStreamSynchronize(c->stream));
+    if (depart_actual) CU(cudaMemcpy(depart_actual, c->d.dep_act, n * 4, cudaMemcpyDeviceToHost));
+    if (arrive_step) CU(cudaMemcpy(arrive_step, c->d.arr, n * 4, cudaMemcpyDeviceToHost));
+    return LPSIM_OK;
+}
+
+int lpsim_get_state(lpsim_ctx *c, uint64_t n, float *x, float *v, uint32_t *edge, uint8_t *lane, uint32_t *ridx,
+                    uint8_t *status) {
+    if (!c) return fail(LPSIM_E_INVALID_ARG, "ctx is NULL");
+    if (!c->loaded) return fail(LPSIM_E_STATE, "lpsim_load_demand has not been called");
+    if (n != c->n_trips) return fail(LPSIM_E_INVALID_ARG, "n does not match the trips loaded");
+    // scratch: x, v, edge, ridx (4 B each) and lane (1 B) per vehicle
+    uint8_t *tmp = static_cast<uint8_t *>(c->dalloc(n * 17 + 64));
+    if (!tmp) return fail(LPSIM_E_OOM, "device scratch allocation failed");
+    float *dx = reinterpret_cast<float *>(tmp);
+    float *dv = dx + n;
+    uint32_t *de = reinterpret_cast<uint32_t *>(dv + n);
+    uint32_t *dr = de + n;
+    uint8_t *dl = reinterpret_cast<uint8_t *>(dr + n);
+    CU(cudaMemsetAsync(tmp, 0, n * 17, c->stream));
+    CU(cudaMemsetAsync(de, 0xFF, n * 4, c->stream));
+    Dev d = c->d;
+    d.s = c->sets[c->cur];
+    launch_state_scatter(d, c->k, dx, dv, de, dl, dr, c->stream);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(c->stream));
+    if (x) CU(cudaMemcpy(x, dx, n * 4, cudaMemcpyDeviceToHost));
+    if (v) CU(cudaMemcpy(v, dv, n * 4, cudaMemcpyDeviceToHost));
+    if (edge) CU(cudaMemcpy(edge, de, n * 4, cudaMemcpyDeviceToHost));
+    if (ridx) CU(cudaMemcpy(ridx, dr, n * 4, cudaMemcpyDeviceToHost));
+    if (lane) CU(cudaMemcpy(lane, dl, n, cudaMemcpyDeviceToHost));
+    if (status) CU(cudaMemcpy(status, c->d.status, n, cudaMemcpyDeviceToHost));
+    // give the scratch back
+    if (!c->blocks.empty() && c->blocks.back() == tmp) {
+        c->blocks.pop_back();
+        if (c->release) c->release(tmp, c->alloc_user);
+        else cudaFree(tmp);
+    }
+    return LPSIM_OK;
+}
+
+uint64_t lpsim_lane_map_size(const lpsim_ctx *c) { return c ? c->canon_cells : 0; }
+
+int lpsim_get_lane_map(lpsim_ctx *c, uint8_t *out, uint64_t size) {
+    if (!c || !out) return fail(LPSIM_E_INVALID_ARG, "NULL argument");
+    if (size != c->canon_cells) return fail(LPSIM_E_INVALID_ARG, "size must equal lpsim_lane_map_size()");
+    CU(cudaStreamSynchronize(c->stream));
+    std::vector<uint8_t> m(c->map_bytes);
+    CU(cudaMemcpy(m.data(), c->d.map[c->k % 3], c->map_bytes, cudaMemcpyDeviceToHost));
+    uint64_t o = 0;
+    for (uint32_t e = 0; e < c->n_edges; e++) {
+        uint32_t stride = row_stride(c->len[e]);
+        for (uint32_t l = 0; l < c->lanes[e]; l++) {
+            std::memcpy(out + o, m.data() + c->moff[e] + (uint64_t)l * stride, c->len[e]);
+            o += c->len[e];
+        }
+    }
+    return LPSIM_OK;
+}
+
+int lpsim_get_counters(lpsim_ctx *c, lpsim_counters *out) {
+    if (!c || !out) return fail(LPSIM_E_INVALID_ARG, "NULL argument");
+    TRY(read_status(c));
+    out->k = c->k;
+    out->veh_steps = c->h_ctr[0];
+    out->arrived = c->h_ctr[1];
+    out->active = c->h_ctr[4] - c->h_ctr[1];
+    out->waiting = c->n_trips - c->h_ctr[4];
+    out->lane_changes = c->h_ctr[2];
+    out->slots = c->h_ctr[9] & 0xFFFFFFFFull;
+    out->launches = c->launches;
+    return LPSIM_OK;
+}
+
+void lpsim_destroy(lpsim_ctx *c) { delete c; }
+
+}  // extern "C"

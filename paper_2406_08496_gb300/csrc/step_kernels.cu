@@ -1,0 +1,548 @@
+// Per-step kernels of the vehicle update (Algorithm 1, Sec. 3.1-3.2).
+//
+// One step k is three launches:
+//   step_p1  every live vehicle: leader search in the step-k lane map,
+//            IDM / free-flow speed, move with the no-crash clamp, and the
+//            decision at the edge end (arrive, ask to cross, hold at the stop
+//            line) or the lane-change intent; writes its step-k+1 cell into
+//            the next map when it stays; posts entry claims (atomicMin of the
+//            vehicle id on the (edge, lane) slot).  Origin edges post the
+//            departure claim of their queue head.
+//   step_p2  crossers and departures: the lowest id of each claimed slot
+//            enters cell 0; the others stop at the stop line.
+//   step_p3  lane-change intenders: gap acceptance against the step-k map and
+//            against the reservations of step_p1/step_p2; the accepted move
+//            their next-map byte sideways.  Claims are reset.
+//
+// Three lane maps rotate: step k reads map[k%3] and writes map[(k+1)%3];
+// map[(k+2)%3] still holds the cells of step k-1, which step_p1 erases (each
+// vehicle remembers its previous cell), so no step needs a full clear.  The
+// intent marks (one byte per cell, imap[k&1]) let an intender see that a
+// cell was reserved by another intender even if that one has already moved
+// its byte sideways: the result is the same as judging every intender
+// against one snapshot, whatever the order the threads run in.
+//
+// Every floating-point expression is written in the same operation order as
+// the rules state; the library is compiled with -fmad=false -prec-div=true
+// -ftz=false, so each operation is one IEEE binary32 rounding.
+#include "lpsim_dev.cuh"
+
+namespace lpsim {
+
+namespace {
+
+__device__ __forceinline__ uint64_t splitmix64_mix(uint64_t z) {
+    // SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014)
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ float unit24(uint64_t h) {
+    return (float)(uint32_t)(h >> 40) * (1.0f / 16777216.0f);
+}
+
+__device__ __forceinline__ uint64_t lc_hash(uint64_t seed, uint32_t id, uint32_t k) {
+    return splitmix64_mix(seed ^ ((uint64_t)id * 0x9E3779B97F4A7C15ull) ^ ((uint64_t)k * 0xD1B54A32D192ED03ull));
+}
+
+__device__ __forceinline__ float fmax0(float t) { return t > 0.0f ? t : 0.0f; }
+
+__device__ __forceinline__ uint8_t speed_byte(float v) {
+    float t = v < 254.0f ? v : 254.0f;
+    return (uint8_t)(uint32_t)t;
+}
+
+// 16-bit mask of the occupied bytes of a 16-byte chunk.
+__device__ __forceinline__ uint32_t occ_mask16(uint4 q) {
+    uint32_t w[4] = {q.x, q.y, q.z, q.w};
+    uint32_t m = 0;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        uint32_t b = __vcmpne4(w[j], 0xFFFFFFFFu);  // 0xFF per occupied byte
+        uint32_t bits = ((b >> 7) & 1u) | ((b >> 14) & 2u) | ((b >> 21) & 4u) | ((b >> 28) & 8u);
+        m |= bits << (4 * j);
+    }
+    return m;
+}
+
+__device__ __forceinline__ uint32_t range_mask16(uint32_t c, uint32_t lo, uint32_t hi) {
+    // bits of chunk [c, c+16) that fall in [lo, hi]
+    uint32_t a = lo > c ? lo - c : 0u;
+    uint32_t b = hi < c + 15u ? hi - c : 15u;
+    return ((0xFFFFu << a) & (0xFFFFu >> (15u - b))) & 0xFFFFu;
+}
+
+// first occupied cell in [lo, hi] of a 16-byte aligned row, or kNone
+__device__ __forceinline__ uint32_t first_occupied(const uint8_t *row, uint32_t lo, uint32_t hi) {
+    if (lo > hi) return kNone;
+    for (uint32_t c = lo & ~15u; c <= hi; c += 16u) {
+        uint32_t m = occ_mask16(*reinterpret_cast<const uint4 *>(row + c)) & range_mask16(c, lo, hi);
+        if (m) return c + (uint32_t)(__ffs((int)m) - 1);
+    }
+    return kNone;
+}
+
+// last occupied cell in [lo, hi], or kNone
+__device__ __forceinline__ uint32_t last_occupied(const uint8_t *row, uint32_t lo, uint32_t hi) {
+    if (lo > hi) return kNone;
+    for (int c = (int)(hi & ~15u); c >= (int)(lo & ~15u); c -= 16) {
+        uint32_t m = occ_mask16(*reinterpret_cast<const uint4 *>(row + c)) & range_mask16((uint32_t)c, lo, hi);
+        if (m) return (uint32_t)c + (31u - (uint32_t)__clz((int)m));
+    }
+    return kNone;
+}
+
+__device__ __forceinline__ float idm_speed(const Model &m, float v, float vf, float s, float v0) {
+    float dv = v - vf;
+    float z = v * m.T + (v * dv) / m.two_sqrt_ab;
+    float s_star = m.s0 + fmax0(z);
+    float r = v / v0;
+    float q = s_star / s;
+    float acc = m.a * ((1.0f - (r * r) * (r * r)) - q * q);
+    return fmax0(v + acc * m.dt);
+}
+
+__device__ __forceinline__ bool is_green(const NodeRec &nr, uint32_t arank, uint32_t k) {
+    if (nr.green == 0) return true;
+    return (k / nr.green) % nr.nphase == arank;
+}
+
+__device__ __forceinline__ void put_cell(uint8_t *map, uint32_t idx, uint8_t val, uint32_t *err) {
+    if (map[idx] != kEmpty) atomicOr(err, kErrCellTaken);
+    map[idx] = val;
+}
+
+// Lane a vehicle entering edge `en` asks for: lanes ordered by distance to
+// the target lane of the movement after `en` (ties to the lower index); the
+// first whose cell 0 is empty in the step-k map.  kNone if none.
+__device__ __forceinline__ uint32_t entry_lane(const Dev &d, const uint8_t *Mc, uint32_t en, const EdgeRec &enr,
+                                               uint32_t next_after) {
+    uint32_t nl = enr.lanes;
+    uint32_t tl = 0;
+    if (next_after != kNone) tl = ((uint32_t)d.orank[next_after] * nl) / d.node[enr.dst].nout;
+    uint32_t stride = row_stride(enr.len);
+    for (uint32_t dd = 0; dd < nl; dd++) {
+        if (tl >= dd && Mc[enr.moff + (tl - dd) * stride] == kEmpty) return tl - dd;
+        if (dd > 0 && tl + dd < nl && Mc[enr.moff + (tl + dd) * stride] == kEmpty) return tl + dd;
+    }
+    return kNone;
+}
+
+__device__ __forceinline__ void stat_entry(const Dev &d, uint32_t e, uint32_t k) {
+    atomicAdd(&d.ent[e], 1ull);
+    if (d.m.bin_steps) {
+        uint32_t b = (k + 1) / d.m.bin_steps;
+        if (b < d.m.n_bins) atomicAdd(&d.bin_in[(size_t)e * d.m.n_bins + b], 1u);
+    }
+}
+
+__device__ __forceinline__ void stat_exit(const Dev &d, uint32_t e, uint32_t k, uint32_t tent) {
+    uint32_t steps = k + 1 - tent;
+    atomicAdd(&d.ext[e], 1ull);
+    atomicAdd(&d.tts[e], (unsigned long long)steps);
+    if (d.m.bin_steps) {
+        uint32_t b = tent / d.m.bin_steps;
+        if (b < d.m.n_bins) {
+            atomicAdd(&d.bin_tt[(size_t)e * d.m.n_bins + b], steps);
+            atomicAdd(&d.bin_cnt[(size_t)e * d.m.n_bins + b], 1u);
+        }
+    }
+}
+
+template <int BLOCK>
+__device__ __forceinline__ void block_add(unsigned long long *dst, uint32_t val) {
+    __shared__ uint32_t red[BLOCK / 32];
+    uint32_t w = __reduce_add_sync(0xFFFFFFFFu, val);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = w;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t t = threadIdx.x < BLOCK / 32 ? red[threadIdx.x] : 0u;
+        t = __reduce_add_sync(0xFFFFFFFFu, t);
+        if (threadIdx.x == 0 && t) atomicAdd(dst, (unsigned long long)t);
+    }
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------- P1
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) step_p1(Dev d, uint32_t koff) {
+    const uint32_t k = *d.kbase + koff;
+    const uint8_t *Mc = d.map[k % 3];
+    uint8_t *Mn = d.map[(k + 1) % 3];
+    uint8_t *Mo = d.map[(k + 2) % 3];       // holds step k-1: erase
+    uint8_t *Iw = d.imap[k & 1];
+    uint8_t *Io = d.imap[(k + 1) & 1];      // marks of step k-1: clear
+    const float *xc = d.s.x[k & 1], *vc = d.s.v[k & 1];
+    float *xw = d.s.x[(k + 1) & 1], *vw = d.s.v[(k + 1) & 1];
+    const uint32_t n = *d.n_slots;
+    const uint32_t total = n + d.n_org;
+    const Model &m = d.m;
+    const bool sample = m.bin_steps && (k % m.bin_steps == 0) && (k / m.bin_steps < m.n_bins);
+    uint32_t live = 0;
+    uint32_t arrived = 0;
+
+    for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < total; i += gridDim.x * BLOCK) {
+        if (i >= n) {
+            // departure request of origin edge j: the queue head, once its step has come
+            uint32_t j = i - n;
+            uint8_t req = kEmpty;
+            uint32_t qh = d.org_qoff[j] + d.org_head[j];
+            if (qh < d.org_qend[j]) {
+                uint32_t h = d.qid[qh];
+                if (d.dep[h] <= k) {
+                    uint32_t e0 = d.org_edge[j];
+                    EdgeRec er = d.edge[e0];
+                    uint32_t r0 = d.roff[h], r1 = d.roff[h + 1];
+                    uint32_t l = entry_lane(d, Mc, e0, er, r0 + 1 < r1 ? d.route[r0 + 1] : kNone);
+                    if (l != kNone) {
+                        atomicMin(&d.claim[d.slot_off[e0] + l], h);
+                        req = (uint8_t)l;
+                    }
+                }
+            }
+            d.dreq[j] = req;
+            continue;
+        }
+        const uint32_t s = i;
+        const uint8_t flag = d.s.flag[s];
+        if (flag == kDead) continue;
+        {
+            uint32_t pc = d.s.pcell[s];
+            if (pc != kNone) Mo[pc] = kEmpty;
+            uint32_t im = d.s.imark[s];
+            if (im != kNone) {
+                Io[im] = 0;
+                d.s.imark[s] = kNone;
+            }
+        }
+        if (flag == kArrivedPending) {
+            d.s.flag[s] = kDead;
+            d.s.pcell[s] = kNone;
+            continue;
+        }
+        live++;
+        const uint32_t id = d.s.id[s];
+        const uint32_t e = d.s.e[s];
+        const uint32_t ln = d.s.lane[s];
+        const float x = xc[s], v = vc[s];
+        const EdgeRec er = d.edge[e];
+        const uint32_t len = er.len;
+        const uint32_t stride = row_stride(len);
+        const uint32_t base = er.moff + ln * stride;
+        const uint32_t c = (uint32_t)x;
+        d.s.pcell[s] = base + c;
+        if (sample) atomicAdd(&d.bin_occ[(size_t)e * m.n_bins + k / m.bin_steps], 1u);
+
+        // leader: nearest occupied cell ahead in the own lane of the own edge.
+        // Cells beyond both d_front and the farthest reach of this step
+        // cannot change the result, so the scan stops there.
+        float d_front = (2.0f * m.dt) * v;
+        float vmax_step = fmaxf(er.v0, v + m.a * m.dt);
+        float reach = fmaxf(d_front, vmax_step * m.dt + m.s0);
+        uint32_t hi = c + (uint32_t)fminf(reach, 65535.0f) + 2u;
+        if (hi > len - 1) hi = len - 1;
+        const uint32_t cf = first_occupied(Mc + base, c + 1, hi);
+        const bool has_f = cf != kNone;
+
+        float vn;
+        if (has_f && ((float)cf - x) <= d_front)
+            vn = idm_speed(m, v, (float)Mc[base + cf], (float)cf - x, er.v0);
+        else
+            vn = er.v0;
+        float xn = x + vn * m.dt;
+        if (has_f) {
+            float lim = (float)cf - m.s0;
+            if (xn > lim) {
+                xn = x > lim ? x : lim;
+                vn = 0.0f;
+            }
+        }
+        const float L = (float)len;
+        const uint32_t rpos = d.s.rpos[s], rlast = d.s.rlast[s];
+        if (xn >= L) {
+            if (rpos == rlast) {
+                stat_exit(d, e, k, d.s.tent[s]);
+                d.arr[id] = k + 1;
+                d.status[id] = kArrived;
+                d.s.flag[s] = kArrivedPending;
+                d.s.act[s] = kActArrive;
+                arrived++;
+                continue;
+            }
+            bool cross = false;
+            if (is_green(d.node[er.dst], er.arank, k)) {
+                const uint32_t en = d.route[rpos + 1];
+                const EdgeRec enr = d.edge[en];
+                uint32_t l = entry_lane(d, Mc, en, enr, rpos + 1 < rlast ? d.route[rpos + 2] : kNone);
+                if (l != kNone) {
+                    atomicMin(&d.claim[d.slot_off[en] + l], id);
+                    d.s.tl[s] = (uint8_t)l;
+                    d.s.act[s] = kActCross;
+                    vw[s] = vn;
+                    uint32_t pos = atomicAdd(&d.counts[k & 1], 1u);
+                    d.cross_list[k & 1][pos] = s;
+                    cross = true;
+                }
+            }
+            if (!cross) {
+                float lim = L - 1.0f;
+                float xh = x > lim ? x : lim;
+                xw[s] = xh;
+                vw[s] = 0.0f;
+                put_cell(Mn, base + (uint32_t)xh, 0, d.err);
+                d.s.act[s] = kActHold;
+            }
+            continue;
+        }
+        xw[s] = xn;
+        vw[s] = vn;
+        const uint32_t cn = (uint32_t)xn;
+        put_cell(Mn, base + cn, speed_byte(vn), d.err);
+        uint8_t act = kActStay;
+        if (er.lanes > 1 && rpos < rlast) {
+            uint32_t tl = ((uint32_t)d.orank[d.route[rpos + 1]] * er.lanes) / d.node[er.dst].nout;
+            if (tl != ln) {
+                bool up = tl > ln;
+                if (up == ((k & 1u) == 1u)) {
+                    float xrem = L - x;
+                    float mp = xrem >= m.x0 ? 0.0f : 1.0f - xrem / m.x0;
+                    if (unit24(lc_hash(m.seed, id, k)) < mp) {
+                        act = kActIntend;
+                        d.s.tl[s] = up ? 1 : 0;  // direction
+                        Iw[base + cn] = 1;
+                        d.s.imark[s] = base + cn;
+                        uint32_t pos = atomicAdd(&d.counts[2 + (k & 1)], 1u);
+                        d.intend_list[k & 1][pos] = s;
+                    }
+                }
+            }
+        }
+        d.s.act[s] = act;
+    }
+    block_add<BLOCK>(&d.ctr[0], live);
+    if (arrived) atomicAdd(&d.ctr[1], (unsigned long long)arrived);
+}
+
+// ----------------------------------------------------------------------- P2
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) step_p2(Dev d, uint32_t koff) {
+    const uint32_t k = *d.kbase + koff;
+    uint8_t *Mn = d.map[(k + 1) % 3];
+    const float *xc = d.s.x[k & 1];
+    float *xw = d.s.x[(k + 1) & 1], *vw = d.s.v[(k + 1) & 1];
+    const uint32_t ncross = d.counts[k & 1];
+    const uint32_t total = ncross + d.n_org;
+    const uint32_t *list = d.cross_list[k & 1];
+    uint32_t events = 0, departed = 0;
+    for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < total; i += gridDim.x * BLOCK) {
+        if (i < ncross) {
+            const uint32_t s = list[i];
+            const uint32_t id = d.s.id[s];
+            const uint32_t e = d.s.e[s];
+            const uint32_t rpos = d.s.rpos[s];
+            const uint32_t en = d.route[rpos + 1];
+            const uint32_t l = d.s.tl[s];
+            const EdgeRec er = d.edge[e];
+            if (d.claim[d.slot_off[en] + l] == id) {
+                const EdgeRec enr = d.edge[en];
+                stat_exit(d, e, k, d.s.tent[s]);
+                stat_entry(d, en, k);
+                d.s.e[s] = en;
+                d.s.rpos[s] = rpos + 1;
+                d.s.lane[s] = (uint8_t)l;
+                d.s.tent[s] = k + 1;
+                d.s.win[s] = 1;
+                xw[s] = 0.0f;
+                put_cell(Mn, enr.moff + l * row_stride(enr.len), speed_byte(vw[s]), d.err);
+                events++;
+            } else {
+                d.s.win[s] = 0;
+                float x = xc[s];
+                float lim = (float)er.len - 1.0f;
+                float xh = x > lim ? x : lim;
+                xw[s] = xh;
+                vw[s] = 0.0f;
+                put_cell(Mn, er.moff + d.s.lane[s] * row_stride(er.len) + (uint32_t)xh, 0, d.err);
+            }
+            continue;
+        }
+        const uint32_t j = i - ncross;
+        const uint8_t l = d.dreq[j];
+        if (l == kEmpty) continue;
+        const uint32_t e0 = d.org_edge[j];
+        const uint32_t h = d.qid[d.org_qoff[j] + d.org_head[j]];
+        if (d.claim[d.slot_off[e0] + l] != h) continue;
+        const uint32_t s = atomicAdd(d.n_slots, 1u);
+        if (s >= d.cap) {
+            atomicOr(d.err, kErrSlotOverflow);
+            continue;
+        }
+        const EdgeRec er = d.edge[e0];
+        d.s.id[s] = h;
+        d.s.e[s] = e0;
+        d.s.rpos[s] = d.roff[h];
+        d.s.rlast[s] = d.roff[h + 1] - 1;
+        d.s.lane[s] = l;
+        d.s.tent[s] = k + 1;
+        d.s.pcell[s] = kNone;
+        d.s.imark[s] = kNone;
+        d.s.flag[s] = kLive;
+        xw[s] = 0.0f;
+        vw[s] = 0.0f;
+        put_cell(Mn, er.moff + l * row_stride(er.len), 0, d.err);
+        d.org_head[j] += 1;
+        d.dep_act[h] = k + 1;
+        d.status[h] = kActive;
+        stat_entry(d, e0, k);
+        events++;
+        departed++;
+    }
+    if (events) atomicAdd(&d.ctr[3], (unsigned long long)events);
+    if (departed) atomicAdd(&d.ctr[4], (unsigned long long)departed);
+}
+
+// ----------------------------------------------------------------------- P3
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) step_p3(Dev d, uint32_t koff) {
+    const uint32_t k = *d.kbase + koff;
+    const uint8_t *Mc = d.map[k % 3];
+    uint8_t *Mn = d.map[(k + 1) % 3];
+    const uint8_t *Iw = d.imap[k & 1];
+    const float *xc = d.s.x[k & 1];
+    const float *xw = d.s.x[(k + 1) & 1], *vw = d.s.v[(k + 1) & 1];
+    const uint32_t nint = d.counts[2 + (k & 1)];
+    const uint32_t ncross = d.counts[k & 1];
+    const uint32_t total = nint + ncross + d.n_org;
+    const Model &m = d.m;
+    uint32_t changes = 0;
+    for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < total; i += gridDim.x * BLOCK) {
+        if (i < nint) {
+            const uint32_t s = d.intend_list[k & 1][i];
+            const uint32_t id = d.s.id[s];
+            const uint32_t e = d.s.e[s];
+            const uint32_t ln = d.s.lane[s];
+            const uint32_t ln2 = d.s.tl[s] ? ln + 1 : ln - 1;
+            const EdgeRec er = d.edge[e];
+            const uint32_t len = er.len, stride = row_stride(len);
+            const uint8_t *row2 = Mc + er.moff + ln2 * stride;
+            const float x = xc[s], xn = xw[s], vn = vw[s];
+            const uint32_t c0 = (uint32_t)x, cn = (uint32_t)xn;
+            uint32_t hi = c0 + 63u < len - 1 ? c0 + 63u : len - 1;
+            const uint32_t ca = first_occupied(row2, c0, hi);
+            const uint32_t cb = c0 > 0 ? last_occupied(row2, c0 > 64u ? c0 - 64u : 0u, c0 - 1) : kNone;
+            float eps_a = 0.0f, eps_b = 0.0f;
+            if (m.eps_amp > 0.0f) {
+                uint64_t h = lc_hash(m.seed, id, k);
+                eps_a = m.eps_amp * (2.0f * unit24(splitmix64_mix(h ^ 0x632BE59BD9B4E019ull)) - 1.0f);
+                eps_b = m.eps_amp * (2.0f * unit24(splitmix64_mix(h ^ 0x8CB92BA72F3D8DD7ull)) - 1.0f);
+            }
+            bool ok = true;
+            if (ca != kNone) {
+                float va = (float)row2[ca];
+                float G_lead = (m.g_a + fmax0(m.alpha_i * vn - m.alpha_a * va)) + eps_a;
+                ok = ((float)ca - xn) >= G_lead;
+            }
+            if (ok && cb != kNone) {
+                float vb = (float)row2[cb];
+                float G_lag = (m.g_b + fmax0(m.alpha_b * vb - m.alpha_i * vn)) + eps_b;
+                ok = (xn - (float)cb) >= G_lag;
+            }
+            if (ok && cn >= 1) {
+                const uint32_t tgt = er.moff + ln2 * stride + cn;
+                if (Mn[tgt] == kEmpty && Iw[tgt] == 0) {
+                    const uint32_t own = er.moff + ln * stride + cn;
+                    Mn[tgt] = Mn[own];
+                    Mn[own] = kEmpty;
+                    d.s.lane[s] = (uint8_t)ln2;
+                    changes++;
+                }
+            }
+            continue;
+        }
+        if (i < nint + ncross) {
+            const uint32_t s = d.cross_list[k & 1][i - nint];
+            if (d.s.win[s]) d.claim[d.slot_off[d.s.e[s]] + d.s.lane[s]] = kNone;
+            continue;
+        }
+        const uint32_t j = i - nint - ncross;
+        const uint8_t l = d.dreq[j];
+        if (l != kEmpty) d.claim[d.slot_off[d.org_edge[j]] + l] = kNone;
+    }
+    if (changes) atomicAdd(&d.ctr[2], (unsigned long long)changes);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        d.counts[(k + 1) & 1] = 0;
+        d.counts[2 + ((k + 1) & 1)] = 0;
+    }
+}
+
+__global__ void chunk_end(Dev d, uint32_t steps) { *d.kbase += steps; }
+
+void launch_step(const Dev &d, uint32_t koff, int grid, int block, cudaStream_t st) {
+    switch (block) {
+    case 128:
+        step_p1<128><<<grid, 128, 0, st>>>(d, koff);
+        step_p2<128><<<grid, 128, 0, st>>>(d, koff);
+        step_p3<128><<<grid, 128, 0, st>>>(d, koff);
+        break;
+    case 512:
+        step_p1<512><<<grid, 512, 0, st>>>(d, koff);
+        step_p2<512><<<grid, 512, 0, st>>>(d, koff);
+        step_p3<512><<<grid, 512, 0, st>>>(d, koff);
+        break;
+    default:
+        step_p1<256><<<grid, 256, 0, st>>>(d, koff);
+        step_p2<256><<<grid, 256, 0, st>>>(d, koff);
+        step_p3<256><<<grid, 256, 0, st>>>(d, koff);
+        break;
+    }
+}
+
+void launch_chunk_end(const Dev &d, uint32_t steps, cudaStream_t st) { chunk_end<<<1, 1, 0, st>>>(d, steps); }
+
+}  // namespace lpsim
+
+namespace lpsim {
+
+namespace {
+
+// state of every live slot, scattered to vehicle-id order
+__global__ void state_scatter(Dev d, uint32_t k, float *x, float *v, uint32_t *edge, uint8_t *lane, uint32_t *ridx) {
+    const uint32_t n = *d.n_slots;
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        if (d.s.flag[s] != kLive) continue;
+        uint32_t id = d.s.id[s];
+        x[id] = d.s.x[k & 1][s];
+        v[id] = d.s.v[k & 1][s];
+        edge[id] = d.s.e[s];
+        lane[id] = d.s.lane[s];
+        ridx[id] = d.s.rpos[s] - d.roff[id];
+    }
+}
+
+__global__ void max_arrival(Dev d, uint64_t n, uint32_t *out) {
+    uint32_t best = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t a = d.arr[i];
+        if (a != kNone && a > best) best = a;
+    }
+    best = __reduce_max_sync(0xFFFFFFFFu, best);
+    if ((threadIdx.x & 31) == 0 && best) atomicMax(out, best);
+}
+
+}  // namespace
+
+void launch_state_scatter(const Dev &d, uint32_t k, float *x, float *v, uint32_t *edge, uint8_t *lane,
+                          uint32_t *ridx, cudaStream_t st) {
+    state_scatter<<<256, 256, 0, st>>>(d, k, x, v, edge, lane, ridx);
+}
+
+void launch_max_arrival(const Dev &d, uint64_t n, uint32_t *out, cudaStream_t st) {
+    max_arrival<<<256, 256, 0, st>>>(d, n, out);
+}
+
+}  // namespace lpsim

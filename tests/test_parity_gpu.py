@@ -1,0 +1,107 @@
+"""GPU library against the CPU oracle, element by element, bit for bit, on
+the same seeded inputs (IEEE binary32 state, integer statistics)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import workloads as W
+from netutil import make_demand, make_net
+from simutil import assert_outputs_equal, assert_state_equal, lockstep
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import paper_2406_08496_gb300 as L
+    L.build()
+    L.load_library()
+    L.use_torch_allocator()
+
+
+def test_grid_day_every_step(grid_day):
+    """8x8 signalised grid, 2,000 trips over 30 min, 3,600 steps."""
+    net, dem = grid_day
+    lockstep(net, dem, dict(bin_steps=300, n_bins=12), 3600, check_every=25)
+
+
+def test_grid_day_first_steps_each_step(grid_day):
+    net, dem = grid_day
+    lockstep(net, dem, {}, 400, check_every=1)
+
+
+@pytest.mark.parametrize("gpu_params", [
+    dict(block_size=128, blocks_per_sm=1, sort_period=1, chunk_steps=6),
+    dict(block_size=512, blocks_per_sm=2, sort_period=7, chunk_steps=42),
+    dict(block_size=256, blocks_per_sm=8, sort_period=32, flags=1),
+    dict(block_size=256, blocks_per_sm=4, sort_period=128, chunk_steps=768),
+])
+def test_launch_configuration_invariance(grid_day, gpu_params):
+    """Results do not depend on block size, grid size, sort period, sorting
+    or graph chunking."""
+    net, dem = grid_day
+    lockstep(net, dem, dict(bin_steps=600, n_bins=6), 2000, check_every=250, gpu_params=gpu_params)
+
+
+def test_small_regional_with_lane_changes():
+    net = W.planar_network(40, 40, seed=21)
+    dem = W.route(net, W.gravity_demand(net, 12000, 22, zones_x=6, zones_y=6, access_per_zone=3,
+                                        beta_m=2500.0, peaks_h=(0.1, 0.25), peak_sigma_h=0.1))
+    o, g = lockstep(net, dem, dict(bin_steps=450, n_bins=8, seed=99), 3000, check_every=100)
+    assert o.counters()["lane_changes"] > 100
+
+
+def test_random_gap_components():
+    net = W.planar_network(32, 32, seed=8)
+    dem = W.route(net, W.gravity_demand(net, 6000, 9, zones_x=4, zones_y=4, access_per_zone=2,
+                                        beta_m=2000.0, peaks_h=(0.05, 0.15), peak_sigma_h=0.05))
+    lockstep(net, dem, dict(eps_amp=1.5, x0=60.0, seed=7), 1500, check_every=50)
+
+
+def test_tiny_scenarios():
+    """The brute-force scenario family (merge, diverge, two signals, edges
+    shorter than one step, 1-5 vehicles) on the GPU."""
+    from test_oracle_bruteforce import scenario
+    for seed in range(0, 120):
+        net, trips, params = scenario(seed)
+        lockstep(net, make_demand(trips), params, 70, check_every=1)
+
+
+def test_edge_cases():
+    # one-cell edges, 4 lanes, single-edge routes, far-future departure, a
+    # queue of 30 vehicles released at once onto a one-lane edge
+    net = make_net(5, [(0, 1, 0.4, 4, 13.9), (1, 2, 1.0, 1, 30.0), (2, 3, 250.0, 2, 5.5), (3, 4, 3.0, 4, 254.0),
+                       (4, 0, 33.3, 3, 11.1)], green={2: 4, 3: 1})
+    trips = [(0, [0, 1, 2, 3, 4]) for _ in range(30)] + [(5, [2]), (1000, [4, 0]), (3, [1, 2, 3])]
+    lockstep(net, make_demand(trips), dict(bin_steps=50, n_bins=30), 1200, check_every=1)
+
+
+def test_run_until_done_matches_oracle(grid_day):
+    import oracle as O
+    from paper_2406_08496_gb300 import Simulation
+    net, dem = grid_day
+    o = O.Oracle(net, {})
+    o.load_demand(dem)
+    g = Simulation(net, {})
+    g.load_demand(dem)
+    ro = o.run(20000)
+    rg = g.run(20000)
+    for key in ("steps", "veh_steps", "arrived", "active", "waiting", "k"):
+        assert ro[key] == rg[key], (key, ro[key], rg[key])
+    assert_outputs_equal(o, g)
+
+
+def test_reset_replays_identically(grid_day):
+    from paper_2406_08496_gb300 import Simulation
+    net, dem = grid_day
+    g = Simulation(net, dict(bin_steps=600, n_bins=6))
+    g.load_demand(dem)
+    g.step(1500)
+    s1, t1, l1 = g.state(), g.trips(), g.link_stats()
+    g.reset()
+    g.step(700)
+    g.step(800)
+    assert_state_equal(s1, g.state())
+    assert np.array_equal(t1["arrive"], g.trips()["arrive"])
+    assert np.array_equal(l1["inflow"], g.link_stats()["inflow"])
