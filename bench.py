@@ -1,0 +1,357 @@
+"""Benchmark of the per-step vehicle update on GB300.
+
+One benchmark step = one simulated day of the regional workload: a planar
+road network at the paper's single-GPU scale (about 224k nodes / 548k
+directed edges) with 2.82M trips (gravity OD from 1,500 zones, AM/PM
+departure peaks, free-flow shortest-path routes), dt = 0.5 s, simulated from
+step 0 until every trip has arrived, with network and trips resident in HBM.
+The metric is vehicle-steps per second (sum over steps of the vehicles on the
+network, divided by the time).
+
+Printed as one JSON line by rank 0, with:
+  roofline      the dominant kernel (step_p1) against the measured HBM copy
+                bandwidth, from CUDA events around every launch in one extra
+                day run with per-kernel timing on;
+  cpu_baseline  the CPU oracle (single thread) on a bounded sample of the
+                same workload;
+  e2e           the same metric through the public API from host buffers
+                (network and trip upload, the run, trip and link-statistics
+                download inside the timed region);
+  clocks        nvidia-smi samples taken during the timed region.
+
+`--impl reference` times the CPU oracle on the bounded sample instead.
+`--gpus N` under torchrun runs N independent replicas (one per GPU).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_VEH_STEP_P1 = 64  # 24 state read + 8 state write + 16 edge record + 16 lane-map window
+DAY_STEPS = 172_800
+SAMPLE_WINDOW = (7 * 7200 + 3600, 7 * 7200 + 3600 + 600)  # trips departing 07:30-07:35
+SAMPLE_STEPS = 1200
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="regional", choices=["regional", "grid", "large"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-window", type=int, default=0,
+                    help="run to 08:00, then profile this many directly launched steps (for ncu) and exit")
+    return ap.parse_args()
+
+
+def load_workload(name: str):
+    import workloads as W
+    if name == "regional":
+        net, dem = W.regional_day(seed=2, n_trips=2_820_000)
+        label = "regional-224k-nodes-2.82M-trips-24h"
+    elif name == "large":
+        net, dem = W.regional_day(seed=3, n_trips=9_010_000, scale="large")
+        label = "regional-1M-nodes-9.01M-trips-24h"
+    else:
+        net, dem = W.grid_day(seed=1)
+        label = "grid-8x8-2000-trips"
+    return net, dem, label
+
+
+def sample_workload(net, dem):
+    """Bounded CPU sample of the same workload: the trips departing in a
+    five-minute window of the morning peak, simulated for 10 minutes."""
+    import workloads as W
+    k0, k1 = SAMPLE_WINDOW
+    keep = (dem["depart_step"] >= k0) & (dem["depart_step"] < k1)
+    sub = W.subset_trips(dem, keep)
+    sub["depart_step"] = (sub["depart_step"] - k0).astype(np.uint32)
+    return sub
+
+
+def run_oracle_sample(net, sub, params):
+    import oracle as O
+    o = O.Oracle(net, params)
+    o.load_demand(sub)
+    t0 = time.perf_counter()
+    r = o.run(SAMPLE_STEPS)
+    dt = time.perf_counter() - t0
+    o.close()
+    return r["veh_steps"], dt
+
+
+class ClockSampler:
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic():
+    """DRAM bytes per launch of step_p1 from the committed ncu summary, if it
+    was taken on the current kernel source."""
+    import hashlib
+    summ = os.path.join(ROOT, "profiles", "step_p1_regional_peak.json")
+    src = os.path.join(ROOT, "paper_2406_08496_gb300", "csrc", "step_kernels.cu")
+    if not os.path.exists(summ):
+        return None
+    with open(summ) as f:
+        d = json.load(f)
+    with open(src, "rb") as f:
+        h = hashlib.sha1(f.read()).hexdigest()[:12]
+    if d.get("source_sha1") != h:
+        return None
+    return d
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    net, dem, label = load_workload(args.workload)
+    sub = sample_workload(net, dem)
+    params = dict(bin_steps=1800, n_bins=0)
+    for _ in range(args.warmup):
+        run_oracle_sample(net, sub, params)
+    vs_tot, t_tot = 0, 0.0
+    for _ in range(args.steps):
+        vs, dt = run_oracle_sample(net, sub, params)
+        vs_tot += vs
+        t_tot += dt
+    value = vs_tot / t_tot
+    sample = (f"{len(sub['depart_step'])} trips departing 07:30-07:35 of the {label} workload, "
+              f"{SAMPLE_STEPS} steps from 07:30, full network")
+    line = {"impl": "reference", "metric": "veh-steps/s", "value": value, "unit": "veh-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_tot / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": label, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "veh-steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "veh-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+
+    import torch
+    import paper_2406_08496_gb300 as L
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    L.build()
+    L.use_torch_allocator()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+
+    net, dem, label = load_workload(args.workload)
+    n_bins = 96 if args.workload != "grid" else 4
+    params = dict(bin_steps=1800, n_bins=n_bins)
+    sim = L.Simulation(net, params)
+    sim.load_demand(dem)
+
+    if args.profile_window:
+        sim.step(8 * 7200)  # to 08:00
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStart()
+        sim.step(args.profile_window)
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStop()
+        c = sim.counters()
+        print(json.dumps({"profile_window": args.profile_window, "k": c["k"], "active": c["active"]}))
+        return
+
+    def day():
+        sim.reset()
+        return sim.run(DAY_STEPS + 100_000)
+
+    for _ in range(args.warmup):
+        day()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+
+    launches0 = sim.counters()["launches"]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    veh_steps = 0
+    steps_per_day = []
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            r = day()
+            veh_steps += r["veh_steps"]
+            steps_per_day.append(r["steps"])
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = sim.counters()["launches"] - launches0
+    t_max = ms
+    vs_all = veh_steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        v = torch.tensor([veh_steps], device="cuda", dtype=torch.float64)
+        dist.all_reduce(v, op=dist.ReduceOp.SUM)
+        vs_all = float(v.item())
+    value = vs_all / (t_max / 1e3)
+
+    out = None
+    if rank == 0:
+        # roofline of the dominant kernel: one more day with per-launch events
+        sim.set_kernel_timing(True)
+        rr = day()
+        kt = sim.kernel_times()
+        sim.set_kernel_timing(False)
+        p1 = kt["step_p1"]
+        if p1["ms"] <= 0 or p1["launches"] == 0:
+            raise RuntimeError(f"no step_p1 launch was timed: {kt}")
+        achieved = BYTES_PER_VEH_STEP_P1 * rr["veh_steps"] / (p1["ms"] / 1e3) / 1e9
+        peak, peak_src = measured_peaks()
+        tot_ms = sum(v["ms"] for v in kt.values())
+        tr = ncu_traffic()
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": (tr or {}).get("dram_bytes_per_launch"),
+                    "kernel": "step_p1", "bytes_per_veh_step": BYTES_PER_VEH_STEP_P1,
+                    "avg_launch_us": p1["ms"] * 1e3 / max(1, p1["launches"]),
+                    "avg_veh_per_launch": rr["veh_steps"] / max(1, p1["launches"]),
+                    "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})",
+                    "kernel_share": {k: v["ms"] / tot_ms for k, v in kt.items()},
+                    "traffic_launch": (tr or {}).get("captured_launch")}
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            sub = sample_workload(net, dem)
+            vs, dt = run_oracle_sample(net, sub, dict(bin_steps=1800, n_bins=0))
+            cpu = {"value": vs / dt, "unit": "veh-steps/s", "cores": 1, "kind": "oracle",
+                   "sample": f"{len(sub['depart_step'])} trips departing 07:30-07:35 of the same day, "
+                             f"{SAMPLE_STEPS} steps from 07:30 on the full network ({vs} veh-steps, {dt:.1f} s)",
+                   "host_cpus": os.cpu_count()}
+        e2e = None
+        if not args.no_e2e:
+            e2e = end_to_end(L, torch, net, dem, params)
+        clocks = clk.summary()
+        out = {"metric": "veh-steps/s", "value": value, "unit": "veh-steps/s", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic",
+               "config": {"workload": label, "nodes": net["n_nodes"], "edges": net["n_edges"],
+                          "trips": int(len(dem["depart_step"])), "dt_s": 0.5,
+                          "sim_steps_per_day": int(np.mean(steps_per_day)),
+                          "step": "one simulated day from step 0 until every trip has arrived",
+                          "parallelism": f"replicas x{world}",
+                          "l2": "inputs larger than L2 (routes 1.4 GB, lane maps 3 x 0.16 GB)"},
+               "wall_per_sim_day_s": t_max / args.steps / 1e3,
+               "pct_hbm_peak": roofline["frac"],
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+               "gpu_launches": int(launches)}
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+def end_to_end(L, torch, net, dem, params):
+    """One day through the public API from host buffers: network and trip
+    upload, the run, trips and link statistics back to the host."""
+    net_bytes = sum(int(np.asarray(net[k]).nbytes) for k in
+                    ("edge_src", "edge_dst", "edge_len", "edge_lanes", "edge_vmax", "node_green"))
+    if net.get("edge_approach_rank") is not None:
+        net_bytes += int(net["edge_approach_rank"].nbytes)
+    dem_bytes = int(dem["depart_step"].nbytes + dem["route_off"].nbytes + dem["route_edges"].nbytes)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim = L.Simulation(net, params)
+    sim.load_demand(dem)
+    r = sim.run(DAY_STEPS + 100_000)
+    trips = sim.trips()
+    ls = sim.link_stats()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    d2h = int(trips["depart"].nbytes + trips["arrive"].nbytes + sum(v.nbytes for v in ls.values()))
+    sim.close()
+    return {"value": r["veh_steps"] / dt, "unit": "veh-steps/s", "h2d_bytes_per_step": net_bytes + dem_bytes,
+            "d2h_bytes_per_step": d2h, "seconds": dt}
+
+
+if __name__ == "__main__":
+    main()

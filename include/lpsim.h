@@ -81,7 +81,7 @@ typedef struct lpsim_params {
     uint32_t n_bins;      /* bins kept per edge */
     uint32_t sort_period; /* steps between re-sorts of the active vehicles by lane-map cell (0 = 64) */
     uint32_t block_size;  /* threads per block of the step kernels: 128, 256, 512 or 0 (= 256) */
-    uint32_t blocks_per_sm; /* resident blocks per SM the step grids are sized for (0 = 4) */
+    uint32_t blocks_per_sm; /* resident 256-thread blocks per SM the step grids are sized for (0 = 6) */
     uint32_t chunk_steps; /* steps captured in one CUDA graph launch (0 = 384); rounded up to a multiple
                              of 2 sort periods and of 3 */
     uint32_t gridlock_steps; /* lpsim_run fails with LPSIM_E_GRIDLOCK after this many steps with active
@@ -199,6 +199,16 @@ uint64_t lpsim_lane_map_size(const lpsim_ctx *ctx);
 int lpsim_get_lane_map(lpsim_ctx *ctx, uint8_t *out, uint64_t size);
 
 int lpsim_get_counters(lpsim_ctx *ctx, lpsim_counters *out);
+
+/* Per-kernel timing.  While on, every launch of the three step kernels
+ * (step_p1: car following, departures and claims; step_p2: entry conflicts;
+ * step_p3: lane changes) and of the compaction/sort sequence is bracketed by
+ * CUDA events on the context's stream, and the elapsed times are summed after
+ * each graph chunk (which then synchronises).  Switching resets the sums.
+ * lpsim_get_kernel_times fills ms[4] (summed milliseconds) and launches[4]
+ * (phase launches timed) in the order step_p1, step_p2, step_p3, compaction. */
+int lpsim_set_kernel_timing(lpsim_ctx *ctx, int on);
+int lpsim_get_kernel_times(lpsim_ctx *ctx, double *ms, uint64_t *launches);
 
 /* Release every device and host resource of the context (NULL is a no-op). */
 void lpsim_destroy(lpsim_ctx *ctx);

@@ -22,14 +22,14 @@ __all__ = ["Simulation", "LpsimError", "DEFAULT_PARAMS", "build", "load_library"
 # workloads; IDM a, b, s0, T; lane-change horizon x0; critical-gap constants.
 DEFAULT_PARAMS = dict(dt=0.5, a=1.0, b=1.5, s0=2.0, T=1.5, x0=100.0, g_a=2.0, g_b=2.0,
                       alpha_i=1.0, alpha_a=1.0, alpha_b=1.0, eps_amp=0.0, seed=12345,
-                      bin_steps=1800, n_bins=0, sort_period=64, block_size=256, blocks_per_sm=4,
+                      bin_steps=1800, n_bins=0, sort_period=64, block_size=256, blocks_per_sm=6,
                       chunk_steps=384, gridlock_steps=0, flags=0)
 FLAG_NO_SORT = 1
 
 EXPORTED = ["lpsim_last_error", "lpsim_version", "lpsim_set_allocator", "lpsim_load_network",
             "lpsim_load_demand", "lpsim_step", "lpsim_run", "lpsim_reset", "lpsim_link_stats",
             "lpsim_get_trips", "lpsim_get_state", "lpsim_lane_map_size", "lpsim_get_lane_map",
-            "lpsim_get_counters", "lpsim_destroy"]
+            "lpsim_get_counters", "lpsim_set_kernel_timing", "lpsim_get_kernel_times", "lpsim_destroy"]
 
 STATUS = {0: "LPSIM_OK", -1: "LPSIM_E_INVALID_ARG", -2: "LPSIM_E_OOM", -3: "LPSIM_E_CUDA", -4: "LPSIM_E_STATE",
           -5: "LPSIM_E_TIMEOUT", -6: "LPSIM_E_GRIDLOCK", -7: "LPSIM_E_INVARIANT"}
@@ -107,6 +107,8 @@ def load_library(path: str | None = None):
     lib.lpsim_lane_map_size.restype = ctypes.c_uint64
     lib.lpsim_get_lane_map.argtypes = [P, P, ctypes.c_uint64]
     lib.lpsim_get_counters.argtypes = [P, ctypes.POINTER(Counters)]
+    lib.lpsim_set_kernel_timing.argtypes = [P, ctypes.c_int]
+    lib.lpsim_get_kernel_times.argtypes = [P, P, P]
     lib.lpsim_destroy.argtypes = [P]
     lib.lpsim_destroy.restype = None
     _lib = lib
@@ -249,6 +251,16 @@ class Simulation:
         out = {"entries": pe[:, 0].copy(), "exits": pe[:, 1].copy(), "tt_steps": pe[:, 2].copy()}
         out.update(bins)
         return out
+
+    def set_kernel_timing(self, on: bool) -> None:
+        _check(self.lib, self.lib.lpsim_set_kernel_timing(self.h, 1 if on else 0))
+
+    def kernel_times(self) -> dict:
+        ms = np.zeros(4, np.float64)
+        n = np.zeros(4, np.uint64)
+        _check(self.lib, self.lib.lpsim_get_kernel_times(self.h, _p(ms), _p(n)))
+        names = ("step_p1", "step_p2", "step_p3", "compact_sort")
+        return {k: {"ms": float(ms[i]), "launches": int(n[i])} for i, k in enumerate(names)}
 
     def close(self) -> None:
         if getattr(self, "h", None):

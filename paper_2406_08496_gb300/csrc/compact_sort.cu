@@ -136,7 +136,12 @@ __device__ __forceinline__ void copy_slot(const Slots &a, uint32_t s, const Slot
     b.tent[o] = a.tent[s];
     b.pcell[o] = a.pcell[s];
     b.imark[o] = a.imark[s];
+    b.base[o] = a.base[s];
+    b.cprev[o] = a.cprev[s];
+    b.len[o] = a.len[s];
+    b.v0[o] = a.v0[s];
     b.lane[o] = a.lane[s];
+    b.tlc[o] = a.tlc[s];
     b.flag[o] = kLive;
     b.x[par][o] = a.x[par][s];
     b.v[par][o] = a.v[par][s];
@@ -174,8 +179,7 @@ __global__ void __launch_bounds__(kBlock) scatter_keys(Dev d, SortWork w, uint32
         for (int j = 0; j < kItems; j++) {
             if (!live[j]) continue;
             uint32_t s = t * kTile + threadIdx.x * kItems + j;
-            EdgeRec er = d.edge[d.s.e[s]];
-            w.key[0][off + rank[j]] = er.moff + d.s.lane[s] * row_stride(er.len) + (uint32_t)x[s];
+            w.key[0][off + rank[j]] = d.s.base[s] + (uint32_t)x[s];
             w.perm[0][off + rank[j]] = s;
         }
     }

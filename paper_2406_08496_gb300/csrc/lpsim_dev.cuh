@@ -8,6 +8,7 @@ namespace lpsim {
 
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint8_t kEmpty = 0xFFu;
+constexpr uint8_t kNoLane = 0xFFu;
 
 // slot life cycle
 constexpr uint8_t kLive = 0;
@@ -58,11 +59,27 @@ struct Model {
 };
 
 // Vehicle slots (structure of arrays).  x and v are double-buffered by step
-// parity: step k reads x[k&1] and writes x[(k+1)&1].
+// parity: step k reads x[k&1] and writes x[(k+1)&1].  The attributes of the
+// current edge that the car-following rule needs (its lane-row start in the
+// map, its length and speed limit) are copied into the slot when the vehicle
+// enters the edge, so the common path reads only the slot and the map.
 struct Slots {
-    uint32_t *id, *e, *rpos, *rlast, *tent, *pcell, *imark;
-    uint8_t *lane, *flag, *act, *tl, *win;
+    // persistent
+    uint32_t *id, *e, *rpos, *rlast, *tent;
+    uint32_t *pcell;   // cell of the previous step (erased this step), kNone
+    uint32_t *imark;   // intent mark of the previous step (cleared this step), kNone
+    uint32_t *base;    // lane-map offset of cell 0 of the current lane
+    uint32_t *cprev;   // claim slot won at the previous step (reset this step), kNone
+    uint16_t *len;     // cells per lane of the current edge
+    uint8_t *lane, *flag;
+    uint8_t *tlc;      // target lane of the movement after the current edge (kNoLane on the last edge)
+    float *v0;         // speed limit of the current edge
     float *x[2], *v[2];
+    // per-step scratch
+    uint8_t *act;
+    uint8_t *tl;       // requested lane (crossers) or direction (intenders: 1 = up)
+    uint8_t *tln;      // target lane after the next edge (crossers)
+    uint32_t *cslot;   // claim slot asked for (crossers)
 };
 
 struct Dev {
@@ -73,7 +90,7 @@ struct Dev {
     const uint8_t *orank;      // rank of the edge among the out-edges of its source
     uint8_t *map[3];           // lane maps, step k reads map[k%3], writes map[(k+1)%3]
     uint8_t *imap[2];          // lane-change intent marks of step k: imap[k&1]
-    uint32_t *claim;           // per (edge, lane): lowest id asking to enter this step
+    uint32_t *claim[2];        // per (edge, lane): lowest id asking to enter, by step parity
     // trips, by vehicle id
     const uint32_t *dep;       // departure step
     const uint32_t *route;     // all routes, vehicle-id order
@@ -84,13 +101,16 @@ struct Dev {
     uint32_t n_org;
     const uint32_t *org_edge, *org_qoff, *org_qend, *qid;
     uint32_t *org_head;
+    uint32_t *org_dep;         // departure step of the queue head (kNone: queue empty)
     uint8_t *dreq;             // requested lane this step (kEmpty = none)
+    uint32_t *dslot, *dprev;   // claim slot asked for this step / won at the previous step
     // slots (current set: the host alternates two sets around each compaction)
     Slots s;
     uint32_t cap;              // slot capacity
     // per-step lists, by step parity
     uint32_t *cross_list[2], *intend_list[2];
     uint32_t *counts;          // [0..1] cross count by parity, [2..3] intend count by parity
+    uint32_t *dep_list[2];     // origin edges that asked for a departure, by parity (counts[4..5])
     // statistics
     unsigned long long *ent, *ext, *tts;
     uint32_t *bin_in, *bin_tt, *bin_cnt, *bin_occ;
@@ -104,7 +124,7 @@ struct Dev {
 };
 
 // kernels of a step; koff = offset of this step inside the chunk
-void launch_step(const Dev &d, uint32_t koff, int grid, int block, cudaStream_t st);
+void launch_phase(const Dev &d, int phase, uint32_t koff, int grid, int block, cudaStream_t st);
 void launch_chunk_end(const Dev &d, uint32_t steps, cudaStream_t st);
 
 // compaction (and optional sort by lane-map cell) of the slots after step k;

@@ -76,9 +76,16 @@ struct lpsim_ctx {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     unsigned long long *h_ctr = nullptr;  // pinned: ctr[0..7], err, n_slots, ...
     uint32_t *d_tmp = nullptr;
+    uint32_t *org_dep0 = nullptr;    // departure step of each origin queue's first trip
     uint64_t launches = 0;
     uint64_t stall_steps = 0;
     unsigned long long last_progress = 0;
+    // per-kernel timing (events around every phase launch of every step)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;     // 5 per step of a chunk
+    double t_ms[4] = {0, 0, 0, 0};   // step_p1, step_p2, step_p3, compaction + sort
+    uint64_t t_n[4] = {0, 0, 0, 0};
+    std::string t_err;               // first failure of cudaEventElapsedTime
 
     void *dalloc(size_t bytes) {
         if (bytes == 0) bytes = 16;
@@ -95,6 +102,7 @@ struct lpsim_ctx {
     ~lpsim_ctx() {
         for (int i = 0; i < 2; i++)
             if (graph[i]) cudaGraphExecDestroy(graph[i]);
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
         if (stream) cudaStreamSynchronize(stream);
         for (void *b : blocks) {
             if (release) release(b, alloc_user);
@@ -150,7 +158,13 @@ int alloc_slots(lpsim_ctx *c, Slots &s, uint32_t cap) {
     TRY(dnew(c, s.flag, cap));
     TRY(dnew(c, s.act, cap));
     TRY(dnew(c, s.tl, cap));
-    TRY(dnew(c, s.win, cap));
+    TRY(dnew(c, s.tlc, cap));
+    TRY(dnew(c, s.tln, cap));
+    TRY(dnew(c, s.base, cap));
+    TRY(dnew(c, s.cprev, cap));
+    TRY(dnew(c, s.cslot, cap));
+    TRY(dnew(c, s.len, cap));
+    TRY(dnew(c, s.v0, cap));
     for (int i = 0; i < 2; i++) {
         TRY(dnew(c, s.x[i], cap));
         TRY(dnew(c, s.v[i], cap));
@@ -164,7 +178,7 @@ int reset_state(lpsim_ctx *c) {
     cudaStream_t st = c->stream;
     for (int i = 0; i < 3; i++) CU(cudaMemsetAsync(d.map[i], 0xFF, c->map_bytes, st));
     for (int i = 0; i < 2; i++) CU(cudaMemsetAsync(d.imap[i], 0, c->map_bytes, st));
-    CU(cudaMemsetAsync(d.claim, 0xFF, c->lane_slots * 4, st));
+    for (int i = 0; i < 2; i++) CU(cudaMemsetAsync(d.claim[i], 0xFF, c->lane_slots * 4, st));
     CU(cudaMemsetAsync(d.ent, 0, c->n_edges * 8ull, st));
     CU(cudaMemsetAsync(d.ext, 0, c->n_edges * 8ull, st));
     CU(cudaMemsetAsync(d.tts, 0, c->n_edges * 8ull, st));
@@ -175,7 +189,7 @@ int reset_state(lpsim_ctx *c) {
         CU(cudaMemsetAsync(d.bin_cnt, 0, nb, st));
         CU(cudaMemsetAsync(d.bin_occ, 0, nb, st));
     }
-    CU(cudaMemsetAsync(d.counts, 0, 4 * 4, st));
+    CU(cudaMemsetAsync(d.counts, 0, 8 * 4, st));
     CU(cudaMemsetAsync(d.kbase, 0, 4, st));
     CU(cudaMemsetAsync(d.n_slots, 0, 4, st));
     CU(cudaMemsetAsync(d.ctr, 0, 8 * 8, st));
@@ -185,6 +199,8 @@ int reset_state(lpsim_ctx *c) {
         CU(cudaMemsetAsync(d.arr, 0xFF, c->n_trips * 4, st));
         CU(cudaMemsetAsync(d.status, 0, c->n_trips, st));
         CU(cudaMemsetAsync(d.org_head, 0, (size_t)d.n_org * 4, st));
+        CU(cudaMemsetAsync(d.dprev, 0xFF, (size_t)d.n_org * 4, st));
+        CU(cudaMemcpyAsync(d.org_dep, c->org_dep0, (size_t)d.n_org * 4, cudaMemcpyDeviceToDevice, st));
     }
     c->k = 0;
     c->cur = 0;
@@ -207,19 +223,61 @@ int read_status(lpsim_ctx *c) {
     return LPSIM_OK;
 }
 
+// The kernels of step `koff` of a chunk (or of a direct step, koff = 0),
+// with timing events around each phase when timing is on.  Returns the slot
+// set current after the step.
+int enqueue_step(lpsim_ctx *c, uint32_t koff, int cur, bool compact) {
+    Dev d = c->d;
+    d.s = c->sets[cur];
+    cudaEvent_t *e = c->timing ? &c->ev[5 * koff] : nullptr;
+    // cudaEventRecordExternal: inside a stream capture the record becomes an
+    // event-record node that timestamps when the graph runs
+    for (int ph = 1; ph <= 3; ph++) {
+        if (e) cudaEventRecordWithFlags(e[ph - 1], c->stream, cudaEventRecordExternal);
+        launch_phase(d, ph, koff, c->grid, c->block, c->stream);
+    }
+    if (e) cudaEventRecordWithFlags(e[3], c->stream, cudaEventRecordExternal);
+    if (compact) {
+        launch_compact(d, c->sets[cur ^ 1], c->w, koff, c->sort, c->grid, c->stream);
+        cur ^= 1;
+        if (e) cudaEventRecordWithFlags(e[4], c->stream, cudaEventRecordExternal);
+    }
+    return cur;
+}
+
+// add the event times of steps [0, n) of the last chunk (after a sync)
+void collect_times(lpsim_ctx *c, uint32_t n, uint64_t k_first) {
+    if (!c->timing) return;
+    for (uint32_t j = 0; j < n; j++) {
+        cudaEvent_t *e = &c->ev[5 * j];
+        float ms = 0.0f;
+        for (int ph = 0; ph < 4; ph++) {
+            if (ph == 3 && (k_first + j + 1) % c->R != 0) break;
+            cudaError_t r = cudaEventElapsedTime(&ms, e[ph], e[ph + 1]);
+            if (r == cudaSuccess) {
+                c->t_ms[ph] += ms;
+                c->t_n[ph] += 1;
+            } else if (c->t_err.empty()) {
+                c->t_err = std::string("cudaEventElapsedTime: ") + cudaGetErrorString(r);
+                cudaGetLastError();
+            }
+        }
+    }
+}
+
 // one step launched directly (kbase == k on entry; kbase == k+1 after)
 int direct_step(lpsim_ctx *c) {
-    Dev d = c->d;
-    d.s = c->sets[c->cur];
-    launch_step(d, 0, c->grid, c->block, c->stream);
+    bool compact = (c->k + 1) % c->R == 0;
+    c->cur = enqueue_step(c, 0, c->cur, compact);
     c->launches += 3;
-    if ((c->k + 1) % c->R == 0) {
-        c->launches += launch_compact(d, c->sets[c->cur ^ 1], c->w, 0, c->sort, c->grid, c->stream);
-        c->cur ^= 1;
-    }
-    launch_chunk_end(d, 1, c->stream);
+    if (compact) c->launches += c->sort ? 3 + 3ull * ((c->w.key_bits + 7) / 8) + 1 : 3;
+    launch_chunk_end(c->d, 1, c->stream);
     c->launches += 1;
     CU(cudaGetLastError());
+    if (c->timing) {
+        CU(cudaStreamSynchronize(c->stream));
+        collect_times(c, 1, c->k);
+    }
     c->k += 1;
     return LPSIM_OK;
 }
@@ -228,16 +286,8 @@ int capture_chunk(lpsim_ctx *c, int start_set) {
     cudaGraph_t g = nullptr;
     CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     int cur = start_set;
-    Dev d = c->d;
-    for (uint32_t koff = 0; koff < c->C; koff++) {
-        d.s = c->sets[cur];
-        launch_step(d, koff, c->grid, c->block, c->stream);
-        if ((koff + 1) % c->R == 0) {
-            launch_compact(d, c->sets[cur ^ 1], c->w, koff, c->sort, c->grid, c->stream);
-            cur ^= 1;
-        }
-    }
-    launch_chunk_end(d, c->C, c->stream);
+    for (uint32_t koff = 0; koff < c->C; koff++) cur = enqueue_step(c, koff, cur, (koff + 1) % c->R == 0);
+    launch_chunk_end(c->d, c->C, c->stream);
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     if (e != cudaSuccess) return fail(LPSIM_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     e = cudaGraphInstantiate(&c->graph[start_set], g, 0);
@@ -258,6 +308,10 @@ int chunk(lpsim_ctx *c) {
     if (!c->graph[c->cur]) TRY(capture_chunk(c, c->cur));
     CU(cudaGraphLaunch(c->graph[c->cur], c->stream));
     c->launches += chunk_launches(c);
+    if (c->timing) {
+        CU(cudaStreamSynchronize(c->stream));
+        collect_times(c, c->C, c->k);
+    }
     c->k += c->C;
     return LPSIM_OK;
 }
@@ -435,7 +489,7 @@ int lpsim_load_network(lpsim_ctx **out, const lpsim_network *net, const lpsim_pa
     uint32_t want = p->chunk_steps ? p->chunk_steps : 384;
     c->C = std::max(base, (want + base - 1) / base * base);
     c->block = p->block_size ? (int)p->block_size : 256;
-    c->grid = c->n_sm * (int)(p->blocks_per_sm ? p->blocks_per_sm : 4) * 256 / c->block;
+    c->grid = c->n_sm * (int)(p->blocks_per_sm ? p->blocks_per_sm : 6) * 256 / c->block;
     if (c->grid < 1) c->grid = 1;
     c->sort = (p->flags & 1u) == 0;
 
@@ -471,14 +525,15 @@ int lpsim_load_network(lpsim_ctx **out, const lpsim_network *net, const lpsim_pa
         if ((rc = dnew(c, d.map[i], c->map_bytes))) return bail(rc);
     for (int i = 0; i < 2; i++)
         if ((rc = dnew(c, d.imap[i], c->map_bytes))) return bail(rc);
-    if ((rc = dnew(c, d.claim, slots)) || (rc = dnew(c, d.ent, ne)) || (rc = dnew(c, d.ext, ne)) ||
+    if ((rc = dnew(c, d.claim[0], slots)) || (rc = dnew(c, d.claim[1], slots)) || (rc = dnew(c, d.ent, ne)) ||
+        (rc = dnew(c, d.ext, ne)) ||
         (rc = dnew(c, d.tts, ne)))
         return bail(rc);
     size_t nb = (size_t)ne * p->n_bins;
     if ((rc = dnew(c, d.bin_in, nb)) || (rc = dnew(c, d.bin_tt, nb)) || (rc = dnew(c, d.bin_cnt, nb)) ||
         (rc = dnew(c, d.bin_occ, nb)))
         return bail(rc);
-    if ((rc = dnew(c, d.counts, 4)) || (rc = dnew(c, d.kbase, 1)) || (rc = dnew(c, d.n_slots, 1)) ||
+    if ((rc = dnew(c, d.counts, 8)) || (rc = dnew(c, d.kbase, 1)) || (rc = dnew(c, d.n_slots, 1)) ||
         (rc = dnew(c, d.ctr, 8)) || (rc = dnew(c, d.err, 1)) || (rc = dnew(c, c->d_tmp, 4)))
         return bail(rc);
     if (cudaMallocHost(&c->h_ctr, 16 * 8) != cudaSuccess) return bail(fail(LPSIM_E_OOM, "pinned allocation failed"));
@@ -561,7 +616,12 @@ int lpsim_load_demand(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, con
     TRY(dnew(c, oqe, norg));
     TRY(dnew(c, dqid, n));
     TRY(dnew(c, d.org_head, norg));
+    TRY(dnew(c, d.org_dep, norg));
+    TRY(dnew(c, c->org_dep0, norg));
+    TRY(dnew(c, d.dslot, norg));
+    TRY(dnew(c, d.dprev, norg));
     TRY(dnew(c, d.dreq, norg));
+    for (int i = 0; i < 2; i++) TRY(dnew(c, d.dep_list[i], norg));
     const uint32_t cap = (uint32_t)n;
     for (int i = 0; i < 2; i++) TRY(alloc_slots(c, c->sets[i], cap));
     for (int i = 0; i < 2; i++) {
@@ -584,6 +644,9 @@ int lpsim_load_demand(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, con
     TRY(upload(c, oq, org_qoff.data(), norg * 4ull));
     TRY(upload(c, oqe, org_qend.data(), norg * 4ull));
     TRY(upload(c, dqid, qid.data(), n * 4));
+    std::vector<uint32_t> od0(norg);
+    for (uint32_t j = 0; j < norg; j++) od0[j] = dep[qid[org_qoff[j]]];
+    TRY(upload(c, c->org_dep0, od0.data(), norg * 4ull));
     d.dep = ddep;
     d.route = droute;
     d.roff = droff;
@@ -733,6 +796,37 @@ int lpsim_get_counters(lpsim_ctx *c, lpsim_counters *out) {
     out->lane_changes = c->h_ctr[2];
     out->slots = c->h_ctr[9] & 0xFFFFFFFFull;
     out->launches = c->launches;
+    return LPSIM_OK;
+}
+
+int lpsim_set_kernel_timing(lpsim_ctx *c, int on) {
+    if (!c) return fail(LPSIM_E_INVALID_ARG, "ctx is NULL");
+    CU(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < 2; i++)
+        if (c->graph[i]) {
+            cudaGraphExecDestroy(c->graph[i]);
+            c->graph[i] = nullptr;
+        }
+    if (on && c->ev.empty()) {
+        c->ev.resize(5ull * c->C);
+        for (auto &e : c->ev) CU(cudaEventCreate(&e));
+    }
+    c->timing = on != 0;
+    c->t_err.clear();
+    for (int i = 0; i < 4; i++) {
+        c->t_ms[i] = 0.0;
+        c->t_n[i] = 0;
+    }
+    return LPSIM_OK;
+}
+
+int lpsim_get_kernel_times(lpsim_ctx *c, double *ms, uint64_t *launches) {
+    if (!c || !ms || !launches) return fail(LPSIM_E_INVALID_ARG, "NULL argument");
+    if (!c->t_err.empty()) return fail(LPSIM_E_CUDA, c->t_err);
+    for (int i = 0; i < 4; i++) {
+        ms[i] = c->t_ms[i];
+        launches[i] = c->t_n[i];
+    }
     return LPSIM_OK;
 }
 

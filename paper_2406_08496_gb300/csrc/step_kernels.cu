@@ -113,14 +113,20 @@ __device__ __forceinline__ void put_cell(uint8_t *map, uint32_t idx, uint8_t val
     map[idx] = val;
 }
 
+// Target lane on edge `edge` for the movement onto `next` (kNoLane if none).
+__device__ __forceinline__ uint32_t target_lane(const Dev &d, const EdgeRec &er, uint32_t next) {
+    if (next == kNone) return kNoLane;
+    return ((uint32_t)d.orank[next] * er.lanes) / d.node[er.dst].nout;
+}
+
 // Lane a vehicle entering edge `en` asks for: lanes ordered by distance to
 // the target lane of the movement after `en` (ties to the lower index); the
 // first whose cell 0 is empty in the step-k map.  kNone if none.
 __device__ __forceinline__ uint32_t entry_lane(const Dev &d, const uint8_t *Mc, uint32_t en, const EdgeRec &enr,
                                                uint32_t next_after) {
     uint32_t nl = enr.lanes;
-    uint32_t tl = 0;
-    if (next_after != kNone) tl = ((uint32_t)d.orank[next_after] * nl) / d.node[enr.dst].nout;
+    uint32_t tl = target_lane(d, enr, next_after);
+    if (tl == kNoLane) tl = 0;
     uint32_t stride = row_stride(enr.len);
     for (uint32_t dd = 0; dd < nl; dd++) {
         if (tl >= dd && Mc[enr.moff + (tl - dd) * stride] == kEmpty) return tl - dd;
@@ -168,15 +174,18 @@ __device__ __forceinline__ void block_add(unsigned long long *dst, uint32_t val)
 // ----------------------------------------------------------------------- P1
 
 template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK) step_p1(Dev d, uint32_t koff) {
+__global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) step_p1(Dev d, uint32_t koff) {
     const uint32_t k = *d.kbase + koff;
+    const uint32_t par = k & 1u;
     const uint8_t *Mc = d.map[k % 3];
     uint8_t *Mn = d.map[(k + 1) % 3];
     uint8_t *Mo = d.map[(k + 2) % 3];       // holds step k-1: erase
-    uint8_t *Iw = d.imap[k & 1];
-    uint8_t *Io = d.imap[(k + 1) & 1];      // marks of step k-1: clear
-    const float *xc = d.s.x[k & 1], *vc = d.s.v[k & 1];
-    float *xw = d.s.x[(k + 1) & 1], *vw = d.s.v[(k + 1) & 1];
+    uint8_t *Iw = d.imap[par];
+    uint8_t *Io = d.imap[par ^ 1u];         // marks of step k-1: clear
+    uint32_t *claim = d.claim[par];
+    uint32_t *claim_old = d.claim[par ^ 1u]; // slots won at step k-1: reset
+    const float *xc = d.s.x[par], *vc = d.s.v[par];
+    float *xw = d.s.x[par ^ 1u], *vw = d.s.v[par ^ 1u];
     const uint32_t n = *d.n_slots;
     const uint32_t total = n + d.n_org;
     const Model &m = d.m;
@@ -186,21 +195,28 @@ __global__ void __launch_bounds__(BLOCK) step_p1(Dev d, uint32_t koff) {
 
     for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < total; i += gridDim.x * BLOCK) {
         if (i >= n) {
-            // departure request of origin edge j: the queue head, once its step has come
-            uint32_t j = i - n;
+            // origin edge j: reset the claim its departure won last step; ask
+            // for a departure of the queue head once its step has come
+            const uint32_t j = i - n;
+            const uint32_t dp = d.dprev[j];
+            if (dp != kNone) {
+                claim_old[dp] = kNone;
+                d.dprev[j] = kNone;
+            }
             uint8_t req = kEmpty;
-            uint32_t qh = d.org_qoff[j] + d.org_head[j];
-            if (qh < d.org_qend[j]) {
-                uint32_t h = d.qid[qh];
-                if (d.dep[h] <= k) {
-                    uint32_t e0 = d.org_edge[j];
-                    EdgeRec er = d.edge[e0];
-                    uint32_t r0 = d.roff[h], r1 = d.roff[h + 1];
-                    uint32_t l = entry_lane(d, Mc, e0, er, r0 + 1 < r1 ? d.route[r0 + 1] : kNone);
-                    if (l != kNone) {
-                        atomicMin(&d.claim[d.slot_off[e0] + l], h);
-                        req = (uint8_t)l;
-                    }
+            if (d.org_dep[j] <= k) {
+                const uint32_t h = d.qid[d.org_qoff[j] + d.org_head[j]];
+                const uint32_t e0 = d.org_edge[j];
+                const EdgeRec er = d.edge[e0];
+                const uint32_t r0 = d.roff[h], r1 = d.roff[h + 1];
+                const uint32_t l = entry_lane(d, Mc, e0, er, r0 + 1 < r1 ? d.route[r0 + 1] : kNone);
+                if (l != kNone) {
+                    const uint32_t slot = d.slot_off[e0] + l;
+                    atomicMin(&claim[slot], h);
+                    d.dslot[j] = slot;
+                    req = (uint8_t)l;
+                    const uint32_t pos = atomicAdd(&d.counts[4 + par], 1u);
+                    d.dep_list[par][pos] = j;
                 }
             }
             d.dreq[j] = req;
@@ -210,12 +226,17 @@ __global__ void __launch_bounds__(BLOCK) step_p1(Dev d, uint32_t koff) {
         const uint8_t flag = d.s.flag[s];
         if (flag == kDead) continue;
         {
-            uint32_t pc = d.s.pcell[s];
+            const uint32_t pc = d.s.pcell[s];
             if (pc != kNone) Mo[pc] = kEmpty;
-            uint32_t im = d.s.imark[s];
+            const uint32_t im = d.s.imark[s];
             if (im != kNone) {
                 Io[im] = 0;
                 d.s.imark[s] = kNone;
+            }
+            const uint32_t cp = d.s.cprev[s];
+            if (cp != kNone) {
+                claim_old[cp] = kNone;
+                d.s.cprev[s] = kNone;
             }
         }
         if (flag == kArrivedPending) {
@@ -224,24 +245,20 @@ __global__ void __launch_bounds__(BLOCK) step_p1(Dev d, uint32_t koff) {
             continue;
         }
         live++;
-        const uint32_t id = d.s.id[s];
-        const uint32_t e = d.s.e[s];
-        const uint32_t ln = d.s.lane[s];
         const float x = xc[s], v = vc[s];
-        const EdgeRec er = d.edge[e];
-        const uint32_t len = er.len;
-        const uint32_t stride = row_stride(len);
-        const uint32_t base = er.moff + ln * stride;
+        const uint32_t base = d.s.base[s];
+        const uint32_t len = d.s.len[s];
+        const float v0 = d.s.v0[s];
         const uint32_t c = (uint32_t)x;
         d.s.pcell[s] = base + c;
-        if (sample) atomicAdd(&d.bin_occ[(size_t)e * m.n_bins + k / m.bin_steps], 1u);
+        if (sample) atomicAdd(&d.bin_occ[(size_t)d.s.e[s] * m.n_bins + k / m.bin_steps], 1u);
 
         // leader: nearest occupied cell ahead in the own lane of the own edge.
         // Cells beyond both d_front and the farthest reach of this step
         // cannot change the result, so the scan stops there.
-        float d_front = (2.0f * m.dt) * v;
-        float vmax_step = fmaxf(er.v0, v + m.a * m.dt);
-        float reach = fmaxf(d_front, vmax_step * m.dt + m.s0);
+        const float d_front = (2.0f * m.dt) * v;
+        const float vmax_step = fmaxf(v0, v + m.a * m.dt);
+        const float reach = fmaxf(d_front, vmax_step * m.dt + m.s0);
         uint32_t hi = c + (uint32_t)fminf(reach, 65535.0f) + 2u;
         if (hi > len - 1) hi = len - 1;
         const uint32_t cf = first_occupied(Mc + base, c + 1, hi);
@@ -249,21 +266,23 @@ __global__ void __launch_bounds__(BLOCK) step_p1(Dev d, uint32_t koff) {
 
         float vn;
         if (has_f && ((float)cf - x) <= d_front)
-            vn = idm_speed(m, v, (float)Mc[base + cf], (float)cf - x, er.v0);
+            vn = idm_speed(m, v, (float)Mc[base + cf], (float)cf - x, v0);
         else
-            vn = er.v0;
+            vn = v0;
         float xn = x + vn * m.dt;
         if (has_f) {
-            float lim = (float)cf - m.s0;
+            const float lim = (float)cf - m.s0;
             if (xn > lim) {
                 xn = x > lim ? x : lim;
                 vn = 0.0f;
             }
         }
         const float L = (float)len;
-        const uint32_t rpos = d.s.rpos[s], rlast = d.s.rlast[s];
         if (xn >= L) {
+            const uint32_t rpos = d.s.rpos[s], rlast = d.s.rlast[s];
+            const uint32_t e = d.s.e[s];
             if (rpos == rlast) {
+                const uint32_t id = d.s.id[s];
                 stat_exit(d, e, k, d.s.tent[s]);
                 d.arr[id] = k + 1;
                 d.status[id] = kArrived;
@@ -273,23 +292,28 @@ __global__ void __launch_bounds__(BLOCK) step_p1(Dev d, uint32_t koff) {
                 continue;
             }
             bool cross = false;
+            const EdgeRec er = d.edge[e];
             if (is_green(d.node[er.dst], er.arank, k)) {
                 const uint32_t en = d.route[rpos + 1];
                 const EdgeRec enr = d.edge[en];
-                uint32_t l = entry_lane(d, Mc, en, enr, rpos + 1 < rlast ? d.route[rpos + 2] : kNone);
+                const uint32_t after = rpos + 1 < rlast ? d.route[rpos + 2] : kNone;
+                const uint32_t l = entry_lane(d, Mc, en, enr, after);
                 if (l != kNone) {
-                    atomicMin(&d.claim[d.slot_off[en] + l], id);
+                    const uint32_t slot = d.slot_off[en] + l;
+                    atomicMin(&claim[slot], d.s.id[s]);
                     d.s.tl[s] = (uint8_t)l;
+                    d.s.cslot[s] = slot;
+                    d.s.tln[s] = (uint8_t)target_lane(d, enr, after);
                     d.s.act[s] = kActCross;
                     vw[s] = vn;
-                    uint32_t pos = atomicAdd(&d.counts[k & 1], 1u);
-                    d.cross_list[k & 1][pos] = s;
+                    const uint32_t pos = atomicAdd(&d.counts[par], 1u);
+                    d.cross_list[par][pos] = s;
                     cross = true;
                 }
             }
             if (!cross) {
-                float lim = L - 1.0f;
-                float xh = x > lim ? x : lim;
+                const float lim = L - 1.0f;
+                const float xh = x > lim ? x : lim;
                 xw[s] = xh;
                 vw[s] = 0.0f;
                 put_cell(Mn, base + (uint32_t)xh, 0, d.err);
@@ -302,21 +326,20 @@ __global__ void __launch_bounds__(BLOCK) step_p1(Dev d, uint32_t koff) {
         const uint32_t cn = (uint32_t)xn;
         put_cell(Mn, base + cn, speed_byte(vn), d.err);
         uint8_t act = kActStay;
-        if (er.lanes > 1 && rpos < rlast) {
-            uint32_t tl = ((uint32_t)d.orank[d.route[rpos + 1]] * er.lanes) / d.node[er.dst].nout;
-            if (tl != ln) {
-                bool up = tl > ln;
-                if (up == ((k & 1u) == 1u)) {
-                    float xrem = L - x;
-                    float mp = xrem >= m.x0 ? 0.0f : 1.0f - xrem / m.x0;
-                    if (unit24(lc_hash(m.seed, id, k)) < mp) {
-                        act = kActIntend;
-                        d.s.tl[s] = up ? 1 : 0;  // direction
-                        Iw[base + cn] = 1;
-                        d.s.imark[s] = base + cn;
-                        uint32_t pos = atomicAdd(&d.counts[2 + (k & 1)], 1u);
-                        d.intend_list[k & 1][pos] = s;
-                    }
+        const uint32_t tl = d.s.tlc[s];  // kNoLane on the last edge of the route
+        const uint32_t ln = d.s.lane[s];
+        if (tl != kNoLane && tl != ln) {
+            const bool up = tl > ln;
+            if (up == (par == 1u)) {
+                const float xrem = L - x;
+                const float mp = xrem >= m.x0 ? 0.0f : 1.0f - xrem / m.x0;
+                if (unit24(lc_hash(m.seed, d.s.id[s], k)) < mp) {
+                    act = kActIntend;
+                    d.s.tl[s] = up ? 1 : 0;  // direction
+                    Iw[base + cn] = 1;
+                    d.s.imark[s] = base + cn;
+                    const uint32_t pos = atomicAdd(&d.counts[2 + par], 1u);
+                    d.intend_list[par][pos] = s;
                 }
             }
         }
@@ -331,70 +354,86 @@ __global__ void __launch_bounds__(BLOCK) step_p1(Dev d, uint32_t koff) {
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) step_p2(Dev d, uint32_t koff) {
     const uint32_t k = *d.kbase + koff;
+    const uint32_t par = k & 1u;
     uint8_t *Mn = d.map[(k + 1) % 3];
-    const float *xc = d.s.x[k & 1];
-    float *xw = d.s.x[(k + 1) & 1], *vw = d.s.v[(k + 1) & 1];
-    const uint32_t ncross = d.counts[k & 1];
-    const uint32_t total = ncross + d.n_org;
-    const uint32_t *list = d.cross_list[k & 1];
+    const uint32_t *claim = d.claim[par];
+    const float *xc = d.s.x[par];
+    float *xw = d.s.x[par ^ 1u], *vw = d.s.v[par ^ 1u];
+    const uint32_t ncross = d.counts[par];
+    const uint32_t total = ncross + d.counts[4 + par];
+    const uint32_t *list = d.cross_list[par];
     uint32_t events = 0, departed = 0;
     for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < total; i += gridDim.x * BLOCK) {
         if (i < ncross) {
             const uint32_t s = list[i];
             const uint32_t id = d.s.id[s];
-            const uint32_t e = d.s.e[s];
-            const uint32_t rpos = d.s.rpos[s];
-            const uint32_t en = d.route[rpos + 1];
-            const uint32_t l = d.s.tl[s];
-            const EdgeRec er = d.edge[e];
-            if (d.claim[d.slot_off[en] + l] == id) {
+            const uint32_t cslot = d.s.cslot[s];
+            if (claim[cslot] == id) {
+                const uint32_t rpos = d.s.rpos[s];
+                const uint32_t e = d.s.e[s];
+                const uint32_t en = d.route[rpos + 1];
                 const EdgeRec enr = d.edge[en];
+                const uint32_t l = d.s.tl[s];
+                const uint32_t nbase = enr.moff + l * row_stride(enr.len);
                 stat_exit(d, e, k, d.s.tent[s]);
                 stat_entry(d, en, k);
                 d.s.e[s] = en;
                 d.s.rpos[s] = rpos + 1;
                 d.s.lane[s] = (uint8_t)l;
                 d.s.tent[s] = k + 1;
-                d.s.win[s] = 1;
+                d.s.tlc[s] = d.s.tln[s];
+                d.s.base[s] = nbase;
+                d.s.len[s] = enr.len;
+                d.s.v0[s] = enr.v0;
+                d.s.cprev[s] = cslot;
                 xw[s] = 0.0f;
-                put_cell(Mn, enr.moff + l * row_stride(enr.len), speed_byte(vw[s]), d.err);
+                put_cell(Mn, nbase, speed_byte(vw[s]), d.err);
                 events++;
             } else {
-                d.s.win[s] = 0;
-                float x = xc[s];
-                float lim = (float)er.len - 1.0f;
-                float xh = x > lim ? x : lim;
+                const float x = xc[s];
+                const float lim = (float)d.s.len[s] - 1.0f;
+                const float xh = x > lim ? x : lim;
                 xw[s] = xh;
                 vw[s] = 0.0f;
-                put_cell(Mn, er.moff + d.s.lane[s] * row_stride(er.len) + (uint32_t)xh, 0, d.err);
+                put_cell(Mn, d.s.base[s] + (uint32_t)xh, 0, d.err);
             }
             continue;
         }
-        const uint32_t j = i - ncross;
-        const uint8_t l = d.dreq[j];
-        if (l == kEmpty) continue;
-        const uint32_t e0 = d.org_edge[j];
-        const uint32_t h = d.qid[d.org_qoff[j] + d.org_head[j]];
-        if (d.claim[d.slot_off[e0] + l] != h) continue;
+        const uint32_t j = d.dep_list[par][i - ncross];
+        const uint32_t qh = d.org_qoff[j] + d.org_head[j];
+        const uint32_t h = d.qid[qh];
+        const uint32_t slot = d.dslot[j];
+        if (claim[slot] != h) continue;
         const uint32_t s = atomicAdd(d.n_slots, 1u);
         if (s >= d.cap) {
             atomicOr(d.err, kErrSlotOverflow);
             continue;
         }
+        const uint32_t e0 = d.org_edge[j];
         const EdgeRec er = d.edge[e0];
+        const uint32_t l = d.dreq[j];
+        const uint32_t r0 = d.roff[h], r1 = d.roff[h + 1];
+        const uint32_t b0 = er.moff + l * row_stride(er.len);
         d.s.id[s] = h;
         d.s.e[s] = e0;
-        d.s.rpos[s] = d.roff[h];
-        d.s.rlast[s] = d.roff[h + 1] - 1;
-        d.s.lane[s] = l;
+        d.s.rpos[s] = r0;
+        d.s.rlast[s] = r1 - 1;
+        d.s.lane[s] = (uint8_t)l;
+        d.s.tlc[s] = (uint8_t)target_lane(d, er, r0 + 1 < r1 ? d.route[r0 + 1] : kNone);
+        d.s.base[s] = b0;
+        d.s.len[s] = er.len;
+        d.s.v0[s] = er.v0;
         d.s.tent[s] = k + 1;
         d.s.pcell[s] = kNone;
         d.s.imark[s] = kNone;
+        d.s.cprev[s] = kNone;
         d.s.flag[s] = kLive;
         xw[s] = 0.0f;
         vw[s] = 0.0f;
-        put_cell(Mn, er.moff + l * row_stride(er.len), 0, d.err);
+        put_cell(Mn, b0, 0, d.err);
+        d.dprev[j] = slot;
         d.org_head[j] += 1;
+        d.org_dep[j] = qh + 1 < d.org_qend[j] ? d.dep[d.qid[qh + 1]] : kNone;
         d.dep_act[h] = k + 1;
         d.status[h] = kActive;
         stat_entry(d, e0, k);
@@ -410,96 +449,83 @@ __global__ void __launch_bounds__(BLOCK) step_p2(Dev d, uint32_t koff) {
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) step_p3(Dev d, uint32_t koff) {
     const uint32_t k = *d.kbase + koff;
+    const uint32_t par = k & 1u;
     const uint8_t *Mc = d.map[k % 3];
     uint8_t *Mn = d.map[(k + 1) % 3];
-    const uint8_t *Iw = d.imap[k & 1];
-    const float *xc = d.s.x[k & 1];
-    const float *xw = d.s.x[(k + 1) & 1], *vw = d.s.v[(k + 1) & 1];
-    const uint32_t nint = d.counts[2 + (k & 1)];
-    const uint32_t ncross = d.counts[k & 1];
-    const uint32_t total = nint + ncross + d.n_org;
+    const uint8_t *Iw = d.imap[par];
+    const float *xc = d.s.x[par];
+    const float *xw = d.s.x[par ^ 1u], *vw = d.s.v[par ^ 1u];
+    const uint32_t nint = d.counts[2 + par];
     const Model &m = d.m;
     uint32_t changes = 0;
-    for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < total; i += gridDim.x * BLOCK) {
-        if (i < nint) {
-            const uint32_t s = d.intend_list[k & 1][i];
-            const uint32_t id = d.s.id[s];
-            const uint32_t e = d.s.e[s];
-            const uint32_t ln = d.s.lane[s];
-            const uint32_t ln2 = d.s.tl[s] ? ln + 1 : ln - 1;
-            const EdgeRec er = d.edge[e];
-            const uint32_t len = er.len, stride = row_stride(len);
-            const uint8_t *row2 = Mc + er.moff + ln2 * stride;
-            const float x = xc[s], xn = xw[s], vn = vw[s];
-            const uint32_t c0 = (uint32_t)x, cn = (uint32_t)xn;
-            uint32_t hi = c0 + 63u < len - 1 ? c0 + 63u : len - 1;
-            const uint32_t ca = first_occupied(row2, c0, hi);
-            const uint32_t cb = c0 > 0 ? last_occupied(row2, c0 > 64u ? c0 - 64u : 0u, c0 - 1) : kNone;
-            float eps_a = 0.0f, eps_b = 0.0f;
-            if (m.eps_amp > 0.0f) {
-                uint64_t h = lc_hash(m.seed, id, k);
-                eps_a = m.eps_amp * (2.0f * unit24(splitmix64_mix(h ^ 0x632BE59BD9B4E019ull)) - 1.0f);
-                eps_b = m.eps_amp * (2.0f * unit24(splitmix64_mix(h ^ 0x8CB92BA72F3D8DD7ull)) - 1.0f);
-            }
-            bool ok = true;
-            if (ca != kNone) {
-                float va = (float)row2[ca];
-                float G_lead = (m.g_a + fmax0(m.alpha_i * vn - m.alpha_a * va)) + eps_a;
-                ok = ((float)ca - xn) >= G_lead;
-            }
-            if (ok && cb != kNone) {
-                float vb = (float)row2[cb];
-                float G_lag = (m.g_b + fmax0(m.alpha_b * vb - m.alpha_i * vn)) + eps_b;
-                ok = (xn - (float)cb) >= G_lag;
-            }
-            if (ok && cn >= 1) {
-                const uint32_t tgt = er.moff + ln2 * stride + cn;
-                if (Mn[tgt] == kEmpty && Iw[tgt] == 0) {
-                    const uint32_t own = er.moff + ln * stride + cn;
-                    Mn[tgt] = Mn[own];
-                    Mn[own] = kEmpty;
-                    d.s.lane[s] = (uint8_t)ln2;
-                    changes++;
-                }
-            }
-            continue;
+    for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < nint; i += gridDim.x * BLOCK) {
+        const uint32_t s = d.intend_list[par][i];
+        const uint32_t ln = d.s.lane[s];
+        const bool up = d.s.tl[s] != 0;
+        const uint32_t len = d.s.len[s], stride = row_stride(len);
+        const uint32_t base = d.s.base[s];
+        const uint32_t base2 = up ? base + stride : base - stride;
+        const uint8_t *row2 = Mc + base2;
+        const float x = xc[s], xn = xw[s], vn = vw[s];
+        const uint32_t c0 = (uint32_t)x, cn = (uint32_t)xn;
+        const uint32_t hi = c0 + 63u < len - 1 ? c0 + 63u : len - 1;
+        const uint32_t ca = first_occupied(row2, c0, hi);
+        const uint32_t cb = c0 > 0 ? last_occupied(row2, c0 > 64u ? c0 - 64u : 0u, c0 - 1) : kNone;
+        float eps_a = 0.0f, eps_b = 0.0f;
+        if (m.eps_amp > 0.0f) {
+            const uint64_t h = lc_hash(m.seed, d.s.id[s], k);
+            eps_a = m.eps_amp * (2.0f * unit24(splitmix64_mix(h ^ 0x632BE59BD9B4E019ull)) - 1.0f);
+            eps_b = m.eps_amp * (2.0f * unit24(splitmix64_mix(h ^ 0x8CB92BA72F3D8DD7ull)) - 1.0f);
         }
-        if (i < nint + ncross) {
-            const uint32_t s = d.cross_list[k & 1][i - nint];
-            if (d.s.win[s]) d.claim[d.slot_off[d.s.e[s]] + d.s.lane[s]] = kNone;
-            continue;
+        bool ok = true;
+        if (ca != kNone) {
+            const float va = (float)row2[ca];
+            const float G_lead = (m.g_a + fmax0(m.alpha_i * vn - m.alpha_a * va)) + eps_a;
+            ok = ((float)ca - xn) >= G_lead;
         }
-        const uint32_t j = i - nint - ncross;
-        const uint8_t l = d.dreq[j];
-        if (l != kEmpty) d.claim[d.slot_off[d.org_edge[j]] + l] = kNone;
+        if (ok && cb != kNone) {
+            const float vb = (float)row2[cb];
+            const float G_lag = (m.g_b + fmax0(m.alpha_b * vb - m.alpha_i * vn)) + eps_b;
+            ok = (xn - (float)cb) >= G_lag;
+        }
+        if (ok && cn >= 1) {
+            const uint32_t tgt = base2 + cn;
+            if (Mn[tgt] == kEmpty && Iw[tgt] == 0) {
+                const uint32_t own = base + cn;
+                Mn[tgt] = Mn[own];
+                Mn[own] = kEmpty;
+                d.s.lane[s] = (uint8_t)(up ? ln + 1 : ln - 1);
+                d.s.base[s] = base2;
+                changes++;
+            }
+        }
     }
     if (changes) atomicAdd(&d.ctr[2], (unsigned long long)changes);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        d.counts[(k + 1) & 1] = 0;
-        d.counts[2 + ((k + 1) & 1)] = 0;
+        d.counts[par ^ 1u] = 0;
+        d.counts[2 + (par ^ 1u)] = 0;
+        d.counts[4 + (par ^ 1u)] = 0;
     }
 }
 
 __global__ void chunk_end(Dev d, uint32_t steps) { *d.kbase += steps; }
 
-void launch_step(const Dev &d, uint32_t koff, int grid, int block, cudaStream_t st) {
+void launch_phase(const Dev &d, int phase, uint32_t koff, int grid, int block, cudaStream_t st) {
+    // step_p2 and step_p3 walk short lists (crossers, intenders, origin
+    // edges): a quarter of the grid is plenty
+    const int g = phase == 1 ? grid : (grid + 3) / 4;
+#define LPSIM_PHASE(B)                                        \
+    do {                                                      \
+        if (phase == 1) step_p1<B><<<g, B, 0, st>>>(d, koff); \
+        else if (phase == 2) step_p2<B><<<g, B, 0, st>>>(d, koff); \
+        else step_p3<B><<<g, B, 0, st>>>(d, koff);            \
+    } while (0)
     switch (block) {
-    case 128:
-        step_p1<128><<<grid, 128, 0, st>>>(d, koff);
-        step_p2<128><<<grid, 128, 0, st>>>(d, koff);
-        step_p3<128><<<grid, 128, 0, st>>>(d, koff);
-        break;
-    case 512:
-        step_p1<512><<<grid, 512, 0, st>>>(d, koff);
-        step_p2<512><<<grid, 512, 0, st>>>(d, koff);
-        step_p3<512><<<grid, 512, 0, st>>>(d, koff);
-        break;
-    default:
-        step_p1<256><<<grid, 256, 0, st>>>(d, koff);
-        step_p2<256><<<grid, 256, 0, st>>>(d, koff);
-        step_p3<256><<<grid, 256, 0, st>>>(d, koff);
-        break;
+    case 128: LPSIM_PHASE(128); break;
+    case 512: LPSIM_PHASE(512); break;
+    default: LPSIM_PHASE(256); break;
     }
+#undef LPSIM_PHASE
 }
 
 void launch_chunk_end(const Dev &d, uint32_t steps, cudaStream_t st) { chunk_end<<<1, 1, 0, st>>>(d, steps); }
