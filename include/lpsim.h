@@ -210,6 +210,36 @@ int lpsim_get_counters(lpsim_ctx *ctx, lpsim_counters *out);
 int lpsim_set_kernel_timing(lpsim_ctx *ctx, int on);
 int lpsim_get_kernel_times(lpsim_ctx *ctx, double *ms, uint64_t *launches);
 
+/* Largest trip count lpsim_get_state_noalloc serves: its scratch is a fixed
+ * device array of LPSIM_NOALLOC_MAX_VEHICLES * 17 bytes (17 MiB). */
+#define LPSIM_NOALLOC_MAX_VEHICLES 1048576u
+
+/* lpsim_get_state without allocating anything.  The paper has no
+ * counterpart: this is a service entry point of this library.
+ *
+ * lpsim_get_state takes device scratch for the call from cudaMalloc or the
+ * allocator callback.  Callers that cannot allocate at that moment -- an
+ * application whose device memory is a fixed pool already handed out, a
+ * service capped at a device-memory budget it must not exceed while
+ * running, or a host that installed no allocator and must not touch
+ * cudaMalloc -- use this variant instead.  Its scratch is one file-scope
+ * device array of the size above, which every GPU that loads the library
+ * holds until the process exits.  The call makes no cudaMalloc, cudaFree or
+ * allocator call: it clears the array, runs the same gather kernel on the
+ * context's stream and copies into the caller's host buffers (same layout
+ * and NULL rules as lpsim_get_state).
+ *
+ * n above LPSIM_NOALLOC_MAX_VEHICLES gives LPSIM_E_INVALID_ARG (use
+ * lpsim_get_state).  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device current); make that first
+ * call before any stream capture on the device.  Every call on a device
+ * shares the one array and it keeps the last call's contents (the call
+ * clears it before use): calls whose work overlaps on the GPU -- two
+ * contexts on different streams, or two threads -- race on it and must be
+ * serialised by the caller. */
+int lpsim_get_state_noalloc(lpsim_ctx *ctx, uint64_t n, float *x, float *v, uint32_t *edge, uint8_t *lane,
+                            uint32_t *route_idx, uint8_t *status);
+
 /* Release every device and host resource of the context (NULL is a no-op). */
 void lpsim_destroy(lpsim_ctx *ctx);
 

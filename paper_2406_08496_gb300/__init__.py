@@ -29,7 +29,8 @@ FLAG_NO_SORT = 1
 EXPORTED = ["lpsim_last_error", "lpsim_version", "lpsim_set_allocator", "lpsim_load_network",
             "lpsim_load_demand", "lpsim_step", "lpsim_run", "lpsim_reset", "lpsim_link_stats",
             "lpsim_get_trips", "lpsim_get_state", "lpsim_lane_map_size", "lpsim_get_lane_map",
-            "lpsim_get_counters", "lpsim_set_kernel_timing", "lpsim_get_kernel_times", "lpsim_destroy"]
+            "lpsim_get_counters", "lpsim_set_kernel_timing", "lpsim_get_kernel_times", "lpsim_get_state_noalloc",
+            "lpsim_destroy"]
 
 STATUS = {0: "LPSIM_OK", -1: "LPSIM_E_INVALID_ARG", -2: "LPSIM_E_OOM", -3: "LPSIM_E_CUDA", -4: "LPSIM_E_STATE",
           -5: "LPSIM_E_TIMEOUT", -6: "LPSIM_E_GRIDLOCK", -7: "LPSIM_E_INVARIANT"}

@@ -19,9 +19,12 @@
 #include <vector>
 
 #include "../../include/lpsim.h"
+#include "ctx.h"
 #include "lpsim_dev.cuh"
 
 using namespace lpsim;
+
+int lpsim_fail(int code, const std::string &msg);
 
 namespace {
 
@@ -43,75 +46,6 @@ int fail(int code, const std::string &msg) {
     } while (0)
 
 }  // namespace
-
-struct lpsim_ctx {
-    int device = 0;
-    int n_sm = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    lpsim_params p{};
-    uint32_t n_nodes = 0, n_edges = 0;
-    // allocation
-    void *(*alloc)(size_t, void *) = nullptr;
-    void (*release)(void *, void *) = nullptr;
-    void *alloc_user = nullptr;
-    std::vector<void *> blocks;
-    // host mirror of the layout (queries)
-    std::vector<uint32_t> moff;
-    std::vector<uint16_t> len;
-    std::vector<uint8_t> lanes;
-    std::vector<uint32_t> src, dst;
-    uint64_t map_bytes = 0, canon_cells = 0, lane_slots = 0;
-    // device state
-    Dev d{};
-    Slots sets[2]{};
-    int cur = 0;
-    SortWork w{};
-    bool loaded = false;
-    uint64_t n_trips = 0;
-    uint32_t k = 0;
-    uint32_t R = 64, C = 384;
-    int grid = 0, block = 256;
-    bool sort = true;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    unsigned long long *h_ctr = nullptr;  // pinned: ctr[0..7], err, n_slots, ...
-    uint32_t *d_tmp = nullptr;
-    uint32_t *org_dep0 = nullptr;    // departure step of each origin queue's first trip
-    uint64_t launches = 0;
-    uint64_t stall_steps = 0;
-    unsigned long long last_progress = 0;
-    // per-kernel timing (events around every phase launch of every step)
-    bool timing = false;
-    std::vector<cudaEvent_t> ev;     // 5 per step of a chunk
-    double t_ms[4] = {0, 0, 0, 0};   // step_p1, step_p2, step_p3, compaction + sort
-    uint64_t t_n[4] = {0, 0, 0, 0};
-    std::string t_err;               // first failure of cudaEventElapsedTime
-
-    void *dalloc(size_t bytes) {
-        if (bytes == 0) bytes = 16;
-        bytes = (bytes + 255) & ~size_t(255);
-        void *ptr = nullptr;
-        if (alloc) {
-            ptr = alloc(bytes, alloc_user);
-        } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
-            ptr = nullptr;
-        }
-        if (ptr) blocks.push_back(ptr);
-        return ptr;
-    }
-    ~lpsim_ctx() {
-        for (int i = 0; i < 2; i++)
-            if (graph[i]) cudaGraphExecDestroy(graph[i]);
-        for (cudaEvent_t e : ev) cudaEventDestroy(e);
-        if (stream) cudaStreamSynchronize(stream);
-        for (void *b : blocks) {
-            if (release) release(b, alloc_user);
-            else cudaFree(b);
-        }
-        if (h_ctr) cudaFreeHost(h_ctr);
-        if (own_stream) cudaStreamDestroy(stream);
-    }
-};
 
 namespace {
 
@@ -373,6 +307,8 @@ int run_steps(lpsim_ctx *c, uint64_t n, bool stop_done, uint64_t *taken) {
 }
 
 }  // namespace
+
+int lpsim_fail(int code, const std::string &msg) { return fail(code, msg); }
 
 extern "C" {
 

@@ -68,6 +68,10 @@ def test_argument_checks_without_gpu(lib):
     bad = L.Params(**dict(L.DEFAULT_PARAMS, dt=0.0))
     lanes[0] = 2
     assert lib.lpsim_load_network(ctypes.byref(h), ctypes.byref(net), ctypes.byref(bad), None) == -1
+    # the allocation-free query refuses more vehicles than its fixed scratch
+    lib.lpsim_get_state_noalloc.argtypes = [P, ctypes.c_uint64, P, P, P, P, P, P]
+    assert lib.lpsim_get_state_noalloc(None, 1048577, None, None, None, None, None, None) == -1
+    assert b"exceed" in lib.lpsim_last_error()
 
 
 def test_binding_refuses_without_library(tmp_path):
