@@ -200,6 +200,58 @@ int lpsim_get_lane_map(lpsim_ctx *ctx, uint8_t *out, uint64_t size);
 
 int lpsim_get_counters(lpsim_ctx *ctx, lpsim_counters *out);
 
+/* ---- batched scenarios ------------------------------------------------
+ * Many independent scenarios (networks with their own trips and lane-change
+ * seed) simulated as one: the networks are laid side by side (node, edge and
+ * lane-map ids of scenario s follow those of scenario s-1), so one launch of
+ * each step kernel advances every scenario.  Vehicles of different scenarios
+ * never share an edge, and each vehicle draws its lane-change numbers from
+ * its scenario's seed and its id within the scenario, so every scenario's
+ * results are identical to simulating it alone.  Query results (link
+ * statistics, lane map, per-vehicle arrays) cover the whole batch in
+ * scenario order; lpsim_batch_offsets gives where each scenario starts. */
+int lpsim_load_network_batch(lpsim_ctx **out, uint32_t n_scen, const lpsim_network *nets, const lpsim_params *p,
+                             void *stream);
+/* Trips of scenario s: n_trips[s] trips with the arrays of lpsim_load_demand
+ * in scenario-local edge ids.  seeds (nullable): lane-change seed per
+ * scenario (default p->seed).  out_vehicle_id (nullable): batch vehicle id
+ * of every trip, scenarios one after the other. */
+int lpsim_load_demand_batch(lpsim_ctx *ctx, uint32_t n_scen, const uint64_t *n_trips,
+                            const uint32_t *const *depart_step, const uint64_t *const *route_off,
+                            const uint32_t *const *route_edges, const uint64_t *seeds, uint32_t *out_vehicle_id);
+/* Prefix offsets (n_scen + 1 entries each, nullable) of nodes, edges,
+ * canonical lane-map cells and trips per scenario. */
+int lpsim_batch_offsets(lpsim_ctx *ctx, uint32_t n_scen, uint64_t *node_off, uint64_t *edge_off, uint64_t *cell_off,
+                        uint64_t *trip_off);
+
+/* ---- checkpoint and launch tuning -------------------------------------
+ * lpsim_snapshot copies the whole simulation state (lane maps, vehicles,
+ * queues, statistics, step) into device memory held by the context;
+ * lpsim_restore returns to it.  Stepping after a restore gives exactly the
+ * results of stepping from the snapshot the first time. */
+int lpsim_snapshot(lpsim_ctx *ctx);
+int lpsim_restore(lpsim_ctx *ctx);
+
+typedef struct lpsim_tune_result {
+    uint32_t block_size, blocks_per_sm, sort_period, chunk_steps; /* chosen (now in use) */
+    double best_ms;     /* wall time of the chosen configuration over the window */
+    double default_ms;  /* wall time of the configuration in use before tuning */
+    uint32_t n_tried;
+} lpsim_tune_result;
+
+/* Autotuner: from the current state, run window_steps steps under each
+ * candidate launch configuration (block size 128/256/512, 2/4/6 resident
+ * 256-thread blocks per SM, sort period 32/64/128), restoring a snapshot
+ * before each, and keep the fastest.  The context is left at the starting
+ * state with the chosen configuration.  Results never depend on the
+ * configuration, only speed does.  Best called at step 0 or at a multiple of
+ * the chunk length. */
+int lpsim_autotune(lpsim_ctx *ctx, uint32_t window_steps, lpsim_tune_result *out);
+
+/* Set the launch configuration directly (e.g. from a stored tuning result). */
+int lpsim_set_config(lpsim_ctx *ctx, uint32_t block_size, uint32_t blocks_per_sm, uint32_t sort_period,
+                     uint32_t chunk_steps);
+
 /* Per-kernel timing.  While on, every launch of the three step kernels
  * (step_p1: car following, departures and claims; step_p2: entry conflicts;
  * step_p3: lane changes) and of the compaction/sort sequence is bracketed by

@@ -30,7 +30,8 @@ EXPORTED = ["lpsim_last_error", "lpsim_version", "lpsim_set_allocator", "lpsim_l
             "lpsim_load_demand", "lpsim_step", "lpsim_run", "lpsim_reset", "lpsim_link_stats",
             "lpsim_get_trips", "lpsim_get_state", "lpsim_lane_map_size", "lpsim_get_lane_map",
             "lpsim_get_counters", "lpsim_set_kernel_timing", "lpsim_get_kernel_times", "lpsim_get_state_noalloc",
-            "lpsim_destroy"]
+            "lpsim_load_network_batch", "lpsim_load_demand_batch", "lpsim_batch_offsets", "lpsim_snapshot",
+            "lpsim_restore", "lpsim_autotune", "lpsim_set_config", "lpsim_destroy"]
 
 STATUS = {0: "LPSIM_OK", -1: "LPSIM_E_INVALID_ARG", -2: "LPSIM_E_OOM", -3: "LPSIM_E_CUDA", -4: "LPSIM_E_STATE",
           -5: "LPSIM_E_TIMEOUT", -6: "LPSIM_E_GRIDLOCK", -7: "LPSIM_E_INVARIANT"}
@@ -63,6 +64,11 @@ class LinkStat(ctypes.Structure):
 class Counters(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("k", "veh_steps", "arrived", "active", "waiting", "lane_changes",
                                                "slots", "launches")]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in ("block_size", "blocks_per_sm", "sort_period", "chunk_steps")] + \
+               [("best_ms", ctypes.c_double), ("default_ms", ctypes.c_double), ("n_tried", ctypes.c_uint32)]
 
 
 class LpsimError(RuntimeError):
@@ -110,6 +116,14 @@ def load_library(path: str | None = None):
     lib.lpsim_get_counters.argtypes = [P, ctypes.POINTER(Counters)]
     lib.lpsim_set_kernel_timing.argtypes = [P, ctypes.c_int]
     lib.lpsim_get_kernel_times.argtypes = [P, P, P]
+    lib.lpsim_get_state_noalloc.argtypes = [P, ctypes.c_uint64, P, P, P, P, P, P]
+    lib.lpsim_load_network_batch.argtypes = [ctypes.POINTER(P), ctypes.c_uint32, P, ctypes.POINTER(Params), P]
+    lib.lpsim_load_demand_batch.argtypes = [P, ctypes.c_uint32, P, P, P, P, P, P]
+    lib.lpsim_batch_offsets.argtypes = [P, ctypes.c_uint32, P, P, P, P]
+    lib.lpsim_snapshot.argtypes = [P]
+    lib.lpsim_restore.argtypes = [P]
+    lib.lpsim_autotune.argtypes = [P, ctypes.c_uint32, ctypes.POINTER(TuneResult)]
+    lib.lpsim_set_config.argtypes = [P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]
     lib.lpsim_destroy.argtypes = [P]
     lib.lpsim_destroy.restype = None
     _lib = lib
@@ -163,6 +177,25 @@ def _current_stream():
     except ImportError:
         pass
     return None
+
+
+def _net_arrays(net: dict) -> dict:
+    out = {
+        "edge_src": np.ascontiguousarray(net["edge_src"], dtype=np.uint32),
+        "edge_dst": np.ascontiguousarray(net["edge_dst"], dtype=np.uint32),
+        "edge_len": np.ascontiguousarray(net["edge_len"], dtype=np.float32),
+        "edge_lanes": np.ascontiguousarray(net["edge_lanes"], dtype=np.uint8),
+        "edge_vmax": np.ascontiguousarray(net["edge_vmax"], dtype=np.float32),
+        "node_green": np.ascontiguousarray(net["node_green"], dtype=np.uint32),
+    }
+    ar = net.get("edge_approach_rank")
+    out["edge_approach_rank"] = None if ar is None else np.ascontiguousarray(ar, dtype=np.uint8)
+    return out
+
+
+def _net_desc(net: dict, n: dict) -> Network:
+    return Network(int(net["n_nodes"]), int(net["n_edges"]), _p(n["edge_src"]), _p(n["edge_dst"]), _p(n["edge_len"]),
+                   _p(n["edge_lanes"]), _p(n["edge_vmax"]), _p(n["node_green"]), _p(n["edge_approach_rank"]))
 
 
 class Simulation:
@@ -263,6 +296,20 @@ class Simulation:
         names = ("step_p1", "step_p2", "step_p3", "compact_sort")
         return {k: {"ms": float(ms[i]), "launches": int(n[i])} for i, k in enumerate(names)}
 
+    def snapshot(self) -> None:
+        _check(self.lib, self.lib.lpsim_snapshot(self.h))
+
+    def restore(self) -> None:
+        _check(self.lib, self.lib.lpsim_restore(self.h))
+
+    def autotune(self, window_steps: int) -> dict:
+        r = TuneResult()
+        _check(self.lib, self.lib.lpsim_autotune(self.h, window_steps, ctypes.byref(r)))
+        return {f: getattr(r, f) for f, _ in TuneResult._fields_}
+
+    def set_config(self, block_size: int, blocks_per_sm: int, sort_period: int, chunk_steps: int) -> None:
+        _check(self.lib, self.lib.lpsim_set_config(self.h, block_size, blocks_per_sm, sort_period, chunk_steps))
+
     def close(self) -> None:
         if getattr(self, "h", None):
             self.lib.lpsim_destroy(self.h)
@@ -279,3 +326,55 @@ class Simulation:
             self.close()
         except Exception:
             pass
+
+
+class BatchSimulation(Simulation):
+    """Many independent scenarios in one context (one launch per step kernel
+    advances them all); each scenario's results equal simulating it alone."""
+
+    def __init__(self, nets: list, params: dict | None = None, stream=None):
+        self.lib = load_library()
+        self.params = dict(DEFAULT_PARAMS)
+        if params:
+            self.params.update(params)
+        self._p = Params(**self.params)
+        self._nets = [_net_arrays(n) for n in nets]
+        descs = (Network * len(nets))(*[_net_desc(n, a) for n, a in zip(nets, self._nets)])
+        h = ctypes.c_void_p()
+        st = stream if stream is not None else _current_stream()
+        _check(self.lib, self.lib.lpsim_load_network_batch(ctypes.byref(h), len(nets), ctypes.cast(descs, ctypes.c_void_p),
+                                                           ctypes.byref(self._p), st))
+        self.h = h
+        self.n_scen = len(nets)
+        self.n_edges = int(sum(int(n["n_edges"]) for n in nets))
+        self.n_bins = int(self.params["n_bins"])
+        self.n = 0
+
+    def load_demand(self, dems: list, seeds=None) -> list:
+        ns = self.n_scen
+        keep = []
+        dep_p = (ctypes.c_void_p * ns)()
+        off_p = (ctypes.c_void_p * ns)()
+        edg_p = (ctypes.c_void_p * ns)()
+        counts = np.array([len(d["depart_step"]) for d in dems], np.uint64)
+        for i, d in enumerate(dems):
+            a = np.ascontiguousarray(d["depart_step"], dtype=np.uint32)
+            b = np.ascontiguousarray(d["route_off"], dtype=np.uint64)
+            c = np.ascontiguousarray(d["route_edges"], dtype=np.uint32)
+            keep += [a, b, c]
+            dep_p[i], off_p[i], edg_p[i] = a.ctypes.data, b.ctypes.data, c.ctypes.data
+        sd = None if seeds is None else np.ascontiguousarray(seeds, dtype=np.uint64)
+        total = int(counts.sum())
+        vid = np.empty(total, np.uint32)
+        _check(self.lib, self.lib.lpsim_load_demand_batch(self.h, ns, _p(counts), ctypes.cast(dep_p, ctypes.c_void_p),
+                                                          ctypes.cast(off_p, ctypes.c_void_p),
+                                                          ctypes.cast(edg_p, ctypes.c_void_p), _p(sd), _p(vid)))
+        self.n = total
+        splits = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+        return [vid[splits[i]:splits[i + 1]] for i in range(ns)]
+
+    def offsets(self) -> dict:
+        ns = self.n_scen
+        arr = {k: np.zeros(ns + 1, np.uint64) for k in ("node", "edge", "cell", "trip")}
+        _check(self.lib, self.lib.lpsim_batch_offsets(self.h, ns, *(_p(arr[k]) for k in ("node", "edge", "cell", "trip"))))
+        return {k: v.astype(np.int64) for k, v in arr.items()}

@@ -49,6 +49,19 @@ struct lpsim_ctx {
     uint64_t launches = 0;
     uint64_t stall_steps = 0;
     unsigned long long last_progress = 0;
+    // device buffers whose contents change while stepping (snapshot / restore)
+    std::vector<std::pair<void *, size_t>> mut;
+    uint8_t *snap = nullptr;
+    size_t snap_bytes = 0;
+    bool has_snap = false;
+    struct {
+        uint32_t k;
+        int cur;
+        uint64_t stall_steps;
+        unsigned long long last_progress;
+    } snap_host{};
+    // batched scenarios: prefix offsets of nodes, edges, canonical lane-map cells and trips
+    std::vector<uint64_t> scen_node_off, scen_edge_off, scen_cell_off, scen_trip_off;
     // per-kernel timing (events around every phase launch of every step)
     bool timing = false;
     std::vector<cudaEvent_t> ev;     // 5 per step of a chunk

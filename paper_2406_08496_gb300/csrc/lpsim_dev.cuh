@@ -95,6 +95,7 @@ struct Dev {
     const uint32_t *dep;       // departure step
     const uint32_t *route;     // all routes, vehicle-id order
     const uint32_t *roff;      // route start of vehicle id (n + 1 entries)
+    const uint64_t *hkey;      // lane-change draw key: scenario seed ^ scenario-local id * C1
     uint32_t *dep_act, *arr;
     uint8_t *status;
     // departure queues, one per origin edge

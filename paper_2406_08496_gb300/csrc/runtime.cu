@@ -62,6 +62,14 @@ int dnew(lpsim_ctx *c, T *&out, size_t count) {
         if (rc_ != LPSIM_OK) return rc_; \
     } while (0)
 
+// a device buffer whose contents change while stepping
+template <class T>
+int dnew_mut(lpsim_ctx *c, T *&out, size_t count) {
+    int rc = dnew(c, out, count);
+    if (rc == LPSIM_OK) c->mut.push_back({(void *)out, count * sizeof(T)});
+    return rc;
+}
+
 int check_params(const lpsim_params *p) {
     if (!p) return fail(LPSIM_E_INVALID_ARG, "params is NULL");
     if (!(p->dt > 0.0f) || !(p->a > 0.0f) || !(p->b > 0.0f) || !(p->s0 >= 0.0f) || !(p->x0 > 0.0f) ||
@@ -81,28 +89,30 @@ int upload(lpsim_ctx *c, void *dst, const void *src, size_t bytes) {
 }
 
 int alloc_slots(lpsim_ctx *c, Slots &s, uint32_t cap) {
-    TRY(dnew(c, s.id, cap));
-    TRY(dnew(c, s.e, cap));
-    TRY(dnew(c, s.rpos, cap));
-    TRY(dnew(c, s.rlast, cap));
-    TRY(dnew(c, s.tent, cap));
-    TRY(dnew(c, s.pcell, cap));
-    TRY(dnew(c, s.imark, cap));
-    TRY(dnew(c, s.lane, cap));
-    TRY(dnew(c, s.flag, cap));
+    // persistent fields (kept by snapshots)
+    TRY(dnew_mut(c, s.id, cap));
+    TRY(dnew_mut(c, s.e, cap));
+    TRY(dnew_mut(c, s.rpos, cap));
+    TRY(dnew_mut(c, s.rlast, cap));
+    TRY(dnew_mut(c, s.tent, cap));
+    TRY(dnew_mut(c, s.pcell, cap));
+    TRY(dnew_mut(c, s.imark, cap));
+    TRY(dnew_mut(c, s.lane, cap));
+    TRY(dnew_mut(c, s.flag, cap));
+    TRY(dnew_mut(c, s.tlc, cap));
+    TRY(dnew_mut(c, s.base, cap));
+    TRY(dnew_mut(c, s.cprev, cap));
+    TRY(dnew_mut(c, s.len, cap));
+    TRY(dnew_mut(c, s.v0, cap));
+    for (int i = 0; i < 2; i++) {
+        TRY(dnew_mut(c, s.x[i], cap));
+        TRY(dnew_mut(c, s.v[i], cap));
+    }
+    // per-step scratch, rewritten before it is read in every step
     TRY(dnew(c, s.act, cap));
     TRY(dnew(c, s.tl, cap));
-    TRY(dnew(c, s.tlc, cap));
     TRY(dnew(c, s.tln, cap));
-    TRY(dnew(c, s.base, cap));
-    TRY(dnew(c, s.cprev, cap));
     TRY(dnew(c, s.cslot, cap));
-    TRY(dnew(c, s.len, cap));
-    TRY(dnew(c, s.v0, cap));
-    for (int i = 0; i < 2; i++) {
-        TRY(dnew(c, s.x[i], cap));
-        TRY(dnew(c, s.v[i], cap));
-    }
     return LPSIM_OK;
 }
 
@@ -325,7 +335,11 @@ int lpsim_set_allocator(void *(*alloc)(size_t, void *), void (*release)(void *, 
     return LPSIM_OK;
 }
 
-int lpsim_load_network(lpsim_ctx **out, const lpsim_network *net, const lpsim_params *p, void *stream) {
+}  // extern "C"
+
+namespace {
+
+int load_network_impl(lpsim_ctx **out, const lpsim_network *net, const lpsim_params *p, void *stream) {
     if (!out) return fail(LPSIM_E_INVALID_ARG, "out is NULL");
     *out = nullptr;
     TRY(check_params(p));
@@ -458,19 +472,18 @@ int lpsim_load_network(lpsim_ctx **out, const lpsim_network *net, const lpsim_pa
     d.slot_off = so;
     d.orank = ork;
     for (int i = 0; i < 3; i++)
-        if ((rc = dnew(c, d.map[i], c->map_bytes))) return bail(rc);
+        if ((rc = dnew_mut(c, d.map[i], c->map_bytes))) return bail(rc);
     for (int i = 0; i < 2; i++)
-        if ((rc = dnew(c, d.imap[i], c->map_bytes))) return bail(rc);
-    if ((rc = dnew(c, d.claim[0], slots)) || (rc = dnew(c, d.claim[1], slots)) || (rc = dnew(c, d.ent, ne)) ||
-        (rc = dnew(c, d.ext, ne)) ||
-        (rc = dnew(c, d.tts, ne)))
+        if ((rc = dnew_mut(c, d.imap[i], c->map_bytes))) return bail(rc);
+    if ((rc = dnew_mut(c, d.claim[0], slots)) || (rc = dnew_mut(c, d.claim[1], slots)) ||
+        (rc = dnew_mut(c, d.ent, ne)) || (rc = dnew_mut(c, d.ext, ne)) || (rc = dnew_mut(c, d.tts, ne)))
         return bail(rc);
     size_t nb = (size_t)ne * p->n_bins;
-    if ((rc = dnew(c, d.bin_in, nb)) || (rc = dnew(c, d.bin_tt, nb)) || (rc = dnew(c, d.bin_cnt, nb)) ||
-        (rc = dnew(c, d.bin_occ, nb)))
+    if ((rc = dnew_mut(c, d.bin_in, nb)) || (rc = dnew_mut(c, d.bin_tt, nb)) || (rc = dnew_mut(c, d.bin_cnt, nb)) ||
+        (rc = dnew_mut(c, d.bin_occ, nb)))
         return bail(rc);
-    if ((rc = dnew(c, d.counts, 8)) || (rc = dnew(c, d.kbase, 1)) || (rc = dnew(c, d.n_slots, 1)) ||
-        (rc = dnew(c, d.ctr, 8)) || (rc = dnew(c, d.err, 1)) || (rc = dnew(c, c->d_tmp, 4)))
+    if ((rc = dnew_mut(c, d.counts, 8)) || (rc = dnew_mut(c, d.kbase, 1)) || (rc = dnew_mut(c, d.n_slots, 1)) ||
+        (rc = dnew_mut(c, d.ctr, 8)) || (rc = dnew_mut(c, d.err, 1)) || (rc = dnew(c, c->d_tmp, 4)))
         return bail(rc);
     if (cudaMallocHost(&c->h_ctr, 16 * 8) != cudaSuccess) return bail(fail(LPSIM_E_OOM, "pinned allocation failed"));
     if ((rc = upload(c, edge, er.data(), ne * sizeof(EdgeRec))) || (rc = upload(c, node, nr.data(), nn * sizeof(NodeRec))) ||
@@ -481,12 +494,96 @@ int lpsim_load_network(lpsim_ctx **out, const lpsim_network *net, const lpsim_pa
     while (bits < 32 && (1ull << bits) < c->map_bytes) bits++;
     c->w.key_bits = bits;
     if ((rc = reset_state(c))) return bail(rc);
+    c->scen_node_off = {0, nn};
+    c->scen_edge_off = {0, ne};
+    c->scen_cell_off = {0, canon};
     *out = c;
     return LPSIM_OK;
 }
 
-int lpsim_load_demand(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, const uint64_t *route_off,
-                      const uint32_t *route_edges, uint32_t *out_vid) {
+}  // namespace
+
+extern "C" {
+
+int lpsim_load_network(lpsim_ctx **out, const lpsim_network *net, const lpsim_params *p, void *stream) {
+    return load_network_impl(out, net, p, stream);
+}
+
+int lpsim_load_network_batch(lpsim_ctx **out, uint32_t n_scen, const lpsim_network *nets, const lpsim_params *p,
+                             void *stream) {
+    if (!out) return fail(LPSIM_E_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_scen == 0 || !nets) return fail(LPSIM_E_INVALID_ARG, "no scenarios");
+    uint64_t nn = 0, ne = 0;
+    bool any_rank = false;
+    for (uint32_t sc = 0; sc < n_scen; sc++) {
+        const lpsim_network &g = nets[sc];
+        if (!g.edge_src || !g.edge_dst || !g.edge_len_m || !g.edge_lanes || !g.edge_vmax || !g.node_green_steps)
+            return fail(LPSIM_E_INVALID_ARG, "scenario " + std::to_string(sc) + ": network array is NULL");
+        nn += g.n_nodes;
+        ne += g.n_edges;
+        any_rank |= g.edge_approach_rank != nullptr;
+    }
+    if (nn >= 0xFFFFFFF0ull || ne >= 0xFFFFFFF0ull) return fail(LPSIM_E_INVALID_ARG, "batch too large");
+    std::vector<uint32_t> src(ne), dst(ne), green(nn);
+    std::vector<float> len(ne), vmax(ne);
+    std::vector<uint8_t> lanes(ne), rank(any_rank ? ne : 0);
+    std::vector<uint64_t> noff{0}, eoff{0}, coff{0};
+    uint64_t no = 0, eo = 0, cells = 0;
+    for (uint32_t sc = 0; sc < n_scen; sc++) {
+        const lpsim_network &g = nets[sc];
+        std::vector<uint32_t> n_in(g.n_nodes, 0);
+        for (uint32_t e = 0; e < g.n_edges; e++) {
+            if (g.edge_src[e] >= g.n_nodes || g.edge_dst[e] >= g.n_nodes)
+                return fail(LPSIM_E_INVALID_ARG, "scenario " + std::to_string(sc) + ": node id out of range");
+            src[eo + e] = (uint32_t)(g.edge_src[e] + no);
+            dst[eo + e] = (uint32_t)(g.edge_dst[e] + no);
+            len[eo + e] = g.edge_len_m[e];
+            vmax[eo + e] = g.edge_vmax[e];
+            lanes[eo + e] = g.edge_lanes[e];
+            uint32_t r = n_in[g.edge_dst[e]]++;
+            if (any_rank) rank[eo + e] = g.edge_approach_rank ? g.edge_approach_rank[e] : (uint8_t)r;
+            cells += (uint64_t)std::max(1.0f, std::ceil(g.edge_len_m[e])) * g.edge_lanes[e];
+        }
+        for (uint32_t i = 0; i < g.n_nodes; i++) green[no + i] = g.node_green_steps[i];
+        no += g.n_nodes;
+        eo += g.n_edges;
+        noff.push_back(no);
+        eoff.push_back(eo);
+        coff.push_back(cells);
+    }
+    lpsim_network u{(uint32_t)nn, (uint32_t)ne, src.data(), dst.data(), len.data(), lanes.data(), vmax.data(),
+                    green.data(), any_rank ? rank.data() : nullptr};
+    TRY(load_network_impl(out, &u, p, stream));
+    (*out)->scen_node_off = noff;
+    (*out)->scen_edge_off = eoff;
+    (*out)->scen_cell_off = coff;
+    return LPSIM_OK;
+}
+
+int lpsim_batch_offsets(lpsim_ctx *c, uint32_t n_scen, uint64_t *node_off, uint64_t *edge_off, uint64_t *cell_off,
+                        uint64_t *trip_off) {
+    if (!c) return fail(LPSIM_E_INVALID_ARG, "ctx is NULL");
+    if (c->scen_edge_off.size() != (size_t)n_scen + 1) return fail(LPSIM_E_INVALID_ARG, "n_scen does not match");
+    for (uint32_t i = 0; i <= n_scen; i++) {
+        if (node_off) node_off[i] = c->scen_node_off[i];
+        if (edge_off) edge_off[i] = c->scen_edge_off[i];
+        if (cell_off) cell_off[i] = c->scen_cell_off[i];
+        if (trip_off) trip_off[i] = c->scen_trip_off.size() == (size_t)n_scen + 1 ? c->scen_trip_off[i] : 0;
+    }
+    return LPSIM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Trips of one simulation or of a batch of scenarios.  scen (nullable): the
+// scenario of each input trip, non-decreasing; seeds (nullable): the
+// lane-change seed of each scenario (default: the context's seed).
+int load_demand_impl(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, const uint64_t *route_off,
+                     const uint32_t *route_edges, uint32_t *out_vid, const uint32_t *scen, uint32_t n_scen,
+                     const uint64_t *seeds) {
     if (!c) return fail(LPSIM_E_INVALID_ARG, "ctx is NULL");
     if (c->loaded) return fail(LPSIM_E_STATE, "demand already loaded");
     if (n == 0) return fail(LPSIM_E_INVALID_ARG, "no trips");
@@ -512,9 +609,15 @@ int lpsim_load_demand(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, con
     std::stable_sort(order.begin(), order.end(),
                      [&](uint32_t a, uint32_t b) { return depart_step[a] < depart_step[b]; });
     std::vector<uint32_t> dep(n), roff(n + 1), route(total ? total : 1);
+    std::vector<uint64_t> hkey(n);
+    std::vector<uint64_t> local(std::max<uint32_t>(n_scen, 1u), 0);
     roff[0] = 0;
     for (uint64_t id = 0; id < n; id++) {
         uint32_t j = order[id];
+        // lane-change draw key: seed ^ (id within the scenario) * C1
+        const uint32_t sc = scen ? scen[j] : 0u;
+        const uint64_t seed = seeds ? seeds[sc] : c->p.seed;
+        hkey[id] = seed ^ (local[sc]++ * 0x9E3779B97F4A7C15ull);
         dep[id] = depart_step[j];
         uint64_t L = route_off[j + 1] - route_off[j];
         std::memcpy(route.data() + roff[id], route_edges + route_off[j], L * 4);
@@ -541,21 +644,23 @@ int lpsim_load_demand(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, con
     Dev &d = c->d;
     const uint32_t norg = (uint32_t)org_edge.size();
     uint32_t *ddep, *droute, *droff, *oe, *oq, *oqe, *dqid;
+    uint64_t *dhkey;
+    TRY(dnew(c, dhkey, n));
     TRY(dnew(c, ddep, n));
     TRY(dnew(c, droute, route.size()));
     TRY(dnew(c, droff, n + 1));
-    TRY(dnew(c, d.dep_act, n));
-    TRY(dnew(c, d.arr, n));
-    TRY(dnew(c, d.status, n));
+    TRY(dnew_mut(c, d.dep_act, n));
+    TRY(dnew_mut(c, d.arr, n));
+    TRY(dnew_mut(c, d.status, n));
     TRY(dnew(c, oe, norg));
     TRY(dnew(c, oq, norg));
     TRY(dnew(c, oqe, norg));
     TRY(dnew(c, dqid, n));
-    TRY(dnew(c, d.org_head, norg));
-    TRY(dnew(c, d.org_dep, norg));
+    TRY(dnew_mut(c, d.org_head, norg));
+    TRY(dnew_mut(c, d.org_dep, norg));
     TRY(dnew(c, c->org_dep0, norg));
     TRY(dnew(c, d.dslot, norg));
-    TRY(dnew(c, d.dprev, norg));
+    TRY(dnew_mut(c, d.dprev, norg));
     TRY(dnew(c, d.dreq, norg));
     for (int i = 0; i < 2; i++) TRY(dnew(c, d.dep_list[i], norg));
     const uint32_t cap = (uint32_t)n;
@@ -573,6 +678,7 @@ int lpsim_load_demand(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, con
         TRY(dnew(c, c->w.key[i], cap));
         TRY(dnew(c, c->w.perm[i], cap));
     }
+    TRY(upload(c, dhkey, hkey.data(), n * 8));
     TRY(upload(c, ddep, dep.data(), n * 4));
     TRY(upload(c, droute, route.data(), route.size() * 4));
     TRY(upload(c, droff, roff.data(), (n + 1) * 4));
@@ -583,6 +689,7 @@ int lpsim_load_demand(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, con
     std::vector<uint32_t> od0(norg);
     for (uint32_t j = 0; j < norg; j++) od0[j] = dep[qid[org_qoff[j]]];
     TRY(upload(c, c->org_dep0, od0.data(), norg * 4ull));
+    d.hkey = dhkey;
     d.dep = ddep;
     d.route = droute;
     d.roff = droff;
@@ -594,8 +701,122 @@ int lpsim_load_demand(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, con
     d.cap = cap;
     c->n_trips = n;
     c->loaded = true;
+    if (!scen) c->scen_trip_off = {0, n};
     TRY(reset_state(c));  // synchronises: the host vectors above may go away
     return LPSIM_OK;
+}
+
+// launch configuration: block size, resident 256-thread blocks per SM, sort
+// period and graph chunk; graphs are rebuilt on the next chunk
+int apply_config(lpsim_ctx *c, uint32_t block, uint32_t bps, uint32_t R, uint32_t chunk) {
+    CU(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < 2; i++)
+        if (c->graph[i]) {
+            cudaGraphExecDestroy(c->graph[i]);
+            c->graph[i] = nullptr;
+        }
+    c->block = (int)block;
+    c->grid = std::max(1, c->n_sm * (int)bps * 256 / (int)block);
+    c->R = R;
+    uint32_t base = 2 * R;
+    base = base % 3 == 0 ? base : base * 3;
+    c->C = std::max(base, (chunk + base - 1) / base * base);
+    c->p.block_size = block;
+    c->p.blocks_per_sm = bps;
+    c->p.sort_period = R;
+    c->p.chunk_steps = chunk;
+    if (c->timing && c->ev.size() < 5ull * c->C) {
+        size_t old = c->ev.size();
+        c->ev.resize(5ull * c->C);
+        for (size_t i = old; i < c->ev.size(); i++) CU(cudaEventCreate(&c->ev[i]));
+    }
+    return LPSIM_OK;
+}
+
+int snapshot_impl(lpsim_ctx *c) {
+    CU(cudaStreamSynchronize(c->stream));
+    size_t total = 0;
+    for (auto &b : c->mut) total += (b.second + 255) & ~size_t(255);
+    if (!c->snap) {
+        c->snap = static_cast<uint8_t *>(c->dalloc(total));
+        if (!c->snap) return fail(LPSIM_E_OOM, "snapshot allocation failed");
+        c->snap_bytes = total;
+    }
+    if (total != c->snap_bytes) return fail(LPSIM_E_STATE, "state layout changed since the first snapshot");
+    size_t o = 0;
+    for (auto &b : c->mut) {
+        CU(cudaMemcpyAsync(c->snap + o, b.first, b.second, cudaMemcpyDeviceToDevice, c->stream));
+        o += (b.second + 255) & ~size_t(255);
+    }
+    CU(cudaStreamSynchronize(c->stream));
+    c->snap_host = {c->k, c->cur, c->stall_steps, c->last_progress};
+    c->has_snap = true;
+    return LPSIM_OK;
+}
+
+int restore_impl(lpsim_ctx *c) {
+    if (!c->has_snap) return fail(LPSIM_E_STATE, "no snapshot taken");
+    CU(cudaStreamSynchronize(c->stream));
+    size_t o = 0;
+    for (auto &b : c->mut) {
+        CU(cudaMemcpyAsync(b.first, c->snap + o, b.second, cudaMemcpyDeviceToDevice, c->stream));
+        o += (b.second + 255) & ~size_t(255);
+    }
+    CU(cudaStreamSynchronize(c->stream));
+    c->k = c->snap_host.k;
+    c->cur = c->snap_host.cur;
+    c->stall_steps = c->snap_host.stall_steps;
+    c->last_progress = c->snap_host.last_progress;
+    return LPSIM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lpsim_load_demand(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, const uint64_t *route_off,
+                      const uint32_t *route_edges, uint32_t *out_vid) {
+    if (c && c->scen_edge_off.size() > 2)
+        return fail(LPSIM_E_STATE, "a batched context takes lpsim_load_demand_batch");
+    return load_demand_impl(c, n, depart_step, route_off, route_edges, out_vid, nullptr, 1, nullptr);
+}
+
+int lpsim_load_demand_batch(lpsim_ctx *c, uint32_t n_scen, const uint64_t *n_trips, const uint32_t *const *depart_step,
+                            const uint64_t *const *route_off, const uint32_t *const *route_edges,
+                            const uint64_t *seeds, uint32_t *out_vid) {
+    if (!c) return fail(LPSIM_E_INVALID_ARG, "ctx is NULL");
+    if (n_scen == 0 || !n_trips || !depart_step || !route_off || !route_edges)
+        return fail(LPSIM_E_INVALID_ARG, "batch array is NULL");
+    if (c->scen_edge_off.size() != (size_t)n_scen + 1)
+        return fail(LPSIM_E_INVALID_ARG, "n_scen does not match the batched network");
+    uint64_t n = 0, tot = 0;
+    for (uint32_t sc = 0; sc < n_scen; sc++) {
+        if (!depart_step[sc] || !route_off[sc] || !route_edges[sc])
+            return fail(LPSIM_E_INVALID_ARG, "scenario " + std::to_string(sc) + ": trip array is NULL");
+        if (route_off[sc][0] != 0) return fail(LPSIM_E_INVALID_ARG, "route_off must start at 0");
+        n += n_trips[sc];
+        tot += route_off[sc][n_trips[sc]];
+    }
+    std::vector<uint32_t> dep(n), scen(n), edges(tot ? tot : 1);
+    std::vector<uint64_t> off(n + 1);
+    uint64_t j = 0, q = 0;
+    off[0] = 0;
+    c->scen_trip_off.assign(1, 0);
+    for (uint32_t sc = 0; sc < n_scen; sc++) {
+        const uint64_t eo = c->scen_edge_off[sc], ecount = c->scen_edge_off[sc + 1] - eo;
+        for (uint64_t t = 0; t < n_trips[sc]; t++, j++) {
+            dep[j] = depart_step[sc][t];
+            scen[j] = sc;
+            for (uint64_t r = route_off[sc][t]; r < route_off[sc][t + 1]; r++) {
+                if (route_edges[sc][r] >= ecount)
+                    return fail(LPSIM_E_INVALID_ARG, "scenario " + std::to_string(sc) + ": edge id out of range");
+                edges[q++] = (uint32_t)(route_edges[sc][r] + eo);
+            }
+            off[j + 1] = q;
+        }
+        c->scen_trip_off.push_back(j);
+    }
+    return load_demand_impl(c, n, dep.data(), off.data(), edges.data(), out_vid, scen.data(), n_scen, seeds);
 }
 
 int lpsim_step(lpsim_ctx *c, uint32_t n_steps) {
@@ -764,6 +985,79 @@ int lpsim_get_kernel_times(lpsim_ctx *c, double *ms, uint64_t *launches) {
         launches[i] = c->t_n[i];
     }
     return LPSIM_OK;
+}
+
+int lpsim_snapshot(lpsim_ctx *c) {
+    if (!c) return fail(LPSIM_E_INVALID_ARG, "ctx is NULL");
+    if (!c->loaded) return fail(LPSIM_E_STATE, "lpsim_load_demand has not been called");
+    return snapshot_impl(c);
+}
+
+int lpsim_restore(lpsim_ctx *c) {
+    if (!c) return fail(LPSIM_E_INVALID_ARG, "ctx is NULL");
+    return restore_impl(c);
+}
+
+int lpsim_autotune(lpsim_ctx *c, uint32_t window_steps, lpsim_tune_result *out) {
+    if (!c) return fail(LPSIM_E_INVALID_ARG, "ctx is NULL");
+    if (!c->loaded) return fail(LPSIM_E_STATE, "lpsim_load_demand has not been called");
+    if (window_steps == 0) return fail(LPSIM_E_INVALID_ARG, "window_steps must be > 0");
+    const uint32_t cur_cfg[4] = {(uint32_t)c->block, c->p.blocks_per_sm ? c->p.blocks_per_sm : 6u, c->R,
+                                 c->p.chunk_steps ? c->p.chunk_steps : 384u};
+    TRY(snapshot_impl(c));
+    const bool timing = c->timing;
+    c->timing = false;
+    struct Cand {
+        uint32_t block, bps, R;
+    };
+    std::vector<Cand> cands;
+    cands.push_back({cur_cfg[0], cur_cfg[1], cur_cfg[2]});
+    for (uint32_t R : {32u, 64u, 128u})
+        for (uint32_t block : {128u, 256u, 512u})
+            for (uint32_t bps : {2u, 4u, 6u})
+                if (!(block == cur_cfg[0] && bps == cur_cfg[1] && R == cur_cfg[2])) cands.push_back({block, bps, R});
+    double best = 1e300, dflt = 0.0;
+    Cand pick = cands[0];
+    for (size_t i = 0; i < cands.size(); i++) {
+        const Cand &cd = cands[i];
+        TRY(apply_config(c, cd.block, cd.bps, cd.R, cur_cfg[3]));
+        TRY(restore_impl(c));
+        // capture the graphs outside the timed window
+        if (c->k % c->C == 0) TRY(capture_chunk(c, c->cur));
+        uint64_t taken = 0;
+        auto t0 = std::chrono::steady_clock::now();
+        TRY(run_steps(c, window_steps, false, &taken));
+        auto t1 = std::chrono::steady_clock::now();
+        double ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+        if (i == 0) dflt = ms;
+        if (ms < best) {
+            best = ms;
+            pick = cd;
+        }
+    }
+    TRY(apply_config(c, pick.block, pick.bps, pick.R, cur_cfg[3]));
+    TRY(restore_impl(c));
+    c->timing = timing;
+    if (out) {
+        out->block_size = pick.block;
+        out->blocks_per_sm = pick.bps;
+        out->sort_period = pick.R;
+        out->chunk_steps = c->C;
+        out->best_ms = best;
+        out->default_ms = dflt;
+        out->n_tried = (uint32_t)cands.size();
+    }
+    return LPSIM_OK;
+}
+
+int lpsim_set_config(lpsim_ctx *c, uint32_t block_size, uint32_t blocks_per_sm, uint32_t sort_period,
+                     uint32_t chunk_steps) {
+    if (!c) return fail(LPSIM_E_INVALID_ARG, "ctx is NULL");
+    if (block_size != 128 && block_size != 256 && block_size != 512)
+        return fail(LPSIM_E_INVALID_ARG, "block_size must be 128, 256 or 512");
+    if (blocks_per_sm == 0 || blocks_per_sm > 8 || sort_period == 0 || chunk_steps == 0)
+        return fail(LPSIM_E_INVALID_ARG, "configuration value out of range");
+    return apply_config(c, block_size, blocks_per_sm, sort_period, chunk_steps);
 }
 
 void lpsim_destroy(lpsim_ctx *c) { delete c; }

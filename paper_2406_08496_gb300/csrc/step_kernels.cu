@@ -42,8 +42,12 @@ __device__ __forceinline__ float unit24(uint64_t h) {
     return (float)(uint32_t)(h >> 40) * (1.0f / 16777216.0f);
 }
 
-__device__ __forceinline__ uint64_t lc_hash(uint64_t seed, uint32_t id, uint32_t k) {
-    return splitmix64_mix(seed ^ ((uint64_t)id * 0x9E3779B97F4A7C15ull) ^ ((uint64_t)k * 0xD1B54A32D192ED03ull));
+// Lane-change draw of vehicle `id` at step k: SplitMix64 of
+// seed ^ local_id * C1 ^ k * C2, where hkey[id] = seed ^ local_id * C1 was
+// formed at load time (local_id = the vehicle's id within its scenario, so a
+// scenario draws the same numbers alone or inside a batch).
+__device__ __forceinline__ uint64_t lc_hash(const Dev &d, uint32_t id, uint32_t k) {
+    return splitmix64_mix(d.hkey[id] ^ ((uint64_t)k * 0xD1B54A32D192ED03ull));
 }
 
 __device__ __forceinline__ float fmax0(float t) { return t > 0.0f ? t : 0.0f; }
@@ -333,7 +337,7 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) step_p1(Dev d, uint32_t k
             if (up == (par == 1u)) {
                 const float xrem = L - x;
                 const float mp = xrem >= m.x0 ? 0.0f : 1.0f - xrem / m.x0;
-                if (unit24(lc_hash(m.seed, d.s.id[s], k)) < mp) {
+                if (unit24(lc_hash(d, d.s.id[s], k)) < mp) {
                     act = kActIntend;
                     d.s.tl[s] = up ? 1 : 0;  // direction
                     Iw[base + cn] = 1;
@@ -473,7 +477,7 @@ __global__ void __launch_bounds__(BLOCK) step_p3(Dev d, uint32_t koff) {
         const uint32_t cb = c0 > 0 ? last_occupied(row2, c0 > 64u ? c0 - 64u : 0u, c0 - 1) : kNone;
         float eps_a = 0.0f, eps_b = 0.0f;
         if (m.eps_amp > 0.0f) {
-            const uint64_t h = lc_hash(m.seed, d.s.id[s], k);
+            const uint64_t h = lc_hash(d, d.s.id[s], k);
             eps_a = m.eps_amp * (2.0f * unit24(splitmix64_mix(h ^ 0x632BE59BD9B4E019ull)) - 1.0f);
             eps_b = m.eps_amp * (2.0f * unit24(splitmix64_mix(h ^ 0x8CB92BA72F3D8DD7ull)) - 1.0f);
         }

@@ -354,3 +354,33 @@ def subset_trips(dem: dict, keep: np.ndarray) -> dict:
     out["route_off"] = new_off
     out["route_edges"] = edges.astype(np.uint32)
     return out
+
+
+def batch_scenarios(n_scen: int = 64, base_seed: int = 100, min_nodes: int = 1000, max_nodes: int = 50_000,
+                    trips_per_node: float = 8.0, min_trips: int = 10_000, max_trips: int = 400_000,
+                    horizon_h: float = 2.0, dt: float = 0.5) -> list:
+    """Independent scenarios of uneven size for batched runs: grid or planar
+    networks of log-uniform node count, demand scaled by U(0.5, 1.5), each
+    with its own seed.  Departures peak twice inside `horizon_h` hours.
+    Returns a list of (network, routed demand, seed)."""
+    out = []
+    for s in range(n_scen):
+        seed = base_seed + s
+        rng = np.random.default_rng(seed)
+        nodes = int(np.exp(rng.uniform(np.log(min_nodes), np.log(max_nodes))))
+        scale = rng.uniform(0.5, 1.5)
+        if rng.random() < 0.5:
+            side = max(3, int(round(np.sqrt(nodes))))
+            net = grid_network(side, side, spacing=250.0)
+        else:
+            side = max(6, int(round(np.sqrt(nodes / 0.84))))
+            net = planar_network(side, side, seed)
+        n_trips = int(np.clip(net["n_nodes"] * trips_per_node * scale, min_trips, max_trips))
+        zx = max(2, side // 10)
+        zy = max(2, side // 17)
+        extent = float(max(net["node_x"].max() - net["node_x"].min(), net["node_y"].max() - net["node_y"].min()))
+        dem = gravity_demand(net, n_trips, seed + 5000, zones_x=zx, zones_y=zy, access_per_zone=4,
+                             beta_m=max(500.0, extent / 6.0), peaks_h=(0.3 * horizon_h, 0.6 * horizon_h),
+                             peak_sigma_h=0.12 * horizon_h, day_s=horizon_h * 3600.0, dt=dt)
+        out.append((net, route(net, dem), seed))
+    return out
