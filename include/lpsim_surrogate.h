@@ -1,0 +1,63 @@
+/*
+ * lpsim_surrogate.h -- C ABI of the link-travel-time surrogate used by the
+ * assignment loop: a small MLP (inputs padded to 64 -> 256 -> 256 -> 256 ->
+ * 1, GELU, BF16 weights and activations, FP32 accumulation) trained on the
+ * simulator's own link statistics with mean-squared error and Adam, with
+ * forward and backward passes in hand-written sm_103a tensor-core kernels
+ * (tcgen05.mma into tensor memory, operands staged by TMA).
+ *
+ * The paper has no surrogate: it is the learned extension of the traffic
+ * assignment the paper's title names (the paper title; dynamic rerouting as
+ * future work, Sec. 6).  The plain simulation stays the judge.
+ *
+ * Conventions as in lpsim.h: int status codes, lpsim_last_error(), host
+ * pointers for all inputs and outputs, the model owns its device memory.
+ * Parameter tensors, in order: W1 (256 x 64), b1 (256), W2 (256 x 256),
+ * b2, W3 (256 x 256), b3, W4 (1 x 256), b4 (1); W is out x in, row-major,
+ * f32.  Columns of W1 beyond n_features multiply zero padding.
+ */
+#ifndef LPSIM_SURROGATE_H
+#define LPSIM_SURROGATE_H
+
+#include <stdint.h>
+
+#include "lpsim.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lpsim_mlp lpsim_mlp;
+
+/* New model with He-initialised weights from `seed`; batch = rows per
+ * training step and per forward chunk (multiple of 128); stream as in
+ * lpsim_load_network (NULL: the model creates its own). */
+int lpsim_mlp_create(lpsim_mlp **out, uint32_t n_features, uint32_t batch, uint64_t seed, void *stream);
+int lpsim_mlp_set_params(lpsim_mlp *m, const float *const *tensors);
+int lpsim_mlp_get_params(lpsim_mlp *m, float *const *tensors);
+
+/* y[i] = MLP(X[i, :]) for n rows of n_features f32 values (BF16 inside). */
+int lpsim_mlp_forward(lpsim_mlp *m, uint64_t n, const float *X, float *y);
+
+/* Forward and backward of one batch (n <= batch rows): mean squared error
+ * against t into *loss (nullable) and its gradient with respect to every
+ * parameter tensor into grads[8] (each nullable). */
+int lpsim_mlp_grad(lpsim_mlp *m, uint64_t n, const float *X, const float *t, float *loss, float *const *grads);
+
+/* `steps` Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr)
+ * on minibatches drawn from shuffled passes over the n samples; losses
+ * (nullable, `steps` entries) receives each step's batch loss. */
+int lpsim_mlp_train(lpsim_mlp *m, uint64_t n, const float *X, const float *t, uint32_t steps, float lr,
+                    uint64_t shuffle_seed, float *losses);
+
+/* Diagnostic: D (M x N, f32) = A (M x K) . B (N x K)^T for BF16 bit
+ * patterns A, B (row-major) on the tensor-core GEMM kernel the model uses.
+ * M % 128 == 0, K % 64 == 0, N == 64 or N % 256 == 0. */
+int lpsim_mlp_gemm_test(uint32_t M, uint32_t N, uint32_t K, const uint16_t *A, const uint16_t *B, float *D);
+
+void lpsim_mlp_destroy(lpsim_mlp *m);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -50,16 +50,22 @@ def init_params(seed: int, dims=DIMS, n_in: int = 9) -> dict:
     return p
 
 
-def forward(p: dict, X: np.ndarray, keep: bool = False):
+def forward(p: dict, X: np.ndarray, keep: bool = False, act_round=None):
     """Returns the output y (n,) and, if keep, the pre-activations Z_l and
-    activations H_l (H_0 = X)."""
+    activations H_l (H_0 = X).  act_round (optional) is applied to every
+    hidden activation, e.g. bf16_round for a network that stores its
+    activations in BF16."""
     H = [np.asarray(X, dtype=np.float64)]
     Z = []
     n_layers = len([k for k in p if k.startswith("W")])
     for l in range(1, n_layers + 1):
         z = H[-1] @ p[f"W{l}"].T + p[f"b{l}"]
         Z.append(z)
-        H.append(gelu(z) if l < n_layers else z)
+        if l < n_layers:
+            h = gelu(z)
+            H.append(act_round(h) if act_round else h)
+        else:
+            H.append(z)
     y = H[-1][:, 0]
     return (y, Z, H) if keep else y
 
@@ -69,9 +75,11 @@ def loss(p: dict, X, t) -> float:
     return float(np.mean((y - t) ** 2))
 
 
-def backward(p: dict, X, t) -> dict:
-    """Gradients of the mean-squared error with respect to every parameter."""
-    y, Z, H = forward(p, X, keep=True)
+def backward(p: dict, X, t, act_round=None) -> dict:
+    """Gradients of the mean-squared error with respect to every parameter
+    (act_round as in forward; the gradient is that of the network with
+    rounded activations, taken through the unrounded GELU)."""
+    y, Z, H = forward(p, X, keep=True, act_round=act_round)
     n = len(t)
     n_layers = len(Z)
     g = {}

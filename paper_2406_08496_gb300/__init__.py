@@ -31,7 +31,9 @@ EXPORTED = ["lpsim_last_error", "lpsim_version", "lpsim_set_allocator", "lpsim_l
             "lpsim_get_trips", "lpsim_get_state", "lpsim_lane_map_size", "lpsim_get_lane_map",
             "lpsim_get_counters", "lpsim_set_kernel_timing", "lpsim_get_kernel_times", "lpsim_get_state_noalloc",
             "lpsim_load_network_batch", "lpsim_load_demand_batch", "lpsim_batch_offsets", "lpsim_snapshot",
-            "lpsim_restore", "lpsim_autotune", "lpsim_set_config", "lpsim_destroy"]
+            "lpsim_restore", "lpsim_autotune", "lpsim_set_config", "lpsim_destroy",
+            "lpsim_mlp_create", "lpsim_mlp_set_params", "lpsim_mlp_get_params", "lpsim_mlp_forward",
+            "lpsim_mlp_grad", "lpsim_mlp_train", "lpsim_mlp_gemm_test", "lpsim_mlp_destroy"]
 
 STATUS = {0: "LPSIM_OK", -1: "LPSIM_E_INVALID_ARG", -2: "LPSIM_E_OOM", -3: "LPSIM_E_CUDA", -4: "LPSIM_E_STATE",
           -5: "LPSIM_E_TIMEOUT", -6: "LPSIM_E_GRIDLOCK", -7: "LPSIM_E_INVARIANT"}
@@ -126,6 +128,15 @@ def load_library(path: str | None = None):
     lib.lpsim_set_config.argtypes = [P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]
     lib.lpsim_destroy.argtypes = [P]
     lib.lpsim_destroy.restype = None
+    lib.lpsim_mlp_create.argtypes = [ctypes.POINTER(P), ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64, P]
+    lib.lpsim_mlp_set_params.argtypes = [P, P]
+    lib.lpsim_mlp_get_params.argtypes = [P, P]
+    lib.lpsim_mlp_forward.argtypes = [P, ctypes.c_uint64, P, P]
+    lib.lpsim_mlp_grad.argtypes = [P, ctypes.c_uint64, P, P, P, P]
+    lib.lpsim_mlp_train.argtypes = [P, ctypes.c_uint64, P, P, ctypes.c_uint32, ctypes.c_float, ctypes.c_uint64, P]
+    lib.lpsim_mlp_gemm_test.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, P, P, P]
+    lib.lpsim_mlp_destroy.argtypes = [P]
+    lib.lpsim_mlp_destroy.restype = None
     _lib = lib
     return lib
 
@@ -378,3 +389,78 @@ class BatchSimulation(Simulation):
         arr = {k: np.zeros(ns + 1, np.uint64) for k in ("node", "edge", "cell", "trip")}
         _check(self.lib, self.lib.lpsim_batch_offsets(self.h, ns, *(_p(arr[k]) for k in ("node", "edge", "cell", "trip"))))
         return {k: v.astype(np.int64) for k, v in arr.items()}
+
+
+PARAM_SHAPES = [(256, 64), (256,), (256, 256), (256,), (256, 256), (256,), (1, 256), (1,)]
+PARAM_NAMES = ["W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4"]
+
+
+def gemm_bf16(A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """D = A . B^T on the tensor-core GEMM kernel; A, B are uint16 BF16 bit
+    patterns (M x K and N x K)."""
+    lib = load_library()
+    A = np.ascontiguousarray(A, dtype=np.uint16)
+    B = np.ascontiguousarray(B, dtype=np.uint16)
+    M, K = A.shape
+    N = B.shape[0]
+    D = np.empty((M, N), np.float32)
+    _check(lib, lib.lpsim_mlp_gemm_test(M, N, K, _p(A), _p(B), _p(D)))
+    return D
+
+
+class Surrogate:
+    """The link-travel-time MLP on the GPU (include/lpsim_surrogate.h)."""
+
+    def __init__(self, n_features: int = 9, batch: int = 8192, seed: int = 0, stream=None):
+        self.lib = load_library()
+        self.nf = n_features
+        self.batch = batch
+        h = ctypes.c_void_p()
+        st = stream if stream is not None else _current_stream()
+        _check(self.lib, self.lib.lpsim_mlp_create(ctypes.byref(h), n_features, batch, seed, st))
+        self.h = h
+
+    def set_params(self, params: dict) -> None:
+        arrs = [np.ascontiguousarray(params[k], dtype=np.float32).reshape(s) for k, s in zip(PARAM_NAMES, PARAM_SHAPES)]
+        ptrs = (ctypes.c_void_p * 8)(*[a.ctypes.data for a in arrs])
+        _check(self.lib, self.lib.lpsim_mlp_set_params(self.h, ctypes.cast(ptrs, ctypes.c_void_p)))
+
+    def get_params(self) -> dict:
+        arrs = [np.empty(s, np.float32) for s in PARAM_SHAPES]
+        ptrs = (ctypes.c_void_p * 8)(*[a.ctypes.data for a in arrs])
+        _check(self.lib, self.lib.lpsim_mlp_get_params(self.h, ctypes.cast(ptrs, ctypes.c_void_p)))
+        return dict(zip(PARAM_NAMES, arrs))
+
+    def forward(self, X: np.ndarray) -> np.ndarray:
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.empty(len(X), np.float32)
+        _check(self.lib, self.lib.lpsim_mlp_forward(self.h, len(X), _p(X), _p(y)))
+        return y
+
+    def grad(self, X: np.ndarray, t: np.ndarray):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        arrs = [np.empty(s, np.float32) for s in PARAM_SHAPES]
+        ptrs = (ctypes.c_void_p * 8)(*[a.ctypes.data for a in arrs])
+        loss = ctypes.c_float()
+        _check(self.lib, self.lib.lpsim_mlp_grad(self.h, len(X), _p(X), _p(t), ctypes.byref(loss),
+                                                 ctypes.cast(ptrs, ctypes.c_void_p)))
+        return float(loss.value), dict(zip(PARAM_NAMES, arrs))
+
+    def train(self, X: np.ndarray, t: np.ndarray, steps: int, lr: float = 1e-3, seed: int = 0) -> np.ndarray:
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        losses = np.empty(steps, np.float32)
+        _check(self.lib, self.lib.lpsim_mlp_train(self.h, len(X), _p(X), _p(t), steps, lr, seed, _p(losses)))
+        return losses
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self.lib.lpsim_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

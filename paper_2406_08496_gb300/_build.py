@@ -15,7 +15,7 @@ from concurrent.futures import ThreadPoolExecutor
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
-SOURCES = ["step_kernels.cu", "compact_sort.cu", "runtime.cu", "noalloc.cu"]
+SOURCES = ["step_kernels.cu", "compact_sort.cu", "runtime.cu", "noalloc.cu", "mlp.cu"]
 HEADERS = ["lpsim_dev.cuh", "ctx.h"]
 LIB = os.path.join(HERE, "liblpsim.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -35,8 +35,9 @@ def _digest() -> str:
     for f in SOURCES + HEADERS:
         with open(os.path.join(CSRC, f), "rb") as fh:
             h.update(fh.read())
-    with open(os.path.join(ROOT, "include", "lpsim.h"), "rb") as fh:
-        h.update(fh.read())
+    for hdr in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        with open(os.path.join(ROOT, "include", hdr), "rb") as fh:
+            h.update(fh.read())
     h.update(" ".join(ARCH + NVCC_FLAGS).encode())
     return h.hexdigest()[:16]
 

@@ -1,0 +1,810 @@
+// Link-travel-time surrogate MLP on the 5th-generation tensor cores.
+//
+// Network: inputs (padded to 64) -> 256 -> 256 -> 256 -> 1, GELU after each
+// hidden layer, BF16 weights and activations, FP32 accumulation, MSE loss,
+// Adam.  Every dense layer, forward and backward, is one BF16 GEMM
+// D[M x N] = A[M x K] . B[N x K]^T with both operands K-major:
+//   forward   Z_l   = H_{l-1} . W_l^T                  (A = H_{l-1}, B = W_l)
+//   backward  dH_l  = dZ_{l+1} . W_{l+1}               (A = dZ, B = W^T copy)
+//   weights   dW_l  = dZ_l^T . H_{l-1}                 (A = dZ^T, B = H^T copies,
+//                                                       K = samples, split over CTAs)
+// GEMM kernel: one 128 x BN output tile per CTA (BN = 256 or 64), K in
+// 64-element slices.  One thread issues TMA loads (128-byte swizzle) of the
+// A and B slices into a 4-stage shared-memory ring guarded by mbarriers,
+// one thread issues tcgen05.mma (M = 128, N = BN, K = 16 per instruction)
+// accumulating in tensor memory, and the four warps read the accumulator
+// back with tcgen05.ld for a fused epilogue (bias, GELU, GELU', the output
+// head, transposed copies for the weight gradients, or FP32 atomics).
+// Every wait on an mbarrier is bounded; on timeout the kernel records an
+// error, stops issuing work and frees its tensor memory before returning.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "../../include/lpsim_surrogate.h"
+#include "ctx.h"
+
+namespace {
+
+int fail(int code, const std::string &m) { return lpsim_fail(code, m); }
+
+#define CU(call)                                                                                            \
+    do {                                                                                                    \
+        cudaError_t e_ = (call);                                                                            \
+        if (e_ != cudaSuccess) return fail(LPSIM_E_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+    } while (0)
+#define TRY(x)                           \
+    do {                                 \
+        int rc_ = (x);                   \
+        if (rc_ != LPSIM_OK) return rc_; \
+    } while (0)
+
+constexpr int kBM = 128;
+constexpr int kBK = 64;  // one 128-byte swizzle atom of BF16
+constexpr int kStages = 4;
+constexpr uint32_t kSpinLimit = 1u << 26;
+
+enum Epi : int {
+    kEpiGelu = 0,      // Z = acc + b -> keep Z (f32), H = GELU(Z) (bf16, row-major and transposed)
+    kEpiGeluHead = 1,  // as kEpiGelu, plus y = H . w4 + b4 (f32)
+    kEpiDgelu = 2,     // dZ = acc * GELU'(Zprev) -> bf16 row-major and transposed
+    kEpiAtomic = 3,    // out (f32) += acc
+    kEpiStore = 4,     // out (f32) = acc
+};
+
+struct GemmArgs {
+    int M, N, K;
+    int ktiles_per_split;
+    const float *bias;     // N
+    float *zout;           // M x N (kEpiGelu*)
+    __nv_bfloat16 *hout;   // M x N
+    __nv_bfloat16 *htout;  // N x M (nullable)
+    const float *zprev;    // M x N (kEpiDgelu)
+    const float *w4;       // N (kEpiGeluHead)
+    const float *b4;       // 1 (kEpiGeluHead)
+    float *yout;           // M (kEpiGeluHead)
+    float *fout;           // M x N (kEpiAtomic, kEpiStore)
+    uint32_t *err;
+};
+
+// ----------------------------------------------------------- device helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// bounded wait for the phase with the given parity to complete; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    for (uint32_t i = 0; i < kSpinLimit; i++) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);  // start address
+    d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset
+    d |= (uint64_t)1 << 46;                   // descriptor version
+    d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+    return d;
+}
+
+// instruction descriptor: BF16 x BF16 -> F32, both K-major, M = 128, N = n
+__host__ __device__ constexpr uint32_t umma_idesc(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+
+__device__ __forceinline__ float gelu_grad(float x) {
+    return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
+}
+
+// ------------------------------------------------------------- GEMM kernel
+
+template <int BN, int EPI>
+__global__ void __launch_bounds__(128, 1)
+    gemm_bf16_tn(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, GemmArgs g) {
+    constexpr uint32_t kABytes = kBM * kBK * 2;
+    constexpr uint32_t kBBytes = BN * kBK * 2;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + kStages * kABytes;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sB + kStages * kBBytes);
+    uint64_t *empty = full + kStages;
+    uint64_t *done = empty + kStages;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    __shared__ int s_fail;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+    const int kt0 = blockIdx.z * g.ktiles_per_split;
+    const int kt_total = (g.K + kBK - 1) / kBK;
+    const int kt1 = min(kt_total, kt0 + g.ktiles_per_split);
+    const int nk = kt1 - kt0;
+
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        for (int s = 0; s < kStages; s++) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(BN < 32 ? 32 : BN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (nk > 0) {
+        if (warp == 0 && lane == 0) {
+            // TMA producer
+            for (int i = 0; i < nk; i++) {
+                const int s = i % kStages;
+                if (i >= kStages && !mbar_wait(&empty[s], ((i / kStages) - 1) & 1)) {
+                    atomicOr(g.err, 1u);
+                    s_fail = 1;
+                    break;
+                }
+                if (s_fail) break;
+                mbar_expect_tx(&full[s], kABytes + kBBytes);
+                tma_load_2d(sA + s * kABytes, &tA, &full[s], (kt0 + i) * kBK, m0);
+                tma_load_2d(sB + s * kBBytes, &tB, &full[s], (kt0 + i) * kBK, n0);
+            }
+        } else if (warp == 1 && lane == 0) {
+            // MMA issuer
+            const uint32_t idesc = umma_idesc(BN);
+            int issued = 0;
+            for (int i = 0; i < nk; i++) {
+                const int s = i % kStages;
+                if (!mbar_wait(&full[s], (i / kStages) & 1)) {
+                    atomicOr(g.err, 2u);
+                    s_fail = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t a0 = smem_u32(sA + s * kABytes), b0 = smem_u32(sB + s * kBBytes);
+#pragma unroll
+                for (int kk = 0; kk < kBK / 16; kk++)
+                    umma_f16(tmem, umma_desc(a0 + kk * 32), umma_desc(b0 + kk * 32), idesc, (i | kk) != 0);
+                umma_commit(&empty[s]);
+                issued++;
+            }
+            umma_commit(done);
+            (void)issued;
+        }
+        __syncwarp();
+        // epilogue: all four warps; warp w owns accumulator lanes 32w..32w+31
+        const bool ok = mbar_wait(done, 0);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!ok) atomicOr(g.err, 4u);
+        const int row = m0 + warp * 32 + lane;
+        float head = 0.0f;
+        if (ok && !s_fail) {
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 32) {
+                uint32_t r[32];
+                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+                if (row >= g.M) continue;
+#pragma unroll
+                for (int j = 0; j < 32; j++) {
+                    const int col = n0 + c0 + j;
+                    const float acc = __uint_as_float(r[j]);
+                    const size_t o = (size_t)row * g.N + col;
+                    if (EPI == kEpiGelu || EPI == kEpiGeluHead) {
+                        const float z = acc + g.bias[col];
+                        g.zout[o] = z;
+                        const __nv_bfloat16 h = __float2bfloat16_rn(gelu(z));
+                        g.hout[o] = h;
+                        if (g.htout) g.htout[(size_t)col * g.M + row] = h;
+                        if (EPI == kEpiGeluHead) head += __bfloat162float(h) * g.w4[col];
+                    } else if (EPI == kEpiDgelu) {
+                        const __nv_bfloat16 dz = __float2bfloat16_rn(acc * gelu_grad(g.zprev[o]));
+                        g.hout[o] = dz;
+                        if (g.htout) g.htout[(size_t)col * g.M + row] = dz;
+                    } else if (EPI == kEpiAtomic) {
+                        atomicAdd(&g.fout[o], acc);
+                    } else {
+                        g.fout[o] = acc;
+                    }
+                }
+            }
+            if (EPI == kEpiGeluHead && row < g.M) g.yout[row] = head + *g.b4;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN < 32 ? 32 : BN));
+}
+
+// ---------------------------------------------------------- small kernels
+
+// X (n x nf f32, host layout) -> Xb (n_pad x 64 bf16, zero padded) and its transpose
+__global__ void pack_inputs(const float *X, int n, int nf, int n_pad, __nv_bfloat16 *Xb, __nv_bfloat16 *XbT) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_pad * 64; i += gridDim.x * blockDim.x) {
+        const int r = i / 64, c = i % 64;
+        const float v = (r < n && c < nf) ? X[(size_t)r * nf + c] : 0.0f;
+        const __nv_bfloat16 b = __float2bfloat16_rn(v);
+        Xb[i] = b;
+        if (XbT) XbT[(size_t)c * n_pad + r] = b;
+    }
+}
+
+// dy = 2/n (y - t) on real rows; dZ3 = dy * w4 * GELU'(Z3) (bf16, row-major and
+// transposed); per-row dy kept for dW4 / db4; loss partial sums
+__global__ void head_backward(const float *y, const float *t, int n, int n_pad, const float *w4, const float *Z3,
+                              __nv_bfloat16 *dZ3, __nv_bfloat16 *dZ3T, float *dy, float *loss_acc) {
+    const float scale = 2.0f / (float)n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_pad * 256; i += gridDim.x * blockDim.x) {
+        const int r = i / 256, c = i % 256;
+        float d = 0.0f;
+        if (r < n) d = scale * (y[r] - t[r]);
+        if (c == 0) {
+            dy[r] = d;
+            if (r < n) atomicAdd(loss_acc, (y[r] - t[r]) * (y[r] - t[r]));
+        }
+        const __nv_bfloat16 b = __float2bfloat16_rn(d * w4[c] * gelu_grad(Z3[i]));
+        dZ3[i] = b;
+        dZ3T[(size_t)c * n_pad + r] = b;
+    }
+}
+
+// dW4[c] = sum_r dy[r] H3[r][c]; db4 = sum_r dy[r]; bias gradients = column sums of dZ
+__global__ void column_sums(const __nv_bfloat16 *A, int rows, int cols, const float *rowscale, float *out) {
+    // one block per column chunk of 32, threads stride over rows
+    const int c = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int r0 = threadIdx.x >> 5, rstep = blockDim.x >> 5;
+    float acc = 0.0f;
+    if (c < cols)
+        for (int r = r0; r < rows; r += rstep) {
+            const float a = __bfloat162float(A[(size_t)r * cols + c]);
+            acc += rowscale ? a * rowscale[r] : a;
+        }
+    __shared__ float red[32][33];
+    red[r0][threadIdx.x & 31] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float s = 0.0f;
+        for (int q = 0; q < rstep; q++) s += red[q][threadIdx.x];
+        if (blockIdx.x * 32 + threadIdx.x < cols) out[blockIdx.x * 32 + threadIdx.x] = s;
+    }
+}
+
+__global__ void sum_vector(const float *v, int n, float *out) {
+    float acc = 0.0f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += v[i];
+    __shared__ float red[1024];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+// Adam (Kingma and Ba 2015, Algorithm 1) on f32 master weights
+__global__ void adam_update(float *p, const float *grad, float *m, float *v, int n, float lr, float b1, float b2,
+                            float eps, float c1, float c2) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float gi = grad[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// bf16 copies of a weight matrix W (out x in, f32) and of its transpose
+__global__ void weights_to_bf16(const float *W, int out, int in, __nv_bfloat16 *Wb, __nv_bfloat16 *WbT) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < out * in; i += gridDim.x * blockDim.x) {
+        const int o = i / in, k = i % in;
+        const __nv_bfloat16 b = __float2bfloat16_rn(W[i]);
+        Wb[i] = b;
+        if (WbT) WbT[(size_t)k * out + o] = b;
+    }
+}
+
+// ------------------------------------------------------------- host side
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+int get_encode() {
+    std::call_once(g_encode_once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    if (!g_encode) return fail(LPSIM_E_CUDA, "cuTensorMapEncodeTiled is not available");
+    return LPSIM_OK;
+}
+
+// K-major BF16 matrix [rows][cols] (cols contiguous) read in boxes of
+// box_rows x 64 with 128-byte swizzle
+int make_map(CUtensorMap *map, const void *ptr, uint64_t rows, uint64_t cols, uint32_t box_rows) {
+    TRY(get_encode());
+    if (cols % 64 != 0 || rows % box_rows != 0 || ((uintptr_t)ptr & 15) != 0)
+        return fail(LPSIM_E_INVALID_ARG, "GEMM operand shape not a multiple of its tile");
+    cuuint64_t dims[2] = {cols, rows};
+    cuuint64_t strides[1] = {cols * 2};
+    cuuint32_t box[2] = {64, box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(LPSIM_E_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return LPSIM_OK;
+}
+
+template <int BN, int EPI>
+int launch_gemm(const CUtensorMap &a, const CUtensorMap &b, const GemmArgs &g, int splits, cudaStream_t st) {
+    const size_t smem = 1024 + kStages * (size_t)(kBM * kBK * 2 + BN * kBK * 2) + (2 * kStages + 1) * 8 + 16;
+    static bool attr_set = false;
+    if (!attr_set) {
+        CU(cudaFuncSetAttribute(gemm_bf16_tn<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set = true;
+    }
+    if (g.M % kBM != 0 || g.N % BN != 0) return fail(LPSIM_E_INVALID_ARG, "GEMM shape not a multiple of the tile");
+    dim3 grid(g.M / kBM, g.N / BN, splits);
+    gemm_bf16_tn<BN, EPI><<<grid, 128, smem, st>>>(a, b, g);
+    CU(cudaGetLastError());
+    return LPSIM_OK;
+}
+
+}  // namespace
+
+// =================================================================== MLP
+
+struct lpsim_mlp {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int nf = 9;       // real input features
+    int B = 8192;     // rows per batch (multiple of 128)
+    std::vector<void *> blocks;
+    // parameters: f32 master, Adam moments, gradients
+    float *P[8] = {}, *G[8] = {}, *Mo[8] = {}, *Ve[8] = {};
+    int sz[8] = {};
+    // bf16 weights (W1..W3) and transposes (W2^T, W3^T)
+    __nv_bfloat16 *Wb[3] = {}, *WbT[3] = {};
+    // activations for one batch
+    __nv_bfloat16 *X0, *X0T, *H[3], *HT[3], *dZ[3], *dZT[3];
+    float *Z[3], *y, *t, *dy, *Xf, *loss_acc;
+    uint32_t *err;
+    CUtensorMap mX0, mW[3], mH[3], mWT[3], mdZ[3], mdZT[3], mHT[3], mX0T;
+    int adam_t = 0;
+    uint64_t launches = 0;
+
+    void *alloc(size_t bytes) {
+        void *p = nullptr;
+        if (cudaMalloc(&p, (bytes + 255) & ~size_t(255)) != cudaSuccess) return nullptr;
+        blocks.push_back(p);
+        return p;
+    }
+    ~lpsim_mlp() {
+        if (stream) cudaStreamSynchronize(stream);
+        for (void *b : blocks) cudaFree(b);
+        if (own_stream) cudaStreamDestroy(stream);
+    }
+};
+
+namespace {
+
+const int kDims[5] = {64, 256, 256, 256, 1};
+
+int mlp_check_err(lpsim_mlp *m) {
+    uint32_t e = 0;
+    CU(cudaMemcpyAsync(&e, m->err, 4, cudaMemcpyDeviceToHost, m->stream));
+    CU(cudaStreamSynchronize(m->stream));
+    if (e) return fail(LPSIM_E_TIMEOUT, "tensor-core GEMM wait gave up (code " + std::to_string(e) + ")");
+    return LPSIM_OK;
+}
+
+int refresh_weights(lpsim_mlp *m) {
+    for (int l = 0; l < 3; l++) {
+        weights_to_bf16<<<64, 256, 0, m->stream>>>(m->P[2 * l], kDims[l + 1], kDims[l], m->Wb[l], m->WbT[l]);
+        m->launches++;
+    }
+    CU(cudaGetLastError());
+    return LPSIM_OK;
+}
+
+// forward of rows [0, B) already packed in X0; keep = training buffers
+int forward_batch(lpsim_mlp *m) {
+    cudaStream_t st = m->stream;
+    for (int l = 0; l < 3; l++) {
+        GemmArgs g{};
+        g.M = m->B;
+        g.N = 256;
+        g.K = kDims[l];
+        g.ktiles_per_split = (g.K + kBK - 1) / kBK;
+        g.bias = m->P[2 * l + 1];
+        g.zout = m->Z[l];
+        g.hout = m->H[l];
+        g.htout = m->HT[l];
+        g.err = m->err;
+        const CUtensorMap &a = l == 0 ? m->mX0 : m->mH[l - 1];
+        if (l < 2) {
+            TRY((launch_gemm<256, kEpiGelu>(a, m->mW[l], g, 1, st)));
+        } else {
+            g.w4 = m->P[6];
+            g.b4 = m->P[7];
+            g.yout = m->y;
+            TRY((launch_gemm<256, kEpiGeluHead>(a, m->mW[l], g, 1, st)));
+        }
+        m->launches++;
+    }
+    return LPSIM_OK;
+}
+
+// backward of the batch in the buffers (after forward_batch); fills G[]
+int backward_batch(lpsim_mlp *m, int n_real) {
+    cudaStream_t st = m->stream;
+    const int B = m->B;
+    for (int i = 0; i < 8; i++) CU(cudaMemsetAsync(m->G[i], 0, m->sz[i] * 4, st));
+    head_backward<<<1024, 256, 0, st>>>(m->y, m->t, n_real, B, m->P[6], m->Z[2], m->dZ[2], m->dZT[2], m->dy,
+                                       m->loss_acc);
+    // dW4 = sum_r dy[r] H3[r][:], db4 = sum dy
+    column_sums<<<256 / 32, 1024, 0, st>>>(m->H[2], B, 256, m->dy, m->G[6]);
+    sum_vector<<<1, 1024, 0, st>>>(m->dy, B, m->G[7]);
+    m->launches += 3;
+    for (int l = 2; l >= 0; l--) {
+        // dW_l = dZ_l^T . H_{l-1}   (A = dZ_l^T [256 x B], B = H_{l-1}^T [in x B])
+        GemmArgs g{};
+        g.M = 256;
+        g.N = kDims[l];
+        g.K = B;
+        const int kt = B / kBK;
+        const int splits = kt >= 64 ? 64 : kt;
+        g.ktiles_per_split = (kt + splits - 1) / splits;
+        g.fout = m->G[2 * l];
+        g.err = m->err;
+        const CUtensorMap &bT = l == 0 ? m->mX0T : m->mHT[l - 1];
+        if (g.N == 256) {
+            TRY((launch_gemm<256, kEpiAtomic>(m->mdZT[l], bT, g, splits, st)));
+        } else {
+            TRY((launch_gemm<64, kEpiAtomic>(m->mdZT[l], bT, g, splits, st)));
+        }
+        // db_l = column sums of dZ_l
+        column_sums<<<256 / 32, 1024, 0, st>>>(m->dZ[l], B, 256, nullptr, m->G[2 * l + 1]);
+        m->launches += 2;
+        if (l > 0) {
+            // dZ_{l-1} = (dZ_l . W_l) * GELU'(Z_{l-1})   (B operand = W_l^T [in x out])
+            GemmArgs h{};
+            h.M = B;
+            h.N = 256;
+            h.K = 256;
+            h.ktiles_per_split = 4;
+            h.zprev = m->Z[l - 1];
+            h.hout = m->dZ[l - 1];
+            h.htout = m->dZT[l - 1];
+            h.err = m->err;
+            TRY((launch_gemm<256, kEpiDgelu>(m->mdZ[l], m->mWT[l], h, 1, st)));
+            m->launches++;
+        }
+    }
+    CU(cudaGetLastError());
+    return LPSIM_OK;
+}
+
+int pack_batch(lpsim_mlp *m, const float *X_host, const float *t_host, uint64_t n) {
+    cudaStream_t st = m->stream;
+    CU(cudaMemcpyAsync(m->Xf, X_host, n * m->nf * 4, cudaMemcpyHostToDevice, st));
+    if (t_host) {
+        CU(cudaMemsetAsync(m->t, 0, m->B * 4, st));
+        CU(cudaMemcpyAsync(m->t, t_host, n * 4, cudaMemcpyHostToDevice, st));
+    }
+    pack_inputs<<<1024, 256, 0, st>>>(m->Xf, (int)n, m->nf, m->B, m->X0, m->X0T);
+    m->launches++;
+    CU(cudaGetLastError());
+    return LPSIM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lpsim_mlp_create(lpsim_mlp **out, uint32_t n_features, uint32_t batch, uint64_t seed, void *stream) {
+    if (!out) return fail(LPSIM_E_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_features == 0 || n_features > 64) return fail(LPSIM_E_INVALID_ARG, "n_features must be 1..64");
+    if (batch == 0 || batch % 128 != 0 || batch > (1u << 20))
+        return fail(LPSIM_E_INVALID_ARG, "batch must be a positive multiple of 128 (at most 2^20)");
+    auto *m = new (std::nothrow) lpsim_mlp();
+    if (!m) return fail(LPSIM_E_OOM, "host allocation failed");
+    auto bail = [&](int rc) {
+        delete m;
+        return rc;
+    };
+    cudaGetDevice(&m->device);
+    m->stream = static_cast<cudaStream_t>(stream);
+    if (!m->stream) {
+        if (cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(fail(LPSIM_E_CUDA, "cannot create a stream"));
+        m->own_stream = true;
+    }
+    m->nf = (int)n_features;
+    m->B = (int)batch;
+    const int B = m->B;
+    for (int l = 0; l < 4; l++) {
+        m->sz[2 * l] = kDims[l + 1] * kDims[l];
+        m->sz[2 * l + 1] = kDims[l + 1];
+    }
+    for (int i = 0; i < 8; i++) {
+        m->P[i] = (float *)m->alloc(m->sz[i] * 4);
+        m->G[i] = (float *)m->alloc(m->sz[i] * 4);
+        m->Mo[i] = (float *)m->alloc(m->sz[i] * 4);
+        m->Ve[i] = (float *)m->alloc(m->sz[i] * 4);
+        if (!m->P[i] || !m->G[i] || !m->Mo[i] || !m->Ve[i]) return bail(fail(LPSIM_E_OOM, "device allocation failed"));
+    }
+    for (int l = 0; l < 3; l++) {
+        m->Wb[l] = (__nv_bfloat16 *)m->alloc(kDims[l + 1] * kDims[l] * 2);
+        m->WbT[l] = (__nv_bfloat16 *)m->alloc(kDims[l + 1] * kDims[l] * 2);
+        m->H[l] = (__nv_bfloat16 *)m->alloc((size_t)B * 256 * 2);
+        m->HT[l] = (__nv_bfloat16 *)m->alloc((size_t)B * 256 * 2);
+        m->dZ[l] = (__nv_bfloat16 *)m->alloc((size_t)B * 256 * 2);
+        m->dZT[l] = (__nv_bfloat16 *)m->alloc((size_t)B * 256 * 2);
+        m->Z[l] = (float *)m->alloc((size_t)B * 256 * 4);
+    }
+    m->X0 = (__nv_bfloat16 *)m->alloc((size_t)B * 64 * 2);
+    m->X0T = (__nv_bfloat16 *)m->alloc((size_t)B * 64 * 2);
+    m->Xf = (float *)m->alloc((size_t)B * 64 * 4);
+    m->y = (float *)m->alloc((size_t)B * 4);
+    m->t = (float *)m->alloc((size_t)B * 4);
+    m->dy = (float *)m->alloc((size_t)B * 4);
+    m->loss_acc = (float *)m->alloc(16);
+    m->err = (uint32_t *)m->alloc(16);
+    if (!m->err || !m->X0 || !m->Xf) return bail(fail(LPSIM_E_OOM, "device allocation failed"));
+    if (cudaMemsetAsync(m->err, 0, 16, m->stream) != cudaSuccess) return bail(fail(LPSIM_E_CUDA, "memset"));
+    // tensor maps of every GEMM operand
+    int rc;
+    if ((rc = make_map(&m->mX0, m->X0, B, 64, kBM)) || (rc = make_map(&m->mX0T, m->X0T, 64, B, 64))) return bail(rc);
+    for (int l = 0; l < 3; l++) {
+        if ((rc = make_map(&m->mW[l], m->Wb[l], 256, kDims[l], 256)) ||
+            (rc = make_map(&m->mWT[l], m->WbT[l], kDims[l], 256, kDims[l] == 64 ? 64 : 256)) ||
+            (rc = make_map(&m->mH[l], m->H[l], B, 256, kBM)) || (rc = make_map(&m->mHT[l], m->HT[l], 256, B, 256)) ||
+            (rc = make_map(&m->mdZ[l], m->dZ[l], B, 256, kBM)) || (rc = make_map(&m->mdZT[l], m->dZT[l], 256, B, kBM)))
+            return bail(rc);
+    }
+    // He initialisation (host, seeded), then upload
+    std::mt19937_64 gen(seed);
+    std::normal_distribution<double> nd(0.0, 1.0);
+    for (int l = 0; l < 4; l++) {
+        const int fan_in = l == 0 ? (int)n_features : kDims[l];
+        std::vector<float> w(m->sz[2 * l]), b(m->sz[2 * l + 1], 0.0f);
+        for (int o = 0; o < kDims[l + 1]; o++)
+            for (int k = 0; k < kDims[l]; k++)
+                w[(size_t)o * kDims[l] + k] =
+                    (l == 0 && k >= (int)n_features) ? 0.0f : (float)(nd(gen) * std::sqrt(2.0 / fan_in));
+        if (cudaMemcpy(m->P[2 * l], w.data(), w.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(m->P[2 * l + 1], b.data(), b.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(fail(LPSIM_E_CUDA, "parameter upload failed"));
+    }
+    for (int i = 0; i < 8; i++) {
+        cudaMemsetAsync(m->Mo[i], 0, m->sz[i] * 4, m->stream);
+        cudaMemsetAsync(m->Ve[i], 0, m->sz[i] * 4, m->stream);
+    }
+    if ((rc = refresh_weights(m))) return bail(rc);
+    if (cudaStreamSynchronize(m->stream) != cudaSuccess) return bail(fail(LPSIM_E_CUDA, "init failed"));
+    *out = m;
+    return LPSIM_OK;
+}
+
+int lpsim_mlp_set_params(lpsim_mlp *m, const float *const *tensors) {
+    if (!m || !tensors) return fail(LPSIM_E_INVALID_ARG, "NULL argument");
+    for (int i = 0; i < 8; i++) {
+        if (!tensors[i]) return fail(LPSIM_E_INVALID_ARG, "parameter tensor is NULL");
+        CU(cudaMemcpyAsync(m->P[i], tensors[i], m->sz[i] * 4, cudaMemcpyHostToDevice, m->stream));
+        CU(cudaMemsetAsync(m->Mo[i], 0, m->sz[i] * 4, m->stream));
+        CU(cudaMemsetAsync(m->Ve[i], 0, m->sz[i] * 4, m->stream));
+    }
+    m->adam_t = 0;
+    TRY(refresh_weights(m));
+    CU(cudaStreamSynchronize(m->stream));
+    return LPSIM_OK;
+}
+
+int lpsim_mlp_get_params(lpsim_mlp *m, float *const *tensors) {
+    if (!m || !tensors) return fail(LPSIM_E_INVALID_ARG, "NULL argument");
+    CU(cudaStreamSynchronize(m->stream));
+    for (int i = 0; i < 8; i++)
+        if (tensors[i]) CU(cudaMemcpy(tensors[i], m->P[i], m->sz[i] * 4, cudaMemcpyDeviceToHost));
+    return LPSIM_OK;
+}
+
+int lpsim_mlp_forward(lpsim_mlp *m, uint64_t n, const float *X, float *y) {
+    if (!m || !X || !y) return fail(LPSIM_E_INVALID_ARG, "NULL argument");
+    for (uint64_t r0 = 0; r0 < n; r0 += m->B) {
+        const uint64_t nb = std::min<uint64_t>(m->B, n - r0);
+        TRY(pack_batch(m, X + r0 * m->nf, nullptr, nb));
+        TRY(forward_batch(m));
+        CU(cudaMemcpyAsync(y + r0, m->y, nb * 4, cudaMemcpyDeviceToHost, m->stream));
+    }
+    CU(cudaStreamSynchronize(m->stream));
+    return mlp_check_err(m);
+}
+
+int lpsim_mlp_grad(lpsim_mlp *m, uint64_t n, const float *X, const float *t, float *loss, float *const *grads) {
+    if (!m || !X || !t) return fail(LPSIM_E_INVALID_ARG, "NULL argument");
+    if (n == 0 || n > (uint64_t)m->B) return fail(LPSIM_E_INVALID_ARG, "n must be 1..batch");
+    TRY(pack_batch(m, X, t, n));
+    TRY(forward_batch(m));
+    CU(cudaMemsetAsync(m->loss_acc, 0, 4, m->stream));
+    TRY(backward_batch(m, (int)n));
+    CU(cudaStreamSynchronize(m->stream));
+    TRY(mlp_check_err(m));
+    if (loss) {
+        float s = 0.0f;
+        CU(cudaMemcpy(&s, m->loss_acc, 4, cudaMemcpyDeviceToHost));
+        *loss = s / (float)n;
+    }
+    if (grads)
+        for (int i = 0; i < 8; i++)
+            if (grads[i]) CU(cudaMemcpy(grads[i], m->G[i], m->sz[i] * 4, cudaMemcpyDeviceToHost));
+    return LPSIM_OK;
+}
+
+int lpsim_mlp_train(lpsim_mlp *m, uint64_t n, const float *X, const float *t, uint32_t steps, float lr,
+                    uint64_t shuffle_seed, float *losses) {
+    if (!m || !X || !t) return fail(LPSIM_E_INVALID_ARG, "NULL argument");
+    if (n == 0) return fail(LPSIM_E_INVALID_ARG, "no samples");
+    std::mt19937_64 gen(shuffle_seed);
+    std::vector<uint64_t> idx(n);
+    for (uint64_t i = 0; i < n; i++) idx[i] = i;
+    std::vector<float> bx((size_t)m->B * m->nf), bt(m->B);
+    uint64_t pos = n;
+    for (uint32_t s = 0; s < steps; s++) {
+        // next minibatch of a shuffled pass over the samples
+        const uint64_t nb = std::min<uint64_t>(m->B, n);
+        for (uint64_t j = 0; j < nb; j++) {
+            if (pos >= n) {
+                std::shuffle(idx.begin(), idx.end(), gen);
+                pos = 0;
+            }
+            const uint64_t r = idx[pos++];
+            std::memcpy(&bx[j * m->nf], X + r * m->nf, m->nf * 4);
+            bt[j] = t[r];
+        }
+        CU(cudaStreamSynchronize(m->stream));  // host staging buffers are reused
+        TRY(pack_batch(m, bx.data(), bt.data(), nb));
+        TRY(forward_batch(m));
+        CU(cudaMemsetAsync(m->loss_acc, 0, 4, m->stream));
+        TRY(backward_batch(m, (int)nb));
+        m->adam_t++;
+        const float c1 = 1.0f - std::pow(0.9f, (float)m->adam_t), c2 = 1.0f - std::pow(0.999f, (float)m->adam_t);
+        for (int i = 0; i < 8; i++) {
+            adam_update<<<(m->sz[i] + 255) / 256, 256, 0, m->stream>>>(m->P[i], m->G[i], m->Mo[i], m->Ve[i], m->sz[i],
+                                                                      lr, 0.9f, 0.999f, 1e-8f, c1, c2);
+            m->launches++;
+        }
+        TRY(refresh_weights(m));
+        if (losses) {
+            float l = 0.0f;
+            CU(cudaMemcpyAsync(&l, m->loss_acc, 4, cudaMemcpyDeviceToHost, m->stream));
+            CU(cudaStreamSynchronize(m->stream));
+            losses[s] = l / (float)nb;
+        }
+    }
+    CU(cudaStreamSynchronize(m->stream));
+    return mlp_check_err(m);
+}
+
+int lpsim_mlp_gemm_test(uint32_t M, uint32_t N, uint32_t K, const uint16_t *A, const uint16_t *B, float *D) {
+    if (!A || !B || !D) return fail(LPSIM_E_INVALID_ARG, "NULL argument");
+    if (M == 0 || M % 128 || (N != 64 && N % 256) || K == 0 || K % 64)
+        return fail(LPSIM_E_INVALID_ARG, "M % 128, K % 64 must be 0 and N 64 or a multiple of 256");
+    void *dA = nullptr, *dB = nullptr, *dD = nullptr, *dE = nullptr;
+    int rc = LPSIM_OK;
+    cudaStream_t st = nullptr;
+    if (cudaMalloc(&dA, (size_t)M * K * 2) || cudaMalloc(&dB, (size_t)N * K * 2) || cudaMalloc(&dD, (size_t)M * N * 4) ||
+        cudaMalloc(&dE, 16))
+        rc = fail(LPSIM_E_OOM, "device allocation failed");
+    CUtensorMap ma, mb;
+    if (!rc) {
+        cudaMemcpy(dA, A, (size_t)M * K * 2, cudaMemcpyHostToDevice);
+        cudaMemcpy(dB, B, (size_t)N * K * 2, cudaMemcpyHostToDevice);
+        cudaMemset(dD, 0, (size_t)M * N * 4);
+        cudaMemset(dE, 0, 16);
+        rc = make_map(&ma, dA, M, K, kBM);
+        if (!rc) rc = make_map(&mb, dB, N, K, N == 64 ? 64 : 256);
+    }
+    if (!rc) {
+        GemmArgs g{};
+        g.M = (int)M;
+        g.N = (int)N;
+        g.K = (int)K;
+        g.ktiles_per_split = (int)(K / kBK);
+        g.fout = (float *)dD;
+        g.err = (uint32_t *)dE;
+        rc = N == 64 ? launch_gemm<64, kEpiStore>(ma, mb, g, 1, st) : launch_gemm<256, kEpiStore>(ma, mb, g, 1, st);
+    }
+    if (!rc) {
+        uint32_t e = 0;
+        if (cudaDeviceSynchronize() != cudaSuccess) rc = fail(LPSIM_E_CUDA, cudaGetErrorString(cudaGetLastError()));
+        else {
+            cudaMemcpy(&e, dE, 4, cudaMemcpyDeviceToHost);
+            cudaMemcpy(D, dD, (size_t)M * N * 4, cudaMemcpyDeviceToHost);
+            if (e) rc = fail(LPSIM_E_TIMEOUT, "GEMM wait gave up (code " + std::to_string(e) + ")");
+        }
+    }
+    cudaFree(dA);
+    cudaFree(dB);
+    cudaFree(dD);
+    cudaFree(dE);
+    return rc;
+}
+
+void lpsim_mlp_destroy(lpsim_mlp *m) { delete m; }
+
+}  // extern "C"
