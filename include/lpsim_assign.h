@@ -1,0 +1,97 @@
+/*
+ * lpsim_assign.h -- host engine of the traffic-assignment loop around the
+ * simulator (method of successive averages with time-dependent shortest
+ * paths), and the feature builder of the link-travel-time surrogate.
+ *
+ * The paper's title is traffic assignment and propagation (the paper title);
+ * its simulator takes routes as given "after the routing" (Sec. 3.1) and it
+ * names dynamic rerouting as future work (Sec. 6).  None of these calls has
+ * a formula in the paper: the relative gap is the textbook Wardrop gap
+ *   RG = sum_trips (t_experienced - t_shortest) / sum_trips t_shortest,
+ * t_experienced from planned departure to arrival in the simulation and
+ * t_shortest the earliest-arrival path time under the link times of the same
+ * simulation (link time looked up by entry time in 15-minute bins, FIFO).
+ *
+ * Conventions as in lpsim.h (status codes, lpsim_last_error(), host
+ * pointers, caller-owned buffers).  Everything here runs on the host CPU
+ * threads; the simulation and the surrogate run on the GPU.
+ */
+#ifndef LPSIM_ASSIGN_H
+#define LPSIM_ASSIGN_H
+
+#include <stdint.h>
+
+#include "lpsim.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* number of surrogate input features per (link, bin): length, lanes, speed
+ * limit, inflow in the bin and the 3 bins before it, occupancy of the link
+ * and mean occupancy of its downstream links, and -- from the reference
+ * simulation the prediction starts from -- the travel-time ratio and the
+ * inflow of the same (link, bin) */
+#define LPSIM_SURROGATE_FEATURES 11u
+
+typedef struct lpsim_assign lpsim_assign;
+
+/* Network (as in lpsim_network), trips (origin and destination node,
+ * departure step) and their initial routes (route_off: n_trips + 1 entries). */
+int lpsim_assign_create(lpsim_assign **out, uint32_t n_nodes, uint32_t n_edges, const uint32_t *src,
+                        const uint32_t *dst, const float *len_m, const uint8_t *lanes, const float *vmax,
+                        uint64_t n_trips, const uint32_t *orig, const uint32_t *dest, const uint32_t *depart_step,
+                        const uint64_t *route_off, const uint32_t *route_edges, float dt, uint64_t seed);
+
+/* Time-dependent shortest paths of every trip under link times tt (n_edges x
+ * n_bins seconds, bin b covers entry steps [b*bin_steps, (b+1)*bin_steps)).
+ * Trips with the same origin and departure period (period_steps) share one
+ * earliest-arrival tree rooted at the middle of the period.  Keeps each
+ * trip's path as its candidate route and its shortest time (s) in t_sp
+ * (nullable, n_trips entries). */
+int lpsim_assign_shortest_paths(lpsim_assign *a, const float *tt, uint32_t n_bins, uint32_t bin_steps,
+                                uint32_t period_steps, uint32_t n_threads, float *t_sp);
+
+/* Relative gap of the last shortest paths against a simulation's trip
+ * outcome (per trip, in the caller's trip order): trips that have not
+ * arrived are left out; *n_used counts the others. */
+int lpsim_assign_gap(lpsim_assign *a, const uint32_t *depart_actual, const uint32_t *arrive_step, double *rg,
+                     uint64_t *n_used);
+
+/* Method of successive averages: each trip moves to its candidate route with
+ * probability `fraction` (seeded by the engine seed and `iteration`). */
+int lpsim_assign_reroute(lpsim_assign *a, double fraction, uint32_t iteration, uint64_t *n_changed);
+
+/* Current routes (route_off: n_trips + 1 entries; route_edges: capacity
+ * entries, at least lpsim_assign_route_length()). */
+uint64_t lpsim_assign_route_length(const lpsim_assign *a);
+int lpsim_assign_get_routes(const lpsim_assign *a, uint64_t *route_off, uint32_t *route_edges, uint64_t capacity);
+
+/* Inflow per (edge, bin) of the current routes propagated with link times tt
+ * (departure at the planned step, each link entered at the running time). */
+int lpsim_assign_load(const lpsim_assign *a, const float *tt, uint32_t n_bins, uint32_t bin_steps, uint32_t *inflow);
+
+/* Surrogate inputs per (edge, bin), edge-major, LPSIM_SURROGATE_FEATURES
+ * floats each, from the inflow counts of the assignment to score, occupancy
+ * samples, and the reference simulation's log travel-time ratio (NaN where
+ * unmeasured) and inflow (all n_edges x n_bins). */
+int lpsim_assign_features(const lpsim_assign *a, uint32_t n_bins, const uint32_t *inflow, const uint32_t *occ,
+                          const float *prev_log_ratio, const uint32_t *prev_inflow, float *X, uint32_t n_features);
+
+/* Link times (s) per (edge, bin) from a simulation's binned traversal sums
+ * and counts; bins without a traversal take the free-flow time len / vmax.
+ * log_ratio (nullable) receives log(measured / free-flow) where measured
+ * (NaN elsewhere): the surrogate's training target. */
+int lpsim_assign_link_times(const lpsim_assign *a, uint32_t n_bins, const uint32_t *tt_sum, const uint32_t *tt_cnt,
+                            float *tt, float *log_ratio);
+
+/* Link times from surrogate outputs y = log(t / free-flow), clamped to
+ * [free-flow, 50 x free-flow]. */
+int lpsim_assign_times_from_ratio(const lpsim_assign *a, uint32_t n_bins, const float *y, float *tt);
+
+void lpsim_assign_destroy(lpsim_assign *a);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -15,7 +15,7 @@ from concurrent.futures import ThreadPoolExecutor
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
-SOURCES = ["step_kernels.cu", "compact_sort.cu", "runtime.cu", "noalloc.cu", "mlp.cu"]
+SOURCES = ["step_kernels.cu", "compact_sort.cu", "runtime.cu", "noalloc.cu", "mlp.cu", "assign.cpp"]
 HEADERS = ["lpsim_dev.cuh", "ctx.h"]
 LIB = os.path.join(HERE, "liblpsim.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -54,7 +54,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(out_dir, exist_ok=True)
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(out_dir, src.replace(".cu", ".o"))
+        obj = os.path.join(out_dir, os.path.splitext(src)[0] + ".o")
         cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-I", os.path.join(ROOT, "include"), "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:

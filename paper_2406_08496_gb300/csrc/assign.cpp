@@ -1,0 +1,351 @@
+// Host side of the traffic-assignment loop around the simulator: the
+// method of successive averages (MSA) with time-dependent shortest paths.
+//
+// The paper's title is traffic *assignment* and propagation; its simulator
+// propagates trips along routes fixed "after the routing" (Sec. 3.1) and it
+// names dynamic rerouting as future work (Sec. 6).  This engine closes the
+// loop: link travel times per 15-minute entry bin come from a simulation
+// (or from the surrogate), time-dependent shortest paths are computed under
+// them (label-setting Dijkstra on earliest arrival, FIFO bin lookup of the
+// link time at the entry time), and a fraction of trips is moved onto the
+// new paths.  The relative gap is the textbook one,
+//   RG = sum_trips (t_experienced - t_shortest) / sum_trips t_shortest.
+// Shortest-path trees are shared by trips with the same origin and
+// departure period; origins are distributed over POSIX threads and each
+// tree is deterministic, so results do not depend on the thread count.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <queue>
+#include <random>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/lpsim_assign.h"
+
+int lpsim_fail(int code, const std::string &msg);
+
+namespace {
+int fail(int code, const std::string &m) { return lpsim_fail(code, m); }
+}  // namespace
+
+struct lpsim_assign {
+    uint32_t n_nodes = 0, n_edges = 0;
+    std::vector<uint32_t> src, dst, lanes;
+    std::vector<float> len, vmax;
+    std::vector<uint32_t> out_off, out_edge;  // CSR of out-edges by source node
+    // trips
+    uint64_t n = 0;
+    std::vector<uint32_t> orig, dest, dep;    // depart step
+    std::vector<std::vector<uint32_t>> route, cand;
+    std::vector<float> tsp;                   // shortest time under the last tt (s)
+    float dt = 0.5f;
+    uint64_t seed = 0;
+};
+
+namespace {
+
+struct TD {
+    const lpsim_assign *a;
+    const float *tt;   // n_edges x n_bins, seconds
+    uint32_t n_bins;
+    float bin_s;
+
+    float cost(uint32_t e, double t) const {
+        int64_t b = (int64_t)std::floor(t / bin_s);
+        if (b < 0) b = 0;
+        if (b >= (int64_t)n_bins) b = n_bins - 1;
+        return tt[(size_t)e * n_bins + b];
+    }
+};
+
+// earliest-arrival Dijkstra from `s` departing at t0; pred = edge into node
+void td_dijkstra(const TD &td, uint32_t s, double t0, std::vector<double> &arr, std::vector<uint32_t> &pred,
+                 std::vector<uint8_t> &done) {
+    const lpsim_assign *a = td.a;
+    std::fill(arr.begin(), arr.end(), INFINITY);
+    std::fill(pred.begin(), pred.end(), UINT32_MAX);
+    std::fill(done.begin(), done.end(), 0);
+    using Item = std::pair<double, uint32_t>;
+    std::priority_queue<Item, std::vector<Item>, std::greater<Item>> pq;
+    arr[s] = t0;
+    pq.push({t0, s});
+    while (!pq.empty()) {
+        auto [t, u] = pq.top();
+        pq.pop();
+        if (done[u]) continue;
+        done[u] = 1;
+        for (uint32_t j = a->out_off[u]; j < a->out_off[u + 1]; j++) {
+            const uint32_t e = a->out_edge[j], v = a->dst[e];
+            if (done[v]) continue;
+            const double nt = t + td.cost(e, t);
+            if (nt < arr[v] || (nt == arr[v] && e < pred[v])) {
+                arr[v] = nt;
+                pred[v] = e;
+                pq.push({nt, v});
+            }
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int lpsim_assign_create(lpsim_assign **out, uint32_t n_nodes, uint32_t n_edges, const uint32_t *src,
+                        const uint32_t *dst, const float *len_m, const uint8_t *lanes, const float *vmax,
+                        uint64_t n_trips, const uint32_t *orig, const uint32_t *dest, const uint32_t *depart_step,
+                        const uint64_t *route_off, const uint32_t *route_edges, float dt, uint64_t seed) {
+    if (!out || !src || !dst || !len_m || !lanes || !vmax || !orig || !dest || !depart_step || !route_off ||
+        !route_edges)
+        return fail(LPSIM_E_INVALID_ARG, "NULL argument");
+    if (!(dt > 0.0f)) return fail(LPSIM_E_INVALID_ARG, "dt must be > 0");
+    auto *a = new (std::nothrow) lpsim_assign();
+    if (!a) return fail(LPSIM_E_OOM, "host allocation failed");
+    a->n_nodes = n_nodes;
+    a->n_edges = n_edges;
+    a->src.assign(src, src + n_edges);
+    a->dst.assign(dst, dst + n_edges);
+    a->len.assign(len_m, len_m + n_edges);
+    a->vmax.assign(vmax, vmax + n_edges);
+    a->lanes.assign(lanes, lanes + n_edges);
+    a->out_off.assign(n_nodes + 1, 0);
+    for (uint32_t e = 0; e < n_edges; e++) {
+        if (src[e] >= n_nodes || dst[e] >= n_nodes) {
+            delete a;
+            return fail(LPSIM_E_INVALID_ARG, "edge endpoint out of range");
+        }
+        a->out_off[src[e] + 1]++;
+    }
+    for (uint32_t i = 0; i < n_nodes; i++) a->out_off[i + 1] += a->out_off[i];
+    a->out_edge.resize(n_edges);
+    std::vector<uint32_t> fill(a->out_off.begin(), a->out_off.end() - 1);
+    for (uint32_t e = 0; e < n_edges; e++) a->out_edge[fill[src[e]]++] = e;
+    a->n = n_trips;
+    a->orig.assign(orig, orig + n_trips);
+    a->dest.assign(dest, dest + n_trips);
+    a->dep.assign(depart_step, depart_step + n_trips);
+    a->route.resize(n_trips);
+    a->cand.resize(n_trips);
+    a->tsp.assign(n_trips, 0.0f);
+    for (uint64_t j = 0; j < n_trips; j++) {
+        if (route_off[j + 1] <= route_off[j] || orig[j] >= n_nodes || dest[j] >= n_nodes) {
+            delete a;
+            return fail(LPSIM_E_INVALID_ARG, "trip " + std::to_string(j) + ": empty route or bad node");
+        }
+        a->route[j].assign(route_edges + route_off[j], route_edges + route_off[j + 1]);
+    }
+    a->dt = dt;
+    a->seed = seed;
+    *out = a;
+    return LPSIM_OK;
+}
+
+int lpsim_assign_shortest_paths(lpsim_assign *a, const float *tt, uint32_t n_bins, uint32_t bin_steps,
+                                uint32_t period_steps, uint32_t n_threads, float *t_sp) {
+    if (!a || !tt || n_bins == 0 || bin_steps == 0 || period_steps == 0)
+        return fail(LPSIM_E_INVALID_ARG, "bad argument");
+    TD td{a, tt, n_bins, (float)bin_steps * a->dt};
+    // group trips by (origin, departure period)
+    std::vector<uint64_t> order(a->n);
+    std::iota(order.begin(), order.end(), 0);
+    auto key = [&](uint64_t j) { return ((uint64_t)a->orig[j] << 32) | (a->dep[j] / period_steps); };
+    std::sort(order.begin(), order.end(), [&](uint64_t x, uint64_t y) {
+        uint64_t kx = key(x), ky = key(y);
+        return kx != ky ? kx < ky : x < y;
+    });
+    std::vector<uint64_t> gstart;
+    for (uint64_t i = 0; i < a->n; i++)
+        if (i == 0 || key(order[i]) != key(order[i - 1])) gstart.push_back(i);
+    gstart.push_back(a->n);
+    const uint64_t ng = gstart.size() - 1;
+    std::atomic<uint64_t> next{0};
+    std::atomic<int> bad{0};
+    auto worker = [&]() {
+        std::vector<double> arr(a->n_nodes);
+        std::vector<uint32_t> pred(a->n_nodes);
+        std::vector<uint8_t> done(a->n_nodes);
+        std::vector<uint32_t> tmp;
+        for (;;) {
+            const uint64_t g = next.fetch_add(1);
+            if (g >= ng) break;
+            const uint64_t j0 = order[gstart[g]];
+            const uint32_t s = a->orig[j0];
+            const uint32_t period = a->dep[j0] / period_steps;
+            // tree from the middle of the departure period
+            const double t0 = ((double)period + 0.5) * period_steps * a->dt;
+            td_dijkstra(td, s, t0, arr, pred, done);
+            for (uint64_t i = gstart[g]; i < gstart[g + 1]; i++) {
+                const uint64_t j = order[i];
+                const uint32_t d = a->dest[j];
+                if (!std::isfinite(arr[d]) || d == s) {
+                    bad = 1;
+                    continue;
+                }
+                tmp.clear();
+                for (uint32_t v = d; v != s;) {
+                    const uint32_t e = pred[v];
+                    tmp.push_back(e);
+                    v = a->src[e];
+                }
+                a->cand[j].assign(tmp.rbegin(), tmp.rend());
+                a->tsp[j] = (float)(arr[d] - t0);
+            }
+        }
+    };
+    const uint32_t nt = std::max<uint32_t>(1, std::min<uint32_t>(n_threads ? n_threads : 1, 256));
+    std::vector<std::thread> th;
+    for (uint32_t i = 0; i < nt; i++) th.emplace_back(worker);
+    for (auto &t : th) t.join();
+    if (bad) return fail(LPSIM_E_INVALID_ARG, "a destination is unreachable from its origin");
+    if (t_sp) std::memcpy(t_sp, a->tsp.data(), a->n * 4);
+    return LPSIM_OK;
+}
+
+int lpsim_assign_gap(lpsim_assign *a, const uint32_t *depart_actual, const uint32_t *arrive_step, double *rg,
+                     uint64_t *n_used) {
+    if (!a || !depart_actual || !arrive_step || !rg) return fail(LPSIM_E_INVALID_ARG, "NULL argument");
+    double num = 0.0, den = 0.0;
+    uint64_t used = 0;
+    for (uint64_t j = 0; j < a->n; j++) {
+        if (arrive_step[j] == 0xFFFFFFFFu || depart_actual[j] == 0xFFFFFFFFu) continue;
+        // experienced time: from the planned departure (waiting to enter counts) to arrival
+        const double texp = (double)(arrive_step[j] - a->dep[j]) * a->dt;
+        num += texp - a->tsp[j];
+        den += a->tsp[j];
+        used++;
+    }
+    *rg = den > 0 ? num / den : 0.0;
+    if (n_used) *n_used = used;
+    return LPSIM_OK;
+}
+
+int lpsim_assign_reroute(lpsim_assign *a, double fraction, uint32_t iteration, uint64_t *n_changed) {
+    if (!a || !(fraction >= 0.0 && fraction <= 1.0)) return fail(LPSIM_E_INVALID_ARG, "bad argument");
+    std::mt19937_64 gen(a->seed * 1000003ull + iteration);
+    std::uniform_real_distribution<double> u(0.0, 1.0);
+    uint64_t changed = 0;
+    for (uint64_t j = 0; j < a->n; j++) {
+        if (u(gen) >= fraction || a->cand[j].empty()) continue;
+        if (a->cand[j] != a->route[j]) {
+            a->route[j] = a->cand[j];
+            changed++;
+        }
+    }
+    if (n_changed) *n_changed = changed;
+    return LPSIM_OK;
+}
+
+uint64_t lpsim_assign_route_length(const lpsim_assign *a) {
+    if (!a) return 0;
+    uint64_t t = 0;
+    for (auto &r : a->route) t += r.size();
+    return t;
+}
+
+int lpsim_assign_get_routes(const lpsim_assign *a, uint64_t *route_off, uint32_t *route_edges, uint64_t capacity) {
+    if (!a || !route_off || !route_edges) return fail(LPSIM_E_INVALID_ARG, "NULL argument");
+    if (capacity < lpsim_assign_route_length(a)) return fail(LPSIM_E_INVALID_ARG, "route buffer too small");
+    uint64_t o = 0;
+    for (uint64_t j = 0; j < a->n; j++) {
+        route_off[j] = o;
+        std::memcpy(route_edges + o, a->route[j].data(), a->route[j].size() * 4);
+        o += a->route[j].size();
+    }
+    route_off[a->n] = o;
+    return LPSIM_OK;
+}
+
+int lpsim_assign_load(const lpsim_assign *a, const float *tt, uint32_t n_bins, uint32_t bin_steps, uint32_t *inflow) {
+    if (!a || !tt || !inflow || n_bins == 0 || bin_steps == 0) return fail(LPSIM_E_INVALID_ARG, "bad argument");
+    TD td{a, tt, n_bins, (float)bin_steps * a->dt};
+    std::memset(inflow, 0, (size_t)a->n_edges * n_bins * 4);
+    for (uint64_t j = 0; j < a->n; j++) {
+        double t = (double)a->dep[j] * a->dt;
+        for (uint32_t e : a->route[j]) {
+            int64_t b = (int64_t)std::floor(t / td.bin_s);
+            if (b >= 0 && b < (int64_t)n_bins) inflow[(size_t)e * n_bins + b]++;
+            t += td.cost(e, t);
+        }
+    }
+    return LPSIM_OK;
+}
+
+int lpsim_assign_features(const lpsim_assign *a, uint32_t n_bins, const uint32_t *inflow, const uint32_t *occ,
+                          const float *prev_log_ratio, const uint32_t *prev_inflow, float *X, uint32_t n_features) {
+    if (!a || !inflow || !occ || !prev_log_ratio || !prev_inflow || !X || n_features != LPSIM_SURROGATE_FEATURES)
+        return fail(LPSIM_E_INVALID_ARG, "bad argument");
+    for (uint32_t e = 0; e < a->n_edges; e++) {
+        const float cells = std::max(1.0f, std::ceil(a->len[e])) * (float)a->lanes[e];
+        // mean occupancy density of the downstream links
+        const uint32_t v = a->dst[e];
+        for (uint32_t b = 0; b < n_bins; b++) {
+            float *x = X + ((size_t)e * n_bins + b) * n_features;
+            x[0] = a->len[e] / 1000.0f;
+            x[1] = (float)a->lanes[e] / 4.0f;
+            x[2] = a->vmax[e] / 30.0f;
+            for (int q = 0; q < 4; q++) {
+                const int64_t bb = (int64_t)b - q;
+                const float f = bb >= 0 ? (float)inflow[(size_t)e * n_bins + bb] : 0.0f;
+                x[3 + q] = std::log1p(f / (float)a->lanes[e]) / 4.0f;
+            }
+            x[7] = 10.0f * (float)occ[(size_t)e * n_bins + b] / cells;
+            float down = 0.0f;
+            uint32_t nd = 0;
+            for (uint32_t j = a->out_off[v]; j < a->out_off[v + 1]; j++) {
+                const uint32_t f = a->out_edge[j];
+                const float fc = std::max(1.0f, std::ceil(a->len[f])) * (float)a->lanes[f];
+                down += (float)occ[(size_t)f * n_bins + b] / fc;
+                nd++;
+            }
+            x[8] = nd ? 10.0f * down / (float)nd : 0.0f;
+            // the reference simulation of the same (edge, bin): its travel-time ratio and inflow
+            const size_t i = (size_t)e * n_bins + b;
+            x[9] = std::isfinite(prev_log_ratio[i]) ? prev_log_ratio[i] : 0.0f;
+            x[10] = std::log1p((float)prev_inflow[i] / (float)a->lanes[e]) / 4.0f;
+        }
+    }
+    return LPSIM_OK;
+}
+
+int lpsim_assign_link_times(const lpsim_assign *a, uint32_t n_bins, const uint32_t *tt_sum, const uint32_t *tt_cnt,
+                            float *tt, float *log_ratio) {
+    if (!a || !tt_sum || !tt_cnt || !tt || n_bins == 0) return fail(LPSIM_E_INVALID_ARG, "bad argument");
+    for (uint32_t e = 0; e < a->n_edges; e++) {
+        const float ff = a->len[e] / a->vmax[e];
+        for (uint32_t b = 0; b < n_bins; b++) {
+            const size_t i = (size_t)e * n_bins + b;
+            if (tt_cnt[i]) {
+                const float m = (float)((double)tt_sum[i] / (double)tt_cnt[i] * a->dt);
+                tt[i] = m;
+                if (log_ratio) log_ratio[i] = std::log(std::max(m, 0.5f * ff) / ff);
+            } else {
+                tt[i] = ff;
+                if (log_ratio) log_ratio[i] = NAN;
+            }
+        }
+    }
+    return LPSIM_OK;
+}
+
+int lpsim_assign_times_from_ratio(const lpsim_assign *a, uint32_t n_bins, const float *y, float *tt) {
+    if (!a || !y || !tt || n_bins == 0) return fail(LPSIM_E_INVALID_ARG, "bad argument");
+    for (uint32_t e = 0; e < a->n_edges; e++) {
+        const float ff = a->len[e] / a->vmax[e];
+        for (uint32_t b = 0; b < n_bins; b++) {
+            const size_t i = (size_t)e * n_bins + b;
+            const float r = std::exp(std::min(std::max(y[i], 0.0f), std::log(50.0f)));
+            tt[i] = ff * r;
+        }
+    }
+    return LPSIM_OK;
+}
+
+void lpsim_assign_destroy(lpsim_assign *a) { delete a; }
+
+}  // extern "C"

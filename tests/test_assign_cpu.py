@@ -1,0 +1,142 @@
+"""Host assignment engine (include/lpsim_assign.h): time-dependent shortest
+paths against brute-force path enumeration, the relative-gap formula, MSA
+re-routing, route loading and link-time tables.  Runs on the CPU."""
+from __future__ import annotations
+
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from netutil import make_net
+
+
+@pytest.fixture(scope="module")
+def A():
+    import paper_2406_08496_gb300 as L
+    L.build()
+    from paper_2406_08496_gb300 import assignment
+    return assignment
+
+
+def _diamond():
+    # 0 -> 1 -> 3, 0 -> 2 -> 3, 1 -> 2, plus 3 -> 0 so every node has an out-edge
+    edges = [(0, 1, 100.0, 1, 10.0), (1, 3, 100.0, 1, 10.0), (0, 2, 150.0, 1, 10.0), (2, 3, 40.0, 1, 10.0),
+             (1, 2, 30.0, 1, 10.0), (3, 0, 50.0, 1, 10.0)]
+    net = make_net(4, edges)
+    return net, edges
+
+
+def _arrival(path, t0, tt, bin_s):
+    t = t0
+    for e in path:
+        b = min(max(int(math.floor(t / bin_s)), 0), tt.shape[1] - 1)
+        t += tt[e, b]
+    return t
+
+
+def _all_paths(edges, s, d):
+    out = []
+    adj = {}
+    for i, (u, v, *_r) in enumerate(edges):
+        adj.setdefault(u, []).append((i, v))
+
+    def rec(u, seen, path):
+        if u == d:
+            out.append(list(path))
+            return
+        for i, v in adj.get(u, []):
+            if v not in seen:
+                rec(v, seen | {v}, path + [i])
+    rec(s, {s}, [])
+    return out
+
+
+def test_time_dependent_paths_match_brute_force(A):
+    net, edges = _diamond()
+    rng = np.random.default_rng(1)
+    n_bins, bin_steps, dt = 6, 20, 0.5
+    bin_s = bin_steps * dt
+    for trial in range(30):
+        # FIFO link times: consecutive bins differ by less than a bin width
+        base = rng.uniform(2.0, 30.0, (6, 1))
+        tt = (base + np.cumsum(rng.uniform(-2.0, 2.0, (6, n_bins)), axis=1)).clip(1.0).astype(np.float32)
+        dep = np.array([0, 13, 31, 55, 70], np.uint32)
+        dem = {"orig": np.zeros(5, np.uint32), "dest": np.full(5, 3, np.uint32), "depart_step": dep,
+               "route_off": np.arange(0, 11, 2, dtype=np.uint64), "route_edges": np.array([0, 1] * 5, np.uint32)}
+        a = A.Assignment(net, dem, dt=dt, seed=3)
+        period = 10
+        tsp = a.shortest_paths(tt, bin_steps, period, n_threads=2)
+        a.reroute(1.0, 0)
+        routes = a.routes()
+        for j in range(5):
+            t0 = ((dep[j] // period) + 0.5) * period * dt
+            best = min(_arrival(p, t0, tt, bin_s) for p in _all_paths(edges, 0, 3))
+            assert abs(tsp[j] - (best - t0)) < 1e-3
+            r = routes["route_edges"][int(routes["route_off"][j]):int(routes["route_off"][j + 1])]
+            assert abs(_arrival(list(r), t0, tt, bin_s) - best) < 1e-3
+
+
+def test_gap_formula(A):
+    net, _ = _diamond()
+    dem = {"orig": np.zeros(3, np.uint32), "dest": np.full(3, 3, np.uint32), "depart_step": np.array([0, 10, 20], np.uint32),
+           "route_off": np.array([0, 2, 4, 6], np.uint64), "route_edges": np.array([0, 1, 0, 1, 0, 1], np.uint32)}
+    a = A.Assignment(net, dem, dt=0.5)
+    tt = np.full((6, 4), 5.0, np.float32)
+    tsp = a.shortest_paths(tt, 100, 100)
+    assert np.allclose(tsp, 10.0)  # 0 -> 2 -> 3 or 0 -> 1 -> 3: two links of 5 s
+    dep_act = np.array([1, 11, 21], np.uint32)
+    arr = np.array([40, 50, 0xFFFFFFFF], np.uint32)  # third trip has not arrived
+    rg, used = a.gap(dep_act, arr)
+    # experienced 20 s and 20 s against 10 s shortest each: (10 + 10) / 20
+    assert used == 2 and abs(rg - 1.0) < 1e-12
+
+
+def test_reroute_fraction_and_load(A):
+    import workloads as W
+    net = W.grid_network(5, 5)
+    dem = W.route(net, W.uniform_demand(net, 400, 2, t_max_s=600.0))
+    a = A.Assignment(net, dem, dt=0.5, seed=7)
+    ne = net["n_edges"]
+    tt = np.tile((net["edge_len"] / net["edge_vmax"]).astype(np.float32)[:, None], (1, 8))
+    tt[::3] *= 3.0  # make some links slow so shortest paths change
+    a.shortest_paths(tt, 300, 300)
+    assert a.reroute(0.0, 0) == 0
+    n1 = a.reroute(0.5, 1)
+    n2 = a.reroute(1.0, 2)
+    assert 0 < n1 and n1 + n2 > 0
+    routes = a.routes()
+    # loading: brute-force inflow per (edge, bin)
+    inflow = a.load(tt, 300)
+    ref = np.zeros((ne, 8), np.int64)
+    off = routes["route_off"].astype(np.int64)
+    for j in range(len(dem["depart_step"])):
+        t = float(dem["depart_step"][j]) * 0.5
+        for e in routes["route_edges"][off[j]:off[j + 1]]:
+            b = int(math.floor(t / 150.0))
+            if 0 <= b < 8:
+                ref[e, b] += 1
+            t += float(tt[e, min(max(b, 0), 7)])
+    assert np.array_equal(inflow, ref)
+
+
+def test_link_times_and_features(A):
+    import workloads as W
+    net = W.grid_network(4, 4)
+    dem = W.route(net, W.uniform_demand(net, 50, 3))
+    a = A.Assignment(net, dem, dt=0.5)
+    ne = net["n_edges"]
+    s = np.zeros((ne, 4), np.uint32)
+    c = np.zeros((ne, 4), np.uint32)
+    s[0, 1], c[0, 1] = 300, 3   # 100 steps = 50 s on average
+    tt, lr = a.link_times(s, c)
+    ff = net["edge_len"] / net["edge_vmax"]
+    assert abs(tt[0, 1] - 50.0) < 1e-4 and abs(lr[0, 1] - math.log(50.0 / ff[0])) < 1e-5
+    assert np.isnan(lr[1, 1]) and abs(tt[1, 1] - ff[1]) < 1e-4
+    y = np.full(ne * 4, math.log(2.0), np.float32)
+    tt2 = a.times_from_ratio(y, 4)
+    assert np.allclose(tt2, 2.0 * np.repeat(ff[:, None], 4, axis=1), rtol=1e-5)
+    X = a.features(np.ones((ne, 4), np.uint32), np.zeros((ne, 4), np.uint32), lr, np.ones((ne, 4), np.uint32))
+    assert X.shape == (ne * 4, 11) and np.all(np.isfinite(X))
+    assert abs(X[1, 9] - lr[0, 1]) < 1e-6 and X[4 + 1, 9] == 0.0  # unmeasured cells read 0

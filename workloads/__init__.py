@@ -384,3 +384,16 @@ def batch_scenarios(n_scen: int = 64, base_seed: int = 100, min_nodes: int = 100
                              peak_sigma_h=0.12 * horizon_h, day_s=horizon_h * 3600.0, dt=dt)
         out.append((net, route(net, dem), seed))
     return out
+
+
+def assignment_case(seed: int = 5, scale: str = "small") -> tuple[dict, dict]:
+    """Regional network and day demand for the assignment loop: the
+    regional generator at reduced scale ("small": ~27k nodes, ~340k trips,
+    the same trips per node as the 224k-node / 2.82M-trip day)."""
+    sizes = {"small": (180, 340_000, 12, 8), "tiny": (60, 30_000, 5, 3)}
+    side, n_trips, zx, zy = sizes[scale]
+    net = planar_network(side, side, seed)
+    extent = float(net["node_x"].max() - net["node_x"].min())
+    dem = gravity_demand(net, n_trips, seed + 1000, zones_x=zx, zones_y=zy, access_per_zone=4,
+                         beta_m=extent / 9.0)
+    return net, route(net, dem)
