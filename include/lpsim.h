@@ -62,6 +62,7 @@ extern "C" {
 #define LPSIM_E_INVARIANT (-7)   /* device check: a lane-map cell written twice in one step */
 
 #define LPSIM_F_NO_SORT 1u
+#define LPSIM_F_CHECK_CELLS 2u
 
 typedef struct lpsim_ctx lpsim_ctx;
 
@@ -86,7 +87,9 @@ typedef struct lpsim_params {
                              of 2 sort periods and of 3 */
     uint32_t gridlock_steps; /* lpsim_run fails with LPSIM_E_GRIDLOCK after this many steps with active
                                 vehicles and no departure, crossing or arrival (0 = never) */
-    uint32_t flags;       /* bit 0 (LPSIM_F_NO_SORT): compact without sorting; other bits must be 0 */
+    uint32_t flags;       /* LPSIM_F_NO_SORT: compact without sorting; LPSIM_F_CHECK_CELLS: check that
+                             every lane-map write lands on an empty cell (LPSIM_E_INVARIANT otherwise;
+                             costs a load per write); other bits must be 0 */
 } lpsim_params;
 
 /* Road network.  Edge e runs edge_src[e] -> edge_dst[e], is edge_len_m[e]

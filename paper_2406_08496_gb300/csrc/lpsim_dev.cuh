@@ -121,6 +121,7 @@ struct Dev {
     unsigned long long *ctr;   // [0] veh_steps, [1] arrived, [2] lane changes, [3] crossings + departures,
                                // [4] departed
     uint32_t *err;
+    uint32_t check;            // 1: verify every next-map write lands on an empty cell
     Model m;
 };
 

@@ -79,7 +79,7 @@ int check_params(const lpsim_params *p) {
     if (p->bin_steps == 0 && p->n_bins != 0) return fail(LPSIM_E_INVALID_ARG, "n_bins without bin_steps");
     if (p->block_size && p->block_size != 128 && p->block_size != 256 && p->block_size != 512)
         return fail(LPSIM_E_INVALID_ARG, "block_size must be 0, 128, 256 or 512");
-    if (p->flags & ~1u) return fail(LPSIM_E_INVALID_ARG, "unknown flag bits");
+    if (p->flags & ~3u) return fail(LPSIM_E_INVALID_ARG, "unknown flag bits");
     return LPSIM_OK;
 }
 
@@ -442,6 +442,7 @@ int load_network_impl(lpsim_ctx **out, const lpsim_network *net, const lpsim_par
     c->grid = c->n_sm * (int)(p->blocks_per_sm ? p->blocks_per_sm : 6) * 256 / c->block;
     if (c->grid < 1) c->grid = 1;
     c->sort = (p->flags & 1u) == 0;
+    c->d.check = (p->flags & 2u) ? 1u : 0u;
 
     Dev &d = c->d;
     d.m.dt = p->dt;

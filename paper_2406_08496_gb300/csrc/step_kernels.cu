@@ -77,6 +77,32 @@ __device__ __forceinline__ uint32_t range_mask16(uint32_t c, uint32_t lo, uint32
     return ((0xFFFFu << a) & (0xFFFFu >> (15u - b))) & 0xFFFFu;
 }
 
+// first occupied cell in [lo, hi] of a 16-byte aligned row, or kNone; the
+// first four 16-byte chunks of the window are loaded together, so a window of
+// up to 49 cells costs one memory round trip
+__device__ __forceinline__ uint32_t first_occupied_wide(const uint8_t *row, uint32_t lo, uint32_t hi) {
+    if (lo > hi) return kNone;
+    const uint32_t c0 = lo & ~15u;
+    uint4 q[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const uint32_t c = c0 + 16u * j;
+        q[j] = c <= hi ? *reinterpret_cast<const uint4 *>(row + c) : make_uint4(~0u, ~0u, ~0u, ~0u);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const uint32_t c = c0 + 16u * j;
+        if (c > hi) break;
+        const uint32_t mk = occ_mask16(q[j]) & range_mask16(c, lo, hi);
+        if (mk) return c + (uint32_t)(__ffs((int)mk) - 1);
+    }
+    for (uint32_t c = c0 + 64u; c <= hi; c += 16u) {
+        const uint32_t mk = occ_mask16(*reinterpret_cast<const uint4 *>(row + c)) & range_mask16(c, lo, hi);
+        if (mk) return c + (uint32_t)(__ffs((int)mk) - 1);
+    }
+    return kNone;
+}
+
 // first occupied cell in [lo, hi] of a 16-byte aligned row, or kNone
 __device__ __forceinline__ uint32_t first_occupied(const uint8_t *row, uint32_t lo, uint32_t hi) {
     if (lo > hi) return kNone;
@@ -112,8 +138,11 @@ __device__ __forceinline__ bool is_green(const NodeRec &nr, uint32_t arank, uint
     return (k / nr.green) % nr.nphase == arank;
 }
 
-__device__ __forceinline__ void put_cell(uint8_t *map, uint32_t idx, uint8_t val, uint32_t *err) {
-    if (map[idx] != kEmpty) atomicOr(err, kErrCellTaken);
+// Write a next-map cell.  With the checking flag the cell is read first and
+// a second writer is reported in the error word; without it the store does
+// not wait for a load (the rules never give one cell two writers).
+__device__ __forceinline__ void put_cell(const Dev &d, uint8_t *map, uint32_t idx, uint8_t val) {
+    if (d.check && map[idx] != kEmpty) atomicOr(d.err, kErrCellTaken);
     map[idx] = val;
 }
 
@@ -160,6 +189,14 @@ __device__ __forceinline__ void stat_exit(const Dev &d, uint32_t e, uint32_t k, 
     }
 }
 
+// Programmatic dependent launch: let the next kernel of the step sequence be
+// scheduled now (its blocks wait in their own prologue), then wait until the
+// previous kernel has completed and its writes are visible.
+__device__ __forceinline__ void pdl_prologue() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 template <int BLOCK>
 __device__ __forceinline__ void block_add(unsigned long long *dst, uint32_t val) {
     __shared__ uint32_t red[BLOCK / 32];
@@ -179,6 +216,7 @@ __device__ __forceinline__ void block_add(unsigned long long *dst, uint32_t val)
 
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) step_p1(Dev d, uint32_t koff) {
+    pdl_prologue();
     const uint32_t k = *d.kbase + koff;
     const uint32_t par = k & 1u;
     const uint8_t *Mc = d.map[k % 3];
@@ -265,7 +303,7 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) step_p1(Dev d, uint32_t k
         const float reach = fmaxf(d_front, vmax_step * m.dt + m.s0);
         uint32_t hi = c + (uint32_t)fminf(reach, 65535.0f) + 2u;
         if (hi > len - 1) hi = len - 1;
-        const uint32_t cf = first_occupied(Mc + base, c + 1, hi);
+        const uint32_t cf = first_occupied_wide(Mc + base, c + 1, hi);
         const bool has_f = cf != kNone;
 
         float vn;
@@ -320,7 +358,7 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) step_p1(Dev d, uint32_t k
                 const float xh = x > lim ? x : lim;
                 xw[s] = xh;
                 vw[s] = 0.0f;
-                put_cell(Mn, base + (uint32_t)xh, 0, d.err);
+                put_cell(d, Mn, base + (uint32_t)xh, 0);
                 d.s.act[s] = kActHold;
             }
             continue;
@@ -328,7 +366,7 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) step_p1(Dev d, uint32_t k
         xw[s] = xn;
         vw[s] = vn;
         const uint32_t cn = (uint32_t)xn;
-        put_cell(Mn, base + cn, speed_byte(vn), d.err);
+        put_cell(d, Mn, base + cn, speed_byte(vn));
         uint8_t act = kActStay;
         const uint32_t tl = d.s.tlc[s];  // kNoLane on the last edge of the route
         const uint32_t ln = d.s.lane[s];
@@ -337,7 +375,8 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) step_p1(Dev d, uint32_t k
             if (up == (par == 1u)) {
                 const float xrem = L - x;
                 const float mp = xrem >= m.x0 ? 0.0f : 1.0f - xrem / m.x0;
-                if (unit24(lc_hash(d, d.s.id[s], k)) < mp) {
+                // u is in [0, 1): no draw can pass when mp <= 0
+                if (mp > 0.0f && unit24(lc_hash(d, d.s.id[s], k)) < mp) {
                     act = kActIntend;
                     d.s.tl[s] = up ? 1 : 0;  // direction
                     Iw[base + cn] = 1;
@@ -357,6 +396,7 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) step_p1(Dev d, uint32_t k
 
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) step_p2(Dev d, uint32_t koff) {
+    pdl_prologue();
     const uint32_t k = *d.kbase + koff;
     const uint32_t par = k & 1u;
     uint8_t *Mn = d.map[(k + 1) % 3];
@@ -391,7 +431,7 @@ __global__ void __launch_bounds__(BLOCK) step_p2(Dev d, uint32_t koff) {
                 d.s.v0[s] = enr.v0;
                 d.s.cprev[s] = cslot;
                 xw[s] = 0.0f;
-                put_cell(Mn, nbase, speed_byte(vw[s]), d.err);
+                put_cell(d, Mn, nbase, speed_byte(vw[s]));
                 events++;
             } else {
                 const float x = xc[s];
@@ -399,7 +439,7 @@ __global__ void __launch_bounds__(BLOCK) step_p2(Dev d, uint32_t koff) {
                 const float xh = x > lim ? x : lim;
                 xw[s] = xh;
                 vw[s] = 0.0f;
-                put_cell(Mn, d.s.base[s] + (uint32_t)xh, 0, d.err);
+                put_cell(d, Mn, d.s.base[s] + (uint32_t)xh, 0);
             }
             continue;
         }
@@ -434,7 +474,7 @@ __global__ void __launch_bounds__(BLOCK) step_p2(Dev d, uint32_t koff) {
         d.s.flag[s] = kLive;
         xw[s] = 0.0f;
         vw[s] = 0.0f;
-        put_cell(Mn, b0, 0, d.err);
+        put_cell(d, Mn, b0, 0);
         d.dprev[j] = slot;
         d.org_head[j] += 1;
         d.org_dep[j] = qh + 1 < d.org_qend[j] ? d.dep[d.qid[qh + 1]] : kNone;
@@ -452,6 +492,7 @@ __global__ void __launch_bounds__(BLOCK) step_p2(Dev d, uint32_t koff) {
 
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) step_p3(Dev d, uint32_t koff) {
+    pdl_prologue();
     const uint32_t k = *d.kbase + koff;
     const uint32_t par = k & 1u;
     const uint8_t *Mc = d.map[k % 3];
@@ -512,17 +553,39 @@ __global__ void __launch_bounds__(BLOCK) step_p3(Dev d, uint32_t koff) {
     }
 }
 
-__global__ void chunk_end(Dev d, uint32_t steps) { *d.kbase += steps; }
+__global__ void chunk_end(Dev d, uint32_t steps) {
+    pdl_prologue();
+    *d.kbase += steps;
+}
+
+namespace {
+
+template <class... Args>
+void launch_pdl(void (*kernel)(Args...), int grid, int block, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+}  // namespace
 
 void launch_phase(const Dev &d, int phase, uint32_t koff, int grid, int block, cudaStream_t st) {
-    // step_p2 and step_p3 walk short lists (crossers, intenders, origin
-    // edges): a quarter of the grid is plenty
+    // step_p2 and step_p3 walk short lists (crossers, intenders, departure
+    // requests): a quarter of the grid is plenty
     const int g = phase == 1 ? grid : (grid + 3) / 4;
-#define LPSIM_PHASE(B)                                        \
-    do {                                                      \
-        if (phase == 1) step_p1<B><<<g, B, 0, st>>>(d, koff); \
-        else if (phase == 2) step_p2<B><<<g, B, 0, st>>>(d, koff); \
-        else step_p3<B><<<g, B, 0, st>>>(d, koff);            \
+#define LPSIM_PHASE(B)                                            \
+    do {                                                          \
+        if (phase == 1) launch_pdl(step_p1<B>, g, B, st, d, koff); \
+        else if (phase == 2) launch_pdl(step_p2<B>, g, B, st, d, koff); \
+        else launch_pdl(step_p3<B>, g, B, st, d, koff);            \
     } while (0)
     switch (block) {
     case 128: LPSIM_PHASE(128); break;
@@ -532,7 +595,7 @@ void launch_phase(const Dev &d, int phase, uint32_t koff, int grid, int block, c
 #undef LPSIM_PHASE
 }
 
-void launch_chunk_end(const Dev &d, uint32_t steps, cudaStream_t st) { chunk_end<<<1, 1, 0, st>>>(d, steps); }
+void launch_chunk_end(const Dev &d, uint32_t steps, cudaStream_t st) { launch_pdl(chunk_end, 1, 1, st, d, steps); }
 
 }  // namespace lpsim
 

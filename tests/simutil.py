@@ -41,7 +41,9 @@ def lockstep(net: dict, dem: dict, params: dict, steps: int, check_every: int = 
     from paper_2406_08496_gb300 import Simulation
     o = O.Oracle(net, params)
     vo = o.load_demand(dem)
-    g = Simulation(net, dict(params, **(gpu_params or {})))
+    gp = dict(params, **(gpu_params or {}))
+    gp["flags"] = gp.get("flags", 0) | 2  # LPSIM_F_CHECK_CELLS: every lane-map write must find an empty cell
+    g = Simulation(net, gp)
     vg = g.load_demand(dem)
     assert np.array_equal(vo, vg)
     done = 0
