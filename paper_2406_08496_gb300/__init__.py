@@ -22,7 +22,7 @@ __all__ = ["Simulation", "LpsimError", "DEFAULT_PARAMS", "build", "load_library"
 # workloads; IDM a, b, s0, T; lane-change horizon x0; critical-gap constants.
 DEFAULT_PARAMS = dict(dt=0.5, a=1.0, b=1.5, s0=2.0, T=1.5, x0=100.0, g_a=2.0, g_b=2.0,
                       alpha_i=1.0, alpha_a=1.0, alpha_b=1.0, eps_amp=0.0, seed=12345,
-                      bin_steps=1800, n_bins=0, sort_period=64, block_size=256, blocks_per_sm=6,
+                      bin_steps=1800, n_bins=0, sort_period=64, block_size=256, blocks_per_sm=4,
                       chunk_steps=384, gridlock_steps=0, flags=0)
 FLAG_NO_SORT = 1
 
@@ -33,7 +33,10 @@ EXPORTED = ["lpsim_last_error", "lpsim_version", "lpsim_set_allocator", "lpsim_l
             "lpsim_load_network_batch", "lpsim_load_demand_batch", "lpsim_batch_offsets", "lpsim_snapshot",
             "lpsim_restore", "lpsim_autotune", "lpsim_set_config", "lpsim_destroy",
             "lpsim_mlp_create", "lpsim_mlp_set_params", "lpsim_mlp_get_params", "lpsim_mlp_forward",
-            "lpsim_mlp_grad", "lpsim_mlp_train", "lpsim_mlp_gemm_test", "lpsim_mlp_destroy"]
+            "lpsim_mlp_grad", "lpsim_mlp_train", "lpsim_mlp_gemm_test", "lpsim_mlp_destroy",
+            "lpsim_assign_create", "lpsim_assign_shortest_paths", "lpsim_assign_gap", "lpsim_assign_reroute",
+            "lpsim_assign_route_length", "lpsim_assign_get_routes", "lpsim_assign_load", "lpsim_assign_features",
+            "lpsim_assign_link_times", "lpsim_assign_times_from_ratio", "lpsim_assign_destroy"]
 
 STATUS = {0: "LPSIM_OK", -1: "LPSIM_E_INVALID_ARG", -2: "LPSIM_E_OOM", -3: "LPSIM_E_CUDA", -4: "LPSIM_E_STATE",
           -5: "LPSIM_E_TIMEOUT", -6: "LPSIM_E_GRIDLOCK", -7: "LPSIM_E_INVARIANT"}

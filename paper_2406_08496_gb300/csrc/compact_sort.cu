@@ -138,6 +138,9 @@ __device__ __forceinline__ void copy_slot(const Slots &a, uint32_t s, const Slot
     b.imark[o] = a.imark[s];
     b.base[o] = a.base[s];
     b.cprev[o] = a.cprev[s];
+    b.en[o] = a.en[s];
+    b.sg[o] = a.sg[s];
+    b.sph[o] = a.sph[s];
     b.len[o] = a.len[s];
     b.v0[o] = a.v0[s];
     b.lane[o] = a.lane[s];

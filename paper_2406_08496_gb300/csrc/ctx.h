@@ -45,7 +45,7 @@ struct lpsim_ctx {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     unsigned long long *h_ctr = nullptr;  // pinned: ctr[0..7], err, n_slots, ...
     uint32_t *d_tmp = nullptr;
-    uint32_t *org_dep0 = nullptr;    // departure step of each origin queue's first trip
+    lpsim::QRec *org_hd0 = nullptr;  // first trip of each origin queue (reset)
     uint64_t launches = 0;
     uint64_t stall_steps = 0;
     unsigned long long last_progress = 0;

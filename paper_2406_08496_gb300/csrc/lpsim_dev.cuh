@@ -58,11 +58,28 @@ struct Model {
     uint32_t bin_steps, n_bins;
 };
 
+// Per route position q (the edge E = route[q] of some trip): the signal at
+// E's downstream node (green steps and phase count of the node, E's phase)
+// and the target lane on E for the movement onto route[q+1] (kNoLane when q
+// is the trip's last position).  Precomputed on the device at load time so a
+// vehicle entering an edge copies what the next edge's end needs.
+struct __align__(8) RouteRec {
+    uint32_t green;
+    uint8_t nphase, arank, tl, pad;
+};
+
+// One trip of a departure queue: vehicle id, departure step, route start and
+// end positions.
+struct __align__(16) QRec {
+    uint32_t h, dep, r0, r1;
+};
+
 // Vehicle slots (structure of arrays).  x and v are double-buffered by step
-// parity: step k reads x[k&1] and writes x[(k+1)&1].  The attributes of the
-// current edge that the car-following rule needs (its lane-row start in the
-// map, its length and speed limit) are copied into the slot when the vehicle
-// enters the edge, so the common path reads only the slot and the map.
+// parity: step k reads x[k&1] and writes x[(k+1)&1].  What the vehicle needs
+// from its current edge (lane-row offset, length, speed limit, the signal at
+// its end, the next edge of the route, the target lane) is copied into the
+// slot when it enters the edge, so the common path reads the slot and the
+// map only, and a crossing reads one edge record more.
 struct Slots {
     // persistent
     uint32_t *id, *e, *rpos, *rlast, *tent;
@@ -70,16 +87,36 @@ struct Slots {
     uint32_t *imark;   // intent mark of the previous step (cleared this step), kNone
     uint32_t *base;    // lane-map offset of cell 0 of the current lane
     uint32_t *cprev;   // claim slot won at the previous step (reset this step), kNone
+    uint32_t *en;      // next edge of the route, kNone on the last edge
+    uint32_t *sg;      // green steps of the signal at the end of the current edge (0 = none)
+    uint16_t *sph;     // phases of that signal | phase of the current edge << 8
     uint16_t *len;     // cells per lane of the current edge
     uint8_t *lane, *flag;
     uint8_t *tlc;      // target lane of the movement after the current edge (kNoLane on the last edge)
     float *v0;         // speed limit of the current edge
     float *x[2], *v[2];
-    // per-step scratch
-    uint8_t *act;
-    uint8_t *tl;       // requested lane (crossers) or direction (intenders: 1 = up)
-    uint8_t *tln;      // target lane after the next edge (crossers)
-    uint32_t *cslot;   // claim slot asked for (crossers)
+    uint8_t *act;      // per-step scratch: what the vehicle did this step
+};
+
+// What step_p2 needs of a vehicle that asked to enter its next edge, packed
+// by step_p1 at the vehicle's position in the crossing list so that step_p2
+// reads it with four 16-byte loads instead of gathering slot fields.
+struct __align__(16) CrossRec {
+    uint32_t s, id, cslot, e;         // slot, vehicle, claim slot, current edge
+    uint32_t en, rpos, tent, base;    // next edge, route position, entry step, current lane row
+    uint32_t nbase, nen, nsg;         // on the next edge: lane row, the edge after, its signal's green
+    float x, vn, nv0;                 // position and speed now, next edge's speed limit
+    uint16_t len, nlen, nsph;         // current / next edge length, next signal phases | phase << 8
+    uint8_t lane, tln;                // lane asked for, target lane on the next edge
+};
+
+// What step_p3 needs of a lane-change intender (packed by step_p1).
+struct __align__(16) IntendRec {
+    uint32_t s, base;                 // slot, current lane row
+    uint64_t hk;                      // lane-change draw key
+    float x, xn, vn;                  // position now and next, speed next
+    uint16_t len;
+    uint8_t lane, up;
 };
 
 struct Dev {
@@ -92,29 +129,37 @@ struct Dev {
     uint8_t *imap[2];          // lane-change intent marks of step k: imap[k&1]
     uint32_t *claim[2];        // per (edge, lane): lowest id asking to enter, by step parity
     // trips, by vehicle id
-    const uint32_t *dep;       // departure step
     const uint32_t *route;     // all routes, vehicle-id order
     const uint32_t *roff;      // route start of vehicle id (n + 1 entries)
+    const RouteRec *rrec;      // per route position
     const uint64_t *hkey;      // lane-change draw key: scenario seed ^ scenario-local id * C1
     uint32_t *dep_act, *arr;
     uint8_t *status;
-    // departure queues, one per origin edge
+    // departure queues, one per origin edge (queue records in queue order)
     uint32_t n_org;
-    const uint32_t *org_edge, *org_qoff, *org_qend, *qid;
-    uint32_t *org_head;
-    uint32_t *org_dep;         // departure step of the queue head (kNone: queue empty)
+    const uint32_t *org_edge, *org_qoff, *org_qend;
+    const EdgeRec *org_rec;    // edge record of each origin edge
+    const QRec *qrec;
+    uint32_t *org_head;        // position of the head in its queue
+    QRec *org_hd;              // head record (h = kNone: queue empty)
     uint8_t *dreq;             // requested lane this step (kEmpty = none)
     uint32_t *dslot, *dprev;   // claim slot asked for this step / won at the previous step
+    uint32_t *den, *dsg;       // stash of the request: next edge, signal
+    uint16_t *dsph;
+    uint8_t *dtlc;
     // slots (current set: the host alternates two sets around each compaction)
     Slots s;
     uint32_t cap;              // slot capacity
     // per-step lists, by step parity
-    uint32_t *cross_list[2], *intend_list[2];
-    uint32_t *counts;          // [0..1] cross count by parity, [2..3] intend count by parity
-    uint32_t *dep_list[2];     // origin edges that asked for a departure, by parity (counts[4..5])
-    // statistics
+    CrossRec *cross_list[2];
+    IntendRec *intend_list[2];
+    uint32_t *counts;          // [0..1] cross count by parity, [2..3] intend count, [4..5] departure requests
+    uint32_t *dep_list[2];     // origin edges that asked for a departure, by parity
+    // statistics; binned arrays are bin-major ([bin][edge]) so the updates of
+    // one step fall in one or two rows that stay in L2
     unsigned long long *ent, *ext, *tts;
     uint32_t *bin_in, *bin_tt, *bin_cnt, *bin_occ;
+    uint32_t n_edges;
     // run state
     uint32_t *kbase;           // step of the first step of the current graph chunk
     uint32_t *n_slots;         // slots in use
@@ -142,6 +187,10 @@ struct SortWork {
 int launch_compact(const Dev &d, const Slots &dst, const SortWork &w, uint32_t koff, bool sort, int grid,
                    cudaStream_t st);
 uint32_t compact_tile();
+
+// per-route-position records (load time)
+void launch_route_records(const Dev &d, uint64_t n_trips, RouteRec *out, cudaStream_t st);
+void launch_transpose_bins(const uint32_t *in, uint32_t n_edges, uint32_t n_bins, uint32_t *out, cudaStream_t st);
 
 // helpers for the query functions
 void launch_state_scatter(const Dev &d, uint32_t k, float *x, float *v, uint32_t *edge, uint8_t *lane,

@@ -80,6 +80,7 @@ int check_params(const lpsim_params *p) {
     if (p->block_size && p->block_size != 128 && p->block_size != 256 && p->block_size != 512)
         return fail(LPSIM_E_INVALID_ARG, "block_size must be 0, 128, 256 or 512");
     if (p->flags & ~3u) return fail(LPSIM_E_INVALID_ARG, "unknown flag bits");
+    if (p->sort_period > 256) return fail(LPSIM_E_INVALID_ARG, "sort_period must be at most 256");
     return LPSIM_OK;
 }
 
@@ -104,15 +105,15 @@ int alloc_slots(lpsim_ctx *c, Slots &s, uint32_t cap) {
     TRY(dnew_mut(c, s.cprev, cap));
     TRY(dnew_mut(c, s.len, cap));
     TRY(dnew_mut(c, s.v0, cap));
+    TRY(dnew_mut(c, s.en, cap));
+    TRY(dnew_mut(c, s.sg, cap));
+    TRY(dnew_mut(c, s.sph, cap));
     for (int i = 0; i < 2; i++) {
         TRY(dnew_mut(c, s.x[i], cap));
         TRY(dnew_mut(c, s.v[i], cap));
     }
     // per-step scratch, rewritten before it is read in every step
     TRY(dnew(c, s.act, cap));
-    TRY(dnew(c, s.tl, cap));
-    TRY(dnew(c, s.tln, cap));
-    TRY(dnew(c, s.cslot, cap));
     return LPSIM_OK;
 }
 
@@ -144,7 +145,7 @@ int reset_state(lpsim_ctx *c) {
         CU(cudaMemsetAsync(d.status, 0, c->n_trips, st));
         CU(cudaMemsetAsync(d.org_head, 0, (size_t)d.n_org * 4, st));
         CU(cudaMemsetAsync(d.dprev, 0xFF, (size_t)d.n_org * 4, st));
-        CU(cudaMemcpyAsync(d.org_dep, c->org_dep0, (size_t)d.n_org * 4, cudaMemcpyDeviceToDevice, st));
+        CU(cudaMemcpyAsync(d.org_hd, c->org_hd0, (size_t)d.n_org * sizeof(QRec), cudaMemcpyDeviceToDevice, st));
     }
     c->k = 0;
     c->cur = 0;
@@ -439,7 +440,7 @@ int load_network_impl(lpsim_ctx **out, const lpsim_network *net, const lpsim_par
     uint32_t want = p->chunk_steps ? p->chunk_steps : 384;
     c->C = std::max(base, (want + base - 1) / base * base);
     c->block = p->block_size ? (int)p->block_size : 256;
-    c->grid = c->n_sm * (int)(p->blocks_per_sm ? p->blocks_per_sm : 6) * 256 / c->block;
+    c->grid = c->n_sm * (int)(p->blocks_per_sm ? p->blocks_per_sm : 4) * 256 / c->block;
     if (c->grid < 1) c->grid = 1;
     c->sort = (p->flags & 1u) == 0;
     c->d.check = (p->flags & 2u) ? 1u : 0u;
@@ -460,6 +461,7 @@ int load_network_impl(lpsim_ctx **out, const lpsim_network *net, const lpsim_par
     d.m.seed = p->seed;
     d.m.bin_steps = p->bin_steps;
     d.m.n_bins = p->n_bins;
+    d.n_edges = ne;
 
     EdgeRec *edge = nullptr;
     NodeRec *node = nullptr;
@@ -644,27 +646,51 @@ int load_demand_impl(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, cons
     }
     Dev &d = c->d;
     const uint32_t norg = (uint32_t)org_edge.size();
-    uint32_t *ddep, *droute, *droff, *oe, *oq, *oqe, *dqid;
+    // queue records (vehicle, departure step, route span) in queue order
+    std::vector<QRec> qrec(n), hd0(norg);
+    for (uint64_t q = 0; q < n; q++) qrec[q] = QRec{qid[q], dep[qid[q]], roff[qid[q]], roff[qid[q] + 1]};
+    std::vector<EdgeRec> orec(norg);
+    {
+        std::vector<EdgeRec> all(c->n_edges);
+        CU(cudaMemcpy(all.data(), d.edge, c->n_edges * sizeof(EdgeRec), cudaMemcpyDeviceToHost));
+        for (uint32_t j = 0; j < norg; j++) {
+            orec[j] = all[org_edge[j]];
+            hd0[j] = qrec[org_qoff[j]];
+        }
+    }
+    uint32_t *droute, *droff, *oe, *oq, *oqe;
     uint64_t *dhkey;
+    QRec *dqrec;
+    EdgeRec *dorec;
+    RouteRec *drrec;
     TRY(dnew(c, dhkey, n));
-    TRY(dnew(c, ddep, n));
     TRY(dnew(c, droute, route.size()));
     TRY(dnew(c, droff, n + 1));
+    TRY(dnew(c, drrec, route.size()));
     TRY(dnew_mut(c, d.dep_act, n));
     TRY(dnew_mut(c, d.arr, n));
     TRY(dnew_mut(c, d.status, n));
     TRY(dnew(c, oe, norg));
     TRY(dnew(c, oq, norg));
     TRY(dnew(c, oqe, norg));
-    TRY(dnew(c, dqid, n));
+    TRY(dnew(c, dqrec, n));
+    TRY(dnew(c, dorec, norg));
     TRY(dnew_mut(c, d.org_head, norg));
-    TRY(dnew_mut(c, d.org_dep, norg));
-    TRY(dnew(c, c->org_dep0, norg));
+    TRY(dnew_mut(c, d.org_hd, norg));
+    TRY(dnew(c, c->org_hd0, norg));
     TRY(dnew(c, d.dslot, norg));
     TRY(dnew_mut(c, d.dprev, norg));
     TRY(dnew(c, d.dreq, norg));
+    TRY(dnew(c, d.den, norg));
+    TRY(dnew(c, d.dsg, norg));
+    TRY(dnew(c, d.dsph, norg));
+    TRY(dnew(c, d.dtlc, norg));
     for (int i = 0; i < 2; i++) TRY(dnew(c, d.dep_list[i], norg));
-    const uint32_t cap = (uint32_t)n;
+    // slots: live vehicles plus the holes left between compactions by
+    // arrivals and by departures that lost an entry conflict
+    const uint64_t cap64 = n + 256ull * norg + 1024;
+    if (cap64 >= 0xFFFFFFF0ull) return fail(LPSIM_E_INVALID_ARG, "too many trips for the slot index");
+    const uint32_t cap = (uint32_t)cap64;
     for (int i = 0; i < 2; i++) TRY(alloc_slots(c, c->sets[i], cap));
     for (int i = 0; i < 2; i++) {
         TRY(dnew(c, d.cross_list[i], cap));
@@ -680,26 +706,27 @@ int load_demand_impl(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, cons
         TRY(dnew(c, c->w.perm[i], cap));
     }
     TRY(upload(c, dhkey, hkey.data(), n * 8));
-    TRY(upload(c, ddep, dep.data(), n * 4));
     TRY(upload(c, droute, route.data(), route.size() * 4));
     TRY(upload(c, droff, roff.data(), (n + 1) * 4));
     TRY(upload(c, oe, org_edge.data(), norg * 4ull));
     TRY(upload(c, oq, org_qoff.data(), norg * 4ull));
     TRY(upload(c, oqe, org_qend.data(), norg * 4ull));
-    TRY(upload(c, dqid, qid.data(), n * 4));
-    std::vector<uint32_t> od0(norg);
-    for (uint32_t j = 0; j < norg; j++) od0[j] = dep[qid[org_qoff[j]]];
-    TRY(upload(c, c->org_dep0, od0.data(), norg * 4ull));
+    TRY(upload(c, dqrec, qrec.data(), n * sizeof(QRec)));
+    TRY(upload(c, dorec, orec.data(), norg * sizeof(EdgeRec)));
+    TRY(upload(c, c->org_hd0, hd0.data(), norg * sizeof(QRec)));
     d.hkey = dhkey;
-    d.dep = ddep;
     d.route = droute;
     d.roff = droff;
+    d.rrec = drrec;
     d.n_org = norg;
     d.org_edge = oe;
     d.org_qoff = oq;
     d.org_qend = oqe;
-    d.qid = dqid;
+    d.qrec = dqrec;
+    d.org_rec = dorec;
     d.cap = cap;
+    launch_route_records(d, n, drrec, c->stream);
+    CU(cudaGetLastError());
     c->n_trips = n;
     c->loaded = true;
     if (!scen) c->scen_trip_off = {0, n};
@@ -871,10 +898,31 @@ int lpsim_link_stats(lpsim_ctx *c, lpsim_link_stat *out, uint64_t n_edges, uint3
     }
     size_t nb = (size_t)c->n_edges * c->p.n_bins * 4;
     if (nb) {
-        if (bin_inflow) CU(cudaMemcpy(bin_inflow, c->d.bin_in, nb, cudaMemcpyDeviceToHost));
-        if (bin_tt_sum) CU(cudaMemcpy(bin_tt_sum, c->d.bin_tt, nb, cudaMemcpyDeviceToHost));
-        if (bin_tt_cnt) CU(cudaMemcpy(bin_tt_cnt, c->d.bin_cnt, nb, cudaMemcpyDeviceToHost));
-        if (bin_occ) CU(cudaMemcpy(bin_occ, c->d.bin_occ, nb, cudaMemcpyDeviceToHost));
+        // device arrays are bin-major: transpose into edge-major scratch first
+        uint32_t *tmp = static_cast<uint32_t *>(c->dalloc(nb));
+        if (!tmp) return fail(LPSIM_E_OOM, "device scratch allocation failed");
+        struct {
+            uint32_t *host;
+            const uint32_t *dev;
+        } outs[] = {{bin_inflow, c->d.bin_in}, {bin_tt_sum, c->d.bin_tt}, {bin_tt_cnt, c->d.bin_cnt},
+                    {bin_occ, c->d.bin_occ}};
+        int rc = LPSIM_OK;
+        for (auto &o : outs) {
+            if (!o.host) continue;
+            launch_transpose_bins(o.dev, c->n_edges, c->p.n_bins, tmp, c->stream);
+            cudaError_t e = cudaMemcpyAsync(o.host, tmp, nb, cudaMemcpyDeviceToHost, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) {
+                rc = fail(LPSIM_E_CUDA, std::string("link statistics: ") + cudaGetErrorString(e));
+                break;
+            }
+        }
+        if (!c->blocks.empty() && c->blocks.back() == tmp) {
+            c->blocks.pop_back();
+            if (c->release) c->release(tmp, c->alloc_user);
+            else cudaFree(tmp);
+        }
+        if (rc) return rc;
     }
     return LPSIM_OK;
 }
@@ -1003,7 +1051,7 @@ int lpsim_autotune(lpsim_ctx *c, uint32_t window_steps, lpsim_tune_result *out) 
     if (!c) return fail(LPSIM_E_INVALID_ARG, "ctx is NULL");
     if (!c->loaded) return fail(LPSIM_E_STATE, "lpsim_load_demand has not been called");
     if (window_steps == 0) return fail(LPSIM_E_INVALID_ARG, "window_steps must be > 0");
-    const uint32_t cur_cfg[4] = {(uint32_t)c->block, c->p.blocks_per_sm ? c->p.blocks_per_sm : 6u, c->R,
+    const uint32_t cur_cfg[4] = {(uint32_t)c->block, c->p.blocks_per_sm ? c->p.blocks_per_sm : 4u, c->R,
                                  c->p.chunk_steps ? c->p.chunk_steps : 384u};
     TRY(snapshot_impl(c));
     const bool timing = c->timing;
@@ -1056,7 +1104,7 @@ int lpsim_set_config(lpsim_ctx *c, uint32_t block_size, uint32_t blocks_per_sm, 
     if (!c) return fail(LPSIM_E_INVALID_ARG, "ctx is NULL");
     if (block_size != 128 && block_size != 256 && block_size != 512)
         return fail(LPSIM_E_INVALID_ARG, "block_size must be 128, 256 or 512");
-    if (blocks_per_sm == 0 || blocks_per_sm > 8 || sort_period == 0 || chunk_steps == 0)
+    if (blocks_per_sm == 0 || blocks_per_sm > 8 || sort_period == 0 || sort_period > 256 || chunk_steps == 0)
         return fail(LPSIM_E_INVALID_ARG, "configuration value out of range");
     return apply_config(c, block_size, blocks_per_sm, sort_period, chunk_steps);
 }

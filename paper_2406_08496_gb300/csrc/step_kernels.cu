@@ -42,14 +42,6 @@ __device__ __forceinline__ float unit24(uint64_t h) {
     return (float)(uint32_t)(h >> 40) * (1.0f / 16777216.0f);
 }
 
-// Lane-change draw of vehicle `id` at step k: SplitMix64 of
-// seed ^ local_id * C1 ^ k * C2, where hkey[id] = seed ^ local_id * C1 was
-// formed at load time (local_id = the vehicle's id within its scenario, so a
-// scenario draws the same numbers alone or inside a batch).
-__device__ __forceinline__ uint64_t lc_hash(const Dev &d, uint32_t id, uint32_t k) {
-    return splitmix64_mix(d.hkey[id] ^ ((uint64_t)k * 0xD1B54A32D192ED03ull));
-}
-
 __device__ __forceinline__ float fmax0(float t) { return t > 0.0f ? t : 0.0f; }
 
 __device__ __forceinline__ uint8_t speed_byte(float v) {
@@ -103,26 +95,6 @@ __device__ __forceinline__ uint32_t first_occupied_wide(const uint8_t *row, uint
     return kNone;
 }
 
-// first occupied cell in [lo, hi] of a 16-byte aligned row, or kNone
-__device__ __forceinline__ uint32_t first_occupied(const uint8_t *row, uint32_t lo, uint32_t hi) {
-    if (lo > hi) return kNone;
-    for (uint32_t c = lo & ~15u; c <= hi; c += 16u) {
-        uint32_t m = occ_mask16(*reinterpret_cast<const uint4 *>(row + c)) & range_mask16(c, lo, hi);
-        if (m) return c + (uint32_t)(__ffs((int)m) - 1);
-    }
-    return kNone;
-}
-
-// last occupied cell in [lo, hi], or kNone
-__device__ __forceinline__ uint32_t last_occupied(const uint8_t *row, uint32_t lo, uint32_t hi) {
-    if (lo > hi) return kNone;
-    for (int c = (int)(hi & ~15u); c >= (int)(lo & ~15u); c -= 16) {
-        uint32_t m = occ_mask16(*reinterpret_cast<const uint4 *>(row + c)) & range_mask16((uint32_t)c, lo, hi);
-        if (m) return (uint32_t)c + (31u - (uint32_t)__clz((int)m));
-    }
-    return kNone;
-}
-
 __device__ __forceinline__ float idm_speed(const Model &m, float v, float vf, float s, float v0) {
     float dv = v - vf;
     float z = v * m.T + (v * dv) / m.two_sqrt_ab;
@@ -133,11 +105,6 @@ __device__ __forceinline__ float idm_speed(const Model &m, float v, float vf, fl
     return fmax0(v + acc * m.dt);
 }
 
-__device__ __forceinline__ bool is_green(const NodeRec &nr, uint32_t arank, uint32_t k) {
-    if (nr.green == 0) return true;
-    return (k / nr.green) % nr.nphase == arank;
-}
-
 // Write a next-map cell.  With the checking flag the cell is read first and
 // a second writer is reported in the error word; without it the store does
 // not wait for a load (the rules never give one cell two writers).
@@ -146,33 +113,11 @@ __device__ __forceinline__ void put_cell(const Dev &d, uint8_t *map, uint32_t id
     map[idx] = val;
 }
 
-// Target lane on edge `edge` for the movement onto `next` (kNoLane if none).
-__device__ __forceinline__ uint32_t target_lane(const Dev &d, const EdgeRec &er, uint32_t next) {
-    if (next == kNone) return kNoLane;
-    return ((uint32_t)d.orank[next] * er.lanes) / d.node[er.dst].nout;
-}
-
-// Lane a vehicle entering edge `en` asks for: lanes ordered by distance to
-// the target lane of the movement after `en` (ties to the lower index); the
-// first whose cell 0 is empty in the step-k map.  kNone if none.
-__device__ __forceinline__ uint32_t entry_lane(const Dev &d, const uint8_t *Mc, uint32_t en, const EdgeRec &enr,
-                                               uint32_t next_after) {
-    uint32_t nl = enr.lanes;
-    uint32_t tl = target_lane(d, enr, next_after);
-    if (tl == kNoLane) tl = 0;
-    uint32_t stride = row_stride(enr.len);
-    for (uint32_t dd = 0; dd < nl; dd++) {
-        if (tl >= dd && Mc[enr.moff + (tl - dd) * stride] == kEmpty) return tl - dd;
-        if (dd > 0 && tl + dd < nl && Mc[enr.moff + (tl + dd) * stride] == kEmpty) return tl + dd;
-    }
-    return kNone;
-}
-
 __device__ __forceinline__ void stat_entry(const Dev &d, uint32_t e, uint32_t k) {
     atomicAdd(&d.ent[e], 1ull);
     if (d.m.bin_steps) {
         uint32_t b = (k + 1) / d.m.bin_steps;
-        if (b < d.m.n_bins) atomicAdd(&d.bin_in[(size_t)e * d.m.n_bins + b], 1u);
+        if (b < d.m.n_bins) atomicAdd(&d.bin_in[(size_t)b * d.n_edges + e], 1u);
     }
 }
 
@@ -183,8 +128,8 @@ __device__ __forceinline__ void stat_exit(const Dev &d, uint32_t e, uint32_t k, 
     if (d.m.bin_steps) {
         uint32_t b = tent / d.m.bin_steps;
         if (b < d.m.n_bins) {
-            atomicAdd(&d.bin_tt[(size_t)e * d.m.n_bins + b], steps);
-            atomicAdd(&d.bin_cnt[(size_t)e * d.m.n_bins + b], 1u);
+            atomicAdd(&d.bin_tt[(size_t)b * d.n_edges + e], steps);
+            atomicAdd(&d.bin_cnt[(size_t)b * d.n_edges + e], 1u);
         }
     }
 }
@@ -214,8 +159,26 @@ __device__ __forceinline__ void block_add(unsigned long long *dst, uint32_t val)
 
 // ----------------------------------------------------------------------- P1
 
+// Lane asked for when entering an edge: lanes ordered by distance to the
+// target lane tl (kNoLane counts as 0; ties to the lower index); the first
+// whose cell 0 is empty in the step-k map.  The up-to-4 first cells are read
+// together.  kNone if none is empty.
+__device__ __forceinline__ uint32_t pick_entry_lane(const uint8_t *Mc, const EdgeRec &er, uint32_t tl) {
+    const uint32_t nl = er.lanes, stride = row_stride(er.len);
+    if (tl == kNoLane) tl = 0;
+    uint32_t empty = 0;  // bit l: cell 0 of lane l is empty
+#pragma unroll
+    for (uint32_t l = 0; l < 4; l++)
+        if (l < nl && Mc[er.moff + l * stride] == kEmpty) empty |= 1u << l;
+    for (uint32_t dd = 0; dd < nl; dd++) {
+        if (tl >= dd && ((empty >> (tl - dd)) & 1u)) return tl - dd;
+        if (dd > 0 && tl + dd < nl && ((empty >> (tl + dd)) & 1u)) return tl + dd;
+    }
+    return kNone;
+}
+
 template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) step_p1(Dev d, uint32_t koff) {
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) step_p1(Dev d, uint32_t koff) {
     pdl_prologue();
     const uint32_t k = *d.kbase + koff;
     const uint32_t par = k & 1u;
@@ -241,21 +204,25 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) step_p1(Dev d, uint32_t k
             // for a departure of the queue head once its step has come
             const uint32_t j = i - n;
             const uint32_t dp = d.dprev[j];
+            const QRec hd = d.org_hd[j];
             if (dp != kNone) {
                 claim_old[dp] = kNone;
                 d.dprev[j] = kNone;
             }
             uint8_t req = kEmpty;
-            if (d.org_dep[j] <= k) {
-                const uint32_t h = d.qid[d.org_qoff[j] + d.org_head[j]];
-                const uint32_t e0 = d.org_edge[j];
-                const EdgeRec er = d.edge[e0];
-                const uint32_t r0 = d.roff[h], r1 = d.roff[h + 1];
-                const uint32_t l = entry_lane(d, Mc, e0, er, r0 + 1 < r1 ? d.route[r0 + 1] : kNone);
+            if (hd.h != kNone && hd.dep <= k) {
+                const EdgeRec er = d.org_rec[j];
+                const RouteRec rr = d.rrec[hd.r0];
+                const uint32_t nxt = hd.r0 + 1 < hd.r1 ? d.route[hd.r0 + 1] : kNone;
+                const uint32_t l = pick_entry_lane(Mc, er, rr.tl);
                 if (l != kNone) {
-                    const uint32_t slot = d.slot_off[e0] + l;
-                    atomicMin(&claim[slot], h);
+                    const uint32_t slot = d.slot_off[d.org_edge[j]] + l;
+                    atomicMin(&claim[slot], hd.h);
                     d.dslot[j] = slot;
+                    d.den[j] = nxt;
+                    d.dsg[j] = rr.green;
+                    d.dsph[j] = (uint16_t)(rr.nphase | (rr.arank << 8));
+                    d.dtlc[j] = rr.tl;
                     req = (uint8_t)l;
                     const uint32_t pos = atomicAdd(&d.counts[4 + par], 1u);
                     d.dep_list[par][pos] = j;
@@ -265,21 +232,33 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) step_p1(Dev d, uint32_t k
             continue;
         }
         const uint32_t s = i;
+        // every slot field, loaded together (one memory round trip)
         const uint8_t flag = d.s.flag[s];
+        const uint32_t pc = d.s.pcell[s];
+        const uint32_t im = d.s.imark[s];
+        const uint32_t cp = d.s.cprev[s];
+        const float x = xc[s], v = vc[s];
+        const uint32_t base = d.s.base[s];
+        const uint32_t len = d.s.len[s];
+        const float v0 = d.s.v0[s];
+        const uint32_t en = d.s.en[s];
+        const uint32_t G = d.s.sg[s];
+        const uint32_t ph = d.s.sph[s];
+        const uint32_t tl = d.s.tlc[s];  // kNoLane on the last edge of the route
+        const uint32_t ln = d.s.lane[s];
+        const uint32_t id = d.s.id[s];
+        const uint32_t e = d.s.e[s];
+        const uint32_t rpos = d.s.rpos[s], rlast = d.s.rlast[s];
+        const uint32_t tent = d.s.tent[s];
         if (flag == kDead) continue;
-        {
-            const uint32_t pc = d.s.pcell[s];
-            if (pc != kNone) Mo[pc] = kEmpty;
-            const uint32_t im = d.s.imark[s];
-            if (im != kNone) {
-                Io[im] = 0;
-                d.s.imark[s] = kNone;
-            }
-            const uint32_t cp = d.s.cprev[s];
-            if (cp != kNone) {
-                claim_old[cp] = kNone;
-                d.s.cprev[s] = kNone;
-            }
+        if (pc != kNone) Mo[pc] = kEmpty;
+        if (im != kNone) {
+            Io[im] = 0;
+            d.s.imark[s] = kNone;
+        }
+        if (cp != kNone) {
+            claim_old[cp] = kNone;
+            d.s.cprev[s] = kNone;
         }
         if (flag == kArrivedPending) {
             d.s.flag[s] = kDead;
@@ -287,13 +266,9 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) step_p1(Dev d, uint32_t k
             continue;
         }
         live++;
-        const float x = xc[s], v = vc[s];
-        const uint32_t base = d.s.base[s];
-        const uint32_t len = d.s.len[s];
-        const float v0 = d.s.v0[s];
         const uint32_t c = (uint32_t)x;
         d.s.pcell[s] = base + c;
-        if (sample) atomicAdd(&d.bin_occ[(size_t)d.s.e[s] * m.n_bins + k / m.bin_steps], 1u);
+        if (sample) atomicAdd(&d.bin_occ[(size_t)(k / m.bin_steps) * d.n_edges + e], 1u);
 
         // leader: nearest occupied cell ahead in the own lane of the own edge.
         // Cells beyond both d_front and the farthest reach of this step
@@ -301,6 +276,25 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) step_p1(Dev d, uint32_t k
         const float d_front = (2.0f * m.dt) * v;
         const float vmax_step = fmaxf(v0, v + m.a * m.dt);
         const float reach = fmaxf(d_front, vmax_step * m.dt + m.s0);
+        const float L = (float)len;
+        // in the same round trip as the scan: the next edge's records for a
+        // vehicle that may reach the stop line, the lane-change key for one
+        // that may draw (both only used under the exact conditions below)
+        const bool may_cross = en != kNone && x + vmax_step * m.dt + 1.0f >= L;
+        const bool may_draw = tl != kNoLane && tl != ln && ((tl > ln) == (par == 1u)) && (L - x) < m.x0;
+        EdgeRec enr{};
+        RouteRec rr{};
+        uint32_t nen = kNone;
+        if (may_cross) {
+            enr = d.edge[en];
+            rr = d.rrec[rpos + 1];
+            nen = rpos + 1 < rlast ? d.route[rpos + 2] : kNone;
+        }
+        // lane-change draw at step k: SplitMix64 of hkey ^ k * C2, where
+        // hkey[id] = seed ^ local_id * C1 was formed at load time (local_id =
+        // the vehicle's id within its scenario, so a scenario draws the same
+        // numbers alone or inside a batch)
+        const uint64_t hk = may_draw ? d.hkey[id] : 0ull;
         uint32_t hi = c + (uint32_t)fminf(reach, 65535.0f) + 2u;
         if (hi > len - 1) hi = len - 1;
         const uint32_t cf = first_occupied_wide(Mc + base, c + 1, hi);
@@ -319,13 +313,10 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) step_p1(Dev d, uint32_t k
                 vn = 0.0f;
             }
         }
-        const float L = (float)len;
         if (xn >= L) {
-            const uint32_t rpos = d.s.rpos[s], rlast = d.s.rlast[s];
-            const uint32_t e = d.s.e[s];
-            if (rpos == rlast) {
-                const uint32_t id = d.s.id[s];
-                stat_exit(d, e, k, d.s.tent[s]);
+            if (en == kNone) {
+                // last edge of the route: arrive
+                stat_exit(d, e, k, tent);
                 d.arr[id] = k + 1;
                 d.status[id] = kArrived;
                 d.s.flag[s] = kArrivedPending;
@@ -334,22 +325,39 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) step_p1(Dev d, uint32_t k
                 continue;
             }
             bool cross = false;
-            const EdgeRec er = d.edge[e];
-            if (is_green(d.node[er.dst], er.arank, k)) {
-                const uint32_t en = d.route[rpos + 1];
-                const EdgeRec enr = d.edge[en];
-                const uint32_t after = rpos + 1 < rlast ? d.route[rpos + 2] : kNone;
-                const uint32_t l = entry_lane(d, Mc, en, enr, after);
+            if (G == 0 || (k / G) % (ph & 0xFFu) == (ph >> 8)) {
+                if (!may_cross) {  // cannot happen: x' <= x + vmax_step * dt < L - 1 otherwise
+                    enr = d.edge[en];
+                    rr = d.rrec[rpos + 1];
+                    nen = rpos + 1 < rlast ? d.route[rpos + 2] : kNone;
+                }
+                const uint32_t l = pick_entry_lane(Mc, enr, rr.tl);
                 if (l != kNone) {
                     const uint32_t slot = d.slot_off[en] + l;
-                    atomicMin(&claim[slot], d.s.id[s]);
-                    d.s.tl[s] = (uint8_t)l;
-                    d.s.cslot[s] = slot;
-                    d.s.tln[s] = (uint8_t)target_lane(d, enr, after);
+                    atomicMin(&claim[slot], id);
+                    CrossRec cr;
+                    cr.s = s;
+                    cr.id = id;
+                    cr.cslot = slot;
+                    cr.e = e;
+                    cr.en = en;
+                    cr.rpos = rpos;
+                    cr.tent = tent;
+                    cr.base = base;
+                    cr.nbase = enr.moff + l * row_stride(enr.len);
+                    cr.nen = nen;
+                    cr.nsg = rr.green;
+                    cr.x = x;
+                    cr.vn = vn;
+                    cr.nv0 = enr.v0;
+                    cr.len = (uint16_t)len;
+                    cr.nlen = enr.len;
+                    cr.nsph = (uint16_t)(rr.nphase | (rr.arank << 8));
+                    cr.lane = (uint8_t)l;
+                    cr.tln = rr.tl;
                     d.s.act[s] = kActCross;
-                    vw[s] = vn;
                     const uint32_t pos = atomicAdd(&d.counts[par], 1u);
-                    d.cross_list[par][pos] = s;
+                    d.cross_list[par][pos] = cr;
                     cross = true;
                 }
             }
@@ -368,22 +376,26 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) step_p1(Dev d, uint32_t k
         const uint32_t cn = (uint32_t)xn;
         put_cell(d, Mn, base + cn, speed_byte(vn));
         uint8_t act = kActStay;
-        const uint32_t tl = d.s.tlc[s];  // kNoLane on the last edge of the route
-        const uint32_t ln = d.s.lane[s];
-        if (tl != kNoLane && tl != ln) {
-            const bool up = tl > ln;
-            if (up == (par == 1u)) {
-                const float xrem = L - x;
-                const float mp = xrem >= m.x0 ? 0.0f : 1.0f - xrem / m.x0;
-                // u is in [0, 1): no draw can pass when mp <= 0
-                if (mp > 0.0f && unit24(lc_hash(d, d.s.id[s], k)) < mp) {
-                    act = kActIntend;
-                    d.s.tl[s] = up ? 1 : 0;  // direction
-                    Iw[base + cn] = 1;
-                    d.s.imark[s] = base + cn;
-                    const uint32_t pos = atomicAdd(&d.counts[2 + par], 1u);
-                    d.intend_list[par][pos] = s;
-                }
+        if (may_draw) {
+            const float xrem = L - x;
+            const float mp = xrem >= m.x0 ? 0.0f : 1.0f - xrem / m.x0;
+            // u is in [0, 1): no draw can pass when mp <= 0
+            if (mp > 0.0f && unit24(splitmix64_mix(hk ^ ((uint64_t)k * 0xD1B54A32D192ED03ull))) < mp) {
+                act = kActIntend;
+                Iw[base + cn] = 1;
+                d.s.imark[s] = base + cn;
+                IntendRec ir;
+                ir.s = s;
+                ir.base = base;
+                ir.hk = hk;
+                ir.x = x;
+                ir.xn = xn;
+                ir.vn = vn;
+                ir.len = (uint16_t)len;
+                ir.lane = (uint8_t)ln;
+                ir.up = tl > ln ? 1 : 0;
+                const uint32_t pos = atomicAdd(&d.counts[2 + par], 1u);
+                d.intend_list[par][pos] = ir;
             }
         }
         d.s.act[s] = act;
@@ -401,72 +413,84 @@ __global__ void __launch_bounds__(BLOCK) step_p2(Dev d, uint32_t koff) {
     const uint32_t par = k & 1u;
     uint8_t *Mn = d.map[(k + 1) % 3];
     const uint32_t *claim = d.claim[par];
-    const float *xc = d.s.x[par];
     float *xw = d.s.x[par ^ 1u], *vw = d.s.v[par ^ 1u];
     const uint32_t ncross = d.counts[par];
-    const uint32_t total = ncross + d.counts[4 + par];
-    const uint32_t *list = d.cross_list[par];
+    const uint32_t ndep = d.counts[4 + par];
+    const uint32_t n0 = *d.n_slots;  // new vehicles take slots n0 .. n0 + ndep - 1
+    const uint32_t total = ncross + ndep;
+    const CrossRec *list = d.cross_list[par];
     uint32_t events = 0, departed = 0;
     for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < total; i += gridDim.x * BLOCK) {
         if (i < ncross) {
-            const uint32_t s = list[i];
-            const uint32_t id = d.s.id[s];
-            const uint32_t cslot = d.s.cslot[s];
-            if (claim[cslot] == id) {
-                const uint32_t rpos = d.s.rpos[s];
-                const uint32_t e = d.s.e[s];
-                const uint32_t en = d.route[rpos + 1];
-                const EdgeRec enr = d.edge[en];
-                const uint32_t l = d.s.tl[s];
-                const uint32_t nbase = enr.moff + l * row_stride(enr.len);
-                stat_exit(d, e, k, d.s.tent[s]);
-                stat_entry(d, en, k);
-                d.s.e[s] = en;
-                d.s.rpos[s] = rpos + 1;
-                d.s.lane[s] = (uint8_t)l;
+            const CrossRec cr = list[i];
+            if (claim[cr.cslot] == cr.id) {
+                const uint32_t s = cr.s;
+                stat_exit(d, cr.e, k, cr.tent);
+                stat_entry(d, cr.en, k);
+                d.s.e[s] = cr.en;
+                d.s.rpos[s] = cr.rpos + 1;
+                d.s.lane[s] = cr.lane;
                 d.s.tent[s] = k + 1;
-                d.s.tlc[s] = d.s.tln[s];
-                d.s.base[s] = nbase;
-                d.s.len[s] = enr.len;
-                d.s.v0[s] = enr.v0;
-                d.s.cprev[s] = cslot;
+                d.s.tlc[s] = cr.tln;
+                d.s.base[s] = cr.nbase;
+                d.s.len[s] = cr.nlen;
+                d.s.v0[s] = cr.nv0;
+                d.s.en[s] = cr.nen;
+                d.s.sg[s] = cr.nsg;
+                d.s.sph[s] = cr.nsph;
+                d.s.cprev[s] = cr.cslot;
                 xw[s] = 0.0f;
-                put_cell(d, Mn, nbase, speed_byte(vw[s]));
+                vw[s] = cr.vn;
+                put_cell(d, Mn, cr.nbase, speed_byte(cr.vn));
                 events++;
             } else {
-                const float x = xc[s];
-                const float lim = (float)d.s.len[s] - 1.0f;
-                const float xh = x > lim ? x : lim;
-                xw[s] = xh;
-                vw[s] = 0.0f;
-                put_cell(d, Mn, d.s.base[s] + (uint32_t)xh, 0);
+                const float lim = (float)cr.len - 1.0f;
+                const float xh = cr.x > lim ? cr.x : lim;
+                xw[cr.s] = xh;
+                vw[cr.s] = 0.0f;
+                put_cell(d, Mn, cr.base + (uint32_t)xh, 0);
             }
             continue;
         }
-        const uint32_t j = d.dep_list[par][i - ncross];
-        const uint32_t qh = d.org_qoff[j] + d.org_head[j];
-        const uint32_t h = d.qid[qh];
+        // departure request number i - ncross: its slot is fixed in advance
+        const uint32_t q = i - ncross;
+        const uint32_t j = d.dep_list[par][q];
+        const uint32_t s = n0 + q;
+        const QRec hd = d.org_hd[j];
         const uint32_t slot = d.dslot[j];
-        if (claim[slot] != h) continue;
-        const uint32_t s = atomicAdd(d.n_slots, 1u);
+        const uint32_t l = d.dreq[j];
+        const uint32_t qh = d.org_qoff[j] + d.org_head[j];
+        const uint32_t qend = d.org_qend[j];
+        const EdgeRec er = d.org_rec[j];
+        const uint32_t nen = d.den[j], nsg = d.dsg[j];
+        const uint16_t nsph = d.dsph[j];
+        const uint8_t tlc = d.dtlc[j];
+        const QRec next = qh + 1 < qend ? d.qrec[qh + 1] : QRec{kNone, kNone, 0, 0};
         if (s >= d.cap) {
             atomicOr(d.err, kErrSlotOverflow);
             continue;
         }
+        if (claim[slot] != hd.h) {
+            d.s.flag[s] = kDead;
+            d.s.pcell[s] = kNone;
+            d.s.imark[s] = kNone;
+            d.s.cprev[s] = kNone;
+            continue;
+        }
         const uint32_t e0 = d.org_edge[j];
-        const EdgeRec er = d.edge[e0];
-        const uint32_t l = d.dreq[j];
-        const uint32_t r0 = d.roff[h], r1 = d.roff[h + 1];
         const uint32_t b0 = er.moff + l * row_stride(er.len);
-        d.s.id[s] = h;
+        d.s.id[s] = hd.h;
         d.s.e[s] = e0;
-        d.s.rpos[s] = r0;
-        d.s.rlast[s] = r1 - 1;
+        d.s.rpos[s] = hd.r0;
+        d.s.rlast[s] = hd.r1 - 1;
         d.s.lane[s] = (uint8_t)l;
-        d.s.tlc[s] = (uint8_t)target_lane(d, er, r0 + 1 < r1 ? d.route[r0 + 1] : kNone);
+        d.s.tlc[s] = tlc;
         d.s.base[s] = b0;
         d.s.len[s] = er.len;
         d.s.v0[s] = er.v0;
+        d.s.en[s] = nen;
+        d.s.sg[s] = nsg;
+        d.s.sph[s] = nsph;
         d.s.tent[s] = k + 1;
         d.s.pcell[s] = kNone;
         d.s.imark[s] = kNone;
@@ -477,9 +501,9 @@ __global__ void __launch_bounds__(BLOCK) step_p2(Dev d, uint32_t koff) {
         put_cell(d, Mn, b0, 0);
         d.dprev[j] = slot;
         d.org_head[j] += 1;
-        d.org_dep[j] = qh + 1 < d.org_qend[j] ? d.dep[d.qid[qh + 1]] : kNone;
-        d.dep_act[h] = k + 1;
-        d.status[h] = kActive;
+        d.org_hd[j] = next;
+        d.dep_act[hd.h] = k + 1;
+        d.status[hd.h] = kActive;
         stat_entry(d, e0, k);
         events++;
         departed++;
@@ -490,6 +514,20 @@ __global__ void __launch_bounds__(BLOCK) step_p2(Dev d, uint32_t koff) {
 
 // ----------------------------------------------------------------------- P3
 
+// occupancy masks of the 5 chunks covering [c0 - 64, c0 + 63] around an
+// aligned base (loaded together)
+template <int N>
+__device__ __forceinline__ void load_chunks(const uint8_t *row, uint32_t c_first, uint32_t c_last, uint32_t (&mk)[N]) {
+    uint4 q[N];
+#pragma unroll
+    for (int j = 0; j < N; j++) {
+        const uint32_t c = c_first + 16u * j;
+        q[j] = c <= c_last ? *reinterpret_cast<const uint4 *>(row + c) : make_uint4(~0u, ~0u, ~0u, ~0u);
+    }
+#pragma unroll
+    for (int j = 0; j < N; j++) mk[j] = occ_mask16(q[j]);
+}
+
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) step_p3(Dev d, uint32_t koff) {
     pdl_prologue();
@@ -498,27 +536,45 @@ __global__ void __launch_bounds__(BLOCK) step_p3(Dev d, uint32_t koff) {
     const uint8_t *Mc = d.map[k % 3];
     uint8_t *Mn = d.map[(k + 1) % 3];
     const uint8_t *Iw = d.imap[par];
-    const float *xc = d.s.x[par];
-    const float *xw = d.s.x[par ^ 1u], *vw = d.s.v[par ^ 1u];
     const uint32_t nint = d.counts[2 + par];
     const Model &m = d.m;
     uint32_t changes = 0;
     for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < nint; i += gridDim.x * BLOCK) {
-        const uint32_t s = d.intend_list[par][i];
-        const uint32_t ln = d.s.lane[s];
-        const bool up = d.s.tl[s] != 0;
-        const uint32_t len = d.s.len[s], stride = row_stride(len);
-        const uint32_t base = d.s.base[s];
+        const IntendRec ir = d.intend_list[par][i];
+        const uint32_t s = ir.s;
+        const uint32_t ln = ir.lane;
+        const bool up = ir.up != 0;
+        const uint32_t len = ir.len, stride = row_stride(len);
+        const uint32_t base = ir.base;
+        const float x = ir.x, xn = ir.xn, vn = ir.vn;
         const uint32_t base2 = up ? base + stride : base - stride;
         const uint8_t *row2 = Mc + base2;
-        const float x = xc[s], xn = xw[s], vn = vw[s];
         const uint32_t c0 = (uint32_t)x, cn = (uint32_t)xn;
+        // window [c0 - 64, c0 + 63] of the target lane, clipped to the row
+        const uint32_t lo = c0 > 64u ? c0 - 64u : 0u;
         const uint32_t hi = c0 + 63u < len - 1 ? c0 + 63u : len - 1;
-        const uint32_t ca = first_occupied(row2, c0, hi);
-        const uint32_t cb = c0 > 0 ? last_occupied(row2, c0 > 64u ? c0 - 64u : 0u, c0 - 1) : kNone;
+        const uint32_t cfirst = lo & ~15u;
+        uint32_t mk[9];
+        load_chunks<9>(row2, cfirst, hi, mk);
+        const uint32_t tgt = base2 + cn;
+        const uint8_t tgt_map = Mn[tgt], tgt_mark = Iw[tgt];
+        uint64_t h = 0;
+        if (m.eps_amp > 0.0f) h = splitmix64_mix(ir.hk ^ ((uint64_t)k * 0xD1B54A32D192ED03ull));
+        // lead: first occupied cell in [c0, hi]; lag: last in [lo, c0 - 1]
+        uint32_t ca = kNone, cb = kNone;
+#pragma unroll
+        for (int j = 0; j < 9; j++) {
+            const uint32_t c = cfirst + 16u * j;
+            if (c > hi) break;
+            const uint32_t a = mk[j] & range_mask16(c, c0, hi);
+            if (ca == kNone && a) ca = c + (uint32_t)(__ffs((int)a) - 1);
+            if (c0 > 0 && c <= c0 - 1) {
+                const uint32_t b = mk[j] & range_mask16(c, lo, c0 - 1);
+                if (b) cb = c + (31u - (uint32_t)__clz((int)b));
+            }
+        }
         float eps_a = 0.0f, eps_b = 0.0f;
         if (m.eps_amp > 0.0f) {
-            const uint64_t h = lc_hash(d, d.s.id[s], k);
             eps_a = m.eps_amp * (2.0f * unit24(splitmix64_mix(h ^ 0x632BE59BD9B4E019ull)) - 1.0f);
             eps_b = m.eps_amp * (2.0f * unit24(splitmix64_mix(h ^ 0x8CB92BA72F3D8DD7ull)) - 1.0f);
         }
@@ -533,23 +589,41 @@ __global__ void __launch_bounds__(BLOCK) step_p3(Dev d, uint32_t koff) {
             const float G_lag = (m.g_b + fmax0(m.alpha_b * vb - m.alpha_i * vn)) + eps_b;
             ok = (xn - (float)cb) >= G_lag;
         }
-        if (ok && cn >= 1) {
-            const uint32_t tgt = base2 + cn;
-            if (Mn[tgt] == kEmpty && Iw[tgt] == 0) {
-                const uint32_t own = base + cn;
-                Mn[tgt] = Mn[own];
-                Mn[own] = kEmpty;
-                d.s.lane[s] = (uint8_t)(up ? ln + 1 : ln - 1);
-                d.s.base[s] = base2;
-                changes++;
-            }
+        if (ok && cn >= 1 && tgt_map == kEmpty && tgt_mark == 0) {
+            const uint32_t own = base + cn;
+            Mn[tgt] = Mn[own];
+            Mn[own] = kEmpty;
+            d.s.lane[s] = (uint8_t)(up ? ln + 1 : ln - 1);
+            d.s.base[s] = base2;
+            changes++;
         }
     }
     if (changes) atomicAdd(&d.ctr[2], (unsigned long long)changes);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
+        // the next step's lists start empty; the departures of this step
+        // have taken their slots
         d.counts[par ^ 1u] = 0;
         d.counts[2 + (par ^ 1u)] = 0;
         d.counts[4 + (par ^ 1u)] = 0;
+        *d.n_slots += d.counts[4 + par];
+    }
+}
+
+// per trip: the route records of its positions
+__global__ void route_records(Dev d, uint64_t n, RouteRec *out) {
+    for (uint64_t h = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; h < n; h += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t r0 = d.roff[h], r1 = d.roff[h + 1];
+        for (uint32_t q = r0; q < r1; q++) {
+            const EdgeRec er = d.edge[d.route[q]];
+            const NodeRec nr = d.node[er.dst];
+            RouteRec rr;
+            rr.green = nr.green;
+            rr.nphase = nr.nphase;
+            rr.arank = er.arank;
+            rr.tl = q + 1 < r1 ? (uint8_t)(((uint32_t)d.orank[d.route[q + 1]] * er.lanes) / nr.nout) : kNoLane;
+            rr.pad = 0;
+            out[q] = rr;
+        }
     }
 }
 
@@ -628,6 +702,23 @@ __global__ void max_arrival(Dev d, uint64_t n, uint32_t *out) {
 }
 
 }  // namespace
+
+// bin-major [bin][edge] -> edge-major [edge][bin]
+__global__ void transpose_bins(const uint32_t *in, uint32_t n_edges, uint32_t n_bins, uint32_t *out) {
+    const size_t total = (size_t)n_edges * n_bins;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t e = i / n_bins, b = i % n_bins;
+        out[i] = in[b * n_edges + e];
+    }
+}
+
+void launch_transpose_bins(const uint32_t *in, uint32_t n_edges, uint32_t n_bins, uint32_t *out, cudaStream_t st) {
+    transpose_bins<<<1024, 256, 0, st>>>(in, n_edges, n_bins, out);
+}
+
+void launch_route_records(const Dev &d, uint64_t n_trips, RouteRec *out, cudaStream_t st) {
+    route_records<<<1024, 128, 0, st>>>(d, n_trips, out);
+}
 
 void launch_state_scatter(const Dev &d, uint32_t k, float *x, float *v, uint32_t *edge, uint8_t *lane,
                           uint32_t *ridx, cudaStream_t st) {
