@@ -49,7 +49,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="regional", choices=["regional", "grid", "large", "batch64", "assignment"])
+    ap.add_argument("--workload", default="regional",
+                    choices=["regional", "grid", "large", "batch64", "assignment", "surrogate"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-window", type=int, default=0,
@@ -262,6 +263,34 @@ def assignment_arm(args, L, torch):
     print(json.dumps(out), flush=True)
 
 
+def surrogate_arm(args):
+    """The surrogate MLP's tensor-core kernels on device-resident batches:
+    inference forward (three BF16 GEMMs with fused bias/GELU/head epilogues)
+    and a training forward + backward, as TFLOP/s against the measured BF16
+    peak."""
+    import paper_2406_08496_gb300 as L
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+        peaks = json.load(f)
+    rows = 131072
+    s = L.Surrogate(n_features=11, batch=rows, seed=0)
+    t = s.time(max(args.steps, 10))
+    mac_fwd = 64 * 256 + 256 * 256 * 2 + 256
+    flop_fwd = 2.0 * rows * mac_fwd
+    flop_train = 3.0 * flop_fwd  # forward, input gradients and weight gradients
+    fwd = flop_fwd / (t["forward_ms"] / 1e3) / 1e12
+    trn = flop_train / (t["train_ms"] / 1e3) / 1e12
+    peak = float(peaks["bf16_tflops"])
+    out = {"metric": "surrogate forward TFLOP/s", "value": fwd, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": 1, "ms_per_step": t["forward_ms"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+           "config": {"workload": f"surrogate-mlp-{rows}-rows", "layers": "64-256-256-256-1", "rows": rows},
+           "roofline": {"bound": "tensor", "achieved": fwd, "peak": peak, "unit": "TFLOP/s", "frac": fwd / peak,
+                        "traffic": None, "kernel": "gemm_bf16_tn (forward)",
+                        "peak_source": "MEASURED_PEAKS.json bf16_tflops (measured)"},
+           "train": {"ms_per_batch": t["train_ms"], "tflops": trn, "frac": trn / peak}}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -288,6 +317,9 @@ def main():
         return
     if args.workload == "assignment":
         assignment_arm(args, L, torch)
+        return
+    if args.workload == "surrogate":
+        surrogate_arm(args)
         return
 
     net, dem, label = load_workload(args.workload)

@@ -55,6 +55,12 @@ int lpsim_mlp_train(lpsim_mlp *m, uint64_t n, const float *X, const float *t, ui
  * M % 128 == 0, K % 64 == 0, N == 64 or N % 256 == 0. */
 int lpsim_mlp_gemm_test(uint32_t M, uint32_t N, uint32_t K, const uint16_t *A, const uint16_t *B, float *D);
 
+/* Timing on the model's stream with CUDA events, on the batch buffers as they
+ * are (device-resident): mean milliseconds of one inference forward pass of
+ * `batch` rows (three tensor-core GEMMs with fused epilogues) and, if
+ * train_ms is not NULL, of one training forward + backward pass. */
+int lpsim_mlp_time(lpsim_mlp *m, uint32_t iters, double *fwd_ms, double *train_ms);
+
 void lpsim_mlp_destroy(lpsim_mlp *m);
 
 #ifdef __cplusplus

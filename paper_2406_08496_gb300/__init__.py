@@ -33,7 +33,7 @@ EXPORTED = ["lpsim_last_error", "lpsim_version", "lpsim_set_allocator", "lpsim_l
             "lpsim_load_network_batch", "lpsim_load_demand_batch", "lpsim_batch_offsets", "lpsim_snapshot",
             "lpsim_restore", "lpsim_autotune", "lpsim_set_config", "lpsim_destroy",
             "lpsim_mlp_create", "lpsim_mlp_set_params", "lpsim_mlp_get_params", "lpsim_mlp_forward",
-            "lpsim_mlp_grad", "lpsim_mlp_train", "lpsim_mlp_gemm_test", "lpsim_mlp_destroy",
+            "lpsim_mlp_grad", "lpsim_mlp_train", "lpsim_mlp_gemm_test", "lpsim_mlp_time", "lpsim_mlp_destroy",
             "lpsim_assign_create", "lpsim_assign_shortest_paths", "lpsim_assign_gap", "lpsim_assign_reroute",
             "lpsim_assign_route_length", "lpsim_assign_get_routes", "lpsim_assign_load", "lpsim_assign_features",
             "lpsim_assign_link_times", "lpsim_assign_times_from_ratio", "lpsim_assign_destroy"]
@@ -138,6 +138,7 @@ def load_library(path: str | None = None):
     lib.lpsim_mlp_grad.argtypes = [P, ctypes.c_uint64, P, P, P, P]
     lib.lpsim_mlp_train.argtypes = [P, ctypes.c_uint64, P, P, ctypes.c_uint32, ctypes.c_float, ctypes.c_uint64, P]
     lib.lpsim_mlp_gemm_test.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, P, P, P]
+    lib.lpsim_mlp_time.argtypes = [P, ctypes.c_uint32, P, P]
     lib.lpsim_mlp_destroy.argtypes = [P]
     lib.lpsim_mlp_destroy.restype = None
     _lib = lib
@@ -456,6 +457,12 @@ class Surrogate:
         losses = np.empty(steps, np.float32)
         _check(self.lib, self.lib.lpsim_mlp_train(self.h, len(X), _p(X), _p(t), steps, lr, seed, _p(losses)))
         return losses
+
+    def time(self, iters: int = 20) -> dict:
+        f = ctypes.c_double()
+        t = ctypes.c_double()
+        _check(self.lib, self.lib.lpsim_mlp_time(self.h, iters, ctypes.byref(f), ctypes.byref(t)))
+        return {"forward_ms": f.value, "train_ms": t.value}
 
     def close(self) -> None:
         if getattr(self, "h", None):

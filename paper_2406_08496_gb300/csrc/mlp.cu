@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(128, 1)
                     const size_t o = (size_t)row * g.N + col;
                     if (EPI == kEpiGelu || EPI == kEpiGeluHead) {
                         const float z = acc + g.bias[col];
-                        g.zout[o] = z;
+                        if (g.zout) g.zout[o] = z;
                         const __nv_bfloat16 h = __float2bfloat16_rn(gelu(z));
                         g.hout[o] = h;
                         if (g.htout) g.htout[(size_t)col * g.M + row] = h;
@@ -481,7 +481,9 @@ int refresh_weights(lpsim_mlp *m) {
 }
 
 // forward of rows [0, B) already packed in X0; keep = training buffers
-int forward_batch(lpsim_mlp *m) {
+// training keeps the pre-activations (for GELU') and transposed activations
+// (for the weight gradients); inference writes only the activations
+int forward_batch(lpsim_mlp *m, bool training = true) {
     cudaStream_t st = m->stream;
     for (int l = 0; l < 3; l++) {
         GemmArgs g{};
@@ -490,9 +492,9 @@ int forward_batch(lpsim_mlp *m) {
         g.K = kDims[l];
         g.ktiles_per_split = (g.K + kBK - 1) / kBK;
         g.bias = m->P[2 * l + 1];
-        g.zout = m->Z[l];
+        g.zout = training ? m->Z[l] : nullptr;
         g.hout = m->H[l];
-        g.htout = m->HT[l];
+        g.htout = training ? m->HT[l] : nullptr;
         g.err = m->err;
         const CUtensorMap &a = l == 0 ? m->mX0 : m->mH[l - 1];
         if (l < 2) {
@@ -688,7 +690,7 @@ int lpsim_mlp_forward(lpsim_mlp *m, uint64_t n, const float *X, float *y) {
     for (uint64_t r0 = 0; r0 < n; r0 += m->B) {
         const uint64_t nb = std::min<uint64_t>(m->B, n - r0);
         TRY(pack_batch(m, X + r0 * m->nf, nullptr, nb));
-        TRY(forward_batch(m));
+        TRY(forward_batch(m, false));
         CU(cudaMemcpyAsync(y + r0, m->y, nb * 4, cudaMemcpyDeviceToHost, m->stream));
     }
     CU(cudaStreamSynchronize(m->stream));
@@ -803,6 +805,37 @@ int lpsim_mlp_gemm_test(uint32_t M, uint32_t N, uint32_t K, const uint16_t *A, c
     cudaFree(dD);
     cudaFree(dE);
     return rc;
+}
+
+int lpsim_mlp_time(lpsim_mlp *m, uint32_t iters, double *fwd_ms, double *train_ms) {
+    if (!m || iters == 0) return fail(LPSIM_E_INVALID_ARG, "bad argument");
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    // whatever the batch buffers hold is a valid input; warm up once
+    TRY(forward_batch(m, false));
+    CU(cudaEventRecord(e0, m->stream));
+    for (uint32_t i = 0; i < iters; i++) TRY(forward_batch(m, false));
+    CU(cudaEventRecord(e1, m->stream));
+    CU(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    CU(cudaEventElapsedTime(&ms, e0, e1));
+    if (fwd_ms) *fwd_ms = ms / iters;
+    if (train_ms) {
+        CU(cudaMemsetAsync(m->loss_acc, 0, 4, m->stream));
+        CU(cudaEventRecord(e0, m->stream));
+        for (uint32_t i = 0; i < iters; i++) {
+            TRY(forward_batch(m, true));
+            TRY(backward_batch(m, m->B));
+        }
+        CU(cudaEventRecord(e1, m->stream));
+        CU(cudaEventSynchronize(e1));
+        CU(cudaEventElapsedTime(&ms, e0, e1));
+        *train_ms = ms / iters;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return mlp_check_err(m);
 }
 
 void lpsim_mlp_destroy(lpsim_mlp *m) { delete m; }
