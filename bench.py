@@ -53,6 +53,9 @@ def parse():
                     choices=["regional", "grid", "large", "batch64", "assignment", "surrogate"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--day-profile", type=int, default=0, metavar="STEPS",
+                    help="time the day in windows of STEPS steps (CUDA-synchronised wall time per window, vehicles "
+                         "on the network) and print one JSON line per window, then exit")
     ap.add_argument("--profile-window", type=int, default=0,
                     help="run to 08:00, then profile this many directly launched steps (for ncu) and exit")
     return ap.parse_args()
@@ -276,7 +279,9 @@ def surrogate_arm(args):
     t = s.time(max(args.steps, 10))
     mac_fwd = 64 * 256 + 256 * 256 * 2 + 256
     flop_fwd = 2.0 * rows * mac_fwd
-    flop_train = 3.0 * flop_fwd  # forward, input gradients and weight gradients
+    # training: the forward, the weight gradients (as many MACs as the forward)
+    # and the input gradients of layers 3 and 2 (layer 1 needs none)
+    flop_train = 2.0 * rows * (2 * mac_fwd + 2 * 256 * 256 + 256)
     fwd = flop_fwd / (t["forward_ms"] / 1e3) / 1e12
     trn = flop_train / (t["train_ms"] / 1e3) / 1e12
     peak = float(peaks["bf16_tflops"])
@@ -328,6 +333,25 @@ def main():
     sim = L.Simulation(net, params)
     sim.load_demand(dem)
 
+    if args.day_profile:
+        sim.step(3840)  # warm-up: graph capture and caches
+        torch.cuda.synchronize()
+        sim.reset()
+        dep = np.sort(dem["depart_step"])
+        while True:
+            c0 = sim.counters()
+            t0 = time.perf_counter()
+            sim.step(args.day_profile)
+            torch.cuda.synchronize()
+            ms = (time.perf_counter() - t0) * 1e3
+            c1 = sim.counters()
+            print(json.dumps({"k": c0["k"], "steps": args.day_profile, "ms": ms,
+                              "us_per_step": ms * 1e3 / args.day_profile, "active_start": c0["active"],
+                              "veh_steps_per_step": (c1["veh_steps"] - c0["veh_steps"]) / args.day_profile,
+                              "departures_due": int(np.searchsorted(dep, c0["k"] + args.day_profile)) - c0["arrived"]}),
+                  flush=True)
+            if c1["arrived"] >= len(dep):
+                return
     if args.profile_window:
         sim.step(8 * 7200)  # to 08:00
         torch.cuda.synchronize()

@@ -3,9 +3,9 @@
  * simulator (method of successive averages with time-dependent shortest
  * paths), and the feature builder of the link-travel-time surrogate.
  *
- * The paper's title is traffic assignment and propagation (the paper title);
- * its simulator takes routes as given "after the routing" (Sec. 3.1) and it
- * names dynamic rerouting as future work (Sec. 6).  None of these calls has
+ * The paper's title names traffic assignment and propagation; its simulator
+ * takes the routes as computed beforehand (Sec. 3.1) and it names dynamic
+ * rerouting as future work (Sec. 5, Conclusion).  None of these calls has
  * a formula in the paper: the relative gap is the textbook Wardrop gap
  *   RG = sum_trips (t_experienced - t_shortest) / sum_trips t_shortest,
  * t_experienced from planned departure to arrival in the simulation and

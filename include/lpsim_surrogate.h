@@ -7,8 +7,8 @@
  * (tcgen05.mma into tensor memory, operands staged by TMA).
  *
  * The paper has no surrogate: it is the learned extension of the traffic
- * assignment the paper's title names (the paper title; dynamic rerouting as
- * future work, Sec. 6).  The plain simulation stays the judge.
+ * assignment named in the paper's title (dynamic rerouting is its future
+ * work, Sec. 5, Conclusion).  The plain simulation still computes every relative gap.
  *
  * Conventions as in lpsim.h: int status codes, lpsim_last_error(), host
  * pointers for all inputs and outputs, the model owns its device memory.

@@ -3,7 +3,7 @@
 //
 // The paper's title is traffic *assignment* and propagation; its simulator
 // propagates trips along routes fixed "after the routing" (Sec. 3.1) and it
-// names dynamic rerouting as future work (Sec. 6).  This engine closes the
+// names dynamic rerouting as future work (Sec. 5, Conclusion).  This engine closes the
 // loop: link travel times per 15-minute entry bin come from a simulation
 // (or from the surrogate), time-dependent shortest paths are computed under
 // them (label-setting Dijkstra on earliest arrival, FIFO bin lookup of the

@@ -110,6 +110,17 @@ struct __align__(16) CrossRec {
     uint8_t lane, tln;                // lane asked for, target lane on the next edge
 };
 
+// What step_p2 needs of a departure request (packed by step_p1 for the queue
+// head of an origin edge that asked to enter).
+struct __align__(16) DepRec {
+    uint32_t j, slot, h, r0;          // origin, claim slot, vehicle, route start
+    uint32_t r1, qoff, qhead, qend;   // route end; the origin's queue records and head position
+    uint32_t base, e0, nen, nsg;      // lane row asked for, origin edge, the edge after it, its signal's green
+    float v0;                         // speed limit of the origin edge
+    uint16_t len, nsph;               // origin edge length, signal phases | phase << 8
+    uint8_t lane, tlc;                // lane asked for, target lane for the movement after the origin edge
+};
+
 // What step_p3 needs of a lane-change intender (packed by step_p1).
 struct __align__(16) IntendRec {
     uint32_t s, base;                 // slot, current lane row
@@ -142,11 +153,7 @@ struct Dev {
     const QRec *qrec;
     uint32_t *org_head;        // position of the head in its queue
     QRec *org_hd;              // head record (h = kNone: queue empty)
-    uint8_t *dreq;             // requested lane this step (kEmpty = none)
-    uint32_t *dslot, *dprev;   // claim slot asked for this step / won at the previous step
-    uint32_t *den, *dsg;       // stash of the request: next edge, signal
-    uint16_t *dsph;
-    uint8_t *dtlc;
+    uint32_t *dprev;           // claim slot won at the previous step (kNone)
     // slots (current set: the host alternates two sets around each compaction)
     Slots s;
     uint32_t cap;              // slot capacity
@@ -154,7 +161,7 @@ struct Dev {
     CrossRec *cross_list[2];
     IntendRec *intend_list[2];
     uint32_t *counts;          // [0..1] cross count by parity, [2..3] intend count, [4..5] departure requests
-    uint32_t *dep_list[2];     // origin edges that asked for a departure, by parity
+    DepRec *dep_rec[2];        // departure requests, by parity
     // statistics; binned arrays are bin-major ([bin][edge]) so the updates of
     // one step fall in one or two rows that stay in L2
     unsigned long long *ent, *ext, *tts;
@@ -170,8 +177,12 @@ struct Dev {
     Model m;
 };
 
-// kernels of a step; koff = offset of this step inside the chunk
-void launch_phase(const Dev &d, int phase, uint32_t koff, int grid, int block, cudaStream_t st);
+// kernels of a step; koff = offset of this step inside the chunk (step k =
+// *kbase + koff); kph = any number congruent to k modulo 6, known when the
+// launch is recorded (koff inside a graph chunk, whose first step is a
+// multiple of 6; k itself for a direct launch), so the kernels pick the
+// parity buffers and the rotating lane maps without waiting for *kbase
+void launch_phase(const Dev &d, int phase, uint32_t koff, uint32_t kph, int grid, int block, cudaStream_t st);
 void launch_chunk_end(const Dev &d, uint32_t steps, cudaStream_t st);
 
 // compaction (and optional sort by lane-map cell) of the slots after step k;

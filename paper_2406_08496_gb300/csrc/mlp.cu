@@ -12,9 +12,10 @@
 // 64-element slices.  One thread issues TMA loads (128-byte swizzle) of the
 // A and B slices into a 4-stage shared-memory ring guarded by mbarriers,
 // one thread issues tcgen05.mma (M = 128, N = BN, K = 16 per instruction)
-// accumulating in tensor memory, and the four warps read the accumulator
-// back with tcgen05.ld for a fused epilogue (bias, GELU, GELU', the output
-// head, transposed copies for the weight gradients, or FP32 atomics).
+// accumulating in tensor memory, and all eight warps read the accumulator
+// back with tcgen05.ld for a fused epilogue (bias, GELU and its derivative,
+// the output head, transposed copies for the weight gradients, bias-gradient
+// column sums, or FP32 atomics).
 // Every wait on an mbarrier is bounded; on timeout the kernel records an
 // error, stops issuing work and frees its tensor memory before returning.
 #include <cuda.h>
@@ -53,21 +54,25 @@ constexpr int kStages = 4;
 constexpr uint32_t kSpinLimit = 1u << 26;
 
 enum Epi : int {
-    kEpiGelu = 0,      // Z = acc + b -> keep Z (f32), H = GELU(Z) (bf16, row-major and transposed)
+    kEpiGelu = 0,      // Z = acc + b -> H = GELU(Z) (bf16, row-major and transposed), GELU'(Z) (f32) for training
     kEpiGeluHead = 1,  // as kEpiGelu, plus y = H . w4 + b4 (f32)
-    kEpiDgelu = 2,     // dZ = acc * GELU'(Zprev) -> bf16 row-major and transposed
+    kEpiDgelu = 2,     // dZ = acc * GELU'(Z_prev) -> bf16 row-major and transposed, per-tile column sums
     kEpiAtomic = 3,    // out (f32) += acc
     kEpiStore = 4,     // out (f32) = acc
 };
 
+constexpr int kThreads = 256;  // eight warps: all take part in the epilogue
+
 struct GemmArgs {
     int M, N, K;
     int ktiles_per_split;
+    int stages;            // depth of the operand ring (1..kStages)
     const float *bias;     // N
-    float *zout;           // M x N (kEpiGelu*)
+    float *gout;           // M x N: GELU'(Z) (kEpiGelu*, nullable)
     __nv_bfloat16 *hout;   // M x N
     __nv_bfloat16 *htout;  // N x M (nullable)
-    const float *zprev;    // M x N (kEpiDgelu)
+    const float *gprev;    // M x N: GELU'(Z_prev) (kEpiDgelu)
+    float *colpart;        // (M / 128) x N: per-row-tile column sums of the output (kEpiDgelu, nullable)
     const float *w4;       // N (kEpiGeluHead)
     const float *b4;       // 1 (kEpiGeluHead)
     float *yout;           // M (kEpiGeluHead)
@@ -152,28 +157,87 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
 
-__device__ __forceinline__ float gelu_grad(float x) {
-    return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
+// Writers of a staged 32 x 32 slice (row pitch 33 floats, so that a warp's
+// accesses fall in 32 different banks).  Row r of the slice is output row
+// rw0 + r, column j is output column col0 + j; rows at or past M are skipped.
+
+// f32 rows, four columns per thread: a warp instruction writes 4 whole rows
+__device__ __forceinline__ void store_rows_f32(const float *stage, float *out, int N, int M, int rw0, int col0,
+                                               int lane) {
+#pragma unroll
+    for (int it = 0; it < 8; it++) {
+        const int r = it * 4 + (lane >> 3), q = (lane & 7) * 4;
+        if (rw0 + r >= M) continue;
+        const float *sp = stage + r * 33 + q;
+        *reinterpret_cast<float4 *>(out + (size_t)(rw0 + r) * N + col0 + q) = make_float4(sp[0], sp[1], sp[2], sp[3]);
+    }
+}
+
+// f32 accumulation into rows (split-K partial sums)
+__device__ __forceinline__ void add_rows_f32(const float *stage, float *out, int N, int M, int rw0, int col0,
+                                             int lane) {
+#pragma unroll 4
+    for (int r = 0; r < 32; r++) {
+        if (rw0 + r >= M) break;
+        atomicAdd(out + (size_t)(rw0 + r) * N + col0 + lane, stage[r * 33 + lane]);
+    }
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&p);
+}
+
+// bf16 rows (the staged values are already bf16-representable), eight
+// columns per thread: a warp instruction writes 8 whole 64-byte row pieces
+__device__ __forceinline__ void store_rows_bf16(const float *stage, __nv_bfloat16 *out, int N, int M, int rw0,
+                                                int col0, int lane) {
+#pragma unroll
+    for (int it = 0; it < 4; it++) {
+        const int r = it * 8 + (lane >> 2), q = (lane & 3) * 8;
+        if (rw0 + r >= M) continue;
+        const float *sp = stage + r * 33 + q;
+        const uint4 v = make_uint4(pack_bf16x2(sp[0], sp[1]), pack_bf16x2(sp[2], sp[3]), pack_bf16x2(sp[4], sp[5]),
+                                   pack_bf16x2(sp[6], sp[7]));
+        *reinterpret_cast<uint4 *>(out + (size_t)(rw0 + r) * N + col0 + q) = v;
+    }
+}
+
+// bf16 transposed copy (out is N x M): eight rows of one column per thread
+__device__ __forceinline__ void store_cols_bf16(const float *stage, __nv_bfloat16 *outT, int M, int rw0, int col0,
+                                                int lane) {
+#pragma unroll
+    for (int it = 0; it < 4; it++) {
+        const int j = it * 8 + (lane >> 2), r0 = (lane & 3) * 8;
+        if (rw0 + r0 >= M) continue;
+        const float *sp = stage + r0 * 33 + j;
+        const uint4 v = make_uint4(pack_bf16x2(sp[0], sp[33]), pack_bf16x2(sp[66], sp[99]),
+                                   pack_bf16x2(sp[132], sp[165]), pack_bf16x2(sp[198], sp[231]));
+        *reinterpret_cast<uint4 *>(outT + (size_t)(col0 + j) * M + rw0 + r0) = v;
+    }
 }
 
 // ------------------------------------------------------------- GEMM kernel
 
 template <int BN, int EPI>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(kThreads, 2)
     gemm_bf16_tn(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, GemmArgs g) {
     constexpr uint32_t kABytes = kBM * kBK * 2;
     constexpr uint32_t kBBytes = BN * kBK * 2;
+    constexpr bool kGelu = EPI == kEpiGelu || EPI == kEpiGeluHead;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *sA = smem;
-    uint8_t *sB = smem + kStages * kABytes;
-    uint64_t *full = reinterpret_cast<uint64_t *>(sB + kStages * kBBytes);
-    uint64_t *empty = full + kStages;
-    uint64_t *done = empty + kStages;
+    const int ns = g.stages;
+    uint8_t *sB = smem + ns * kABytes;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sB + ns * kBBytes);
+    uint64_t *empty = full + ns;
+    uint64_t *done = empty + ns;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
     __shared__ int s_fail;
+    __shared__ float s_head[2][kBM];  // output-head partial sums of the two column halves
+    __shared__ float s_col[4][BN];    // column sums of the four 32-row quarters
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
@@ -184,7 +248,7 @@ __global__ void __launch_bounds__(128, 1)
 
     if (threadIdx.x == 0) {
         s_fail = 0;
-        for (int s = 0; s < kStages; s++) {
+        for (int s = 0; s < ns; s++) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
@@ -201,12 +265,13 @@ __global__ void __launch_bounds__(128, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
+    bool ok = false;
     if (nk > 0) {
         if (warp == 0 && lane == 0) {
             // TMA producer
             for (int i = 0; i < nk; i++) {
-                const int s = i % kStages;
-                if (i >= kStages && !mbar_wait(&empty[s], ((i / kStages) - 1) & 1)) {
+                const int s = i % ns;
+                if (i >= ns && !mbar_wait(&empty[s], ((i / ns) - 1) & 1)) {
                     atomicOr(g.err, 1u);
                     s_fail = 1;
                     break;
@@ -219,10 +284,9 @@ __global__ void __launch_bounds__(128, 1)
         } else if (warp == 1 && lane == 0) {
             // MMA issuer
             const uint32_t idesc = umma_idesc(BN);
-            int issued = 0;
             for (int i = 0; i < nk; i++) {
-                const int s = i % kStages;
-                if (!mbar_wait(&full[s], (i / kStages) & 1)) {
+                const int s = i % ns;
+                if (!mbar_wait(&full[s], (i / ns) & 1)) {
                     atomicOr(g.err, 2u);
                     s_fail = 1;
                     break;
@@ -233,120 +297,205 @@ __global__ void __launch_bounds__(128, 1)
                 for (int kk = 0; kk < kBK / 16; kk++)
                     umma_f16(tmem, umma_desc(a0 + kk * 32), umma_desc(b0 + kk * 32), idesc, (i | kk) != 0);
                 umma_commit(&empty[s]);
-                issued++;
             }
             umma_commit(done);
-            (void)issued;
         }
         __syncwarp();
-        // epilogue: all four warps; warp w owns accumulator lanes 32w..32w+31
-        const bool ok = mbar_wait(done, 0);
+        // Epilogue, all eight warps.  A warp may only read the tensor-memory
+        // lanes of its quarter (warp % 4), i.e. accumulator rows
+        // m0 + 32 (warp % 4) .. + 31, one row per thread; warps 0-3 take the
+        // first half of the columns and warps 4-7 the second.  Every 32-column
+        // slice is staged through shared memory (the operand ring is idle once
+        // the last MMA has completed) so that the global reads and writes are
+        // whole rows (or whole transposed columns) per warp instruction.
+        ok = mbar_wait(done, 0);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (!ok) atomicOr(g.err, 4u);
-        const int row = m0 + warp * 32 + lane;
+        const int q = warp & 3, ch = warp >> 2;
+        float *stZ = reinterpret_cast<float *>(smem) + warp * (2 * 32 * 33);  // 32 x 32 slices, row pitch 33
+        float *stH = stZ + 32 * 33;
+        const int rw0 = m0 + q * 32;
         float head = 0.0f;
         if (ok && !s_fail) {
 #pragma unroll 1
-            for (int c0 = 0; c0 < BN; c0 += 32) {
-                uint32_t r[32];
-                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-                if (row >= g.M) continue;
+            for (int cc = 0; cc < BN / 2; cc += 32) {
+                const int c0 = ch * (BN / 2) + cc;
+                const int col0 = n0 + c0;
+                if (EPI == kEpiDgelu) {
+                    // GELU'(Z_prev) slice, read row by row
 #pragma unroll
-                for (int j = 0; j < 32; j++) {
-                    const int col = n0 + c0 + j;
-                    const float acc = __uint_as_float(r[j]);
-                    const size_t o = (size_t)row * g.N + col;
-                    if (EPI == kEpiGelu || EPI == kEpiGeluHead) {
-                        const float z = acc + g.bias[col];
-                        if (g.zout) g.zout[o] = z;
-                        const __nv_bfloat16 h = __float2bfloat16_rn(gelu(z));
-                        g.hout[o] = h;
-                        if (g.htout) g.htout[(size_t)col * g.M + row] = h;
-                        if (EPI == kEpiGeluHead) head += __bfloat162float(h) * g.w4[col];
-                    } else if (EPI == kEpiDgelu) {
-                        const __nv_bfloat16 dz = __float2bfloat16_rn(acc * gelu_grad(g.zprev[o]));
-                        g.hout[o] = dz;
-                        if (g.htout) g.htout[(size_t)col * g.M + row] = dz;
-                    } else if (EPI == kEpiAtomic) {
-                        atomicAdd(&g.fout[o], acc);
-                    } else {
-                        g.fout[o] = acc;
+                    for (int it = 0; it < 8; it++) {
+                        const int r = it * 4 + (lane >> 3), qq = (lane & 7) * 4;
+                        float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (rw0 + r < g.M)
+                            z4 = *reinterpret_cast<const float4 *>(g.gprev + (size_t)(rw0 + r) * g.N + col0 + qq);
+                        float *sp = stZ + r * 33 + qq;
+                        sp[0] = z4.x;
+                        sp[1] = z4.y;
+                        sp[2] = z4.z;
+                        sp[3] = z4.w;
                     }
+                    __syncwarp();
                 }
+                uint32_t r[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
+                float *mz = stZ + lane * 33, *mh = stH + lane * 33;
+                if (kGelu) {
+#pragma unroll
+                    for (int j = 0; j < 32; j++) {
+                        const float z = __uint_as_float(r[j]) + g.bias[col0 + j];
+                        const float e = erff(z * 0.70710678118654752f);
+                        const float h = __bfloat162float(__float2bfloat16_rn(0.5f * z * (1.0f + e)));
+                        mh[j] = h;
+                        if (g.gout) mz[j] = 0.5f * (1.0f + e) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+                        if (EPI == kEpiGeluHead) head += h * g.w4[col0 + j];
+                    }
+                } else if (EPI == kEpiDgelu) {
+#pragma unroll
+                    for (int j = 0; j < 32; j++)
+                        mh[j] = __bfloat162float(__float2bfloat16_rn(__uint_as_float(r[j]) * mz[j]));
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; j++) mh[j] = __uint_as_float(r[j]);
+                }
+                __syncwarp();
+                if (kGelu && g.gout) store_rows_f32(stZ, g.gout, g.N, g.M, rw0, col0, lane);
+                if (kGelu || EPI == kEpiDgelu) {
+                    store_rows_bf16(stH, g.hout, g.N, g.M, rw0, col0, lane);
+                    if (g.htout) store_cols_bf16(stH, g.htout, g.M, rw0, col0, lane);
+                } else if (EPI == kEpiAtomic) {
+                    add_rows_f32(stH, g.fout, g.N, g.M, rw0, col0, lane);
+                } else {
+                    store_rows_f32(stH, g.fout, g.N, g.M, rw0, col0, lane);
+                }
+                if (EPI == kEpiDgelu && g.colpart) {
+                    float cs = 0.0f;
+                    for (int rr = 0; rr < 32; rr++)
+                        if (rw0 + rr < g.M) cs += stH[rr * 33 + lane];
+                    s_col[q][c0 + lane] = cs;
+                }
+                __syncwarp();
             }
-            if (EPI == kEpiGeluHead && row < g.M) g.yout[row] = head + *g.b4;
         }
+        if (EPI == kEpiGeluHead) s_head[ch][q * 32 + lane] = head;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN < 32 ? 32 : BN));
+    if (nk > 0 && ok && !s_fail) {
+        if (EPI == kEpiGeluHead && threadIdx.x < kBM && m0 + (int)threadIdx.x < g.M)
+            g.yout[m0 + threadIdx.x] = (s_head[0][threadIdx.x] + s_head[1][threadIdx.x]) + *g.b4;
+        if (EPI == kEpiDgelu && g.colpart && threadIdx.x < BN)
+            g.colpart[(size_t)blockIdx.x * g.N + n0 + threadIdx.x] =
+                ((s_col[0][threadIdx.x] + s_col[1][threadIdx.x]) + s_col[2][threadIdx.x]) + s_col[3][threadIdx.x];
+    }
 }
 
 // ---------------------------------------------------------- small kernels
 
-// X (n x nf f32, host layout) -> Xb (n_pad x 64 bf16, zero padded) and its transpose
+// X (n x nf f32, host layout) -> Xb (n_pad x 64 bf16, zero padded) and its
+// transpose.  Block (32, 8) handles a 32-row x 32-column tile; the transposed
+// copy goes through shared memory so both writes are whole rows.
 __global__ void pack_inputs(const float *X, int n, int nf, int n_pad, __nv_bfloat16 *Xb, __nv_bfloat16 *XbT) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_pad * 64; i += gridDim.x * blockDim.x) {
-        const int r = i / 64, c = i % 64;
+    __shared__ __nv_bfloat16 tile[32][34];
+    const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32, tx = threadIdx.x, ty = threadIdx.y;
+    for (int rr = ty; rr < 32; rr += 8) {
+        const int r = r0 + rr, c = c0 + tx;
         const float v = (r < n && c < nf) ? X[(size_t)r * nf + c] : 0.0f;
         const __nv_bfloat16 b = __float2bfloat16_rn(v);
-        Xb[i] = b;
-        if (XbT) XbT[(size_t)c * n_pad + r] = b;
+        Xb[(size_t)r * 64 + c] = b;
+        tile[rr][tx] = b;
     }
+    if (!XbT) return;
+    __syncthreads();
+    for (int cc = ty; cc < 32; cc += 8) XbT[(size_t)(c0 + cc) * n_pad + r0 + tx] = tile[tx][cc];
 }
 
 // dy = 2/n (y - t) on real rows; dZ3 = dy * w4 * GELU'(Z3) (bf16, row-major and
-// transposed); per-row dy kept for dW4 / db4; loss partial sums
-__global__ void head_backward(const float *y, const float *t, int n, int n_pad, const float *w4, const float *Z3,
+// transposed; GELU'(Z3) was stored by the forward pass); per-row dy kept for
+// dW4 / db4; the squared errors summed into loss_acc.  Tiles of 32 rows x 32
+// columns as in pack_inputs.
+__global__ void head_backward(const float *y, const float *t, int n, int n_pad, const float *w4, const float *G3,
                               __nv_bfloat16 *dZ3, __nv_bfloat16 *dZ3T, float *dy, float *loss_acc) {
+    __shared__ __nv_bfloat16 tile[32][34];
     const float scale = 2.0f / (float)n;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_pad * 256; i += gridDim.x * blockDim.x) {
-        const int r = i / 256, c = i % 256;
-        float d = 0.0f;
-        if (r < n) d = scale * (y[r] - t[r]);
-        if (c == 0) {
-            dy[r] = d;
-            if (r < n) atomicAdd(loss_acc, (y[r] - t[r]) * (y[r] - t[r]));
-        }
-        const __nv_bfloat16 b = __float2bfloat16_rn(d * w4[c] * gelu_grad(Z3[i]));
-        dZ3[i] = b;
-        dZ3T[(size_t)c * n_pad + r] = b;
+    const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32, tx = threadIdx.x, ty = threadIdx.y;
+    for (int rr = ty; rr < 32; rr += 8) {
+        const int r = r0 + rr, c = c0 + tx;
+        const float d = r < n ? scale * (y[r] - t[r]) : 0.0f;
+        const __nv_bfloat16 b = __float2bfloat16_rn(d * w4[c] * G3[(size_t)r * 256 + c]);
+        dZ3[(size_t)r * 256 + c] = b;
+        tile[rr][tx] = b;
     }
-}
-
-// dW4[c] = sum_r dy[r] H3[r][c]; db4 = sum_r dy[r]; bias gradients = column sums of dZ
-__global__ void column_sums(const __nv_bfloat16 *A, int rows, int cols, const float *rowscale, float *out) {
-    // one block per column chunk of 32, threads stride over rows
-    const int c = blockIdx.x * 32 + (threadIdx.x & 31);
-    const int r0 = threadIdx.x >> 5, rstep = blockDim.x >> 5;
-    float acc = 0.0f;
-    if (c < cols)
-        for (int r = r0; r < rows; r += rstep) {
-            const float a = __bfloat162float(A[(size_t)r * cols + c]);
-            acc += rowscale ? a * rowscale[r] : a;
-        }
-    __shared__ float red[32][33];
-    red[r0][threadIdx.x & 31] = acc;
+    if (blockIdx.y == 0 && ty == 0) {
+        // one warp per 32 rows: dy and the loss
+        const int r = r0 + tx;
+        const float e = r < n ? y[r] - t[r] : 0.0f;
+        dy[r] = r < n ? scale * e : 0.0f;
+        float sq = e * e;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xFFFFFFFFu, sq, o);
+        if (tx == 0 && sq != 0.0f) atomicAdd(loss_acc, sq);
+    }
     __syncthreads();
-    if (threadIdx.x < 32) {
-        float s = 0.0f;
-        for (int q = 0; q < rstep; q++) s += red[q][threadIdx.x];
-        if (blockIdx.x * 32 + threadIdx.x < cols) out[blockIdx.x * 32 + threadIdx.x] = s;
+    for (int cc = ty; cc < 32; cc += 8) dZ3T[(size_t)(c0 + cc) * n_pad + r0 + tx] = tile[tx][cc];
+}
+
+// Column sums of A (rows x cols bf16), optionally weighted by rowscale[r]:
+// the bias gradients (column sums of dZ) and dW4 (dy-weighted sums of H3).
+// Stage 1: block (32, 8) sums a band of rows for 32 columns into part[band][c];
+// stage 2 adds the bands in order.
+constexpr int kSumBands = 256;
+
+__global__ void column_partials(const __nv_bfloat16 *A, int rows, int cols, const float *rowscale, float *part) {
+    __shared__ float red[8][33];
+    const int c = blockIdx.x * 32 + threadIdx.x;
+    const int band = (rows + kSumBands - 1) / kSumBands;
+    const int rb = blockIdx.y * band, re = min(rows, rb + band);
+    float acc = 0.0f;
+    for (int r = rb + threadIdx.y; r < re; r += 8) {
+        const float a = __bfloat162float(A[(size_t)r * cols + c]);
+        acc += rowscale ? a * rowscale[r] : a;
+    }
+    red[threadIdx.y][threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.y == 0) {
+        float s2 = 0.0f;
+        for (int q = 0; q < 8; q++) s2 += red[q][threadIdx.x];
+        part[(size_t)blockIdx.y * cols + c] = s2;
     }
 }
 
-__global__ void sum_vector(const float *v, int n, float *out) {
+// out[c] = sum over bands b of part[b][c], in a fixed order (a block per column)
+__global__ void reduce_bands(const float *part, int n_bands, int cols, float *out) {
+    __shared__ float red[256];
+    const int c = blockIdx.x;
     float acc = 0.0f;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += v[i];
-    __shared__ float red[1024];
+    for (int b = threadIdx.x; b < n_bands; b += 256) acc += part[(size_t)b * cols + c];
     red[threadIdx.x] = acc;
     __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) *out = red[0];
+    if (threadIdx.x == 0) out[c] = red[0];
+}
+
+// part[b] = sum of v over band b of kSumBands equal bands
+__global__ void vector_partials(const float *v, int n, float *part) {
+    __shared__ float red[256];
+    const int band = (n + kSumBands - 1) / kSumBands;
+    const int rb = blockIdx.x * band, re = min(n, rb + band);
+    float acc = 0.0f;
+    for (int i = rb + threadIdx.x; i < re; i += 256) acc += v[i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
 // Adam (Kingma and Ba 2015, Algorithm 1) on f32 master weights
@@ -408,16 +557,24 @@ int make_map(CUtensorMap *map, const void *ptr, uint64_t rows, uint64_t cols, ui
 }
 
 template <int BN, int EPI>
-int launch_gemm(const CUtensorMap &a, const CUtensorMap &b, const GemmArgs &g, int splits, cudaStream_t st) {
-    const size_t smem = 1024 + kStages * (size_t)(kBM * kBK * 2 + BN * kBK * 2) + (2 * kStages + 1) * 8 + 16;
+int launch_gemm(const CUtensorMap &a, const CUtensorMap &b, const GemmArgs &g_in, int splits, cudaStream_t st) {
+    // short K (the layer GEMMs, at most 4 slices): a 2-deep ring, so two CTAs
+    // share an SM and one's epilogue overlaps the other's loads; long K (the
+    // split weight-gradient GEMMs): the full ring
+    GemmArgs g = g_in;
+    g.stages = (BN == 256 && g.ktiles_per_split <= 4) ? 2 : kStages;
+    const size_t max_smem = 1024 + kStages * (size_t)(kBM * kBK * 2 + BN * kBK * 2) + (2 * kStages + 1) * 8 + 16;
+    const size_t smem = 1024 + g.stages * (size_t)(kBM * kBK * 2 + BN * kBK * 2) + (2 * g.stages + 1) * 8 + 16;
+    if ((size_t)g.stages * (kBM * kBK * 2 + BN * kBK * 2) < (size_t)kThreads / 32 * 2 * 32 * 33 * 4)
+        return fail(LPSIM_E_STATE, "GEMM epilogue staging does not fit in the operand ring");
     static bool attr_set = false;
     if (!attr_set) {
-        CU(cudaFuncSetAttribute(gemm_bf16_tn<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        CU(cudaFuncSetAttribute(gemm_bf16_tn<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem));
         attr_set = true;
     }
     if (g.M % kBM != 0 || g.N % BN != 0) return fail(LPSIM_E_INVALID_ARG, "GEMM shape not a multiple of the tile");
     dim3 grid(g.M / kBM, g.N / BN, splits);
-    gemm_bf16_tn<BN, EPI><<<grid, 128, smem, st>>>(a, b, g);
+    gemm_bf16_tn<BN, EPI><<<grid, kThreads, smem, st>>>(a, b, g);
     CU(cudaGetLastError());
     return LPSIM_OK;
 }
@@ -440,7 +597,8 @@ struct lpsim_mlp {
     __nv_bfloat16 *Wb[3] = {}, *WbT[3] = {};
     // activations for one batch
     __nv_bfloat16 *X0, *X0T, *H[3], *HT[3], *dZ[3], *dZT[3];
-    float *Z[3], *y, *t, *dy, *Xf, *loss_acc;
+    float *Gp[3];  // GELU'(Z_l) of the last training forward (f32)
+    float *y, *t, *dy, *Xf, *loss_acc, *colpart;
     uint32_t *err;
     CUtensorMap mX0, mW[3], mH[3], mWT[3], mdZ[3], mdZT[3], mHT[3], mX0T;
     int adam_t = 0;
@@ -462,6 +620,14 @@ struct lpsim_mlp {
 namespace {
 
 const int kDims[5] = {64, 256, 256, 256, 1};
+
+int column_sums(const __nv_bfloat16 *A, int rows, int cols, const float *rowscale, float *out, float *part,
+                cudaStream_t st) {
+    column_partials<<<dim3(cols / 32, kSumBands), dim3(32, 8), 0, st>>>(A, rows, cols, rowscale, part);
+    reduce_bands<<<cols, 256, 0, st>>>(part, kSumBands, cols, out);
+    CU(cudaGetLastError());
+    return LPSIM_OK;
+}
 
 int mlp_check_err(lpsim_mlp *m) {
     uint32_t e = 0;
@@ -492,7 +658,7 @@ int forward_batch(lpsim_mlp *m, bool training = true) {
         g.K = kDims[l];
         g.ktiles_per_split = (g.K + kBK - 1) / kBK;
         g.bias = m->P[2 * l + 1];
-        g.zout = training ? m->Z[l] : nullptr;
+        g.gout = training ? m->Gp[l] : nullptr;
         g.hout = m->H[l];
         g.htout = training ? m->HT[l] : nullptr;
         g.err = m->err;
@@ -515,12 +681,13 @@ int backward_batch(lpsim_mlp *m, int n_real) {
     cudaStream_t st = m->stream;
     const int B = m->B;
     for (int i = 0; i < 8; i++) CU(cudaMemsetAsync(m->G[i], 0, m->sz[i] * 4, st));
-    head_backward<<<1024, 256, 0, st>>>(m->y, m->t, n_real, B, m->P[6], m->Z[2], m->dZ[2], m->dZT[2], m->dy,
-                                       m->loss_acc);
+    head_backward<<<dim3(B / 32, 256 / 32), dim3(32, 8), 0, st>>>(m->y, m->t, n_real, B, m->P[6], m->Gp[2], m->dZ[2],
+                                                                 m->dZT[2], m->dy, m->loss_acc);
     // dW4 = sum_r dy[r] H3[r][:], db4 = sum dy
-    column_sums<<<256 / 32, 1024, 0, st>>>(m->H[2], B, 256, m->dy, m->G[6]);
-    sum_vector<<<1, 1024, 0, st>>>(m->dy, B, m->G[7]);
-    m->launches += 3;
+    TRY(column_sums(m->H[2], B, 256, m->dy, m->G[6], m->colpart, st));
+    vector_partials<<<kSumBands, 256, 0, st>>>(m->dy, B, m->colpart);
+    reduce_bands<<<1, 256, 0, st>>>(m->colpart, kSumBands, 1, m->G[7]);
+    m->launches += 5;
     for (int l = 2; l >= 0; l--) {
         // dW_l = dZ_l^T . H_{l-1}   (A = dZ_l^T [256 x B], B = H_{l-1}^T [in x B])
         GemmArgs g{};
@@ -538,9 +705,12 @@ int backward_batch(lpsim_mlp *m, int n_real) {
         } else {
             TRY((launch_gemm<64, kEpiAtomic>(m->mdZT[l], bT, g, splits, st)));
         }
-        // db_l = column sums of dZ_l
-        column_sums<<<256 / 32, 1024, 0, st>>>(m->dZ[l], B, 256, nullptr, m->G[2 * l + 1]);
-        m->launches += 2;
+        if (l == 2) {
+            // db3 = column sums of dZ3 (db2, db1 come from the GELU' epilogues below)
+            TRY(column_sums(m->dZ[l], B, 256, nullptr, m->G[2 * l + 1], m->colpart, st));
+            m->launches += 2;
+        }
+        m->launches += 1;
         if (l > 0) {
             // dZ_{l-1} = (dZ_l . W_l) * GELU'(Z_{l-1})   (B operand = W_l^T [in x out])
             GemmArgs h{};
@@ -548,12 +718,15 @@ int backward_batch(lpsim_mlp *m, int n_real) {
             h.N = 256;
             h.K = 256;
             h.ktiles_per_split = 4;
-            h.zprev = m->Z[l - 1];
+            h.gprev = m->Gp[l - 1];
+            h.colpart = m->colpart;
             h.hout = m->dZ[l - 1];
             h.htout = m->dZT[l - 1];
             h.err = m->err;
             TRY((launch_gemm<256, kEpiDgelu>(m->mdZ[l], m->mWT[l], h, 1, st)));
-            m->launches++;
+            // db_{l-1} = column sums of dZ_{l-1}: the per-row-tile sums of the epilogue, added in order
+            reduce_bands<<<256, 256, 0, st>>>(m->colpart, B / kBM, 256, m->G[2 * (l - 1) + 1]);
+            m->launches += 2;
         }
     }
     CU(cudaGetLastError());
@@ -567,7 +740,7 @@ int pack_batch(lpsim_mlp *m, const float *X_host, const float *t_host, uint64_t 
         CU(cudaMemsetAsync(m->t, 0, m->B * 4, st));
         CU(cudaMemcpyAsync(m->t, t_host, n * 4, cudaMemcpyHostToDevice, st));
     }
-    pack_inputs<<<1024, 256, 0, st>>>(m->Xf, (int)n, m->nf, m->B, m->X0, m->X0T);
+    pack_inputs<<<dim3(m->B / 32, 2), dim3(32, 8), 0, st>>>(m->Xf, (int)n, m->nf, m->B, m->X0, m->X0T);
     m->launches++;
     CU(cudaGetLastError());
     return LPSIM_OK;
@@ -617,7 +790,7 @@ int lpsim_mlp_create(lpsim_mlp **out, uint32_t n_features, uint32_t batch, uint6
         m->HT[l] = (__nv_bfloat16 *)m->alloc((size_t)B * 256 * 2);
         m->dZ[l] = (__nv_bfloat16 *)m->alloc((size_t)B * 256 * 2);
         m->dZT[l] = (__nv_bfloat16 *)m->alloc((size_t)B * 256 * 2);
-        m->Z[l] = (float *)m->alloc((size_t)B * 256 * 4);
+        m->Gp[l] = (float *)m->alloc((size_t)B * 256 * 4);
     }
     m->X0 = (__nv_bfloat16 *)m->alloc((size_t)B * 64 * 2);
     m->X0T = (__nv_bfloat16 *)m->alloc((size_t)B * 64 * 2);
@@ -626,6 +799,7 @@ int lpsim_mlp_create(lpsim_mlp **out, uint32_t n_features, uint32_t batch, uint6
     m->t = (float *)m->alloc((size_t)B * 4);
     m->dy = (float *)m->alloc((size_t)B * 4);
     m->loss_acc = (float *)m->alloc(16);
+    m->colpart = (float *)m->alloc((size_t)std::max(kSumBands, B / kBM) * 256 * 4);
     m->err = (uint32_t *)m->alloc(16);
     if (!m->err || !m->X0 || !m->Xf) return bail(fail(LPSIM_E_OOM, "device allocation failed"));
     if (cudaMemsetAsync(m->err, 0, 16, m->stream) != cudaSuccess) return bail(fail(LPSIM_E_CUDA, "memset"));

@@ -171,7 +171,7 @@ int read_status(lpsim_ctx *c) {
 // The kernels of step `koff` of a chunk (or of a direct step, koff = 0),
 // with timing events around each phase when timing is on.  Returns the slot
 // set current after the step.
-int enqueue_step(lpsim_ctx *c, uint32_t koff, int cur, bool compact) {
+int enqueue_step(lpsim_ctx *c, uint32_t koff, uint32_t kph, int cur, bool compact) {
     Dev d = c->d;
     d.s = c->sets[cur];
     cudaEvent_t *e = c->timing ? &c->ev[5 * koff] : nullptr;
@@ -179,7 +179,7 @@ int enqueue_step(lpsim_ctx *c, uint32_t koff, int cur, bool compact) {
     // event-record node that timestamps when the graph runs
     for (int ph = 1; ph <= 3; ph++) {
         if (e) cudaEventRecordWithFlags(e[ph - 1], c->stream, cudaEventRecordExternal);
-        launch_phase(d, ph, koff, c->grid, c->block, c->stream);
+        launch_phase(d, ph, koff, kph, c->grid, c->block, c->stream);
     }
     if (e) cudaEventRecordWithFlags(e[3], c->stream, cudaEventRecordExternal);
     if (compact) {
@@ -213,7 +213,7 @@ void collect_times(lpsim_ctx *c, uint32_t n, uint64_t k_first) {
 // one step launched directly (kbase == k on entry; kbase == k+1 after)
 int direct_step(lpsim_ctx *c) {
     bool compact = (c->k + 1) % c->R == 0;
-    c->cur = enqueue_step(c, 0, c->cur, compact);
+    c->cur = enqueue_step(c, 0, (uint32_t)(c->k % 6), c->cur, compact);
     c->launches += 3;
     if (compact) c->launches += c->sort ? 3 + 3ull * ((c->w.key_bits + 7) / 8) + 1 : 3;
     launch_chunk_end(c->d, 1, c->stream);
@@ -231,7 +231,8 @@ int capture_chunk(lpsim_ctx *c, int start_set) {
     cudaGraph_t g = nullptr;
     CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     int cur = start_set;
-    for (uint32_t koff = 0; koff < c->C; koff++) cur = enqueue_step(c, koff, cur, (koff + 1) % c->R == 0);
+    // a chunk always starts at a multiple of C, itself a multiple of 6
+    for (uint32_t koff = 0; koff < c->C; koff++) cur = enqueue_step(c, koff, koff, cur, (koff + 1) % c->R == 0);
     launch_chunk_end(c->d, c->C, c->stream);
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     if (e != cudaSuccess) return fail(LPSIM_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
@@ -250,6 +251,7 @@ uint64_t chunk_launches(const lpsim_ctx *c) {
 }
 
 int chunk(lpsim_ctx *c) {
+    if (c->C % 6 != 0 || c->k % c->C != 0) return fail(LPSIM_E_STATE, "graph chunk not aligned to a multiple of 6 steps");
     if (!c->graph[c->cur]) TRY(capture_chunk(c, c->cur));
     CU(cudaGraphLaunch(c->graph[c->cur], c->stream));
     c->launches += chunk_launches(c);
@@ -678,14 +680,8 @@ int load_demand_impl(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, cons
     TRY(dnew_mut(c, d.org_head, norg));
     TRY(dnew_mut(c, d.org_hd, norg));
     TRY(dnew(c, c->org_hd0, norg));
-    TRY(dnew(c, d.dslot, norg));
     TRY(dnew_mut(c, d.dprev, norg));
-    TRY(dnew(c, d.dreq, norg));
-    TRY(dnew(c, d.den, norg));
-    TRY(dnew(c, d.dsg, norg));
-    TRY(dnew(c, d.dsph, norg));
-    TRY(dnew(c, d.dtlc, norg));
-    for (int i = 0; i < 2; i++) TRY(dnew(c, d.dep_list[i], norg));
+    for (int i = 0; i < 2; i++) TRY(dnew(c, d.dep_rec[i], norg));
     // slots: live vehicles plus the holes left between compactions by
     // arrivals and by departures that lost an entry conflict
     const uint64_t cap64 = n + 256ull * norg + 1024;

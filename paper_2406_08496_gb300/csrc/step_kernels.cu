@@ -6,8 +6,9 @@
 //            decision at the edge end (arrive, ask to cross, hold at the stop
 //            line) or the lane-change intent; writes its step-k+1 cell into
 //            the next map when it stays; posts entry claims (atomicMin of the
-//            vehicle id on the (edge, lane) slot).  Origin edges post the
-//            departure claim of their queue head.
+//            vehicle id on the (edge, lane) slot) with a record of what the
+//            resolution needs.  Origin edges post the departure claim of
+//            their queue head.
 //   step_p2  crossers and departures: the lowest id of each claimed slot
 //            enters cell 0; the others stop at the stop line.
 //   step_p3  lane-change intenders: gap acceptance against the step-k map and
@@ -22,9 +23,18 @@
 // its byte sideways: the result is the same as judging every intender
 // against one snapshot, whatever the order the threads run in.
 //
+// Latency, not bandwidth, bounds these kernels (a step moves a few MB), so
+// each is arranged to need as few dependent memory round trips as possible:
+// the parity buffers and maps are chosen from a launch argument, the first
+// records of a thread are loaded together with the step number and the list
+// lengths, and records that a later phase needs are packed by the phase that
+// already holds the values.
+//
 // Every floating-point expression is written in the same operation order as
 // the rules state; the library is compiled with -fmad=false -prec-div=true
 // -ftz=false, so each operation is one IEEE binary32 rounding.
+#include <algorithm>
+
 #include "lpsim_dev.cuh"
 
 namespace lpsim {
@@ -142,6 +152,22 @@ __device__ __forceinline__ void pdl_prologue() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
+// Position in a per-step list for each calling lane: one atomic per group of
+// lanes that arrive together (list order does not matter to any result).
+__device__ __forceinline__ uint32_t warp_append(uint32_t *counter) {
+    const uint32_t mask = __activemask();
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t leader = (uint32_t)__ffs((int)mask) - 1u;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(counter, (uint32_t)__popc((int)mask));
+    base = __shfl_sync(mask, base, (int)leader);
+    return base + (uint32_t)__popc((int)(mask & ((1u << lane) - 1u)));
+}
+
+// Keeps the loads above it above a following branch (so the first records of
+// a thread are in flight while the list length is still on its way).
+__device__ __forceinline__ void loads_issued() { asm volatile("" ::: "memory"); }
+
 template <int BLOCK>
 __device__ __forceinline__ void block_add(unsigned long long *dst, uint32_t val) {
     __shared__ uint32_t red[BLOCK / 32];
@@ -161,15 +187,20 @@ __device__ __forceinline__ void block_add(unsigned long long *dst, uint32_t val)
 
 // Lane asked for when entering an edge: lanes ordered by distance to the
 // target lane tl (kNoLane counts as 0; ties to the lower index); the first
-// whose cell 0 is empty in the step-k map.  The up-to-4 first cells are read
-// together.  kNone if none is empty.
-__device__ __forceinline__ uint32_t pick_entry_lane(const uint8_t *Mc, const EdgeRec &er, uint32_t tl) {
+// whose cell 0 is empty in the step-k map.  entry_cells reads the up-to-4
+// first cells together (it needs only the edge record, so the reads overlap
+// the load of tl); kNone if none is empty.
+__device__ __forceinline__ uint32_t entry_cells(const uint8_t *Mc, const EdgeRec &er) {
     const uint32_t nl = er.lanes, stride = row_stride(er.len);
-    if (tl == kNoLane) tl = 0;
     uint32_t empty = 0;  // bit l: cell 0 of lane l is empty
 #pragma unroll
     for (uint32_t l = 0; l < 4; l++)
         if (l < nl && Mc[er.moff + l * stride] == kEmpty) empty |= 1u << l;
+    return empty;
+}
+
+__device__ __forceinline__ uint32_t pick_entry_lane(uint32_t empty, uint32_t nl, uint32_t tl) {
+    if (tl == kNoLane) tl = 0;
     for (uint32_t dd = 0; dd < nl; dd++) {
         if (tl >= dd && ((empty >> (tl - dd)) & 1u)) return tl - dd;
         if (dd > 0 && tl + dd < nl && ((empty >> (tl + dd)) & 1u)) return tl + dd;
@@ -178,61 +209,73 @@ __device__ __forceinline__ uint32_t pick_entry_lane(const uint8_t *Mc, const Edg
 }
 
 template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) step_p1(Dev d, uint32_t koff) {
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) step_p1(Dev d, uint32_t koff, uint32_t kph) {
     pdl_prologue();
-    const uint32_t k = *d.kbase + koff;
-    const uint32_t par = k & 1u;
-    const uint8_t *Mc = d.map[k % 3];
-    uint8_t *Mn = d.map[(k + 1) % 3];
-    uint8_t *Mo = d.map[(k + 2) % 3];       // holds step k-1: erase
+    const uint32_t par = kph & 1u, r3 = kph % 3u;
+    const uint8_t *Mc = d.map[r3];
+    uint8_t *Mn = d.map[r3 == 2u ? 0u : r3 + 1u];
+    uint8_t *Mo = d.map[r3 == 0u ? 2u : r3 - 1u];  // holds step k-1: erase
     uint8_t *Iw = d.imap[par];
     uint8_t *Io = d.imap[par ^ 1u];         // marks of step k-1: clear
     uint32_t *claim = d.claim[par];
     uint32_t *claim_old = d.claim[par ^ 1u]; // slots won at step k-1: reset
     const float *xc = d.s.x[par], *vc = d.s.v[par];
     float *xw = d.s.x[par ^ 1u], *vw = d.s.v[par ^ 1u];
+    const uint32_t k = *d.kbase + koff;
     const uint32_t n = *d.n_slots;
-    const uint32_t total = n + d.n_org;
+    const uint32_t norg = d.n_org;
+    const uint32_t lim = norg + d.cap;  // items: origin edges first, then slots
     const Model &m = d.m;
     const bool sample = m.bin_steps && (k % m.bin_steps == 0) && (k / m.bin_steps < m.n_bins);
     uint32_t live = 0;
     uint32_t arrived = 0;
-
-    for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < total; i += gridDim.x * BLOCK) {
-        if (i >= n) {
+    for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < lim; i += gridDim.x * BLOCK) {
+        if (i < norg) {
             // origin edge j: reset the claim its departure won last step; ask
             // for a departure of the queue head once its step has come
-            const uint32_t j = i - n;
+            const uint32_t j = i;
             const uint32_t dp = d.dprev[j];
             const QRec hd = d.org_hd[j];
+            const EdgeRec er = d.org_rec[j];
+            const uint32_t e0 = d.org_edge[j];
+            const uint32_t qoff = d.org_qoff[j], qhead = d.org_head[j], qend = d.org_qend[j];
             if (dp != kNone) {
                 claim_old[dp] = kNone;
                 d.dprev[j] = kNone;
             }
-            uint8_t req = kEmpty;
             if (hd.h != kNone && hd.dep <= k) {
-                const EdgeRec er = d.org_rec[j];
                 const RouteRec rr = d.rrec[hd.r0];
                 const uint32_t nxt = hd.r0 + 1 < hd.r1 ? d.route[hd.r0 + 1] : kNone;
-                const uint32_t l = pick_entry_lane(Mc, er, rr.tl);
+                const uint32_t so = d.slot_off[e0];
+                const uint32_t l = pick_entry_lane(entry_cells(Mc, er), er.lanes, rr.tl);
                 if (l != kNone) {
-                    const uint32_t slot = d.slot_off[d.org_edge[j]] + l;
-                    atomicMin(&claim[slot], hd.h);
-                    d.dslot[j] = slot;
-                    d.den[j] = nxt;
-                    d.dsg[j] = rr.green;
-                    d.dsph[j] = (uint16_t)(rr.nphase | (rr.arank << 8));
-                    d.dtlc[j] = rr.tl;
-                    req = (uint8_t)l;
-                    const uint32_t pos = atomicAdd(&d.counts[4 + par], 1u);
-                    d.dep_list[par][pos] = j;
+                    atomicMin(&claim[so + l], hd.h);
+                    DepRec dr;
+                    dr.j = j;
+                    dr.slot = so + l;
+                    dr.h = hd.h;
+                    dr.r0 = hd.r0;
+                    dr.r1 = hd.r1;
+                    dr.qoff = qoff;
+                    dr.qhead = qhead;
+                    dr.qend = qend;
+                    dr.base = er.moff + l * row_stride(er.len);
+                    dr.e0 = e0;
+                    dr.nen = nxt;
+                    dr.nsg = rr.green;
+                    dr.v0 = er.v0;
+                    dr.len = er.len;
+                    dr.nsph = (uint16_t)(rr.nphase | (rr.arank << 8));
+                    dr.lane = (uint8_t)l;
+                    dr.tlc = rr.tl;
+                    d.dep_rec[par][warp_append(&d.counts[4 + par])] = dr;
                 }
             }
-            d.dreq[j] = req;
             continue;
         }
-        const uint32_t s = i;
-        // every slot field, loaded together (one memory round trip)
+        const uint32_t s = i - norg;
+        // every slot field, loaded together (one memory round trip, shared
+        // with the loads of the step number and the slot count)
         const uint8_t flag = d.s.flag[s];
         const uint32_t pc = d.s.pcell[s];
         const uint32_t im = d.s.imark[s];
@@ -250,6 +293,8 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) step_p1(Dev d, uint32_t k
         const uint32_t e = d.s.e[s];
         const uint32_t rpos = d.s.rpos[s], rlast = d.s.rlast[s];
         const uint32_t tent = d.s.tent[s];
+        loads_issued();
+        if (s >= n) break;
         if (flag == kDead) continue;
         if (pc != kNone) Mo[pc] = kEmpty;
         if (im != kNone) {
@@ -331,7 +376,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) step_p1(Dev d, uint32_t k
                     rr = d.rrec[rpos + 1];
                     nen = rpos + 1 < rlast ? d.route[rpos + 2] : kNone;
                 }
-                const uint32_t l = pick_entry_lane(Mc, enr, rr.tl);
+                const uint32_t l = pick_entry_lane(entry_cells(Mc, enr), enr.lanes, rr.tl);
                 if (l != kNone) {
                     const uint32_t slot = d.slot_off[en] + l;
                     atomicMin(&claim[slot], id);
@@ -356,8 +401,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) step_p1(Dev d, uint32_t k
                     cr.lane = (uint8_t)l;
                     cr.tln = rr.tl;
                     d.s.act[s] = kActCross;
-                    const uint32_t pos = atomicAdd(&d.counts[par], 1u);
-                    d.cross_list[par][pos] = cr;
+                    d.cross_list[par][warp_append(&d.counts[par])] = cr;
                     cross = true;
                 }
             }
@@ -394,8 +438,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) step_p1(Dev d, uint32_t k
                 ir.len = (uint16_t)len;
                 ir.lane = (uint8_t)ln;
                 ir.up = tl > ln ? 1 : 0;
-                const uint32_t pos = atomicAdd(&d.counts[2 + par], 1u);
-                d.intend_list[par][pos] = ir;
+                d.intend_list[par][warp_append(&d.counts[2 + par])] = ir;
             }
         }
         d.s.act[s] = act;
@@ -406,23 +449,27 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) step_p1(Dev d, uint32_t k
 
 // ----------------------------------------------------------------------- P2
 
+// The last gdep blocks (enough for one request per origin edge) take the
+// departure requests, the others the crossers, so that each thread's first
+// record is loaded together with its list's length.
 template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK) step_p2(Dev d, uint32_t koff) {
+__global__ void __launch_bounds__(BLOCK) step_p2(Dev d, uint32_t koff, uint32_t kph, uint32_t gdep) {
     pdl_prologue();
-    const uint32_t k = *d.kbase + koff;
-    const uint32_t par = k & 1u;
-    uint8_t *Mn = d.map[(k + 1) % 3];
+    const uint32_t par = kph & 1u, r3 = kph % 3u;
+    uint8_t *Mn = d.map[r3 == 2u ? 0u : r3 + 1u];
     const uint32_t *claim = d.claim[par];
     float *xw = d.s.x[par ^ 1u], *vw = d.s.v[par ^ 1u];
-    const uint32_t ncross = d.counts[par];
-    const uint32_t ndep = d.counts[4 + par];
-    const uint32_t n0 = *d.n_slots;  // new vehicles take slots n0 .. n0 + ndep - 1
-    const uint32_t total = ncross + ndep;
-    const CrossRec *list = d.cross_list[par];
+    const uint32_t k = *d.kbase + koff;
+    const bool crossers = blockIdx.x < gridDim.x - gdep;
     uint32_t events = 0, departed = 0;
-    for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < total; i += gridDim.x * BLOCK) {
-        if (i < ncross) {
+    if (crossers) {
+        const uint32_t ncross = d.counts[par];
+        const uint32_t nthr = (gridDim.x - gdep) * BLOCK;
+        const CrossRec *list = d.cross_list[par];
+        for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < d.cap; i += nthr) {
             const CrossRec cr = list[i];
+            loads_issued();
+            if (i >= ncross) break;
             if (claim[cr.cslot] == cr.id) {
                 const uint32_t s = cr.s;
                 stat_exit(d, cr.e, k, cr.tent);
@@ -450,63 +497,63 @@ __global__ void __launch_bounds__(BLOCK) step_p2(Dev d, uint32_t koff) {
                 vw[cr.s] = 0.0f;
                 put_cell(d, Mn, cr.base + (uint32_t)xh, 0);
             }
-            continue;
         }
-        // departure request number i - ncross: its slot is fixed in advance
-        const uint32_t q = i - ncross;
-        const uint32_t j = d.dep_list[par][q];
-        const uint32_t s = n0 + q;
-        const QRec hd = d.org_hd[j];
-        const uint32_t slot = d.dslot[j];
-        const uint32_t l = d.dreq[j];
-        const uint32_t qh = d.org_qoff[j] + d.org_head[j];
-        const uint32_t qend = d.org_qend[j];
-        const EdgeRec er = d.org_rec[j];
-        const uint32_t nen = d.den[j], nsg = d.dsg[j];
-        const uint16_t nsph = d.dsph[j];
-        const uint8_t tlc = d.dtlc[j];
-        const QRec next = qh + 1 < qend ? d.qrec[qh + 1] : QRec{kNone, kNone, 0, 0};
-        if (s >= d.cap) {
-            atomicOr(d.err, kErrSlotOverflow);
-            continue;
-        }
-        if (claim[slot] != hd.h) {
-            d.s.flag[s] = kDead;
+    }
+    if (!crossers) {
+        // departure request q: its slot n0 + q is fixed in advance
+        const uint32_t ndep = d.counts[4 + par];
+        const uint32_t n0 = *d.n_slots;
+        const uint32_t b0 = gridDim.x - gdep;
+        const uint32_t nthr = gdep * BLOCK;
+        const DepRec *list = d.dep_rec[par];
+        for (uint32_t q = (blockIdx.x - b0) * BLOCK + threadIdx.x; q < d.n_org; q += nthr) {
+            const DepRec dr = list[q];
+            loads_issued();
+            if (q >= ndep) break;
+            const uint32_t s = n0 + q;
+            const uint32_t qh = dr.qoff + dr.qhead;
+            const QRec next = qh + 1 < dr.qend ? d.qrec[qh + 1] : QRec{kNone, kNone, 0, 0};
+            const uint32_t won = claim[dr.slot];
+            if (s >= d.cap) {
+                atomicOr(d.err, kErrSlotOverflow);
+                continue;
+            }
+            if (won != dr.h) {
+                d.s.flag[s] = kDead;
+                d.s.pcell[s] = kNone;
+                d.s.imark[s] = kNone;
+                d.s.cprev[s] = kNone;
+                continue;
+            }
+            d.s.id[s] = dr.h;
+            d.s.e[s] = dr.e0;
+            d.s.rpos[s] = dr.r0;
+            d.s.rlast[s] = dr.r1 - 1;
+            d.s.lane[s] = dr.lane;
+            d.s.tlc[s] = dr.tlc;
+            d.s.base[s] = dr.base;
+            d.s.len[s] = dr.len;
+            d.s.v0[s] = dr.v0;
+            d.s.en[s] = dr.nen;
+            d.s.sg[s] = dr.nsg;
+            d.s.sph[s] = dr.nsph;
+            d.s.tent[s] = k + 1;
             d.s.pcell[s] = kNone;
             d.s.imark[s] = kNone;
             d.s.cprev[s] = kNone;
-            continue;
+            d.s.flag[s] = kLive;
+            xw[s] = 0.0f;
+            vw[s] = 0.0f;
+            put_cell(d, Mn, dr.base, 0);
+            d.dprev[dr.j] = dr.slot;
+            d.org_head[dr.j] = dr.qhead + 1;
+            d.org_hd[dr.j] = next;
+            d.dep_act[dr.h] = k + 1;
+            d.status[dr.h] = kActive;
+            stat_entry(d, dr.e0, k);
+            events++;
+            departed++;
         }
-        const uint32_t e0 = d.org_edge[j];
-        const uint32_t b0 = er.moff + l * row_stride(er.len);
-        d.s.id[s] = hd.h;
-        d.s.e[s] = e0;
-        d.s.rpos[s] = hd.r0;
-        d.s.rlast[s] = hd.r1 - 1;
-        d.s.lane[s] = (uint8_t)l;
-        d.s.tlc[s] = tlc;
-        d.s.base[s] = b0;
-        d.s.len[s] = er.len;
-        d.s.v0[s] = er.v0;
-        d.s.en[s] = nen;
-        d.s.sg[s] = nsg;
-        d.s.sph[s] = nsph;
-        d.s.tent[s] = k + 1;
-        d.s.pcell[s] = kNone;
-        d.s.imark[s] = kNone;
-        d.s.cprev[s] = kNone;
-        d.s.flag[s] = kLive;
-        xw[s] = 0.0f;
-        vw[s] = 0.0f;
-        put_cell(d, Mn, b0, 0);
-        d.dprev[j] = slot;
-        d.org_head[j] += 1;
-        d.org_hd[j] = next;
-        d.dep_act[hd.h] = k + 1;
-        d.status[hd.h] = kActive;
-        stat_entry(d, e0, k);
-        events++;
-        departed++;
     }
     if (events) atomicAdd(&d.ctr[3], (unsigned long long)events);
     if (departed) atomicAdd(&d.ctr[4], (unsigned long long)departed);
@@ -529,18 +576,20 @@ __device__ __forceinline__ void load_chunks(const uint8_t *row, uint32_t c_first
 }
 
 template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK) step_p3(Dev d, uint32_t koff) {
+__global__ void __launch_bounds__(BLOCK) step_p3(Dev d, uint32_t koff, uint32_t kph) {
     pdl_prologue();
-    const uint32_t k = *d.kbase + koff;
-    const uint32_t par = k & 1u;
-    const uint8_t *Mc = d.map[k % 3];
-    uint8_t *Mn = d.map[(k + 1) % 3];
+    const uint32_t par = kph & 1u, r3 = kph % 3u;
+    const uint8_t *Mc = d.map[r3];
+    uint8_t *Mn = d.map[r3 == 2u ? 0u : r3 + 1u];
     const uint8_t *Iw = d.imap[par];
+    const uint32_t k = *d.kbase + koff;
     const uint32_t nint = d.counts[2 + par];
     const Model &m = d.m;
     uint32_t changes = 0;
-    for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < nint; i += gridDim.x * BLOCK) {
+    for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < d.cap; i += gridDim.x * BLOCK) {
         const IntendRec ir = d.intend_list[par][i];
+        loads_issued();
+        if (i >= nint) break;
         const uint32_t s = ir.s;
         const uint32_t ln = ir.lane;
         const bool up = ir.up != 0;
@@ -651,15 +700,17 @@ void launch_pdl(void (*kernel)(Args...), int grid, int block, cudaStream_t st, A
 
 }  // namespace
 
-void launch_phase(const Dev &d, int phase, uint32_t koff, int grid, int block, cudaStream_t st) {
-    // step_p2 and step_p3 walk short lists (crossers, intenders, departure
-    // requests): a quarter of the grid is plenty
+void launch_phase(const Dev &d, int phase, uint32_t koff, uint32_t kph, int grid, int block, cudaStream_t st) {
+    // step_p2 and step_p3 walk short lists (crossers, intenders): a quarter
+    // of the grid is plenty; step_p2 adds one block per `block` origin edges
+    // for the departure requests (at most one per origin edge and step)
     const int g = phase == 1 ? grid : (grid + 3) / 4;
-#define LPSIM_PHASE(B)                                            \
-    do {                                                          \
-        if (phase == 1) launch_pdl(step_p1<B>, g, B, st, d, koff); \
-        else if (phase == 2) launch_pdl(step_p2<B>, g, B, st, d, koff); \
-        else launch_pdl(step_p3<B>, g, B, st, d, koff);            \
+    const uint32_t gdep = std::max(1u, (d.n_org + (uint32_t)block - 1) / (uint32_t)block);
+#define LPSIM_PHASE(B)                                                                  \
+    do {                                                                                \
+        if (phase == 1) launch_pdl(step_p1<B>, g, B, st, d, koff, kph);                 \
+        else if (phase == 2) launch_pdl(step_p2<B>, g + (int)gdep, B, st, d, koff, kph, gdep); \
+        else launch_pdl(step_p3<B>, g, B, st, d, koff, kph);                            \
     } while (0)
     switch (block) {
     case 128: LPSIM_PHASE(128); break;
