@@ -416,13 +416,17 @@ def main():
         tot_ms = sum(v["ms"] for v in kt.values())
         tr = ncu_traffic()
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": (tr or {}).get("dram_bytes_per_launch"),
+                    # ncu DRAM bytes per vehicle-step of a morning-peak launch, scaled to this
+                    # run's average launch (traffic grows with the vehicles processed)
+                    "traffic": (tr["dram_bytes_per_veh_step"] * rr["veh_steps"] / max(1, p1["launches"])
+                                if tr else None),
                     "kernel": "step_p1", "bytes_per_veh_step": BYTES_PER_VEH_STEP_P1,
                     "avg_launch_us": p1["ms"] * 1e3 / max(1, p1["launches"]),
                     "avg_veh_per_launch": rr["veh_steps"] / max(1, p1["launches"]),
                     "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})",
                     "kernel_share": {k: v["ms"] / tot_ms for k, v in kt.items()},
-                    "traffic_launch": (tr or {}).get("captured_launch")}
+                    "traffic_source": ("profiles/step_p1_regional_peak.json: " + tr["captured_launch"]) if tr else
+                    "stale or missing ncu summary"}
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             sub = sample_workload(net, dem)

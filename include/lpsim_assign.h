@@ -62,6 +62,20 @@ int lpsim_assign_gap(lpsim_assign *a, const uint32_t *depart_actual, const uint3
  * probability `fraction` (seeded by the engine seed and `iteration`). */
 int lpsim_assign_reroute(lpsim_assign *a, double fraction, uint32_t iteration, uint64_t *n_changed);
 
+/* Per-trip excess of the current route over the shortest path of the last
+ * lpsim_assign_shortest_paths call, in seconds, predicted under link times
+ * tt (edge-major, n_bins bins of bin_steps steps): the route is traversed from
+ * the planned departure with each link's time looked up at its entry time.
+ * lpsim_assign_gap sets the same per-trip excess from a simulation's
+ * experienced times instead (0 for trips that did not arrive). */
+int lpsim_assign_route_excess(lpsim_assign *a, const float *tt, uint32_t n_bins, uint32_t bin_steps);
+
+/* Method of successive averages, worst first: the round(fraction * n_trips)
+ * trips with the largest relative excess (excess / shortest time; only trips
+ * whose candidate route differs and whose excess is positive; ties to the
+ * lower trip index) move to their candidate route.  *n_changed = trips moved. */
+int lpsim_assign_reroute_worst(lpsim_assign *a, double fraction, uint64_t *n_changed);
+
 /* Current routes (route_off: n_trips + 1 entries; route_edges: capacity
  * entries, at least lpsim_assign_route_length()). */
 uint64_t lpsim_assign_route_length(const lpsim_assign *a);

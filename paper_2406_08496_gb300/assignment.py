@@ -29,6 +29,8 @@ def _lib():
                                                     ctypes.c_uint32, P]
         lib.lpsim_assign_gap.argtypes = [P, P, P, P, P]
         lib.lpsim_assign_reroute.argtypes = [P, ctypes.c_double, ctypes.c_uint32, P]
+        lib.lpsim_assign_route_excess.argtypes = [P, P, ctypes.c_uint32, ctypes.c_uint32]
+        lib.lpsim_assign_reroute_worst.argtypes = [P, ctypes.c_double, P]
         lib.lpsim_assign_route_length.argtypes = [P]
         lib.lpsim_assign_route_length.restype = ctypes.c_uint64
         lib.lpsim_assign_get_routes.argtypes = [P, P, P, ctypes.c_uint64]
@@ -90,6 +92,15 @@ class Assignment:
         _check(self.lib, self.lib.lpsim_assign_reroute(self.h, fraction, iteration, ctypes.byref(n)))
         return n.value
 
+    def route_excess(self, tt: np.ndarray, bin_steps: int) -> None:
+        tt = np.ascontiguousarray(tt, dtype=np.float32)
+        _check(self.lib, self.lib.lpsim_assign_route_excess(self.h, _p(tt), tt.shape[1], bin_steps))
+
+    def reroute_worst(self, fraction: float) -> int:
+        n = ctypes.c_uint64()
+        _check(self.lib, self.lib.lpsim_assign_reroute_worst(self.h, fraction, ctypes.byref(n)))
+        return n.value
+
     def routes(self) -> dict:
         total = int(self.lib.lpsim_assign_route_length(self.h))
         off = np.empty(self.n + 1, np.uint64)
@@ -143,7 +154,7 @@ class Assignment:
 def msa(net: dict, dem: dict, mode: str = "plain", iterations: int = 10, fraction: float = 0.1,
         target_gap: float = 0.01, sim_params: dict | None = None, bin_steps: int = 1800, n_bins: int = 96,
         period_steps: int = 3600, max_steps: int = 300_000, surrogate_steps: int = 400, surrogate_batch: int = 8192,
-        seed: int = 0, log=None) -> dict:
+        seed: int = 0, select: str = "worst", log=None) -> dict:
     """Method of successive averages.  plain: every iteration simulates the
     current routes, measures the relative gap and moves `fraction` of the
     trips to their time-dependent shortest paths under the simulated link
@@ -152,9 +163,17 @@ def msa(net: dict, dem: dict, mode: str = "plain", iterations: int = 10, fractio
     simulation, predict the link times of the current routes with the
     surrogate (inflows from loading the routes with the last simulated
     times) and re-route under the prediction.  Every reported gap is
-    measured by a full simulation.  Returns the iteration history and the
-    wall time to reach target_gap (None if never reached)."""
-    assert mode in ("plain", "surrogate")
+    measured by a full simulation.  select: which trips move -- "worst" (the
+    fraction with the largest relative excess of their route over the
+    shortest path, from the simulation or, in surrogate iterations, from the
+    prediction) or "random" (each trip with probability fraction).  Returns
+    the iteration history and the wall time to reach target_gap (None if
+    never reached)."""
+    assert mode in ("plain", "surrogate") and select in ("worst", "random")
+
+    def move(it):
+        return A.reroute_worst(fraction) if select == "worst" else A.reroute(fraction, it)
+
     params = dict(bin_steps=bin_steps, n_bins=n_bins)
     params.update(sim_params or {})
     A = Assignment(net, dem, dt=0.5, seed=seed)
@@ -206,16 +225,18 @@ def msa(net: dict, dem: dict, mode: str = "plain", iterations: int = 10, fractio
                 if log:
                     log(rec)
                 break
-            rec["rerouted"] = A.reroute(fraction, it)
+            rec["rerouted"] = move(it)
         else:
             inflow = A.load(tt_last, bin_steps)
             X = A.features(inflow, occ_last, lr_last, in_last)
             y = mlp.forward(X)
             tt_pred = A.times_from_ratio(y, n_bins)
             A.shortest_paths(tt_pred, bin_steps, period_steps)
+            if select == "worst":
+                A.route_excess(tt_pred, bin_steps)
             rec = dict(iteration=it, kind="surrogate", gap=None, wall_s=time.perf_counter() - t_start,
                        iter_s=time.perf_counter() - t0)
-            rec["rerouted"] = A.reroute(fraction, it)
+            rec["rerouted"] = move(it)
         hist.append(rec)
         if log:
             log(rec)

@@ -2,9 +2,9 @@
 // method of successive averages (MSA) with time-dependent shortest paths.
 //
 // The paper's title is traffic *assignment* and propagation; its simulator
-// propagates trips along routes fixed "after the routing" (Sec. 3.1) and it
-// names dynamic rerouting as future work (Sec. 5, Conclusion).  This engine closes the
-// loop: link travel times per 15-minute entry bin come from a simulation
+// propagates trips along routes computed beforehand (Sec. 3.1) and it names
+// dynamic rerouting as future work (Sec. 5, Conclusion).  This engine closes
+// the loop: link travel times per 15-minute entry bin come from a simulation
 // (or from the surrogate), time-dependent shortest paths are computed under
 // them (label-setting Dijkstra on earliest arrival, FIFO bin lookup of the
 // link time at the entry time), and a fraction of trips is moved onto the
@@ -44,6 +44,7 @@ struct lpsim_assign {
     std::vector<uint32_t> orig, dest, dep;    // depart step
     std::vector<std::vector<uint32_t>> route, cand;
     std::vector<float> tsp;                   // shortest time under the last tt (s)
+    std::vector<float> excess;                // current route's time minus tsp (s), from a simulation or a prediction
     float dt = 0.5f;
     uint64_t seed = 0;
 };
@@ -133,6 +134,7 @@ int lpsim_assign_create(lpsim_assign **out, uint32_t n_nodes, uint32_t n_edges, 
     a->route.resize(n_trips);
     a->cand.resize(n_trips);
     a->tsp.assign(n_trips, 0.0f);
+    a->excess.assign(n_trips, 0.0f);
     for (uint64_t j = 0; j < n_trips; j++) {
         if (route_off[j + 1] <= route_off[j] || orig[j] >= n_nodes || dest[j] >= n_nodes) {
             delete a;
@@ -213,11 +215,13 @@ int lpsim_assign_gap(lpsim_assign *a, const uint32_t *depart_actual, const uint3
     double num = 0.0, den = 0.0;
     uint64_t used = 0;
     for (uint64_t j = 0; j < a->n; j++) {
+        a->excess[j] = 0.0f;
         if (arrive_step[j] == 0xFFFFFFFFu || depart_actual[j] == 0xFFFFFFFFu) continue;
         // experienced time: from the planned departure (waiting to enter counts) to arrival
         const double texp = (double)(arrive_step[j] - a->dep[j]) * a->dt;
         num += texp - a->tsp[j];
         den += a->tsp[j];
+        a->excess[j] = (float)(texp - a->tsp[j]);
         used++;
     }
     *rg = den > 0 ? num / den : 0.0;
@@ -238,6 +242,36 @@ int lpsim_assign_reroute(lpsim_assign *a, double fraction, uint32_t iteration, u
         }
     }
     if (n_changed) *n_changed = changed;
+    return LPSIM_OK;
+}
+
+int lpsim_assign_route_excess(lpsim_assign *a, const float *tt, uint32_t n_bins, uint32_t bin_steps) {
+    if (!a || !tt || n_bins == 0 || bin_steps == 0) return fail(LPSIM_E_INVALID_ARG, "bad argument");
+    TD td{a, tt, n_bins, (float)bin_steps * a->dt};
+    for (uint64_t j = 0; j < a->n; j++) {
+        const double t0 = (double)a->dep[j] * a->dt;
+        double t = t0;
+        for (uint32_t e : a->route[j]) t += td.cost(e, t);
+        a->excess[j] = (float)(t - t0 - a->tsp[j]);
+    }
+    return LPSIM_OK;
+}
+
+int lpsim_assign_reroute_worst(lpsim_assign *a, double fraction, uint64_t *n_changed) {
+    if (!a || !(fraction >= 0.0 && fraction <= 1.0)) return fail(LPSIM_E_INVALID_ARG, "bad argument");
+    // trips whose candidate differs from their route, by relative excess
+    // (largest first, ties to the lower index)
+    std::vector<uint64_t> pick;
+    for (uint64_t j = 0; j < a->n; j++)
+        if (!a->cand[j].empty() && a->excess[j] > 0.0f && a->cand[j] != a->route[j]) pick.push_back(j);
+    const uint64_t want = std::min<uint64_t>(pick.size(), (uint64_t)std::llround(fraction * (double)a->n));
+    auto rel = [&](uint64_t j) { return (double)a->excess[j] / std::max(1.0, (double)a->tsp[j]); };
+    std::partial_sort(pick.begin(), pick.begin() + want, pick.end(), [&](uint64_t x, uint64_t y) {
+        const double rx = rel(x), ry = rel(y);
+        return rx != ry ? rx > ry : x < y;
+    });
+    for (uint64_t i = 0; i < want; i++) a->route[pick[i]] = a->cand[pick[i]];
+    if (n_changed) *n_changed = want;
     return LPSIM_OK;
 }
 

@@ -49,6 +49,8 @@ struct lpsim_ctx {
     uint64_t launches = 0;
     uint64_t stall_steps = 0;
     unsigned long long last_progress = 0;
+    std::vector<uint32_t> dep_sorted;  // departure step by vehicle id (nondecreasing)
+    uint64_t skipped = 0;              // idle steps jumped over (nothing on the network)
     // device buffers whose contents change while stepping (snapshot / restore)
     std::vector<std::pair<void *, size_t>> mut;
     uint8_t *snap = nullptr;

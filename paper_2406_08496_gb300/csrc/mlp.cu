@@ -341,14 +341,39 @@ __global__ void __launch_bounds__(kThreads, 2)
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
                 float *mz = stZ + lane * 33, *mh = stH + lane * 33;
                 if (kGelu) {
+                    // bias (and head weights) four columns at a time: 16-byte loads, the same for every lane
+                    uint32_t hp[16];  // the row's 32 activations as bf16 pairs
 #pragma unroll
-                    for (int j = 0; j < 32; j++) {
-                        const float z = __uint_as_float(r[j]) + g.bias[col0 + j];
-                        const float e = erff(z * 0.70710678118654752f);
-                        const float h = __bfloat162float(__float2bfloat16_rn(0.5f * z * (1.0f + e)));
-                        mh[j] = h;
-                        if (g.gout) mz[j] = 0.5f * (1.0f + e) + z * 0.39894228040143268f * expf(-0.5f * z * z);
-                        if (EPI == kEpiGeluHead) head += h * g.w4[col0 + j];
+                    for (int q4 = 0; q4 < 8; q4++) {
+                        const float4 b4v = reinterpret_cast<const float4 *>(g.bias + col0)[q4];
+                        float4 w4v = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (EPI == kEpiGeluHead) w4v = reinterpret_cast<const float4 *>(g.w4 + col0)[q4];
+                        const float bq[4] = {b4v.x, b4v.y, b4v.z, b4v.w};
+                        const float wq[4] = {w4v.x, w4v.y, w4v.z, w4v.w};
+                        __nv_bfloat16 hb[4];
+#pragma unroll
+                        for (int u = 0; u < 4; u++) {
+                            const int j = 4 * q4 + u;
+                            const float z = __uint_as_float(r[j]) + bq[u];
+                            const float e = erff(z * 0.70710678118654752f);
+                            hb[u] = __float2bfloat16_rn(0.5f * z * (1.0f + e));
+                            const float h = __bfloat162float(hb[u]);
+                            if (g.htout) mh[j] = h;
+                            if (g.gout)
+                                mz[j] = 0.5f * (1.0f + e) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+                            if (EPI == kEpiGeluHead) head += h * wq[u];
+                        }
+                        const __nv_bfloat162 p0 = __halves2bfloat162(hb[0], hb[1]);
+                        const __nv_bfloat162 p1 = __halves2bfloat162(hb[2], hb[3]);
+                        hp[2 * q4] = *reinterpret_cast<const uint32_t *>(&p0);
+                        hp[2 * q4 + 1] = *reinterpret_cast<const uint32_t *>(&p1);
+                    }
+                    // the row-major activations straight from registers: 64 contiguous bytes per row
+                    if (g.hout && rw0 + lane < g.M) {
+                        uint4 *dst = reinterpret_cast<uint4 *>(g.hout + (size_t)(rw0 + lane) * g.N + col0);
+#pragma unroll
+                        for (int q4 = 0; q4 < 4; q4++)
+                            dst[q4] = make_uint4(hp[4 * q4], hp[4 * q4 + 1], hp[4 * q4 + 2], hp[4 * q4 + 3]);
                     }
                 } else if (EPI == kEpiDgelu) {
 #pragma unroll
@@ -359,8 +384,10 @@ __global__ void __launch_bounds__(kThreads, 2)
                     for (int j = 0; j < 32; j++) mh[j] = __uint_as_float(r[j]);
                 }
                 __syncwarp();
-                if (kGelu && g.gout) store_rows_f32(stZ, g.gout, g.N, g.M, rw0, col0, lane);
-                if (kGelu || EPI == kEpiDgelu) {
+                if (kGelu) {
+                    if (g.gout) store_rows_f32(stZ, g.gout, g.N, g.M, rw0, col0, lane);
+                    if (g.htout) store_cols_bf16(stH, g.htout, g.M, rw0, col0, lane);
+                } else if (EPI == kEpiDgelu) {
                     store_rows_bf16(stH, g.hout, g.N, g.M, rw0, col0, lane);
                     if (g.htout) store_cols_bf16(stH, g.htout, g.M, rw0, col0, lane);
                 } else if (EPI == kEpiAtomic) {
@@ -669,6 +696,7 @@ int forward_batch(lpsim_mlp *m, bool training = true) {
             g.w4 = m->P[6];
             g.b4 = m->P[7];
             g.yout = m->y;
+            if (!training) g.hout = nullptr;  // inference needs only y
             TRY((launch_gemm<256, kEpiGeluHead>(a, m->mW[l], g, 1, st)));
         }
         m->launches++;

@@ -281,10 +281,28 @@ int run_steps(lpsim_ctx *c, uint64_t n, bool stop_done, uint64_t *taken) {
             for (uint32_t j = 0; j < todo; j++) TRY(direct_step(c));
         }
         left -= c->k - before;
+        const unsigned long long prog_before = c->last_progress;
         TRY(read_status(c));
         // gridlock watch: vehicles on the network and no crossing, departure or arrival
         unsigned long long prog = c->h_ctr[1] + c->h_ctr[3];
         unsigned long long active = c->h_ctr[4] - c->h_ctr[1];
+        // Idle network: a whole chunk passed with no vehicle on the network and
+        // nothing departing or arriving, so every map, claim and mark is clear
+        // and every trip due so far has arrived.  The steps until the next
+        // departure change nothing: jump to the chunk that holds it.
+        if (active == 0 && prog == prog_before && c->k % c->C == 0 && c->k - before == c->C && left > 0) {
+            auto nx = std::lower_bound(c->dep_sorted.begin(), c->dep_sorted.end(), c->k);
+            if (nx != c->dep_sorted.end()) {
+                const uint64_t target = std::min<uint64_t>((uint64_t)(*nx / c->C) * c->C, c->k + left / c->C * c->C);
+                if (target > c->k) {
+                    left -= target - c->k;
+                    c->k = (uint32_t)target;
+                    c->skipped += target - before - c->C;
+                    CU(cudaMemcpyAsync(c->d.kbase, &c->k, 4, cudaMemcpyHostToDevice, c->stream));
+                    CU(cudaStreamSynchronize(c->stream));
+                }
+            }
+        }
         if (prog != c->last_progress || active == 0) {
             c->last_progress = prog;
             c->stall_steps = 0;
@@ -629,6 +647,7 @@ int load_demand_impl(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, cons
         roff[id + 1] = (uint32_t)(roff[id] + L);
         if (out_vid) out_vid[j] = (uint32_t)id;
     }
+    c->dep_sorted = dep;  // nondecreasing: ids are ranks by departure step
     // departure queues: ids grouped by first edge, ascending within a group
     std::vector<uint32_t> cnt(c->n_edges + 1, 0);
     for (uint64_t id = 0; id < n; id++) cnt[route[roff[id]] + 1]++;

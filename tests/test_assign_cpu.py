@@ -140,3 +140,55 @@ def test_link_times_and_features(A):
     X = a.features(np.ones((ne, 4), np.uint32), np.zeros((ne, 4), np.uint32), lr, np.ones((ne, 4), np.uint32))
     assert X.shape == (ne * 4, 11) and np.all(np.isfinite(X))
     assert abs(X[1, 9] - lr[0, 1]) < 1e-6 and X[4 + 1, 9] == 0.0  # unmeasured cells read 0
+
+
+def test_worst_first_reroute(A):
+    """Per-trip excess from a simulated outcome (gap) and from predicted link
+    times (route_excess); worst-first re-routing moves exactly the requested
+    share, largest relative excess first, never a trip already on its
+    candidate path."""
+    import workloads as W
+    net = W.grid_network(5, 5)
+    dem = W.route(net, W.uniform_demand(net, 300, 4, t_max_s=600.0))
+    n = len(dem["depart_step"])
+    ff = (net["edge_len"] / net["edge_vmax"]).astype(np.float32)
+    tt = np.tile(ff[:, None], (1, 8))
+    tt[::3] *= 3.0
+    bin_steps = 300
+    a = A.Assignment(net, dem, dt=0.5, seed=2)
+    tsp = a.shortest_paths(tt, bin_steps, 300)
+    a.route_excess(tt, bin_steps)
+    # reference: each trip's current route traversed under tt, minus its shortest time
+    off = dem["route_off"].astype(np.int64)
+    exc = np.empty(n)
+    for j in range(n):
+        t0 = float(dem["depart_step"][j]) * 0.5
+        t = t0
+        for e in dem["route_edges"][off[j]:off[j + 1]]:
+            t += float(tt[e, min(max(int(math.floor(t / 150.0)), 0), 7)])
+        exc[j] = t - t0 - tsp[j]
+    before = a.routes()
+    moved = a.reroute_worst(0.1)
+    after = a.routes()
+
+    def route(r, j):
+        return tuple(r["route_edges"][int(r["route_off"][j]):int(r["route_off"][j + 1])])
+    changed = [j for j in range(n) if route(before, j) != route(after, j)]
+    # the candidates: the same engine state moved wholesale
+    b = A.Assignment(net, dem, dt=0.5, seed=2)
+    b.shortest_paths(tt, bin_steps, 300)
+    b.reroute(1.0, 0)
+    cand = b.routes()
+    eligible = [j for j in range(n) if exc[j] > 0 and route(cand, j) != route(before, j)]
+    rel = exc / np.maximum(1.0, tsp)
+    want = min(len(eligible), round(0.1 * n))
+    top = sorted(eligible, key=lambda j: (-rel[j], j))[:want]
+    assert moved == want > 0
+    # same set up to float32 rounding of the excess at the cut
+    assert len(set(changed) ^ set(top)) <= 2
+    assert all(route(after, j) == route(cand, j) for j in changed)
+    # a simulated outcome: the gap call resets the excess from experienced times
+    dep_act = dem["depart_step"].astype(np.uint32)
+    arr = np.full(n, 0xFFFFFFFF, np.uint32)  # nobody arrived: no excess, nothing moves
+    a.gap(dep_act, arr)
+    assert a.reroute_worst(0.5) == 0

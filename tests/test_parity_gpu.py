@@ -105,3 +105,35 @@ def test_reset_replays_identically(grid_day):
     assert_state_equal(s1, g.state())
     assert np.array_equal(t1["arrive"], g.trips()["arrive"])
     assert np.array_equal(l1["inflow"], g.link_stats()["inflow"])
+
+
+@pytest.mark.parametrize("chunk_steps", [384, 42])
+def test_idle_hours_match_oracle(grid_day, chunk_steps):
+    """Two waves of departures eight simulated hours apart: the network
+    empties between them (the library jumps over the idle steps) and every
+    output still matches the oracle, which steps through all of them; so do
+    runs that stop inside the idle stretch and resume."""
+    import oracle as O
+    import workloads as Wk
+    from paper_2406_08496_gb300 import Simulation
+    net, dem = grid_day
+    keep = np.zeros(len(dem["depart_step"]), bool)
+    keep[::4] = True
+    sub = Wk.subset_trips(dem, keep)
+    dep = sub["depart_step"].astype(np.int64)
+    dep[1::2] += 8 * 7200
+    sub["depart_step"] = dep.astype(np.uint32)
+    params = dict(bin_steps=3600, n_bins=20)
+    o = O.Oracle(net, params)
+    o.load_demand(sub)
+    g = Simulation(net, dict(params, chunk_steps=chunk_steps))
+    g.load_demand(sub)
+    for n in (9000, 20000, 10000):  # the second call starts and ends inside the idle stretch
+        o.step(n)
+        g.step(n)
+        assert_state_equal(o.state(), g.state(), f"after {n}")
+    ro = o.run(40000)
+    rg = g.run(40000)
+    for key in ("steps", "veh_steps", "arrived", "active", "waiting", "k"):
+        assert ro[key] == rg[key], (key, ro[key], rg[key])
+    assert_outputs_equal(o, g, n_bins=20)
