@@ -247,22 +247,33 @@ def batch_arm(args, L, torch, rank, world, local):
 
 
 def assignment_arm(args, L, torch):
-    """Plain and surrogate-assisted MSA on the reduced regional case; every
-    gap measured by a full simulation."""
+    """Plain and surrogate-assisted MSA on the reduced regional case (27k
+    nodes, 340k trips, same trips per node as the 2.82M-trip day), each run
+    until the relative gap reaches 1% or for --steps iterations; every gap
+    measured by a full simulation.  value = the surrogate arm's wall time to
+    the 1% gap (null if not reached); both arms' times to 2%, 1.5% and 1%."""
     import workloads as W
     from paper_2406_08496_gb300.assignment import msa
     net, dem = W.assignment_case(scale="small")
+    iters = max(args.steps, 4)
     res = {}
     for mode in ("plain", "surrogate"):
-        r = msa(net, dem, mode, iterations=max(args.steps, 4), target_gap=0.02)
-        res[mode] = {"time_to_2pct_gap_s": r["time_to_target_s"], "final_gap": r["final_gap"],
-                     "wall_s": r["wall_s"], "gaps": [h["gap"] for h in r["history"]]}
-    out = {"metric": "time-to-2%-gap", "value": res["surrogate"]["time_to_2pct_gap_s"], "unit": "s",
-           "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "warmup": 0, "dtype": "f32+bf16",
+        r = msa(net, dem, mode, iterations=iters, target_gap=0.01)
+        hist = [(h["wall_s"], h["gap"]) for h in r["history"] if h["gap"] is not None]
+
+        def hit(th):
+            return next((t for t, g in hist if g <= th), None)
+        res[mode] = {"time_to_1pct_gap_s": hit(0.01), "time_to_1.5pct_gap_s": hit(0.015),
+                     "time_to_2pct_gap_s": hit(0.02), "final_gap": r["final_gap"], "wall_s": r["wall_s"],
+                     "iterations": len(r["history"]), "gaps": [round(g, 5) for _, g in hist],
+                     "gap_wall_s": [round(t, 2) for t, _ in hist]}
+    out = {"metric": "time-to-1%-gap", "value": res["surrogate"]["time_to_1pct_gap_s"], "unit": "s",
+           "higher_is_better": False, "n_gpus": 1, "steps": iters, "warmup": 0, "dtype": "f32+bf16",
            "data": "synthetic", "vs_baseline": None,
            "config": {"workload": "assignment-27k-nodes-340k-trips", "nodes": net["n_nodes"],
-                      "edges": net["n_edges"], "trips": int(len(dem["depart_step"])), "reroute_fraction": 0.1},
-           "arms": res}
+                      "edges": net["n_edges"], "trips": int(len(dem["depart_step"])), "reroute_fraction": 0.1,
+                      "selection": "random", "full_simulation": "every iteration (plain), every 2nd (surrogate)"},
+           "plain_time_to_1pct_gap_s": res["plain"]["time_to_1pct_gap_s"], "arms": res}
     print(json.dumps(out), flush=True)
 
 

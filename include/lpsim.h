@@ -63,6 +63,7 @@ extern "C" {
 
 #define LPSIM_F_NO_SORT 1u
 #define LPSIM_F_CHECK_CELLS 2u
+#define LPSIM_F_NO_LIGHT 4u
 
 typedef struct lpsim_ctx lpsim_ctx;
 
@@ -89,7 +90,9 @@ typedef struct lpsim_params {
                                 vehicles and no departure, crossing or arrival (0 = never) */
     uint32_t flags;       /* LPSIM_F_NO_SORT: compact without sorting; LPSIM_F_CHECK_CELLS: check that
                              every lane-map write lands on an empty cell (LPSIM_E_INVARIANT otherwise;
-                             costs a load per write); other bits must be 0 */
+                             costs a load per write); LPSIM_F_NO_LIGHT: never run a chunk in the
+                             single-block light-load kernel (results are the same either way);
+                             other bits must be 0 */
 } lpsim_params;
 
 /* Road network.  Edge e runs edge_src[e] -> edge_dst[e], is edge_len_m[e]

@@ -70,11 +70,13 @@ int lpsim_assign_reroute(lpsim_assign *a, double fraction, uint32_t iteration, u
  * experienced times instead (0 for trips that did not arrive). */
 int lpsim_assign_route_excess(lpsim_assign *a, const float *tt, uint32_t n_bins, uint32_t bin_steps);
 
-/* Method of successive averages, worst first: the round(fraction * n_trips)
- * trips with the largest relative excess (excess / shortest time; only trips
- * whose candidate route differs and whose excess is positive; ties to the
- * lower trip index) move to their candidate route.  *n_changed = trips moved. */
-int lpsim_assign_reroute_worst(lpsim_assign *a, double fraction, uint64_t *n_changed);
+/* Method of successive averages, worst first: up to round(fraction * n_trips)
+ * trips with the largest relative excess (excess / shortest time, the
+ * shortest time counted as at least 1 s) move to their candidate route; only
+ * trips whose candidate differs and whose relative excess is above
+ * min_rel_excess (an indifference band, >= 0) are eligible; ties go to the
+ * lower trip index.  *n_changed = trips moved. */
+int lpsim_assign_reroute_worst(lpsim_assign *a, double fraction, double min_rel_excess, uint64_t *n_changed);
 
 /* Current routes (route_off: n_trips + 1 entries; route_edges: capacity
  * entries, at least lpsim_assign_route_length()). */

@@ -30,7 +30,7 @@ def _lib():
         lib.lpsim_assign_gap.argtypes = [P, P, P, P, P]
         lib.lpsim_assign_reroute.argtypes = [P, ctypes.c_double, ctypes.c_uint32, P]
         lib.lpsim_assign_route_excess.argtypes = [P, P, ctypes.c_uint32, ctypes.c_uint32]
-        lib.lpsim_assign_reroute_worst.argtypes = [P, ctypes.c_double, P]
+        lib.lpsim_assign_reroute_worst.argtypes = [P, ctypes.c_double, ctypes.c_double, P]
         lib.lpsim_assign_route_length.argtypes = [P]
         lib.lpsim_assign_route_length.restype = ctypes.c_uint64
         lib.lpsim_assign_get_routes.argtypes = [P, P, P, ctypes.c_uint64]
@@ -96,9 +96,9 @@ class Assignment:
         tt = np.ascontiguousarray(tt, dtype=np.float32)
         _check(self.lib, self.lib.lpsim_assign_route_excess(self.h, _p(tt), tt.shape[1], bin_steps))
 
-    def reroute_worst(self, fraction: float) -> int:
+    def reroute_worst(self, fraction: float, min_rel_excess: float = 0.0) -> int:
         n = ctypes.c_uint64()
-        _check(self.lib, self.lib.lpsim_assign_reroute_worst(self.h, fraction, ctypes.byref(n)))
+        _check(self.lib, self.lib.lpsim_assign_reroute_worst(self.h, fraction, min_rel_excess, ctypes.byref(n)))
         return n.value
 
     def routes(self) -> dict:
@@ -154,7 +154,7 @@ class Assignment:
 def msa(net: dict, dem: dict, mode: str = "plain", iterations: int = 10, fraction: float = 0.1,
         target_gap: float = 0.01, sim_params: dict | None = None, bin_steps: int = 1800, n_bins: int = 96,
         period_steps: int = 3600, max_steps: int = 300_000, surrogate_steps: int = 400, surrogate_batch: int = 8192,
-        seed: int = 0, select: str = "worst", log=None) -> dict:
+        seed: int = 0, select: str = "random", min_rel_excess: float = 0.0, log=None) -> dict:
     """Method of successive averages.  plain: every iteration simulates the
     current routes, measures the relative gap and moves `fraction` of the
     trips to their time-dependent shortest paths under the simulated link
@@ -163,16 +163,17 @@ def msa(net: dict, dem: dict, mode: str = "plain", iterations: int = 10, fractio
     simulation, predict the link times of the current routes with the
     surrogate (inflows from loading the routes with the last simulated
     times) and re-route under the prediction.  Every reported gap is
-    measured by a full simulation.  select: which trips move -- "worst" (the
-    fraction with the largest relative excess of their route over the
-    shortest path, from the simulation or, in surrogate iterations, from the
-    prediction) or "random" (each trip with probability fraction).  Returns
+    measured by a full simulation.  select: which trips move -- "random"
+    (each trip with probability fraction, seeded) or "worst" (the fraction
+    with the largest relative excess of their route over the shortest path
+    under the iteration's link times, measured or predicted; only trips more
+    than min_rel_excess worse than their shortest path).  Returns
     the iteration history and the wall time to reach target_gap (None if
     never reached)."""
     assert mode in ("plain", "surrogate") and select in ("worst", "random")
 
     def move(it):
-        return A.reroute_worst(fraction) if select == "worst" else A.reroute(fraction, it)
+        return A.reroute_worst(fraction, min_rel_excess) if select == "worst" else A.reroute(fraction, it)
 
     params = dict(bin_steps=bin_steps, n_bins=n_bins)
     params.update(sim_params or {})
@@ -198,6 +199,10 @@ def msa(net: dict, dem: dict, mode: str = "plain", iterations: int = 10, fractio
             tt, logratio = A.link_times(ls["tt_sum"], ls["tt_cnt"])
             A.shortest_paths(tt, bin_steps, period_steps)
             rg, used = A.gap(tr["depart"][vid], tr["arrive"][vid])
+            if select == "worst":
+                # rank trips by their route's excess under the measured link
+                # times (as the surrogate iterations do under predicted ones)
+                A.route_excess(tt, bin_steps)
             now = time.perf_counter() - t_start
             rec = dict(iteration=it, kind="simulation", gap=rg, trips_used=used, veh_steps=run["veh_steps"],
                        wall_s=now, iter_s=time.perf_counter() - t0, sim_s=t_sim,

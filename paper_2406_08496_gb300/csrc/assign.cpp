@@ -51,6 +51,29 @@ struct lpsim_assign {
 
 namespace {
 
+// f(first, last) over fixed-size pieces of [0, n), spread over the host's
+// threads; piece boundaries do not depend on the thread count, so anything
+// reduced per piece and then added in piece order is reproducible.
+constexpr uint64_t kPiece = 16384;
+
+template <class F>
+void parallel_pieces(uint64_t n, F &&f) {
+    const uint64_t np = (n + kPiece - 1) / kPiece;
+    const uint64_t hw = std::max(1u, std::thread::hardware_concurrency());
+    const unsigned nt = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(np, hw));
+    if (nt <= 1) {
+        for (uint64_t p = 0; p < np; p++) f(p * kPiece, std::min(n, (p + 1) * kPiece), p);
+        return;
+    }
+    std::atomic<uint64_t> next{0};
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; t++)
+        th.emplace_back([&] {
+            for (uint64_t p; (p = next.fetch_add(1)) < np;) f(p * kPiece, std::min(n, (p + 1) * kPiece), p);
+        });
+    for (auto &x : th) x.join();
+}
+
 struct TD {
     const lpsim_assign *a;
     const float *tt;   // n_edges x n_bins, seconds
@@ -212,17 +235,27 @@ int lpsim_assign_shortest_paths(lpsim_assign *a, const float *tt, uint32_t n_bin
 int lpsim_assign_gap(lpsim_assign *a, const uint32_t *depart_actual, const uint32_t *arrive_step, double *rg,
                      uint64_t *n_used) {
     if (!a || !depart_actual || !arrive_step || !rg) return fail(LPSIM_E_INVALID_ARG, "NULL argument");
+    const uint64_t np = (a->n + kPiece - 1) / kPiece;
+    std::vector<double> pnum(np, 0.0), pden(np, 0.0);
+    std::vector<uint64_t> pused(np, 0);
+    parallel_pieces(a->n, [&](uint64_t j0, uint64_t j1, uint64_t p) {
+        for (uint64_t j = j0; j < j1; j++) {
+            a->excess[j] = 0.0f;
+            if (arrive_step[j] == 0xFFFFFFFFu || depart_actual[j] == 0xFFFFFFFFu) continue;
+            // experienced time: from the planned departure (waiting to enter counts) to arrival
+            const double texp = (double)(arrive_step[j] - a->dep[j]) * a->dt;
+            pnum[p] += texp - a->tsp[j];
+            pden[p] += a->tsp[j];
+            a->excess[j] = (float)(texp - a->tsp[j]);
+            pused[p]++;
+        }
+    });
     double num = 0.0, den = 0.0;
     uint64_t used = 0;
-    for (uint64_t j = 0; j < a->n; j++) {
-        a->excess[j] = 0.0f;
-        if (arrive_step[j] == 0xFFFFFFFFu || depart_actual[j] == 0xFFFFFFFFu) continue;
-        // experienced time: from the planned departure (waiting to enter counts) to arrival
-        const double texp = (double)(arrive_step[j] - a->dep[j]) * a->dt;
-        num += texp - a->tsp[j];
-        den += a->tsp[j];
-        a->excess[j] = (float)(texp - a->tsp[j]);
-        used++;
+    for (uint64_t p = 0; p < np; p++) {
+        num += pnum[p];
+        den += pden[p];
+        used += pused[p];
     }
     *rg = den > 0 ? num / den : 0.0;
     if (n_used) *n_used = used;
@@ -248,24 +281,29 @@ int lpsim_assign_reroute(lpsim_assign *a, double fraction, uint32_t iteration, u
 int lpsim_assign_route_excess(lpsim_assign *a, const float *tt, uint32_t n_bins, uint32_t bin_steps) {
     if (!a || !tt || n_bins == 0 || bin_steps == 0) return fail(LPSIM_E_INVALID_ARG, "bad argument");
     TD td{a, tt, n_bins, (float)bin_steps * a->dt};
-    for (uint64_t j = 0; j < a->n; j++) {
-        const double t0 = (double)a->dep[j] * a->dt;
-        double t = t0;
-        for (uint32_t e : a->route[j]) t += td.cost(e, t);
-        a->excess[j] = (float)(t - t0 - a->tsp[j]);
-    }
+    parallel_pieces(a->n, [&](uint64_t j0, uint64_t j1, uint64_t) {
+        for (uint64_t j = j0; j < j1; j++) {
+            const double t0 = (double)a->dep[j] * a->dt;
+            double t = t0;
+            for (uint32_t e : a->route[j]) t += td.cost(e, t);
+            a->excess[j] = (float)(t - t0 - a->tsp[j]);
+        }
+    });
     return LPSIM_OK;
 }
 
-int lpsim_assign_reroute_worst(lpsim_assign *a, double fraction, uint64_t *n_changed) {
-    if (!a || !(fraction >= 0.0 && fraction <= 1.0)) return fail(LPSIM_E_INVALID_ARG, "bad argument");
-    // trips whose candidate differs from their route, by relative excess
-    // (largest first, ties to the lower index)
+int lpsim_assign_reroute_worst(lpsim_assign *a, double fraction, double min_rel_excess, uint64_t *n_changed) {
+    if (!a || !(fraction >= 0.0 && fraction <= 1.0) || !(min_rel_excess >= 0.0))
+        return fail(LPSIM_E_INVALID_ARG, "bad argument");
+    auto rel = [&](uint64_t j) { return (double)a->excess[j] / std::max(1.0, (double)a->tsp[j]); };
+    // trips whose candidate differs from their route and whose route is worse
+    // than it by more than min_rel_excess, by relative excess (largest first,
+    // ties to the lower index)
     std::vector<uint64_t> pick;
     for (uint64_t j = 0; j < a->n; j++)
-        if (!a->cand[j].empty() && a->excess[j] > 0.0f && a->cand[j] != a->route[j]) pick.push_back(j);
+        if (!a->cand[j].empty() && a->excess[j] > 0.0f && rel(j) > min_rel_excess && a->cand[j] != a->route[j])
+            pick.push_back(j);
     const uint64_t want = std::min<uint64_t>(pick.size(), (uint64_t)std::llround(fraction * (double)a->n));
-    auto rel = [&](uint64_t j) { return (double)a->excess[j] / std::max(1.0, (double)a->tsp[j]); };
     std::partial_sort(pick.begin(), pick.begin() + want, pick.end(), [&](uint64_t x, uint64_t y) {
         const double rx = rel(x), ry = rel(y);
         return rx != ry ? rx > ry : x < y;
@@ -299,14 +337,17 @@ int lpsim_assign_load(const lpsim_assign *a, const float *tt, uint32_t n_bins, u
     if (!a || !tt || !inflow || n_bins == 0 || bin_steps == 0) return fail(LPSIM_E_INVALID_ARG, "bad argument");
     TD td{a, tt, n_bins, (float)bin_steps * a->dt};
     std::memset(inflow, 0, (size_t)a->n_edges * n_bins * 4);
-    for (uint64_t j = 0; j < a->n; j++) {
-        double t = (double)a->dep[j] * a->dt;
-        for (uint32_t e : a->route[j]) {
-            int64_t b = (int64_t)std::floor(t / td.bin_s);
-            if (b >= 0 && b < (int64_t)n_bins) inflow[(size_t)e * n_bins + b]++;
-            t += td.cost(e, t);
+    parallel_pieces(a->n, [&](uint64_t j0, uint64_t j1, uint64_t) {
+        for (uint64_t j = j0; j < j1; j++) {
+            double t = (double)a->dep[j] * a->dt;
+            for (uint32_t e : a->route[j]) {
+                int64_t b = (int64_t)std::floor(t / td.bin_s);
+                if (b >= 0 && b < (int64_t)n_bins)
+                    __atomic_fetch_add(&inflow[(size_t)e * n_bins + b], 1u, __ATOMIC_RELAXED);
+                t += td.cost(e, t);
+            }
         }
-    }
+    });
     return LPSIM_OK;
 }
 
@@ -314,36 +355,38 @@ int lpsim_assign_features(const lpsim_assign *a, uint32_t n_bins, const uint32_t
                           const float *prev_log_ratio, const uint32_t *prev_inflow, float *X, uint32_t n_features) {
     if (!a || !inflow || !occ || !prev_log_ratio || !prev_inflow || !X || n_features != LPSIM_SURROGATE_FEATURES)
         return fail(LPSIM_E_INVALID_ARG, "bad argument");
-    for (uint32_t e = 0; e < a->n_edges; e++) {
-        const float cells = std::max(1.0f, std::ceil(a->len[e])) * (float)a->lanes[e];
-        // mean occupancy density of the downstream links
-        const uint32_t v = a->dst[e];
-        for (uint32_t b = 0; b < n_bins; b++) {
-            float *x = X + ((size_t)e * n_bins + b) * n_features;
-            x[0] = a->len[e] / 1000.0f;
-            x[1] = (float)a->lanes[e] / 4.0f;
-            x[2] = a->vmax[e] / 30.0f;
-            for (int q = 0; q < 4; q++) {
-                const int64_t bb = (int64_t)b - q;
-                const float f = bb >= 0 ? (float)inflow[(size_t)e * n_bins + bb] : 0.0f;
-                x[3 + q] = std::log1p(f / (float)a->lanes[e]) / 4.0f;
+    parallel_pieces(a->n_edges, [&](uint64_t e0, uint64_t e1, uint64_t) {
+        for (uint32_t e = (uint32_t)e0; e < (uint32_t)e1; e++) {
+            const float cells = std::max(1.0f, std::ceil(a->len[e])) * (float)a->lanes[e];
+            // mean occupancy density of the downstream links
+            const uint32_t v = a->dst[e];
+            for (uint32_t b = 0; b < n_bins; b++) {
+                float *x = X + ((size_t)e * n_bins + b) * n_features;
+                x[0] = a->len[e] / 1000.0f;
+                x[1] = (float)a->lanes[e] / 4.0f;
+                x[2] = a->vmax[e] / 30.0f;
+                for (int q = 0; q < 4; q++) {
+                    const int64_t bb = (int64_t)b - q;
+                    const float f = bb >= 0 ? (float)inflow[(size_t)e * n_bins + bb] : 0.0f;
+                    x[3 + q] = std::log1p(f / (float)a->lanes[e]) / 4.0f;
+                }
+                x[7] = 10.0f * (float)occ[(size_t)e * n_bins + b] / cells;
+                float down = 0.0f;
+                uint32_t nd = 0;
+                for (uint32_t j = a->out_off[v]; j < a->out_off[v + 1]; j++) {
+                    const uint32_t f = a->out_edge[j];
+                    const float fc = std::max(1.0f, std::ceil(a->len[f])) * (float)a->lanes[f];
+                    down += (float)occ[(size_t)f * n_bins + b] / fc;
+                    nd++;
+                }
+                x[8] = nd ? 10.0f * down / (float)nd : 0.0f;
+                // the reference simulation of the same (edge, bin): its travel-time ratio and inflow
+                const size_t i = (size_t)e * n_bins + b;
+                x[9] = std::isfinite(prev_log_ratio[i]) ? prev_log_ratio[i] : 0.0f;
+                x[10] = std::log1p((float)prev_inflow[i] / (float)a->lanes[e]) / 4.0f;
             }
-            x[7] = 10.0f * (float)occ[(size_t)e * n_bins + b] / cells;
-            float down = 0.0f;
-            uint32_t nd = 0;
-            for (uint32_t j = a->out_off[v]; j < a->out_off[v + 1]; j++) {
-                const uint32_t f = a->out_edge[j];
-                const float fc = std::max(1.0f, std::ceil(a->len[f])) * (float)a->lanes[f];
-                down += (float)occ[(size_t)f * n_bins + b] / fc;
-                nd++;
-            }
-            x[8] = nd ? 10.0f * down / (float)nd : 0.0f;
-            // the reference simulation of the same (edge, bin): its travel-time ratio and inflow
-            const size_t i = (size_t)e * n_bins + b;
-            x[9] = std::isfinite(prev_log_ratio[i]) ? prev_log_ratio[i] : 0.0f;
-            x[10] = std::log1p((float)prev_inflow[i] / (float)a->lanes[e]) / 4.0f;
         }
-    }
+    });
     return LPSIM_OK;
 }
 

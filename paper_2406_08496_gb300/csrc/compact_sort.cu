@@ -129,20 +129,13 @@ __device__ __forceinline__ void tile_ranks(const uint8_t *flag, uint32_t t, uint
 }
 
 __device__ __forceinline__ void copy_slot(const Slots &a, uint32_t s, const Slots &b, uint32_t o, int par) {
+    reinterpret_cast<uint4 *>(b.es + o)[0] = reinterpret_cast<const uint4 *>(a.es + s)[0];
+    reinterpret_cast<uint4 *>(b.es + o)[1] = reinterpret_cast<const uint4 *>(a.es + s)[1];
     b.id[o] = a.id[s];
-    b.e[o] = a.e[s];
-    b.rpos[o] = a.rpos[s];
     b.rlast[o] = a.rlast[s];
-    b.tent[o] = a.tent[s];
     b.pcell[o] = a.pcell[s];
     b.imark[o] = a.imark[s];
-    b.base[o] = a.base[s];
     b.cprev[o] = a.cprev[s];
-    b.en[o] = a.en[s];
-    b.sg[o] = a.sg[s];
-    b.sph[o] = a.sph[s];
-    b.len[o] = a.len[s];
-    b.v0[o] = a.v0[s];
     b.lane[o] = a.lane[s];
     b.tlc[o] = a.tlc[s];
     b.flag[o] = kLive;
@@ -182,7 +175,7 @@ __global__ void __launch_bounds__(kBlock) scatter_keys(Dev d, SortWork w, uint32
         for (int j = 0; j < kItems; j++) {
             if (!live[j]) continue;
             uint32_t s = t * kTile + threadIdx.x * kItems + j;
-            w.key[0][off + rank[j]] = d.s.base[s] + (uint32_t)x[s];
+            w.key[0][off + rank[j]] = d.s.es[s].base + (uint32_t)x[s];
             w.perm[0][off + rank[j]] = s;
         }
     }

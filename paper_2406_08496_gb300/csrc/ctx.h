@@ -50,6 +50,9 @@ struct lpsim_ctx {
     uint64_t stall_steps = 0;
     unsigned long long last_progress = 0;
     std::vector<uint32_t> dep_sorted;  // departure step by vehicle id (nondecreasing)
+    uint32_t *small_list = nullptr;    // light-load chunks: origin edges that can act, and their count
+    uint32_t *small_n = nullptr;
+    uint64_t light_chunks = 0;
     uint64_t skipped = 0;              // idle steps jumped over (nothing on the network)
     // device buffers whose contents change while stepping (snapshot / restore)
     std::vector<std::pair<void *, size_t>> mut;

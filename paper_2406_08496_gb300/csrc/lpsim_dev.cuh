@@ -27,6 +27,11 @@ constexpr uint8_t kWaiting = 0;
 constexpr uint8_t kActive = 1;
 constexpr uint8_t kArrived = 2;
 
+// light-load mode: one block of kSmallBlock threads runs a whole chunk when at
+// most kSmallMax trips can be on the network or waiting during it
+constexpr int kSmallBlock = 1024;
+constexpr uint32_t kSmallMax = 1536;
+
 // device error bits
 constexpr uint32_t kErrCellTaken = 1u;   // a lane-map cell written twice in one step
 constexpr uint32_t kErrSlotOverflow = 2u;
@@ -74,26 +79,57 @@ struct __align__(16) QRec {
     uint32_t h, dep, r0, r1;
 };
 
-// Vehicle slots (structure of arrays).  x and v are double-buffered by step
-// parity: step k reads x[k&1] and writes x[(k+1)&1].  What the vehicle needs
-// from its current edge (lane-row offset, length, speed limit, the signal at
-// its end, the next edge of the route, the target lane) is copied into the
-// slot when it enters the edge, so the common path reads the slot and the
-// map only, and a crossing reads one edge record more.
+// What a vehicle copies when it enters an edge, plus its lane row (which a
+// lane change moves): one 32-byte record per slot, read with two 16-byte
+// loads and rewritten on entry with two 16-byte stores into one sector.
+struct __align__(32) EdgeState {
+    uint32_t base;     // lane-map offset of cell 0 of the current lane
+    uint32_t e;        // current edge
+    uint32_t rpos;     // route position of the current edge
+    uint32_t tent;     // step the vehicle entered the current edge
+    uint32_t en;       // next edge of the route, kNone on the last edge
+    uint32_t sg;       // green steps of the signal at the end of the current edge (0 = none)
+    float v0;          // speed limit of the current edge
+    uint16_t len;      // cells per lane of the current edge
+    uint16_t sph;      // phases of that signal | phase of the current edge << 8
+};
+
+__device__ __forceinline__ EdgeState load_es(const EdgeState *p) {
+    const uint4 a = reinterpret_cast<const uint4 *>(p)[0], b = reinterpret_cast<const uint4 *>(p)[1];
+    EdgeState r;
+    r.base = a.x;
+    r.e = a.y;
+    r.rpos = a.z;
+    r.tent = a.w;
+    r.en = b.x;
+    r.sg = b.y;
+    r.v0 = __uint_as_float(b.z);
+    r.len = (uint16_t)(b.w & 0xFFFFu);
+    r.sph = (uint16_t)(b.w >> 16);
+    return r;
+}
+
+__device__ __forceinline__ void store_es(EdgeState *p, const EdgeState &r) {
+    reinterpret_cast<uint4 *>(p)[0] = make_uint4(r.base, r.e, r.rpos, r.tent);
+    reinterpret_cast<uint4 *>(p)[1] =
+        make_uint4(r.en, r.sg, __float_as_uint(r.v0), (uint32_t)r.len | ((uint32_t)r.sph << 16));
+}
+
+// Vehicle slots.  x and v are double-buffered by step parity: step k reads
+// x[k&1] and writes x[(k+1)&1].  What the vehicle needs from its current edge
+// (lane-row offset, length, speed limit, the signal at its end, the next edge
+// of the route) is copied into its EdgeState when it enters the edge, so the
+// common path reads the slot and the map only, and a crossing reads one edge
+// record more.
 struct Slots {
+    EdgeState *es;
     // persistent
-    uint32_t *id, *e, *rpos, *rlast, *tent;
+    uint32_t *id, *rlast;
     uint32_t *pcell;   // cell of the previous step (erased this step), kNone
     uint32_t *imark;   // intent mark of the previous step (cleared this step), kNone
-    uint32_t *base;    // lane-map offset of cell 0 of the current lane
     uint32_t *cprev;   // claim slot won at the previous step (reset this step), kNone
-    uint32_t *en;      // next edge of the route, kNone on the last edge
-    uint32_t *sg;      // green steps of the signal at the end of the current edge (0 = none)
-    uint16_t *sph;     // phases of that signal | phase of the current edge << 8
-    uint16_t *len;     // cells per lane of the current edge
     uint8_t *lane, *flag;
     uint8_t *tlc;      // target lane of the movement after the current edge (kNoLane on the last edge)
-    float *v0;         // speed limit of the current edge
     float *x[2], *v[2];
     uint8_t *act;      // per-step scratch: what the vehicle did this step
 };
@@ -184,6 +220,10 @@ struct Dev {
 // parity buffers and the rotating lane maps without waiting for *kbase
 void launch_phase(const Dev &d, int phase, uint32_t koff, uint32_t kph, int grid, int block, cudaStream_t st);
 void launch_chunk_end(const Dev &d, uint32_t steps, cudaStream_t st);
+// steps [k0, k0 + nsteps) in one block (light load); olist: n_org scratch
+// entries, no: one device counter
+cudaError_t launch_small(const Dev &d, uint32_t k0, uint32_t nsteps, uint32_t *olist, uint32_t *no,
+                         cudaStream_t st);
 
 // compaction (and optional sort by lane-map cell) of the slots after step k;
 // src/dst slot sets; writes *n_slots

@@ -79,7 +79,7 @@ int check_params(const lpsim_params *p) {
     if (p->bin_steps == 0 && p->n_bins != 0) return fail(LPSIM_E_INVALID_ARG, "n_bins without bin_steps");
     if (p->block_size && p->block_size != 128 && p->block_size != 256 && p->block_size != 512)
         return fail(LPSIM_E_INVALID_ARG, "block_size must be 0, 128, 256 or 512");
-    if (p->flags & ~3u) return fail(LPSIM_E_INVALID_ARG, "unknown flag bits");
+    if (p->flags & ~7u) return fail(LPSIM_E_INVALID_ARG, "unknown flag bits");
     if (p->sort_period > 256) return fail(LPSIM_E_INVALID_ARG, "sort_period must be at most 256");
     return LPSIM_OK;
 }
@@ -91,23 +91,15 @@ int upload(lpsim_ctx *c, void *dst, const void *src, size_t bytes) {
 
 int alloc_slots(lpsim_ctx *c, Slots &s, uint32_t cap) {
     // persistent fields (kept by snapshots)
+    TRY(dnew_mut(c, s.es, cap));
     TRY(dnew_mut(c, s.id, cap));
-    TRY(dnew_mut(c, s.e, cap));
-    TRY(dnew_mut(c, s.rpos, cap));
     TRY(dnew_mut(c, s.rlast, cap));
-    TRY(dnew_mut(c, s.tent, cap));
     TRY(dnew_mut(c, s.pcell, cap));
     TRY(dnew_mut(c, s.imark, cap));
     TRY(dnew_mut(c, s.lane, cap));
     TRY(dnew_mut(c, s.flag, cap));
     TRY(dnew_mut(c, s.tlc, cap));
-    TRY(dnew_mut(c, s.base, cap));
     TRY(dnew_mut(c, s.cprev, cap));
-    TRY(dnew_mut(c, s.len, cap));
-    TRY(dnew_mut(c, s.v0, cap));
-    TRY(dnew_mut(c, s.en, cap));
-    TRY(dnew_mut(c, s.sg, cap));
-    TRY(dnew_mut(c, s.sph, cap));
     for (int i = 0; i < 2; i++) {
         TRY(dnew_mut(c, s.x[i], cap));
         TRY(dnew_mut(c, s.v[i], cap));
@@ -263,11 +255,39 @@ int chunk(lpsim_ctx *c) {
     return LPSIM_OK;
 }
 
+// Light load: at most kSmallMax trips can be on the network or waiting in
+// the chunk starting at step k (trips due before its end minus those arrived;
+// h_ctr is current).  Kernel timing measures the grid-wide kernels, so it
+// keeps them.
+bool light_chunk_ok(const lpsim_ctx *c) {
+    if ((c->p.flags & LPSIM_F_NO_LIGHT) || c->timing) return false;
+    const uint64_t due = (uint64_t)(std::lower_bound(c->dep_sorted.begin(), c->dep_sorted.end(), c->k + c->C) -
+                                    c->dep_sorted.begin());
+    return due <= c->h_ctr[1] + kSmallMax;
+}
+
+// One chunk in the light-load kernel, then the compaction that closes every
+// chunk and the step-counter update.
+int light_chunk(lpsim_ctx *c) {
+    Dev d = c->d;
+    d.s = c->sets[c->cur];
+    CU(launch_small(d, c->k, c->C, c->small_list, c->small_n, c->stream));
+    launch_compact(d, c->sets[c->cur ^ 1], c->w, c->C - 1, c->sort, c->grid, c->stream);
+    c->cur ^= 1;
+    launch_chunk_end(c->d, c->C, c->stream);
+    CU(cudaGetLastError());
+    c->launches += 3 + (c->sort ? 3 + 3ull * ((c->w.key_bits + 7) / 8) + 1 : 3);
+    c->light_chunks++;
+    c->k += c->C;
+    return LPSIM_OK;
+}
+
 // Run up to n steps; stop early once every trip has arrived (if stop_done).
 // Returns steps actually taken in *taken.
 int run_steps(lpsim_ctx *c, uint64_t n, bool stop_done, uint64_t *taken) {
     const uint32_t k0 = c->k;
     uint64_t left = n;
+    TRY(read_status(c));
     while (left > 0) {
         if (stop_done) {
             TRY(read_status(c));
@@ -275,7 +295,10 @@ int run_steps(lpsim_ctx *c, uint64_t n, bool stop_done, uint64_t *taken) {
         }
         uint64_t before = c->k;
         if (c->k % c->C == 0 && left >= c->C) {
-            TRY(chunk(c));
+            if (light_chunk_ok(c))
+                TRY(light_chunk(c));
+            else
+                TRY(chunk(c));
         } else {
             uint32_t todo = (uint32_t)std::min<uint64_t>(left, c->k % c->C == 0 ? left : c->C - c->k % c->C);
             for (uint32_t j = 0; j < todo; j++) TRY(direct_step(c));
@@ -701,6 +724,8 @@ int load_demand_impl(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, cons
     TRY(dnew(c, c->org_hd0, norg));
     TRY(dnew_mut(c, d.dprev, norg));
     for (int i = 0; i < 2; i++) TRY(dnew(c, d.dep_rec[i], norg));
+    TRY(dnew(c, c->small_list, std::max<uint32_t>(norg, 1u)));
+    TRY(dnew(c, c->small_n, 4));
     // slots: live vehicles plus the holes left between compactions by
     // arrivals and by departures that lost an entry conflict
     const uint64_t cap64 = n + 256ull * norg + 1024;

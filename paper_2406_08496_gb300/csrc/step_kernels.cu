@@ -208,240 +208,284 @@ __device__ __forceinline__ uint32_t pick_entry_lane(uint32_t empty, uint32_t nl,
     return kNone;
 }
 
+// The buffers of step k (parity and map rotation from kph, any number
+// congruent to k modulo 6).
+struct StepView {
+    uint32_t k, par;
+    const uint8_t *Mc;
+    uint8_t *Mn, *Mo;  // next map; map of step k-1 (erased cell by cell)
+    uint8_t *Iw, *Io;  // intent marks of step k; of step k-1 (cleared)
+    uint32_t *claim, *claim_old;  // entry claims of step k; those won at step k-1 (reset)
+    const float *xc, *vc;
+    float *xw, *vw;
+    bool sample;  // occupancy sample taken at this step
+};
+
+__device__ __forceinline__ StepView step_view(const Dev &d, uint32_t k, uint32_t kph) {
+    StepView w;
+    const uint32_t par = kph & 1u, r3 = kph % 3u;
+    w.k = k;
+    w.par = par;
+    w.Mc = d.map[r3];
+    w.Mn = d.map[r3 == 2u ? 0u : r3 + 1u];
+    w.Mo = d.map[r3 == 0u ? 2u : r3 - 1u];
+    w.Iw = d.imap[par];
+    w.Io = d.imap[par ^ 1u];
+    w.claim = d.claim[par];
+    w.claim_old = d.claim[par ^ 1u];
+    w.xc = d.s.x[par];
+    w.vc = d.s.v[par];
+    w.xw = d.s.x[par ^ 1u];
+    w.vw = d.s.v[par ^ 1u];
+    w.sample = d.m.bin_steps && (k % d.m.bin_steps == 0) && (k / d.m.bin_steps < d.m.n_bins);
+    return w;
+}
+
+// Origin edge j: reset the claim its departure won last step; ask for a
+// departure of the queue head once its step has come.
+__device__ __forceinline__ void p1_origin(const Dev &d, const StepView &w, uint32_t j) {
+    const uint32_t k = w.k, par = w.par;
+    const uint8_t *Mc = w.Mc;
+    uint32_t *claim = w.claim, *claim_old = w.claim_old;
+    const uint32_t dp = d.dprev[j];
+    const QRec hd = d.org_hd[j];
+    const EdgeRec er = d.org_rec[j];
+    const uint32_t e0 = d.org_edge[j];
+    const uint32_t qoff = d.org_qoff[j], qhead = d.org_head[j], qend = d.org_qend[j];
+    if (dp != kNone) {
+        claim_old[dp] = kNone;
+        d.dprev[j] = kNone;
+    }
+    if (hd.h != kNone && hd.dep <= k) {
+        const RouteRec rr = d.rrec[hd.r0];
+        const uint32_t nxt = hd.r0 + 1 < hd.r1 ? d.route[hd.r0 + 1] : kNone;
+        const uint32_t so = d.slot_off[e0];
+        const uint32_t l = pick_entry_lane(entry_cells(Mc, er), er.lanes, rr.tl);
+        if (l != kNone) {
+            atomicMin(&claim[so + l], hd.h);
+            DepRec dr;
+            dr.j = j;
+            dr.slot = so + l;
+            dr.h = hd.h;
+            dr.r0 = hd.r0;
+            dr.r1 = hd.r1;
+            dr.qoff = qoff;
+            dr.qhead = qhead;
+            dr.qend = qend;
+            dr.base = er.moff + l * row_stride(er.len);
+            dr.e0 = e0;
+            dr.nen = nxt;
+            dr.nsg = rr.green;
+            dr.v0 = er.v0;
+            dr.len = er.len;
+            dr.nsph = (uint16_t)(rr.nphase | (rr.arank << 8));
+            dr.lane = (uint8_t)l;
+            dr.tlc = rr.tl;
+            d.dep_rec[par][warp_append(&d.counts[4 + par])] = dr;
+        }
+    }
+}
+
+// Slot s (every field loaded in one round trip, together with whatever the
+// caller loaded just before); false once s is past the slot count n.
+__device__ __forceinline__ bool p1_slot(const Dev &d, const StepView &w, uint32_t s, uint32_t n, uint32_t &live,
+                                        uint32_t &arrived) {
+    const uint32_t k = w.k, par = w.par;
+    const uint8_t *Mc = w.Mc;
+    uint8_t *Mn = w.Mn, *Mo = w.Mo, *Iw = w.Iw, *Io = w.Io;
+    uint32_t *claim = w.claim, *claim_old = w.claim_old;
+    const float *xc = w.xc, *vc = w.vc;
+    float *xw = w.xw, *vw = w.vw;
+    const bool sample = w.sample;
+    const Model &m = d.m;
+    // every slot field, loaded together (one memory round trip, shared
+    // with the loads of the step number and the slot count)
+    const uint8_t flag = d.s.flag[s];
+    const uint32_t pc = d.s.pcell[s];
+    const uint32_t im = d.s.imark[s];
+    const uint32_t cp = d.s.cprev[s];
+    const float x = xc[s], v = vc[s];
+    const EdgeState es = load_es(d.s.es + s);
+    const uint32_t base = es.base;
+    const uint32_t len = es.len;
+    const float v0 = es.v0;
+    const uint32_t en = es.en;
+    const uint32_t G = es.sg;
+    const uint32_t ph = es.sph;
+    const uint32_t tl = d.s.tlc[s];  // kNoLane on the last edge of the route
+    const uint32_t ln = d.s.lane[s];
+    const uint32_t id = d.s.id[s];
+    const uint32_t e = es.e;
+    const uint32_t rpos = es.rpos, rlast = d.s.rlast[s];
+    const uint32_t tent = es.tent;
+    loads_issued();
+    if (s >= n) return false;
+    if (flag == kDead) return true;
+    if (pc != kNone) Mo[pc] = kEmpty;
+    if (im != kNone) {
+        Io[im] = 0;
+        d.s.imark[s] = kNone;
+    }
+    if (cp != kNone) {
+        claim_old[cp] = kNone;
+        d.s.cprev[s] = kNone;
+    }
+    if (flag == kArrivedPending) {
+        d.s.flag[s] = kDead;
+        d.s.pcell[s] = kNone;
+        return true;
+    }
+    live++;
+    const uint32_t c = (uint32_t)x;
+    d.s.pcell[s] = base + c;
+    if (sample) atomicAdd(&d.bin_occ[(size_t)(k / m.bin_steps) * d.n_edges + e], 1u);
+
+    // leader: nearest occupied cell ahead in the own lane of the own edge.
+    // Cells beyond both d_front and the farthest reach of this step
+    // cannot change the result, so the scan stops there.
+    const float d_front = (2.0f * m.dt) * v;
+    const float vmax_step = fmaxf(v0, v + m.a * m.dt);
+    const float reach = fmaxf(d_front, vmax_step * m.dt + m.s0);
+    const float L = (float)len;
+    // in the same round trip as the scan: the next edge's records for a
+    // vehicle that may reach the stop line, the lane-change key for one
+    // that may draw (both only used under the exact conditions below)
+    const bool may_cross = en != kNone && x + vmax_step * m.dt + 1.0f >= L;
+    const bool may_draw = tl != kNoLane && tl != ln && ((tl > ln) == (par == 1u)) && (L - x) < m.x0;
+    EdgeRec enr{};
+    RouteRec rr{};
+    uint32_t nen = kNone;
+    if (may_cross) {
+        enr = d.edge[en];
+        rr = d.rrec[rpos + 1];
+        nen = rpos + 1 < rlast ? d.route[rpos + 2] : kNone;
+    }
+    // lane-change draw at step k: SplitMix64 of hkey ^ k * C2, where
+    // hkey[id] = seed ^ local_id * C1 was formed at load time (local_id =
+    // the vehicle's id within its scenario, so a scenario draws the same
+    // numbers alone or inside a batch)
+    const uint64_t hk = may_draw ? d.hkey[id] : 0ull;
+    uint32_t hi = c + (uint32_t)fminf(reach, 65535.0f) + 2u;
+    if (hi > len - 1) hi = len - 1;
+    const uint32_t cf = first_occupied_wide(Mc + base, c + 1, hi);
+    const bool has_f = cf != kNone;
+
+    float vn;
+    if (has_f && ((float)cf - x) <= d_front)
+        vn = idm_speed(m, v, (float)Mc[base + cf], (float)cf - x, v0);
+    else
+        vn = v0;
+    float xn = x + vn * m.dt;
+    if (has_f) {
+        const float lim = (float)cf - m.s0;
+        if (xn > lim) {
+            xn = x > lim ? x : lim;
+            vn = 0.0f;
+        }
+    }
+    if (xn >= L) {
+        if (en == kNone) {
+            // last edge of the route: arrive
+            stat_exit(d, e, k, tent);
+            d.arr[id] = k + 1;
+            d.status[id] = kArrived;
+            d.s.flag[s] = kArrivedPending;
+            d.s.act[s] = kActArrive;
+            arrived++;
+            return true;
+        }
+        bool cross = false;
+        if (G == 0 || (k / G) % (ph & 0xFFu) == (ph >> 8)) {
+            if (!may_cross) {  // cannot happen: x' <= x + vmax_step * dt < L - 1 otherwise
+                enr = d.edge[en];
+                rr = d.rrec[rpos + 1];
+                nen = rpos + 1 < rlast ? d.route[rpos + 2] : kNone;
+            }
+            const uint32_t l = pick_entry_lane(entry_cells(Mc, enr), enr.lanes, rr.tl);
+            if (l != kNone) {
+                const uint32_t slot = d.slot_off[en] + l;
+                atomicMin(&claim[slot], id);
+                CrossRec cr;
+                cr.s = s;
+                cr.id = id;
+                cr.cslot = slot;
+                cr.e = e;
+                cr.en = en;
+                cr.rpos = rpos;
+                cr.tent = tent;
+                cr.base = base;
+                cr.nbase = enr.moff + l * row_stride(enr.len);
+                cr.nen = nen;
+                cr.nsg = rr.green;
+                cr.x = x;
+                cr.vn = vn;
+                cr.nv0 = enr.v0;
+                cr.len = (uint16_t)len;
+                cr.nlen = enr.len;
+                cr.nsph = (uint16_t)(rr.nphase | (rr.arank << 8));
+                cr.lane = (uint8_t)l;
+                cr.tln = rr.tl;
+                d.s.act[s] = kActCross;
+                d.cross_list[par][warp_append(&d.counts[par])] = cr;
+                cross = true;
+            }
+        }
+        if (!cross) {
+            const float lim = L - 1.0f;
+            const float xh = x > lim ? x : lim;
+            xw[s] = xh;
+            vw[s] = 0.0f;
+            put_cell(d, Mn, base + (uint32_t)xh, 0);
+            d.s.act[s] = kActHold;
+        }
+        return true;
+    }
+    xw[s] = xn;
+    vw[s] = vn;
+    const uint32_t cn = (uint32_t)xn;
+    put_cell(d, Mn, base + cn, speed_byte(vn));
+    uint8_t act = kActStay;
+    if (may_draw) {
+        const float xrem = L - x;
+        const float mp = xrem >= m.x0 ? 0.0f : 1.0f - xrem / m.x0;
+        // u is in [0, 1): no draw can pass when mp <= 0
+        if (mp > 0.0f && unit24(splitmix64_mix(hk ^ ((uint64_t)k * 0xD1B54A32D192ED03ull))) < mp) {
+            act = kActIntend;
+            Iw[base + cn] = 1;
+            d.s.imark[s] = base + cn;
+            IntendRec ir;
+            ir.s = s;
+            ir.base = base;
+            ir.hk = hk;
+            ir.x = x;
+            ir.xn = xn;
+            ir.vn = vn;
+            ir.len = (uint16_t)len;
+            ir.lane = (uint8_t)ln;
+            ir.up = tl > ln ? 1 : 0;
+            d.intend_list[par][warp_append(&d.counts[2 + par])] = ir;
+        }
+    }
+    d.s.act[s] = act;
+    return true;
+}
+
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) step_p1(Dev d, uint32_t koff, uint32_t kph) {
     pdl_prologue();
-    const uint32_t par = kph & 1u, r3 = kph % 3u;
-    const uint8_t *Mc = d.map[r3];
-    uint8_t *Mn = d.map[r3 == 2u ? 0u : r3 + 1u];
-    uint8_t *Mo = d.map[r3 == 0u ? 2u : r3 - 1u];  // holds step k-1: erase
-    uint8_t *Iw = d.imap[par];
-    uint8_t *Io = d.imap[par ^ 1u];         // marks of step k-1: clear
-    uint32_t *claim = d.claim[par];
-    uint32_t *claim_old = d.claim[par ^ 1u]; // slots won at step k-1: reset
-    const float *xc = d.s.x[par], *vc = d.s.v[par];
-    float *xw = d.s.x[par ^ 1u], *vw = d.s.v[par ^ 1u];
     const uint32_t k = *d.kbase + koff;
     const uint32_t n = *d.n_slots;
+    const StepView w = step_view(d, k, kph);
     const uint32_t norg = d.n_org;
     const uint32_t lim = norg + d.cap;  // items: origin edges first, then slots
-    const Model &m = d.m;
-    const bool sample = m.bin_steps && (k % m.bin_steps == 0) && (k / m.bin_steps < m.n_bins);
     uint32_t live = 0;
     uint32_t arrived = 0;
     for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < lim; i += gridDim.x * BLOCK) {
         if (i < norg) {
-            // origin edge j: reset the claim its departure won last step; ask
-            // for a departure of the queue head once its step has come
-            const uint32_t j = i;
-            const uint32_t dp = d.dprev[j];
-            const QRec hd = d.org_hd[j];
-            const EdgeRec er = d.org_rec[j];
-            const uint32_t e0 = d.org_edge[j];
-            const uint32_t qoff = d.org_qoff[j], qhead = d.org_head[j], qend = d.org_qend[j];
-            if (dp != kNone) {
-                claim_old[dp] = kNone;
-                d.dprev[j] = kNone;
-            }
-            if (hd.h != kNone && hd.dep <= k) {
-                const RouteRec rr = d.rrec[hd.r0];
-                const uint32_t nxt = hd.r0 + 1 < hd.r1 ? d.route[hd.r0 + 1] : kNone;
-                const uint32_t so = d.slot_off[e0];
-                const uint32_t l = pick_entry_lane(entry_cells(Mc, er), er.lanes, rr.tl);
-                if (l != kNone) {
-                    atomicMin(&claim[so + l], hd.h);
-                    DepRec dr;
-                    dr.j = j;
-                    dr.slot = so + l;
-                    dr.h = hd.h;
-                    dr.r0 = hd.r0;
-                    dr.r1 = hd.r1;
-                    dr.qoff = qoff;
-                    dr.qhead = qhead;
-                    dr.qend = qend;
-                    dr.base = er.moff + l * row_stride(er.len);
-                    dr.e0 = e0;
-                    dr.nen = nxt;
-                    dr.nsg = rr.green;
-                    dr.v0 = er.v0;
-                    dr.len = er.len;
-                    dr.nsph = (uint16_t)(rr.nphase | (rr.arank << 8));
-                    dr.lane = (uint8_t)l;
-                    dr.tlc = rr.tl;
-                    d.dep_rec[par][warp_append(&d.counts[4 + par])] = dr;
-                }
-            }
+            p1_origin(d, w, i);
             continue;
         }
-        const uint32_t s = i - norg;
-        // every slot field, loaded together (one memory round trip, shared
-        // with the loads of the step number and the slot count)
-        const uint8_t flag = d.s.flag[s];
-        const uint32_t pc = d.s.pcell[s];
-        const uint32_t im = d.s.imark[s];
-        const uint32_t cp = d.s.cprev[s];
-        const float x = xc[s], v = vc[s];
-        const uint32_t base = d.s.base[s];
-        const uint32_t len = d.s.len[s];
-        const float v0 = d.s.v0[s];
-        const uint32_t en = d.s.en[s];
-        const uint32_t G = d.s.sg[s];
-        const uint32_t ph = d.s.sph[s];
-        const uint32_t tl = d.s.tlc[s];  // kNoLane on the last edge of the route
-        const uint32_t ln = d.s.lane[s];
-        const uint32_t id = d.s.id[s];
-        const uint32_t e = d.s.e[s];
-        const uint32_t rpos = d.s.rpos[s], rlast = d.s.rlast[s];
-        const uint32_t tent = d.s.tent[s];
-        loads_issued();
-        if (s >= n) break;
-        if (flag == kDead) continue;
-        if (pc != kNone) Mo[pc] = kEmpty;
-        if (im != kNone) {
-            Io[im] = 0;
-            d.s.imark[s] = kNone;
-        }
-        if (cp != kNone) {
-            claim_old[cp] = kNone;
-            d.s.cprev[s] = kNone;
-        }
-        if (flag == kArrivedPending) {
-            d.s.flag[s] = kDead;
-            d.s.pcell[s] = kNone;
-            continue;
-        }
-        live++;
-        const uint32_t c = (uint32_t)x;
-        d.s.pcell[s] = base + c;
-        if (sample) atomicAdd(&d.bin_occ[(size_t)(k / m.bin_steps) * d.n_edges + e], 1u);
-
-        // leader: nearest occupied cell ahead in the own lane of the own edge.
-        // Cells beyond both d_front and the farthest reach of this step
-        // cannot change the result, so the scan stops there.
-        const float d_front = (2.0f * m.dt) * v;
-        const float vmax_step = fmaxf(v0, v + m.a * m.dt);
-        const float reach = fmaxf(d_front, vmax_step * m.dt + m.s0);
-        const float L = (float)len;
-        // in the same round trip as the scan: the next edge's records for a
-        // vehicle that may reach the stop line, the lane-change key for one
-        // that may draw (both only used under the exact conditions below)
-        const bool may_cross = en != kNone && x + vmax_step * m.dt + 1.0f >= L;
-        const bool may_draw = tl != kNoLane && tl != ln && ((tl > ln) == (par == 1u)) && (L - x) < m.x0;
-        EdgeRec enr{};
-        RouteRec rr{};
-        uint32_t nen = kNone;
-        if (may_cross) {
-            enr = d.edge[en];
-            rr = d.rrec[rpos + 1];
-            nen = rpos + 1 < rlast ? d.route[rpos + 2] : kNone;
-        }
-        // lane-change draw at step k: SplitMix64 of hkey ^ k * C2, where
-        // hkey[id] = seed ^ local_id * C1 was formed at load time (local_id =
-        // the vehicle's id within its scenario, so a scenario draws the same
-        // numbers alone or inside a batch)
-        const uint64_t hk = may_draw ? d.hkey[id] : 0ull;
-        uint32_t hi = c + (uint32_t)fminf(reach, 65535.0f) + 2u;
-        if (hi > len - 1) hi = len - 1;
-        const uint32_t cf = first_occupied_wide(Mc + base, c + 1, hi);
-        const bool has_f = cf != kNone;
-
-        float vn;
-        if (has_f && ((float)cf - x) <= d_front)
-            vn = idm_speed(m, v, (float)Mc[base + cf], (float)cf - x, v0);
-        else
-            vn = v0;
-        float xn = x + vn * m.dt;
-        if (has_f) {
-            const float lim = (float)cf - m.s0;
-            if (xn > lim) {
-                xn = x > lim ? x : lim;
-                vn = 0.0f;
-            }
-        }
-        if (xn >= L) {
-            if (en == kNone) {
-                // last edge of the route: arrive
-                stat_exit(d, e, k, tent);
-                d.arr[id] = k + 1;
-                d.status[id] = kArrived;
-                d.s.flag[s] = kArrivedPending;
-                d.s.act[s] = kActArrive;
-                arrived++;
-                continue;
-            }
-            bool cross = false;
-            if (G == 0 || (k / G) % (ph & 0xFFu) == (ph >> 8)) {
-                if (!may_cross) {  // cannot happen: x' <= x + vmax_step * dt < L - 1 otherwise
-                    enr = d.edge[en];
-                    rr = d.rrec[rpos + 1];
-                    nen = rpos + 1 < rlast ? d.route[rpos + 2] : kNone;
-                }
-                const uint32_t l = pick_entry_lane(entry_cells(Mc, enr), enr.lanes, rr.tl);
-                if (l != kNone) {
-                    const uint32_t slot = d.slot_off[en] + l;
-                    atomicMin(&claim[slot], id);
-                    CrossRec cr;
-                    cr.s = s;
-                    cr.id = id;
-                    cr.cslot = slot;
-                    cr.e = e;
-                    cr.en = en;
-                    cr.rpos = rpos;
-                    cr.tent = tent;
-                    cr.base = base;
-                    cr.nbase = enr.moff + l * row_stride(enr.len);
-                    cr.nen = nen;
-                    cr.nsg = rr.green;
-                    cr.x = x;
-                    cr.vn = vn;
-                    cr.nv0 = enr.v0;
-                    cr.len = (uint16_t)len;
-                    cr.nlen = enr.len;
-                    cr.nsph = (uint16_t)(rr.nphase | (rr.arank << 8));
-                    cr.lane = (uint8_t)l;
-                    cr.tln = rr.tl;
-                    d.s.act[s] = kActCross;
-                    d.cross_list[par][warp_append(&d.counts[par])] = cr;
-                    cross = true;
-                }
-            }
-            if (!cross) {
-                const float lim = L - 1.0f;
-                const float xh = x > lim ? x : lim;
-                xw[s] = xh;
-                vw[s] = 0.0f;
-                put_cell(d, Mn, base + (uint32_t)xh, 0);
-                d.s.act[s] = kActHold;
-            }
-            continue;
-        }
-        xw[s] = xn;
-        vw[s] = vn;
-        const uint32_t cn = (uint32_t)xn;
-        put_cell(d, Mn, base + cn, speed_byte(vn));
-        uint8_t act = kActStay;
-        if (may_draw) {
-            const float xrem = L - x;
-            const float mp = xrem >= m.x0 ? 0.0f : 1.0f - xrem / m.x0;
-            // u is in [0, 1): no draw can pass when mp <= 0
-            if (mp > 0.0f && unit24(splitmix64_mix(hk ^ ((uint64_t)k * 0xD1B54A32D192ED03ull))) < mp) {
-                act = kActIntend;
-                Iw[base + cn] = 1;
-                d.s.imark[s] = base + cn;
-                IntendRec ir;
-                ir.s = s;
-                ir.base = base;
-                ir.hk = hk;
-                ir.x = x;
-                ir.xn = xn;
-                ir.vn = vn;
-                ir.len = (uint16_t)len;
-                ir.lane = (uint8_t)ln;
-                ir.up = tl > ln ? 1 : 0;
-                d.intend_list[par][warp_append(&d.counts[2 + par])] = ir;
-            }
-        }
-        d.s.act[s] = act;
+        if (!p1_slot(d, w, i - norg, n, live, arrived)) break;
     }
     block_add<BLOCK>(&d.ctr[0], live);
     if (arrived) atomicAdd(&d.ctr[1], (unsigned long long)arrived);
@@ -449,17 +493,104 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) step_p1(Dev d, uint32_t k
 
 // ----------------------------------------------------------------------- P2
 
+// Crossing request cr: the lowest id asking for the (edge, lane) enters its
+// cell 0, the others hold at the stop line.
+__device__ __forceinline__ void p2_cross(const Dev &d, const StepView &w, const CrossRec &cr, uint32_t &events) {
+    const uint32_t k = w.k;
+    uint8_t *Mn = w.Mn;
+    float *xw = w.xw, *vw = w.vw;
+    if (w.claim[cr.cslot] == cr.id) {
+        const uint32_t s = cr.s;
+        stat_exit(d, cr.e, k, cr.tent);
+        stat_entry(d, cr.en, k);
+        EdgeState ne;
+        ne.base = cr.nbase;
+        ne.e = cr.en;
+        ne.rpos = cr.rpos + 1;
+        ne.tent = k + 1;
+        ne.en = cr.nen;
+        ne.sg = cr.nsg;
+        ne.v0 = cr.nv0;
+        ne.len = cr.nlen;
+        ne.sph = cr.nsph;
+        store_es(d.s.es + s, ne);
+        d.s.lane[s] = cr.lane;
+        d.s.tlc[s] = cr.tln;
+        d.s.cprev[s] = cr.cslot;
+        xw[s] = 0.0f;
+        vw[s] = cr.vn;
+        put_cell(d, Mn, cr.nbase, speed_byte(cr.vn));
+        events++;
+    } else {
+        const float lim = (float)cr.len - 1.0f;
+        const float xh = cr.x > lim ? cr.x : lim;
+        xw[cr.s] = xh;
+        vw[cr.s] = 0.0f;
+        put_cell(d, Mn, cr.base + (uint32_t)xh, 0);
+    }
+}
+
+// Departure request number q (slot n0 + q, fixed in advance): the queue head
+// enters cell 0 of its first edge if it holds the lowest id asking for it.
+__device__ __forceinline__ void p2_dep(const Dev &d, const StepView &w, const DepRec &dr, uint32_t q, uint32_t n0,
+                                       uint32_t &events, uint32_t &departed) {
+    const uint32_t k = w.k;
+    const uint32_t s = n0 + q;
+    const uint32_t qh = dr.qoff + dr.qhead;
+    const QRec next = qh + 1 < dr.qend ? d.qrec[qh + 1] : QRec{kNone, kNone, 0, 0};
+    const uint32_t won = w.claim[dr.slot];
+    if (s >= d.cap) {
+        atomicOr(d.err, kErrSlotOverflow);
+        return;
+    }
+    if (won != dr.h) {
+        d.s.flag[s] = kDead;
+        d.s.pcell[s] = kNone;
+        d.s.imark[s] = kNone;
+        d.s.cprev[s] = kNone;
+        return;
+    }
+    EdgeState ne;
+    ne.base = dr.base;
+    ne.e = dr.e0;
+    ne.rpos = dr.r0;
+    ne.tent = k + 1;
+    ne.en = dr.nen;
+    ne.sg = dr.nsg;
+    ne.v0 = dr.v0;
+    ne.len = dr.len;
+    ne.sph = dr.nsph;
+    store_es(d.s.es + s, ne);
+    d.s.id[s] = dr.h;
+    d.s.rlast[s] = dr.r1 - 1;
+    d.s.lane[s] = dr.lane;
+    d.s.tlc[s] = dr.tlc;
+    d.s.pcell[s] = kNone;
+    d.s.imark[s] = kNone;
+    d.s.cprev[s] = kNone;
+    d.s.flag[s] = kLive;
+    w.xw[s] = 0.0f;
+    w.vw[s] = 0.0f;
+    put_cell(d, w.Mn, dr.base, 0);
+    d.dprev[dr.j] = dr.slot;
+    d.org_head[dr.j] = dr.qhead + 1;
+    d.org_hd[dr.j] = next;
+    d.dep_act[dr.h] = k + 1;
+    d.status[dr.h] = kActive;
+    stat_entry(d, dr.e0, k);
+    events++;
+    departed++;
+}
+
 // The last gdep blocks (enough for one request per origin edge) take the
 // departure requests, the others the crossers, so that each thread's first
 // record is loaded together with its list's length.
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) step_p2(Dev d, uint32_t koff, uint32_t kph, uint32_t gdep) {
     pdl_prologue();
-    const uint32_t par = kph & 1u, r3 = kph % 3u;
-    uint8_t *Mn = d.map[r3 == 2u ? 0u : r3 + 1u];
-    const uint32_t *claim = d.claim[par];
-    float *xw = d.s.x[par ^ 1u], *vw = d.s.v[par ^ 1u];
+    const uint32_t par = kph & 1u;
     const uint32_t k = *d.kbase + koff;
+    const StepView w = step_view(d, k, kph);
     const bool crossers = blockIdx.x < gridDim.x - gdep;
     uint32_t events = 0, departed = 0;
     if (crossers) {
@@ -470,37 +601,9 @@ __global__ void __launch_bounds__(BLOCK) step_p2(Dev d, uint32_t koff, uint32_t 
             const CrossRec cr = list[i];
             loads_issued();
             if (i >= ncross) break;
-            if (claim[cr.cslot] == cr.id) {
-                const uint32_t s = cr.s;
-                stat_exit(d, cr.e, k, cr.tent);
-                stat_entry(d, cr.en, k);
-                d.s.e[s] = cr.en;
-                d.s.rpos[s] = cr.rpos + 1;
-                d.s.lane[s] = cr.lane;
-                d.s.tent[s] = k + 1;
-                d.s.tlc[s] = cr.tln;
-                d.s.base[s] = cr.nbase;
-                d.s.len[s] = cr.nlen;
-                d.s.v0[s] = cr.nv0;
-                d.s.en[s] = cr.nen;
-                d.s.sg[s] = cr.nsg;
-                d.s.sph[s] = cr.nsph;
-                d.s.cprev[s] = cr.cslot;
-                xw[s] = 0.0f;
-                vw[s] = cr.vn;
-                put_cell(d, Mn, cr.nbase, speed_byte(cr.vn));
-                events++;
-            } else {
-                const float lim = (float)cr.len - 1.0f;
-                const float xh = cr.x > lim ? cr.x : lim;
-                xw[cr.s] = xh;
-                vw[cr.s] = 0.0f;
-                put_cell(d, Mn, cr.base + (uint32_t)xh, 0);
-            }
+            p2_cross(d, w, cr, events);
         }
-    }
-    if (!crossers) {
-        // departure request q: its slot n0 + q is fixed in advance
+    } else {
         const uint32_t ndep = d.counts[4 + par];
         const uint32_t n0 = *d.n_slots;
         const uint32_t b0 = gridDim.x - gdep;
@@ -510,49 +613,7 @@ __global__ void __launch_bounds__(BLOCK) step_p2(Dev d, uint32_t koff, uint32_t 
             const DepRec dr = list[q];
             loads_issued();
             if (q >= ndep) break;
-            const uint32_t s = n0 + q;
-            const uint32_t qh = dr.qoff + dr.qhead;
-            const QRec next = qh + 1 < dr.qend ? d.qrec[qh + 1] : QRec{kNone, kNone, 0, 0};
-            const uint32_t won = claim[dr.slot];
-            if (s >= d.cap) {
-                atomicOr(d.err, kErrSlotOverflow);
-                continue;
-            }
-            if (won != dr.h) {
-                d.s.flag[s] = kDead;
-                d.s.pcell[s] = kNone;
-                d.s.imark[s] = kNone;
-                d.s.cprev[s] = kNone;
-                continue;
-            }
-            d.s.id[s] = dr.h;
-            d.s.e[s] = dr.e0;
-            d.s.rpos[s] = dr.r0;
-            d.s.rlast[s] = dr.r1 - 1;
-            d.s.lane[s] = dr.lane;
-            d.s.tlc[s] = dr.tlc;
-            d.s.base[s] = dr.base;
-            d.s.len[s] = dr.len;
-            d.s.v0[s] = dr.v0;
-            d.s.en[s] = dr.nen;
-            d.s.sg[s] = dr.nsg;
-            d.s.sph[s] = dr.nsph;
-            d.s.tent[s] = k + 1;
-            d.s.pcell[s] = kNone;
-            d.s.imark[s] = kNone;
-            d.s.cprev[s] = kNone;
-            d.s.flag[s] = kLive;
-            xw[s] = 0.0f;
-            vw[s] = 0.0f;
-            put_cell(d, Mn, dr.base, 0);
-            d.dprev[dr.j] = dr.slot;
-            d.org_head[dr.j] = dr.qhead + 1;
-            d.org_hd[dr.j] = next;
-            d.dep_act[dr.h] = k + 1;
-            d.status[dr.h] = kActive;
-            stat_entry(d, dr.e0, k);
-            events++;
-            departed++;
+            p2_dep(d, w, dr, q, n0, events, departed);
         }
     }
     if (events) atomicAdd(&d.ctr[3], (unsigned long long)events);
@@ -575,86 +636,149 @@ __device__ __forceinline__ void load_chunks(const uint8_t *row, uint32_t c_first
     for (int j = 0; j < N; j++) mk[j] = occ_mask16(q[j]);
 }
 
+// Lane-change intender ir: gap acceptance against the step-k map and the
+// reservations of the next map; the accepted move their byte sideways.
+__device__ __forceinline__ void p3_intend(const Dev &d, const StepView &w, const IntendRec &ir, uint32_t &changes) {
+    const uint32_t k = w.k;
+    const uint8_t *Mc = w.Mc;
+    uint8_t *Mn = w.Mn;
+    const uint8_t *Iw = w.Iw;
+    const Model &m = d.m;
+    const uint32_t s = ir.s;
+    const uint32_t ln = ir.lane;
+    const bool up = ir.up != 0;
+    const uint32_t len = ir.len, stride = row_stride(len);
+    const uint32_t base = ir.base;
+    const float x = ir.x, xn = ir.xn, vn = ir.vn;
+    const uint32_t base2 = up ? base + stride : base - stride;
+    const uint8_t *row2 = Mc + base2;
+    const uint32_t c0 = (uint32_t)x, cn = (uint32_t)xn;
+    // window [c0 - 64, c0 + 63] of the target lane, clipped to the row
+    const uint32_t lo = c0 > 64u ? c0 - 64u : 0u;
+    const uint32_t hi = c0 + 63u < len - 1 ? c0 + 63u : len - 1;
+    const uint32_t cfirst = lo & ~15u;
+    uint32_t mk[9];
+    load_chunks<9>(row2, cfirst, hi, mk);
+    const uint32_t tgt = base2 + cn;
+    const uint8_t tgt_map = Mn[tgt], tgt_mark = Iw[tgt];
+    uint64_t h = 0;
+    if (m.eps_amp > 0.0f) h = splitmix64_mix(ir.hk ^ ((uint64_t)k * 0xD1B54A32D192ED03ull));
+    // lead: first occupied cell in [c0, hi]; lag: last in [lo, c0 - 1]
+    uint32_t ca = kNone, cb = kNone;
+#pragma unroll
+    for (int j = 0; j < 9; j++) {
+        const uint32_t c = cfirst + 16u * j;
+        if (c > hi) break;
+        const uint32_t a = mk[j] & range_mask16(c, c0, hi);
+        if (ca == kNone && a) ca = c + (uint32_t)(__ffs((int)a) - 1);
+        if (c0 > 0 && c <= c0 - 1) {
+            const uint32_t b = mk[j] & range_mask16(c, lo, c0 - 1);
+            if (b) cb = c + (31u - (uint32_t)__clz((int)b));
+        }
+    }
+    float eps_a = 0.0f, eps_b = 0.0f;
+    if (m.eps_amp > 0.0f) {
+        eps_a = m.eps_amp * (2.0f * unit24(splitmix64_mix(h ^ 0x632BE59BD9B4E019ull)) - 1.0f);
+        eps_b = m.eps_amp * (2.0f * unit24(splitmix64_mix(h ^ 0x8CB92BA72F3D8DD7ull)) - 1.0f);
+    }
+    bool ok = true;
+    if (ca != kNone) {
+        const float va = (float)row2[ca];
+        const float G_lead = (m.g_a + fmax0(m.alpha_i * vn - m.alpha_a * va)) + eps_a;
+        ok = ((float)ca - xn) >= G_lead;
+    }
+    if (ok && cb != kNone) {
+        const float vb = (float)row2[cb];
+        const float G_lag = (m.g_b + fmax0(m.alpha_b * vb - m.alpha_i * vn)) + eps_b;
+        ok = (xn - (float)cb) >= G_lag;
+    }
+    if (ok && cn >= 1 && tgt_map == kEmpty && tgt_mark == 0) {
+        const uint32_t own = base + cn;
+        Mn[tgt] = Mn[own];
+        Mn[own] = kEmpty;
+        d.s.lane[s] = (uint8_t)(up ? ln + 1 : ln - 1);
+        d.s.es[s].base = base2;
+        changes++;
+    }
+}
+
+// End of step k (one thread): the next step's lists start empty; the
+// departures of this step have taken their slots.
+__device__ __forceinline__ void step_tail(const Dev &d, uint32_t par) {
+    d.counts[par ^ 1u] = 0;
+    d.counts[2 + (par ^ 1u)] = 0;
+    d.counts[4 + (par ^ 1u)] = 0;
+    *d.n_slots += d.counts[4 + par];
+}
+
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) step_p3(Dev d, uint32_t koff, uint32_t kph) {
     pdl_prologue();
-    const uint32_t par = kph & 1u, r3 = kph % 3u;
-    const uint8_t *Mc = d.map[r3];
-    uint8_t *Mn = d.map[r3 == 2u ? 0u : r3 + 1u];
-    const uint8_t *Iw = d.imap[par];
+    const uint32_t par = kph & 1u;
     const uint32_t k = *d.kbase + koff;
+    const StepView w = step_view(d, k, kph);
     const uint32_t nint = d.counts[2 + par];
-    const Model &m = d.m;
     uint32_t changes = 0;
     for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < d.cap; i += gridDim.x * BLOCK) {
         const IntendRec ir = d.intend_list[par][i];
         loads_issued();
         if (i >= nint) break;
-        const uint32_t s = ir.s;
-        const uint32_t ln = ir.lane;
-        const bool up = ir.up != 0;
-        const uint32_t len = ir.len, stride = row_stride(len);
-        const uint32_t base = ir.base;
-        const float x = ir.x, xn = ir.xn, vn = ir.vn;
-        const uint32_t base2 = up ? base + stride : base - stride;
-        const uint8_t *row2 = Mc + base2;
-        const uint32_t c0 = (uint32_t)x, cn = (uint32_t)xn;
-        // window [c0 - 64, c0 + 63] of the target lane, clipped to the row
-        const uint32_t lo = c0 > 64u ? c0 - 64u : 0u;
-        const uint32_t hi = c0 + 63u < len - 1 ? c0 + 63u : len - 1;
-        const uint32_t cfirst = lo & ~15u;
-        uint32_t mk[9];
-        load_chunks<9>(row2, cfirst, hi, mk);
-        const uint32_t tgt = base2 + cn;
-        const uint8_t tgt_map = Mn[tgt], tgt_mark = Iw[tgt];
-        uint64_t h = 0;
-        if (m.eps_amp > 0.0f) h = splitmix64_mix(ir.hk ^ ((uint64_t)k * 0xD1B54A32D192ED03ull));
-        // lead: first occupied cell in [c0, hi]; lag: last in [lo, c0 - 1]
-        uint32_t ca = kNone, cb = kNone;
-#pragma unroll
-        for (int j = 0; j < 9; j++) {
-            const uint32_t c = cfirst + 16u * j;
-            if (c > hi) break;
-            const uint32_t a = mk[j] & range_mask16(c, c0, hi);
-            if (ca == kNone && a) ca = c + (uint32_t)(__ffs((int)a) - 1);
-            if (c0 > 0 && c <= c0 - 1) {
-                const uint32_t b = mk[j] & range_mask16(c, lo, c0 - 1);
-                if (b) cb = c + (31u - (uint32_t)__clz((int)b));
-            }
-        }
-        float eps_a = 0.0f, eps_b = 0.0f;
-        if (m.eps_amp > 0.0f) {
-            eps_a = m.eps_amp * (2.0f * unit24(splitmix64_mix(h ^ 0x632BE59BD9B4E019ull)) - 1.0f);
-            eps_b = m.eps_amp * (2.0f * unit24(splitmix64_mix(h ^ 0x8CB92BA72F3D8DD7ull)) - 1.0f);
-        }
-        bool ok = true;
-        if (ca != kNone) {
-            const float va = (float)row2[ca];
-            const float G_lead = (m.g_a + fmax0(m.alpha_i * vn - m.alpha_a * va)) + eps_a;
-            ok = ((float)ca - xn) >= G_lead;
-        }
-        if (ok && cb != kNone) {
-            const float vb = (float)row2[cb];
-            const float G_lag = (m.g_b + fmax0(m.alpha_b * vb - m.alpha_i * vn)) + eps_b;
-            ok = (xn - (float)cb) >= G_lag;
-        }
-        if (ok && cn >= 1 && tgt_map == kEmpty && tgt_mark == 0) {
-            const uint32_t own = base + cn;
-            Mn[tgt] = Mn[own];
-            Mn[own] = kEmpty;
-            d.s.lane[s] = (uint8_t)(up ? ln + 1 : ln - 1);
-            d.s.base[s] = base2;
-            changes++;
-        }
+        p3_intend(d, w, ir, changes);
     }
     if (changes) atomicAdd(&d.ctr[2], (unsigned long long)changes);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        // the next step's lists start empty; the departures of this step
-        // have taken their slots
-        d.counts[par ^ 1u] = 0;
-        d.counts[2 + (par ^ 1u)] = 0;
-        d.counts[4 + (par ^ 1u)] = 0;
-        *d.n_slots += d.counts[4 + par];
+    if (blockIdx.x == 0 && threadIdx.x == 0) step_tail(d, par);
+}
+
+// ------------------------------------------------------------ light load
+
+// Many steps in one block when few vehicles move: the three phases of a
+// step are separated by block barriers instead of kernel boundaries.  The
+// host picks this kernel for a chunk only when at most kSmallMax trips can be
+// on the network or waiting during it; olist holds the origin edges that can
+// act in the chunk (a queue head due before its end, or a claim to reset).
+// Every phase body is the one the grid-wide kernels run, so the results are
+// the same.  (Clusters of 2-8 such blocks, synchronised by cluster barriers,
+// were measured slower than the grid-wide kernels for 2k-12k trips.)
+__global__ void __launch_bounds__(kSmallBlock, 1)
+    step_small(Dev d, uint32_t k0, uint32_t nsteps, const uint32_t *olist, const uint32_t *no_ptr) {
+    const uint32_t tid = threadIdx.x;
+    const uint32_t no = *no_ptr;
+    for (uint32_t t = 0; t < nsteps; t++) {
+        const uint32_t k = k0 + t, par = k & 1u;
+        const StepView w = step_view(d, k, k);
+        // P1
+        const uint32_t n = *d.n_slots;
+        uint32_t live = 0, arrived = 0;
+        for (uint32_t i = tid; i < no; i += kSmallBlock) p1_origin(d, w, olist[i]);
+        for (uint32_t s = tid; s < n; s += kSmallBlock) p1_slot(d, w, s, n, live, arrived);
+        block_add<kSmallBlock>(&d.ctr[0], live);
+        if (arrived) atomicAdd(&d.ctr[1], (unsigned long long)arrived);
+        __syncthreads();
+        // P2
+        uint32_t events = 0, departed = 0;
+        const uint32_t ncross = d.counts[par], ndep = d.counts[4 + par];
+        for (uint32_t i = tid; i < ncross; i += kSmallBlock) p2_cross(d, w, d.cross_list[par][i], events);
+        for (uint32_t q = tid; q < ndep; q += kSmallBlock) p2_dep(d, w, d.dep_rec[par][q], q, n, events, departed);
+        if (events) atomicAdd(&d.ctr[3], (unsigned long long)events);
+        if (departed) atomicAdd(&d.ctr[4], (unsigned long long)departed);
+        __syncthreads();
+        // P3
+        uint32_t changes = 0;
+        const uint32_t nint = d.counts[2 + par];
+        for (uint32_t i = tid; i < nint; i += kSmallBlock) p3_intend(d, w, d.intend_list[par][i], changes);
+        if (changes) atomicAdd(&d.ctr[2], (unsigned long long)changes);
+        __syncthreads();
+        if (tid == 0) step_tail(d, par);
+        __syncthreads();
+    }
+}
+
+// Origin edges that can act in steps [k0, k1): a queue head due before k1,
+// or a claim won at the previous step still to reset.
+__global__ void small_origins(Dev d, uint32_t k1, uint32_t *olist, uint32_t *no) {
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < d.n_org; j += gridDim.x * blockDim.x) {
+        const QRec hd = d.org_hd[j];
+        if (d.dprev[j] != kNone || (hd.h != kNone && hd.dep < k1)) olist[warp_append(no)] = j;
     }
 }
 
@@ -722,6 +846,15 @@ void launch_phase(const Dev &d, int phase, uint32_t koff, uint32_t kph, int grid
 
 void launch_chunk_end(const Dev &d, uint32_t steps, cudaStream_t st) { launch_pdl(chunk_end, 1, 1, st, d, steps); }
 
+cudaError_t launch_small(const Dev &d, uint32_t k0, uint32_t nsteps, uint32_t *olist, uint32_t *no,
+                         cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(no, 0, 4, st);
+    if (e != cudaSuccess) return e;
+    small_origins<<<(d.n_org + 255) / 256 + 1, 256, 0, st>>>(d, k0 + nsteps, olist, no);
+    step_small<<<1, kSmallBlock, 0, st>>>(d, k0, nsteps, olist, no);
+    return cudaGetLastError();
+}
+
 }  // namespace lpsim
 
 namespace lpsim {
@@ -736,9 +869,9 @@ __global__ void state_scatter(Dev d, uint32_t k, float *x, float *v, uint32_t *e
         uint32_t id = d.s.id[s];
         x[id] = d.s.x[k & 1][s];
         v[id] = d.s.v[k & 1][s];
-        edge[id] = d.s.e[s];
+        edge[id] = d.s.es[s].e;
         lane[id] = d.s.lane[s];
-        ridx[id] = d.s.rpos[s] - d.roff[id];
+        ridx[id] = d.s.es[s].rpos - d.roff[id];
     }
 }
 

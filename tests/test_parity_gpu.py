@@ -137,3 +137,59 @@ def test_idle_hours_match_oracle(grid_day, chunk_steps):
     for key in ("steps", "veh_steps", "arrived", "active", "waiting", "k"):
         assert ro[key] == rg[key], (key, ro[key], rg[key])
     assert_outputs_equal(o, g, n_bins=20)
+
+
+@pytest.mark.parametrize("flags", [0, 4])
+def test_light_load_chunks_match_oracle(grid_day, flags):
+    """A quarter of the grid day's trips: at most 1,536 trips are ever due
+    and not yet arrived, so every graph chunk runs in the single-block
+    light-load kernel (flags 0) or in the grid-wide kernels (flags 4 =
+    LPSIM_F_NO_LIGHT); both match the oracle bit for bit at every chunk
+    boundary and at the end."""
+    import oracle as O
+    import workloads as Wk
+    from paper_2406_08496_gb300 import Simulation
+    net, dem = grid_day
+    keep = np.zeros(len(dem["depart_step"]), bool)
+    keep[::4] = True
+    sub = Wk.subset_trips(dem, keep)
+    params = dict(bin_steps=600, n_bins=8)
+    o = O.Oracle(net, params)
+    o.load_demand(sub)
+    g = Simulation(net, dict(params, flags=flags))
+    g.load_demand(sub)
+    for _ in range(8):
+        o.step(384)
+        g.step(384)
+        assert_state_equal(o.state(), g.state(), f"step {o.counters()['k']}")
+    ro = o.run(20000)
+    rg = g.run(20000)
+    for key in ("steps", "veh_steps", "arrived", "active", "waiting", "k"):
+        assert ro[key] == rg[key], (key, ro[key], rg[key])
+    assert_outputs_equal(o, g, n_bins=8)
+    co, cg = o.counters(), g.counters()
+    assert co["lane_changes"] == cg["lane_changes"]
+
+
+def test_light_and_grid_wide_chunks_alternate():
+    """8,000 trips on a 12x12 grid: the chunks switch between the grid-wide
+    kernels and the light-load block as the network fills and drains; every
+    output matches the oracle."""
+    import oracle as O
+    from paper_2406_08496_gb300 import Simulation
+    net = W.grid_network(12, 12)
+    dem = W.route(net, W.uniform_demand(net, 8000, 11, t_max_s=3600.0))
+    params = dict(bin_steps=1200, n_bins=12)
+    o = O.Oracle(net, params)
+    o.load_demand(dem)
+    g = Simulation(net, params)
+    g.load_demand(dem)
+    for _ in range(6):
+        o.step(1536)
+        g.step(1536)
+        assert_state_equal(o.state(), g.state(), f"step {o.counters()['k']}")
+    ro = o.run(60000)
+    rg = g.run(60000)
+    for key in ("steps", "veh_steps", "arrived", "active", "waiting", "k"):
+        assert ro[key] == rg[key], (key, ro[key], rg[key])
+    assert_outputs_equal(o, g, n_bins=12)
