@@ -47,8 +47,9 @@ int lpsim_assign_create(lpsim_assign **out, uint32_t n_nodes, uint32_t n_edges, 
  * n_bins seconds, bin b covers entry steps [b*bin_steps, (b+1)*bin_steps)).
  * Trips with the same origin and departure period (period_steps) share one
  * earliest-arrival tree rooted at the middle of the period.  Keeps each
- * trip's path as its candidate route and its shortest time (s) in t_sp
- * (nullable, n_trips entries). */
+ * trip's tree path as its candidate route and, in t_sp (nullable, n_trips
+ * entries), that path's travel time (s) when left at the trip's own
+ * departure step. */
 int lpsim_assign_shortest_paths(lpsim_assign *a, const float *tt, uint32_t n_bins, uint32_t bin_steps,
                                 uint32_t period_steps, uint32_t n_threads, float *t_sp);
 

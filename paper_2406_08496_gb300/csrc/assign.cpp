@@ -219,7 +219,12 @@ int lpsim_assign_shortest_paths(lpsim_assign *a, const float *tt, uint32_t n_bin
                     v = a->src[e];
                 }
                 a->cand[j].assign(tmp.rbegin(), tmp.rend());
-                a->tsp[j] = (float)(arr[d] - t0);
+                // the tree's path, timed from the trip's own departure (the
+                // same start as its experienced time)
+                const double tj = (double)a->dep[j] * a->dt;
+                double tt_j = tj;
+                for (uint32_t e : a->cand[j]) tt_j += td.cost(e, tt_j);
+                a->tsp[j] = (float)(tt_j - tj);
             }
         }
     };

@@ -15,13 +15,6 @@ constexpr uint8_t kLive = 0;
 constexpr uint8_t kArrivedPending = 1;  // arrived this step: its cell is erased next step
 constexpr uint8_t kDead = 2;
 
-// per-step action of a live slot
-constexpr uint8_t kActStay = 0;
-constexpr uint8_t kActIntend = 1;
-constexpr uint8_t kActHold = 2;
-constexpr uint8_t kActCross = 3;
-constexpr uint8_t kActArrive = 4;
-
 // trip status (public)
 constexpr uint8_t kWaiting = 0;
 constexpr uint8_t kActive = 1;
@@ -131,7 +124,6 @@ struct Slots {
     uint8_t *lane, *flag;
     uint8_t *tlc;      // target lane of the movement after the current edge (kNoLane on the last edge)
     float *x[2], *v[2];
-    uint8_t *act;      // per-step scratch: what the vehicle did this step
 };
 
 // What step_p2 needs of a vehicle that asked to enter its next edge, packed

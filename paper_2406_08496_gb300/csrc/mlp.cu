@@ -419,6 +419,212 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
 }
 
+
+// ------------------------------------------------ fused inference forward
+//
+// All three hidden layers and the head of the inference forward in one
+// persistent kernel.  Per 128-row tile the input slice arrives by TMA; each
+// layer's accumulator (128 x 256 f32) lives in tensor memory; the epilogue
+// writes the layer's BF16 activations straight into shared memory in the
+// 128-byte-swizzled K-major layout that the next layer's MMA reads, so the
+// hidden activations never leave the SM and the forward moves only the
+// inputs (128 B per row) and the outputs (4 B per row) through HBM.  Weights
+// stream from L2 through a ring of 256 x 64 slices.  Roles: warp 0 lane 0
+// loads, warp 1 lane 0 issues the MMAs, warps 2-17 run the epilogues (four per
+// tensor-memory lane quarter, each a quarter of the 256 columns).
+
+constexpr int kFwdEpiWarps = 16;
+constexpr int kFwdThreads = (2 + kFwdEpiWarps) * 32;
+constexpr int kFwdBStages = 3;
+constexpr uint32_t kSliceA = kBM * kBK * 2;  // one 64-wide K slice of a 128-row operand: 16 KB
+constexpr uint32_t kSliceB = 256 * kBK * 2;  // one 64-wide K slice of a weight matrix: 32 KB
+constexpr size_t kFwdSmem = 1024 + 5 * kSliceA + kFwdBStages * kSliceB + 128;  // + 10 mbarriers and the TMEM address
+
+struct FwdArgs {
+    int n_tiles;
+    const float *b1, *b2, *b3, *w4, *b4;
+    float *y;
+    uint32_t *err;
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__global__ void __launch_bounds__(kFwdThreads, 1)
+    mlp_forward_fused(const __grid_constant__ CUtensorMap tX, const __grid_constant__ CUtensorMap tW1,
+                      const __grid_constant__ CUtensorMap tW2, const __grid_constant__ CUtensorMap tW3, FwdArgs g) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *sX = smem;                  // input slice of the tile
+    uint8_t *sA = sX + kSliceA;          // the tile's activations: four K slices
+    uint8_t *sB = sA + 4 * kSliceA;      // weight-slice ring
+    uint64_t *b_full = reinterpret_cast<uint64_t *>(sB + kFwdBStages * kSliceB);
+    uint64_t *b_empty = b_full + kFwdBStages;
+    uint64_t *x_full = b_empty + kFwdBStages;
+    uint64_t *x_empty = x_full + 1;
+    uint64_t *acc_full = x_empty + 1;  // MMA -> epilogue: a layer's accumulator is complete
+    uint64_t *ep_done = acc_full + 1;  // epilogue -> MMA: accumulator drained (and activations written)
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(ep_done + 1);
+    __shared__ volatile int s_fail;
+    __shared__ float s_head[4][kBM];
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        for (int s = 0; s < kFwdBStages; s++) {
+            mbar_init(&b_full[s], 1);
+            mbar_init(&b_empty[s], 1);
+        }
+        mbar_init(x_full, 1);
+        mbar_init(x_empty, 1);
+        mbar_init(acc_full, 1);
+        mbar_init(ep_done, kFwdEpiWarps);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(256));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t bi = 0;
+            int it = 0;
+            for (int t = blockIdx.x; t < g.n_tiles && !s_fail; t += gridDim.x, it++) {
+                // the previous tile's first layer has read the input slice
+                if (it > 0 && !mbar_wait(x_empty, (it - 1) & 1)) {
+                    atomicOr(g.err, 8u);
+                    s_fail = 1;
+                    break;
+                }
+                mbar_expect_tx(x_full, kSliceA);
+                tma_load_2d(sX, &tX, x_full, 0, t * kBM);
+                for (int l = 0; l < 3 && !s_fail; l++) {
+                    const CUtensorMap *tw = l == 0 ? &tW1 : l == 1 ? &tW2 : &tW3;
+                    const int nks = l == 0 ? 1 : 4;
+                    for (int ks = 0; ks < nks; ks++, bi++) {
+                        const int s = bi % kFwdBStages;
+                        if (bi >= kFwdBStages && !mbar_wait(&b_empty[s], ((bi / kFwdBStages) - 1) & 1)) {
+                            atomicOr(g.err, 8u);
+                            s_fail = 1;
+                            break;
+                        }
+                        mbar_expect_tx(&b_full[s], kSliceB);
+                        tma_load_2d(sB + s * kSliceB, tw, &b_full[s], ks * kBK, 0);
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = umma_idesc(256);
+            uint32_t bi = 0, nl = 0;
+            int it = 0;
+            for (int t = blockIdx.x; t < g.n_tiles && !s_fail; t += gridDim.x, it++) {
+                for (int l = 0; l < 3 && !s_fail; l++, nl++) {
+                    if ((nl > 0 && !mbar_wait(ep_done, (nl - 1) & 1)) || (l == 0 && !mbar_wait(x_full, it & 1))) {
+                        atomicOr(g.err, 16u);
+                        s_fail = 1;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const int nks = l == 0 ? 1 : 4;
+                    for (int ks = 0; ks < nks; ks++, bi++) {
+                        const int s = bi % kFwdBStages;
+                        if (!mbar_wait(&b_full[s], (bi / kFwdBStages) & 1)) {
+                            atomicOr(g.err, 16u);
+                            s_fail = 1;
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t a0 = l == 0 ? smem_u32(sX) : smem_u32(sA + ks * kSliceA);
+                        const uint32_t b0 = smem_u32(sB + s * kSliceB);
+#pragma unroll
+                        for (int kk = 0; kk < kBK / 16; kk++)
+                            umma_f16(tmem, umma_desc(a0 + kk * 32), umma_desc(b0 + kk * 32), idesc, (ks | kk) != 0);
+                        umma_commit(&b_empty[s]);
+                    }
+                    if (l == 0) umma_commit(x_empty);
+                    umma_commit(acc_full);
+                }
+            }
+        }
+    } else {
+        // epilogue warps: rows q*32 + lane of the tile, columns [64 cq, 64 cq + 64)
+        const int q = warp & 3, cq = (warp - 2) >> 2;
+        const int row = q * 32 + lane;
+        uint32_t nl = 0;
+        for (int t = blockIdx.x; t < g.n_tiles; t += gridDim.x) {
+            float head = 0.0f;
+            for (int l = 0; l < 3; l++, nl++) {
+                const bool ok = !s_fail && mbar_wait(acc_full, nl & 1);
+                if (!ok) {
+                    if (!s_fail) atomicOr(g.err, 32u);
+                    s_fail = 1;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const float *bias = l == 0 ? g.b1 : l == 1 ? g.b2 : g.b3;
+#pragma unroll 1
+                for (int c2 = 0; c2 < 2 && ok; c2++) {
+                    const int c0 = cq * 64 + c2 * 32;
+                    uint32_t r[32];
+                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
+                    uint32_t hp[16];
+#pragma unroll
+                    for (int q4 = 0; q4 < 8; q4++) {
+                        const float4 b4v = reinterpret_cast<const float4 *>(bias + c0)[q4];
+                        float4 w4v = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (l == 2) w4v = reinterpret_cast<const float4 *>(g.w4 + c0)[q4];
+                        const float bq[4] = {b4v.x, b4v.y, b4v.z, b4v.w};
+                        const float wq[4] = {w4v.x, w4v.y, w4v.z, w4v.w};
+                        __nv_bfloat16 hb[4];
+#pragma unroll
+                        for (int u = 0; u < 4; u++) {
+                            const float z = __uint_as_float(r[4 * q4 + u]) + bq[u];
+                            hb[u] = __float2bfloat16_rn(0.5f * z * (1.0f + erff(z * 0.70710678118654752f)));
+                            if (l == 2) head += __bfloat162float(hb[u]) * wq[u];
+                        }
+                        const __nv_bfloat162 p0 = __halves2bfloat162(hb[0], hb[1]);
+                        const __nv_bfloat162 p1 = __halves2bfloat162(hb[2], hb[3]);
+                        hp[2 * q4] = *reinterpret_cast<const uint32_t *>(&p0);
+                        hp[2 * q4 + 1] = *reinterpret_cast<const uint32_t *>(&p1);
+                    }
+                    if (l < 2) {
+                        // next layer's A operand: K slice c0 / 64, 16-byte chunks (c0 % 64) / 8 .. + 3 of this
+                        // row, at the 128-byte-swizzled positions (chunk ^ row % 8) TMA would have used
+                        const int ch0 = (c0 & 63) >> 3;
+                        uint8_t *rowp = sA + (c0 >> 6) * kSliceA + (row >> 3) * 1024 + (row & 7) * 128;
+#pragma unroll
+                        for (int i = 0; i < 4; i++)
+                            *reinterpret_cast<uint4 *>(rowp + (((ch0 + i) ^ (row & 7)) << 4)) =
+                                make_uint4(hp[4 * i], hp[4 * i + 1], hp[4 * i + 2], hp[4 * i + 3]);
+                    }
+                }
+                // the activations written by the generic proxy are read by the tensor cores next
+                if (l < 2) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(ep_done);
+            }
+            // the head: the four column quarters of each row, added in order
+            s_head[cq][row] = head;
+            asm volatile("bar.sync 1, %0;" ::"r"(kFwdEpiWarps * 32) : "memory");
+            if (cq == 0 && !s_fail)
+                g.y[t * kBM + row] = (((s_head[0][row] + s_head[1][row]) + s_head[2][row]) + s_head[3][row]) + *g.b4;
+            asm volatile("bar.sync 1, %0;" ::"r"(kFwdEpiWarps * 32) : "memory");
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+}
+
 // ---------------------------------------------------------- small kernels
 
 // X (n x nf f32, host layout) -> Xb (n_pad x 64 bf16, zero padded) and its
@@ -612,6 +818,7 @@ int launch_gemm(const CUtensorMap &a, const CUtensorMap &b, const GemmArgs &g_in
 
 struct lpsim_mlp {
     int device = 0;
+    int n_sm = 1;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int nf = 9;       // real input features
@@ -676,7 +883,31 @@ int refresh_weights(lpsim_mlp *m) {
 // forward of rows [0, B) already packed in X0; keep = training buffers
 // training keeps the pre-activations (for GELU') and transposed activations
 // (for the weight gradients); inference writes only the activations
+int forward_fused(lpsim_mlp *m) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        CU(cudaFuncSetAttribute(mlp_forward_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem));
+        attr_set = true;
+    }
+    FwdArgs g{};
+    g.n_tiles = m->B / kBM;
+    g.b1 = m->P[1];
+    g.b2 = m->P[3];
+    g.b3 = m->P[5];
+    g.w4 = m->P[6];
+    g.b4 = m->P[7];
+    g.y = m->y;
+    g.err = m->err;
+    const int grid = std::min(g.n_tiles, m->n_sm);
+    mlp_forward_fused<<<grid, kFwdThreads, kFwdSmem, m->stream>>>(m->mX0, m->mW[0], m->mW[1], m->mW[2], g);
+    m->launches++;
+    CU(cudaGetLastError());
+    return LPSIM_OK;
+}
+
 int forward_batch(lpsim_mlp *m, bool training = true) {
+    // inference: every layer in one kernel, activations kept on chip
+    if (!training) return forward_fused(m);
     cudaStream_t st = m->stream;
     for (int l = 0; l < 3; l++) {
         GemmArgs g{};
@@ -791,6 +1022,7 @@ int lpsim_mlp_create(lpsim_mlp **out, uint32_t n_features, uint32_t batch, uint6
         return rc;
     };
     cudaGetDevice(&m->device);
+    cudaDeviceGetAttribute(&m->n_sm, cudaDevAttrMultiProcessorCount, m->device);
     m->stream = static_cast<cudaStream_t>(stream);
     if (!m->stream) {
         if (cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking) != cudaSuccess)

@@ -104,8 +104,6 @@ int alloc_slots(lpsim_ctx *c, Slots &s, uint32_t cap) {
         TRY(dnew_mut(c, s.x[i], cap));
         TRY(dnew_mut(c, s.v[i], cap));
     }
-    // per-step scratch, rewritten before it is read in every step
-    TRY(dnew(c, s.act, cap));
     return LPSIM_OK;
 }
 

@@ -390,7 +390,6 @@ __device__ __forceinline__ bool p1_slot(const Dev &d, const StepView &w, uint32_
             d.arr[id] = k + 1;
             d.status[id] = kArrived;
             d.s.flag[s] = kArrivedPending;
-            d.s.act[s] = kActArrive;
             arrived++;
             return true;
         }
@@ -425,7 +424,6 @@ __device__ __forceinline__ bool p1_slot(const Dev &d, const StepView &w, uint32_
                 cr.nsph = (uint16_t)(rr.nphase | (rr.arank << 8));
                 cr.lane = (uint8_t)l;
                 cr.tln = rr.tl;
-                d.s.act[s] = kActCross;
                 d.cross_list[par][warp_append(&d.counts[par])] = cr;
                 cross = true;
             }
@@ -436,7 +434,6 @@ __device__ __forceinline__ bool p1_slot(const Dev &d, const StepView &w, uint32_
             xw[s] = xh;
             vw[s] = 0.0f;
             put_cell(d, Mn, base + (uint32_t)xh, 0);
-            d.s.act[s] = kActHold;
         }
         return true;
     }
@@ -444,13 +441,11 @@ __device__ __forceinline__ bool p1_slot(const Dev &d, const StepView &w, uint32_
     vw[s] = vn;
     const uint32_t cn = (uint32_t)xn;
     put_cell(d, Mn, base + cn, speed_byte(vn));
-    uint8_t act = kActStay;
     if (may_draw) {
         const float xrem = L - x;
         const float mp = xrem >= m.x0 ? 0.0f : 1.0f - xrem / m.x0;
         // u is in [0, 1): no draw can pass when mp <= 0
         if (mp > 0.0f && unit24(splitmix64_mix(hk ^ ((uint64_t)k * 0xD1B54A32D192ED03ull))) < mp) {
-            act = kActIntend;
             Iw[base + cn] = 1;
             d.s.imark[s] = base + cn;
             IntendRec ir;
@@ -466,7 +461,6 @@ __device__ __forceinline__ bool p1_slot(const Dev &d, const StepView &w, uint32_
             d.intend_list[par][warp_append(&d.counts[2 + par])] = ir;
         }
     }
-    d.s.act[s] = act;
     return true;
 }
 

@@ -73,9 +73,12 @@ def test_time_dependent_paths_match_brute_force(A):
         for j in range(5):
             t0 = ((dep[j] // period) + 0.5) * period * dt
             best = min(_arrival(p, t0, tt, bin_s) for p in _all_paths(edges, 0, 3))
-            assert abs(tsp[j] - (best - t0)) < 1e-3
             r = routes["route_edges"][int(routes["route_off"][j]):int(routes["route_off"][j + 1])]
+            # the route is an earliest-arrival path from the period's middle ...
             assert abs(_arrival(list(r), t0, tt, bin_s) - best) < 1e-3
+            # ... and its time is counted from the trip's own departure
+            tj = float(dep[j]) * dt
+            assert abs(tsp[j] - (_arrival(list(r), tj, tt, bin_s) - tj)) < 1e-3
 
 
 def test_gap_formula(A):
