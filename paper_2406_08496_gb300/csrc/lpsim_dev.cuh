@@ -190,6 +190,15 @@ struct Dev {
     IntendRec *intend_list[2];
     uint32_t *counts;          // [0..1] cross count by parity, [2..3] intend count, [4..5] departure requests
     DepRec *dep_rec[2];        // departure requests, by parity
+    // crossings of the current chunk (or direct step), applied to the link
+    // statistics by one kernel at its end instead of seven scattered atomics
+    // per crossing inside step_p2: {edge left, edge entered, step the edge
+    // left was entered, step} or {kNone, ...} for a crossing request that lost.
+    // *ev_n entries so far; past ev_cap the crossings update the counters
+    // directly.
+    uint4 *ev_log;
+    uint32_t ev_cap;
+    uint32_t *ev_n;
     // statistics; binned arrays are bin-major ([bin][edge]) so the updates of
     // one step fall in one or two rows that stay in L2
     unsigned long long *ent, *ext, *tts;
@@ -212,6 +221,8 @@ struct Dev {
 // parity buffers and the rotating lane maps without waiting for *kbase
 void launch_phase(const Dev &d, int phase, uint32_t koff, uint32_t kph, int grid, int block, cudaStream_t st);
 void launch_chunk_end(const Dev &d, uint32_t steps, cudaStream_t st);
+// the logged crossings of the chunk into the link statistics (before chunk_end)
+void launch_apply_crossings(const Dev &d, int grid, cudaStream_t st);
 // steps [k0, k0 + nsteps) in one block (light load); olist: n_org scratch
 // entries, no: one device counter
 cudaError_t launch_small(const Dev &d, uint32_t k0, uint32_t nsteps, uint32_t *olist, uint32_t *no,

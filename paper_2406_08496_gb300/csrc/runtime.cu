@@ -127,6 +127,7 @@ int reset_state(lpsim_ctx *c) {
     CU(cudaMemsetAsync(d.counts, 0, 8 * 4, st));
     CU(cudaMemsetAsync(d.kbase, 0, 4, st));
     CU(cudaMemsetAsync(d.n_slots, 0, 4, st));
+    CU(cudaMemsetAsync(d.ev_n, 0, 4, st));
     CU(cudaMemsetAsync(d.ctr, 0, 8 * 8, st));
     CU(cudaMemsetAsync(d.err, 0, 4, st));
     if (c->loaded) {
@@ -166,16 +167,20 @@ int enqueue_step(lpsim_ctx *c, uint32_t koff, uint32_t kph, int cur, bool compac
     d.s = c->sets[cur];
     cudaEvent_t *e = c->timing ? &c->ev[5 * koff] : nullptr;
     // cudaEventRecordExternal: inside a stream capture the record becomes an
-    // event-record node that timestamps when the graph runs
+    // event-record node that timestamps when the graph runs (the flag is for
+    // captures only; a direct step records plainly)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (e) cudaStreamIsCapturing(c->stream, &cs);
+    const unsigned flags = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
     for (int ph = 1; ph <= 3; ph++) {
-        if (e) cudaEventRecordWithFlags(e[ph - 1], c->stream, cudaEventRecordExternal);
+        if (e) cudaEventRecordWithFlags(e[ph - 1], c->stream, flags);
         launch_phase(d, ph, koff, kph, c->grid, c->block, c->stream);
     }
-    if (e) cudaEventRecordWithFlags(e[3], c->stream, cudaEventRecordExternal);
+    if (e) cudaEventRecordWithFlags(e[3], c->stream, flags);
     if (compact) {
         launch_compact(d, c->sets[cur ^ 1], c->w, koff, c->sort, c->grid, c->stream);
         cur ^= 1;
-        if (e) cudaEventRecordWithFlags(e[4], c->stream, cudaEventRecordExternal);
+        if (e) cudaEventRecordWithFlags(e[4], c->stream, flags);
     }
     return cur;
 }
@@ -206,8 +211,9 @@ int direct_step(lpsim_ctx *c) {
     c->cur = enqueue_step(c, 0, (uint32_t)(c->k % 6), c->cur, compact);
     c->launches += 3;
     if (compact) c->launches += c->sort ? 3 + 3ull * ((c->w.key_bits + 7) / 8) + 1 : 3;
+    launch_apply_crossings(c->d, c->grid, c->stream);
     launch_chunk_end(c->d, 1, c->stream);
-    c->launches += 1;
+    c->launches += 2;
     CU(cudaGetLastError());
     if (c->timing) {
         CU(cudaStreamSynchronize(c->stream));
@@ -223,6 +229,7 @@ int capture_chunk(lpsim_ctx *c, int start_set) {
     int cur = start_set;
     // a chunk always starts at a multiple of C, itself a multiple of 6
     for (uint32_t koff = 0; koff < c->C; koff++) cur = enqueue_step(c, koff, koff, cur, (koff + 1) % c->R == 0);
+    launch_apply_crossings(c->d, c->grid, c->stream);
     launch_chunk_end(c->d, c->C, c->stream);
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     if (e != cudaSuccess) return fail(LPSIM_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
@@ -237,7 +244,7 @@ int capture_chunk(lpsim_ctx *c, int start_set) {
 uint64_t chunk_launches(const lpsim_ctx *c) {
     uint64_t per_compact = 3;
     if (c->sort) per_compact = 2 + 1 + 3ull * ((c->w.key_bits + 7) / 8) + 1;
-    return 3ull * c->C + (c->C / c->R) * per_compact + 1;
+    return 3ull * c->C + (c->C / c->R) * per_compact + 2;
 }
 
 int chunk(lpsim_ctx *c) {
@@ -272,9 +279,10 @@ int light_chunk(lpsim_ctx *c) {
     CU(launch_small(d, c->k, c->C, c->small_list, c->small_n, c->stream));
     launch_compact(d, c->sets[c->cur ^ 1], c->w, c->C - 1, c->sort, c->grid, c->stream);
     c->cur ^= 1;
+    launch_apply_crossings(c->d, c->grid, c->stream);
     launch_chunk_end(c->d, c->C, c->stream);
     CU(cudaGetLastError());
-    c->launches += 3 + (c->sort ? 3 + 3ull * ((c->w.key_bits + 7) / 8) + 1 : 3);
+    c->launches += 4 + (c->sort ? 3 + 3ull * ((c->w.key_bits + 7) / 8) + 1 : 3);
     c->light_chunks++;
     c->k += c->C;
     return LPSIM_OK;
@@ -527,6 +535,7 @@ int load_network_impl(lpsim_ctx **out, const lpsim_network *net, const lpsim_par
         (rc = dnew_mut(c, d.bin_occ, nb)))
         return bail(rc);
     if ((rc = dnew_mut(c, d.counts, 8)) || (rc = dnew_mut(c, d.kbase, 1)) || (rc = dnew_mut(c, d.n_slots, 1)) ||
+        (rc = dnew_mut(c, d.ev_n, 1)) ||
         (rc = dnew_mut(c, d.ctr, 8)) || (rc = dnew_mut(c, d.err, 1)) || (rc = dnew(c, c->d_tmp, 4)))
         return bail(rc);
     if (cudaMallocHost(&c->h_ctr, 16 * 8) != cudaSuccess) return bail(fail(LPSIM_E_OOM, "pinned allocation failed"));
@@ -722,6 +731,10 @@ int load_demand_impl(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, cons
     TRY(dnew(c, c->org_hd0, norg));
     TRY(dnew_mut(c, d.dprev, norg));
     for (int i = 0; i < 2; i++) TRY(dnew(c, d.dep_rec[i], norg));
+    // crossing log: room for a chunk at the busiest hour of a day (past it the
+    // step kernels update the statistics directly)
+    d.ev_cap = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(4ull * n, 1ull << 20), 1ull << 25);
+    TRY(dnew(c, d.ev_log, d.ev_cap));
     TRY(dnew(c, c->small_list, std::max<uint32_t>(norg, 1u)));
     TRY(dnew(c, c->small_n, 4));
     // slots: live vehicles plus the holes left between compactions by

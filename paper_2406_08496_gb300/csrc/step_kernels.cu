@@ -249,14 +249,16 @@ __device__ __forceinline__ void p1_origin(const Dev &d, const StepView &w, uint3
     uint32_t *claim = w.claim, *claim_old = w.claim_old;
     const uint32_t dp = d.dprev[j];
     const QRec hd = d.org_hd[j];
-    const EdgeRec er = d.org_rec[j];
-    const uint32_t e0 = d.org_edge[j];
-    const uint32_t qoff = d.org_qoff[j], qhead = d.org_head[j], qend = d.org_qend[j];
     if (dp != kNone) {
         claim_old[dp] = kNone;
         d.dprev[j] = kNone;
     }
     if (hd.h != kNone && hd.dep <= k) {
+        // only a due head needs its origin's records (most origin edges are
+        // idle in most steps)
+        const EdgeRec er = d.org_rec[j];
+        const uint32_t e0 = d.org_edge[j];
+        const uint32_t qoff = d.org_qoff[j], qhead = d.org_head[j], qend = d.org_qend[j];
         const RouteRec rr = d.rrec[hd.r0];
         const uint32_t nxt = hd.r0 + 1 < hd.r1 ? d.route[hd.r0 + 1] : kNone;
         const uint32_t so = d.slot_off[e0];
@@ -489,14 +491,19 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) step_p1(Dev d, uint32_t k
 
 // Crossing request cr: the lowest id asking for the (edge, lane) enters its
 // cell 0, the others hold at the stop line.
-__device__ __forceinline__ void p2_cross(const Dev &d, const StepView &w, const CrossRec &cr, uint32_t &events) {
+__device__ __forceinline__ void p2_cross(const Dev &d, const StepView &w, const CrossRec &cr, uint32_t ev,
+                                         uint32_t &events) {
     const uint32_t k = w.k;
     uint8_t *Mn = w.Mn;
     float *xw = w.xw, *vw = w.vw;
     if (w.claim[cr.cslot] == cr.id) {
         const uint32_t s = cr.s;
-        stat_exit(d, cr.e, k, cr.tent);
-        stat_entry(d, cr.en, k);
+        if (ev < d.ev_cap) {
+            d.ev_log[ev] = make_uint4(cr.e, cr.en, cr.tent, k);
+        } else {
+            stat_exit(d, cr.e, k, cr.tent);
+            stat_entry(d, cr.en, k);
+        }
         EdgeState ne;
         ne.base = cr.nbase;
         ne.e = cr.en;
@@ -516,6 +523,7 @@ __device__ __forceinline__ void p2_cross(const Dev &d, const StepView &w, const 
         put_cell(d, Mn, cr.nbase, speed_byte(cr.vn));
         events++;
     } else {
+        if (ev < d.ev_cap) d.ev_log[ev] = make_uint4(kNone, 0u, 0u, 0u);
         const float lim = (float)cr.len - 1.0f;
         const float xh = cr.x > lim ? cr.x : lim;
         xw[cr.s] = xh;
@@ -589,13 +597,14 @@ __global__ void __launch_bounds__(BLOCK) step_p2(Dev d, uint32_t koff, uint32_t 
     uint32_t events = 0, departed = 0;
     if (crossers) {
         const uint32_t ncross = d.counts[par];
+        const uint32_t ev0 = *d.ev_n;  // this step's crossings follow the chunk's earlier ones in the log
         const uint32_t nthr = (gridDim.x - gdep) * BLOCK;
         const CrossRec *list = d.cross_list[par];
         for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < d.cap; i += nthr) {
             const CrossRec cr = list[i];
             loads_issued();
             if (i >= ncross) break;
-            p2_cross(d, w, cr, events);
+            p2_cross(d, w, cr, ev0 + i, events);
         }
     } else {
         const uint32_t ndep = d.counts[4 + par];
@@ -703,6 +712,7 @@ __device__ __forceinline__ void step_tail(const Dev &d, uint32_t par) {
     d.counts[2 + (par ^ 1u)] = 0;
     d.counts[4 + (par ^ 1u)] = 0;
     *d.n_slots += d.counts[4 + par];
+    *d.ev_n += d.counts[par];
 }
 
 template <int BLOCK>
@@ -750,8 +760,8 @@ __global__ void __launch_bounds__(kSmallBlock, 1)
         __syncthreads();
         // P2
         uint32_t events = 0, departed = 0;
-        const uint32_t ncross = d.counts[par], ndep = d.counts[4 + par];
-        for (uint32_t i = tid; i < ncross; i += kSmallBlock) p2_cross(d, w, d.cross_list[par][i], events);
+        const uint32_t ncross = d.counts[par], ndep = d.counts[4 + par], ev0 = *d.ev_n;
+        for (uint32_t i = tid; i < ncross; i += kSmallBlock) p2_cross(d, w, d.cross_list[par][i], ev0 + i, events);
         for (uint32_t q = tid; q < ndep; q += kSmallBlock) p2_dep(d, w, d.dep_rec[par][q], q, n, events, departed);
         if (events) atomicAdd(&d.ctr[3], (unsigned long long)events);
         if (departed) atomicAdd(&d.ctr[4], (unsigned long long)departed);
@@ -794,9 +804,21 @@ __global__ void route_records(Dev d, uint64_t n, RouteRec *out) {
     }
 }
 
+// the crossing log of the chunk into the link statistics
+__global__ void apply_crossings(Dev d) {
+    const uint32_t n = min(*d.ev_n, d.ev_cap);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint4 r = d.ev_log[i];
+        if (r.x == kNone) continue;
+        stat_exit(d, r.x, r.w, r.z);
+        stat_entry(d, r.y, r.w);
+    }
+}
+
 __global__ void chunk_end(Dev d, uint32_t steps) {
     pdl_prologue();
     *d.kbase += steps;
+    *d.ev_n = 0;
 }
 
 namespace {
@@ -839,6 +861,8 @@ void launch_phase(const Dev &d, int phase, uint32_t koff, uint32_t kph, int grid
 }
 
 void launch_chunk_end(const Dev &d, uint32_t steps, cudaStream_t st) { launch_pdl(chunk_end, 1, 1, st, d, steps); }
+
+void launch_apply_crossings(const Dev &d, int grid, cudaStream_t st) { apply_crossings<<<grid, 256, 0, st>>>(d); }
 
 cudaError_t launch_small(const Dev &d, uint32_t k0, uint32_t nsteps, uint32_t *olist, uint32_t *no,
                          cudaStream_t st) {

@@ -193,3 +193,24 @@ def test_light_and_grid_wide_chunks_alternate():
     for key in ("steps", "veh_steps", "arrived", "active", "waiting", "k"):
         assert ro[key] == rg[key], (key, ro[key], rg[key])
     assert_outputs_equal(o, g, n_bins=12)
+
+
+def test_kernel_timing_direct_and_graph_steps(grid_day):
+    """Per-kernel timing around direct steps and graph chunks alike, and the
+    results unchanged by it."""
+    from paper_2406_08496_gb300 import Simulation
+    net, dem = grid_day
+    g = Simulation(net, {})
+    g.load_demand(dem)
+    g.set_kernel_timing(True)
+    g.step(5)      # direct steps (not at a chunk boundary afterwards)
+    g.step(379)    # direct steps up to the chunk boundary
+    g.step(768)    # two graph chunks
+    kt = g.kernel_times()
+    g.set_kernel_timing(False)
+    assert kt["step_p1"]["launches"] == 1152 and kt["step_p1"]["ms"] > 0
+    assert kt["step_p2"]["ms"] > 0 and kt["step_p3"]["ms"] > 0
+    ref = Simulation(net, {})
+    ref.load_demand(dem)
+    ref.step(1152)
+    assert_state_equal(ref.state(), g.state(), "timing on vs off")
