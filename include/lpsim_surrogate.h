@@ -61,6 +61,12 @@ int lpsim_mlp_gemm_test(uint32_t M, uint32_t N, uint32_t K, const uint16_t *A, c
  * train_ms is not NULL, of one training forward + backward pass. */
 int lpsim_mlp_time(lpsim_mlp *m, uint32_t iters, double *fwd_ms, double *train_ms);
 
+/* Diagnostics: GELU(z) and GELU'(z) of n inputs (host arrays) as the
+ * tensor-core epilogues compute them -- z Phi(z) and Phi(z) + z phi(z) with
+ * the standard normal CDF from Abramowitz and Stegun 26.2.17 (|error| <
+ * 7.5e-8) -- so that tests can hold them to their error bound. */
+int lpsim_mlp_gelu_eval(uint64_t n, const float *z, float *gelu, float *dgelu);
+
 void lpsim_mlp_destroy(lpsim_mlp *m);
 
 #ifdef __cplusplus

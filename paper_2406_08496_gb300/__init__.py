@@ -33,7 +33,8 @@ EXPORTED = ["lpsim_last_error", "lpsim_version", "lpsim_set_allocator", "lpsim_l
             "lpsim_load_network_batch", "lpsim_load_demand_batch", "lpsim_batch_offsets", "lpsim_snapshot",
             "lpsim_restore", "lpsim_autotune", "lpsim_set_config", "lpsim_destroy",
             "lpsim_mlp_create", "lpsim_mlp_set_params", "lpsim_mlp_get_params", "lpsim_mlp_forward",
-            "lpsim_mlp_grad", "lpsim_mlp_train", "lpsim_mlp_gemm_test", "lpsim_mlp_time", "lpsim_mlp_destroy",
+            "lpsim_mlp_grad", "lpsim_mlp_train", "lpsim_mlp_gemm_test", "lpsim_mlp_time", "lpsim_mlp_gelu_eval",
+            "lpsim_mlp_destroy",
             "lpsim_assign_create", "lpsim_assign_shortest_paths", "lpsim_assign_gap", "lpsim_assign_reroute",
             "lpsim_assign_route_excess", "lpsim_assign_reroute_worst", "lpsim_assign_route_length",
             "lpsim_assign_get_routes", "lpsim_assign_load", "lpsim_assign_features", "lpsim_assign_link_times", "lpsim_assign_times_from_ratio", "lpsim_assign_destroy"]
@@ -139,6 +140,7 @@ def load_library(path: str | None = None):
     lib.lpsim_mlp_train.argtypes = [P, ctypes.c_uint64, P, P, ctypes.c_uint32, ctypes.c_float, ctypes.c_uint64, P]
     lib.lpsim_mlp_gemm_test.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, P, P, P]
     lib.lpsim_mlp_time.argtypes = [P, ctypes.c_uint32, P, P]
+    lib.lpsim_mlp_gelu_eval.argtypes = [ctypes.c_uint64, P, P, P]
     lib.lpsim_mlp_destroy.argtypes = [P]
     lib.lpsim_mlp_destroy.restype = None
     _lib = lib
@@ -410,6 +412,16 @@ def gemm_bf16(A: np.ndarray, B: np.ndarray) -> np.ndarray:
     D = np.empty((M, N), np.float32)
     _check(lib, lib.lpsim_mlp_gemm_test(M, N, K, _p(A), _p(B), _p(D)))
     return D
+
+
+def gelu_eval(z: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """GELU(z) and GELU'(z) as the surrogate's epilogues compute them."""
+    lib = load_library()
+    z = np.ascontiguousarray(z, dtype=np.float32)
+    g = np.empty_like(z)
+    dg = np.empty_like(z)
+    _check(lib, lib.lpsim_mlp_gelu_eval(z.size, _p(z), _p(g), _p(dg)))
+    return g, dg
 
 
 class Surrogate:

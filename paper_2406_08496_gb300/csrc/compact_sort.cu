@@ -133,6 +133,7 @@ __device__ __forceinline__ void copy_slot(const Slots &a, uint32_t s, const Slot
     reinterpret_cast<uint4 *>(b.es + o)[1] = reinterpret_cast<const uint4 *>(a.es + s)[1];
     b.id[o] = a.id[s];
     b.rlast[o] = a.rlast[s];
+    b.tent[o] = a.tent[s];
     b.pcell[o] = a.pcell[s];
     b.imark[o] = a.imark[s];
     b.cprev[o] = a.cprev[s];

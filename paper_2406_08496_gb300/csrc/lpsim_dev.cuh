@@ -74,38 +74,46 @@ struct __align__(16) QRec {
 
 // What a vehicle copies when it enters an edge, plus its lane row (which a
 // lane change moves): one 32-byte record per slot, read with two 16-byte
-// loads and rewritten on entry with two 16-byte stores into one sector.
+// loads and rewritten on entry with two 16-byte stores into one sector.  It
+// holds the next edge's lane-map row geometry too, so a vehicle that may
+// reach the stop line reads the entry cells of the next edge in the same
+// round trip as its own leader scan.
 struct __align__(32) EdgeState {
     uint32_t base;     // lane-map offset of cell 0 of the current lane
-    uint32_t e;        // current edge
-    uint32_t rpos;     // route position of the current edge
-    uint32_t tent;     // step the vehicle entered the current edge
+    uint32_t rpos;     // route position of the current edge (the edge is route[rpos])
     uint32_t en;       // next edge of the route, kNone on the last edge
     uint32_t sg;       // green steps of the signal at the end of the current edge (0 = none)
     float v0;          // speed limit of the current edge
+    uint32_t nmoff;    // lane-map offset of lane 0 of the next edge (0 on the last edge)
     uint16_t len;      // cells per lane of the current edge
     uint16_t sph;      // phases of that signal | phase of the current edge << 8
+    uint16_t nlen;     // cells per lane of the next edge
+    uint8_t nlanes;    // lanes of the next edge
+    uint8_t pad;
 };
 
 __device__ __forceinline__ EdgeState load_es(const EdgeState *p) {
     const uint4 a = reinterpret_cast<const uint4 *>(p)[0], b = reinterpret_cast<const uint4 *>(p)[1];
     EdgeState r;
     r.base = a.x;
-    r.e = a.y;
-    r.rpos = a.z;
-    r.tent = a.w;
-    r.en = b.x;
-    r.sg = b.y;
-    r.v0 = __uint_as_float(b.z);
-    r.len = (uint16_t)(b.w & 0xFFFFu);
-    r.sph = (uint16_t)(b.w >> 16);
+    r.rpos = a.y;
+    r.en = a.z;
+    r.sg = a.w;
+    r.v0 = __uint_as_float(b.x);
+    r.nmoff = b.y;
+    r.len = (uint16_t)(b.z & 0xFFFFu);
+    r.sph = (uint16_t)(b.z >> 16);
+    r.nlen = (uint16_t)(b.w & 0xFFFFu);
+    r.nlanes = (uint8_t)((b.w >> 16) & 0xFFu);
+    r.pad = 0;
     return r;
 }
 
 __device__ __forceinline__ void store_es(EdgeState *p, const EdgeState &r) {
-    reinterpret_cast<uint4 *>(p)[0] = make_uint4(r.base, r.e, r.rpos, r.tent);
-    reinterpret_cast<uint4 *>(p)[1] =
-        make_uint4(r.en, r.sg, __float_as_uint(r.v0), (uint32_t)r.len | ((uint32_t)r.sph << 16));
+    reinterpret_cast<uint4 *>(p)[0] = make_uint4(r.base, r.rpos, r.en, r.sg);
+    reinterpret_cast<uint4 *>(p)[1] = make_uint4(__float_as_uint(r.v0), r.nmoff,
+                                                 (uint32_t)r.len | ((uint32_t)r.sph << 16),
+                                                 (uint32_t)r.nlen | ((uint32_t)r.nlanes << 16));
 }
 
 // Vehicle slots.  x and v are double-buffered by step parity: step k reads
@@ -118,6 +126,7 @@ struct Slots {
     EdgeState *es;
     // persistent
     uint32_t *id, *rlast;
+    uint32_t *tent;    // step the vehicle entered its current edge
     uint32_t *pcell;   // cell of the previous step (erased this step), kNone
     uint32_t *imark;   // intent mark of the previous step (cleared this step), kNone
     uint32_t *cprev;   // claim slot won at the previous step (reset this step), kNone

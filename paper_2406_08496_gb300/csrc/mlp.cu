@@ -218,6 +218,25 @@ __device__ __forceinline__ void store_cols_bf16(const float *stage, __nv_bfloat1
     }
 }
 
+// Standard normal CDF and density for GELU(z) = z Phi(z) and
+// GELU'(z) = Phi(z) + z phi(z): the rational approximation of Abramowitz and
+// Stegun 26.2.17, Phi(x) = 1 - phi(x) (b1 t + ... + b5 t^5), t = 1 / (1 + p x)
+// for x >= 0 (|error| < 7.5e-8; Phi(-x) = 1 - Phi(x)).  Two MUFU operations
+// (reciprocal, exponential) and a short Horner chain, against the longer
+// general-purpose erf; the error is far below the BF16 rounding of the
+// activations.
+__device__ __forceinline__ void norm_cdf_pdf(float z, float &cdf, float &pdf) {
+    const float az = fabsf(z);
+    const float t = __fdividef(1.0f, __fmaf_rn(0.2316419f, az, 1.0f));
+    pdf = 0.3989422804f * __expf(-0.5f * z * z);
+    float poly = __fmaf_rn(1.330274429f, t, -1.821255978f);
+    poly = __fmaf_rn(poly, t, 1.781477937f);
+    poly = __fmaf_rn(poly, t, -0.356563782f);
+    poly = __fmaf_rn(poly, t, 0.319381530f);
+    const float tail = pdf * (poly * t);  // 1 - Phi(|z|)
+    cdf = z >= 0.0f ? 1.0f - tail : tail;
+}
+
 // ------------------------------------------------------------- GEMM kernel
 
 template <int BN, int EPI>
@@ -355,12 +374,12 @@ __global__ void __launch_bounds__(kThreads, 2)
                         for (int u = 0; u < 4; u++) {
                             const int j = 4 * q4 + u;
                             const float z = __uint_as_float(r[j]) + bq[u];
-                            const float e = erff(z * 0.70710678118654752f);
-                            hb[u] = __float2bfloat16_rn(0.5f * z * (1.0f + e));
+                            float cdf, pdf;
+                            norm_cdf_pdf(z, cdf, pdf);
+                            hb[u] = __float2bfloat16_rn(z * cdf);
                             const float h = __bfloat162float(hb[u]);
                             if (g.htout) mh[j] = h;
-                            if (g.gout)
-                                mz[j] = 0.5f * (1.0f + e) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+                            if (g.gout) mz[j] = cdf + z * pdf;
                             if (EPI == kEpiGeluHead) head += h * wq[u];
                         }
                         const __nv_bfloat162 p0 = __halves2bfloat162(hb[0], hb[1]);
@@ -587,7 +606,9 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
 #pragma unroll
                         for (int u = 0; u < 4; u++) {
                             const float z = __uint_as_float(r[4 * q4 + u]) + bq[u];
-                            hb[u] = __float2bfloat16_rn(0.5f * z * (1.0f + erff(z * 0.70710678118654752f)));
+                            float cdf, pdf;
+                            norm_cdf_pdf(z, cdf, pdf);
+                            hb[u] = __float2bfloat16_rn(z * cdf);
                             if (l == 2) head += __bfloat162float(hb[u]) * wq[u];
                         }
                         const __nv_bfloat162 p0 = __halves2bfloat162(hb[0], hb[1]);
@@ -626,6 +647,16 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
 }
 
 // ---------------------------------------------------------- small kernels
+
+// GELU and its derivative as the epilogues compute them (diagnostics)
+__global__ void gelu_eval(const float *z, uint64_t n, float *gelu, float *dgelu) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        float cdf, pdf;
+        norm_cdf_pdf(z[i], cdf, pdf);
+        gelu[i] = z[i] * cdf;
+        dgelu[i] = cdf + z[i] * pdf;
+    }
+}
 
 // X (n x nf f32, host layout) -> Xb (n_pad x 64 bf16, zero padded) and its
 // transpose.  Block (32, 8) handles a 32-row x 32-column tile; the transposed
@@ -1270,6 +1301,23 @@ int lpsim_mlp_time(lpsim_mlp *m, uint32_t iters, double *fwd_ms, double *train_m
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return mlp_check_err(m);
+}
+
+int lpsim_mlp_gelu_eval(uint64_t n, const float *z, float *gelu, float *dgelu) {
+    if (!z || !gelu || !dgelu) return fail(LPSIM_E_INVALID_ARG, "NULL argument");
+    if (n == 0) return LPSIM_OK;
+    float *dz = nullptr;
+    CU(cudaMalloc(&dz, n * 12));
+    cudaError_t e = cudaMemcpy(dz, z, n * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        gelu_eval<<<(unsigned)std::min<uint64_t>((n + 255) / 256, 4096), 256>>>(dz, n, dz + n, dz + 2 * n);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(gelu, dz + n, n * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(dgelu, dz + 2 * n, n * 4, cudaMemcpyDeviceToHost);
+    cudaFree(dz);
+    if (e != cudaSuccess) return fail(LPSIM_E_CUDA, std::string("gelu_eval: ") + cudaGetErrorString(e));
+    return LPSIM_OK;
 }
 
 void lpsim_mlp_destroy(lpsim_mlp *m) { delete m; }

@@ -94,6 +94,7 @@ int alloc_slots(lpsim_ctx *c, Slots &s, uint32_t cap) {
     TRY(dnew_mut(c, s.es, cap));
     TRY(dnew_mut(c, s.id, cap));
     TRY(dnew_mut(c, s.rlast, cap));
+    TRY(dnew_mut(c, s.tent, cap));
     TRY(dnew_mut(c, s.pcell, cap));
     TRY(dnew_mut(c, s.imark, cap));
     TRY(dnew_mut(c, s.lane, cap));

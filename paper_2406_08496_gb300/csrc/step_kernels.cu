@@ -164,6 +164,45 @@ __device__ __forceinline__ uint32_t warp_append(uint32_t *counter) {
     return base + (uint32_t)__popc((int)(mask & ((1u << lane) - 1u)));
 }
 
+// Per-block staging of the per-step lists: step_p1 appends an item to shared
+// memory (a shared-memory atomic) and the block moves its items to the
+// global list with one global atomic at its end, so no thread's chain waits on
+// a global round trip for a list position.  Items beyond the room of the
+// stage go to the global list directly.
+constexpr uint32_t kStageCross = 128, kStageIntend = 128, kStageDep = 64;
+
+static_assert(sizeof(CrossRec) == 64 && sizeof(IntendRec) == 32 && sizeof(DepRec) == 64, "record sizes");
+
+struct P1Sinks {
+    CrossRec *cr;
+    IntendRec *ir;
+    DepRec *dr;
+    uint32_t *n;  // [3]: staged crossing requests, intents, departure requests
+};
+
+template <class T>
+__device__ __forceinline__ void stage_put(T *buf, uint32_t room, uint32_t *n, T *glist, uint32_t *gcount,
+                                          const T &item) {
+    const uint32_t pos = atomicAdd(n, 1u);
+    if (pos < room)
+        buf[pos] = item;
+    else
+        glist[warp_append(gcount)] = item;
+}
+
+// after a block barrier: the staged items to glist (every thread takes part)
+template <class T>
+__device__ __forceinline__ void stage_flush(const T *buf, uint32_t room, const uint32_t *n, T *glist,
+                                            uint32_t *gcount, uint32_t *s_base) {
+    const uint32_t cnt = min(*n, room);
+    if (threadIdx.x == 0) *s_base = cnt ? atomicAdd(gcount, cnt) : 0u;
+    __syncthreads();
+    const uint32_t words = cnt * (uint32_t)(sizeof(T) / 16);
+    const uint4 *src = reinterpret_cast<const uint4 *>(buf);
+    uint4 *dst = reinterpret_cast<uint4 *>(glist + *s_base);
+    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+}
+
 // Keeps the loads above it above a following branch (so the first records of
 // a thread are in flight while the list length is still on its way).
 __device__ __forceinline__ void loads_issued() { asm volatile("" ::: "memory"); }
@@ -243,7 +282,7 @@ __device__ __forceinline__ StepView step_view(const Dev &d, uint32_t k, uint32_t
 
 // Origin edge j: reset the claim its departure won last step; ask for a
 // departure of the queue head once its step has come.
-__device__ __forceinline__ void p1_origin(const Dev &d, const StepView &w, uint32_t j) {
+__device__ __forceinline__ void p1_origin(const Dev &d, const StepView &w, const P1Sinks &sk, uint32_t j) {
     const uint32_t k = w.k, par = w.par;
     const uint8_t *Mc = w.Mc;
     uint32_t *claim = w.claim, *claim_old = w.claim_old;
@@ -283,15 +322,15 @@ __device__ __forceinline__ void p1_origin(const Dev &d, const StepView &w, uint3
             dr.nsph = (uint16_t)(rr.nphase | (rr.arank << 8));
             dr.lane = (uint8_t)l;
             dr.tlc = rr.tl;
-            d.dep_rec[par][warp_append(&d.counts[4 + par])] = dr;
+            stage_put(sk.dr, kStageDep, sk.n + 2, d.dep_rec[par], &d.counts[4 + par], dr);
         }
     }
 }
 
 // Slot s (every field loaded in one round trip, together with whatever the
 // caller loaded just before); false once s is past the slot count n.
-__device__ __forceinline__ bool p1_slot(const Dev &d, const StepView &w, uint32_t s, uint32_t n, uint32_t &live,
-                                        uint32_t &arrived) {
+__device__ __forceinline__ bool p1_slot(const Dev &d, const StepView &w, const P1Sinks &sk, uint32_t s, uint32_t n,
+                                        uint32_t &live, uint32_t &arrived) {
     const uint32_t k = w.k, par = w.par;
     const uint8_t *Mc = w.Mc;
     uint8_t *Mn = w.Mn, *Mo = w.Mo, *Iw = w.Iw, *Io = w.Io;
@@ -317,9 +356,7 @@ __device__ __forceinline__ bool p1_slot(const Dev &d, const StepView &w, uint32_
     const uint32_t tl = d.s.tlc[s];  // kNoLane on the last edge of the route
     const uint32_t ln = d.s.lane[s];
     const uint32_t id = d.s.id[s];
-    const uint32_t e = es.e;
     const uint32_t rpos = es.rpos, rlast = d.s.rlast[s];
-    const uint32_t tent = es.tent;
     loads_issued();
     if (s >= n) return false;
     if (flag == kDead) return true;
@@ -340,7 +377,7 @@ __device__ __forceinline__ bool p1_slot(const Dev &d, const StepView &w, uint32_
     live++;
     const uint32_t c = (uint32_t)x;
     d.s.pcell[s] = base + c;
-    if (sample) atomicAdd(&d.bin_occ[(size_t)(k / m.bin_steps) * d.n_edges + e], 1u);
+    if (sample) atomicAdd(&d.bin_occ[(size_t)(k / m.bin_steps) * d.n_edges + d.route[rpos]], 1u);
 
     // leader: nearest occupied cell ahead in the own lane of the own edge.
     // Cells beyond both d_front and the farthest reach of this step
@@ -352,15 +389,27 @@ __device__ __forceinline__ bool p1_slot(const Dev &d, const StepView &w, uint32_
     // in the same round trip as the scan: the next edge's records for a
     // vehicle that may reach the stop line, the lane-change key for one
     // that may draw (both only used under the exact conditions below)
-    const bool may_cross = en != kNone && x + vmax_step * m.dt + 1.0f >= L;
+    const bool may_end = x + vmax_step * m.dt + 1.0f >= L;  // may reach the stop line (or arrive)
+    const bool may_cross = en != kNone && may_end;
     const bool may_draw = tl != kNoLane && tl != ln && ((tl > ln) == (par == 1u)) && (L - x) < m.x0;
-    EdgeRec enr{};
+    float nv0 = 0.0f;
     RouteRec rr{};
-    uint32_t nen = kNone;
+    uint32_t nen = kNone, e = kNone, tent = 0, empty = 0, so = 0;
+    if (may_end) {
+        // the current edge and its entry step (for the statistics)
+        e = d.route[rpos];
+        tent = d.s.tent[s];
+    }
     if (may_cross) {
-        enr = d.edge[en];
+        nv0 = d.edge[en].v0;
         rr = d.rrec[rpos + 1];
         nen = rpos + 1 < rlast ? d.route[rpos + 2] : kNone;
+        so = d.slot_off[en];
+        // entry cells of the next edge, from the geometry kept in the slot
+        const uint32_t stride = row_stride(es.nlen);
+#pragma unroll
+        for (uint32_t l = 0; l < 4; l++)
+            if (l < es.nlanes && Mc[es.nmoff + l * stride] == kEmpty) empty |= 1u << l;
     }
     // lane-change draw at step k: SplitMix64 of hkey ^ k * C2, where
     // hkey[id] = seed ^ local_id * C1 was formed at load time (local_id =
@@ -387,7 +436,7 @@ __device__ __forceinline__ bool p1_slot(const Dev &d, const StepView &w, uint32_
     }
     if (xn >= L) {
         if (en == kNone) {
-            // last edge of the route: arrive
+            // last edge of the route: arrive (may_end holds: x' <= x + vmax_step * dt)
             stat_exit(d, e, k, tent);
             d.arr[id] = k + 1;
             d.status[id] = kArrived;
@@ -397,14 +446,10 @@ __device__ __forceinline__ bool p1_slot(const Dev &d, const StepView &w, uint32_
         }
         bool cross = false;
         if (G == 0 || (k / G) % (ph & 0xFFu) == (ph >> 8)) {
-            if (!may_cross) {  // cannot happen: x' <= x + vmax_step * dt < L - 1 otherwise
-                enr = d.edge[en];
-                rr = d.rrec[rpos + 1];
-                nen = rpos + 1 < rlast ? d.route[rpos + 2] : kNone;
-            }
-            const uint32_t l = pick_entry_lane(entry_cells(Mc, enr), enr.lanes, rr.tl);
+            // may_cross holds here: x' >= L needs x + vmax_step * dt >= L
+            const uint32_t l = pick_entry_lane(empty, es.nlanes, rr.tl);
             if (l != kNone) {
-                const uint32_t slot = d.slot_off[en] + l;
+                const uint32_t slot = so + l;
                 atomicMin(&claim[slot], id);
                 CrossRec cr;
                 cr.s = s;
@@ -415,18 +460,18 @@ __device__ __forceinline__ bool p1_slot(const Dev &d, const StepView &w, uint32_
                 cr.rpos = rpos;
                 cr.tent = tent;
                 cr.base = base;
-                cr.nbase = enr.moff + l * row_stride(enr.len);
+                cr.nbase = es.nmoff + l * row_stride(es.nlen);
                 cr.nen = nen;
                 cr.nsg = rr.green;
                 cr.x = x;
                 cr.vn = vn;
-                cr.nv0 = enr.v0;
+                cr.nv0 = nv0;
                 cr.len = (uint16_t)len;
-                cr.nlen = enr.len;
+                cr.nlen = es.nlen;
                 cr.nsph = (uint16_t)(rr.nphase | (rr.arank << 8));
                 cr.lane = (uint8_t)l;
                 cr.tln = rr.tl;
-                d.cross_list[par][warp_append(&d.counts[par])] = cr;
+                stage_put(sk.cr, kStageCross, sk.n, d.cross_list[par], &d.counts[par], cr);
                 cross = true;
             }
         }
@@ -460,10 +505,19 @@ __device__ __forceinline__ bool p1_slot(const Dev &d, const StepView &w, uint32_
             ir.len = (uint16_t)len;
             ir.lane = (uint8_t)ln;
             ir.up = tl > ln ? 1 : 0;
-            d.intend_list[par][warp_append(&d.counts[2 + par])] = ir;
+            stage_put(sk.ir, kStageIntend, sk.n + 1, d.intend_list[par], &d.counts[2 + par], ir);
         }
     }
     return true;
+}
+
+// the block's staged records to the step's lists (after a block barrier)
+__device__ __forceinline__ void p1_flush(const Dev &d, uint32_t par, const P1Sinks &sk, uint32_t *s_base) {
+    stage_flush(sk.cr, kStageCross, sk.n, d.cross_list[par], &d.counts[par], s_base);
+    __syncthreads();
+    stage_flush(sk.ir, kStageIntend, sk.n + 1, d.intend_list[par], &d.counts[2 + par], s_base);
+    __syncthreads();
+    stage_flush(sk.dr, kStageDep, sk.n + 2, d.dep_rec[par], &d.counts[4 + par], s_base);
 }
 
 template <int BLOCK>
@@ -474,17 +528,25 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) step_p1(Dev d, uint32_t k
     const StepView w = step_view(d, k, kph);
     const uint32_t norg = d.n_org;
     const uint32_t lim = norg + d.cap;  // items: origin edges first, then slots
+    __shared__ __align__(16) CrossRec s_cr[kStageCross];
+    __shared__ __align__(16) IntendRec s_ir[kStageIntend];
+    __shared__ __align__(16) DepRec s_dr[kStageDep];
+    __shared__ uint32_t s_n[3], s_base;
+    if (threadIdx.x < 3) s_n[threadIdx.x] = 0;
+    __syncthreads();
+    const P1Sinks sk{s_cr, s_ir, s_dr, s_n};
     uint32_t live = 0;
     uint32_t arrived = 0;
     for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < lim; i += gridDim.x * BLOCK) {
         if (i < norg) {
-            p1_origin(d, w, i);
+            p1_origin(d, w, sk, i);
             continue;
         }
-        if (!p1_slot(d, w, i - norg, n, live, arrived)) break;
+        if (!p1_slot(d, w, sk, i - norg, n, live, arrived)) break;
     }
     block_add<BLOCK>(&d.ctr[0], live);
     if (arrived) atomicAdd(&d.ctr[1], (unsigned long long)arrived);
+    p1_flush(d, w.par, sk, &s_base);
 }
 
 // ----------------------------------------------------------------------- P2
@@ -496,6 +558,8 @@ __device__ __forceinline__ void p2_cross(const Dev &d, const StepView &w, const 
     const uint32_t k = w.k;
     uint8_t *Mn = w.Mn;
     float *xw = w.xw, *vw = w.vw;
+    // the edge after the next one (for the record of a winner), loaded with the claim
+    const EdgeRec nn = cr.nen != kNone ? d.edge[cr.nen] : EdgeRec{0, 0, 0, 0, 0.0f, 0};
     if (w.claim[cr.cslot] == cr.id) {
         const uint32_t s = cr.s;
         if (ev < d.ev_cap) {
@@ -506,15 +570,18 @@ __device__ __forceinline__ void p2_cross(const Dev &d, const StepView &w, const 
         }
         EdgeState ne;
         ne.base = cr.nbase;
-        ne.e = cr.en;
         ne.rpos = cr.rpos + 1;
-        ne.tent = k + 1;
         ne.en = cr.nen;
         ne.sg = cr.nsg;
         ne.v0 = cr.nv0;
+        ne.nmoff = nn.moff;
         ne.len = cr.nlen;
         ne.sph = cr.nsph;
+        ne.nlen = nn.len;
+        ne.nlanes = nn.lanes;
+        ne.pad = 0;
         store_es(d.s.es + s, ne);
+        d.s.tent[s] = k + 1;
         d.s.lane[s] = cr.lane;
         d.s.tlc[s] = cr.tln;
         d.s.cprev[s] = cr.cslot;
@@ -541,6 +608,7 @@ __device__ __forceinline__ void p2_dep(const Dev &d, const StepView &w, const De
     const uint32_t qh = dr.qoff + dr.qhead;
     const QRec next = qh + 1 < dr.qend ? d.qrec[qh + 1] : QRec{kNone, kNone, 0, 0};
     const uint32_t won = w.claim[dr.slot];
+    const EdgeRec nn = dr.nen != kNone ? d.edge[dr.nen] : EdgeRec{0, 0, 0, 0, 0.0f, 0};
     if (s >= d.cap) {
         atomicOr(d.err, kErrSlotOverflow);
         return;
@@ -554,15 +622,18 @@ __device__ __forceinline__ void p2_dep(const Dev &d, const StepView &w, const De
     }
     EdgeState ne;
     ne.base = dr.base;
-    ne.e = dr.e0;
     ne.rpos = dr.r0;
-    ne.tent = k + 1;
     ne.en = dr.nen;
     ne.sg = dr.nsg;
     ne.v0 = dr.v0;
+    ne.nmoff = nn.moff;
     ne.len = dr.len;
     ne.sph = dr.nsph;
+    ne.nlen = nn.len;
+    ne.nlanes = nn.lanes;
+    ne.pad = 0;
     store_es(d.s.es + s, ne);
+    d.s.tent[s] = k + 1;
     d.s.id[s] = dr.h;
     d.s.rlast[s] = dr.r1 - 1;
     d.s.lane[s] = dr.lane;
@@ -747,16 +818,24 @@ __global__ void __launch_bounds__(kSmallBlock, 1)
     step_small(Dev d, uint32_t k0, uint32_t nsteps, const uint32_t *olist, const uint32_t *no_ptr) {
     const uint32_t tid = threadIdx.x;
     const uint32_t no = *no_ptr;
+    __shared__ __align__(16) CrossRec s_cr[kStageCross];
+    __shared__ __align__(16) IntendRec s_ir[kStageIntend];
+    __shared__ __align__(16) DepRec s_dr[kStageDep];
+    __shared__ uint32_t s_n[3], s_base;
+    const P1Sinks sk{s_cr, s_ir, s_dr, s_n};
     for (uint32_t t = 0; t < nsteps; t++) {
         const uint32_t k = k0 + t, par = k & 1u;
         const StepView w = step_view(d, k, k);
         // P1
+        if (tid < 3) s_n[tid] = 0;
+        __syncthreads();
         const uint32_t n = *d.n_slots;
         uint32_t live = 0, arrived = 0;
-        for (uint32_t i = tid; i < no; i += kSmallBlock) p1_origin(d, w, olist[i]);
-        for (uint32_t s = tid; s < n; s += kSmallBlock) p1_slot(d, w, s, n, live, arrived);
+        for (uint32_t i = tid; i < no; i += kSmallBlock) p1_origin(d, w, sk, olist[i]);
+        for (uint32_t s = tid; s < n; s += kSmallBlock) p1_slot(d, w, sk, s, n, live, arrived);
         block_add<kSmallBlock>(&d.ctr[0], live);
         if (arrived) atomicAdd(&d.ctr[1], (unsigned long long)arrived);
+        p1_flush(d, par, sk, &s_base);
         __syncthreads();
         // P2
         uint32_t events = 0, departed = 0;
@@ -887,7 +966,7 @@ __global__ void state_scatter(Dev d, uint32_t k, float *x, float *v, uint32_t *e
         uint32_t id = d.s.id[s];
         x[id] = d.s.x[k & 1][s];
         v[id] = d.s.v[k & 1][s];
-        edge[id] = d.s.es[s].e;
+        edge[id] = d.route[d.s.es[s].rpos];
         lane[id] = d.s.lane[s];
         ridx[id] = d.s.es[s].rpos - d.roff[id];
     }

@@ -122,3 +122,23 @@ def test_training_reduces_loss():
     tv = (np.sin(2 * Xv[:, 0]) + Xv[:, 1] * Xv[:, 2] + 0.5 * np.abs(Xv[:, 3]) - Xv[:, 4] ** 2)
     mse = float(np.mean((s.forward(Xv) - tv) ** 2))
     assert mse < 0.05 * float(np.var(tv)), mse
+
+
+def test_gelu_within_its_error_bound():
+    """The epilogues' GELU and GELU' (normal CDF by Abramowitz and Stegun
+    26.2.17, |error| < 7.5e-8) against the float64 closed forms, over the
+    range the activations take and beyond: the bound plus a few float32
+    roundings of each term."""
+    import oracle.mlp as M
+    from paper_2406_08496_gb300 import gelu_eval
+    z = np.concatenate([np.linspace(-12.0, 12.0, 200001), np.random.default_rng(4).standard_normal(100000) * 3.0])
+    z = z.astype(np.float32)
+    g, dg = gelu_eval(z)
+    z64 = z.astype(np.float64)
+    ref_g, ref_dg = M.gelu(z64), M.gelu_grad(z64)
+    # 7.5e-8 of the method plus float32 evaluation (fast reciprocal and
+    # exponential, four fused multiply-adds, a few products): 5e-7 in Phi
+    tol_g = 5e-7 * np.abs(z64) + 2e-7 * np.abs(ref_g) + 1e-30
+    tol_dg = 6e-7 + 2e-7 * np.abs(z64)
+    assert np.all(np.abs(g - ref_g) <= tol_g), float(np.max(np.abs(g - ref_g) / tol_g))
+    assert np.all(np.abs(dg - ref_dg) <= tol_dg), float(np.max(np.abs(dg - ref_dg) / tol_dg))

@@ -334,9 +334,13 @@ def grid_day(seed: int = 1, n_trips: int = 2000) -> tuple[dict, dict]:
 
 
 def regional_day(seed: int = 2, n_trips: int = 2_820_000, scale: str = "paper") -> tuple[dict, dict]:
-    """Regional planar network and a 24 h gravity demand with AM/PM peaks."""
+    """Regional planar network and a 24 h gravity demand with AM/PM peaks.
+    The zone grid grows with the network's area (50 x 30 zones at the
+    paper's scale, 107 x 64 on the large network), so each zone -- and each
+    access node -- keeps about the same size and load."""
     net = regional_network(seed, scale)
-    dem = route(net, gravity_demand(net, n_trips, seed + 1000))
+    zx, zy = (50, 30) if scale == "paper" else (107, 64)
+    dem = route(net, gravity_demand(net, n_trips, seed + 1000, zones_x=zx, zones_y=zy))
     return net, dem
 
 
