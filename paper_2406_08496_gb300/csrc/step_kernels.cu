@@ -505,7 +505,14 @@ __device__ __forceinline__ bool p1_slot(const Dev &d, const StepView &w, const P
             ir.len = (uint16_t)len;
             ir.lane = (uint8_t)ln;
             ir.up = tl > ln ? 1 : 0;
-            stage_put(sk.ir, kStageIntend, sk.n + 1, d.intend_list[par], &d.counts[2 + par], ir);
+            // A stop-line hold (a crossing request that loses in step_p2) can only take cell
+            // len - 1 of its lane; an intent aiming at any other cell is decided in step_p2
+            // alongside the crossings, one aiming at len - 1 waits for step_p3.  Those few
+            // go to the top of the same list, growing downwards.
+            if (cn + 1 < len)
+                stage_put(sk.ir, kStageIntend, sk.n + 1, d.intend_list[par], &d.counts[2 + par], ir);
+            else
+                d.intend_list[par][d.cap - 1 - warp_append(&d.counts[6 + par])] = ir;
         }
     }
     return true;
@@ -655,45 +662,6 @@ __device__ __forceinline__ void p2_dep(const Dev &d, const StepView &w, const De
     departed++;
 }
 
-// The last gdep blocks (enough for one request per origin edge) take the
-// departure requests, the others the crossers, so that each thread's first
-// record is loaded together with its list's length.
-template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK) step_p2(Dev d, uint32_t koff, uint32_t kph, uint32_t gdep) {
-    pdl_prologue();
-    const uint32_t par = kph & 1u;
-    const uint32_t k = *d.kbase + koff;
-    const StepView w = step_view(d, k, kph);
-    const bool crossers = blockIdx.x < gridDim.x - gdep;
-    uint32_t events = 0, departed = 0;
-    if (crossers) {
-        const uint32_t ncross = d.counts[par];
-        const uint32_t ev0 = *d.ev_n;  // this step's crossings follow the chunk's earlier ones in the log
-        const uint32_t nthr = (gridDim.x - gdep) * BLOCK;
-        const CrossRec *list = d.cross_list[par];
-        for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < d.cap; i += nthr) {
-            const CrossRec cr = list[i];
-            loads_issued();
-            if (i >= ncross) break;
-            p2_cross(d, w, cr, ev0 + i, events);
-        }
-    } else {
-        const uint32_t ndep = d.counts[4 + par];
-        const uint32_t n0 = *d.n_slots;
-        const uint32_t b0 = gridDim.x - gdep;
-        const uint32_t nthr = gdep * BLOCK;
-        const DepRec *list = d.dep_rec[par];
-        for (uint32_t q = (blockIdx.x - b0) * BLOCK + threadIdx.x; q < d.n_org; q += nthr) {
-            const DepRec dr = list[q];
-            loads_issued();
-            if (q >= ndep) break;
-            p2_dep(d, w, dr, q, n0, events, departed);
-        }
-    }
-    if (events) atomicAdd(&d.ctr[3], (unsigned long long)events);
-    if (departed) atomicAdd(&d.ctr[4], (unsigned long long)departed);
-}
-
 // ----------------------------------------------------------------------- P3
 
 // occupancy masks of the 5 chunks covering [c0 - 64, c0 + 63] around an
@@ -776,30 +744,78 @@ __device__ __forceinline__ void p3_intend(const Dev &d, const StepView &w, const
     }
 }
 
+// Blocks [0, gc) take the crossing requests, [gc, gc + gi) the lane-change
+// intents aiming at a cell no stop-line hold can take, the last gdep (enough
+// for one request per origin edge) the departure requests; each thread's
+// first record is loaded together with its list's length.
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) step_p2(Dev d, uint32_t koff, uint32_t kph, uint32_t gc, uint32_t gi) {
+    pdl_prologue();
+    const uint32_t par = kph & 1u;
+    const uint32_t k = *d.kbase + koff;
+    const StepView w = step_view(d, k, kph);
+    uint32_t events = 0, departed = 0, changes = 0;
+    if (blockIdx.x < gc) {
+        const uint32_t ncross = d.counts[par];
+        const uint32_t ev0 = *d.ev_n;  // this step's crossings follow the chunk's earlier ones in the log
+        const CrossRec *list = d.cross_list[par];
+        for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < d.cap; i += gc * BLOCK) {
+            const CrossRec cr = list[i];
+            loads_issued();
+            if (i >= ncross) break;
+            p2_cross(d, w, cr, ev0 + i, events);
+        }
+    } else if (blockIdx.x < gc + gi) {
+        const uint32_t nint = d.counts[2 + par];
+        const IntendRec *list = d.intend_list[par];
+        for (uint32_t i = (blockIdx.x - gc) * BLOCK + threadIdx.x; i < d.cap; i += gi * BLOCK) {
+            const IntendRec ir = list[i];
+            loads_issued();
+            if (i >= nint) break;
+            p3_intend(d, w, ir, changes);
+        }
+    } else {
+        const uint32_t ndep = d.counts[4 + par];
+        const uint32_t n0 = *d.n_slots;
+        const uint32_t b0 = gc + gi;
+        const uint32_t nthr = (gridDim.x - b0) * BLOCK;
+        const DepRec *list = d.dep_rec[par];
+        for (uint32_t q = (blockIdx.x - b0) * BLOCK + threadIdx.x; q < d.n_org; q += nthr) {
+            const DepRec dr = list[q];
+            loads_issued();
+            if (q >= ndep) break;
+            p2_dep(d, w, dr, q, n0, events, departed);
+        }
+    }
+    if (events) atomicAdd(&d.ctr[3], (unsigned long long)events);
+    if (departed) atomicAdd(&d.ctr[4], (unsigned long long)departed);
+    if (changes) atomicAdd(&d.ctr[2], (unsigned long long)changes);
+}
+
 // End of step k (one thread): the next step's lists start empty; the
 // departures of this step have taken their slots.
 __device__ __forceinline__ void step_tail(const Dev &d, uint32_t par) {
     d.counts[par ^ 1u] = 0;
     d.counts[2 + (par ^ 1u)] = 0;
     d.counts[4 + (par ^ 1u)] = 0;
+    d.counts[6 + (par ^ 1u)] = 0;
     *d.n_slots += d.counts[4 + par];
     *d.ev_n += d.counts[par];
 }
 
+// The lane-change intents aiming at a stop-line cell (after step_p2 placed
+// the holds), then the end of the step.
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) step_p3(Dev d, uint32_t koff, uint32_t kph) {
     pdl_prologue();
     const uint32_t par = kph & 1u;
     const uint32_t k = *d.kbase + koff;
     const StepView w = step_view(d, k, kph);
-    const uint32_t nint = d.counts[2 + par];
+    const uint32_t nint = d.counts[6 + par];
+    const IntendRec *top = d.intend_list[par] + (d.cap - 1);
     uint32_t changes = 0;
-    for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < d.cap; i += gridDim.x * BLOCK) {
-        const IntendRec ir = d.intend_list[par][i];
-        loads_issued();
-        if (i >= nint) break;
-        p3_intend(d, w, ir, changes);
-    }
+    for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < nint; i += gridDim.x * BLOCK)
+        p3_intend(d, w, *(top - i), changes);
     if (changes) atomicAdd(&d.ctr[2], (unsigned long long)changes);
     if (blockIdx.x == 0 && threadIdx.x == 0) step_tail(d, par);
 }
@@ -838,17 +854,17 @@ __global__ void __launch_bounds__(kSmallBlock, 1)
         p1_flush(d, par, sk, &s_base);
         __syncthreads();
         // P2
-        uint32_t events = 0, departed = 0;
+        uint32_t events = 0, departed = 0, changes = 0;
         const uint32_t ncross = d.counts[par], ndep = d.counts[4 + par], ev0 = *d.ev_n;
+        const uint32_t nint = d.counts[2 + par], nlate = d.counts[6 + par];
         for (uint32_t i = tid; i < ncross; i += kSmallBlock) p2_cross(d, w, d.cross_list[par][i], ev0 + i, events);
+        for (uint32_t i = tid; i < nint; i += kSmallBlock) p3_intend(d, w, d.intend_list[par][i], changes);
         for (uint32_t q = tid; q < ndep; q += kSmallBlock) p2_dep(d, w, d.dep_rec[par][q], q, n, events, departed);
         if (events) atomicAdd(&d.ctr[3], (unsigned long long)events);
         if (departed) atomicAdd(&d.ctr[4], (unsigned long long)departed);
         __syncthreads();
         // P3
-        uint32_t changes = 0;
-        const uint32_t nint = d.counts[2 + par];
-        for (uint32_t i = tid; i < nint; i += kSmallBlock) p3_intend(d, w, d.intend_list[par][i], changes);
+        for (uint32_t i = tid; i < nlate; i += kSmallBlock) p3_intend(d, w, d.intend_list[par][d.cap - 1 - i], changes);
         if (changes) atomicAdd(&d.ctr[2], (unsigned long long)changes);
         __syncthreads();
         if (tid == 0) step_tail(d, par);
@@ -925,11 +941,12 @@ void launch_phase(const Dev &d, int phase, uint32_t koff, uint32_t kph, int grid
     // for the departure requests (at most one per origin edge and step)
     const int g = phase == 1 ? grid : (grid + 3) / 4;
     const uint32_t gdep = std::max(1u, (d.n_org + (uint32_t)block - 1) / (uint32_t)block);
+    const int g3 = (g + 3) / 4;  // step_p3: the few intents at stop-line cells
 #define LPSIM_PHASE(B)                                                                  \
     do {                                                                                \
         if (phase == 1) launch_pdl(step_p1<B>, g, B, st, d, koff, kph);                 \
-        else if (phase == 2) launch_pdl(step_p2<B>, g + (int)gdep, B, st, d, koff, kph, gdep); \
-        else launch_pdl(step_p3<B>, g, B, st, d, koff, kph);                            \
+        else if (phase == 2) launch_pdl(step_p2<B>, 2 * g + (int)gdep, B, st, d, koff, kph, (uint32_t)g, (uint32_t)g); \
+        else launch_pdl(step_p3<B>, g3, B, st, d, koff, kph);                           \
     } while (0)
     switch (block) {
     case 128: LPSIM_PHASE(128); break;

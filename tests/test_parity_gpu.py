@@ -158,9 +158,9 @@ def test_light_load_chunks_match_oracle(grid_day, flags):
     o.load_demand(sub)
     g = Simulation(net, dict(params, flags=flags))
     g.load_demand(sub)
-    for _ in range(8):
-        o.step(384)
-        g.step(384)
+    for _ in range(4):
+        o.step(768)  # one graph chunk at the default chunk length
+        g.step(768)
         assert_state_equal(o.state(), g.state(), f"step {o.counters()['k']}")
     ro = o.run(20000)
     rg = g.run(20000)
@@ -204,13 +204,13 @@ def test_kernel_timing_direct_and_graph_steps(grid_day):
     g.load_demand(dem)
     g.set_kernel_timing(True)
     g.step(5)      # direct steps (not at a chunk boundary afterwards)
-    g.step(379)    # direct steps up to the chunk boundary
-    g.step(768)    # two graph chunks
+    g.step(763)    # direct steps up to the chunk boundary (default chunk: 768 steps)
+    g.step(1536)   # two graph chunks
     kt = g.kernel_times()
     g.set_kernel_timing(False)
-    assert kt["step_p1"]["launches"] == 1152 and kt["step_p1"]["ms"] > 0
+    assert kt["step_p1"]["launches"] == 2304 and kt["step_p1"]["ms"] > 0
     assert kt["step_p2"]["ms"] > 0 and kt["step_p3"]["ms"] > 0
     ref = Simulation(net, {})
     ref.load_demand(dem)
-    ref.step(1152)
+    ref.step(2304)
     assert_state_equal(ref.state(), g.state(), "timing on vs off")
