@@ -190,18 +190,6 @@ __device__ __forceinline__ void stage_put(T *buf, uint32_t room, uint32_t *n, T 
         glist[warp_append(gcount)] = item;
 }
 
-// after a block barrier: the staged items to glist (every thread takes part)
-template <class T>
-__device__ __forceinline__ void stage_flush(const T *buf, uint32_t room, const uint32_t *n, T *glist,
-                                            uint32_t *gcount, uint32_t *s_base) {
-    const uint32_t cnt = min(*n, room);
-    if (threadIdx.x == 0) *s_base = cnt ? atomicAdd(gcount, cnt) : 0u;
-    __syncthreads();
-    const uint32_t words = cnt * (uint32_t)(sizeof(T) / 16);
-    const uint4 *src = reinterpret_cast<const uint4 *>(buf);
-    uint4 *dst = reinterpret_cast<uint4 *>(glist + *s_base);
-    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
-}
 
 // Keeps the loads above it above a following branch (so the first records of
 // a thread are in flight while the list length is still on its way).
@@ -518,13 +506,28 @@ __device__ __forceinline__ bool p1_slot(const Dev &d, const StepView &w, const P
     return true;
 }
 
-// the block's staged records to the step's lists (after a block barrier)
+// 16-byte words of the staged records into a global list (every thread)
+template <class T>
+__device__ __forceinline__ void stage_copy(const T *buf, uint32_t cnt, T *glist, uint32_t base) {
+    const uint32_t words = cnt * (uint32_t)(sizeof(T) / 16);
+    const uint4 *src = reinterpret_cast<const uint4 *>(buf);
+    uint4 *dst = reinterpret_cast<uint4 *>(glist + base);
+    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+}
+
+// The block's staged records to the step's lists (after a block barrier):
+// the three list positions are reserved by three threads at once (one
+// global round trip), then every thread copies.
 __device__ __forceinline__ void p1_flush(const Dev &d, uint32_t par, const P1Sinks &sk, uint32_t *s_base) {
-    stage_flush(sk.cr, kStageCross, sk.n, d.cross_list[par], &d.counts[par], s_base);
+    if (threadIdx.x < 3) {
+        const uint32_t room = threadIdx.x == 0 ? kStageCross : threadIdx.x == 1 ? kStageIntend : kStageDep;
+        const uint32_t cnt = min(sk.n[threadIdx.x], room);
+        s_base[threadIdx.x] = cnt ? atomicAdd(&d.counts[2 * threadIdx.x + par], cnt) : 0u;
+    }
     __syncthreads();
-    stage_flush(sk.ir, kStageIntend, sk.n + 1, d.intend_list[par], &d.counts[2 + par], s_base);
-    __syncthreads();
-    stage_flush(sk.dr, kStageDep, sk.n + 2, d.dep_rec[par], &d.counts[4 + par], s_base);
+    stage_copy(sk.cr, min(sk.n[0], kStageCross), d.cross_list[par], s_base[0]);
+    stage_copy(sk.ir, min(sk.n[1], kStageIntend), d.intend_list[par], s_base[1]);
+    stage_copy(sk.dr, min(sk.n[2], kStageDep), d.dep_rec[par], s_base[2]);
 }
 
 template <int BLOCK>
@@ -538,7 +541,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) step_p1(Dev d, uint32_t k
     __shared__ __align__(16) CrossRec s_cr[kStageCross];
     __shared__ __align__(16) IntendRec s_ir[kStageIntend];
     __shared__ __align__(16) DepRec s_dr[kStageDep];
-    __shared__ uint32_t s_n[3], s_base;
+    __shared__ uint32_t s_n[3], s_base[3];
     if (threadIdx.x < 3) s_n[threadIdx.x] = 0;
     __syncthreads();
     const P1Sinks sk{s_cr, s_ir, s_dr, s_n};
@@ -553,7 +556,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) step_p1(Dev d, uint32_t k
     }
     block_add<BLOCK>(&d.ctr[0], live);
     if (arrived) atomicAdd(&d.ctr[1], (unsigned long long)arrived);
-    p1_flush(d, w.par, sk, &s_base);
+    p1_flush(d, w.par, sk, s_base);
 }
 
 // ----------------------------------------------------------------------- P2
@@ -811,13 +814,34 @@ __global__ void __launch_bounds__(BLOCK) step_p3(Dev d, uint32_t koff, uint32_t 
     const uint32_t par = kph & 1u;
     const uint32_t k = *d.kbase + koff;
     const StepView w = step_view(d, k, kph);
+    const bool closer = blockIdx.x == 0 && threadIdx.x == 0;
+    // the closing thread reads what the end of the step needs right away
+    // (none of it changes in this kernel), so the list reset waits on no load
+    uint32_t ndep = 0, ncross = 0, ns = 0, ne = 0;
+    if (closer) {
+        ndep = d.counts[4 + par];
+        ncross = d.counts[par];
+        ns = *d.n_slots;
+        ne = *d.ev_n;
+    }
     const uint32_t nint = d.counts[6 + par];
     const IntendRec *top = d.intend_list[par] + (d.cap - 1);
     uint32_t changes = 0;
-    for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < nint; i += gridDim.x * BLOCK)
-        p3_intend(d, w, *(top - i), changes);
+    for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < d.cap; i += gridDim.x * BLOCK) {
+        const IntendRec ir = *(top - i);
+        loads_issued();
+        if (i >= nint) break;
+        p3_intend(d, w, ir, changes);
+    }
     if (changes) atomicAdd(&d.ctr[2], (unsigned long long)changes);
-    if (blockIdx.x == 0 && threadIdx.x == 0) step_tail(d, par);
+    if (closer) {
+        d.counts[par ^ 1u] = 0;
+        d.counts[2 + (par ^ 1u)] = 0;
+        d.counts[4 + (par ^ 1u)] = 0;
+        d.counts[6 + (par ^ 1u)] = 0;
+        *d.n_slots = ns + ndep;
+        *d.ev_n = ne + ncross;
+    }
 }
 
 // ------------------------------------------------------------ light load
@@ -837,7 +861,7 @@ __global__ void __launch_bounds__(kSmallBlock, 1)
     __shared__ __align__(16) CrossRec s_cr[kStageCross];
     __shared__ __align__(16) IntendRec s_ir[kStageIntend];
     __shared__ __align__(16) DepRec s_dr[kStageDep];
-    __shared__ uint32_t s_n[3], s_base;
+    __shared__ uint32_t s_n[3], s_base[3];
     const P1Sinks sk{s_cr, s_ir, s_dr, s_n};
     for (uint32_t t = 0; t < nsteps; t++) {
         const uint32_t k = k0 + t, par = k & 1u;
@@ -851,7 +875,7 @@ __global__ void __launch_bounds__(kSmallBlock, 1)
         for (uint32_t s = tid; s < n; s += kSmallBlock) p1_slot(d, w, sk, s, n, live, arrived);
         block_add<kSmallBlock>(&d.ctr[0], live);
         if (arrived) atomicAdd(&d.ctr[1], (unsigned long long)arrived);
-        p1_flush(d, par, sk, &s_base);
+        p1_flush(d, par, sk, s_base);
         __syncthreads();
         // P2
         uint32_t events = 0, departed = 0, changes = 0;
