@@ -439,6 +439,31 @@ def main():
                     "kernel_share": {k: v["ms"] / tot_ms for k, v in kt.items()},
                     "traffic_source": ("profiles/step_p1_regional_peak.json: " + tr["captured_launch"]) if tr else
                     "stale or missing ncu summary"}
+        # the same at the morning peak (the hour the roofline target is about):
+        # one graph chunk of kernel-timed steps from 08:00
+        peak_window = None
+        if args.workload == "regional":
+            sim.reset()
+            sim.step(8 * 7200)
+            c0 = sim.counters()
+            sim.set_kernel_timing(True)
+            sim.step(768)
+            kw = sim.kernel_times()
+            sim.set_kernel_timing(False)
+            vs_w = sim.counters()["veh_steps"] - c0["veh_steps"]
+            pw = kw["step_p1"]
+            if pw["ms"] > 0 and pw["launches"]:
+                ach = BYTES_PER_VEH_STEP_P1 * vs_w / (pw["ms"] / 1e3) / 1e9
+                per_launch_s = pw["ms"] / 1e3 / pw["launches"]
+                dram = tr["dram_bytes_per_launch"] if tr else None
+                peak_window = {"window": "steps 57,600-58,367 (08:00-08:06:24)", "achieved": ach,
+                               "frac": ach / peak, "unit": "GB/s",
+                               "avg_launch_us": per_launch_s * 1e6, "avg_veh_per_launch": vs_w / pw["launches"],
+                               "dram_gbs": dram / per_launch_s / 1e9 if dram else None,
+                               "dram_frac": dram / per_launch_s / 1e9 / peak if dram else None,
+                               "dram_source": "ncu DRAM bytes of a step_p1 launch at 08:00 "
+                                              "(profiles/step_p1_regional_peak.json) / live launch time"}
+            roofline["peak_window"] = peak_window
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             sub = sample_workload(net, dem)

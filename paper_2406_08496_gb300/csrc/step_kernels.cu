@@ -762,7 +762,8 @@ __global__ void __launch_bounds__(BLOCK) step_p2(Dev d, uint32_t koff, uint32_t 
         const uint32_t ncross = d.counts[par];
         const uint32_t ev0 = *d.ev_n;  // this step's crossings follow the chunk's earlier ones in the log
         const CrossRec *list = d.cross_list[par];
-        for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < d.cap; i += gc * BLOCK) {
+        // item i goes to block i % gc: a short list spreads over every block (and SM)
+        for (uint32_t i = threadIdx.x * gc + blockIdx.x; i < d.cap; i += gc * BLOCK) {
             const CrossRec cr = list[i];
             loads_issued();
             if (i >= ncross) break;
@@ -771,7 +772,7 @@ __global__ void __launch_bounds__(BLOCK) step_p2(Dev d, uint32_t koff, uint32_t 
     } else if (blockIdx.x < gc + gi) {
         const uint32_t nint = d.counts[2 + par];
         const IntendRec *list = d.intend_list[par];
-        for (uint32_t i = (blockIdx.x - gc) * BLOCK + threadIdx.x; i < d.cap; i += gi * BLOCK) {
+        for (uint32_t i = threadIdx.x * gi + (blockIdx.x - gc); i < d.cap; i += gi * BLOCK) {
             const IntendRec ir = list[i];
             loads_issued();
             if (i >= nint) break;
