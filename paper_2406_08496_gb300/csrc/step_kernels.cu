@@ -966,7 +966,7 @@ void launch_phase(const Dev &d, int phase, uint32_t koff, uint32_t kph, int grid
     // for the departure requests (at most one per origin edge and step)
     const int g = phase == 1 ? grid : (grid + 3) / 4;
     const uint32_t gdep = std::max(1u, (d.n_org + (uint32_t)block - 1) / (uint32_t)block);
-    const int g3 = (g + 3) / 4;  // step_p3: the few intents at stop-line cells
+    const int g3 = 2;  // step_p3: the few intents at stop-line cells (about a hundred per step at most)
 #define LPSIM_PHASE(B)                                                                  \
     do {                                                                                \
         if (phase == 1) launch_pdl(step_p1<B>, g, B, st, d, koff, kph);                 \
