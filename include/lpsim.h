@@ -93,6 +93,9 @@ typedef struct lpsim_params {
                              costs a load per write); LPSIM_F_NO_LIGHT: never run a chunk in the
                              single-block light-load kernel (results are the same either way);
                              other bits must be 0 */
+    uint32_t light_trips; /* a chunk runs in the single-block light-load kernel when at most this many
+                             trips can be on the network or waiting during it (0 = 1536); a speed
+                             setting only, results are the same for every value */
 } lpsim_params;
 
 /* Road network.  Edge e runs edge_src[e] -> edge_dst[e], is edge_len_m[e]

@@ -21,7 +21,8 @@ constexpr uint8_t kActive = 1;
 constexpr uint8_t kArrived = 2;
 
 // light-load mode: one block of kSmallBlock threads runs a whole chunk when at
-// most kSmallMax trips can be on the network or waiting during it
+// most kSmallMax trips (the default of lpsim_params.light_trips) can be on the
+// network or waiting during it
 constexpr int kSmallBlock = 1024;
 constexpr uint32_t kSmallMax = 1536;
 

@@ -261,7 +261,7 @@ int chunk(lpsim_ctx *c) {
     return LPSIM_OK;
 }
 
-// Light load: at most kSmallMax trips can be on the network or waiting in
+// Light load: at most light_trips trips can be on the network or waiting in
 // the chunk starting at step k (trips due before its end minus those arrived;
 // h_ctr is current).  Kernel timing measures the grid-wide kernels, so it
 // keeps them.
@@ -269,7 +269,7 @@ bool light_chunk_ok(const lpsim_ctx *c) {
     if ((c->p.flags & LPSIM_F_NO_LIGHT) || c->timing) return false;
     const uint64_t due = (uint64_t)(std::lower_bound(c->dep_sorted.begin(), c->dep_sorted.end(), c->k + c->C) -
                                     c->dep_sorted.begin());
-    return due <= c->h_ctr[1] + kSmallMax;
+    return due <= c->h_ctr[1] + (c->p.light_trips ? c->p.light_trips : kSmallMax);
 }
 
 // One chunk in the light-load kernel, then the compaction that closes every

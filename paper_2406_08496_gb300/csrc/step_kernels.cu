@@ -177,7 +177,7 @@ struct P1Sinks {
     CrossRec *cr;
     IntendRec *ir;
     DepRec *dr;
-    uint32_t *n;  // [3]: staged crossing requests, intents, departure requests
+    uint32_t *n;  // [4]: staged crossing requests, intents, departure requests; stop-line intents
 };
 
 template <class T>
@@ -206,6 +206,14 @@ __device__ __forceinline__ void block_add(unsigned long long *dst, uint32_t val)
         t = __reduce_add_sync(0xFFFFFFFFu, t);
         if (threadIdx.x == 0 && t) atomicAdd(dst, (unsigned long long)t);
     }
+}
+
+// a counter summed over a full warp (64-bit: a whole chunk's sums)
+__device__ __forceinline__ void warp_add64(unsigned long long *dst, uint32_t val) {
+    unsigned long long v = val;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    if ((threadIdx.x & 31u) == 0 && v) atomicAdd(dst, v);
 }
 
 }  // namespace
@@ -499,8 +507,10 @@ __device__ __forceinline__ bool p1_slot(const Dev &d, const StepView &w, const P
             // go to the top of the same list, growing downwards.
             if (cn + 1 < len)
                 stage_put(sk.ir, kStageIntend, sk.n + 1, d.intend_list[par], &d.counts[2 + par], ir);
-            else
+            else {
                 d.intend_list[par][d.cap - 1 - warp_append(&d.counts[6 + par])] = ir;
+                atomicAdd(sk.n + 3, 1u);
+            }
         }
     }
     return true;
@@ -541,8 +551,8 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) step_p1(Dev d, uint32_t k
     __shared__ __align__(16) CrossRec s_cr[kStageCross];
     __shared__ __align__(16) IntendRec s_ir[kStageIntend];
     __shared__ __align__(16) DepRec s_dr[kStageDep];
-    __shared__ uint32_t s_n[3], s_base[3];
-    if (threadIdx.x < 3) s_n[threadIdx.x] = 0;
+    __shared__ uint32_t s_n[4], s_base[3];
+    if (threadIdx.x < 4) s_n[threadIdx.x] = 0;
     __syncthreads();
     const P1Sinks sk{s_cr, s_ir, s_dr, s_n};
     uint32_t live = 0;
@@ -849,52 +859,70 @@ __global__ void __launch_bounds__(BLOCK) step_p3(Dev d, uint32_t koff, uint32_t 
 
 // Many steps in one block when few vehicles move: the three phases of a
 // step are separated by block barriers instead of kernel boundaries.  The
-// host picks this kernel for a chunk only when at most kSmallMax trips can be
-// on the network or waiting during it; olist holds the origin edges that can
-// act in the chunk (a queue head due before its end, or a claim to reset).
-// Every phase body is the one the grid-wide kernels run, so the results are
-// the same.  (Clusters of 2-8 such blocks, synchronised by cluster barriers,
-// were measured slower than the grid-wide kernels for 2k-12k trips.)
+// host picks this kernel for a chunk only when few trips can be on the
+// network or waiting during it; olist holds the origin edges that can act in
+// the chunk (a queue head due before its end, or a claim to reset).  Every
+// phase body is the one the grid-wide kernels run, so the results are the
+// same.  What the grid-wide kernels pass through global memory stays on chip
+// here: the per-step lists are read from the block's stages (only items
+// beyond a stage's room go through the global lists, from position 0), the
+// list lengths come from the stage counters, the slot count and the crossing
+// log position live in registers and the statistics counters are summed
+// over the whole chunk.  A step then costs three block barriers and no
+// global round trip of its own.  (Clusters of 2-8 such blocks, synchronised
+// by cluster barriers, were measured slower than the grid-wide kernels for
+// 2k-12k trips.)
 __global__ void __launch_bounds__(kSmallBlock, 1)
     step_small(Dev d, uint32_t k0, uint32_t nsteps, const uint32_t *olist, const uint32_t *no_ptr) {
     const uint32_t tid = threadIdx.x;
     const uint32_t no = *no_ptr;
+    uint32_t n = *d.n_slots, ev0 = *d.ev_n;
     __shared__ __align__(16) CrossRec s_cr[kStageCross];
     __shared__ __align__(16) IntendRec s_ir[kStageIntend];
     __shared__ __align__(16) DepRec s_dr[kStageDep];
-    __shared__ uint32_t s_n[3], s_base[3];
+    __shared__ uint32_t s_n[4];
     const P1Sinks sk{s_cr, s_ir, s_dr, s_n};
+    if (tid < 4) s_n[tid] = 0;
+    __syncthreads();
+    uint32_t live = 0, arrived = 0, events = 0, departed = 0, changes = 0;
     for (uint32_t t = 0; t < nsteps; t++) {
         const uint32_t k = k0 + t, par = k & 1u;
         const StepView w = step_view(d, k, k);
         // P1
-        if (tid < 3) s_n[tid] = 0;
-        __syncthreads();
-        const uint32_t n = *d.n_slots;
-        uint32_t live = 0, arrived = 0;
         for (uint32_t i = tid; i < no; i += kSmallBlock) p1_origin(d, w, sk, olist[i]);
         for (uint32_t s = tid; s < n; s += kSmallBlock) p1_slot(d, w, sk, s, n, live, arrived);
-        block_add<kSmallBlock>(&d.ctr[0], live);
-        if (arrived) atomicAdd(&d.ctr[1], (unsigned long long)arrived);
-        p1_flush(d, par, sk, s_base);
         __syncthreads();
-        // P2
-        uint32_t events = 0, departed = 0, changes = 0;
-        const uint32_t ncross = d.counts[par], ndep = d.counts[4 + par], ev0 = *d.ev_n;
-        const uint32_t nint = d.counts[2 + par], nlate = d.counts[6 + par];
-        for (uint32_t i = tid; i < ncross; i += kSmallBlock) p2_cross(d, w, d.cross_list[par][i], ev0 + i, events);
-        for (uint32_t i = tid; i < nint; i += kSmallBlock) p3_intend(d, w, d.intend_list[par][i], changes);
-        for (uint32_t q = tid; q < ndep; q += kSmallBlock) p2_dep(d, w, d.dep_rec[par][q], q, n, events, departed);
-        if (events) atomicAdd(&d.ctr[3], (unsigned long long)events);
-        if (departed) atomicAdd(&d.ctr[4], (unsigned long long)departed);
+        // P2: staged items first, then the overflow in the global lists
+        const uint32_t ncross = s_n[0], nint = s_n[1], ndep = s_n[2], nlate = s_n[3];
+        for (uint32_t i = tid; i < ncross; i += kSmallBlock)
+            p2_cross(d, w, i < kStageCross ? s_cr[i] : d.cross_list[par][i - kStageCross], ev0 + i, events);
+        for (uint32_t i = tid; i < nint; i += kSmallBlock)
+            p3_intend(d, w, i < kStageIntend ? s_ir[i] : d.intend_list[par][i - kStageIntend], changes);
+        for (uint32_t q = tid; q < ndep; q += kSmallBlock)
+            p2_dep(d, w, q < kStageDep ? s_dr[q] : d.dep_rec[par][q - kStageDep], q, n, events, departed);
         __syncthreads();
-        // P3
+        // P3 (every thread has read the stage counters: the next step's start here)
+        if (tid < 4) s_n[tid] = 0;
         for (uint32_t i = tid; i < nlate; i += kSmallBlock) p3_intend(d, w, d.intend_list[par][d.cap - 1 - i], changes);
-        if (changes) atomicAdd(&d.ctr[2], (unsigned long long)changes);
-        __syncthreads();
-        if (tid == 0) step_tail(d, par);
+        if (tid == 0) {  // the next step's global lists start empty
+            d.counts[par ^ 1u] = 0;
+            d.counts[2 + (par ^ 1u)] = 0;
+            d.counts[4 + (par ^ 1u)] = 0;
+            d.counts[6 + (par ^ 1u)] = 0;
+        }
+        n += ndep;
+        ev0 += ncross;
         __syncthreads();
     }
+    if (tid == 0) {
+        *d.n_slots = n;
+        *d.ev_n = ev0;
+    }
+    warp_add64(&d.ctr[0], live);
+    warp_add64(&d.ctr[1], arrived);
+    warp_add64(&d.ctr[2], changes);
+    warp_add64(&d.ctr[3], events);
+    warp_add64(&d.ctr[4], departed);
 }
 
 // Origin edges that can act in steps [k0, k1): a queue head due before k1,

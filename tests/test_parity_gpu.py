@@ -195,6 +195,33 @@ def test_light_and_grid_wide_chunks_alternate():
     assert_outputs_equal(o, g, n_bins=12)
 
 
+def test_light_kernel_lists_beyond_its_stages():
+    """Every chunk in the light-load block (light_trips far above the trip
+    count) while 6,000 trips leave a 12x12 grid within two minutes: hundreds
+    of departure requests and crossing requests per step, more than the
+    block's shared-memory stages hold, so the overflow through the global
+    lists is exercised; every output matches the oracle."""
+    import oracle as O
+    from paper_2406_08496_gb300 import Simulation
+    net = W.grid_network(12, 12)
+    dem = W.route(net, W.uniform_demand(net, 6000, 13, t_max_s=120.0))
+    params = dict(bin_steps=600, n_bins=6)
+    o = O.Oracle(net, params)
+    o.load_demand(dem)
+    g = Simulation(net, dict(params, light_trips=10**9))
+    g.load_demand(dem)
+    for _ in range(3):
+        o.step(768)
+        g.step(768)
+        assert_state_equal(o.state(), g.state(), f"step {o.counters()['k']}")
+    ro = o.run(60000)
+    rg = g.run(60000)
+    for key in ("steps", "veh_steps", "arrived", "active", "waiting", "k"):
+        assert ro[key] == rg[key], (key, ro[key], rg[key])
+    assert_outputs_equal(o, g, n_bins=6)
+    assert o.counters()["lane_changes"] == g.counters()["lane_changes"]
+
+
 def test_kernel_timing_direct_and_graph_steps(grid_day):
     """Per-kernel timing around direct steps and graph chunks alike, and the
     results unchanged by it."""
