@@ -208,7 +208,15 @@ __device__ __forceinline__ void block_add(unsigned long long *dst, uint32_t val)
     }
 }
 
-// a counter summed over a full warp (64-bit: a whole chunk's sums)
+// A statistics counter summed over a full warp, then one atomic per warp:
+// per-thread atomics on one address serialise in L2 (one per crossing
+// vehicle made step_p2 take 60% longer at the morning peak).
+__device__ __forceinline__ void warp_add(unsigned long long *dst, uint32_t val) {
+    const uint32_t w = __reduce_add_sync(0xFFFFFFFFu, val);
+    if ((threadIdx.x & 31u) == 0 && w) atomicAdd(dst, (unsigned long long)w);
+}
+
+// the same in 64 bits (a whole chunk's sums)
 __device__ __forceinline__ void warp_add64(unsigned long long *dst, uint32_t val) {
     unsigned long long v = val;
 #pragma unroll
@@ -565,7 +573,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) step_p1(Dev d, uint32_t k
         if (!p1_slot(d, w, sk, i - norg, n, live, arrived)) break;
     }
     block_add<BLOCK>(&d.ctr[0], live);
-    if (arrived) atomicAdd(&d.ctr[1], (unsigned long long)arrived);
+    warp_add(&d.ctr[1], arrived);
     p1_flush(d, w.par, sk, s_base);
 }
 
@@ -748,9 +756,10 @@ __device__ __forceinline__ void p3_intend(const Dev &d, const StepView &w, const
         ok = (xn - (float)cb) >= G_lag;
     }
     if (ok && cn >= 1 && tgt_map == kEmpty && tgt_mark == 0) {
-        const uint32_t own = base + cn;
-        Mn[tgt] = Mn[own];
-        Mn[own] = kEmpty;
+        // the own next cell holds the byte step P1 wrote there (its intent
+        // mark keeps every other mover out of it)
+        Mn[tgt] = speed_byte(vn);
+        Mn[base + cn] = kEmpty;
         d.s.lane[s] = (uint8_t)(up ? ln + 1 : ln - 1);
         d.s.es[s].base = base2;
         changes++;
@@ -801,9 +810,9 @@ __global__ void __launch_bounds__(BLOCK) step_p2(Dev d, uint32_t koff, uint32_t 
             p2_dep(d, w, dr, q, n0, events, departed);
         }
     }
-    if (events) atomicAdd(&d.ctr[3], (unsigned long long)events);
-    if (departed) atomicAdd(&d.ctr[4], (unsigned long long)departed);
-    if (changes) atomicAdd(&d.ctr[2], (unsigned long long)changes);
+    warp_add(&d.ctr[3], events);
+    warp_add(&d.ctr[4], departed);
+    warp_add(&d.ctr[2], changes);
 }
 
 // End of step k (one thread): the next step's lists start empty; the
@@ -844,7 +853,7 @@ __global__ void __launch_bounds__(BLOCK) step_p3(Dev d, uint32_t koff, uint32_t 
         if (i >= nint) break;
         p3_intend(d, w, ir, changes);
     }
-    if (changes) atomicAdd(&d.ctr[2], (unsigned long long)changes);
+    warp_add(&d.ctr[2], changes);
     if (closer) {
         d.counts[par ^ 1u] = 0;
         d.counts[2 + (par ^ 1u)] = 0;
