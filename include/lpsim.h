@@ -261,13 +261,14 @@ int lpsim_autotune(lpsim_ctx *ctx, uint32_t window_steps, lpsim_tune_result *out
 int lpsim_set_config(lpsim_ctx *ctx, uint32_t block_size, uint32_t blocks_per_sm, uint32_t sort_period,
                      uint32_t chunk_steps);
 
-/* Per-kernel timing.  While on, every launch of the three step kernels
- * (step_p1: car following, departures and claims; step_p2: entry conflicts;
- * step_p3: lane changes) and of the compaction/sort sequence is bracketed by
- * CUDA events on the context's stream, and the elapsed times are summed after
- * each graph chunk (which then synchronises).  Switching resets the sums.
- * lpsim_get_kernel_times fills ms[4] (summed milliseconds) and launches[4]
- * (phase launches timed) in the order step_p1, step_p2, step_p3, compaction. */
+/* Per-kernel timing.  While on, every launch of the two step kernels
+ * (step_p1: car following, edge-end decisions, lane-change intents,
+ * departure and entry claims; step_p2: entry conflicts, departures, lane
+ * changes) and of the compaction/sort sequence is bracketed by CUDA events on
+ * the context's stream, and the elapsed times are summed after each graph
+ * chunk (which then synchronises).  Switching resets the sums.
+ * lpsim_get_kernel_times fills ms[3] (summed milliseconds) and launches[3]
+ * (phase launches timed) in the order step_p1, step_p2, compaction. */
 int lpsim_set_kernel_timing(lpsim_ctx *ctx, int on);
 int lpsim_get_kernel_times(lpsim_ctx *ctx, double *ms, uint64_t *launches);
 

@@ -308,10 +308,10 @@ class Simulation:
         _check(self.lib, self.lib.lpsim_set_kernel_timing(self.h, 1 if on else 0))
 
     def kernel_times(self) -> dict:
-        ms = np.zeros(4, np.float64)
-        n = np.zeros(4, np.uint64)
+        ms = np.zeros(3, np.float64)
+        n = np.zeros(3, np.uint64)
         _check(self.lib, self.lib.lpsim_get_kernel_times(self.h, _p(ms), _p(n)))
-        names = ("step_p1", "step_p2", "step_p3", "compact_sort")
+        names = ("step_p1", "step_p2", "compact_sort")
         return {k: {"ms": float(ms[i]), "launches": int(n[i])} for i, k in enumerate(names)}
 
     def snapshot(self) -> None:

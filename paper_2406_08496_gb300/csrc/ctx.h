@@ -70,8 +70,8 @@ struct lpsim_ctx {
     // per-kernel timing (events around every phase launch of every step)
     bool timing = false;
     std::vector<cudaEvent_t> ev;     // 5 per step of a chunk
-    double t_ms[4] = {0, 0, 0, 0};   // step_p1, step_p2, step_p3, compaction + sort
-    uint64_t t_n[4] = {0, 0, 0, 0};
+    double t_ms[3] = {0, 0, 0};   // step_p1, step_p2, compaction + sort
+    uint64_t t_n[3] = {0, 0, 0};
     std::string t_err;               // first failure of cudaEventElapsedTime
 
     void *dalloc(size_t bytes) {

@@ -159,7 +159,7 @@ struct __align__(16) DepRec {
     uint8_t lane, tlc;                // lane asked for, target lane for the movement after the origin edge
 };
 
-// What step_p3 needs of a lane-change intender (packed by step_p1).
+// What step_p2 needs of a lane-change intender (packed by step_p1).
 struct __align__(16) IntendRec {
     uint32_t s, base;                 // slot, current lane row
     uint64_t hk;                      // lane-change draw key
@@ -198,7 +198,8 @@ struct Dev {
     // per-step lists, by step parity
     CrossRec *cross_list[2];
     IntendRec *intend_list[2];
-    uint32_t *counts;          // [0..1] cross count by parity, [2..3] intend count, [4..5] departure requests
+    uint32_t *counts;          // [0..1] cross count by parity, [2..3] intend count, [4..5] departure requests,
+                               // [6..7] stop-line intents (at the top of intend_list)
     DepRec *dep_rec[2];        // departure requests, by parity
     // crossings of the current chunk (or direct step), applied to the link
     // statistics by one kernel at its end instead of seven scattered atomics
@@ -209,6 +210,14 @@ struct Dev {
     uint4 *ev_log;
     uint32_t ev_cap;
     uint32_t *ev_n;
+    // {*n_slots, *ev_n} at the start of the current step (written by
+    // step_P1, read by step_P2, which advances the two live values)
+    uint32_t *snap;
+    // per lane row (index = the row's map offset / 16): the crossing request
+    // made from it at step k, {k, claim slot, vehicle id, 0}; a stop-line
+    // lane-change intent reads the row it aims at to learn whether a hold
+    // will land on its target cell in the same kernel
+    uint4 *xreq;
     // statistics; binned arrays are bin-major ([bin][edge]) so the updates of
     // one step fall in one or two rows that stay in L2
     unsigned long long *ent, *ext, *tts;

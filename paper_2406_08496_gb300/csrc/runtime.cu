@@ -114,6 +114,7 @@ int reset_state(lpsim_ctx *c) {
     cudaStream_t st = c->stream;
     for (int i = 0; i < 3; i++) CU(cudaMemsetAsync(d.map[i], 0xFF, c->map_bytes, st));
     for (int i = 0; i < 2; i++) CU(cudaMemsetAsync(d.imap[i], 0, c->map_bytes, st));
+    CU(cudaMemsetAsync(d.xreq, 0xFF, c->map_bytes, st));  // no request at any step
     for (int i = 0; i < 2; i++) CU(cudaMemsetAsync(d.claim[i], 0xFF, c->lane_slots * 4, st));
     CU(cudaMemsetAsync(d.ent, 0, c->n_edges * 8ull, st));
     CU(cudaMemsetAsync(d.ext, 0, c->n_edges * 8ull, st));
@@ -166,22 +167,22 @@ int read_status(lpsim_ctx *c) {
 int enqueue_step(lpsim_ctx *c, uint32_t koff, uint32_t kph, int cur, bool compact) {
     Dev d = c->d;
     d.s = c->sets[cur];
-    cudaEvent_t *e = c->timing ? &c->ev[5 * koff] : nullptr;
+    cudaEvent_t *e = c->timing ? &c->ev[4 * koff] : nullptr;
     // cudaEventRecordExternal: inside a stream capture the record becomes an
     // event-record node that timestamps when the graph runs (the flag is for
     // captures only; a direct step records plainly)
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (e) cudaStreamIsCapturing(c->stream, &cs);
     const unsigned flags = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
-    for (int ph = 1; ph <= 3; ph++) {
+    for (int ph = 1; ph <= 2; ph++) {
         if (e) cudaEventRecordWithFlags(e[ph - 1], c->stream, flags);
         launch_phase(d, ph, koff, kph, c->grid, c->block, c->stream);
     }
-    if (e) cudaEventRecordWithFlags(e[3], c->stream, flags);
+    if (e) cudaEventRecordWithFlags(e[2], c->stream, flags);
     if (compact) {
         launch_compact(d, c->sets[cur ^ 1], c->w, koff, c->sort, c->grid, c->stream);
         cur ^= 1;
-        if (e) cudaEventRecordWithFlags(e[4], c->stream, flags);
+        if (e) cudaEventRecordWithFlags(e[3], c->stream, flags);
     }
     return cur;
 }
@@ -190,10 +191,10 @@ int enqueue_step(lpsim_ctx *c, uint32_t koff, uint32_t kph, int cur, bool compac
 void collect_times(lpsim_ctx *c, uint32_t n, uint64_t k_first) {
     if (!c->timing) return;
     for (uint32_t j = 0; j < n; j++) {
-        cudaEvent_t *e = &c->ev[5 * j];
+        cudaEvent_t *e = &c->ev[4 * j];
         float ms = 0.0f;
-        for (int ph = 0; ph < 4; ph++) {
-            if (ph == 3 && (k_first + j + 1) % c->R != 0) break;
+        for (int ph = 0; ph < 3; ph++) {
+            if (ph == 2 && (k_first + j + 1) % c->R != 0) break;
             cudaError_t r = cudaEventElapsedTime(&ms, e[ph], e[ph + 1]);
             if (r == cudaSuccess) {
                 c->t_ms[ph] += ms;
@@ -210,7 +211,7 @@ void collect_times(lpsim_ctx *c, uint32_t n, uint64_t k_first) {
 int direct_step(lpsim_ctx *c) {
     bool compact = (c->k + 1) % c->R == 0;
     c->cur = enqueue_step(c, 0, (uint32_t)(c->k % 6), c->cur, compact);
-    c->launches += 3;
+    c->launches += 2;
     if (compact) c->launches += c->sort ? 3 + 3ull * ((c->w.key_bits + 7) / 8) + 1 : 3;
     launch_apply_crossings(c->d, c->grid, c->stream);
     launch_chunk_end(c->d, 1, c->stream);
@@ -245,7 +246,7 @@ int capture_chunk(lpsim_ctx *c, int start_set) {
 uint64_t chunk_launches(const lpsim_ctx *c) {
     uint64_t per_compact = 3;
     if (c->sort) per_compact = 2 + 1 + 3ull * ((c->w.key_bits + 7) / 8) + 1;
-    return 3ull * c->C + (c->C / c->R) * per_compact + 2;
+    return 2ull * c->C + (c->C / c->R) * per_compact + 2;
 }
 
 int chunk(lpsim_ctx *c) {
@@ -528,6 +529,9 @@ int load_network_impl(lpsim_ctx **out, const lpsim_network *net, const lpsim_par
         if ((rc = dnew_mut(c, d.map[i], c->map_bytes))) return bail(rc);
     for (int i = 0; i < 2; i++)
         if ((rc = dnew_mut(c, d.imap[i], c->map_bytes))) return bail(rc);
+    // one crossing-request record per 16 map bytes: every lane row starts on
+    // a 16-byte boundary and spans at least 16 bytes
+    if ((rc = dnew_mut(c, d.xreq, c->map_bytes / 16)) || (rc = dnew_mut(c, d.snap, 2))) return bail(rc);
     if ((rc = dnew_mut(c, d.claim[0], slots)) || (rc = dnew_mut(c, d.claim[1], slots)) ||
         (rc = dnew_mut(c, d.ent, ne)) || (rc = dnew_mut(c, d.ext, ne)) || (rc = dnew_mut(c, d.tts, ne)))
         return bail(rc);
@@ -805,9 +809,9 @@ int apply_config(lpsim_ctx *c, uint32_t block, uint32_t bps, uint32_t R, uint32_
     c->p.blocks_per_sm = bps;
     c->p.sort_period = R;
     c->p.chunk_steps = chunk;
-    if (c->timing && c->ev.size() < 5ull * c->C) {
+    if (c->timing && c->ev.size() < 4ull * c->C) {
         size_t old = c->ev.size();
-        c->ev.resize(5ull * c->C);
+        c->ev.resize(4ull * c->C);
         for (size_t i = old; i < c->ev.size(); i++) CU(cudaEventCreate(&c->ev[i]));
     }
     return LPSIM_OK;
@@ -1066,12 +1070,12 @@ int lpsim_set_kernel_timing(lpsim_ctx *c, int on) {
             c->graph[i] = nullptr;
         }
     if (on && c->ev.empty()) {
-        c->ev.resize(5ull * c->C);
+        c->ev.resize(4ull * c->C);
         for (auto &e : c->ev) CU(cudaEventCreate(&e));
     }
     c->timing = on != 0;
     c->t_err.clear();
-    for (int i = 0; i < 4; i++) {
+    for (int i = 0; i < 3; i++) {
         c->t_ms[i] = 0.0;
         c->t_n[i] = 0;
     }
@@ -1081,7 +1085,7 @@ int lpsim_set_kernel_timing(lpsim_ctx *c, int on) {
 int lpsim_get_kernel_times(lpsim_ctx *c, double *ms, uint64_t *launches) {
     if (!c || !ms || !launches) return fail(LPSIM_E_INVALID_ARG, "NULL argument");
     if (!c->t_err.empty()) return fail(LPSIM_E_CUDA, c->t_err);
-    for (int i = 0; i < 4; i++) {
+    for (int i = 0; i < 3; i++) {
         ms[i] = c->t_ms[i];
         launches[i] = c->t_n[i];
     }

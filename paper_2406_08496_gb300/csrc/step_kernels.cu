@@ -1,6 +1,6 @@
 // Per-step kernels of the vehicle update (Algorithm 1, Sec. 3.1-3.2).
 //
-// One step k is three launches:
+// One step k is two launches:
 //   step_p1  every live vehicle: leader search in the step-k lane map,
 //            IDM / free-flow speed, move with the no-crash clamp, and the
 //            decision at the edge end (arrive, ask to cross, hold at the stop
@@ -10,10 +10,16 @@
 //            resolution needs.  Origin edges post the departure claim of
 //            their queue head.
 //   step_p2  crossers and departures: the lowest id of each claimed slot
-//            enters cell 0; the others stop at the stop line.
-//   step_p3  lane-change intenders: gap acceptance against the step-k map and
-//            against the reservations of step_p1/step_p2; the accepted move
-//            their next-map byte sideways.  Claims are reset.
+//            enters cell 0; the others stop at the stop line.  Lane-change
+//            intenders, in the same launch: gap acceptance against the
+//            step-k map and the next map; the accepted move their next-map
+//            byte sideways.  A stop-line hold can only land on cell len - 1
+//            of its own lane, so an intent aiming at any other cell cannot
+//            meet one; an intent aiming at a cell len - 1 reads the crossing
+//            request made from that lane (at most one: only the lane's front
+//            vehicle can reach the stop line) and its claim, which step_p1
+//            settled, and so knows whether a hold will land there.  The same
+//            launch closes the step (list counts, slot count, crossing log).
 //
 // Three lane maps rotate: step k reads map[k%3] and writes map[(k+1)%3];
 // map[(k+2)%3] still holds the cells of step k-1, which step_p1 erases (each
@@ -455,6 +461,7 @@ __device__ __forceinline__ bool p1_slot(const Dev &d, const StepView &w, const P
             if (l != kNone) {
                 const uint32_t slot = so + l;
                 atomicMin(&claim[slot], id);
+                d.xreq[base >> 4] = make_uint4(k, slot, id, 0u);
                 CrossRec cr;
                 cr.s = s;
                 cr.id = id;
@@ -509,10 +516,9 @@ __device__ __forceinline__ bool p1_slot(const Dev &d, const StepView &w, const P
             ir.len = (uint16_t)len;
             ir.lane = (uint8_t)ln;
             ir.up = tl > ln ? 1 : 0;
-            // A stop-line hold (a crossing request that loses in step_p2) can only take cell
-            // len - 1 of its lane; an intent aiming at any other cell is decided in step_p2
-            // alongside the crossings, one aiming at len - 1 waits for step_p3.  Those few
-            // go to the top of the same list, growing downwards.
+            // An intent aiming at cell len - 1 (where a stop-line hold may land) goes to
+            // the top of the same list, growing downwards: step_p2 checks those few
+            // against the crossing request of the target lane.
             if (cn + 1 < len)
                 stage_put(sk.ir, kStageIntend, sk.n + 1, d.intend_list[par], &d.counts[2 + par], ir);
             else {
@@ -553,6 +559,10 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) step_p1(Dev d, uint32_t k
     pdl_prologue();
     const uint32_t k = *d.kbase + koff;
     const uint32_t n = *d.n_slots;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        d.snap[0] = n;
+        d.snap[1] = *d.ev_n;
+    }
     const StepView w = step_view(d, k, kph);
     const uint32_t norg = d.n_org;
     const uint32_t lim = norg + d.cap;  // items: origin edges first, then slots
@@ -700,8 +710,12 @@ __device__ __forceinline__ void load_chunks(const uint8_t *row, uint32_t c_first
 }
 
 // Lane-change intender ir: gap acceptance against the step-k map and the
-// reservations of the next map; the accepted move their byte sideways.
-__device__ __forceinline__ void p3_intend(const Dev &d, const StepView &w, const IntendRec &ir, uint32_t &changes) {
+// reservations of the next map; the accepted move their byte sideways.  With
+// `late` (the intent aims at cell len - 1 and runs alongside the crossing
+// requests) a hold that a losing crosser of the target lane is placing in the
+// same kernel counts as occupying the target cell.
+__device__ __forceinline__ void lane_change(const Dev &d, const StepView &w, const IntendRec &ir, uint32_t &changes,
+                                          bool late) {
     const uint32_t k = w.k;
     const uint8_t *Mc = w.Mc;
     uint8_t *Mn = w.Mn;
@@ -724,6 +738,7 @@ __device__ __forceinline__ void p3_intend(const Dev &d, const StepView &w, const
     load_chunks<9>(row2, cfirst, hi, mk);
     const uint32_t tgt = base2 + cn;
     const uint8_t tgt_map = Mn[tgt], tgt_mark = Iw[tgt];
+    const uint4 xr = late ? d.xreq[base2 >> 4] : make_uint4(kNone, 0u, 0u, 0u);
     uint64_t h = 0;
     if (m.eps_amp > 0.0f) h = splitmix64_mix(ir.hk ^ ((uint64_t)k * 0xD1B54A32D192ED03ull));
     // lead: first occupied cell in [c0, hi]; lag: last in [lo, c0 - 1]
@@ -755,6 +770,9 @@ __device__ __forceinline__ void p3_intend(const Dev &d, const StepView &w, const
         const float G_lag = (m.g_b + fmax0(m.alpha_b * vb - m.alpha_i * vn)) + eps_b;
         ok = (xn - (float)cb) >= G_lag;
     }
+    // a crossing request from the target lane at this step that lost its
+    // claim holds at cell len - 1, the target cell of a late intent
+    if (ok && xr.x == k) ok = w.claim[xr.y] == xr.z;
     if (ok && cn >= 1 && tgt_map == kEmpty && tgt_mark == 0) {
         // the own next cell holds the byte step P1 wrote there (its intent
         // mark keeps every other mover out of it)
@@ -767,19 +785,29 @@ __device__ __forceinline__ void p3_intend(const Dev &d, const StepView &w, const
 }
 
 // Blocks [0, gc) take the crossing requests, [gc, gc + gi) the lane-change
-// intents aiming at a cell no stop-line hold can take, the last gdep (enough
-// for one request per origin edge) the departure requests; each thread's
-// first record is loaded together with its list's length.
+// intents aiming at a cell no stop-line hold can take, block gc + gi those
+// aiming at a cell len - 1, the last gdep (enough for one request per origin
+// edge) the departure requests; each thread's first record is loaded
+// together with its list's length.  Thread 0 of block 0 closes the step: the
+// next step's lists start empty, this step's departures have taken their
+// slots and its crossings their log entries (every other thread reads the
+// step's starting values from the snapshot step_p1 took).
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) step_p2(Dev d, uint32_t koff, uint32_t kph, uint32_t gc, uint32_t gi) {
     pdl_prologue();
     const uint32_t par = kph & 1u;
     const uint32_t k = *d.kbase + koff;
     const StepView w = step_view(d, k, kph);
+    const bool closer = blockIdx.x == 0 && threadIdx.x == 0;
+    uint32_t ndep_c = 0, ns = 0;
+    if (closer) {
+        ndep_c = d.counts[4 + par];
+        ns = d.snap[0];
+    }
     uint32_t events = 0, departed = 0, changes = 0;
     if (blockIdx.x < gc) {
         const uint32_t ncross = d.counts[par];
-        const uint32_t ev0 = *d.ev_n;  // this step's crossings follow the chunk's earlier ones in the log
+        const uint32_t ev0 = d.snap[1];  // this step's crossings follow the chunk's earlier ones in the log
         const CrossRec *list = d.cross_list[par];
         // item i goes to block i % gc: a short list spreads over every block (and SM)
         for (uint32_t i = threadIdx.x * gc + blockIdx.x; i < d.cap; i += gc * BLOCK) {
@@ -788,6 +816,14 @@ __global__ void __launch_bounds__(BLOCK) step_p2(Dev d, uint32_t koff, uint32_t 
             if (i >= ncross) break;
             p2_cross(d, w, cr, ev0 + i, events);
         }
+        if (closer) {
+            d.counts[par ^ 1u] = 0;
+            d.counts[2 + (par ^ 1u)] = 0;
+            d.counts[4 + (par ^ 1u)] = 0;
+            d.counts[6 + (par ^ 1u)] = 0;
+            *d.n_slots = ns + ndep_c;
+            *d.ev_n = ev0 + ncross;
+        }
     } else if (blockIdx.x < gc + gi) {
         const uint32_t nint = d.counts[2 + par];
         const IntendRec *list = d.intend_list[par];
@@ -795,12 +831,21 @@ __global__ void __launch_bounds__(BLOCK) step_p2(Dev d, uint32_t koff, uint32_t 
             const IntendRec ir = list[i];
             loads_issued();
             if (i >= nint) break;
-            p3_intend(d, w, ir, changes);
+            lane_change(d, w, ir, changes, false);
+        }
+    } else if (blockIdx.x == gc + gi) {
+        const uint32_t nlate = d.counts[6 + par];
+        const IntendRec *top = d.intend_list[par] + (d.cap - 1);
+        for (uint32_t i = threadIdx.x; i < d.cap; i += BLOCK) {
+            const IntendRec ir = *(top - i);
+            loads_issued();
+            if (i >= nlate) break;
+            lane_change(d, w, ir, changes, true);
         }
     } else {
         const uint32_t ndep = d.counts[4 + par];
-        const uint32_t n0 = *d.n_slots;
-        const uint32_t b0 = gc + gi;
+        const uint32_t n0 = d.snap[0];
+        const uint32_t b0 = gc + gi + 1;
         const uint32_t nthr = (gridDim.x - b0) * BLOCK;
         const DepRec *list = d.dep_rec[par];
         for (uint32_t q = (blockIdx.x - b0) * BLOCK + threadIdx.x; q < d.n_org; q += nthr) {
@@ -813,55 +858,6 @@ __global__ void __launch_bounds__(BLOCK) step_p2(Dev d, uint32_t koff, uint32_t 
     warp_add(&d.ctr[3], events);
     warp_add(&d.ctr[4], departed);
     warp_add(&d.ctr[2], changes);
-}
-
-// End of step k (one thread): the next step's lists start empty; the
-// departures of this step have taken their slots.
-__device__ __forceinline__ void step_tail(const Dev &d, uint32_t par) {
-    d.counts[par ^ 1u] = 0;
-    d.counts[2 + (par ^ 1u)] = 0;
-    d.counts[4 + (par ^ 1u)] = 0;
-    d.counts[6 + (par ^ 1u)] = 0;
-    *d.n_slots += d.counts[4 + par];
-    *d.ev_n += d.counts[par];
-}
-
-// The lane-change intents aiming at a stop-line cell (after step_p2 placed
-// the holds), then the end of the step.
-template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK) step_p3(Dev d, uint32_t koff, uint32_t kph) {
-    pdl_prologue();
-    const uint32_t par = kph & 1u;
-    const uint32_t k = *d.kbase + koff;
-    const StepView w = step_view(d, k, kph);
-    const bool closer = blockIdx.x == 0 && threadIdx.x == 0;
-    // the closing thread reads what the end of the step needs right away
-    // (none of it changes in this kernel), so the list reset waits on no load
-    uint32_t ndep = 0, ncross = 0, ns = 0, ne = 0;
-    if (closer) {
-        ndep = d.counts[4 + par];
-        ncross = d.counts[par];
-        ns = *d.n_slots;
-        ne = *d.ev_n;
-    }
-    const uint32_t nint = d.counts[6 + par];
-    const IntendRec *top = d.intend_list[par] + (d.cap - 1);
-    uint32_t changes = 0;
-    for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < d.cap; i += gridDim.x * BLOCK) {
-        const IntendRec ir = *(top - i);
-        loads_issued();
-        if (i >= nint) break;
-        p3_intend(d, w, ir, changes);
-    }
-    warp_add(&d.ctr[2], changes);
-    if (closer) {
-        d.counts[par ^ 1u] = 0;
-        d.counts[2 + (par ^ 1u)] = 0;
-        d.counts[4 + (par ^ 1u)] = 0;
-        d.counts[6 + (par ^ 1u)] = 0;
-        *d.n_slots = ns + ndep;
-        *d.ev_n = ne + ncross;
-    }
 }
 
 // ------------------------------------------------------------ light load
@@ -906,13 +902,14 @@ __global__ void __launch_bounds__(kSmallBlock, 1)
         for (uint32_t i = tid; i < ncross; i += kSmallBlock)
             p2_cross(d, w, i < kStageCross ? s_cr[i] : d.cross_list[par][i - kStageCross], ev0 + i, events);
         for (uint32_t i = tid; i < nint; i += kSmallBlock)
-            p3_intend(d, w, i < kStageIntend ? s_ir[i] : d.intend_list[par][i - kStageIntend], changes);
+            lane_change(d, w, i < kStageIntend ? s_ir[i] : d.intend_list[par][i - kStageIntend], changes, false);
         for (uint32_t q = tid; q < ndep; q += kSmallBlock)
             p2_dep(d, w, q < kStageDep ? s_dr[q] : d.dep_rec[par][q - kStageDep], q, n, events, departed);
         __syncthreads();
         // P3 (every thread has read the stage counters: the next step's start here)
         if (tid < 4) s_n[tid] = 0;
-        for (uint32_t i = tid; i < nlate; i += kSmallBlock) p3_intend(d, w, d.intend_list[par][d.cap - 1 - i], changes);
+        for (uint32_t i = tid; i < nlate; i += kSmallBlock)
+            lane_change(d, w, d.intend_list[par][d.cap - 1 - i], changes, false);
         if (tid == 0) {  // the next step's global lists start empty
             d.counts[par ^ 1u] = 0;
             d.counts[2 + (par ^ 1u)] = 0;
@@ -998,17 +995,17 @@ void launch_pdl(void (*kernel)(Args...), int grid, int block, cudaStream_t st, A
 }  // namespace
 
 void launch_phase(const Dev &d, int phase, uint32_t koff, uint32_t kph, int grid, int block, cudaStream_t st) {
-    // step_p2 and step_p3 walk short lists (crossers, intenders): a quarter
-    // of the grid is plenty; step_p2 adds one block per `block` origin edges
-    // for the departure requests (at most one per origin edge and step)
-    const int g = phase == 1 ? grid : (grid + 3) / 4;
+    // step_p2 walks short lists (crossers, intenders): a quarter of the grid
+    // each for the crossers and the intents, one block for the intents at
+    // stop-line cells (about a hundred per step at most), and one block per
+    // `block` origin edges for the departure requests (at most one per origin
+    // edge and step)
+    const int g = (grid + 3) / 4;
     const uint32_t gdep = std::max(1u, (d.n_org + (uint32_t)block - 1) / (uint32_t)block);
-    const int g3 = 2;  // step_p3: the few intents at stop-line cells (about a hundred per step at most)
 #define LPSIM_PHASE(B)                                                                  \
     do {                                                                                \
-        if (phase == 1) launch_pdl(step_p1<B>, g, B, st, d, koff, kph);                 \
-        else if (phase == 2) launch_pdl(step_p2<B>, 2 * g + (int)gdep, B, st, d, koff, kph, (uint32_t)g, (uint32_t)g); \
-        else launch_pdl(step_p3<B>, g3, B, st, d, koff, kph);                           \
+        if (phase == 1) launch_pdl(step_p1<B>, grid, B, st, d, koff, kph);              \
+        else launch_pdl(step_p2<B>, 2 * g + 1 + (int)gdep, B, st, d, koff, kph, (uint32_t)g, (uint32_t)g); \
     } while (0)
     switch (block) {
     case 128: LPSIM_PHASE(128); break;

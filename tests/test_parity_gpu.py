@@ -222,6 +222,37 @@ def test_light_kernel_lists_beyond_its_stages():
     assert o.counters()["lane_changes"] == g.counters()["lane_changes"]
 
 
+@pytest.mark.parametrize("seed,eps_amp", [(2, 6.0), (5, 10.0)])
+@pytest.mark.parametrize("flags", [0, 4])
+def test_stop_line_intents_beside_losing_crossers(seed, eps_amp, flags):
+    """Short three-lane edges (60 m), 20-step greens and wide random gap
+    components: lane-change intents that end on a stop-line cell pass the gap
+    test (a dozen per run), and in each of these two runs one of them aims
+    at the cell where a crosser of the target lane, losing its entry claim in
+    the same step, is held.  step_p2 decides such an intent alongside the
+    crossings from the target lane's crossing request and its claim; the
+    run matches the oracle, which decides it after placing the holds.  With
+    flags 4 no chunk runs in the light-load block."""
+    import oracle as O
+    from paper_2406_08496_gb300 import Simulation
+    net = W.grid_network(8, 8, spacing=60.0, lanes=3, vmax=13.9, green_steps=20)
+    dem = W.route(net, W.uniform_demand(net, 5000, seed, t_max_s=200.0))
+    params = dict(bin_steps=600, n_bins=2, eps_amp=eps_amp)
+    o = O.Oracle(net, params)
+    o.load_demand(dem)
+    g = Simulation(net, dict(params, flags=flags))
+    g.load_demand(dem)
+    o.step(768)
+    g.step(768)
+    assert_state_equal(o.state(), g.state(), f"step {o.counters()['k']}")
+    ro = o.run(40000)
+    rg = g.run(40000)
+    for key in ("steps", "veh_steps", "arrived", "active", "waiting", "k"):
+        assert ro[key] == rg[key], (key, ro[key], rg[key])
+    assert_outputs_equal(o, g, n_bins=2)
+    assert o.counters()["lane_changes"] == g.counters()["lane_changes"]
+
+
 def test_kernel_timing_direct_and_graph_steps(grid_day):
     """Per-kernel timing around direct steps and graph chunks alike, and the
     results unchanged by it."""
@@ -236,7 +267,7 @@ def test_kernel_timing_direct_and_graph_steps(grid_day):
     kt = g.kernel_times()
     g.set_kernel_timing(False)
     assert kt["step_p1"]["launches"] == 2304 and kt["step_p1"]["ms"] > 0
-    assert kt["step_p2"]["ms"] > 0 and kt["step_p3"]["ms"] > 0
+    assert kt["step_p2"]["ms"] > 0 and kt["step_p2"]["launches"] == 2304
     ref = Simulation(net, {})
     ref.load_demand(dem)
     ref.step(2304)
