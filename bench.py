@@ -359,6 +359,7 @@ def main():
             c1 = sim.counters()
             print(json.dumps({"k": c0["k"], "steps": args.day_profile, "ms": ms,
                               "us_per_step": ms * 1e3 / args.day_profile, "active_start": c0["active"],
+                              "slots_start": c0["slots"],
                               "veh_steps_per_step": (c1["veh_steps"] - c0["veh_steps"]) / args.day_profile,
                               "departures_due": int(np.searchsorted(dep, c0["k"] + args.day_profile)) - c0["arrived"]}),
                   flush=True)

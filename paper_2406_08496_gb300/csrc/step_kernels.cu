@@ -400,13 +400,17 @@ __device__ __forceinline__ bool p1_slot(const Dev &d, const StepView &w, const P
     // vehicle that may reach the stop line, the lane-change key for one
     // that may draw (both only used under the exact conditions below)
     const bool may_end = x + vmax_step * m.dt + 1.0f >= L;  // may reach the stop line (or arrive)
-    const bool may_cross = en != kNone && may_end;
+    // the signal of the edge end, from the slot record: a vehicle facing red
+    // only holds, so it needs none of the crossing records
+    const bool green = may_end && en != kNone && (G == 0 || (k / G) % (ph & 0xFFu) == (ph >> 8));
+    const bool may_cross = green;
     const bool may_draw = tl != kNoLane && tl != ln && ((tl > ln) == (par == 1u)) && (L - x) < m.x0;
     float nv0 = 0.0f;
     RouteRec rr{};
     uint32_t nen = kNone, e = kNone, tent = 0, empty = 0, so = 0;
-    if (may_end) {
-        // the current edge and its entry step (for the statistics)
+    if (may_cross || (may_end && en == kNone)) {
+        // the current edge and its entry step (for the statistics of a
+        // crossing or an arrival)
         e = d.route[rpos];
         tent = d.s.tent[s];
     }
@@ -455,7 +459,7 @@ __device__ __forceinline__ bool p1_slot(const Dev &d, const StepView &w, const P
             return true;
         }
         bool cross = false;
-        if (G == 0 || (k / G) % (ph & 0xFFu) == (ph >> 8)) {
+        if (green) {
             // may_cross holds here: x' >= L needs x + vmax_step * dt >= L
             const uint32_t l = pick_entry_lane(empty, es.nlanes, rr.tl);
             if (l != kNone) {
