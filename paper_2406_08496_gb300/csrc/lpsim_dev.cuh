@@ -61,7 +61,11 @@ struct Model {
 // E's downstream node (green steps and phase count of the node, E's phase)
 // and the target lane on E for the movement onto route[q+1] (kNoLane when q
 // is the trip's last position).  Precomputed on the device at load time so a
-// vehicle entering an edge copies what the next edge's end needs.
+// vehicle entering an edge copies what the next edge's end needs.  (Eight
+// bytes: four consecutive positions of a route share a 32-byte sector, so a
+// vehicle finds the next position's record in L2 more often than not; adding
+// the edge's speed limit and claim slot, tables that stay in L2 anyway, made
+// the step slower.)
 struct __align__(8) RouteRec {
     uint32_t green;
     uint8_t nphase, arank, tl, pad;
@@ -182,6 +186,7 @@ struct Dev {
     const uint32_t *roff;      // route start of vehicle id (n + 1 entries)
     const RouteRec *rrec;      // per route position
     const uint64_t *hkey;      // lane-change draw key: scenario seed ^ scenario-local id * C1
+    uint32_t hkey_from_id;     // 1: one scenario, whose key is m.seed ^ id * C1 (no load needed)
     uint32_t *dep_act, *arr;
     uint8_t *status;
     // departure queues, one per origin edge (queue records in queue order)

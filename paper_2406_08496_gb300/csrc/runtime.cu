@@ -771,6 +771,7 @@ int load_demand_impl(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, cons
     TRY(upload(c, dorec, orec.data(), norg * sizeof(EdgeRec)));
     TRY(upload(c, c->org_hd0, hd0.data(), norg * sizeof(QRec)));
     d.hkey = dhkey;
+    d.hkey_from_id = scen ? 0u : 1u;
     d.route = droute;
     d.roff = droff;
     d.rrec = drrec;

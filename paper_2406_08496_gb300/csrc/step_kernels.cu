@@ -177,7 +177,8 @@ __device__ __forceinline__ uint32_t warp_append(uint32_t *counter) {
 // stage go to the global list directly.
 constexpr uint32_t kStageCross = 128, kStageIntend = 128, kStageDep = 64;
 
-static_assert(sizeof(CrossRec) == 64 && sizeof(IntendRec) == 32 && sizeof(DepRec) == 64, "record sizes");
+static_assert(sizeof(CrossRec) == 64 && sizeof(IntendRec) == 32 && sizeof(DepRec) == 64 && sizeof(RouteRec) == 8,
+              "record sizes");
 
 struct P1Sinks {
     CrossRec *cr;
@@ -429,7 +430,9 @@ __device__ __forceinline__ bool p1_slot(const Dev &d, const StepView &w, const P
     // hkey[id] = seed ^ local_id * C1 was formed at load time (local_id =
     // the vehicle's id within its scenario, so a scenario draws the same
     // numbers alone or inside a batch)
-    const uint64_t hk = may_draw ? d.hkey[id] : 0ull;
+    const uint64_t hk = !may_draw ? 0ull
+                        : d.hkey_from_id ? d.m.seed ^ ((uint64_t)id * 0x9E3779B97F4A7C15ull)
+                                         : d.hkey[id];
     uint32_t hi = c + (uint32_t)fminf(reach, 65535.0f) + 2u;
     if (hi > len - 1) hi = len - 1;
     const uint32_t cf = first_occupied_wide(Mc + base, c + 1, hi);
