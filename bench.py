@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="regional",
                     choices=["regional", "grid", "large", "batch64", "assignment", "surrogate"])
+    ap.add_argument("--iterations", type=int, default=40,
+                    help="assignment workload: MSA iterations at most per arm (each stops at the 1%% gap)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--day-profile", type=int, default=0, metavar="STEPS",
@@ -249,13 +251,13 @@ def batch_arm(args, L, torch, rank, world, local):
 def assignment_arm(args, L, torch):
     """Plain and surrogate-assisted MSA on the reduced regional case (27k
     nodes, 340k trips, same trips per node as the 2.82M-trip day), each run
-    until the relative gap reaches 1% or for --steps iterations; every gap
+    until the relative gap reaches 1% or for --iterations iterations; every gap
     measured by a full simulation.  value = the surrogate arm's wall time to
     the 1% gap (null if not reached); both arms' times to 2%, 1.5% and 1%."""
     import workloads as W
     from paper_2406_08496_gb300.assignment import msa
     net, dem = W.assignment_case(scale="small")
-    iters = max(args.steps, 4)
+    iters = args.iterations
     res = {}
     for mode in ("plain", "surrogate"):
         r = msa(net, dem, mode, iterations=iters, target_gap=0.01)

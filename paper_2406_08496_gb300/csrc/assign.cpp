@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "../../include/lpsim_assign.h"
+#include "host_par.h"
 
 int lpsim_fail(int code, const std::string &msg);
 
@@ -51,28 +52,8 @@ struct lpsim_assign {
 
 namespace {
 
-// f(first, last) over fixed-size pieces of [0, n), spread over the host's
-// threads; piece boundaries do not depend on the thread count, so anything
-// reduced per piece and then added in piece order is reproducible.
-constexpr uint64_t kPiece = 16384;
-
-template <class F>
-void parallel_pieces(uint64_t n, F &&f) {
-    const uint64_t np = (n + kPiece - 1) / kPiece;
-    const uint64_t hw = std::max(1u, std::thread::hardware_concurrency());
-    const unsigned nt = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(np, hw));
-    if (nt <= 1) {
-        for (uint64_t p = 0; p < np; p++) f(p * kPiece, std::min(n, (p + 1) * kPiece), p);
-        return;
-    }
-    std::atomic<uint64_t> next{0};
-    std::vector<std::thread> th;
-    for (unsigned t = 0; t < nt; t++)
-        th.emplace_back([&] {
-            for (uint64_t p; (p = next.fetch_add(1)) < np;) f(p * kPiece, std::min(n, (p + 1) * kPiece), p);
-        });
-    for (auto &x : th) x.join();
-}
+using lpsim::kPiece;
+using lpsim::parallel_pieces;
 
 struct TD {
     const lpsim_assign *a;

@@ -5,7 +5,7 @@
 // slots), the trips in vehicle-id order (departure rank), the departure
 // queues of the origin edges, two sets of vehicle slots (the compaction
 // writes one set from the other), the link statistics and a few counters.
-// Steps run as CUDA-graph chunks of `chunk_steps` steps (three step kernels
+// Steps run as CUDA-graph chunks of `chunk_steps` steps (two step kernels
 // per step plus a compaction, optionally a radix sort, every `sort_period`
 // steps); steps that do not fill an aligned chunk are launched one by one.
 #include <algorithm>
@@ -20,6 +20,7 @@
 
 #include "../../include/lpsim.h"
 #include "ctx.h"
+#include "host_par.h"
 #include "lpsim_dev.cuh"
 
 using namespace lpsim;
@@ -648,40 +649,85 @@ int load_demand_impl(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, cons
     if (!depart_step || !route_off || !route_edges) return fail(LPSIM_E_INVALID_ARG, "trip array is NULL");
     if (n >= 0xFFFFFFF0ull) return fail(LPSIM_E_INVALID_ARG, "too many trips");
     if (route_off[0] != 0) return fail(LPSIM_E_INVALID_ARG, "route_off[0] must be 0");
-    for (uint64_t j = 0; j < n; j++)
-        if (route_off[j + 1] <= route_off[j])
-            return fail(LPSIM_E_INVALID_ARG, "trip " + std::to_string(j) + ": empty route or route_off not increasing");
+    // Checks, spread over the host's threads; the lowest failing trip is
+    // reported (offsets first, then edges, as a sequential pass would).
+    {
+        std::mutex mu;
+        uint64_t bad = n;
+        parallel_pieces(n, [&](uint64_t j0, uint64_t j1, uint64_t) {
+            for (uint64_t j = j0; j < j1; j++)
+                if (route_off[j + 1] <= route_off[j]) {
+                    std::lock_guard<std::mutex> g(mu);
+                    bad = std::min(bad, j);
+                    return;
+                }
+        });
+        if (bad < n)
+            return fail(LPSIM_E_INVALID_ARG, "trip " + std::to_string(bad) + ": empty route or route_off not increasing");
+    }
     const uint64_t total = route_off[n];
     if (total >= 0xFFFFFFF0ull) return fail(LPSIM_E_INVALID_ARG, "total route length must stay below 2^32");
-    for (uint64_t j = 0; j < n; j++) {
-        for (uint64_t q = route_off[j]; q < route_off[j + 1]; q++) {
-            uint32_t e = route_edges[q];
-            if (e >= c->n_edges) return fail(LPSIM_E_INVALID_ARG, "trip " + std::to_string(j) + ": edge id out of range");
-            if (q > route_off[j] && c->dst[route_edges[q - 1]] != c->src[e])
-                return fail(LPSIM_E_INVALID_ARG, "trip " + std::to_string(j) + ": route edges are not contiguous");
-        }
+    {
+        std::mutex mu;
+        uint64_t bad = n;
+        int kind = 0;
+        const uint32_t *src = c->src.data(), *dst = c->dst.data();
+        const uint32_t ne = c->n_edges;
+        parallel_pieces(n, [&](uint64_t j0, uint64_t j1, uint64_t) {
+            for (uint64_t j = j0; j < j1; j++) {
+                int k = 0;
+                for (uint64_t q = route_off[j]; q < route_off[j + 1] && !k; q++) {
+                    const uint32_t e = route_edges[q];
+                    if (e >= ne) k = 1;
+                    else if (q > route_off[j] && dst[route_edges[q - 1]] != src[e]) k = 2;
+                }
+                if (k) {
+                    std::lock_guard<std::mutex> g(mu);
+                    if (j < bad) {
+                        bad = j;
+                        kind = k;
+                    }
+                    return;
+                }
+            }
+        });
+        if (bad < n)
+            return fail(LPSIM_E_INVALID_ARG, "trip " + std::to_string(bad) + (kind == 1 ? ": edge id out of range"
+                                                                                  : ": route edges are not contiguous"));
     }
-    // vehicle ids: stable sort by departure step
+    // vehicle ids: stable sort by departure step (a counting sort when the
+    // steps span less than 2^24)
     std::vector<uint32_t> order(n);
-    std::iota(order.begin(), order.end(), 0u);
-    std::stable_sort(order.begin(), order.end(),
-                     [&](uint32_t a, uint32_t b) { return depart_step[a] < depart_step[b]; });
+    const uint32_t max_dep = *std::max_element(depart_step, depart_step + n);
+    if (max_dep < (1u << 24)) {
+        std::vector<uint64_t> pos((size_t)max_dep + 2, 0);
+        for (uint64_t j = 0; j < n; j++) pos[(size_t)depart_step[j] + 1]++;
+        for (size_t t = 1; t < pos.size(); t++) pos[t] += pos[t - 1];
+        for (uint64_t j = 0; j < n; j++) order[pos[depart_step[j]]++] = (uint32_t)j;
+    } else {
+        std::iota(order.begin(), order.end(), 0u);
+        std::stable_sort(order.begin(), order.end(),
+                         [&](uint32_t a, uint32_t b) { return depart_step[a] < depart_step[b]; });
+    }
     std::vector<uint32_t> dep(n), roff(n + 1), route(total ? total : 1);
-    std::vector<uint64_t> hkey(n);
+    // lane-change draw keys: seed ^ (id within the scenario) * C1; a single
+    // scenario's key follows from the id on the device
+    std::vector<uint64_t> hkey(scen ? n : 0);
     std::vector<uint64_t> local(std::max<uint32_t>(n_scen, 1u), 0);
     roff[0] = 0;
     for (uint64_t id = 0; id < n; id++) {
-        uint32_t j = order[id];
-        // lane-change draw key: seed ^ (id within the scenario) * C1
-        const uint32_t sc = scen ? scen[j] : 0u;
-        const uint64_t seed = seeds ? seeds[sc] : c->p.seed;
-        hkey[id] = seed ^ (local[sc]++ * 0x9E3779B97F4A7C15ull);
+        const uint32_t j = order[id];
+        if (scen) hkey[id] = (seeds ? seeds[scen[j]] : c->p.seed) ^ (local[scen[j]]++ * 0x9E3779B97F4A7C15ull);
         dep[id] = depart_step[j];
-        uint64_t L = route_off[j + 1] - route_off[j];
-        std::memcpy(route.data() + roff[id], route_edges + route_off[j], L * 4);
-        roff[id + 1] = (uint32_t)(roff[id] + L);
+        roff[id + 1] = (uint32_t)(roff[id] + (route_off[j + 1] - route_off[j]));
         if (out_vid) out_vid[j] = (uint32_t)id;
     }
+    parallel_pieces(n, [&](uint64_t i0, uint64_t i1, uint64_t) {
+        for (uint64_t id = i0; id < i1; id++) {
+            const uint32_t j = order[id];
+            std::memcpy(route.data() + roff[id], route_edges + route_off[j], (size_t)(roff[id + 1] - roff[id]) * 4);
+        }
+    });
     c->dep_sorted = dep;  // nondecreasing: ids are ranks by departure step
     // departure queues: ids grouped by first edge, ascending within a group
     std::vector<uint32_t> cnt(c->n_edges + 1, 0);
@@ -719,7 +765,8 @@ int load_demand_impl(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, cons
     QRec *dqrec;
     EdgeRec *dorec;
     RouteRec *drrec;
-    TRY(dnew(c, dhkey, n));
+    dhkey = nullptr;
+    if (scen) TRY(dnew(c, dhkey, n));
     TRY(dnew(c, droute, route.size()));
     TRY(dnew(c, droff, n + 1));
     TRY(dnew(c, drrec, route.size()));
@@ -761,7 +808,7 @@ int load_demand_impl(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, cons
         TRY(dnew(c, c->w.key[i], cap));
         TRY(dnew(c, c->w.perm[i], cap));
     }
-    TRY(upload(c, dhkey, hkey.data(), n * 8));
+    if (scen) TRY(upload(c, dhkey, hkey.data(), n * 8));
     TRY(upload(c, droute, route.data(), route.size() * 4));
     TRY(upload(c, droff, roff.data(), (n + 1) * 4));
     TRY(upload(c, oe, org_edge.data(), norg * 4ull));
