@@ -70,8 +70,12 @@ struct TD {
 };
 
 // earliest-arrival Dijkstra from `s` departing at t0; pred = edge into node
+// Time-dependent Dijkstra from s departing at t0.  want[v] == stamp marks the
+// n_want nodes the caller needs; the search stops once all of them are
+// settled (their arrival times and predecessor chains are final then: a
+// settled node's predecessor was settled before it).
 void td_dijkstra(const TD &td, uint32_t s, double t0, std::vector<double> &arr, std::vector<uint32_t> &pred,
-                 std::vector<uint8_t> &done) {
+                 std::vector<uint8_t> &done, const std::vector<uint32_t> &want, uint32_t stamp, uint32_t n_want) {
     const lpsim_assign *a = td.a;
     std::fill(arr.begin(), arr.end(), INFINITY);
     std::fill(pred.begin(), pred.end(), UINT32_MAX);
@@ -85,6 +89,7 @@ void td_dijkstra(const TD &td, uint32_t s, double t0, std::vector<double> &arr, 
         pq.pop();
         if (done[u]) continue;
         done[u] = 1;
+        if (want[u] == stamp && --n_want == 0) break;
         for (uint32_t j = a->out_off[u]; j < a->out_off[u + 1]; j++) {
             const uint32_t e = a->out_edge[j], v = a->dst[e];
             if (done[v]) continue;
@@ -176,6 +181,7 @@ int lpsim_assign_shortest_paths(lpsim_assign *a, const float *tt, uint32_t n_bin
         std::vector<double> arr(a->n_nodes);
         std::vector<uint32_t> pred(a->n_nodes);
         std::vector<uint8_t> done(a->n_nodes);
+        std::vector<uint32_t> want(a->n_nodes, 0);
         std::vector<uint32_t> tmp;
         for (;;) {
             const uint64_t g = next.fetch_add(1);
@@ -185,7 +191,17 @@ int lpsim_assign_shortest_paths(lpsim_assign *a, const float *tt, uint32_t n_bin
             const uint32_t period = a->dep[j0] / period_steps;
             // tree from the middle of the departure period
             const double t0 = ((double)period + 0.5) * period_steps * a->dt;
-            td_dijkstra(td, s, t0, arr, pred, done);
+            // the group's destinations, marked with a stamp unique to the group
+            const uint32_t stamp = (uint32_t)g + 1u;
+            uint32_t n_want = 0;
+            for (uint64_t i = gstart[g]; i < gstart[g + 1]; i++) {
+                const uint32_t d = a->dest[order[i]];
+                if (want[d] != stamp) {
+                    want[d] = stamp;
+                    n_want++;
+                }
+            }
+            td_dijkstra(td, s, t0, arr, pred, done, want, stamp, n_want);
             for (uint64_t i = gstart[g]; i < gstart[g + 1]; i++) {
                 const uint64_t j = order[i];
                 const uint32_t d = a->dest[j];
