@@ -179,6 +179,20 @@ def ncu_traffic():
     return d
 
 
+def whole_job(ms: float, units: float, dist, device: str):
+    """The whole job over N ranks: the longest rank's timed span (max) and
+    the units every rank processed (sum); value = units / span.  One rank
+    (dist None) returns its own pair."""
+    if dist is None:
+        return float(ms), float(units)
+    import torch
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    v = torch.tensor([float(units)], device=device, dtype=torch.float64)
+    dist.all_reduce(v, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(v.item())
+
+
 def reference_arm(args, rank, world):
     if rank != 0:
         return
@@ -204,7 +218,7 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def batch_arm(args, L, torch, rank, world, local):
+def batch_arm(args, L, torch, rank, world, local, dist=None):
     """64 independent scenarios of uneven size (grid and planar networks of
     1k-50k nodes, 10k-400k trips, each with its own seed) advanced by one
     launch of each step kernel per step; the launch configuration comes from
@@ -227,16 +241,23 @@ def batch_arm(args, L, torch, rank, world, local):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     vs = 0
     launches0 = sim.counters()["launches"]
-    with ClockSampler(local) as clk:
+    def barrier():
         torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+
+    with ClockSampler(local) as clk:
+        barrier()
         ev0.record(stream)
         for _ in range(args.steps):
             sim.reset()
             r = sim.run(horizon)
             vs += r["veh_steps"]
         ev1.record(stream)
-        torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
+        barrier()
+    ms, vs = whole_job(ev0.elapsed_time(ev1), vs, dist, "cuda")
+    if rank != 0:
+        return
     trips = int(sum(len(d["depart_step"]) for d in dems))
     out = {"metric": "veh-steps/s", "value": vs / (ms / 1e3), "unit": "veh-steps/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -332,7 +353,10 @@ def main():
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     if args.workload == "batch64":
-        batch_arm(args, L, torch, rank, world, local)
+        batch_arm(args, L, torch, rank, world, local, dist)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
         return
     if args.workload == "assignment":
         assignment_arm(args, L, torch)
@@ -405,15 +429,7 @@ def main():
         barrier()
     ms = ev0.elapsed_time(ev1)
     launches = sim.counters()["launches"] - launches0
-    t_max = ms
-    vs_all = veh_steps
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        v = torch.tensor([veh_steps], device="cuda", dtype=torch.float64)
-        dist.all_reduce(v, op=dist.ReduceOp.SUM)
-        vs_all = float(v.item())
+    t_max, vs_all = whole_job(ms, veh_steps, dist, "cuda")
     value = vs_all / (t_max / 1e3)
 
     out = None
