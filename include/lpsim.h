@@ -165,7 +165,12 @@ int lpsim_load_network(lpsim_ctx **out, const lpsim_network *net, const lpsim_pa
  * route length must stay below 2^32.  Vehicle ids are the ranks of a stable
  * sort of the trips by depart_step (the paper sorts by departure time,
  * Sec. 4, Table 6); out_vehicle_id (nullable, n_trips entries) receives trip
- * j's id.  Resets the step counter to 0.  Once per context. */
+ * j's id.  Resets the step counter to 0.  Once per context.  Errors:
+ * LPSIM_E_INVALID_ARG when route_off is not increasing from 0 (an empty
+ * route), an edge id is out of range or consecutive route edges do not
+ * meet; the message names the lowest failing trip, offset errors before edge
+ * errors (the checks run on the host's threads); LPSIM_E_STATE on a second
+ * call. */
 int lpsim_load_demand(lpsim_ctx *ctx, uint64_t n_trips, const uint32_t *depart_step, const uint64_t *route_off,
                       const uint32_t *route_edges, uint32_t *out_vehicle_id);
 
