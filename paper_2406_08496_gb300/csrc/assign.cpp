@@ -55,38 +55,57 @@ namespace {
 using lpsim::kPiece;
 using lpsim::parallel_pieces;
 
+// Time-dependent link costs: the time to traverse edge e when entering it at
+// time t is the table value of e in the bin holding t (first / last bin
+// outside the table).  The table is kept bin-major (n_bins x n_edges): a
+// search or a route walk stays within a few bins, so the values it reads sit
+// in a few contiguous rows that stay in the host caches, where the
+// caller's edge-major layout put every edge's value on its own cache line.
 struct TD {
     const lpsim_assign *a;
-    const float *tt;   // n_edges x n_bins, seconds
+    std::vector<float> tbm;  // n_bins x n_edges, seconds
     uint32_t n_bins;
     float bin_s;
+
+    TD(const lpsim_assign *a_, const float *tt, uint32_t n_bins_, float bin_s_)
+        : a(a_), tbm((size_t)n_bins_ * a_->n_edges), n_bins(n_bins_), bin_s(bin_s_) {
+        const uint32_t ne = a->n_edges;
+        parallel_pieces(ne, [&](uint64_t e0, uint64_t e1, uint64_t) {
+            for (uint64_t e = e0; e < e1; e++)
+                for (uint32_t b = 0; b < n_bins; b++) tbm[(size_t)b * ne + e] = tt[e * n_bins + b];
+        });
+    }
 
     float cost(uint32_t e, double t) const {
         int64_t b = (int64_t)std::floor(t / bin_s);
         if (b < 0) b = 0;
         if (b >= (int64_t)n_bins) b = n_bins - 1;
-        return tt[(size_t)e * n_bins + b];
+        return tbm[(size_t)b * a->n_edges + e];
     }
 };
 
-// earliest-arrival Dijkstra from `s` departing at t0; pred = edge into node
 // Time-dependent Dijkstra from s departing at t0.  want[v] == stamp marks the
 // n_want nodes the caller needs; the search stops once all of them are
 // settled (their arrival times and predecessor chains are final then: a
 // settled node's predecessor was settled before it).
+using HeapItem = std::pair<double, uint32_t>;
+
 void td_dijkstra(const TD &td, uint32_t s, double t0, std::vector<double> &arr, std::vector<uint32_t> &pred,
-                 std::vector<uint8_t> &done, const std::vector<uint32_t> &want, uint32_t stamp, uint32_t n_want) {
+                 std::vector<uint8_t> &done, const std::vector<uint32_t> &want, uint32_t stamp, uint32_t n_want,
+                 std::vector<HeapItem> &heap) {
     const lpsim_assign *a = td.a;
     std::fill(arr.begin(), arr.end(), INFINITY);
     std::fill(pred.begin(), pred.end(), UINT32_MAX);
     std::fill(done.begin(), done.end(), 0);
-    using Item = std::pair<double, uint32_t>;
-    std::priority_queue<Item, std::vector<Item>, std::greater<Item>> pq;
+    // a min-heap on the caller's storage (kept between searches)
+    const std::greater<HeapItem> later;
+    heap.clear();
     arr[s] = t0;
-    pq.push({t0, s});
-    while (!pq.empty()) {
-        auto [t, u] = pq.top();
-        pq.pop();
+    heap.push_back({t0, s});
+    while (!heap.empty()) {
+        std::pop_heap(heap.begin(), heap.end(), later);
+        const auto [t, u] = heap.back();
+        heap.pop_back();
         if (done[u]) continue;
         done[u] = 1;
         if (want[u] == stamp && --n_want == 0) break;
@@ -97,7 +116,8 @@ void td_dijkstra(const TD &td, uint32_t s, double t0, std::vector<double> &arr, 
             if (nt < arr[v] || (nt == arr[v] && e < pred[v])) {
                 arr[v] = nt;
                 pred[v] = e;
-                pq.push({nt, v});
+                heap.push_back({nt, v});
+                std::push_heap(heap.begin(), heap.end(), later);
             }
         }
     }
@@ -161,7 +181,7 @@ int lpsim_assign_shortest_paths(lpsim_assign *a, const float *tt, uint32_t n_bin
                                 uint32_t period_steps, uint32_t n_threads, float *t_sp) {
     if (!a || !tt || n_bins == 0 || bin_steps == 0 || period_steps == 0)
         return fail(LPSIM_E_INVALID_ARG, "bad argument");
-    TD td{a, tt, n_bins, (float)bin_steps * a->dt};
+    const TD td(a, tt, n_bins, (float)bin_steps * a->dt);
     // group trips by (origin, departure period)
     std::vector<uint64_t> order(a->n);
     std::iota(order.begin(), order.end(), 0);
@@ -182,6 +202,7 @@ int lpsim_assign_shortest_paths(lpsim_assign *a, const float *tt, uint32_t n_bin
         std::vector<uint32_t> pred(a->n_nodes);
         std::vector<uint8_t> done(a->n_nodes);
         std::vector<uint32_t> want(a->n_nodes, 0);
+        std::vector<HeapItem> heap;
         std::vector<uint32_t> tmp;
         for (;;) {
             const uint64_t g = next.fetch_add(1);
@@ -201,7 +222,7 @@ int lpsim_assign_shortest_paths(lpsim_assign *a, const float *tt, uint32_t n_bin
                     n_want++;
                 }
             }
-            td_dijkstra(td, s, t0, arr, pred, done, want, stamp, n_want);
+            td_dijkstra(td, s, t0, arr, pred, done, want, stamp, n_want, heap);
             for (uint64_t i = gstart[g]; i < gstart[g + 1]; i++) {
                 const uint64_t j = order[i];
                 const uint32_t d = a->dest[j];
@@ -282,7 +303,7 @@ int lpsim_assign_reroute(lpsim_assign *a, double fraction, uint32_t iteration, u
 
 int lpsim_assign_route_excess(lpsim_assign *a, const float *tt, uint32_t n_bins, uint32_t bin_steps) {
     if (!a || !tt || n_bins == 0 || bin_steps == 0) return fail(LPSIM_E_INVALID_ARG, "bad argument");
-    TD td{a, tt, n_bins, (float)bin_steps * a->dt};
+    const TD td(a, tt, n_bins, (float)bin_steps * a->dt);
     parallel_pieces(a->n, [&](uint64_t j0, uint64_t j1, uint64_t) {
         for (uint64_t j = j0; j < j1; j++) {
             const double t0 = (double)a->dep[j] * a->dt;
@@ -337,7 +358,7 @@ int lpsim_assign_get_routes(const lpsim_assign *a, uint64_t *route_off, uint32_t
 
 int lpsim_assign_load(const lpsim_assign *a, const float *tt, uint32_t n_bins, uint32_t bin_steps, uint32_t *inflow) {
     if (!a || !tt || !inflow || n_bins == 0 || bin_steps == 0) return fail(LPSIM_E_INVALID_ARG, "bad argument");
-    TD td{a, tt, n_bins, (float)bin_steps * a->dt};
+    const TD td(a, tt, n_bins, (float)bin_steps * a->dt);
     std::memset(inflow, 0, (size_t)a->n_edges * n_bins * 4);
     parallel_pieces(a->n, [&](uint64_t j0, uint64_t j1, uint64_t) {
         for (uint64_t j = j0; j < j1; j++) {
