@@ -713,15 +713,27 @@ int load_demand_impl(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, cons
     // lane-change draw keys: seed ^ (id within the scenario) * C1; a single
     // scenario's key follows from the id on the device
     std::vector<uint64_t> hkey(scen ? n : 0);
-    std::vector<uint64_t> local(std::max<uint32_t>(n_scen, 1u), 0);
-    roff[0] = 0;
-    for (uint64_t id = 0; id < n; id++) {
-        const uint32_t j = order[id];
-        if (scen) hkey[id] = (seeds ? seeds[scen[j]] : c->p.seed) ^ (local[scen[j]]++ * 0x9E3779B97F4A7C15ull);
-        dep[id] = depart_step[j];
-        roff[id + 1] = (uint32_t)(roff[id] + (route_off[j + 1] - route_off[j]));
-        if (out_vid) out_vid[j] = (uint32_t)id;
+    if (scen) {
+        std::vector<uint64_t> local(std::max<uint32_t>(n_scen, 1u), 0);
+        for (uint64_t id = 0; id < n; id++) {
+            const uint32_t j = order[id];
+            hkey[id] = (seeds ? seeds[scen[j]] : c->p.seed) ^ (local[scen[j]]++ * 0x9E3779B97F4A7C15ull);
+        }
     }
+    // per id (gathers spread over the host's threads): departure step, route
+    // length, first edge; the route offsets are their prefix sum
+    std::vector<uint32_t> first(n);
+    parallel_pieces(n, [&](uint64_t i0, uint64_t i1, uint64_t) {
+        for (uint64_t id = i0; id < i1; id++) {
+            const uint32_t j = order[id];
+            dep[id] = depart_step[j];
+            roff[id + 1] = (uint32_t)(route_off[j + 1] - route_off[j]);
+            first[id] = route_edges[route_off[j]];
+            if (out_vid) out_vid[j] = (uint32_t)id;
+        }
+    });
+    roff[0] = 0;
+    for (uint64_t id = 0; id < n; id++) roff[id + 1] += roff[id];
     parallel_pieces(n, [&](uint64_t i0, uint64_t i1, uint64_t) {
         for (uint64_t id = i0; id < i1; id++) {
             const uint32_t j = order[id];
@@ -731,7 +743,7 @@ int load_demand_impl(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, cons
     c->dep_sorted = dep;  // nondecreasing: ids are ranks by departure step
     // departure queues: ids grouped by first edge, ascending within a group
     std::vector<uint32_t> cnt(c->n_edges + 1, 0);
-    for (uint64_t id = 0; id < n; id++) cnt[route[roff[id]] + 1]++;
+    for (uint64_t id = 0; id < n; id++) cnt[first[id] + 1]++;
     std::vector<uint32_t> org_edge, org_qoff, org_qend;
     for (uint32_t e = 0; e < c->n_edges; e++) {
         if (cnt[e + 1]) {
@@ -744,13 +756,15 @@ int load_demand_impl(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, cons
     std::vector<uint32_t> qid(n);
     {
         std::vector<uint32_t> fill(cnt.begin(), cnt.end() - 1);
-        for (uint64_t id = 0; id < n; id++) qid[fill[route[roff[id]]]++] = (uint32_t)id;
+        for (uint64_t id = 0; id < n; id++) qid[fill[first[id]]++] = (uint32_t)id;
     }
     Dev &d = c->d;
     const uint32_t norg = (uint32_t)org_edge.size();
     // queue records (vehicle, departure step, route span) in queue order
     std::vector<QRec> qrec(n), hd0(norg);
-    for (uint64_t q = 0; q < n; q++) qrec[q] = QRec{qid[q], dep[qid[q]], roff[qid[q]], roff[qid[q] + 1]};
+    parallel_pieces(n, [&](uint64_t q0, uint64_t q1, uint64_t) {
+        for (uint64_t q = q0; q < q1; q++) qrec[q] = QRec{qid[q], dep[qid[q]], roff[qid[q]], roff[qid[q] + 1]};
+    });
     std::vector<EdgeRec> orec(norg);
     {
         std::vector<EdgeRec> all(c->n_edges);
