@@ -151,34 +151,6 @@ class Assignment:
             pass
 
 
-class TrainingPool:
-    """The surrogate's training set, grown in place: each simulation's rows
-    (those with a measured link time) are appended in order into arrays whose
-    capacity doubles, so every training call gets a contiguous view of all
-    rows so far without re-joining the earlier simulations' rows."""
-
-    def __init__(self, n_features: int):
-        self.X = np.empty((0, n_features), np.float32)
-        self.t = np.empty(0, np.float32)
-        self.n = 0
-
-    def append(self, keep: np.ndarray, X: np.ndarray, t: np.ndarray) -> None:
-        k = int(np.count_nonzero(keep))
-        if self.n + k > len(self.t):
-            cap = max(2 * len(self.t), self.n + k)
-            X2 = np.empty((cap, self.X.shape[1]), np.float32)
-            t2 = np.empty(cap, np.float32)
-            X2[:self.n] = self.X[:self.n]
-            t2[:self.n] = self.t[:self.n]
-            self.X, self.t = X2, t2
-        np.compress(keep, X, axis=0, out=self.X[self.n:self.n + k])
-        np.compress(keep, t, out=self.t[self.n:self.n + k])
-        self.n += k
-
-    def view(self):
-        return self.X[:self.n], self.t[:self.n]
-
-
 def msa(net: dict, dem: dict, mode: str = "plain", iterations: int = 10, fraction: float = 0.1,
         target_gap: float = 0.01, sim_params: dict | None = None, bin_steps: int = 1800, n_bins: int = 96,
         period_steps: int = 3600, max_steps: int = 300_000, surrogate_steps: int = 400, surrogate_batch: int = 8192,
@@ -207,7 +179,7 @@ def msa(net: dict, dem: dict, mode: str = "plain", iterations: int = 10, fractio
     params.update(sim_params or {})
     A = Assignment(net, dem, dt=0.5, seed=seed)
     mlp = Surrogate(n_features=N_FEATURES, batch=surrogate_batch, seed=seed) if mode == "surrogate" else None
-    pool = TrainingPool(N_FEATURES)
+    train_X, train_t = [], []
     hist = []
     t_start = time.perf_counter()
     t_hit = None
@@ -244,8 +216,9 @@ def msa(net: dict, dem: dict, mode: str = "plain", iterations: int = 10, fractio
                 ref_in = ls["inflow"] if in_last is None else in_last
                 X = A.features(ls["inflow"], ls["occ"], ref_lr, ref_in)
                 ok = (ls["tt_cnt"].reshape(-1) >= 2) & np.isfinite(logratio.reshape(-1))
-                pool.append(ok, X, logratio.reshape(-1))
-                Xa, ta = pool.view()
+                train_X.append(X[ok])
+                train_t.append(logratio.reshape(-1)[ok])
+                Xa, ta = np.concatenate(train_X), np.concatenate(train_t)
                 t1 = time.perf_counter()
                 losses = mlp.train(Xa, ta, steps=surrogate_steps, lr=1e-3, seed=seed + it)
                 rec["train_s"] = time.perf_counter() - t1

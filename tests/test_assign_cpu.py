@@ -195,22 +195,3 @@ def test_worst_first_reroute(A):
     arr = np.full(n, 0xFFFFFFFF, np.uint32)  # nobody arrived: no excess, nothing moves
     a.gap(dep_act, arr)
     assert a.reroute_worst(0.5) == 0
-
-
-def test_training_pool_keeps_rows_in_order():
-    """The surrogate's training pool holds exactly the concatenation of the
-    kept rows of every append, in order, across capacity growth."""
-    from paper_2406_08496_gb300.assignment import TrainingPool
-    rng = np.random.default_rng(5)
-    pool = TrainingPool(3)
-    ref_X, ref_t = [], []
-    for size in (10, 1, 40, 0, 25, 300):
-        X = rng.standard_normal((size, 3)).astype(np.float32)
-        t = rng.standard_normal(size).astype(np.float32)
-        keep = rng.random(size) < 0.6
-        pool.append(keep, X, t)
-        ref_X.append(X[keep])
-        ref_t.append(t[keep])
-        Xa, ta = pool.view()
-        assert np.array_equal(Xa, np.concatenate(ref_X)) and np.array_equal(ta, np.concatenate(ref_t))
-        assert Xa.flags["C_CONTIGUOUS"] and ta.flags["C_CONTIGUOUS"]
