@@ -459,14 +459,20 @@ def main():
                     "traffic_source": ("profiles/step_p1_regional_peak.json: " + tr["captured_launch"]) if tr else
                     "stale or missing ncu summary"}
         # the same at the morning peak (the hour the roofline target is about):
-        # one graph chunk of kernel-timed steps from 08:00
+        # the graph chunk of kernel-timed steps that holds 08:00
         peak_window = None
         if args.workload == "regional":
+            cw = int(L.DEFAULT_PARAMS["chunk_steps"])
+            kw0 = (8 * 7200) // cw * cw
+
+            def clock(k):
+                sec = int(k * 0.5)
+                return f"{sec // 3600:02d}:{sec // 60 % 60:02d}:{sec % 60:02d}"
             sim.reset()
-            sim.step(8 * 7200)
+            sim.step(kw0)
             c0 = sim.counters()
             sim.set_kernel_timing(True)
-            sim.step(768)
+            sim.step(cw)
             kw = sim.kernel_times()
             sim.set_kernel_timing(False)
             vs_w = sim.counters()["veh_steps"] - c0["veh_steps"]
@@ -475,7 +481,8 @@ def main():
                 ach = BYTES_PER_VEH_STEP_P1 * vs_w / (pw["ms"] / 1e3) / 1e9
                 per_launch_s = pw["ms"] / 1e3 / pw["launches"]
                 dram = tr["dram_bytes_per_launch"] if tr else None
-                peak_window = {"window": "steps 57,600-58,367 (08:00-08:06:24)", "achieved": ach,
+                peak_window = {"window": f"steps {kw0:,}-{kw0 + cw - 1:,} ({clock(kw0)}-{clock(kw0 + cw)})",
+                               "achieved": ach,
                                "frac": ach / peak, "unit": "GB/s",
                                "avg_launch_us": per_launch_s * 1e6, "avg_veh_per_launch": vs_w / pw["launches"],
                                "dram_gbs": dram / per_launch_s / 1e9 if dram else None,

@@ -81,10 +81,10 @@ typedef struct lpsim_params {
     uint64_t seed;     /* seed of the lane-change draws (SplitMix64 of seed, vehicle id, step) */
     uint32_t bin_steps;   /* steps per link-statistics bin (0 = no binned statistics) */
     uint32_t n_bins;      /* bins kept per edge */
-    uint32_t sort_period; /* steps between re-sorts of the active vehicles by lane-map cell (0 = 128, at most 256) */
+    uint32_t sort_period; /* steps between re-sorts of the active vehicles by lane-map cell (0 = 256, at most 256) */
     uint32_t block_size;  /* threads per block of the step kernels: 128, 256, 512 or 0 (= 256) */
     uint32_t blocks_per_sm; /* resident 256-thread blocks per SM the step grids are sized for (0 = 4) */
-    uint32_t chunk_steps; /* steps captured in one CUDA graph launch (0 = 768); rounded up to a multiple
+    uint32_t chunk_steps; /* steps captured in one CUDA graph launch (0 = 1536); rounded up to a multiple
                              of 2 sort periods and of 3 */
     uint32_t gridlock_steps; /* lpsim_run fails with LPSIM_E_GRIDLOCK after this many steps with active
                                 vehicles and no departure, crossing or arrival (0 = never) */

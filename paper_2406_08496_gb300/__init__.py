@@ -22,8 +22,8 @@ __all__ = ["Simulation", "LpsimError", "DEFAULT_PARAMS", "build", "load_library"
 # workloads; IDM a, b, s0, T; lane-change horizon x0; critical-gap constants.
 DEFAULT_PARAMS = dict(dt=0.5, a=1.0, b=1.5, s0=2.0, T=1.5, x0=100.0, g_a=2.0, g_b=2.0,
                       alpha_i=1.0, alpha_a=1.0, alpha_b=1.0, eps_amp=0.0, seed=12345,
-                      bin_steps=1800, n_bins=0, sort_period=128, block_size=256, blocks_per_sm=4,
-                      chunk_steps=768, gridlock_steps=0, flags=0, light_trips=0)
+                      bin_steps=1800, n_bins=0, sort_period=256, block_size=256, blocks_per_sm=4,
+                      chunk_steps=1536, gridlock_steps=0, flags=0, light_trips=0)
 FLAG_NO_SORT = 1
 
 EXPORTED = ["lpsim_last_error", "lpsim_version", "lpsim_set_allocator", "lpsim_load_network",

@@ -486,10 +486,10 @@ int load_network_impl(lpsim_ctx **out, const lpsim_network *net, const lpsim_par
     c->map_bytes = cells + 16;
     c->canon_cells = canon;
     c->lane_slots = slots;
-    c->R = p->sort_period ? p->sort_period : 128;
+    c->R = p->sort_period ? p->sort_period : 256;
     uint32_t base = 2 * c->R;
     base = base % 3 == 0 ? base : base * 3;  // chunk = multiple of 2R and of 3 (lane-map rotation)
-    uint32_t want = p->chunk_steps ? p->chunk_steps : 768;
+    uint32_t want = p->chunk_steps ? p->chunk_steps : 1536;
     c->C = std::max(base, (want + base - 1) / base * base);
     c->block = p->block_size ? (int)p->block_size : 256;
     c->grid = c->n_sm * (int)(p->blocks_per_sm ? p->blocks_per_sm : 4) * 256 / c->block;
@@ -1170,7 +1170,7 @@ int lpsim_autotune(lpsim_ctx *c, uint32_t window_steps, lpsim_tune_result *out) 
     if (!c->loaded) return fail(LPSIM_E_STATE, "lpsim_load_demand has not been called");
     if (window_steps == 0) return fail(LPSIM_E_INVALID_ARG, "window_steps must be > 0");
     const uint32_t cur_cfg[4] = {(uint32_t)c->block, c->p.blocks_per_sm ? c->p.blocks_per_sm : 4u, c->R,
-                                 c->p.chunk_steps ? c->p.chunk_steps : 768u};
+                                 c->p.chunk_steps ? c->p.chunk_steps : 1536u};
     TRY(snapshot_impl(c));
     const bool timing = c->timing;
     c->timing = false;

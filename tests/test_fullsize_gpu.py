@@ -4,8 +4,8 @@ chunk; no debug flags).
 
 * A sample the oracle can finish: every trip of the 2.82M-trip day that
   departs in a five-minute window of the morning peak, simulated alone on the
-  full 224k-node network for 1,200 steps.  Every output is compared bit for
-  bit.
+  full 224k-node network for 1,536 steps (one graph chunk).  Every output is
+  compared bit for bit.
 * The whole day on the GPU, checked through properties that hold at any size:
   every trip departs no earlier than planned and arrives; each trip's travel
   time is at least its route length at the network's top speed; every edge
@@ -25,7 +25,7 @@ from simutil import assert_outputs_equal
 pytestmark = pytest.mark.gpu
 
 PEAK_WINDOW = (7 * 7200 + 3600, 7 * 7200 + 3600 + 600)  # departures 07:30-07:35 (dt = 0.5 s)
-WINDOW_STEPS = 1200
+WINDOW_STEPS = 1536  # one graph chunk of the default length
 DAY_STEPS = 172_800
 
 

@@ -158,9 +158,9 @@ def test_light_load_chunks_match_oracle(grid_day, flags):
     o.load_demand(sub)
     g = Simulation(net, dict(params, flags=flags))
     g.load_demand(sub)
-    for _ in range(4):
-        o.step(768)  # one graph chunk at the default chunk length
-        g.step(768)
+    for _ in range(2):
+        o.step(1536)  # one graph chunk at the default chunk length
+        g.step(1536)
         assert_state_equal(o.state(), g.state(), f"step {o.counters()['k']}")
     ro = o.run(20000)
     rg = g.run(20000)
@@ -210,9 +210,9 @@ def test_light_kernel_lists_beyond_its_stages():
     o.load_demand(dem)
     g = Simulation(net, dict(params, light_trips=10**9))
     g.load_demand(dem)
-    for _ in range(3):
-        o.step(768)
-        g.step(768)
+    for _ in range(2):
+        o.step(1536)  # one light-load chunk each
+        g.step(1536)
         assert_state_equal(o.state(), g.state(), f"step {o.counters()['k']}")
     ro = o.run(60000)
     rg = g.run(60000)
@@ -262,13 +262,13 @@ def test_kernel_timing_direct_and_graph_steps(grid_day):
     g.load_demand(dem)
     g.set_kernel_timing(True)
     g.step(5)      # direct steps (not at a chunk boundary afterwards)
-    g.step(763)    # direct steps up to the chunk boundary (default chunk: 768 steps)
-    g.step(1536)   # two graph chunks
+    g.step(1531)   # direct steps up to the chunk boundary (default chunk: 1,536 steps)
+    g.step(3072)   # two graph chunks
     kt = g.kernel_times()
     g.set_kernel_timing(False)
-    assert kt["step_p1"]["launches"] == 2304 and kt["step_p1"]["ms"] > 0
-    assert kt["step_p2"]["ms"] > 0 and kt["step_p2"]["launches"] == 2304
+    assert kt["step_p1"]["launches"] == 4608 and kt["step_p1"]["ms"] > 0
+    assert kt["step_p2"]["ms"] > 0 and kt["step_p2"]["launches"] == 4608
     ref = Simulation(net, {})
     ref.load_demand(dem)
-    ref.step(2304)
+    ref.step(4608)
     assert_state_equal(ref.state(), g.state(), "timing on vs off")
