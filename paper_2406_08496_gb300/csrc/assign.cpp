@@ -90,6 +90,46 @@ struct TD {
 // settled node's predecessor was settled before it).
 using HeapItem = std::pair<double, uint32_t>;
 
+// Min-heap of (arrival time, node) pairs with four children per node
+// (shallower than a binary heap: fewer levels to sift through per push and
+// pop), ordered like the pairs themselves; its storage is the caller's.
+struct Heap4 {
+    std::vector<HeapItem> &h;
+    bool empty() const { return h.empty(); }
+    void push(const HeapItem &x) {
+        size_t i = h.size();
+        h.push_back(x);
+        while (i > 0) {
+            const size_t p = (i - 1) >> 2;
+            if (!(x < h[p])) break;
+            h[i] = h[p];
+            i = p;
+        }
+        h[i] = x;
+    }
+    HeapItem pop() {
+        const HeapItem top = h[0];
+        const HeapItem x = h.back();
+        h.pop_back();
+        const size_t n = h.size();
+        if (n == 0) return top;
+        size_t i = 0;
+        for (;;) {
+            const size_t c0 = 4 * i + 1;
+            if (c0 >= n) break;
+            size_t m = c0;
+            const size_t c1 = std::min(c0 + 4, n);
+            for (size_t c = c0 + 1; c < c1; c++)
+                if (h[c] < h[m]) m = c;
+            if (!(h[m] < x)) break;
+            h[i] = h[m];
+            i = m;
+        }
+        h[i] = x;
+        return top;
+    }
+};
+
 void td_dijkstra(const TD &td, uint32_t s, double t0, std::vector<double> &arr, std::vector<uint32_t> &pred,
                  std::vector<uint8_t> &done, const std::vector<uint32_t> &want, uint32_t stamp, uint32_t n_want,
                  std::vector<HeapItem> &heap) {
@@ -98,14 +138,12 @@ void td_dijkstra(const TD &td, uint32_t s, double t0, std::vector<double> &arr, 
     std::fill(pred.begin(), pred.end(), UINT32_MAX);
     std::fill(done.begin(), done.end(), 0);
     // a min-heap on the caller's storage (kept between searches)
-    const std::greater<HeapItem> later;
     heap.clear();
+    Heap4 pq{heap};
     arr[s] = t0;
-    heap.push_back({t0, s});
-    while (!heap.empty()) {
-        std::pop_heap(heap.begin(), heap.end(), later);
-        const auto [t, u] = heap.back();
-        heap.pop_back();
+    pq.push({t0, s});
+    while (!pq.empty()) {
+        const auto [t, u] = pq.pop();
         if (done[u]) continue;
         done[u] = 1;
         if (want[u] == stamp && --n_want == 0) break;
@@ -116,8 +154,7 @@ void td_dijkstra(const TD &td, uint32_t s, double t0, std::vector<double> &arr, 
             if (nt < arr[v] || (nt == arr[v] && e < pred[v])) {
                 arr[v] = nt;
                 pred[v] = e;
-                heap.push_back({nt, v});
-                std::push_heap(heap.begin(), heap.end(), later);
+                pq.push({nt, v});
             }
         }
     }
