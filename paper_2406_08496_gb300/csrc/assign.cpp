@@ -415,9 +415,16 @@ int lpsim_assign_features(const lpsim_assign *a, uint32_t n_bins, const uint32_t
                           const float *prev_log_ratio, const uint32_t *prev_inflow, float *X, uint32_t n_features) {
     if (!a || !inflow || !occ || !prev_log_ratio || !prev_inflow || !X || n_features != LPSIM_SURROGATE_FEATURES)
         return fail(LPSIM_E_INVALID_ARG, "bad argument");
+    // cells of every edge (for the occupancy densities), once
+    std::vector<float> cells(a->n_edges);
     parallel_pieces(a->n_edges, [&](uint64_t e0, uint64_t e1, uint64_t) {
+        for (uint64_t e = e0; e < e1; e++) cells[e] = std::max(1.0f, std::ceil(a->len[e])) * (float)a->lanes[e];
+    });
+    parallel_pieces(a->n_edges, [&](uint64_t e0, uint64_t e1, uint64_t) {
+        std::vector<float> lin(n_bins);  // the edge's scaled log inflow per bin, each computed once
         for (uint32_t e = (uint32_t)e0; e < (uint32_t)e1; e++) {
-            const float cells = std::max(1.0f, std::ceil(a->len[e])) * (float)a->lanes[e];
+            for (uint32_t b = 0; b < n_bins; b++)
+                lin[b] = std::log1p((float)inflow[(size_t)e * n_bins + b] / (float)a->lanes[e]) / 4.0f;
             // mean occupancy density of the downstream links
             const uint32_t v = a->dst[e];
             for (uint32_t b = 0; b < n_bins; b++) {
@@ -425,18 +432,14 @@ int lpsim_assign_features(const lpsim_assign *a, uint32_t n_bins, const uint32_t
                 x[0] = a->len[e] / 1000.0f;
                 x[1] = (float)a->lanes[e] / 4.0f;
                 x[2] = a->vmax[e] / 30.0f;
-                for (int q = 0; q < 4; q++) {
-                    const int64_t bb = (int64_t)b - q;
-                    const float f = bb >= 0 ? (float)inflow[(size_t)e * n_bins + bb] : 0.0f;
-                    x[3 + q] = std::log1p(f / (float)a->lanes[e]) / 4.0f;
-                }
-                x[7] = 10.0f * (float)occ[(size_t)e * n_bins + b] / cells;
+                // inflow of this bin and the three before it (log1p(0) = 0 before the first)
+                for (int q = 0; q < 4; q++) x[3 + q] = (int64_t)b - q >= 0 ? lin[b - q] : 0.0f;
+                x[7] = 10.0f * (float)occ[(size_t)e * n_bins + b] / cells[e];
                 float down = 0.0f;
                 uint32_t nd = 0;
                 for (uint32_t j = a->out_off[v]; j < a->out_off[v + 1]; j++) {
                     const uint32_t f = a->out_edge[j];
-                    const float fc = std::max(1.0f, std::ceil(a->len[f])) * (float)a->lanes[f];
-                    down += (float)occ[(size_t)f * n_bins + b] / fc;
+                    down += (float)occ[(size_t)f * n_bins + b] / cells[f];
                     nd++;
                 }
                 x[8] = nd ? 10.0f * down / (float)nd : 0.0f;
@@ -453,33 +456,37 @@ int lpsim_assign_features(const lpsim_assign *a, uint32_t n_bins, const uint32_t
 int lpsim_assign_link_times(const lpsim_assign *a, uint32_t n_bins, const uint32_t *tt_sum, const uint32_t *tt_cnt,
                             float *tt, float *log_ratio) {
     if (!a || !tt_sum || !tt_cnt || !tt || n_bins == 0) return fail(LPSIM_E_INVALID_ARG, "bad argument");
-    for (uint32_t e = 0; e < a->n_edges; e++) {
-        const float ff = a->len[e] / a->vmax[e];
-        for (uint32_t b = 0; b < n_bins; b++) {
-            const size_t i = (size_t)e * n_bins + b;
-            if (tt_cnt[i]) {
-                const float m = (float)((double)tt_sum[i] / (double)tt_cnt[i] * a->dt);
-                tt[i] = m;
-                if (log_ratio) log_ratio[i] = std::log(std::max(m, 0.5f * ff) / ff);
-            } else {
-                tt[i] = ff;
-                if (log_ratio) log_ratio[i] = NAN;
+    parallel_pieces(a->n_edges, [&](uint64_t e0, uint64_t e1, uint64_t) {
+        for (uint64_t e = e0; e < e1; e++) {
+            const float ff = a->len[e] / a->vmax[e];
+            for (uint32_t b = 0; b < n_bins; b++) {
+                const size_t i = (size_t)e * n_bins + b;
+                if (tt_cnt[i]) {
+                    const float m = (float)((double)tt_sum[i] / (double)tt_cnt[i] * a->dt);
+                    tt[i] = m;
+                    if (log_ratio) log_ratio[i] = std::log(std::max(m, 0.5f * ff) / ff);
+                } else {
+                    tt[i] = ff;
+                    if (log_ratio) log_ratio[i] = NAN;
+                }
             }
         }
-    }
+    });
     return LPSIM_OK;
 }
 
 int lpsim_assign_times_from_ratio(const lpsim_assign *a, uint32_t n_bins, const float *y, float *tt) {
     if (!a || !y || !tt || n_bins == 0) return fail(LPSIM_E_INVALID_ARG, "bad argument");
-    for (uint32_t e = 0; e < a->n_edges; e++) {
-        const float ff = a->len[e] / a->vmax[e];
-        for (uint32_t b = 0; b < n_bins; b++) {
-            const size_t i = (size_t)e * n_bins + b;
-            const float r = std::exp(std::min(std::max(y[i], 0.0f), std::log(50.0f)));
-            tt[i] = ff * r;
+    const float ymax = std::log(50.0f);
+    parallel_pieces(a->n_edges, [&](uint64_t e0, uint64_t e1, uint64_t) {
+        for (uint64_t e = e0; e < e1; e++) {
+            const float ff = a->len[e] / a->vmax[e];
+            for (uint32_t b = 0; b < n_bins; b++) {
+                const size_t i = (size_t)e * n_bins + b;
+                tt[i] = ff * std::exp(std::min(std::max(y[i], 0.0f), ymax));
+            }
         }
-    }
+    });
     return LPSIM_OK;
 }
 
