@@ -179,6 +179,17 @@ def ncu_traffic():
     return d
 
 
+def l2_note(net, dem) -> str:
+    """What the timed region reads, against the 129 MB L2: the route array
+    and the three rotating lane maps (each lane row padded to 16 bytes)."""
+    cells = np.maximum(1, np.ceil(np.asarray(net["edge_len"], np.float64))).astype(np.int64)
+    rows = ((cells + 15) // 16 * 16) * np.asarray(net["edge_lanes"], np.int64)
+    map_gb = float(rows.sum() + 16) / 1e9
+    route_gb = float(np.asarray(dem["route_edges"]).size * 4) / 1e9
+    return (f"inputs larger than L2 (129 MB): routes {route_gb:.2f} GB, lane maps 3 x {map_gb:.3f} GB; "
+            "no flush between steps")
+
+
 def whole_job(ms: float, units: float, dist, device: str):
     """The whole job over N ranks: the longest rank's timed span (max) and
     the units every rank processed (sum); value = units / span.  One rank
@@ -434,34 +445,48 @@ def main():
 
     out = None
     if rank == 0:
-        # roofline of the dominant kernel: one more day with per-launch events
+        # roofline of the dominant kernel: one more day with the kernels
+        # stamping their own device spans (graphs, programmatic dependent
+        # launch and light-load chunks as in the timed days), bracketed by
+        # CUDA events on the library's stream
         sim.set_kernel_timing(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
         rr = day()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        day_ms = e0.elapsed_time(e1)
         kt = sim.kernel_times()
         sim.set_kernel_timing(False)
         p1 = kt["step_p1"]
         if p1["ms"] <= 0 or p1["launches"] == 0:
             raise RuntimeError(f"no step_p1 launch was timed: {kt}")
-        achieved = BYTES_PER_VEH_STEP_P1 * rr["veh_steps"] / (p1["ms"] / 1e3) / 1e9
+        achieved = BYTES_PER_VEH_STEP_P1 * p1["veh_steps"] / (p1["ms"] / 1e3) / 1e9
         peak, peak_src = measured_peaks()
-        tot_ms = sum(v["ms"] for v in kt.values())
         tr = ncu_traffic()
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                     # ncu DRAM bytes per vehicle-step of a morning-peak launch, scaled to this
                     # run's average launch (traffic grows with the vehicles processed)
-                    "traffic": (tr["dram_bytes_per_veh_step"] * rr["veh_steps"] / max(1, p1["launches"])
+                    "traffic": (tr["dram_bytes_per_veh_step"] * p1["veh_steps"] / max(1, p1["launches"])
                                 if tr else None),
                     "kernel": "step_p1", "bytes_per_veh_step": BYTES_PER_VEH_STEP_P1,
                     "avg_launch_us": p1["ms"] * 1e3 / max(1, p1["launches"]),
-                    "avg_veh_per_launch": rr["veh_steps"] / max(1, p1["launches"]),
+                    "avg_veh_per_launch": p1["veh_steps"] / max(1, p1["launches"]),
+                    "launches": p1["launches"], "veh_steps": p1["veh_steps"],
+                    "timing": "device spans stamped by the kernels (first block start to last block end, "
+                              "%globaltimer) over one extra day run as timed; CUDA events around that day",
+                    "day_ms_events": day_ms,
+                    "kernel_ms": {k: v["ms"] for k, v in kt.items()},
+                    "kernel_launches": {k: v["launches"] for k, v in kt.items()},
+                    "kernel_share_of_day": {k: v["ms"] / day_ms for k, v in kt.items()},
                     "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})",
-                    "kernel_share": {k: v["ms"] / tot_ms for k, v in kt.items()},
                     "traffic_source": ("profiles/step_p1_regional_peak.json: " + tr["captured_launch"]) if tr else
                     "stale or missing ncu summary"}
         # the same at the morning peak (the hour the roofline target is about):
-        # the graph chunk of kernel-timed steps that holds 08:00
+        # the graph chunk that holds 08:00
         peak_window = None
-        if args.workload == "regional":
+        if args.workload in ("regional", "large"):
             cw = int(L.DEFAULT_PARAMS["chunk_steps"])
             kw0 = (8 * 7200) // cw * cw
 
@@ -470,25 +495,31 @@ def main():
                 return f"{sec // 3600:02d}:{sec // 60 % 60:02d}:{sec % 60:02d}"
             sim.reset()
             sim.step(kw0)
-            c0 = sim.counters()
             sim.set_kernel_timing(True)
+            torch.cuda.synchronize()
+            e0.record(stream)
             sim.step(cw)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            win_ms = e0.elapsed_time(e1)
             kw = sim.kernel_times()
             sim.set_kernel_timing(False)
-            vs_w = sim.counters()["veh_steps"] - c0["veh_steps"]
             pw = kw["step_p1"]
             if pw["ms"] > 0 and pw["launches"]:
-                ach = BYTES_PER_VEH_STEP_P1 * vs_w / (pw["ms"] / 1e3) / 1e9
+                ach = BYTES_PER_VEH_STEP_P1 * pw["veh_steps"] / (pw["ms"] / 1e3) / 1e9
                 per_launch_s = pw["ms"] / 1e3 / pw["launches"]
-                dram = tr["dram_bytes_per_launch"] if tr else None
+                dram = tr["dram_bytes_per_veh_step"] * pw["veh_steps"] / pw["launches"] if tr else None
                 peak_window = {"window": f"steps {kw0:,}-{kw0 + cw - 1:,} ({clock(kw0)}-{clock(kw0 + cw)})",
-                               "achieved": ach,
-                               "frac": ach / peak, "unit": "GB/s",
-                               "avg_launch_us": per_launch_s * 1e6, "avg_veh_per_launch": vs_w / pw["launches"],
+                               "achieved": ach, "frac": ach / peak, "unit": "GB/s",
+                               "avg_launch_us": per_launch_s * 1e6,
+                               "avg_veh_per_launch": pw["veh_steps"] / pw["launches"],
+                               "window_ms_events": win_ms,
+                               "kernel_share_of_window": {k: v["ms"] / win_ms for k, v in kw.items()},
                                "dram_gbs": dram / per_launch_s / 1e9 if dram else None,
                                "dram_frac": dram / per_launch_s / 1e9 / peak if dram else None,
-                               "dram_source": "ncu DRAM bytes of a step_p1 launch at 08:00 "
-                                              "(profiles/step_p1_regional_peak.json) / live launch time"}
+                               "dram_source": "ncu DRAM bytes per vehicle-step of step_p1 launches at 08:00 "
+                                              "(profiles/step_p1_regional_peak.json) x this window's vehicles "
+                                              "per launch / live span"}
             roofline["peak_window"] = peak_window
         cpu = None
         if not args.no_cpu_baseline and world == 1:
@@ -511,7 +542,7 @@ def main():
                           "sim_steps_per_day": int(np.mean(steps_per_day)),
                           "step": "one simulated day from step 0 until every trip has arrived",
                           "parallelism": f"replicas x{world}",
-                          "l2": "inputs larger than L2 (routes 1.4 GB, lane maps 3 x 0.16 GB)"},
+                          "l2": l2_note(net, dem)},
                "wall_per_sim_day_s": t_max / args.steps / 1e3,
                "pct_hbm_peak": roofline["frac"],
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,

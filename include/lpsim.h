@@ -161,7 +161,9 @@ int lpsim_load_network(lpsim_ctx **out, const lpsim_network *net, const lpsim_pa
  * first edge "after the routing").  Trip j departs no earlier than step
  * depart_step[j] and follows route_edges[route_off[j] .. route_off[j+1]), a
  * non-empty sequence of edges where each edge starts at the node the previous
- * one ends at.  route_off has n_trips + 1 entries starting at 0; the total
+ * one ends at.  n_trips may be 0 (an empty demand: steps move nothing and
+ * lpsim_run returns at once); depart_step and route_edges may then be NULL.
+ * route_off has n_trips + 1 entries starting at 0; the total
  * route length must stay below 2^32.  Vehicle ids are the ranks of a stable
  * sort of the trips by depart_step (the paper sorts by departure time,
  * Sec. 4, Table 6); out_vehicle_id (nullable, n_trips entries) receives trip
@@ -174,44 +176,87 @@ int lpsim_load_network(lpsim_ctx **out, const lpsim_network *net, const lpsim_pa
 int lpsim_load_demand(lpsim_ctx *ctx, uint64_t n_trips, const uint32_t *depart_step, const uint64_t *route_off,
                       const uint32_t *route_edges, uint32_t *out_vehicle_id);
 
-/* Advance n_steps steps.  Returns after the steps have completed on the
- * device and the device status word was read. */
+/* Advance n_steps steps of Algorithm 1 (Vehicle Propagation, Sec. 3.1-3.2):
+ * each step moves every vehicle from its step-k state to step k+1 using only
+ * step-k state (eq. vehicle_dynamics, Sec. 3.1) -- departure when the first
+ * cell of the first edge is free, leader search within d_front, IDM car
+ * following (eq. Car Following) or the free-flow speed, signal control at the
+ * stop line, lane change (eq. Lane Change) with gap acceptance (eq. Gap
+ * Acceptance), entry to the next route edge one vehicle at a time (Sec. 3.2).
+ * Returns after the steps have completed on the device and the device status
+ * word was read.  n_steps 0 only reads the status word.  Errors:
+ * LPSIM_E_STATE before lpsim_load_demand; LPSIM_E_INVARIANT when the
+ * LPSIM_F_CHECK_CELLS check found a lane-map cell written twice or the slot
+ * capacity overflowed; LPSIM_E_CUDA when a launch or copy failed (the context
+ * is then unusable: destroy it).  A failed call may have taken some of the
+ * steps; lpsim_get_counters tells how many. */
 int lpsim_step(lpsim_ctx *ctx, uint32_t n_steps);
 
-/* Step until every trip has arrived or max_steps steps were taken; out
- * (nullable) receives the totals of this call. */
+/* Step (Algorithm 1, as lpsim_step) until every trip has arrived or
+ * max_steps steps were taken -- the whole-run simulation whose wall time the
+ * paper reports (Sec. 4).  out (nullable) receives the totals of this call:
+ * steps taken, vehicle-steps (sum over those steps of the vehicles on the
+ * network), trips arrived / active / waiting, the current step and the host
+ * wall time.  Errors as lpsim_step, plus LPSIM_E_GRIDLOCK when
+ * params.gridlock_steps is non-zero and that many steps passed with vehicles
+ * on the network and no departure, crossing or arrival (a host-side check of
+ * the device counters after each graph chunk; no kernel waits on it). */
 int lpsim_run(lpsim_ctx *ctx, uint32_t max_steps, lpsim_run_result *out);
 
-/* Back to step 0 with the same network and trips: empty lane maps, every
- * trip waiting, statistics cleared.  No host-device transfer of inputs. */
+/* Back to step 0 with the same network and trips (the state before the
+ * first step of Algorithm 1: every trip waiting for t_depart, empty lane
+ * maps), statistics cleared.  No host-device transfer of inputs.  Errors:
+ * LPSIM_E_CUDA. */
 int lpsim_reset(lpsim_ctx *ctx);
 
-/* Link statistics.  out (nullable): n_edges records.  The binned arrays
- * (each nullable, n_edges * n_bins u32, edge-major) receive per (edge, bin):
- * inflow counted at entry step k+1 in bin (k+1)/bin_steps; steps spent and
- * exit count of the vehicles that entered in that bin; the vehicles on the
- * edge at the first step of the bin.  n_edges and n_bins must equal the
- * context's. */
+/* Link statistics, from the step each vehicle entered its current edge
+ * (t_start of Algorithm 1, recorded "on a new edge") and the step it left:
+ * out (nullable) receives n_edges records {entries, exits, summed steps on the
+ * edge}.  The signature is wider than a per-edge query alone: the four binned
+ * arrays (each nullable, n_edges * n_bins u32, edge-major; bins of
+ * params.bin_steps steps) feed the assignment loop and its travel-time
+ * surrogate -- per (edge, bin): inflow counted at entry step k+1 in bin
+ * (k+1)/bin_steps; steps spent and exit count of the vehicles that entered in
+ * that bin; the vehicles on the edge at the first step of the bin.  Errors:
+ * LPSIM_E_INVALID_ARG when n_edges or (with a binned array) n_bins differ from
+ * the context's; LPSIM_E_OOM when the device scratch of the binned transpose
+ * cannot be allocated; LPSIM_E_CUDA. */
 int lpsim_link_stats(lpsim_ctx *ctx, lpsim_link_stat *out, uint64_t n_edges, uint32_t *bin_inflow,
                      uint32_t *bin_tt_sum, uint32_t *bin_tt_cnt, uint32_t *bin_occ, uint32_t n_bins);
 
-/* Per vehicle id (n entries each, n = trips loaded): the step at which it
+/* Per-trip outputs of the simulation (Algorithm 1 State: t_depart; the
+ * trip's travel time is what the paper's assignment use rests on, Sec. 1):
+ * per vehicle id (n entries each, n = trips loaded) the step at which it
  * entered the network (0xFFFFFFFF if not yet) and the step at which it
- * arrived (0xFFFFFFFF if not yet).  Either pointer may be NULL. */
+ * arrived (0xFFFFFFFF if not yet).  Either pointer may be NULL.  Errors:
+ * LPSIM_E_STATE before lpsim_load_demand; LPSIM_E_INVALID_ARG when n differs
+ * from the trips loaded; LPSIM_E_CUDA. */
 int lpsim_get_trips(lpsim_ctx *ctx, uint64_t n, uint32_t *depart_actual, uint32_t *arrive_step);
 
-/* Per vehicle id (n entries each): position on the edge (m), speed (m/s),
- * edge, lane, index in its route and status (0 waiting, 1 active, 2 arrived);
- * non-active vehicles read x = v = 0, edge 0xFFFFFFFF, lane 0, index 0.  Any
- * pointer may be NULL. */
+/* Vehicle state of Algorithm 1 (Output: position P and speed v) and of the
+ * vehicle record of Sec. 3.1 (Vehicle Data Information: current edge,
+ * position on it, place in the route): per vehicle id (n entries each, n =
+ * trips loaded) position on the edge (m), speed (m/s), edge, lane, index in
+ * its route and status (0 waiting, 1 active, 2 arrived); non-active vehicles
+ * read x = v = 0, edge 0xFFFFFFFF, lane 0, index 0.  Any pointer may be NULL.
+ * Takes n * 17 bytes of device scratch for the call (from cudaMalloc or the
+ * allocator callback) and gives it back before returning, on every path.
+ * Errors: LPSIM_E_STATE before lpsim_load_demand; LPSIM_E_INVALID_ARG when n
+ * differs from the trips loaded; LPSIM_E_OOM; LPSIM_E_CUDA. */
 int lpsim_get_state(lpsim_ctx *ctx, uint64_t n, float *x, float *v, uint32_t *edge, uint8_t *lane,
                     uint32_t *route_idx, uint8_t *status);
 
-/* Lane map at the current step in canonical layout: edges in id order, lanes
- * in order, cells 0..len-1, no padding; size = lpsim_lane_map_size(). */
+/* Lane map at the current step (Sec. 3.1, Lane Map: one byte per metre of
+ * lane, 255 = empty, 0..254 = speed of the occupying vehicle; lanes of an
+ * edge one after the other) in canonical layout: edges in id order, lanes in
+ * order, cells 0..len-1, no padding; size = lpsim_lane_map_size() bytes.
+ * Errors: LPSIM_E_INVALID_ARG on a NULL pointer or a wrong size. */
 uint64_t lpsim_lane_map_size(const lpsim_ctx *ctx);
 int lpsim_get_lane_map(lpsim_ctx *ctx, uint8_t *out, uint64_t size);
 
+/* Run counters (no paper counterpart: the quantities the benchmarks report,
+ * vehicle-steps above all).  Reads the device status word; errors as
+ * lpsim_step. */
 int lpsim_get_counters(lpsim_ctx *ctx, lpsim_counters *out);
 
 /* ---- batched scenarios ------------------------------------------------
@@ -255,7 +300,7 @@ typedef struct lpsim_tune_result {
 
 /* Autotuner: from the current state, run window_steps steps under each
  * candidate launch configuration (block size 128/256/512, 2/4/6 resident
- * 256-thread blocks per SM, sort period 32/64/128), restoring a snapshot
+ * 256-thread blocks per SM, sort period 64/128/256), restoring a snapshot
  * before each, and keep the fastest.  The context is left at the starting
  * state with the chosen configuration.  Results never depend on the
  * configuration, only speed does.  Best called at step 0 or at a multiple of
@@ -266,16 +311,28 @@ int lpsim_autotune(lpsim_ctx *ctx, uint32_t window_steps, lpsim_tune_result *out
 int lpsim_set_config(lpsim_ctx *ctx, uint32_t block_size, uint32_t blocks_per_sm, uint32_t sort_period,
                      uint32_t chunk_steps);
 
-/* Per-kernel timing.  While on, every launch of the two step kernels
- * (step_p1: car following, edge-end decisions, lane-change intents,
- * departure and entry claims; step_p2: entry conflicts, departures, lane
- * changes) and of the compaction/sort sequence is bracketed by CUDA events on
- * the context's stream, and the elapsed times are summed after each graph
- * chunk (which then synchronises).  Switching resets the sums.
- * lpsim_get_kernel_times fills ms[3] (summed milliseconds) and launches[3]
- * (phase launches timed) in the order step_p1, step_p2, compaction. */
+/* Per-kernel timing.  While on, each launch of the step kernels (step_p1:
+ * car following, edge-end decisions, lane-change intents, departure and
+ * entry claims; step_p2: entry conflicts, departures, lane changes), of the
+ * compaction/sort sequence and of the light-load kernel stamps its own span
+ * on the device: the GPU global timer when its first block starts working
+ * (after the previous kernel's results are visible) and when its last block
+ * ends.  One small kernel per graph chunk adds the spans up.  Nothing is
+ * inserted between the kernels, so the CUDA graphs keep their programmatic
+ * dependent launches and the light-load kernel still runs; spans of
+ * consecutive kernels do not overlap, so their sum never exceeds the wall
+ * time of the steps.  Switching on clears the sums; switching off keeps them
+ * readable. */
 int lpsim_set_kernel_timing(lpsim_ctx *ctx, int on);
-int lpsim_get_kernel_times(lpsim_ctx *ctx, double *ms, uint64_t *launches);
+
+typedef struct lpsim_kernel_times {
+    double ms[4];           /* summed spans, ms: step_p1, step_p2, compaction + sort, light-load kernel */
+    uint64_t launches[4];   /* launches timed, same order */
+    uint64_t p1_veh_steps;  /* vehicle-steps handled by the timed step_p1 launches */
+} lpsim_kernel_times;
+
+/* Sums since timing was last switched on (zeros if it never was). */
+int lpsim_get_kernel_times(lpsim_ctx *ctx, lpsim_kernel_times *out);
 
 /* Largest trip count lpsim_get_state_noalloc serves: its scratch is a fixed
  * device array of LPSIM_NOALLOC_MAX_VEHICLES * 17 bytes (17 MiB). */
@@ -298,8 +355,9 @@ int lpsim_get_kernel_times(lpsim_ctx *ctx, double *ms, uint64_t *launches);
  *
  * n above LPSIM_NOALLOC_MAX_VEHICLES gives LPSIM_E_INVALID_ARG (use
  * lpsim_get_state).  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress, with that device current); make that first
- * call before any stream capture on the device.  Every call on a device
+ * address (cudaGetSymbolAddress, with that device current), and so does the
+ * first call after the device's context was replaced (cudaDeviceReset); make
+ * those first calls before any stream capture on the device.  Every call on a device
  * shares the one array and it keeps the last call's contents (the call
  * clears it before use): calls whose work overlaps on the GPU -- two
  * contexts on different streams, or two threads -- race on it and must be

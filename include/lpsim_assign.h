@@ -10,7 +10,12 @@
  *   RG = sum_trips (t_experienced - t_shortest) / sum_trips t_shortest,
  * t_experienced from planned departure to arrival in the simulation and
  * t_shortest the earliest-arrival path time under the link times of the same
- * simulation (link time looked up by entry time in 15-minute bins, FIFO).
+ * simulation.  Link times come per (edge, 15-minute entry bin), rounded to
+ * whole milliseconds; entering edge e at time t in bin b arrives at
+ *   min(t + c[b][e], min over later bins b' of (start of b' + c[b'][e])),
+ * i.e. an entry may be held back to a later bin when that arrives earlier,
+ * which makes every link FIFO (a later entry never arrives earlier) and the
+ * earliest-arrival searches exact.
  *
  * Conventions as in lpsim.h (status codes, lpsim_last_error(), host
  * pointers, caller-owned buffers).  Everything here runs on the host CPU
@@ -52,6 +57,19 @@ int lpsim_assign_create(lpsim_assign **out, uint32_t n_nodes, uint32_t n_edges, 
  * departure step. */
 int lpsim_assign_shortest_paths(lpsim_assign *a, const float *tt, uint32_t n_bins, uint32_t bin_steps,
                                 uint32_t period_steps, uint32_t n_threads, float *t_sp);
+
+/* lpsim_assign_shortest_paths with the earliest-arrival trees searched on
+ * the GPU (device current at the first call; one warp per tree, thousands of
+ * trees at a time, label-correcting rounds on 64-bit (arrival, edge)
+ * labels).  Same candidate routes and t_sp, bit for bit, as the host
+ * searches: link times are whole milliseconds, so every arrival is an exact
+ * sum, and both keep the earliest arrival with ties to the lower entering
+ * edge id.  The graph, trip table and search workspaces (some 24 bytes per
+ * node per concurrent tree, at most 16 GiB) stay on the device between calls
+ * and are released by lpsim_assign_destroy.  Errors as the host call, plus
+ * LPSIM_E_CUDA, LPSIM_E_OOM and LPSIM_E_STATE (another device current). */
+int lpsim_assign_shortest_paths_gpu(lpsim_assign *a, const float *tt, uint32_t n_bins, uint32_t bin_steps,
+                                    uint32_t period_steps, float *t_sp);
 
 /* Relative gap of the last shortest paths against a simulation's trip
  * outcome (per trip, in the caller's trip order): trips that have not

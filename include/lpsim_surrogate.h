@@ -50,6 +50,16 @@ int lpsim_mlp_grad(lpsim_mlp *m, uint64_t n, const float *X, const float *t, flo
 int lpsim_mlp_train(lpsim_mlp *m, uint64_t n, const float *X, const float *t, uint32_t steps, float lr,
                     uint64_t shuffle_seed, float *losses);
 
+/* One Adam step (Kingma and Ba 2015, Algorithm 1; beta1 0.9, beta2 0.999,
+ * eps 1e-8, learning rate lr) on the FP32 master weights with gradients
+ * given by the caller: grads[8] host tensors in the parameter order above
+ * (none NULL), e.g. gradients averaged over several models' lpsim_mlp_grad
+ * calls.  The same update lpsim_mlp_train applies after each minibatch; it
+ * continues that call's step count t (lpsim_mlp_set_params resets it) and
+ * refreshes the BF16 weight copies.  Errors: LPSIM_E_INVALID_ARG on a NULL
+ * tensor or a negative or non-finite lr; LPSIM_E_CUDA. */
+int lpsim_mlp_apply_grads(lpsim_mlp *m, const float *const *grads, float lr);
+
 /* Diagnostic: D (M x N, f32) = A (M x K) . B (N x K)^T for BF16 bit
  * patterns A, B (row-major) on the tensor-core GEMM kernel the model uses.
  * M % 128 == 0, K % 64 == 0, N == 64 or N % 256 == 0. */

@@ -33,9 +33,9 @@ EXPORTED = ["lpsim_last_error", "lpsim_version", "lpsim_set_allocator", "lpsim_l
             "lpsim_load_network_batch", "lpsim_load_demand_batch", "lpsim_batch_offsets", "lpsim_snapshot",
             "lpsim_restore", "lpsim_autotune", "lpsim_set_config", "lpsim_destroy",
             "lpsim_mlp_create", "lpsim_mlp_set_params", "lpsim_mlp_get_params", "lpsim_mlp_forward",
-            "lpsim_mlp_grad", "lpsim_mlp_train", "lpsim_mlp_gemm_test", "lpsim_mlp_time", "lpsim_mlp_gelu_eval",
+            "lpsim_mlp_grad", "lpsim_mlp_train", "lpsim_mlp_apply_grads", "lpsim_mlp_gemm_test", "lpsim_mlp_time", "lpsim_mlp_gelu_eval",
             "lpsim_mlp_destroy",
-            "lpsim_assign_create", "lpsim_assign_shortest_paths", "lpsim_assign_gap", "lpsim_assign_reroute",
+            "lpsim_assign_create", "lpsim_assign_shortest_paths", "lpsim_assign_shortest_paths_gpu", "lpsim_assign_gap", "lpsim_assign_reroute",
             "lpsim_assign_route_excess", "lpsim_assign_reroute_worst", "lpsim_assign_route_length",
             "lpsim_assign_get_routes", "lpsim_assign_load", "lpsim_assign_features", "lpsim_assign_link_times", "lpsim_assign_times_from_ratio", "lpsim_assign_destroy"]
 
@@ -76,6 +76,10 @@ class Counters(ctypes.Structure):
 class TuneResult(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in ("block_size", "blocks_per_sm", "sort_period", "chunk_steps")] + \
                [("best_ms", ctypes.c_double), ("default_ms", ctypes.c_double), ("n_tried", ctypes.c_uint32)]
+
+
+class KernelTimes(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 4), ("launches", ctypes.c_uint64 * 4), ("p1_veh_steps", ctypes.c_uint64)]
 
 
 class LpsimError(RuntimeError):
@@ -122,7 +126,7 @@ def load_library(path: str | None = None):
     lib.lpsim_get_lane_map.argtypes = [P, P, ctypes.c_uint64]
     lib.lpsim_get_counters.argtypes = [P, ctypes.POINTER(Counters)]
     lib.lpsim_set_kernel_timing.argtypes = [P, ctypes.c_int]
-    lib.lpsim_get_kernel_times.argtypes = [P, P, P]
+    lib.lpsim_get_kernel_times.argtypes = [P, ctypes.POINTER(KernelTimes)]
     lib.lpsim_get_state_noalloc.argtypes = [P, ctypes.c_uint64, P, P, P, P, P, P]
     lib.lpsim_load_network_batch.argtypes = [ctypes.POINTER(P), ctypes.c_uint32, P, ctypes.POINTER(Params), P]
     lib.lpsim_load_demand_batch.argtypes = [P, ctypes.c_uint32, P, P, P, P, P, P]
@@ -139,6 +143,7 @@ def load_library(path: str | None = None):
     lib.lpsim_mlp_forward.argtypes = [P, ctypes.c_uint64, P, P]
     lib.lpsim_mlp_grad.argtypes = [P, ctypes.c_uint64, P, P, P, P]
     lib.lpsim_mlp_train.argtypes = [P, ctypes.c_uint64, P, P, ctypes.c_uint32, ctypes.c_float, ctypes.c_uint64, P]
+    lib.lpsim_mlp_apply_grads.argtypes = [P, P, ctypes.c_float]
     lib.lpsim_mlp_gemm_test.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, P, P, P]
     lib.lpsim_mlp_time.argtypes = [P, ctypes.c_uint32, P, P]
     lib.lpsim_mlp_gelu_eval.argtypes = [ctypes.c_uint64, P, P, P]
@@ -308,11 +313,14 @@ class Simulation:
         _check(self.lib, self.lib.lpsim_set_kernel_timing(self.h, 1 if on else 0))
 
     def kernel_times(self) -> dict:
-        ms = np.zeros(3, np.float64)
-        n = np.zeros(3, np.uint64)
-        _check(self.lib, self.lib.lpsim_get_kernel_times(self.h, _p(ms), _p(n)))
-        names = ("step_p1", "step_p2", "compact_sort")
-        return {k: {"ms": float(ms[i]), "launches": int(n[i])} for i, k in enumerate(names)}
+        """Summed device spans per kernel since timing was switched on, and
+        the vehicle-steps the step_p1 launches handled."""
+        t = KernelTimes()
+        _check(self.lib, self.lib.lpsim_get_kernel_times(self.h, ctypes.byref(t)))
+        names = ("step_p1", "step_p2", "compact_sort", "step_small")
+        out = {k: {"ms": float(t.ms[i]), "launches": int(t.launches[i])} for i, k in enumerate(names)}
+        out["step_p1"]["veh_steps"] = int(t.p1_veh_steps)
+        return out
 
     def snapshot(self) -> None:
         _check(self.lib, self.lib.lpsim_snapshot(self.h))
@@ -470,6 +478,12 @@ class Surrogate:
         losses = np.empty(steps, np.float32)
         _check(self.lib, self.lib.lpsim_mlp_train(self.h, len(X), _p(X), _p(t), steps, lr, seed, _p(losses)))
         return losses
+
+    def apply_grads(self, grads: dict, lr: float) -> None:
+        """One Adam step with the given gradients (the update train applies)."""
+        arrs = [np.ascontiguousarray(grads[k], dtype=np.float32).reshape(s) for k, s in zip(PARAM_NAMES, PARAM_SHAPES)]
+        ptrs = (ctypes.c_void_p * 8)(*[a.ctypes.data for a in arrs])
+        _check(self.lib, self.lib.lpsim_mlp_apply_grads(self.h, ctypes.cast(ptrs, ctypes.c_void_p), lr))
 
     def time(self, iters: int = 20) -> dict:
         f = ctypes.c_double()

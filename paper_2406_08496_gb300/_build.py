@@ -15,8 +15,8 @@ from concurrent.futures import ThreadPoolExecutor
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
-SOURCES = ["step_kernels.cu", "compact_sort.cu", "runtime.cu", "noalloc.cu", "mlp.cu", "assign.cpp"]
-HEADERS = ["lpsim_dev.cuh", "ctx.h", "host_par.h"]
+SOURCES = ["step_kernels.cu", "compact_sort.cu", "runtime.cu", "noalloc.cu", "mlp.cu", "assign.cpp", "assign_gpu.cu"]
+HEADERS = ["lpsim_dev.cuh", "ctx.h", "host_par.h", "assign_internal.h"]
 LIB = os.path.join(HERE, "liblpsim.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-prec-div=true", "-prec-sqrt=true", "-ftz=false",

@@ -2,9 +2,9 @@
 averages with time-dependent shortest paths, plain or surrogate-assisted.
 
 Binding of include/lpsim_assign.h plus the iteration driver.  All arithmetic
-runs in the library: simulations and the surrogate on the GPU, routing,
-gaps, loading and features in the host engine (C++ threads); this module
-only sequences the calls.
+runs in the library: simulations, the surrogate and (by default) the
+time-dependent shortest paths on the GPU; gaps, loading and features in the
+host engine (C++ threads); this module only sequences the calls.
 """
 from __future__ import annotations
 
@@ -27,6 +27,7 @@ def _lib():
                                             ctypes.c_uint64, P, P, P, P, P, ctypes.c_float, ctypes.c_uint64]
         lib.lpsim_assign_shortest_paths.argtypes = [P, P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                                     ctypes.c_uint32, P]
+        lib.lpsim_assign_shortest_paths_gpu.argtypes = [P, P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, P]
         lib.lpsim_assign_gap.argtypes = [P, P, P, P, P]
         lib.lpsim_assign_reroute.argtypes = [P, ctypes.c_double, ctypes.c_uint32, P]
         lib.lpsim_assign_route_excess.argtypes = [P, P, ctypes.c_uint32, ctypes.c_uint32]
@@ -77,6 +78,14 @@ class Assignment:
         nt = n_threads or (os.cpu_count() or 1)
         _check(self.lib, self.lib.lpsim_assign_shortest_paths(self.h, _p(tt), tt.shape[1], bin_steps, period_steps,
                                                               nt, _p(tsp)))
+        return tsp
+
+    def shortest_paths_gpu(self, tt: np.ndarray, bin_steps: int, period_steps: int):
+        """The same trees searched on the GPU (identical routes and times)."""
+        tt = np.ascontiguousarray(tt, dtype=np.float32)
+        tsp = np.empty(self.n, np.float32)
+        _check(self.lib, self.lib.lpsim_assign_shortest_paths_gpu(self.h, _p(tt), tt.shape[1], bin_steps,
+                                                                  period_steps, _p(tsp)))
         return tsp
 
     def gap(self, depart_actual: np.ndarray, arrive_step: np.ndarray):
@@ -154,7 +163,7 @@ class Assignment:
 def msa(net: dict, dem: dict, mode: str = "plain", iterations: int = 10, fraction: float = 0.1,
         target_gap: float = 0.01, sim_params: dict | None = None, bin_steps: int = 1800, n_bins: int = 96,
         period_steps: int = 3600, max_steps: int = 300_000, surrogate_steps: int = 400, surrogate_batch: int = 8192,
-        seed: int = 0, select: str = "random", min_rel_excess: float = 0.0, log=None) -> dict:
+        seed: int = 0, select: str = "random", min_rel_excess: float = 0.0, paths: str = "gpu", log=None) -> dict:
     """Method of successive averages.  plain: every iteration simulates the
     current routes, measures the relative gap and moves `fraction` of the
     trips to their time-dependent shortest paths under the simulated link
@@ -167,10 +176,12 @@ def msa(net: dict, dem: dict, mode: str = "plain", iterations: int = 10, fractio
     (each trip with probability fraction, seeded) or "worst" (the fraction
     with the largest relative excess of their route over the shortest path
     under the iteration's link times, measured or predicted; only trips more
-    than min_rel_excess worse than their shortest path).  Returns
-    the iteration history and the wall time to reach target_gap (None if
-    never reached)."""
-    assert mode in ("plain", "surrogate") and select in ("worst", "random")
+    than min_rel_excess worse than their shortest path).  paths: where the
+    time-dependent shortest paths are searched -- "gpu" (one warp per tree)
+    or "host" (Dijkstra on the host threads); both give the same routes and
+    times.  Returns the iteration history and the wall time to reach
+    target_gap (None if never reached)."""
+    assert mode in ("plain", "surrogate") and select in ("worst", "random") and paths in ("gpu", "host")
 
     def move(it):
         return A.reroute_worst(fraction, min_rel_excess) if select == "worst" else A.reroute(fraction, it)
@@ -178,6 +189,7 @@ def msa(net: dict, dem: dict, mode: str = "plain", iterations: int = 10, fractio
     params = dict(bin_steps=bin_steps, n_bins=n_bins)
     params.update(sim_params or {})
     A = Assignment(net, dem, dt=0.5, seed=seed)
+    search = A.shortest_paths_gpu if paths == "gpu" else A.shortest_paths
     mlp = Surrogate(n_features=N_FEATURES, batch=surrogate_batch, seed=seed) if mode == "surrogate" else None
     train_X, train_t = [], []
     hist = []
@@ -197,7 +209,7 @@ def msa(net: dict, dem: dict, mode: str = "plain", iterations: int = 10, fractio
             sim.close()
             t_sim = time.perf_counter() - t0
             tt, logratio = A.link_times(ls["tt_sum"], ls["tt_cnt"])
-            A.shortest_paths(tt, bin_steps, period_steps)
+            search(tt, bin_steps, period_steps)
             rg, used = A.gap(tr["depart"][vid], tr["arrive"][vid])
             if select == "worst":
                 # rank trips by their route's excess under the measured link
@@ -236,7 +248,7 @@ def msa(net: dict, dem: dict, mode: str = "plain", iterations: int = 10, fractio
             X = A.features(inflow, occ_last, lr_last, in_last)
             y = mlp.forward(X)
             tt_pred = A.times_from_ratio(y, n_bins)
-            A.shortest_paths(tt_pred, bin_steps, period_steps)
+            search(tt_pred, bin_steps, period_steps)
             if select == "worst":
                 A.route_excess(tt_pred, bin_steps)
             rec = dict(iteration=it, kind="surrogate", gap=None, wall_s=time.perf_counter() - t_start,

@@ -27,68 +27,26 @@
 #include <vector>
 
 #include "../../include/lpsim_assign.h"
+#include "assign_internal.h"
 #include "host_par.h"
 
 int lpsim_fail(int code, const std::string &msg);
 
 namespace {
 int fail(int code, const std::string &m) { return lpsim_fail(code, m); }
+using namespace lpsim_assign_detail;
 }  // namespace
-
-struct lpsim_assign {
-    uint32_t n_nodes = 0, n_edges = 0;
-    std::vector<uint32_t> src, dst, lanes;
-    std::vector<float> len, vmax;
-    std::vector<uint32_t> out_off, out_edge;  // CSR of out-edges by source node
-    // trips
-    uint64_t n = 0;
-    std::vector<uint32_t> orig, dest, dep;    // depart step
-    std::vector<std::vector<uint32_t>> route, cand;
-    std::vector<float> tsp;                   // shortest time under the last tt (s)
-    std::vector<float> excess;                // current route's time minus tsp (s), from a simulation or a prediction
-    float dt = 0.5f;
-    uint64_t seed = 0;
-};
 
 namespace {
 
 using lpsim::kPiece;
 using lpsim::parallel_pieces;
 
-// Time-dependent link costs: the time to traverse edge e when entering it at
-// time t is the table value of e in the bin holding t (first / last bin
-// outside the table).  The table is kept bin-major (n_bins x n_edges): a
-// search or a route walk stays within a few bins, so the values it reads sit
-// in a few contiguous rows that stay in the host caches, where the
-// caller's edge-major layout put every edge's value on its own cache line.
-struct TD {
-    const lpsim_assign *a;
-    std::vector<float> tbm;  // n_bins x n_edges, seconds
-    uint32_t n_bins;
-    float bin_s;
-
-    TD(const lpsim_assign *a_, const float *tt, uint32_t n_bins_, float bin_s_)
-        : a(a_), tbm((size_t)n_bins_ * a_->n_edges), n_bins(n_bins_), bin_s(bin_s_) {
-        const uint32_t ne = a->n_edges;
-        parallel_pieces(ne, [&](uint64_t e0, uint64_t e1, uint64_t) {
-            for (uint64_t e = e0; e < e1; e++)
-                for (uint32_t b = 0; b < n_bins; b++) tbm[(size_t)b * ne + e] = tt[e * n_bins + b];
-        });
-    }
-
-    float cost(uint32_t e, double t) const {
-        int64_t b = (int64_t)std::floor(t / bin_s);
-        if (b < 0) b = 0;
-        if (b >= (int64_t)n_bins) b = n_bins - 1;
-        return tbm[(size_t)b * a->n_edges + e];
-    }
-};
-
 // Time-dependent Dijkstra from s departing at t0.  want[v] == stamp marks the
 // n_want nodes the caller needs; the search stops once all of them are
 // settled (their arrival times and predecessor chains are final then: a
 // settled node's predecessor was settled before it).
-using HeapItem = std::pair<double, uint32_t>;
+using HeapItem = std::pair<uint64_t, uint32_t>;
 
 // Min-heap of (arrival time, node) pairs with four children per node
 // (shallower than a binary heap: fewer levels to sift through per push and
@@ -130,11 +88,13 @@ struct Heap4 {
     }
 };
 
-void td_dijkstra(const TD &td, uint32_t s, double t0, std::vector<double> &arr, std::vector<uint32_t> &pred,
+constexpr uint64_t kUnreached = ~0ull;
+
+void td_dijkstra(const TD &td, uint32_t s, uint64_t t0, std::vector<uint64_t> &arr, std::vector<uint32_t> &pred,
                  std::vector<uint8_t> &done, const std::vector<uint32_t> &want, uint32_t stamp, uint32_t n_want,
                  std::vector<HeapItem> &heap) {
     const lpsim_assign *a = td.a;
-    std::fill(arr.begin(), arr.end(), INFINITY);
+    std::fill(arr.begin(), arr.end(), kUnreached);
     std::fill(pred.begin(), pred.end(), UINT32_MAX);
     std::fill(done.begin(), done.end(), 0);
     // a min-heap on the caller's storage (kept between searches)
@@ -150,7 +110,7 @@ void td_dijkstra(const TD &td, uint32_t s, double t0, std::vector<double> &arr, 
         for (uint32_t j = a->out_off[u]; j < a->out_off[u + 1]; j++) {
             const uint32_t e = a->out_edge[j], v = a->dst[e];
             if (done[v]) continue;
-            const double nt = t + td.cost(e, t);
+            const uint64_t nt = td.arrive(e, t);
             if (nt < arr[v] || (nt == arr[v] && e < pred[v])) {
                 arr[v] = nt;
                 pred[v] = e;
@@ -218,24 +178,15 @@ int lpsim_assign_shortest_paths(lpsim_assign *a, const float *tt, uint32_t n_bin
                                 uint32_t period_steps, uint32_t n_threads, float *t_sp) {
     if (!a || !tt || n_bins == 0 || bin_steps == 0 || period_steps == 0)
         return fail(LPSIM_E_INVALID_ARG, "bad argument");
-    const TD td(a, tt, n_bins, (float)bin_steps * a->dt);
+    const TD td(a, tt, n_bins, bin_steps);
     // group trips by (origin, departure period)
-    std::vector<uint64_t> order(a->n);
-    std::iota(order.begin(), order.end(), 0);
-    auto key = [&](uint64_t j) { return ((uint64_t)a->orig[j] << 32) | (a->dep[j] / period_steps); };
-    std::sort(order.begin(), order.end(), [&](uint64_t x, uint64_t y) {
-        uint64_t kx = key(x), ky = key(y);
-        return kx != ky ? kx < ky : x < y;
-    });
-    std::vector<uint64_t> gstart;
-    for (uint64_t i = 0; i < a->n; i++)
-        if (i == 0 || key(order[i]) != key(order[i - 1])) gstart.push_back(i);
-    gstart.push_back(a->n);
+    std::vector<uint64_t> order, gstart;
+    group_trips(a, period_steps, order, gstart);
     const uint64_t ng = gstart.size() - 1;
     std::atomic<uint64_t> next{0};
     std::atomic<int> bad{0};
     auto worker = [&]() {
-        std::vector<double> arr(a->n_nodes);
+        std::vector<uint64_t> arr(a->n_nodes);
         std::vector<uint32_t> pred(a->n_nodes);
         std::vector<uint8_t> done(a->n_nodes);
         std::vector<uint32_t> want(a->n_nodes, 0);
@@ -248,7 +199,7 @@ int lpsim_assign_shortest_paths(lpsim_assign *a, const float *tt, uint32_t n_bin
             const uint32_t s = a->orig[j0];
             const uint32_t period = a->dep[j0] / period_steps;
             // tree from the middle of the departure period
-            const double t0 = ((double)period + 0.5) * period_steps * a->dt;
+            const uint64_t t0 = period_root_ms(a, period, period_steps);
             // the group's destinations, marked with a stamp unique to the group
             const uint32_t stamp = (uint32_t)g + 1u;
             uint32_t n_want = 0;
@@ -263,7 +214,7 @@ int lpsim_assign_shortest_paths(lpsim_assign *a, const float *tt, uint32_t n_bin
             for (uint64_t i = gstart[g]; i < gstart[g + 1]; i++) {
                 const uint64_t j = order[i];
                 const uint32_t d = a->dest[j];
-                if (!std::isfinite(arr[d]) || d == s) {
+                if (arr[d] == kUnreached || d == s) {
                     bad = 1;
                     continue;
                 }
@@ -276,10 +227,10 @@ int lpsim_assign_shortest_paths(lpsim_assign *a, const float *tt, uint32_t n_bin
                 a->cand[j].assign(tmp.rbegin(), tmp.rend());
                 // the tree's path, timed from the trip's own departure (the
                 // same start as its experienced time)
-                const double tj = (double)a->dep[j] * a->dt;
-                double tt_j = tj;
-                for (uint32_t e : a->cand[j]) tt_j += td.cost(e, tt_j);
-                a->tsp[j] = (float)(tt_j - tj);
+                const uint64_t tj = to_ms((double)a->dep[j] * a->dt);
+                uint64_t tt_j = tj;
+                for (uint32_t e : a->cand[j]) tt_j = td.arrive(e, tt_j);
+                a->tsp[j] = (float)((double)(tt_j - tj) / 1000.0);
             }
         }
     };
@@ -340,13 +291,13 @@ int lpsim_assign_reroute(lpsim_assign *a, double fraction, uint32_t iteration, u
 
 int lpsim_assign_route_excess(lpsim_assign *a, const float *tt, uint32_t n_bins, uint32_t bin_steps) {
     if (!a || !tt || n_bins == 0 || bin_steps == 0) return fail(LPSIM_E_INVALID_ARG, "bad argument");
-    const TD td(a, tt, n_bins, (float)bin_steps * a->dt);
+    const TD td(a, tt, n_bins, bin_steps);
     parallel_pieces(a->n, [&](uint64_t j0, uint64_t j1, uint64_t) {
         for (uint64_t j = j0; j < j1; j++) {
-            const double t0 = (double)a->dep[j] * a->dt;
-            double t = t0;
-            for (uint32_t e : a->route[j]) t += td.cost(e, t);
-            a->excess[j] = (float)(t - t0 - a->tsp[j]);
+            const uint64_t t0 = to_ms((double)a->dep[j] * a->dt);
+            uint64_t t = t0;
+            for (uint32_t e : a->route[j]) t = td.arrive(e, t);
+            a->excess[j] = (float)((double)(t - t0) / 1000.0 - a->tsp[j]);
         }
     });
     return LPSIM_OK;
@@ -395,16 +346,15 @@ int lpsim_assign_get_routes(const lpsim_assign *a, uint64_t *route_off, uint32_t
 
 int lpsim_assign_load(const lpsim_assign *a, const float *tt, uint32_t n_bins, uint32_t bin_steps, uint32_t *inflow) {
     if (!a || !tt || !inflow || n_bins == 0 || bin_steps == 0) return fail(LPSIM_E_INVALID_ARG, "bad argument");
-    const TD td(a, tt, n_bins, (float)bin_steps * a->dt);
+    const TD td(a, tt, n_bins, bin_steps);
     std::memset(inflow, 0, (size_t)a->n_edges * n_bins * 4);
     parallel_pieces(a->n, [&](uint64_t j0, uint64_t j1, uint64_t) {
         for (uint64_t j = j0; j < j1; j++) {
-            double t = (double)a->dep[j] * a->dt;
+            uint64_t t = to_ms((double)a->dep[j] * a->dt);
             for (uint32_t e : a->route[j]) {
-                int64_t b = (int64_t)std::floor(t / td.bin_s);
-                if (b >= 0 && b < (int64_t)n_bins)
-                    __atomic_fetch_add(&inflow[(size_t)e * n_bins + b], 1u, __ATOMIC_RELAXED);
-                t += td.cost(e, t);
+                const uint64_t b = t / td.bin_ms;
+                if (b < n_bins) __atomic_fetch_add(&inflow[(size_t)e * n_bins + b], 1u, __ATOMIC_RELAXED);
+                t = td.arrive(e, t);
             }
         }
     });

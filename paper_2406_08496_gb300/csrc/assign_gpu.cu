@@ -1,0 +1,467 @@
+// Time-dependent shortest paths of the assignment loop on the GPU.
+//
+// The assignment loop (method of successive averages around the simulator)
+// needs, every iteration, the earliest-arrival path of every trip under the
+// link times of that iteration: routing is the step upstream of the
+// simulation ("after the routing", Sec. 3.1), and re-routing between
+// simulations is the paper's stated next step (Sec. 5).  Trips with the same
+// origin and 30-minute departure period share one tree rooted at the middle
+// of the period; at the regional scale that is some 10^5 trees per iteration
+// on a 224k-node graph, far more than the host's threads finish in seconds.
+//
+// Here every tree is searched by one warp, thousands of warps at a time (a
+// tree's frontier is a wave of a few hundred nodes; many trees in flight
+// hide the memory latency each relaxation pays):
+//   * label-correcting search in rounds: the frontier's nodes relax their
+//     out-edges with the arrival function of the bin holding their arrival
+//     time (FIFO by construction, see TD), and a node whose label improved
+//     joins the next round's frontier (once: a per-node round stamp);
+//   * a label is (arrival ms << 32 | entering edge id) in one 64-bit word,
+//     so atomicMin keeps the earliest arrival and, among equal arrivals, the
+//     lower edge id -- the fixed point is exactly the tree the host's
+//     Dijkstra builds (lpsim_assign_shortest_paths), with integer millisecond
+//     link times making every arrival an exact sum;
+//   * once every destination of the group has a label, the latest of them
+//     bounds the search: a node reached later than it cannot lie on any of
+//     their paths (link times are positive), so it is not expanded;
+//   * each trip's path is read back along the entering edges, written to the
+//     output in travel order and timed from the trip's own departure;
+//   * the labels the tree set are reset from its list of reached nodes, so a
+//     warp's workspace is reused without clearing the whole graph.
+// Every loop is bounded (rounds and path walks by the node count); a bound
+// that is hit sets an error bit the host reports.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lpsim_assign.h"
+#include "assign_internal.h"
+#include "host_par.h"
+
+int lpsim_fail(int code, const std::string &msg);
+
+using namespace lpsim_assign_detail;
+
+namespace {
+
+int fail(int code, const std::string &m) { return lpsim_fail(code, m); }
+
+#define CU(call)                                                                                      \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess) return fail(LPSIM_E_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+constexpr uint64_t kUnreached = ~0ull;
+constexpr uint32_t kNoEdge = 0xFFFFFFFFu;
+constexpr int kWarpsPerBlock = 4;
+constexpr int kBlocksPerSm = 4;                      // 16 warps (trees) per SM
+constexpr uint64_t kWorkspaceBudget = 16ull << 30;   // bytes of per-warp workspaces at most
+
+// error bits
+constexpr uint32_t kErrUnreachable = 1u;  // a destination not reached (or equal to its origin)
+constexpr uint32_t kErrCapacity = 2u;     // the path buffer was too small (the host retries)
+constexpr uint32_t kErrBound = 4u;        // a round or path-walk bound was hit
+
+struct GroupRec {
+    uint32_t src;    // origin node
+    uint32_t t0;     // root time (ms)
+    uint32_t first;  // first position in the trip order
+    uint32_t count;  // trips
+};
+
+struct TreeArgs {
+    uint32_t n_nodes, n_edges, n_bins, bin_ms;
+    const uint32_t *out_off;  // n_nodes + 1
+    const uint2 *adj;         // per out-edge position: {edge, head node}
+    const uint32_t *src;      // per edge: tail node
+    const uint2 *cms;         // n_bins x n_edges: {link time ms, earliest arrival entering a later bin ms}
+    uint32_t n_groups;
+    const GroupRec *groups;
+    const uint32_t *order;    // trip per position, group by group
+    const uint32_t *dest;     // per trip
+    const uint32_t *dep_ms;   // per trip: planned departure (ms)
+    // outputs per trip
+    unsigned long long *path_off;
+    uint32_t *path_len;
+    float *tsp;
+    uint32_t *edges;          // path edges, travel order
+    unsigned long long cap;   // entries of edges
+    unsigned long long *cursor;
+    // per-warp workspaces
+    uint64_t *lab;            // n_warps x n_nodes
+    uint32_t *inq;            // n_warps x n_nodes: round stamp of the last push
+    uint32_t *touched;        // n_warps x n_nodes
+    uint32_t *fa, *fb;        // n_warps x n_nodes: frontiers
+    uint32_t *stamp;          // per warp: last round stamp used
+    uint32_t *next_group;
+    uint32_t *err;
+};
+
+__device__ __forceinline__ uint32_t bin_of(const TreeArgs &A, uint64_t t) {
+    const uint64_t b = t / A.bin_ms;
+    return b < A.n_bins ? (uint32_t)b : A.n_bins - 1u;
+}
+
+// arrival when entering edge e at time t (ms): min(t + c, M) of t's bin
+__device__ __forceinline__ uint64_t arrive(const uint2 lt, uint64_t t) {
+    const uint64_t a = t + lt.x;
+    return a < (uint64_t)lt.y ? a : (uint64_t)lt.y;
+}
+
+// Latest current arrival over the group's destinations (its trips'), or
+// kUnreached while any is unreached; every lane gets the result.
+__device__ __forceinline__ uint64_t dest_bound(const TreeArgs &A, const GroupRec &G, const uint64_t *lab,
+                                               uint32_t lane) {
+    uint64_t m = 0;
+    for (uint32_t q = lane; q < G.count; q += 32) {
+        const uint64_t l = __ldcg(reinterpret_cast<const unsigned long long *>(lab + A.dest[A.order[G.first + q]]));
+        const uint64_t t = l == kUnreached ? kUnreached : (l >> 32);
+        m = t > m ? t : m;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t y = __shfl_xor_sync(0xFFFFFFFFu, m, o);
+        m = y > m ? y : m;
+    }
+    return m;
+}
+
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) td_trees(TreeArgs A) {
+    const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+    const size_t gw = (size_t)blockIdx.x * kWarpsPerBlock + wib;
+    uint64_t *lab = A.lab + gw * A.n_nodes;
+    uint32_t *inq = A.inq + gw * A.n_nodes;
+    uint32_t *touched = A.touched + gw * A.n_nodes;
+    uint32_t *fa = A.fa + gw * A.n_nodes, *fb = A.fb + gw * A.n_nodes;
+    __shared__ uint32_t s_next[kWarpsPerBlock], s_touched[kWarpsPerBlock];
+    uint32_t stamp = A.stamp[gw];
+    for (;;) {
+        uint32_t g = 0;
+        if (lane == 0) g = atomicAdd(A.next_group, 1u);
+        g = __shfl_sync(0xFFFFFFFFu, g, 0);
+        if (g >= A.n_groups) break;
+        const GroupRec G = A.groups[g];
+        if (lane == 0) {
+            __stcg(reinterpret_cast<unsigned long long *>(lab + G.src), ((uint64_t)G.t0 << 32) | kNoEdge);
+            __stcg(touched, G.src);
+            __stcg(fa, G.src);
+        }
+        uint32_t nf = 1, nt = 1;
+        uint64_t ub = kUnreached;  // latest destination arrival so far (ms), once all are reached
+        __threadfence_block();
+        __syncwarp();
+        bool bounded = true;
+        for (uint32_t round = 0; nf > 0; round++) {
+            if (round > A.n_nodes) {  // a label-correcting search settles within n rounds
+                bounded = false;
+                break;
+            }
+            stamp++;
+            if (lane == 0) {
+                s_next[wib] = 0;
+                s_touched[wib] = nt;
+            }
+            __syncwarp();
+            for (uint32_t i = lane; i < nf; i += 32) {
+                const uint32_t u = __ldcg(fa + i);
+                const uint64_t lu = __ldcg(reinterpret_cast<const unsigned long long *>(lab + u));
+                const uint64_t tu = lu >> 32;
+                if (ub != kUnreached && tu >= ub) continue;
+                const uint2 *crow = A.cms + (size_t)bin_of(A, tu) * A.n_edges;
+                const uint32_t j1 = A.out_off[u + 1];
+                for (uint32_t j = A.out_off[u]; j < j1; j++) {
+                    const uint2 ev = A.adj[j];
+                    const uint64_t at = arrive(crow[ev.x], tu);
+                    if (at > 0xFFFFFFFFull || (ub != kUnreached && at > ub)) continue;
+                    const unsigned long long cand = (at << 32) | ev.x;
+                    const unsigned long long old =
+                        atomicMin(reinterpret_cast<unsigned long long *>(lab + ev.y), cand);
+                    if (cand < old) {
+                        if (old == kUnreached) __stcg(touched + atomicAdd(&s_touched[wib], 1u), ev.y);
+                        if (atomicExch(inq + ev.y, stamp) != stamp) __stcg(fb + atomicAdd(&s_next[wib], 1u), ev.y);
+                    }
+                }
+            }
+            __threadfence_block();
+            __syncwarp();
+            nf = s_next[wib];
+            nt = s_touched[wib];
+            uint32_t *t = fa;
+            fa = fb;
+            fb = t;
+            if ((round & 3u) == 3u) ub = dest_bound(A, G, lab, lane);
+            __syncwarp();
+        }
+        if (!bounded && lane == 0) atomicOr(A.err, kErrBound);
+        // paths of the group's trips, in travel order, timed from each trip's departure
+        for (uint32_t q = lane; q < G.count; q += 32) {
+            const uint32_t j = A.order[G.first + q];
+            const uint32_t d = A.dest[j];
+            A.path_len[j] = 0;
+            const uint64_t ld = __ldcg(reinterpret_cast<const unsigned long long *>(lab + d));
+            if (ld == kUnreached || d == G.src || !bounded) {
+                atomicOr(A.err, kErrUnreachable);
+                continue;
+            }
+            uint32_t L = 0;
+            bool ok = true;
+            for (uint32_t v = d; v != G.src;) {
+                const uint32_t e = (uint32_t)__ldcg(reinterpret_cast<const unsigned long long *>(lab + v));
+                if (++L > A.n_nodes || e >= A.n_edges) {
+                    ok = false;
+                    break;
+                }
+                v = A.src[e];
+            }
+            if (!ok) {
+                atomicOr(A.err, kErrBound);
+                continue;
+            }
+            const unsigned long long off = atomicAdd(A.cursor, (unsigned long long)L);
+            if (off + L > A.cap) {
+                atomicOr(A.err, kErrCapacity);
+                continue;
+            }
+            uint32_t pos = L;
+            for (uint32_t v = d; v != G.src && pos > 0;) {
+                const uint32_t e = (uint32_t)__ldcg(reinterpret_cast<const unsigned long long *>(lab + v));
+                A.edges[off + --pos] = e;  // e < n_edges: the counting walk checked this chain
+                v = A.src[e];
+            }
+            const uint64_t tj = A.dep_ms[j];
+            uint64_t t = tj;
+            for (uint32_t p = 0; p < L; p++) t = arrive(A.cms[(size_t)bin_of(A, t) * A.n_edges + A.edges[off + p]], t);
+            A.path_off[j] = off;
+            A.path_len[j] = L;
+            A.tsp[j] = (float)((double)(t - tj) / 1000.0);
+        }
+        // clear the labels this tree set
+        __syncwarp();
+        for (uint32_t i = lane; i < nt; i += 32)
+            __stcg(reinterpret_cast<unsigned long long *>(lab + __ldcg(touched + i)), (unsigned long long)kUnreached);
+        __threadfence_block();
+        __syncwarp();
+    }
+    if (lane == 0) A.stamp[gw] = stamp;
+}
+
+}  // namespace
+
+// Device copy of the graph, the trip table and the search workspaces.
+struct AssignGpu {
+    int device = -1;
+    int n_sm = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<void *> blocks;
+    uint32_t n_warps = 0;
+    TreeArgs A{};
+    uint32_t period_steps = 0;  // grouping held in A.groups / A.order
+    std::vector<uint64_t> order, gstart;
+    unsigned long long cap = 0;
+
+    void *alloc(size_t bytes) {
+        void *p = nullptr;
+        if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) return nullptr;
+        blocks.push_back(p);
+        return p;
+    }
+    void release(void *p) {
+        auto it = std::find(blocks.begin(), blocks.end(), p);
+        if (it != blocks.end()) {
+            blocks.erase(it);
+            cudaFree(p);
+        }
+    }
+    ~AssignGpu() {
+        if (stream) cudaStreamSynchronize(stream);
+        for (void *b : blocks) cudaFree(b);
+        if (stream) cudaStreamDestroy(stream);
+    }
+};
+
+void assign_gpu_free(AssignGpu *g) { delete g; }
+
+namespace {
+
+template <class T>
+int dput(AssignGpu *g, T *&dst, const T *src, size_t count) {
+    dst = static_cast<T *>(g->alloc(count * sizeof(T)));
+    if (!dst) return fail(LPSIM_E_OOM, "device allocation of " + std::to_string(count * sizeof(T)) + " bytes failed");
+    if (count) CU(cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyHostToDevice, g->stream));
+    return LPSIM_OK;
+}
+
+#define TRY(x)                           \
+    do {                                 \
+        int rc_ = (x);                   \
+        if (rc_ != LPSIM_OK) return rc_; \
+    } while (0)
+
+// graph, trips and workspaces (first call)
+int gpu_setup(lpsim_assign *a) {
+    auto *g = new (std::nothrow) AssignGpu();
+    if (!g) return fail(LPSIM_E_OOM, "host allocation failed");
+    a->gpu = g;
+    CU(cudaGetDevice(&g->device));
+    CU(cudaDeviceGetAttribute(&g->n_sm, cudaDevAttrMultiProcessorCount, g->device));
+    CU(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
+    if (a->n >= 0xFFFFFFFFull) return fail(LPSIM_E_INVALID_ARG, "too many trips for the GPU search");
+    TreeArgs &A = g->A;
+    A.n_nodes = a->n_nodes;
+    A.n_edges = a->n_edges;
+    std::vector<uint2> adj(a->n_edges);
+    for (uint32_t j = 0; j < a->n_edges; j++) adj[j] = make_uint2(a->out_edge[j], a->dst[a->out_edge[j]]);
+    std::vector<uint32_t> dep_ms(a->n);
+    for (uint64_t j = 0; j < a->n; j++) {
+        const uint64_t t = to_ms((double)a->dep[j] * a->dt);
+        if (t > 0xFFFFFFFFull) return fail(LPSIM_E_INVALID_ARG, "departure beyond the 32-bit millisecond range");
+        dep_ms[j] = (uint32_t)t;
+    }
+    uint32_t *oo, *sr, *de, *dm;
+    uint2 *ad;
+    TRY(dput(g, oo, a->out_off.data(), a->out_off.size()));
+    TRY(dput(g, ad, adj.data(), adj.size()));
+    TRY(dput(g, sr, a->src.data(), a->src.size()));
+    TRY(dput(g, de, a->dest.data(), a->dest.size()));
+    TRY(dput(g, dm, dep_ms.data(), dep_ms.size()));
+    A.out_off = oo;
+    A.adj = ad;
+    A.src = sr;
+    A.dest = de;
+    A.dep_ms = dm;
+    A.path_off = static_cast<unsigned long long *>(g->alloc(a->n * 8));
+    A.path_len = static_cast<uint32_t *>(g->alloc(a->n * 4));
+    A.tsp = static_cast<float *>(g->alloc(a->n * 4));
+    A.cursor = static_cast<unsigned long long *>(g->alloc(8));
+    A.next_group = static_cast<uint32_t *>(g->alloc(4));
+    A.err = static_cast<uint32_t *>(g->alloc(4));
+    if (!A.path_off || !A.path_len || !A.tsp || !A.cursor || !A.next_group || !A.err)
+        return fail(LPSIM_E_OOM, "device allocation failed");
+    // workspaces: as many warps as fit the budget, at most 16 per SM
+    const uint64_t per_warp = (uint64_t)a->n_nodes * (8 + 4 * 4);
+    uint64_t warps = std::min<uint64_t>((uint64_t)g->n_sm * kBlocksPerSm * kWarpsPerBlock,
+                                        std::max<uint64_t>(kWorkspaceBudget / std::max<uint64_t>(per_warp, 1), 1));
+    warps = std::max<uint64_t>(kWarpsPerBlock, warps / kWarpsPerBlock * kWarpsPerBlock);
+    g->n_warps = (uint32_t)warps;
+    const size_t nn = (size_t)warps * a->n_nodes;
+    A.lab = static_cast<uint64_t *>(g->alloc(nn * 8));
+    A.inq = static_cast<uint32_t *>(g->alloc(nn * 4));
+    A.touched = static_cast<uint32_t *>(g->alloc(nn * 4));
+    A.fa = static_cast<uint32_t *>(g->alloc(nn * 4));
+    A.fb = static_cast<uint32_t *>(g->alloc(nn * 4));
+    A.stamp = static_cast<uint32_t *>(g->alloc(warps * 4));
+    if (!A.lab || !A.inq || !A.touched || !A.fa || !A.fb || !A.stamp)
+        return fail(LPSIM_E_OOM, "device allocation of the search workspaces failed");
+    CU(cudaMemsetAsync(A.lab, 0xFF, nn * 8, g->stream));
+    CU(cudaMemsetAsync(A.inq, 0, nn * 4, g->stream));
+    CU(cudaMemsetAsync(A.stamp, 0, warps * 4, g->stream));
+    CU(cudaStreamSynchronize(g->stream));
+    return LPSIM_OK;
+}
+
+// trip groups of a departure period length (kept between calls)
+int gpu_groups(lpsim_assign *a, uint32_t period_steps) {
+    AssignGpu *g = a->gpu;
+    if (g->period_steps == period_steps) return LPSIM_OK;
+    group_trips(a, period_steps, g->order, g->gstart);
+    const uint64_t ng = g->gstart.size() - 1;
+    std::vector<GroupRec> recs(ng);
+    std::vector<uint32_t> ord(a->n);
+    for (uint64_t i = 0; i < a->n; i++) ord[i] = (uint32_t)g->order[i];
+    for (uint64_t q = 0; q < ng; q++) {
+        const uint64_t j0 = g->order[g->gstart[q]];
+        const uint64_t t0 = period_root_ms(a, a->dep[j0] / period_steps, period_steps);
+        if (t0 > 0xFFFFFFFFull) return fail(LPSIM_E_INVALID_ARG, "departure period beyond the millisecond range");
+        recs[q] = GroupRec{a->orig[j0], (uint32_t)t0, (uint32_t)g->gstart[q],
+                           (uint32_t)(g->gstart[q + 1] - g->gstart[q])};
+    }
+    if (g->A.groups) g->release(const_cast<GroupRec *>(g->A.groups));
+    if (g->A.order) g->release(const_cast<uint32_t *>(g->A.order));
+    GroupRec *dg;
+    uint32_t *dord;
+    TRY(dput(g, dg, recs.data(), recs.size()));
+    TRY(dput(g, dord, ord.data(), ord.size()));
+    g->A.groups = dg;
+    g->A.order = dord;
+    g->A.n_groups = (uint32_t)ng;
+    g->period_steps = period_steps;
+    return LPSIM_OK;
+}
+
+}  // namespace
+
+extern "C" int lpsim_assign_shortest_paths_gpu(lpsim_assign *a, const float *tt, uint32_t n_bins, uint32_t bin_steps,
+                                               uint32_t period_steps, float *t_sp) {
+    if (!a || !tt || n_bins == 0 || bin_steps == 0 || period_steps == 0)
+        return fail(LPSIM_E_INVALID_ARG, "bad argument");
+    if (a->n == 0) return LPSIM_OK;
+    if (!a->gpu) TRY(gpu_setup(a));
+    AssignGpu *g = a->gpu;
+    int dev = -1;
+    CU(cudaGetDevice(&dev));
+    if (dev != g->device) return fail(LPSIM_E_STATE, "the device current at the first GPU search must be current");
+    TRY(gpu_groups(a, period_steps));
+    TreeArgs &A = g->A;
+    // link times in whole milliseconds, bin-major (the host searches' table)
+    const TD td(a, tt, n_bins, bin_steps);
+    if (td.bin_ms > 0xFFFFFFFFull) return fail(LPSIM_E_INVALID_ARG, "bin longer than the 32-bit millisecond range");
+    static_assert(sizeof(LinkTime) == sizeof(uint2), "link-time record");
+    if (A.cms && A.n_bins != n_bins) {
+        g->release(const_cast<uint2 *>(A.cms));
+        A.cms = nullptr;
+    }
+    if (!A.cms) {
+        A.cms = static_cast<uint2 *>(g->alloc(td.tbm.size() * sizeof(uint2)));
+        if (!A.cms) return fail(LPSIM_E_OOM, "device allocation of the link-time table failed");
+    }
+    CU(cudaMemcpyAsync(const_cast<uint2 *>(A.cms), td.tbm.data(), td.tbm.size() * sizeof(uint2),
+                       cudaMemcpyHostToDevice, g->stream));
+    A.n_bins = n_bins;
+    A.bin_ms = (uint32_t)td.bin_ms;
+    // path buffer: room for the current routes' length and half as much again
+    if (!g->cap) {
+        uint64_t total = 0;
+        for (auto &r : a->route) total += r.size();
+        g->cap = std::max<uint64_t>(total + total / 2, 1u << 20);
+        A.edges = static_cast<uint32_t *>(g->alloc(g->cap * 4));
+        if (!A.edges) return fail(LPSIM_E_OOM, "device allocation of the path buffer failed");
+    }
+    unsigned long long used = 0;
+    uint32_t err = 0;
+    for (int attempt = 0; attempt < 3; attempt++) {
+        A.cap = g->cap;
+        CU(cudaMemsetAsync(A.cursor, 0, 8, g->stream));
+        CU(cudaMemsetAsync(A.next_group, 0, 4, g->stream));
+        CU(cudaMemsetAsync(A.err, 0, 4, g->stream));
+        td_trees<<<g->n_warps / kWarpsPerBlock, kWarpsPerBlock * 32, 0, g->stream>>>(A);
+        CU(cudaGetLastError());
+        CU(cudaMemcpyAsync(&used, A.cursor, 8, cudaMemcpyDeviceToHost, g->stream));
+        CU(cudaMemcpyAsync(&err, A.err, 4, cudaMemcpyDeviceToHost, g->stream));
+        CU(cudaStreamSynchronize(g->stream));
+        if (!(err & kErrCapacity)) break;
+        // the paths did not fit: a buffer of the length they asked for, and again
+        g->release(A.edges);
+        g->cap = used + used / 4 + 1024;
+        A.edges = static_cast<uint32_t *>(g->alloc(g->cap * 4));
+        if (!A.edges) return fail(LPSIM_E_OOM, "device allocation of the path buffer failed");
+    }
+    if (err & kErrBound) return fail(LPSIM_E_INVARIANT, "GPU path search exceeded its round or path-length bound");
+    if (err & kErrUnreachable) return fail(LPSIM_E_INVALID_ARG, "a destination is unreachable from its origin");
+    if (err & kErrCapacity) return fail(LPSIM_E_OOM, "path buffer still too small after resizing");
+    std::vector<unsigned long long> off(a->n);
+    std::vector<uint32_t> len(a->n), edges(used);
+    CU(cudaMemcpyAsync(off.data(), A.path_off, a->n * 8, cudaMemcpyDeviceToHost, g->stream));
+    CU(cudaMemcpyAsync(len.data(), A.path_len, a->n * 4, cudaMemcpyDeviceToHost, g->stream));
+    CU(cudaMemcpyAsync(a->tsp.data(), A.tsp, a->n * 4, cudaMemcpyDeviceToHost, g->stream));
+    if (used) CU(cudaMemcpyAsync(edges.data(), A.edges, used * 4, cudaMemcpyDeviceToHost, g->stream));
+    CU(cudaStreamSynchronize(g->stream));
+    lpsim::parallel_pieces(a->n, [&](uint64_t j0, uint64_t j1, uint64_t) {
+        for (uint64_t j = j0; j < j1; j++) a->cand[j].assign(edges.begin() + off[j], edges.begin() + off[j] + len[j]);
+    });
+    if (t_sp) std::memcpy(t_sp, a->tsp.data(), a->n * 4);
+    return LPSIM_OK;
+}

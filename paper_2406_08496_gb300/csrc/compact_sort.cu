@@ -26,6 +26,7 @@ __device__ __forceinline__ uint32_t n_src(const SortWork &w) { return w.tile_off
 
 // live slots per tile; arrived slots get their last cell erased here
 __global__ void __launch_bounds__(kBlock) tile_count(Dev d, SortWork w, uint32_t koff) {
+    span_start(d, 3 * koff + 2);
     const uint32_t k = *d.kbase + koff;
     const uint32_t n = *d.n_slots;
     const uint32_t ntiles = (n + kTile - 1) / kTile;
@@ -159,6 +160,7 @@ __global__ void __launch_bounds__(kBlock) scatter_slots(Dev d, Slots dst, SortWo
         for (int j = 0; j < kItems; j++)
             if (live[j]) copy_slot(d.s, t * kTile + threadIdx.x * kItems + j, dst, off + rank[j], par);
     }
+    span_end(d, 3 * koff + 2);
 }
 
 // sort keys: the cell each live vehicle occupies in the map of step k+1
@@ -291,6 +293,7 @@ __global__ void __launch_bounds__(kBlock) gather_slots(Dev d, Slots dst, SortWor
     const int par = (k + 1) & 1;
     for (uint32_t i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock)
         copy_slot(d.s, w.perm[in][i], dst, i, par);
+    span_end(d, 3 * koff + 2);
 }
 
 }  // namespace

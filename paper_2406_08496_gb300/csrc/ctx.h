@@ -67,12 +67,11 @@ struct lpsim_ctx {
     } snap_host{};
     // batched scenarios: prefix offsets of nodes, edges, canonical lane-map cells and trips
     std::vector<uint64_t> scen_node_off, scen_edge_off, scen_cell_off, scen_trip_off;
-    // per-kernel timing (events around every phase launch of every step)
+    // per-kernel timing: device spans stamped by the kernels themselves
+    // (d.tspan, d.tacc; see lpsim_dev.cuh), room for tspan_steps steps
     bool timing = false;
-    std::vector<cudaEvent_t> ev;     // 5 per step of a chunk
-    double t_ms[3] = {0, 0, 0};   // step_p1, step_p2, compaction + sort
-    uint64_t t_n[3] = {0, 0, 0};
-    std::string t_err;               // first failure of cudaEventElapsedTime
+    unsigned long long *tspan_buf = nullptr;  // d.tspan while timing is on
+    uint32_t tspan_steps = 0;
 
     void *dalloc(size_t bytes) {
         if (bytes == 0) bytes = 16;
@@ -89,7 +88,6 @@ struct lpsim_ctx {
     ~lpsim_ctx() {
         for (int i = 0; i < 2; i++)
             if (graph[i]) cudaGraphExecDestroy(graph[i]);
-        for (cudaEvent_t e : ev) cudaEventDestroy(e);
         if (stream) cudaStreamSynchronize(stream);
         for (void *b : blocks) {
             if (release) release(b, alloc_user);

@@ -235,8 +235,38 @@ struct Dev {
                                // [4] departed
     uint32_t *err;
     uint32_t check;            // 1: verify every next-map write lands on an empty cell
+    // Kernel timing (nullptr when off): per step koff of a chunk, the span of
+    // each phase as {~first block start, last block end} in %globaltimer
+    // nanoseconds -- tspan[6 koff + 2 ph], ph 0 step_p1, 1 step_p2, 2 the
+    // compaction sequence -- and {~start, end} of the light-load kernel at
+    // tspan[6 C]; the start is stored inverted so that atomicMax over a
+    // zeroed slot keeps the earliest.  timing_fold adds the spans into
+    // tacc: [0..3] ns of step_p1, step_p2, compaction, light-load kernel,
+    // [4..7] their launches, [8] vehicle-steps handled by step_p1.
+    unsigned long long *tspan, *tacc;
+    uint32_t tspan_light;      // index of the light-load kernel's pair (6 C)
     Model m;
 };
+
+// %globaltimer (nanoseconds, one clock for the whole GPU)
+__device__ __forceinline__ unsigned long long gtime() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Start and end stamps of a kernel's span in slot pair `pair` (timing only;
+// one thread per block; the end stamp after a block barrier, so the block's
+// last thread has finished).
+__device__ __forceinline__ void span_start(const Dev &d, uint32_t pair) {
+    if (d.tspan && threadIdx.x == 0) atomicMax(&d.tspan[2 * pair], ~gtime());
+}
+__device__ __forceinline__ void span_end(const Dev &d, uint32_t pair) {
+    if (d.tspan) {
+        __syncthreads();
+        if (threadIdx.x == 0) atomicMax(&d.tspan[2 * pair + 1], gtime());
+    }
+}
 
 // kernels of a step; koff = offset of this step inside the chunk (step k =
 // *kbase + koff); kph = any number congruent to k modulo 6, known when the
@@ -247,6 +277,9 @@ void launch_phase(const Dev &d, int phase, uint32_t koff, uint32_t kph, int grid
 void launch_chunk_end(const Dev &d, uint32_t steps, cudaStream_t st);
 // the logged crossings of the chunk into the link statistics (before chunk_end)
 void launch_apply_crossings(const Dev &d, int grid, cudaStream_t st);
+// kernel timing: the spans of steps [0, nsteps) of the chunk (and of the
+// light-load kernel) into the accumulators; clears the span slots
+void launch_timing_fold(const Dev &d, uint32_t nsteps, cudaStream_t st);
 // steps [k0, k0 + nsteps) in one block (light load); olist: n_org scratch
 // entries, no: one device counter
 cudaError_t launch_small(const Dev &d, uint32_t k0, uint32_t nsteps, uint32_t *olist, uint32_t *no,

@@ -911,6 +911,25 @@ int refresh_weights(lpsim_mlp *m) {
     return LPSIM_OK;
 }
 
+// One Adam step (Kingma and Ba 2015, Algorithm 1) with the gradients in G[]:
+// beta1 0.9, beta2 0.999, eps 1e-8 as FP32 constants; the bias corrections
+// 1 - beta^t are formed in double from those FP32 values and rounded once
+// (in float arithmetic 1 - beta2^t loses most of its digits to cancellation);
+// then the BF16 weight copies are refreshed.
+int adam_step(lpsim_mlp *m, float lr) {
+    m->adam_t++;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float c1 = (float)(1.0 - std::pow((double)b1, (double)m->adam_t));
+    const float c2 = (float)(1.0 - std::pow((double)b2, (double)m->adam_t));
+    for (int i = 0; i < 8; i++) {
+        adam_update<<<(m->sz[i] + 255) / 256, 256, 0, m->stream>>>(m->P[i], m->G[i], m->Mo[i], m->Ve[i], m->sz[i], lr,
+                                                                  b1, b2, eps, c1, c2);
+        m->launches++;
+    }
+    CU(cudaGetLastError());
+    return refresh_weights(m);
+}
+
 // forward of rows [0, B) already packed in X0; keep = training buffers
 // training keeps the pre-activations (for GELU') and transposed activations
 // (for the weight gradients); inference writes only the activations
@@ -1208,14 +1227,7 @@ int lpsim_mlp_train(lpsim_mlp *m, uint64_t n, const float *X, const float *t, ui
         TRY(forward_batch(m));
         CU(cudaMemsetAsync(m->loss_acc, 0, 4, m->stream));
         TRY(backward_batch(m, (int)nb));
-        m->adam_t++;
-        const float c1 = 1.0f - std::pow(0.9f, (float)m->adam_t), c2 = 1.0f - std::pow(0.999f, (float)m->adam_t);
-        for (int i = 0; i < 8; i++) {
-            adam_update<<<(m->sz[i] + 255) / 256, 256, 0, m->stream>>>(m->P[i], m->G[i], m->Mo[i], m->Ve[i], m->sz[i],
-                                                                      lr, 0.9f, 0.999f, 1e-8f, c1, c2);
-            m->launches++;
-        }
-        TRY(refresh_weights(m));
+        TRY(adam_step(m, lr));
         if (losses) {
             float l = 0.0f;
             CU(cudaMemcpyAsync(&l, m->loss_acc, 4, cudaMemcpyDeviceToHost, m->stream));
@@ -1225,6 +1237,18 @@ int lpsim_mlp_train(lpsim_mlp *m, uint64_t n, const float *X, const float *t, ui
     }
     CU(cudaStreamSynchronize(m->stream));
     return mlp_check_err(m);
+}
+
+int lpsim_mlp_apply_grads(lpsim_mlp *m, const float *const *grads, float lr) {
+    if (!m || !grads) return fail(LPSIM_E_INVALID_ARG, "NULL argument");
+    if (!(lr >= 0.0f) || !std::isfinite(lr)) return fail(LPSIM_E_INVALID_ARG, "lr must be finite and >= 0");
+    for (int i = 0; i < 8; i++)
+        if (!grads[i]) return fail(LPSIM_E_INVALID_ARG, "gradient tensor is NULL");
+    CU(cudaStreamSynchronize(m->stream));
+    for (int i = 0; i < 8; i++) CU(cudaMemcpyAsync(m->G[i], grads[i], m->sz[i] * 4, cudaMemcpyHostToDevice, m->stream));
+    TRY(adam_step(m, lr));
+    CU(cudaStreamSynchronize(m->stream));
+    return LPSIM_OK;
 }
 
 int lpsim_mlp_gemm_test(uint32_t M, uint32_t N, uint32_t K, const uint16_t *A, const uint16_t *B, float *D) {

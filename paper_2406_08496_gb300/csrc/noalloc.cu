@@ -14,6 +14,8 @@
 #include <mutex>
 #include <string>
 
+#include <cuda.h>
+
 #include "../../include/lpsim.h"
 #include "ctx.h"
 #include "lpsim_dev.cuh"
@@ -29,23 +31,57 @@ static __device__ __align__(256) unsigned char g_state_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-void *g_scratch[kMaxDevices] = {};
+// per device: the scratch array's device address and the context it belongs to
+struct ScratchAddr {
+    void *ptr;
+    unsigned long long ctx_id;
+};
+ScratchAddr g_scratch[kMaxDevices] = {};
 
 int fail(int code, const std::string &m) { return lpsim_fail(code, m); }
 
-// Device address of the scratch array on the current device (set up once per
-// device; cudaGetSymbolAddress gives the address the kernels can use).
+// Unique id of the current context (driver entry points looked up through the
+// runtime, so the library does not link the driver library).  0 if unknown.
+unsigned long long current_context_id() {
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(fn);
+        fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(fn);
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Device address of the scratch array on the current device.  Set up once
+// per device and context: cudaGetSymbolAddress gives the address the kernels
+// can use; a new context on the device (after cudaDeviceReset, say) holds the
+// array at a new address, so a change of context id repeats the look-up.
 int scratch_address(int dev, void **out) {
     if (dev < 0 || dev >= kMaxDevices) return fail(LPSIM_E_STATE, "device index out of range");
+    const unsigned long long id = current_context_id();
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch[dev]) {
+    if (!g_scratch[dev].ptr || id == 0 || g_scratch[dev].ctx_id != id) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_state_scratch);
         if (e != cudaSuccess || !p)
             return fail(LPSIM_E_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
-        g_scratch[dev] = p;
+        g_scratch[dev] = ScratchAddr{p, id};
     }
-    *out = g_scratch[dev];
+    *out = g_scratch[dev].ptr;
     return LPSIM_OK;
 }
 

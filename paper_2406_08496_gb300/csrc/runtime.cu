@@ -162,50 +162,19 @@ int read_status(lpsim_ctx *c) {
     return LPSIM_OK;
 }
 
-// The kernels of step `koff` of a chunk (or of a direct step, koff = 0),
-// with timing events around each phase when timing is on.  Returns the slot
-// set current after the step.
+// The kernels of step `koff` of a chunk (or of a direct step, koff = 0).
+// Returns the slot set current after the step.  (With kernel timing on, the
+// kernels stamp their own spans; nothing is inserted between them, so the
+// graph keeps its programmatic dependent launches.)
 int enqueue_step(lpsim_ctx *c, uint32_t koff, uint32_t kph, int cur, bool compact) {
     Dev d = c->d;
     d.s = c->sets[cur];
-    cudaEvent_t *e = c->timing ? &c->ev[4 * koff] : nullptr;
-    // cudaEventRecordExternal: inside a stream capture the record becomes an
-    // event-record node that timestamps when the graph runs (the flag is for
-    // captures only; a direct step records plainly)
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (e) cudaStreamIsCapturing(c->stream, &cs);
-    const unsigned flags = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
-    for (int ph = 1; ph <= 2; ph++) {
-        if (e) cudaEventRecordWithFlags(e[ph - 1], c->stream, flags);
-        launch_phase(d, ph, koff, kph, c->grid, c->block, c->stream);
-    }
-    if (e) cudaEventRecordWithFlags(e[2], c->stream, flags);
+    for (int ph = 1; ph <= 2; ph++) launch_phase(d, ph, koff, kph, c->grid, c->block, c->stream);
     if (compact) {
         launch_compact(d, c->sets[cur ^ 1], c->w, koff, c->sort, c->grid, c->stream);
         cur ^= 1;
-        if (e) cudaEventRecordWithFlags(e[3], c->stream, flags);
     }
     return cur;
-}
-
-// add the event times of steps [0, n) of the last chunk (after a sync)
-void collect_times(lpsim_ctx *c, uint32_t n, uint64_t k_first) {
-    if (!c->timing) return;
-    for (uint32_t j = 0; j < n; j++) {
-        cudaEvent_t *e = &c->ev[4 * j];
-        float ms = 0.0f;
-        for (int ph = 0; ph < 3; ph++) {
-            if (ph == 2 && (k_first + j + 1) % c->R != 0) break;
-            cudaError_t r = cudaEventElapsedTime(&ms, e[ph], e[ph + 1]);
-            if (r == cudaSuccess) {
-                c->t_ms[ph] += ms;
-                c->t_n[ph] += 1;
-            } else if (c->t_err.empty()) {
-                c->t_err = std::string("cudaEventElapsedTime: ") + cudaGetErrorString(r);
-                cudaGetLastError();
-            }
-        }
-    }
 }
 
 // one step launched directly (kbase == k on entry; kbase == k+1 after)
@@ -217,11 +186,8 @@ int direct_step(lpsim_ctx *c) {
     launch_apply_crossings(c->d, c->grid, c->stream);
     launch_chunk_end(c->d, 1, c->stream);
     c->launches += 2;
+    if (c->d.tspan) launch_timing_fold(c->d, 1, c->stream);
     CU(cudaGetLastError());
-    if (c->timing) {
-        CU(cudaStreamSynchronize(c->stream));
-        collect_times(c, 1, c->k);
-    }
     c->k += 1;
     return LPSIM_OK;
 }
@@ -234,6 +200,7 @@ int capture_chunk(lpsim_ctx *c, int start_set) {
     for (uint32_t koff = 0; koff < c->C; koff++) cur = enqueue_step(c, koff, koff, cur, (koff + 1) % c->R == 0);
     launch_apply_crossings(c->d, c->grid, c->stream);
     launch_chunk_end(c->d, c->C, c->stream);
+    if (c->d.tspan) launch_timing_fold(c->d, c->C, c->stream);
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     if (e != cudaSuccess) return fail(LPSIM_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     e = cudaGraphInstantiate(&c->graph[start_set], g, 0);
@@ -255,20 +222,15 @@ int chunk(lpsim_ctx *c) {
     if (!c->graph[c->cur]) TRY(capture_chunk(c, c->cur));
     CU(cudaGraphLaunch(c->graph[c->cur], c->stream));
     c->launches += chunk_launches(c);
-    if (c->timing) {
-        CU(cudaStreamSynchronize(c->stream));
-        collect_times(c, c->C, c->k);
-    }
     c->k += c->C;
     return LPSIM_OK;
 }
 
 // Light load: at most light_trips trips can be on the network or waiting in
 // the chunk starting at step k (trips due before its end minus those arrived;
-// h_ctr is current).  Kernel timing measures the grid-wide kernels, so it
-// keeps them.
+// h_ctr is current).
 bool light_chunk_ok(const lpsim_ctx *c) {
-    if ((c->p.flags & LPSIM_F_NO_LIGHT) || c->timing) return false;
+    if (c->p.flags & LPSIM_F_NO_LIGHT) return false;
     const uint64_t due = (uint64_t)(std::lower_bound(c->dep_sorted.begin(), c->dep_sorted.end(), c->k + c->C) -
                                     c->dep_sorted.begin());
     return due <= c->h_ctr[1] + (c->p.light_trips ? c->p.light_trips : kSmallMax);
@@ -284,6 +246,7 @@ int light_chunk(lpsim_ctx *c) {
     c->cur ^= 1;
     launch_apply_crossings(c->d, c->grid, c->stream);
     launch_chunk_end(c->d, c->C, c->stream);
+    if (c->d.tspan) launch_timing_fold(c->d, c->C, c->stream);
     CU(cudaGetLastError());
     c->launches += 4 + (c->sort ? 3 + 3ull * ((c->w.key_bits + 7) / 8) + 1 : 3);
     c->light_chunks++;
@@ -645,8 +608,10 @@ int load_demand_impl(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, cons
                      const uint64_t *seeds) {
     if (!c) return fail(LPSIM_E_INVALID_ARG, "ctx is NULL");
     if (c->loaded) return fail(LPSIM_E_STATE, "demand already loaded");
-    if (n == 0) return fail(LPSIM_E_INVALID_ARG, "no trips");
-    if (!depart_step || !route_off || !route_edges) return fail(LPSIM_E_INVALID_ARG, "trip array is NULL");
+    // n == 0 is a valid (empty) demand: every step finds nothing to move and
+    // lpsim_run returns at once
+    if (!route_off || (n > 0 && (!depart_step || !route_edges)))
+        return fail(LPSIM_E_INVALID_ARG, "trip array is NULL");
     if (n >= 0xFFFFFFF0ull) return fail(LPSIM_E_INVALID_ARG, "too many trips");
     if (route_off[0] != 0) return fail(LPSIM_E_INVALID_ARG, "route_off[0] must be 0");
     // Checks, spread over the host's threads; the lowest failing trip is
@@ -698,7 +663,7 @@ int load_demand_impl(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, cons
     // vehicle ids: stable sort by departure step (a counting sort when the
     // steps span less than 2^24)
     std::vector<uint32_t> order(n);
-    const uint32_t max_dep = *std::max_element(depart_step, depart_step + n);
+    const uint32_t max_dep = n ? *std::max_element(depart_step, depart_step + n) : 0u;
     if (max_dep < (1u << 24)) {
         std::vector<uint64_t> pos((size_t)max_dep + 2, 0);
         for (uint64_t j = 0; j < n; j++) pos[(size_t)depart_step[j] + 1]++;
@@ -852,6 +817,24 @@ int load_demand_impl(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, cons
     return LPSIM_OK;
 }
 
+// span slots for a chunk of c->C steps (kernel timing); the accumulators
+// keep their sums
+int timing_buffers(lpsim_ctx *c) {
+    if (!c->d.tacc) {
+        TRY(dnew(c, c->d.tacc, 16));
+        CU(cudaMemsetAsync(c->d.tacc, 0, 16 * 8, c->stream));
+    }
+    if (c->tspan_steps < c->C) {
+        TRY(dnew(c, c->tspan_buf, 2ull * (3ull * c->C + 1)));
+        CU(cudaMemsetAsync(c->tspan_buf, 0, 2ull * (3ull * c->C + 1) * 8, c->stream));
+        c->tspan_steps = c->C;
+    }
+    c->d.tspan = c->tspan_buf;
+    c->d.tspan_light = 3 * c->C;
+    CU(cudaStreamSynchronize(c->stream));
+    return LPSIM_OK;
+}
+
 // launch configuration: block size, resident 256-thread blocks per SM, sort
 // period and graph chunk; graphs are rebuilt on the next chunk
 int apply_config(lpsim_ctx *c, uint32_t block, uint32_t bps, uint32_t R, uint32_t chunk) {
@@ -871,11 +854,7 @@ int apply_config(lpsim_ctx *c, uint32_t block, uint32_t bps, uint32_t R, uint32_
     c->p.blocks_per_sm = bps;
     c->p.sort_period = R;
     c->p.chunk_steps = chunk;
-    if (c->timing && c->ev.size() < 4ull * c->C) {
-        size_t old = c->ev.size();
-        c->ev.resize(4ull * c->C);
-        for (size_t i = old; i < c->ev.size(); i++) CU(cudaEventCreate(&c->ev[i]));
-    }
+    if (c->timing) TRY(timing_buffers(c));
     return LPSIM_OK;
 }
 
@@ -1019,6 +998,17 @@ int lpsim_link_stats(lpsim_ctx *c, lpsim_link_stat *out, uint64_t n_edges, uint3
         // device arrays are bin-major: transpose into edge-major scratch first
         uint32_t *tmp = static_cast<uint32_t *>(c->dalloc(nb));
         if (!tmp) return fail(LPSIM_E_OOM, "device scratch allocation failed");
+        struct Giveback {
+            lpsim_ctx *c;
+            void *p;
+            ~Giveback() {
+                cudaStreamSynchronize(c->stream);
+                auto it = std::find(c->blocks.begin(), c->blocks.end(), p);
+                if (it != c->blocks.end()) c->blocks.erase(it);
+                if (c->release) c->release(p, c->alloc_user);
+                else cudaFree(p);
+            }
+        } giveback{c, tmp};
         struct {
             uint32_t *host;
             const uint32_t *dev;
@@ -1034,11 +1024,6 @@ int lpsim_link_stats(lpsim_ctx *c, lpsim_link_stat *out, uint64_t n_edges, uint3
                 rc = fail(LPSIM_E_CUDA, std::string("link statistics: ") + cudaGetErrorString(e));
                 break;
             }
-        }
-        if (!c->blocks.empty() && c->blocks.back() == tmp) {
-            c->blocks.pop_back();
-            if (c->release) c->release(tmp, c->alloc_user);
-            else cudaFree(tmp);
         }
         if (rc) return rc;
     }
@@ -1060,9 +1045,21 @@ int lpsim_get_state(lpsim_ctx *c, uint64_t n, float *x, float *v, uint32_t *edge
     if (!c) return fail(LPSIM_E_INVALID_ARG, "ctx is NULL");
     if (!c->loaded) return fail(LPSIM_E_STATE, "lpsim_load_demand has not been called");
     if (n != c->n_trips) return fail(LPSIM_E_INVALID_ARG, "n does not match the trips loaded");
-    // scratch: x, v, edge, ridx (4 B each) and lane (1 B) per vehicle
+    // scratch: x, v, edge, ridx (4 B each) and lane (1 B) per vehicle; given
+    // back on every exit path (after the stream has finished with it)
     uint8_t *tmp = static_cast<uint8_t *>(c->dalloc(n * 17 + 64));
     if (!tmp) return fail(LPSIM_E_OOM, "device scratch allocation failed");
+    struct Giveback {
+        lpsim_ctx *c;
+        void *p;
+        ~Giveback() {
+            cudaStreamSynchronize(c->stream);
+            auto it = std::find(c->blocks.begin(), c->blocks.end(), p);
+            if (it != c->blocks.end()) c->blocks.erase(it);
+            if (c->release) c->release(p, c->alloc_user);
+            else cudaFree(p);
+        }
+    } giveback{c, tmp};
     float *dx = reinterpret_cast<float *>(tmp);
     float *dv = dx + n;
     uint32_t *de = reinterpret_cast<uint32_t *>(dv + n);
@@ -1081,12 +1078,6 @@ int lpsim_get_state(lpsim_ctx *c, uint64_t n, float *x, float *v, uint32_t *edge
     if (ridx) CU(cudaMemcpy(ridx, dr, n * 4, cudaMemcpyDeviceToHost));
     if (lane) CU(cudaMemcpy(lane, dl, n, cudaMemcpyDeviceToHost));
     if (status) CU(cudaMemcpy(status, c->d.status, n, cudaMemcpyDeviceToHost));
-    // give the scratch back
-    if (!c->blocks.empty() && c->blocks.back() == tmp) {
-        c->blocks.pop_back();
-        if (c->release) c->release(tmp, c->alloc_user);
-        else cudaFree(tmp);
-    }
     return LPSIM_OK;
 }
 
@@ -1131,26 +1122,31 @@ int lpsim_set_kernel_timing(lpsim_ctx *c, int on) {
             cudaGraphExecDestroy(c->graph[i]);
             c->graph[i] = nullptr;
         }
-    if (on && c->ev.empty()) {
-        c->ev.resize(4ull * c->C);
-        for (auto &e : c->ev) CU(cudaEventCreate(&e));
-    }
-    c->timing = on != 0;
-    c->t_err.clear();
-    for (int i = 0; i < 3; i++) {
-        c->t_ms[i] = 0.0;
-        c->t_n[i] = 0;
+    if (on) {
+        TRY(timing_buffers(c));
+        CU(cudaMemsetAsync(c->d.tacc, 0, 16 * 8, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+        c->timing = true;
+    } else {
+        // the sums stay readable; the kernels stop stamping
+        c->timing = false;
+        c->d.tspan = nullptr;
     }
     return LPSIM_OK;
 }
 
-int lpsim_get_kernel_times(lpsim_ctx *c, double *ms, uint64_t *launches) {
-    if (!c || !ms || !launches) return fail(LPSIM_E_INVALID_ARG, "NULL argument");
-    if (!c->t_err.empty()) return fail(LPSIM_E_CUDA, c->t_err);
-    for (int i = 0; i < 3; i++) {
-        ms[i] = c->t_ms[i];
-        launches[i] = c->t_n[i];
+int lpsim_get_kernel_times(lpsim_ctx *c, lpsim_kernel_times *out) {
+    if (!c || !out) return fail(LPSIM_E_INVALID_ARG, "NULL argument");
+    std::memset(out, 0, sizeof(*out));
+    if (!c->d.tacc) return LPSIM_OK;
+    unsigned long long a[16];
+    CU(cudaStreamSynchronize(c->stream));
+    CU(cudaMemcpy(a, c->d.tacc, sizeof(a), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < 4; i++) {
+        out->ms[i] = (double)a[i] * 1e-6;
+        out->launches[i] = a[4 + i];
     }
+    out->p1_veh_steps = a[8];
     return LPSIM_OK;
 }
 
@@ -1172,14 +1168,16 @@ int lpsim_autotune(lpsim_ctx *c, uint32_t window_steps, lpsim_tune_result *out) 
     const uint32_t cur_cfg[4] = {(uint32_t)c->block, c->p.blocks_per_sm ? c->p.blocks_per_sm : 4u, c->R,
                                  c->p.chunk_steps ? c->p.chunk_steps : 1536u};
     TRY(snapshot_impl(c));
+    // candidates run without kernel timing
     const bool timing = c->timing;
     c->timing = false;
+    c->d.tspan = nullptr;
     struct Cand {
         uint32_t block, bps, R;
     };
     std::vector<Cand> cands;
     cands.push_back({cur_cfg[0], cur_cfg[1], cur_cfg[2]});
-    for (uint32_t R : {32u, 64u, 128u})
+    for (uint32_t R : {64u, 128u, 256u})
         for (uint32_t block : {128u, 256u, 512u})
             for (uint32_t bps : {2u, 4u, 6u})
                 if (!(block == cur_cfg[0] && bps == cur_cfg[1] && R == cur_cfg[2])) cands.push_back({block, bps, R});
@@ -1204,7 +1202,10 @@ int lpsim_autotune(lpsim_ctx *c, uint32_t window_steps, lpsim_tune_result *out) 
     }
     TRY(apply_config(c, pick.block, pick.bps, pick.R, cur_cfg[3]));
     TRY(restore_impl(c));
-    c->timing = timing;
+    if (timing) {
+        c->timing = true;
+        TRY(timing_buffers(c));
+    }
     if (out) {
         out->block_size = pick.block;
         out->blocks_per_sm = pick.bps;

@@ -203,7 +203,7 @@ __device__ __forceinline__ void stage_put(T *buf, uint32_t room, uint32_t *n, T 
 __device__ __forceinline__ void loads_issued() { asm volatile("" ::: "memory"); }
 
 template <int BLOCK>
-__device__ __forceinline__ void block_add(unsigned long long *dst, uint32_t val) {
+__device__ __forceinline__ void block_add(unsigned long long *dst, uint32_t val, unsigned long long *dst2 = nullptr) {
     __shared__ uint32_t red[BLOCK / 32];
     uint32_t w = __reduce_add_sync(0xFFFFFFFFu, val);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = w;
@@ -211,7 +211,10 @@ __device__ __forceinline__ void block_add(unsigned long long *dst, uint32_t val)
     if (threadIdx.x < 32) {
         uint32_t t = threadIdx.x < BLOCK / 32 ? red[threadIdx.x] : 0u;
         t = __reduce_add_sync(0xFFFFFFFFu, t);
-        if (threadIdx.x == 0 && t) atomicAdd(dst, (unsigned long long)t);
+        if (threadIdx.x == 0 && t) {
+            atomicAdd(dst, (unsigned long long)t);
+            if (dst2) atomicAdd(dst2, (unsigned long long)t);
+        }
     }
 }
 
@@ -564,6 +567,7 @@ __device__ __forceinline__ void p1_flush(const Dev &d, uint32_t par, const P1Sin
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) step_p1(Dev d, uint32_t koff, uint32_t kph) {
     pdl_prologue();
+    span_start(d, 3 * koff);
     const uint32_t k = *d.kbase + koff;
     const uint32_t n = *d.n_slots;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -589,9 +593,10 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) step_p1(Dev d, uint32_t k
         }
         if (!p1_slot(d, w, sk, i - norg, n, live, arrived)) break;
     }
-    block_add<BLOCK>(&d.ctr[0], live);
+    block_add<BLOCK>(&d.ctr[0], live, d.tacc ? &d.tacc[8] : nullptr);
     warp_add(&d.ctr[1], arrived);
     p1_flush(d, w.par, sk, s_base);
+    span_end(d, 3 * koff);
 }
 
 // ----------------------------------------------------------------------- P2
@@ -802,6 +807,7 @@ __device__ __forceinline__ void lane_change(const Dev &d, const StepView &w, con
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) step_p2(Dev d, uint32_t koff, uint32_t kph, uint32_t gc, uint32_t gi) {
     pdl_prologue();
+    span_start(d, 3 * koff + 1);
     const uint32_t par = kph & 1u;
     const uint32_t k = *d.kbase + koff;
     const StepView w = step_view(d, k, kph);
@@ -865,6 +871,7 @@ __global__ void __launch_bounds__(BLOCK) step_p2(Dev d, uint32_t koff, uint32_t 
     warp_add(&d.ctr[3], events);
     warp_add(&d.ctr[4], departed);
     warp_add(&d.ctr[2], changes);
+    span_end(d, 3 * koff + 1);
 }
 
 // ------------------------------------------------------------ light load
@@ -886,6 +893,7 @@ __global__ void __launch_bounds__(BLOCK) step_p2(Dev d, uint32_t koff, uint32_t 
 // 2k-12k trips.)
 __global__ void __launch_bounds__(kSmallBlock, 1)
     step_small(Dev d, uint32_t k0, uint32_t nsteps, const uint32_t *olist, const uint32_t *no_ptr) {
+    span_start(d, d.tspan_light);
     const uint32_t tid = threadIdx.x;
     const uint32_t no = *no_ptr;
     uint32_t n = *d.n_slots, ev0 = *d.ev_n;
@@ -936,6 +944,7 @@ __global__ void __launch_bounds__(kSmallBlock, 1)
     warp_add64(&d.ctr[2], changes);
     warp_add64(&d.ctr[3], events);
     warp_add64(&d.ctr[4], departed);
+    span_end(d, d.tspan_light);
 }
 
 // Origin edges that can act in steps [k0, k1): a queue head due before k1,
@@ -973,6 +982,40 @@ __global__ void apply_crossings(Dev d) {
         if (r.x == kNone) continue;
         stat_exit(d, r.x, r.w, r.z);
         stat_entry(d, r.y, r.w);
+    }
+}
+
+// kernel timing: fold the spans of steps [0, nsteps) of the chunk and of the
+// light-load kernel into the accumulators and clear their slots (one block)
+__global__ void __launch_bounds__(1024) timing_fold(Dev d, uint32_t nsteps) {
+    __shared__ unsigned long long red[8][32];
+    unsigned long long acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (uint32_t j = threadIdx.x; j <= nsteps; j += blockDim.x) {
+        for (uint32_t ph = 0; ph < 3; ph++) {
+            const uint32_t pair = j < nsteps ? 3 * j + ph : (ph == 0 ? d.tspan_light : kNone);
+            if (pair == kNone) continue;
+            const unsigned long long a = d.tspan[2 * pair], b = d.tspan[2 * pair + 1];
+            if (b != 0ull) {
+                const int slot = j < nsteps ? (int)ph : 3;
+                acc[slot] += b - ~a;
+                acc[4 + slot] += 1ull;
+                d.tspan[2 * pair] = 0ull;
+                d.tspan[2 * pair + 1] = 0ull;
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+        unsigned long long v = acc[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+        if ((threadIdx.x & 31u) == 0) red[q][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        unsigned long long t = 0;
+        for (uint32_t w = 0; w < blockDim.x / 32; w++) t += red[threadIdx.x][w];
+        d.tacc[threadIdx.x] += t;
     }
 }
 
@@ -1025,6 +1068,8 @@ void launch_phase(const Dev &d, int phase, uint32_t koff, uint32_t kph, int grid
 void launch_chunk_end(const Dev &d, uint32_t steps, cudaStream_t st) { launch_pdl(chunk_end, 1, 1, st, d, steps); }
 
 void launch_apply_crossings(const Dev &d, int grid, cudaStream_t st) { apply_crossings<<<grid, 256, 0, st>>>(d); }
+
+void launch_timing_fold(const Dev &d, uint32_t nsteps, cudaStream_t st) { timing_fold<<<1, 1024, 0, st>>>(d, nsteps); }
 
 cudaError_t launch_small(const Dev &d, uint32_t k0, uint32_t nsteps, uint32_t *olist, uint32_t *no,
                          cudaStream_t st) {

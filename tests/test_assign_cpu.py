@@ -28,12 +28,23 @@ def _diamond():
     return net, edges
 
 
+def _cost_ms(seconds):
+    """A link time in whole milliseconds (nearest, at least 1 ms)."""
+    return max(1, int(math.floor(float(seconds) * 1000.0 + 0.5)))
+
+
 def _arrival(path, t0, tt, bin_s):
-    t = t0
+    """Arrival time (s) of a path entered at t0 (s).  A link entered at t
+    (ms) in bin b (the last bin beyond the table) is left at the earliest of
+    t + c[b] and, for every later bin b', the start of b' + c[b'] (the entry
+    may be held back to a later bin); times are whole milliseconds."""
+    t = int(math.floor(t0 * 1000.0 + 0.5))
+    bin_ms = int(round(bin_s * 1000.0))
+    nb = tt.shape[1]
     for e in path:
-        b = min(max(int(math.floor(t / bin_s)), 0), tt.shape[1] - 1)
-        t += tt[e, b]
-    return t
+        b = min(t // bin_ms, nb - 1)
+        t = min([t + _cost_ms(tt[e, b])] + [b2 * bin_ms + _cost_ms(tt[e, b2]) for b2 in range(b + 1, nb)])
+    return t / 1000.0
 
 
 def _all_paths(edges, s, d):
@@ -75,7 +86,7 @@ def test_time_dependent_paths_match_brute_force(A):
             best = min(_arrival(p, t0, tt, bin_s) for p in _all_paths(edges, 0, 3))
             r = routes["route_edges"][int(routes["route_off"][j]):int(routes["route_off"][j + 1])]
             # the route is an earliest-arrival path from the period's middle ...
-            assert abs(_arrival(list(r), t0, tt, bin_s) - best) < 1e-3
+            assert _arrival(list(r), t0, tt, bin_s) == best
             # ... and its time is counted from the trip's own departure
             tj = float(dep[j]) * dt
             assert abs(tsp[j] - (_arrival(list(r), tj, tt, bin_s) - tj)) < 1e-3

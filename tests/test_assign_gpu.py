@@ -24,6 +24,75 @@ def case():
     return W.assignment_case(scale="tiny")
 
 
+def _tables(net, n_bins, seed, spread=0.8):
+    """Link-time tables around free flow, each (edge, bin) scaled by its own
+    random factor -- times fall as well as rise between bins, so the FIFO
+    rule (holding an entry back to a later bin) is exercised."""
+    rng = np.random.default_rng(seed)
+    ff = (net["edge_len"] / net["edge_vmax"]).astype(np.float64)[:, None]
+    return (ff * np.exp(rng.uniform(0.0, spread, (net["n_edges"], n_bins)))).astype(np.float32)
+
+
+def _paths(A, search, tt, bin_steps, period_steps):
+    tsp = search(tt, bin_steps, period_steps)
+    A.reroute(1.0, 0)  # every trip takes its candidate: the routes are the paths
+    return tsp, A.routes()
+
+
+@pytest.mark.parametrize("scale,period_steps,seed", [("tiny", 3600, 1), ("tiny", 600, 2), ("tiny", 36000, 3),
+                                                     ("small", 3600, 4)])
+def test_gpu_paths_equal_host_paths(scale, period_steps, seed):
+    """The GPU search (one warp per tree, label-correcting rounds on packed
+    (arrival, edge) labels) returns the host Dijkstra's routes and times bit
+    for bit: the earliest arrival, ties to the lower entering edge id."""
+    from paper_2406_08496_gb300.assignment import Assignment
+    net, dem = W.assignment_case(scale=scale)
+    tt = _tables(net, 96, seed)
+    host = Assignment(net, dem, seed=seed)
+    gpu = Assignment(net, dem, seed=seed)
+    th, rh = _paths(host, host.shortest_paths, tt, 1800, period_steps)
+    tg, rg = _paths(gpu, gpu.shortest_paths_gpu, tt, 1800, period_steps)
+    assert np.array_equal(th.view(np.uint32), tg.view(np.uint32))
+    assert np.array_equal(rh["route_off"], rg["route_off"])
+    assert np.array_equal(rh["route_edges"], rg["route_edges"])
+    # a second call on the same engine reuses its device state
+    tt2 = _tables(net, 96, seed + 10)
+    th2 = host.shortest_paths(tt2, 1800, period_steps)
+    tg2 = gpu.shortest_paths_gpu(tt2, 1800, period_steps)
+    assert np.array_equal(th2.view(np.uint32), tg2.view(np.uint32))
+    host.close()
+    gpu.close()
+
+
+def test_gpu_paths_match_brute_force():
+    """On a five-edge diamond, every trip's GPU route is an earliest-arrival
+    path among all simple paths, from the middle of its period, and its time
+    is that path's from the trip's own departure."""
+    from test_assign_cpu import _all_paths, _arrival, _diamond
+    from paper_2406_08496_gb300.assignment import Assignment
+    net, edges = _diamond()
+    rng = np.random.default_rng(5)
+    n_bins, bin_steps, dt, period = 6, 20, 0.5, 10
+    bin_s = bin_steps * dt
+    dep = np.array([0, 13, 31, 55, 70], np.uint32)
+    for _ in range(20):
+        tt = rng.uniform(1.0, 30.0, (6, n_bins)).astype(np.float32)
+        dem = {"orig": np.zeros(5, np.uint32), "dest": np.full(5, 3, np.uint32), "depart_step": dep,
+               "route_off": np.arange(0, 11, 2, dtype=np.uint64), "route_edges": np.array([0, 1] * 5, np.uint32)}
+        a = Assignment(net, dem, dt=dt, seed=3)
+        tsp = a.shortest_paths_gpu(tt, bin_steps, period)
+        a.reroute(1.0, 0)
+        routes = a.routes()
+        for j in range(5):
+            t0 = ((dep[j] // period) + 0.5) * period * dt
+            best = min(_arrival(p, t0, tt, bin_s) for p in _all_paths(edges, 0, 3))
+            r = list(routes["route_edges"][int(routes["route_off"][j]):int(routes["route_off"][j + 1])])
+            assert _arrival(r, t0, tt, bin_s) == best
+            tj = float(dep[j]) * dt
+            assert abs(tsp[j] - (_arrival(r, tj, tt, bin_s) - tj)) < 1e-3
+        a.close()
+
+
 def test_msa_plain_reduces_gap(case):
     from paper_2406_08496_gb300.assignment import msa
     net, dem = case

@@ -1,12 +1,14 @@
-"""Parity at the full regional size, in the launch configuration the
-benchmark times (default block size, blocks per SM, sort period and graph
-chunk; no debug flags).
+"""Parity at the full regional size (the 2.82M-trip day on 224k nodes) and at
+the large size (the 9.01M-trip day on 1.01M nodes), in the launch
+configuration the benchmark times (default block size, blocks per SM, sort
+period and graph chunk; no debug flags).
 
 * A sample the oracle can finish: every trip of the 2.82M-trip day that
   departs in a five-minute window of the morning peak, simulated alone on the
   full 224k-node network for 1,536 steps (one graph chunk).  Every output is
   compared bit for bit.
-* The whole day on the GPU, checked through properties that hold at any size:
+* The same for the 9.01M-trip day (departures 07:30-07:33).
+* Each whole day on the GPU, checked through properties that hold at any size:
   every trip departs no earlier than planned and arrives; each trip's travel
   time is at least its route length at the network's top speed; every edge
   was left as often as it was entered, and entered once per route position;
@@ -35,14 +37,32 @@ def regional():
     return W.regional_day(seed=2, n_trips=2_820_000)
 
 
+@pytest.fixture(scope="module")
+def large():
+    import workloads as W
+    return W.regional_day(seed=3, n_trips=9_010_000, scale="large")
+
+
 def test_regional_peak_window_matches_oracle(regional):
+    peak_window_matches_oracle(regional, PEAK_WINDOW, min_trips=10_000)
+
+
+def test_large_peak_window_matches_oracle(large):
+    """The 9.01M-trip day: its 07:30-07:33 departures on the full 1.01M-node
+    network for one graph chunk, bit for bit."""
+    net, dem = large
+    assert net["n_nodes"] > 1_000_000 and len(dem["depart_step"]) == 9_010_000
+    peak_window_matches_oracle(large, (PEAK_WINDOW[0], PEAK_WINDOW[0] + 360), min_trips=20_000)
+
+
+def peak_window_matches_oracle(workload, window, min_trips):
     import workloads as W
     from paper_2406_08496_gb300 import Simulation
-    net, dem = regional
-    keep = (dem["depart_step"] >= PEAK_WINDOW[0]) & (dem["depart_step"] < PEAK_WINDOW[1])
+    net, dem = workload
+    keep = (dem["depart_step"] >= window[0]) & (dem["depart_step"] < window[1])
     sub = W.subset_trips(dem, keep)
-    sub["depart_step"] = (sub["depart_step"] - PEAK_WINDOW[0]).astype(np.uint32)
-    assert len(sub["depart_step"]) > 10_000
+    sub["depart_step"] = (sub["depart_step"] - window[0]).astype(np.uint32)
+    assert len(sub["depart_step"]) > min_trips
     params = dict(bin_steps=1800, n_bins=2)
     o = O.Oracle(net, params)
     vo = o.load_demand(sub)
@@ -51,7 +71,7 @@ def test_regional_peak_window_matches_oracle(regional):
     assert np.array_equal(vo, vg)
     o.step(WINDOW_STEPS)
     g.step(WINDOW_STEPS)
-    assert_outputs_equal(o, g, n_bins=2, where="regional peak window")
+    assert_outputs_equal(o, g, n_bins=2, where=f"peak window of {net['n_nodes']} nodes")
     co, cg = o.counters(), g.counters()
     for key in ("veh_steps", "arrived", "active", "waiting", "lane_changes"):
         assert co[key] == cg[key], (key, co[key], cg[key])
@@ -59,8 +79,16 @@ def test_regional_peak_window_matches_oracle(regional):
 
 
 def test_regional_day_properties(regional):
+    day_properties(regional)
+
+
+def test_large_day_properties(large):
+    day_properties(large)
+
+
+def day_properties(workload):
     from paper_2406_08496_gb300 import Simulation
-    net, dem = regional
+    net, dem = workload
     n = len(dem["depart_step"])
     g = Simulation(net, dict(bin_steps=1800, n_bins=96))
     vid = g.load_demand(dem)

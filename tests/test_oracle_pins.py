@@ -517,3 +517,31 @@ def test_entry_conflict_lowest_id_wins():
                     entered[i] = k
         # both depart at step 0 (different first edges), reach x' >= 14 in step 2
         assert entered == {0: 2, 1: 4}
+
+
+def test_ring_of_one_cell_edges_gridlocks():
+    """Four one-cell single-lane edges in a ring, one vehicle departing onto
+    each at step 0: from step 1 on every vehicle reaches the end of its edge
+    (v0 dt = 2.5 m >= 1 m) and asks for cell 0 of the next edge, which the
+    vehicle ahead holds in the step-k map, so no lane is free and it holds at
+    x = max(x, L - 1) = 0 with v = 0.  The state is a fixed point: nothing
+    enters, leaves or moves, and each step adds four vehicle-steps."""
+    net = make_net(4, [(0, 1, 1.0, 1, 5.0), (1, 2, 1.0, 1, 5.0), (2, 3, 1.0, 1, 5.0), (3, 0, 1.0, 1, 5.0)])
+    trips = [(j // 4, [(j % 4 + q) % 4 for q in range(10)]) for j in range(16)]
+    o = O.Oracle(net)
+    o.load_demand(make_demand(trips))
+    o.step(1)
+    s1, m1 = o.state(), o.lane_map().copy()
+    assert np.array_equal(m1, np.zeros(4, np.uint8))
+    assert int((s1["status"] == 1).sum()) == 4
+    for k in (2, 50, 3001):
+        o.step(k - o.counters()["k"])
+        c = o.counters()
+        assert c == {"k": k, "veh_steps": 4 * (k - 1), "arrived": 0, "active": 4, "waiting": 12,
+                     "lane_changes": 0}, c
+        s = o.state()
+        for key in ("status", "edge", "lane", "ridx", "x", "v"):
+            assert np.array_equal(s[key], s1[key]), key
+        assert np.array_equal(o.lane_map(), m1)
+    ls = o.link_stats()
+    assert np.array_equal(ls["entries"], np.ones(4, np.uint64)) and not ls["exits"].any()

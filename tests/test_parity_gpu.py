@@ -253,21 +253,40 @@ def test_stop_line_intents_beside_losing_crossers(seed, eps_amp, flags):
     assert o.counters()["lane_changes"] == g.counters()["lane_changes"]
 
 
-def test_kernel_timing_direct_and_graph_steps(grid_day):
-    """Per-kernel timing around direct steps and graph chunks alike, and the
-    results unchanged by it."""
+@pytest.mark.parametrize("flags", [4, 0])
+def test_kernel_timing_direct_and_graph_steps(grid_day, flags):
+    """Per-kernel span timing over direct steps and graph chunks alike (with
+    and without light-load chunks), every launch accounted for, the spans
+    summing to no more than the wall time, and the results unchanged."""
+    import time
+
+    import torch
     from paper_2406_08496_gb300 import Simulation
     net, dem = grid_day
-    g = Simulation(net, {})
+    g = Simulation(net, dict(flags=flags))
     g.load_demand(dem)
     g.set_kernel_timing(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     g.step(5)      # direct steps (not at a chunk boundary afterwards)
     g.step(1531)   # direct steps up to the chunk boundary (default chunk: 1,536 steps)
-    g.step(3072)   # two graph chunks
+    g.step(3072)   # two graph chunks (or light-load chunks)
+    torch.cuda.synchronize()
+    wall_ms = (time.perf_counter() - t0) * 1e3
     kt = g.kernel_times()
     g.set_kernel_timing(False)
-    assert kt["step_p1"]["launches"] == 4608 and kt["step_p1"]["ms"] > 0
-    assert kt["step_p2"]["ms"] > 0 and kt["step_p2"]["launches"] == 4608
+    vs = g.counters()["veh_steps"]
+    n_light = kt["step_small"]["launches"]
+    assert kt["step_p1"]["launches"] + 1536 * n_light == 4608, kt
+    assert kt["step_p2"]["launches"] == kt["step_p1"]["launches"]
+    # compaction every 256 steps, and once at the end of each light-load chunk
+    assert kt["compact_sort"]["launches"] == (4608 - 1536 * n_light) // 256 + n_light, kt
+    assert kt["step_p1"]["ms"] > 0 and kt["step_p2"]["ms"] > 0
+    assert sum(v["ms"] for v in kt.values()) <= wall_ms
+    if flags == 4:
+        assert n_light == 0 and kt["step_p1"]["veh_steps"] == vs
+    else:
+        assert n_light > 0 and 0 < kt["step_p1"]["veh_steps"] < vs
     ref = Simulation(net, {})
     ref.load_demand(dem)
     ref.step(4608)

@@ -391,9 +391,12 @@ def batch_scenarios(n_scen: int = 64, base_seed: int = 100, min_nodes: int = 100
 
 
 def assignment_case(seed: int = 5, scale: str = "small") -> tuple[dict, dict]:
-    """Regional network and day demand for the assignment loop: the
-    regional generator at reduced scale ("small": ~27k nodes, ~340k trips,
-    the same trips per node as the 224k-node / 2.82M-trip day)."""
+    """Regional network and day demand for the assignment loop: "paper" is
+    the 224k-node network with the 2.82M-trip day (regional_day, seed 2);
+    "small" and "tiny" are the regional generator at reduced scale (~27k
+    nodes / ~340k trips -- the same trips per node -- and ~3k / 30k)."""
+    if scale == "paper":
+        return regional_day(seed=2, n_trips=2_820_000)
     sizes = {"small": (180, 340_000, 12, 8), "tiny": (60, 30_000, 5, 3)}
     side, n_trips, zx, zy = sizes[scale]
     net = planar_network(side, side, seed)

@@ -11,7 +11,11 @@
  * short paths go to the lower edge id: pred[v] is the smallest-id in-edge
  * that attains dist[v].  Integer costs make the result identical on every
  * host.  Origins are distributed over POSIX threads; each origin's tree is
- * deterministic, so the output does not depend on the thread count.
+ * deterministic, so the output does not depend on the thread count.  A
+ * search stops once every destination of its origin's trips is settled:
+ * with positive costs a settled node's distance and predecessor are final,
+ * and so are those of the settled nodes on its path, so the routes are the
+ * same as those of the full tree.
  */
 #include <pthread.h>
 #include <stdint.h>
@@ -117,6 +121,7 @@ static void *worker(void *arg) {
     uint8_t *done = (uint8_t *)malloc(nn);
     heap_item *heap = (heap_item *)malloc(((size_t)c->n_edges + nn + 1) * sizeof(heap_item));
     uint32_t *tmp = (uint32_t *)malloc((size_t)nn * 4 + 4);
+    uint32_t *want = (uint32_t *)calloc((size_t)nn, 4);  /* origin group + 1 for its destinations */
     uint32_t used = 0;
     for (;;) {
         pthread_mutex_lock(&c->mu);
@@ -124,6 +129,11 @@ static void *worker(void *arg) {
         pthread_mutex_unlock(&c->mu);
         if (g >= c->n_origins) break;
         uint32_t s = c->origins[g];
+        uint32_t n_want = 0;
+        for (uint64_t j = c->grp_off[g]; j < c->grp_off[g + 1]; j++) {
+            uint32_t d = c->dest[c->grp_trip[j]];
+            if (want[d] != g + 1) { want[d] = g + 1; n_want++; }
+        }
         for (uint32_t i = 0; i < nn; i++) { dist[i] = UINT64_MAX; pred[i] = UINT32_MAX; done[i] = 0; }
         uint64_t hn = 0;
         dist[s] = 0;
@@ -133,6 +143,7 @@ static void *worker(void *arg) {
             uint32_t u = it.node;
             if (done[u] || it.key != dist[u]) continue;
             done[u] = 1;
+            if (want[u] == g + 1 && --n_want == 0) break;
             for (uint32_t j = c->out_off[u]; j < c->out_off[u + 1]; j++) {
                 uint32_t e = c->out_edge[j];
                 uint32_t v = c->dst[e];
@@ -158,7 +169,7 @@ static void *worker(void *arg) {
             c->trip_len[trip] = len;
         }
     }
-    free(dist); free(pred); free(done); free(heap); free(tmp);
+    free(dist); free(pred); free(done); free(heap); free(tmp); free(want);
     return NULL;
 }
 
