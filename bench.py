@@ -53,6 +53,10 @@ def parse():
                     choices=["regional", "grid", "large", "batch64", "assignment", "surrogate"])
     ap.add_argument("--iterations", type=int, default=40,
                     help="assignment workload: MSA iterations at most per arm (each stops at the 1%% gap)")
+    ap.add_argument("--assignment-scale", default="paper", choices=["paper", "small", "tiny"],
+                    help="assignment workload: the 2.82M-trip regional day (paper) or the reduced cases")
+    ap.add_argument("--paths", default="gpu", choices=["gpu", "host"],
+                    help="assignment workload: where the time-dependent shortest paths are searched")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--day-profile", type=int, default=0, metavar="STEPS",
@@ -60,6 +64,8 @@ def parse():
                          "on the network) and print one JSON line per window, then exit")
     ap.add_argument("--profile-window", type=int, default=0,
                     help="run to 08:00, then profile this many directly launched steps (for ncu) and exit")
+    ap.add_argument("--no-sort", action="store_true",
+                    help="compact the vehicle slots without sorting them by lane-map cell (LPSIM_F_NO_SORT)")
     return ap.parse_args()
 
 
@@ -281,32 +287,40 @@ def batch_arm(args, L, torch, rank, world, local, dist=None):
 
 
 def assignment_arm(args, L, torch):
-    """Plain and surrogate-assisted MSA on the reduced regional case (27k
-    nodes, 340k trips, same trips per node as the 2.82M-trip day), each run
-    until the relative gap reaches 1% or for --iterations iterations; every gap
-    measured by a full simulation.  value = the surrogate arm's wall time to
+    """Plain and surrogate-assisted MSA on the regional day (the 224k-node
+    network and its 2.82M trips; --assignment-scale picks a reduced case),
+    each run until the relative gap reaches 1% or for --iterations
+    iterations; every gap is measured by a full simulation and both arms use
+    the same routing code (--paths).  value = the surrogate arm's wall time to
     the 1% gap (null if not reached); both arms' times to 2%, 1.5% and 1%."""
     import workloads as W
     from paper_2406_08496_gb300.assignment import msa
-    net, dem = W.assignment_case(scale="small")
+    net, dem = W.assignment_case(scale=args.assignment_scale)
     iters = args.iterations
     res = {}
     for mode in ("plain", "surrogate"):
-        r = msa(net, dem, mode, iterations=iters, target_gap=0.01)
+        r = msa(net, dem, mode, iterations=iters, target_gap=0.01, paths=args.paths,
+                surrogate_batch=131072 if args.assignment_scale == "paper" else 8192)
         hist = [(h["wall_s"], h["gap"]) for h in r["history"] if h["gap"] is not None]
 
         def hit(th):
             return next((t for t, g in hist if g <= th), None)
+        sims = [h for h in r["history"] if h["kind"] == "simulation"]
         res[mode] = {"time_to_1pct_gap_s": hit(0.01), "time_to_1.5pct_gap_s": hit(0.015),
                      "time_to_2pct_gap_s": hit(0.02), "final_gap": r["final_gap"], "wall_s": r["wall_s"],
                      "iterations": len(r["history"]), "gaps": [round(g, 5) for _, g in hist],
-                     "gap_wall_s": [round(t, 2) for t, _ in hist]}
+                     "gap_wall_s": [round(t, 2) for t, _ in hist],
+                     "sim_s_mean": float(np.mean([h["sim_s"] for h in sims])) if sims else None,
+                     "paths_s_mean": float(np.mean([h["paths_s"] for h in sims])) if sims else None}
+    trips = int(len(dem["depart_step"]))
+    label = {"paper": "assignment-224k-nodes-2.82M-trips", "small": "assignment-27k-nodes-340k-trips",
+             "tiny": "assignment-3k-nodes-30k-trips"}[args.assignment_scale]
     out = {"metric": "time-to-1%-gap", "value": res["surrogate"]["time_to_1pct_gap_s"], "unit": "s",
            "higher_is_better": False, "n_gpus": 1, "steps": iters, "warmup": 0, "dtype": "f32+bf16",
            "data": "synthetic", "vs_baseline": None,
-           "config": {"workload": "assignment-27k-nodes-340k-trips", "nodes": net["n_nodes"],
-                      "edges": net["n_edges"], "trips": int(len(dem["depart_step"])), "reroute_fraction": 0.1,
-                      "selection": "random", "full_simulation": "every iteration (plain), every 2nd (surrogate)"},
+           "config": {"workload": label, "nodes": net["n_nodes"], "edges": net["n_edges"], "trips": trips,
+                      "reroute_fraction": 0.1, "selection": "random", "paths": args.paths,
+                      "full_simulation": "every iteration (plain), every 2nd (surrogate)"},
            "plain_time_to_1pct_gap_s": res["plain"]["time_to_1pct_gap_s"], "arms": res}
     print(json.dumps(out), flush=True)
 
@@ -323,7 +337,9 @@ def surrogate_arm(args):
     rows = 131072
     s = L.Surrogate(n_features=11, batch=rows, seed=0)
     t = s.time(max(args.steps, 10))
-    mac_fwd = 64 * 256 + 256 * 256 * 2 + 256
+    # the method's own multiply-adds per row: 11 real inputs (the zero
+    # padding of the input columns is not the method's work)
+    mac_fwd = 11 * 256 + 256 * 256 * 2 + 256
     flop_fwd = 2.0 * rows * mac_fwd
     # training: the forward, the weight gradients (as many MACs as the forward)
     # and the input gradients of layers 3 and 2 (layer 1 needs none)
@@ -379,6 +395,8 @@ def main():
     net, dem, label = load_workload(args.workload)
     n_bins = 96 if args.workload != "grid" else 4
     params = dict(bin_steps=1800, n_bins=n_bins)
+    if args.no_sort:
+        params["flags"] = 1
     sim = L.Simulation(net, params)
     sim.load_demand(dem)
 

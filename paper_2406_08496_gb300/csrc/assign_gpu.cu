@@ -12,18 +12,24 @@
 // Here every tree is searched by one warp, thousands of warps at a time (a
 // tree's frontier is a wave of a few hundred nodes; many trees in flight
 // hide the memory latency each relaxation pays):
-//   * label-correcting search in rounds: the frontier's nodes relax their
-//     out-edges with the arrival function of the bin holding their arrival
-//     time (FIFO by construction, see TD), and a node whose label improved
-//     joins the next round's frontier (once: a per-node round stamp);
+//   * label-correcting search in rounds over time buckets (near-far): the
+//     near set's nodes relax their out-edges with the arrival function of
+//     the bin holding their arrival time (FIFO by construction, see TD); a
+//     node whose label improved joins the next round's near set when its
+//     arrival is below the bucket threshold (once per round: a round stamp)
+//     and the far pile otherwise (once: a mark); when the near set empties,
+//     every label below the threshold is final, the threshold moves on by
+//     the bucket width and the far nodes below it become the near set --
+//     close to Dijkstra's work, with a whole near set relaxed per round;
 //   * a label is (arrival ms << 32 | entering edge id) in one 64-bit word,
 //     so atomicMin keeps the earliest arrival and, among equal arrivals, the
 //     lower edge id -- the fixed point is exactly the tree the host's
 //     Dijkstra builds (lpsim_assign_shortest_paths), with integer millisecond
 //     link times making every arrival an exact sum;
-//   * once every destination of the group has a label, the latest of them
-//     bounds the search: a node reached later than it cannot lie on any of
-//     their paths (link times are positive), so it is not expanded;
+//   * the search ends once every destination of the group is below the
+//     threshold (settled); until then the latest destination label bounds
+//     it: a node reached later cannot lie on any of their paths (link times
+//     are positive), so it is not expanded;
 //   * each trip's path is read back along the entering edges, written to the
 //     output in travel order and timed from the trip's own departure;
 //   * the labels the tree set are reset from its list of reached nodes, so a
@@ -60,6 +66,10 @@ constexpr uint32_t kNoEdge = 0xFFFFFFFFu;
 constexpr int kWarpsPerBlock = 4;
 constexpr int kBlocksPerSm = 4;                      // 16 warps (trees) per SM
 constexpr uint64_t kWorkspaceBudget = 16ull << 30;   // bytes of per-warp workspaces at most
+#ifndef LPSIM_ASSIGN_DELTA_MS
+#define LPSIM_ASSIGN_DELTA_MS 60000
+#endif
+constexpr uint64_t kDeltaMs = LPSIM_ASSIGN_DELTA_MS;  // bucket width of the search thresholds (ms)
 
 // error bits
 constexpr uint32_t kErrUnreachable = 1u;  // a destination not reached (or equal to its origin)
@@ -95,8 +105,11 @@ struct TreeArgs {
     uint64_t *lab;            // n_warps x n_nodes
     uint32_t *inq;            // n_warps x n_nodes: round stamp of the last push
     uint32_t *touched;        // n_warps x n_nodes
-    uint32_t *fa, *fb;        // n_warps x n_nodes: frontiers
+    uint32_t *fa, *fb;        // n_warps x n_nodes: near sets (this round, next round)
+    uint32_t *far;            // n_warps x n_nodes: far pile (labels at or above the threshold)
+    uint32_t *fmark;          // n_warps x n_nodes: tree mark of the nodes in the far pile
     uint32_t *stamp;          // per warp: last round stamp used
+    uint64_t delta_ms;        // bucket width of the thresholds
     uint32_t *next_group;
     uint32_t *err;
 };
@@ -135,68 +148,129 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) td_trees(TreeArgs A) {
     const size_t gw = (size_t)blockIdx.x * kWarpsPerBlock + wib;
     uint64_t *lab = A.lab + gw * A.n_nodes;
     uint32_t *inq = A.inq + gw * A.n_nodes;
+    uint32_t *fmark = A.fmark + gw * A.n_nodes;
     uint32_t *touched = A.touched + gw * A.n_nodes;
     uint32_t *fa = A.fa + gw * A.n_nodes, *fb = A.fb + gw * A.n_nodes;
-    __shared__ uint32_t s_next[kWarpsPerBlock], s_touched[kWarpsPerBlock];
+    uint32_t *far = A.far + gw * A.n_nodes;
+    __shared__ uint32_t s_next[kWarpsPerBlock], s_touched[kWarpsPerBlock], s_far[kWarpsPerBlock];
     uint32_t stamp = A.stamp[gw];
+    // rounds of a search at most: every round settles or re-labels a node,
+    // and a node's label improves a bounded number of times
+    const uint64_t max_rounds = 8ull * A.n_nodes + (1ull << 20);
     for (;;) {
         uint32_t g = 0;
         if (lane == 0) g = atomicAdd(A.next_group, 1u);
         g = __shfl_sync(0xFFFFFFFFu, g, 0);
         if (g >= A.n_groups) break;
         const GroupRec G = A.groups[g];
+        const uint32_t tmark = ++stamp;  // this tree's mark of the nodes in its far pile
         if (lane == 0) {
             __stcg(reinterpret_cast<unsigned long long *>(lab + G.src), ((uint64_t)G.t0 << 32) | kNoEdge);
             __stcg(touched, G.src);
             __stcg(fa, G.src);
         }
-        uint32_t nf = 1, nt = 1;
+        uint32_t nn = 1, nt = 1, nfar = 0;
+        uint64_t theta = (uint64_t)G.t0 + A.delta_ms;  // labels below theta are expanded now, the rest wait
         uint64_t ub = kUnreached;  // latest destination arrival so far (ms), once all are reached
         __threadfence_block();
         __syncwarp();
         bool bounded = true;
-        for (uint32_t round = 0; nf > 0; round++) {
-            if (round > A.n_nodes) {  // a label-correcting search settles within n rounds
+        for (uint64_t round = 0;; round++) {
+            if (round > max_rounds) {
                 bounded = false;
                 break;
             }
-            stamp++;
-            if (lane == 0) {
-                s_next[wib] = 0;
-                s_touched[wib] = nt;
-            }
-            __syncwarp();
-            for (uint32_t i = lane; i < nf; i += 32) {
-                const uint32_t u = __ldcg(fa + i);
-                const uint64_t lu = __ldcg(reinterpret_cast<const unsigned long long *>(lab + u));
-                const uint64_t tu = lu >> 32;
-                if (ub != kUnreached && tu >= ub) continue;
-                const uint2 *crow = A.cms + (size_t)bin_of(A, tu) * A.n_edges;
-                const uint32_t j1 = A.out_off[u + 1];
-                for (uint32_t j = A.out_off[u]; j < j1; j++) {
-                    const uint2 ev = A.adj[j];
-                    const uint64_t at = arrive(crow[ev.x], tu);
-                    if (at > 0xFFFFFFFFull || (ub != kUnreached && at > ub)) continue;
-                    const unsigned long long cand = (at << 32) | ev.x;
-                    const unsigned long long old =
-                        atomicMin(reinterpret_cast<unsigned long long *>(lab + ev.y), cand);
-                    if (cand < old) {
-                        if (old == kUnreached) __stcg(touched + atomicAdd(&s_touched[wib], 1u), ev.y);
-                        if (atomicExch(inq + ev.y, stamp) != stamp) __stcg(fb + atomicAdd(&s_next[wib], 1u), ev.y);
+            if (nn > 0) {
+                // one round of the near set: relax the out-edges of its nodes
+                stamp++;
+                if (lane == 0) {
+                    s_next[wib] = 0;
+                    s_touched[wib] = nt;
+                    s_far[wib] = nfar;
+                }
+                __syncwarp();
+                for (uint32_t i = lane; i < nn; i += 32) {
+                    const uint32_t u = __ldcg(fa + i);
+                    const uint64_t tu = __ldcg(reinterpret_cast<const unsigned long long *>(lab + u)) >> 32;
+                    if (tu >= ub) continue;
+                    const uint2 *crow = A.cms + (size_t)bin_of(A, tu) * A.n_edges;
+                    const uint32_t j1 = A.out_off[u + 1];
+                    for (uint32_t j = A.out_off[u]; j < j1; j++) {
+                        const uint2 ev = A.adj[j];
+                        const uint64_t at = arrive(crow[ev.x], tu);
+                        if (at > 0xFFFFFFFFull || at > ub) continue;
+                        const unsigned long long cand = (at << 32) | ev.x;
+                        const unsigned long long old =
+                            atomicMin(reinterpret_cast<unsigned long long *>(lab + ev.y), cand);
+                        if (cand < old) {
+                            if (old == kUnreached) __stcg(touched + atomicAdd(&s_touched[wib], 1u), ev.y);
+                            if (at < theta) {
+                                if (atomicExch(inq + ev.y, stamp) != stamp)
+                                    __stcg(fb + atomicAdd(&s_next[wib], 1u), ev.y);
+                            } else if (atomicExch(fmark + ev.y, tmark) != tmark) {
+                                __stcg(far + atomicAdd(&s_far[wib], 1u), ev.y);
+                            }
+                        }
                     }
                 }
+                __threadfence_block();
+                __syncwarp();
+                nn = s_next[wib];
+                nt = s_touched[wib];
+                nfar = s_far[wib];
+                uint32_t *t = fa;
+                fa = fb;
+                fb = t;
+                __syncwarp();
+                continue;
+            }
+            // the near set is empty: every label below theta is final
+            ub = dest_bound(A, G, lab, lane);
+            if (ub < theta || nfar == 0) break;  // every destination settled (or nothing left)
+            // next threshold: move the far nodes below it to the near set, keep
+            // the rest (the far list holds each node once: its mark)
+            uint64_t next = theta + A.delta_ms;
+            for (int pass = 0; pass < 2 && nn == 0 && nfar > 0; pass++) {
+                uint32_t kept = 0;
+                uint64_t tmin = kUnreached;
+                for (uint32_t c0 = 0; c0 < nfar; c0 += 32) {
+                    const uint32_t i = c0 + lane;
+                    uint32_t v = 0;
+                    uint64_t tv = kUnreached;
+                    if (i < nfar) {
+                        v = __ldcg(far + i);
+                        tv = __ldcg(reinterpret_cast<const unsigned long long *>(lab + v)) >> 32;
+                    }
+                    const bool drop = i < nfar && tv < theta;            // settled in an earlier bucket
+                    const bool move = i < nfar && tv >= theta && tv < next;
+                    const bool keep = i < nfar && tv >= next;
+                    const uint32_t mk = __ballot_sync(0xFFFFFFFFu, keep), mm = __ballot_sync(0xFFFFFFFFu, move);
+                    const uint32_t below = (1u << lane) - 1u;
+                    __syncwarp();  // every lane has read its entry before any is overwritten
+                    if (drop || move) __stcg(fmark + v, 0u);
+                    if (keep) __stcg(far + kept + __popc(mk & below), v);
+                    if (move) __stcg(fa + nn + __popc(mm & below), v);
+                    kept += __popc(mk);
+                    nn += __popc(mm);
+                    uint64_t tk = keep ? tv : kUnreached;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const uint64_t y = __shfl_xor_sync(0xFFFFFFFFu, tk, o);
+                        tk = y < tk ? y : tk;
+                    }
+                    tmin = tk < tmin ? tk : tmin;
+                }
+                nfar = kept;
+                theta = next;
+                // nothing below the threshold: jump to the earliest far label
+                if (nn == 0 && nfar > 0) next = tmin + A.delta_ms;
             }
             __threadfence_block();
             __syncwarp();
-            nf = s_next[wib];
-            nt = s_touched[wib];
-            uint32_t *t = fa;
-            fa = fb;
-            fb = t;
-            if ((round & 3u) == 3u) ub = dest_bound(A, G, lab, lane);
-            __syncwarp();
         }
         if (!bounded && lane == 0) atomicOr(A.err, kErrBound);
+        // far marks of the nodes still in the far pile (the others were cleared)
+        for (uint32_t i = lane; i < nfar; i += 32) __stcg(fmark + __ldcg(far + i), 0u);
         // paths of the group's trips, in travel order, timed from each trip's departure
         for (uint32_t q = lane; q < G.count; q += 32) {
             const uint32_t j = A.order[G.first + q];
@@ -342,7 +416,7 @@ int gpu_setup(lpsim_assign *a) {
     if (!A.path_off || !A.path_len || !A.tsp || !A.cursor || !A.next_group || !A.err)
         return fail(LPSIM_E_OOM, "device allocation failed");
     // workspaces: as many warps as fit the budget, at most 16 per SM
-    const uint64_t per_warp = (uint64_t)a->n_nodes * (8 + 4 * 4);
+    const uint64_t per_warp = (uint64_t)a->n_nodes * (8 + 6 * 4);
     uint64_t warps = std::min<uint64_t>((uint64_t)g->n_sm * kBlocksPerSm * kWarpsPerBlock,
                                         std::max<uint64_t>(kWorkspaceBudget / std::max<uint64_t>(per_warp, 1), 1));
     warps = std::max<uint64_t>(kWarpsPerBlock, warps / kWarpsPerBlock * kWarpsPerBlock);
@@ -353,11 +427,15 @@ int gpu_setup(lpsim_assign *a) {
     A.touched = static_cast<uint32_t *>(g->alloc(nn * 4));
     A.fa = static_cast<uint32_t *>(g->alloc(nn * 4));
     A.fb = static_cast<uint32_t *>(g->alloc(nn * 4));
+    A.far = static_cast<uint32_t *>(g->alloc(nn * 4));
+    A.fmark = static_cast<uint32_t *>(g->alloc(nn * 4));
     A.stamp = static_cast<uint32_t *>(g->alloc(warps * 4));
-    if (!A.lab || !A.inq || !A.touched || !A.fa || !A.fb || !A.stamp)
+    if (!A.lab || !A.inq || !A.touched || !A.fa || !A.fb || !A.far || !A.fmark || !A.stamp)
         return fail(LPSIM_E_OOM, "device allocation of the search workspaces failed");
     CU(cudaMemsetAsync(A.lab, 0xFF, nn * 8, g->stream));
     CU(cudaMemsetAsync(A.inq, 0, nn * 4, g->stream));
+    CU(cudaMemsetAsync(A.fmark, 0, nn * 4, g->stream));
+    A.delta_ms = kDeltaMs;
     CU(cudaMemsetAsync(A.stamp, 0, warps * 4, g->stream));
     CU(cudaStreamSynchronize(g->stream));
     return LPSIM_OK;

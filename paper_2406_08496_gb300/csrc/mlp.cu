@@ -461,6 +461,7 @@ constexpr size_t kFwdSmem = 1024 + 5 * kSliceA + kFwdBStages * kSliceB + 128;  /
 
 struct FwdArgs {
     int n_tiles;
+    int l1_k16;  // 16-wide K steps of layer 1 that hold real inputs (the rest of the 64 columns is zero padding)
     const float *b1, *b2, *b3, *w4, *b4;
     float *y;
     uint32_t *err;
@@ -564,9 +565,13 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                         const uint32_t a0 = l == 0 ? smem_u32(sX) : smem_u32(sA + ks * kSliceA);
                         const uint32_t b0 = smem_u32(sB + s * kSliceB);
+                        // layer 1: only the K steps that hold real inputs (zero columns add nothing)
+                        const int nkk = l == 0 ? g.l1_k16 : kBK / 16;
 #pragma unroll
                         for (int kk = 0; kk < kBK / 16; kk++)
-                            umma_f16(tmem, umma_desc(a0 + kk * 32), umma_desc(b0 + kk * 32), idesc, (ks | kk) != 0);
+                            if (kk < nkk)
+                                umma_f16(tmem, umma_desc(a0 + kk * 32), umma_desc(b0 + kk * 32), idesc,
+                                         (ks | kk) != 0);
                         umma_commit(&b_empty[s]);
                     }
                     if (l == 0) umma_commit(x_empty);
@@ -941,6 +946,7 @@ int forward_fused(lpsim_mlp *m) {
     }
     FwdArgs g{};
     g.n_tiles = m->B / kBM;
+    g.l1_k16 = (m->nf + 15) / 16;
     g.b1 = m->P[1];
     g.b2 = m->P[3];
     g.b3 = m->P[5];
