@@ -311,7 +311,12 @@ def assignment_arm(args, L, torch):
                      "iterations": len(r["history"]), "gaps": [round(g, 5) for _, g in hist],
                      "gap_wall_s": [round(t, 2) for t, _ in hist],
                      "sim_s_mean": float(np.mean([h["sim_s"] for h in sims])) if sims else None,
-                     "paths_s_mean": float(np.mean([h["paths_s"] for h in sims])) if sims else None}
+                     "paths_s_mean": float(np.mean([h["paths_s"] for h in sims])) if sims else None,
+                     "train_s_mean": (float(np.mean([h["train_s"] for h in sims if "train_s" in h]))
+                                      if any("train_s" in h for h in sims) else None),
+                     "surrogate_iter_s_mean": (float(np.mean([h["iter_s"] for h in r["history"]
+                                                              if h["kind"] == "surrogate"]))
+                                               if any(h["kind"] == "surrogate" for h in r["history"]) else None)}
     trips = int(len(dem["depart_step"]))
     label = {"paper": "assignment-224k-nodes-2.82M-trips", "small": "assignment-27k-nodes-340k-trips",
              "tiny": "assignment-3k-nodes-30k-trips"}[args.assignment_scale]

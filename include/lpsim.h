@@ -176,6 +176,35 @@ int lpsim_load_network(lpsim_ctx **out, const lpsim_network *net, const lpsim_pa
 int lpsim_load_demand(lpsim_ctx *ctx, uint64_t n_trips, const uint32_t *depart_step, const uint64_t *route_off,
                       const uint32_t *route_edges, uint32_t *out_vehicle_id);
 
+/* Vehicle types (Algorithm 1 State: the vehicle type V, recorded whenever a
+ * vehicle moves onto an edge; multimodal traffic is the paper's next step,
+ * Sec. 5).  A type carries its own car-following parameters (eq. Car
+ * Following: IDM with delta = 4) and a top speed: a vehicle's free-flow
+ * speed on an edge (Algorithm 1: v <- v_free) is min(edge limit, vmax), the
+ * IDM and the no-crash clamp use the type's a, b, s0, T.  Lane change and
+ * gap acceptance do not depend on the type. */
+#define LPSIM_MAX_VEHICLE_TYPES 8u
+typedef struct lpsim_vehicle_type {
+    float a;     /* IDM acceleration potential, m/s^2 (> 0) */
+    float b;     /* IDM comfortable deceleration, m/s^2 (> 0) */
+    float s0;    /* standstill spacing, m (>= 0) */
+    float T;     /* desired time headway, s */
+    float vmax;  /* top speed, m/s, in (0, 254] */
+} lpsim_vehicle_type;
+
+/* Types 0..n_types-1 (1 <= n_types <= LPSIM_MAX_VEHICLE_TYPES), before
+ * lpsim_load_demand_typed.  Without this call every vehicle has the
+ * lpsim_params a, b, s0, T and no top speed of its own.  Errors:
+ * LPSIM_E_INVALID_ARG on a count or value out of range; LPSIM_E_STATE once
+ * trips are loaded. */
+int lpsim_set_vehicle_types(lpsim_ctx *ctx, uint32_t n_types, const lpsim_vehicle_type *types);
+
+/* lpsim_load_demand with a vehicle type per trip: vtype[j] (n_trips entries,
+ * each below the number of types set; NULL = every trip type 0).  Errors as
+ * lpsim_load_demand, plus LPSIM_E_INVALID_ARG on a type out of range. */
+int lpsim_load_demand_typed(lpsim_ctx *ctx, uint64_t n_trips, const uint32_t *depart_step, const uint64_t *route_off,
+                            const uint32_t *route_edges, const uint8_t *vtype, uint32_t *out_vehicle_id);
+
 /* Advance n_steps steps of Algorithm 1 (Vehicle Propagation, Sec. 3.1-3.2):
  * each step moves every vehicle from its step-k state to step k+1 using only
  * step-k state (eq. vehicle_dynamics, Sec. 3.1) -- departure when the first

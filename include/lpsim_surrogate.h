@@ -44,9 +44,27 @@ int lpsim_mlp_forward(lpsim_mlp *m, uint64_t n, const float *X, float *y);
  * parameter tensor into grads[8] (each nullable). */
 int lpsim_mlp_grad(lpsim_mlp *m, uint64_t n, const float *X, const float *t, float *loss, float *const *grads);
 
+/* Training pool: samples (n rows of n_features f32 inputs X and targets t,
+ * host arrays, copied) appended to a device-resident pool that the model
+ * keeps between calls, so a training set that grows with every simulation
+ * is uploaded once per row.  lpsim_mlp_pool_clear empties it.  Errors:
+ * LPSIM_E_INVALID_ARG (NULL arrays with n > 0), LPSIM_E_OOM. */
+int lpsim_mlp_pool_add(lpsim_mlp *m, uint64_t n, const float *X, const float *t);
+int lpsim_mlp_pool_clear(lpsim_mlp *m);
+uint64_t lpsim_mlp_pool_size(const lpsim_mlp *m);
+
 /* `steps` Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr)
- * on minibatches drawn from shuffled passes over the n samples; losses
- * (nullable, `steps` entries) receives each step's batch loss. */
+ * on minibatches of min(batch, pool size) rows drawn from shuffled passes
+ * over the pool: pass q visits every row once in the order of a seeded
+ * pseudo-random permutation (a Feistel network with cycle walking, keyed by
+ * shuffle_seed and q), gathered on the device, so no minibatch crosses the
+ * host.  losses (nullable, `steps` entries) receives each step's batch loss.
+ * Errors: LPSIM_E_INVALID_ARG on an empty pool; LPSIM_E_TIMEOUT (a bounded
+ * device wait or permutation walk gave up); LPSIM_E_OOM. */
+int lpsim_mlp_train_pool(lpsim_mlp *m, uint32_t steps, float lr, uint64_t shuffle_seed, float *losses);
+
+/* lpsim_mlp_pool_clear, lpsim_mlp_pool_add of the n samples, then
+ * lpsim_mlp_train_pool. */
 int lpsim_mlp_train(lpsim_mlp *m, uint64_t n, const float *X, const float *t, uint32_t steps, float lr,
                     uint64_t shuffle_seed, float *losses);
 

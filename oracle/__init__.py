@@ -36,6 +36,10 @@ class OrcParams(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("bin_steps", ctypes.c_uint32), ("n_bins", ctypes.c_uint32)]
 
 
+class OrcVehicleType(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_float) for n in ("a", "b", "s0", "T", "vmax")]
+
+
 def build() -> str:
     src = os.path.join(_HERE, "lpsim_oracle.c")
     hdr = os.path.join(_HERE, "lpsim_oracle.h")
@@ -62,6 +66,8 @@ def _lib():
             lib.orc_create.argtypes = [ctypes.POINTER(P), ctypes.c_uint32, ctypes.c_uint32, P, P, P, P, P, P, P,
                                        ctypes.POINTER(OrcParams)]
             lib.orc_load_demand.argtypes = [P, ctypes.c_uint64, P, P, P, P]
+            lib.orc_load_demand_typed.argtypes = [P, ctypes.c_uint64, P, P, P, P, P]
+            lib.orc_set_vehicle_types.argtypes = [P, ctypes.c_uint32, P]
             lib.orc_step.argtypes = [P, ctypes.c_uint32]
             lib.orc_run.argtypes = [P, ctypes.c_uint32, P]
             lib.orc_get_state.argtypes = [P, P, P, P, P, P, P]
@@ -107,7 +113,9 @@ def idm_speed(v: float, vf: float, s: float, v0: float, **params) -> float:
 class Oracle:
     """One simulation on the CPU oracle."""
 
-    def __init__(self, net: dict, params: dict | None = None):
+    def __init__(self, net: dict, params: dict | None = None, vehicle_types: list | None = None):
+        """vehicle_types (optional): per type a dict of a, b, s0, T and vmax;
+        trips then name their type in the demand's "vtype" array."""
         self.lib = _lib()
         self.params = dict(DEFAULT_PARAMS)
         if params:
@@ -127,6 +135,10 @@ class Oracle:
                                    ctypes.byref(self._p)), "orc_create")
         self.h = h
         self.n = 0
+        if vehicle_types:
+            arr = (OrcVehicleType * len(vehicle_types))(*[OrcVehicleType(**t) for t in vehicle_types])
+            _check(self.lib.orc_set_vehicle_types(self.h, len(vehicle_types), ctypes.cast(arr, ctypes.c_void_p)),
+                   "orc_set_vehicle_types")
 
     def load_demand(self, dem: dict) -> np.ndarray:
         dep = np.ascontiguousarray(dem["depart_step"], dtype=np.uint32)
@@ -134,8 +146,11 @@ class Oracle:
         edges = np.ascontiguousarray(dem["route_edges"], dtype=np.uint32)
         if edges.size == 0:
             edges = np.zeros(1, dtype=np.uint32)
+        vt = dem.get("vtype")
+        vt = None if vt is None else np.ascontiguousarray(vt, dtype=np.uint8)
         vid = np.empty(len(dep), dtype=np.uint32)
-        _check(self.lib.orc_load_demand(self.h, len(dep), _p(dep), _p(off), _p(edges), _p(vid)), "orc_load_demand")
+        _check(self.lib.orc_load_demand_typed(self.h, len(dep), _p(dep), _p(off), _p(edges), _p(vt), _p(vid)),
+               "orc_load_demand")
         self.n = len(dep)
         return vid
 

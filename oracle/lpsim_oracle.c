@@ -27,6 +27,10 @@
  *                   s_star = s0 + max(0, v*T + v*(v - v_f)/(2 sqrt(a b)))
  *                   acc = a*(1 - (v/v0)^4 - (s_star/s)^2),  v' = max(0, v + acc*dt)
  *                 else v' = v_free = the edge speed limit (Algorithm 1).
+ *      types      (Algorithm 1 State: vehicle type V; multimodal, Sec. 5)
+ *                 a vehicle of type t uses the type's a, b, s0, T above and
+ *                 v0 = v_free = min(edge limit, vmax_t); type 0 defaults to
+ *                 the run parameters and vmax 254.
  *      move       x' = x + v'*dt; no-crash clamp (Sec. 3.1 Remark: vehicles do
  *                 not crash): if x' > c_f - s0 then x' = max(x, c_f - s0), v' = 0.
  *      edge end   x' >= L_e: on the last route edge the vehicle arrives; else,
@@ -74,9 +78,16 @@ enum { ACT_NONE = 0, ACT_STAY, ACT_INTEND, ACT_HOLD, ACT_CROSS, ACT_ARRIVE };
 #define EMPTY 255u
 #define NO_CLAIM 0xFFFFFFFFu
 
+typedef struct {
+    float a, s0, T, two_sqrt_ab, vmax;
+} vtype_rec;
+
 struct orc_sim {
     orc_params p;
     float two_sqrt_ab;
+    vtype_rec types[ORC_MAX_TYPES];
+    uint32_t n_types;
+    uint8_t *vt;                /* vehicle type, by id */
     /* network */
     uint32_t n_nodes, n_edges;
     uint32_t *src, *dst, *len, *green, *n_in, *n_out, *n_phase;
@@ -164,15 +175,26 @@ static uint32_t entry_lane(const orc_sim *s, uint32_t id, uint64_t q) {
     return EMPTY;
 }
 
-float orc_idm_speed(const orc_params *p, float v, float vf, float s, float v0) {
-    float two_sqrt_ab = (float)(2.0 * sqrt((double)p->a * (double)p->b));
+/* the IDM branch for a vehicle of type y: speed v, leader byte speed vf,
+ * gap s, free-flow speed v0 */
+static float idm_speed_type(const vtype_rec *y, float dt, float v, float vf, float s, float v0) {
     float dv = v - vf;
-    float z = v * p->T + (v * dv) / two_sqrt_ab;
-    float s_star = p->s0 + fmax0(z);
+    float z = v * y->T + (v * dv) / y->two_sqrt_ab;
+    float s_star = y->s0 + fmax0(z);
     float r = v / v0;
     float q = s_star / s;
-    float acc = p->a * ((1.0f - (r * r) * (r * r)) - q * q);
-    return fmax0(v + acc * p->dt);
+    float acc = y->a * ((1.0f - (r * r) * (r * r)) - q * q);
+    return fmax0(v + acc * dt);
+}
+
+float orc_idm_speed(const orc_params *p, float v, float vf, float s, float v0) {
+    vtype_rec y;
+    y.a = p->a;
+    y.s0 = p->s0;
+    y.T = p->T;
+    y.two_sqrt_ab = (float)(2.0 * sqrt((double)p->a * (double)p->b));
+    y.vmax = 254.0f;
+    return idm_speed_type(&y, p->dt, v, vf, s, v0);
 }
 
 static int put(orc_sim *s, uint64_t idx, uint8_t val) {
@@ -224,6 +246,12 @@ int orc_create(orc_sim **out, uint32_t n_nodes, uint32_t n_edges, const uint32_t
     *out = s;
     s->p = *p;
     s->two_sqrt_ab = (float)(2.0 * sqrt((double)p->a * (double)p->b));
+    s->n_types = 1;
+    s->types[0].a = p->a;
+    s->types[0].s0 = p->s0;
+    s->types[0].T = p->T;
+    s->types[0].two_sqrt_ab = s->two_sqrt_ab;
+    s->types[0].vmax = 254.0f;
     s->n_nodes = n_nodes;
     s->n_edges = n_edges;
     XALLOC(s->src, n_edges); XALLOC(s->dst, n_edges); XALLOC(s->len, n_edges); XALLOC(s->v0, n_edges);
@@ -270,12 +298,38 @@ int orc_create(orc_sim **out, uint32_t n_nodes, uint32_t n_edges, const uint32_t
     return 0;
 }
 
+int orc_set_vehicle_types(orc_sim *s, uint32_t n_types, const orc_vehicle_type *types) {
+    if (!s || !types || n_types == 0 || n_types > ORC_MAX_TYPES) return -1;
+    if (s->loaded) return -4;
+    for (uint32_t t = 0; t < n_types; t++) {
+        const orc_vehicle_type *y = &types[t];
+        if (!(y->a > 0.0f) || !(y->b > 0.0f) || !(y->s0 >= 0.0f) || !(y->T == y->T) || !(y->vmax > 0.0f) ||
+            !(y->vmax <= 254.0f))
+            return -1;
+        s->types[t].a = y->a;
+        s->types[t].s0 = y->s0;
+        s->types[t].T = y->T;
+        s->types[t].two_sqrt_ab = (float)(2.0 * sqrt((double)y->a * (double)y->b));
+        s->types[t].vmax = y->vmax;
+    }
+    s->n_types = n_types;
+    return 0;
+}
+
 int orc_load_demand(orc_sim *s, uint64_t n, const uint32_t *depart_step, const uint64_t *route_off,
                     const uint32_t *route_edges, uint32_t *out_vid) {
+    return orc_load_demand_typed(s, n, depart_step, route_off, route_edges, NULL, out_vid);
+}
+
+int orc_load_demand_typed(orc_sim *s, uint64_t n, const uint32_t *depart_step, const uint64_t *route_off,
+                          const uint32_t *route_edges, const uint8_t *vtype, uint32_t *out_vid) {
     if (!s || !depart_step || !route_off || !route_edges) return -1;
     if (s->loaded) return -4;
     if (n >= 0xFFFFFFFFull) return -1;
     if (route_off[0] != 0) return -1;
+    if (vtype)
+        for (uint64_t j = 0; j < n; j++)
+            if (vtype[j] >= s->n_types) return -1;
     for (uint64_t j = 0; j < n; j++) {
         if (route_off[j + 1] <= route_off[j]) return -1; /* empty route */
         for (uint64_t q = route_off[j]; q < route_off[j + 1]; q++) {
@@ -308,13 +362,14 @@ int orc_load_demand(orc_sim *s, uint64_t n, const uint32_t *depart_step, const u
         free(tmp);
     }
     s->n = n;
-    XALLOC(s->dep, n); XALLOC(s->roff, n + 1);
+    XALLOC(s->dep, n); XALLOC(s->roff, n + 1); XALLOC(s->vt, n);
     uint64_t total = route_off[n];
     XALLOC(s->redge, total);
     s->roff[0] = 0;
     for (uint64_t id = 0; id < n; id++) {
         uint64_t j = order[id];
         s->dep[id] = depart_step[j];
+        s->vt[id] = vtype ? vtype[j] : 0;
         uint64_t len = route_off[j + 1] - route_off[j];
         memcpy(s->redge + s->roff[id], route_edges + route_off[j], len * sizeof(uint32_t));
         s->roff[id + 1] = s->roff[id] + len;
@@ -360,15 +415,19 @@ static void decide(orc_sim *s, uint32_t i, uint32_t k) {
     for (uint32_t q = c + 1; q < len; q++)
         if (s->Mcur[base + q] != EMPTY) { has_f = 1; cf = q; break; }
 
+    /* the vehicle's type: its IDM parameters, and its free-flow speed on
+     * this edge, the lower of the edge limit and the type's top speed */
+    const vtype_rec *y = &s->types[s->vt[i]];
+    float v0 = s->v0[e] < y->vmax ? s->v0[e] : y->vmax;
     float vn;
     float d_front = (2.0f * p->dt) * v;
     if (has_f && ((float)cf - x) <= d_front)
-        vn = orc_idm_speed(p, v, (float)s->Mcur[base + cf], (float)cf - x, s->v0[e]);
+        vn = idm_speed_type(y, p->dt, v, (float)s->Mcur[base + cf], (float)cf - x, v0);
     else
-        vn = s->v0[e];
+        vn = v0;
     float xn = x + vn * p->dt;
     if (has_f) {
-        float lim = (float)cf - p->s0;
+        float lim = (float)cf - y->s0;
         if (xn > lim) { xn = x > lim ? x : lim; vn = 0.0f; }
     }
     s->xn[i] = xn;
@@ -722,7 +781,7 @@ void orc_destroy(orc_sim *s) {
                     s->act, s->tlane, s->accept, s->dir, s->e, s->r, s->t_enter, s->dep_act, s->arr, s->x,
                     s->v, s->xn, s->vn, s->old_cell, s->active, s->next_active, s->qoff, s->qhead, s->qid,
                     s->pending, s->is_pending, s->dreq, s->claim, s->ent, s->ext, s->tts, s->bin_in,
-                    s->bin_tt, s->bin_cnt, s->bin_occ};
+                    s->bin_tt, s->bin_cnt, s->bin_occ, s->vt};
     for (size_t j = 0; j < sizeof ptrs / sizeof ptrs[0]; j++) free(ptrs[j]);
     free(s);
 }

@@ -44,6 +44,18 @@ typedef struct orc_params {
 
 typedef struct orc_sim orc_sim;
 
+/* Vehicle type (Algorithm 1 State: vehicle type V, recorded when the vehicle
+ * moves onto an edge; multimodal traffic is the paper's next step, Sec. 5):
+ * its own car-following parameters and a top speed.  The free-flow speed of
+ * a vehicle on an edge is min(edge limit, vmax) and the IDM uses the type's
+ * a, b, s0, T (delta = 4); the no-crash clamp keeps the type's s0. */
+typedef struct orc_vehicle_type {
+    float a, b, s0, T;  /* IDM: max accel, comfortable decel, standstill gap, headway */
+    float vmax;         /* top speed, m/s (in (0, 254]) */
+} orc_vehicle_type;
+
+#define ORC_MAX_TYPES 8
+
 /* Network: node i has green_steps[i] steps of green per approach (0 =
  * uncontrolled); edge e goes src[e] -> dst[e], is len_m[e] metres long
  * (ceil'ed to whole cells), has lanes[e] in 1..4 and speed limit vmax[e].
@@ -60,6 +72,16 @@ int orc_create(orc_sim **out, uint32_t n_nodes, uint32_t n_edges,
  * (nullable) receives trip j's id. */
 int orc_load_demand(orc_sim *s, uint64_t n_trips, const uint32_t *depart_step,
                     const uint64_t *route_off, const uint32_t *route_edges, uint32_t *out_vid);
+
+/* Vehicle types 0..n_types-1 (n_types <= ORC_MAX_TYPES), before
+ * orc_load_demand*; without this call there is one type with the params'
+ * a, b, s0, T and vmax 254. */
+int orc_set_vehicle_types(orc_sim *s, uint32_t n_types, const orc_vehicle_type *types);
+
+/* orc_load_demand with a type per trip (vtype[j] < the number of types;
+ * NULL: every trip type 0). */
+int orc_load_demand_typed(orc_sim *s, uint64_t n_trips, const uint32_t *depart_step, const uint64_t *route_off,
+                          const uint32_t *route_edges, const uint8_t *vtype, uint32_t *out_vid);
 
 int orc_step(orc_sim *s, uint32_t n_steps);
 

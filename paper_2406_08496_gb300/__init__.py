@@ -27,13 +27,14 @@ DEFAULT_PARAMS = dict(dt=0.5, a=1.0, b=1.5, s0=2.0, T=1.5, x0=100.0, g_a=2.0, g_
 FLAG_NO_SORT = 1
 
 EXPORTED = ["lpsim_last_error", "lpsim_version", "lpsim_set_allocator", "lpsim_load_network",
-            "lpsim_load_demand", "lpsim_step", "lpsim_run", "lpsim_reset", "lpsim_link_stats",
+            "lpsim_load_demand", "lpsim_load_demand_typed", "lpsim_set_vehicle_types", "lpsim_step", "lpsim_run", "lpsim_reset", "lpsim_link_stats",
             "lpsim_get_trips", "lpsim_get_state", "lpsim_lane_map_size", "lpsim_get_lane_map",
             "lpsim_get_counters", "lpsim_set_kernel_timing", "lpsim_get_kernel_times", "lpsim_get_state_noalloc",
             "lpsim_load_network_batch", "lpsim_load_demand_batch", "lpsim_batch_offsets", "lpsim_snapshot",
             "lpsim_restore", "lpsim_autotune", "lpsim_set_config", "lpsim_destroy",
             "lpsim_mlp_create", "lpsim_mlp_set_params", "lpsim_mlp_get_params", "lpsim_mlp_forward",
-            "lpsim_mlp_grad", "lpsim_mlp_train", "lpsim_mlp_apply_grads", "lpsim_mlp_gemm_test", "lpsim_mlp_time", "lpsim_mlp_gelu_eval",
+            "lpsim_mlp_grad", "lpsim_mlp_train", "lpsim_mlp_apply_grads", "lpsim_mlp_pool_add",
+            "lpsim_mlp_pool_clear", "lpsim_mlp_pool_size", "lpsim_mlp_train_pool", "lpsim_mlp_gemm_test", "lpsim_mlp_time", "lpsim_mlp_gelu_eval",
             "lpsim_mlp_destroy",
             "lpsim_assign_create", "lpsim_assign_shortest_paths", "lpsim_assign_shortest_paths_gpu", "lpsim_assign_gap", "lpsim_assign_reroute",
             "lpsim_assign_route_excess", "lpsim_assign_reroute_worst", "lpsim_assign_route_length",
@@ -78,6 +79,10 @@ class TuneResult(ctypes.Structure):
                [("best_ms", ctypes.c_double), ("default_ms", ctypes.c_double), ("n_tried", ctypes.c_uint32)]
 
 
+class VehicleType(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_float) for n in ("a", "b", "s0", "T", "vmax")]
+
+
 class KernelTimes(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 4), ("launches", ctypes.c_uint64 * 4), ("p1_veh_steps", ctypes.c_uint64)]
 
@@ -115,6 +120,8 @@ def load_library(path: str | None = None):
     lib.lpsim_set_allocator.argtypes = [ALLOC_T, FREE_T, P]
     lib.lpsim_load_network.argtypes = [ctypes.POINTER(P), ctypes.POINTER(Network), ctypes.POINTER(Params), P]
     lib.lpsim_load_demand.argtypes = [P, ctypes.c_uint64, P, P, P, P]
+    lib.lpsim_load_demand_typed.argtypes = [P, ctypes.c_uint64, P, P, P, P, P]
+    lib.lpsim_set_vehicle_types.argtypes = [P, ctypes.c_uint32, P]
     lib.lpsim_step.argtypes = [P, ctypes.c_uint32]
     lib.lpsim_run.argtypes = [P, ctypes.c_uint32, ctypes.POINTER(RunResult)]
     lib.lpsim_reset.argtypes = [P]
@@ -144,6 +151,11 @@ def load_library(path: str | None = None):
     lib.lpsim_mlp_grad.argtypes = [P, ctypes.c_uint64, P, P, P, P]
     lib.lpsim_mlp_train.argtypes = [P, ctypes.c_uint64, P, P, ctypes.c_uint32, ctypes.c_float, ctypes.c_uint64, P]
     lib.lpsim_mlp_apply_grads.argtypes = [P, P, ctypes.c_float]
+    lib.lpsim_mlp_pool_add.argtypes = [P, ctypes.c_uint64, P, P]
+    lib.lpsim_mlp_pool_clear.argtypes = [P]
+    lib.lpsim_mlp_pool_size.argtypes = [P]
+    lib.lpsim_mlp_pool_size.restype = ctypes.c_uint64
+    lib.lpsim_mlp_train_pool.argtypes = [P, ctypes.c_uint32, ctypes.c_float, ctypes.c_uint64, P]
     lib.lpsim_mlp_gemm_test.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, P, P, P]
     lib.lpsim_mlp_time.argtypes = [P, ctypes.c_uint32, P, P]
     lib.lpsim_mlp_gelu_eval.argtypes = [ctypes.c_uint64, P, P, P]
@@ -228,7 +240,9 @@ class Simulation:
     edge_vmax, node_green and optionally edge_approach_rank (numpy arrays).
     """
 
-    def __init__(self, net: dict, params: dict | None = None, stream=None):
+    def __init__(self, net: dict, params: dict | None = None, stream=None, vehicle_types: list | None = None):
+        """vehicle_types (optional): per type a dict of a, b, s0, T and vmax;
+        trips then name their type in the demand's "vtype" array."""
         self.lib = load_library()
         self.params = dict(DEFAULT_PARAMS)
         if params:
@@ -254,13 +268,20 @@ class Simulation:
         _check(self.lib, self.lib.lpsim_load_network(ctypes.byref(h), ctypes.byref(desc), ctypes.byref(self._p), st))
         self.h = h
         self.n = 0
+        if vehicle_types:
+            arr = (VehicleType * len(vehicle_types))(*[VehicleType(**t) for t in vehicle_types])
+            _check(self.lib, self.lib.lpsim_set_vehicle_types(self.h, len(vehicle_types),
+                                                              ctypes.cast(arr, ctypes.c_void_p)))
 
     def load_demand(self, dem: dict) -> np.ndarray:
         dep = np.ascontiguousarray(dem["depart_step"], dtype=np.uint32)
         off = np.ascontiguousarray(dem["route_off"], dtype=np.uint64)
         edges = np.ascontiguousarray(dem["route_edges"], dtype=np.uint32)
+        vt = dem.get("vtype")
+        vt = None if vt is None else np.ascontiguousarray(vt, dtype=np.uint8)
         vid = np.empty(len(dep), dtype=np.uint32)
-        _check(self.lib, self.lib.lpsim_load_demand(self.h, len(dep), _p(dep), _p(off), _p(edges), _p(vid)))
+        _check(self.lib, self.lib.lpsim_load_demand_typed(self.h, len(dep), _p(dep), _p(off), _p(edges), _p(vt),
+                                                          _p(vid)))
         self.n = len(dep)
         return vid
 
@@ -477,6 +498,24 @@ class Surrogate:
         t = np.ascontiguousarray(t, dtype=np.float32)
         losses = np.empty(steps, np.float32)
         _check(self.lib, self.lib.lpsim_mlp_train(self.h, len(X), _p(X), _p(t), steps, lr, seed, _p(losses)))
+        return losses
+
+    def pool_add(self, X: np.ndarray, t: np.ndarray) -> None:
+        """Append training samples to the model's device-resident pool."""
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        _check(self.lib, self.lib.lpsim_mlp_pool_add(self.h, len(X), _p(X), _p(t)))
+
+    def pool_clear(self) -> None:
+        _check(self.lib, self.lib.lpsim_mlp_pool_clear(self.h))
+
+    def pool_size(self) -> int:
+        return int(self.lib.lpsim_mlp_pool_size(self.h))
+
+    def train_pool(self, steps: int, lr: float = 1e-3, seed: int = 0) -> np.ndarray:
+        """Adam steps on minibatches of shuffled passes over the pool."""
+        losses = np.empty(steps, np.float32)
+        _check(self.lib, self.lib.lpsim_mlp_train_pool(self.h, steps, lr, seed, _p(losses)))
         return losses
 
     def apply_grads(self, grads: dict, lr: float) -> None:

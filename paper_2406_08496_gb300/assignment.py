@@ -191,7 +191,6 @@ def msa(net: dict, dem: dict, mode: str = "plain", iterations: int = 10, fractio
     A = Assignment(net, dem, dt=0.5, seed=seed)
     search = A.shortest_paths_gpu if paths == "gpu" else A.shortest_paths
     mlp = Surrogate(n_features=N_FEATURES, batch=surrogate_batch, seed=seed) if mode == "surrogate" else None
-    train_X, train_t = [], []
     hist = []
     t_start = time.perf_counter()
     t_hit = None
@@ -228,14 +227,13 @@ def msa(net: dict, dem: dict, mode: str = "plain", iterations: int = 10, fractio
                 ref_in = ls["inflow"] if in_last is None else in_last
                 X = A.features(ls["inflow"], ls["occ"], ref_lr, ref_in)
                 ok = (ls["tt_cnt"].reshape(-1) >= 2) & np.isfinite(logratio.reshape(-1))
-                train_X.append(X[ok])
-                train_t.append(logratio.reshape(-1)[ok])
-                Xa, ta = np.concatenate(train_X), np.concatenate(train_t)
                 t1 = time.perf_counter()
-                losses = mlp.train(Xa, ta, steps=surrogate_steps, lr=1e-3, seed=seed + it)
+                # every simulation's samples join the model's device-resident pool
+                mlp.pool_add(X[ok], logratio.reshape(-1)[ok])
+                losses = mlp.train_pool(surrogate_steps, lr=1e-3, seed=seed + it)
                 rec["train_s"] = time.perf_counter() - t1
                 rec["surrogate_loss"] = float(losses[-20:].mean())
-                rec["surrogate_samples"] = int(len(ta))
+                rec["surrogate_samples"] = mlp.pool_size()
             tt_last, occ_last, lr_last, in_last = tt, ls["occ"], logratio, ls["inflow"]
             if t_hit is not None:
                 hist.append(rec)

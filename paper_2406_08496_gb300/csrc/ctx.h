@@ -65,6 +65,8 @@ struct lpsim_ctx {
         uint64_t stall_steps;
         unsigned long long last_progress;
     } snap_host{};
+    // vehicle types (lpsim_set_vehicle_types), uploaded with the trips
+    std::vector<lpsim_vehicle_type> types;
     // batched scenarios: prefix offsets of nodes, edges, canonical lane-map cells and trips
     std::vector<uint64_t> scen_node_off, scen_edge_off, scen_cell_off, scen_trip_off;
     // per-kernel timing: device spans stamped by the kernels themselves

@@ -57,6 +57,13 @@ struct Model {
     uint32_t bin_steps, n_bins;
 };
 
+// Vehicle type: its car-following parameters and top speed (free-flow speed
+// on an edge = min(edge limit, vmax)).
+constexpr uint32_t kMaxTypes = 8;
+struct __align__(32) TypeRec {
+    float a, s0, T, two_sqrt_ab, vmax, pad[3];
+};
+
 // Per route position q (the edge E = route[q] of some trip): the signal at
 // E's downstream node (green steps and phase count of the node, E's phase)
 // and the target lane on E for the movement onto route[q+1] (kNoLane when q
@@ -94,7 +101,7 @@ struct __align__(32) EdgeState {
     uint16_t sph;      // phases of that signal | phase of the current edge << 8
     uint16_t nlen;     // cells per lane of the next edge
     uint8_t nlanes;    // lanes of the next edge
-    uint8_t pad;
+    uint8_t vt;        // vehicle type (Algorithm 1 State: V, recorded on every new edge)
 };
 
 __device__ __forceinline__ EdgeState load_es(const EdgeState *p) {
@@ -110,7 +117,7 @@ __device__ __forceinline__ EdgeState load_es(const EdgeState *p) {
     r.sph = (uint16_t)(b.z >> 16);
     r.nlen = (uint16_t)(b.w & 0xFFFFu);
     r.nlanes = (uint8_t)((b.w >> 16) & 0xFFu);
-    r.pad = 0;
+    r.vt = (uint8_t)(b.w >> 24);
     return r;
 }
 
@@ -118,7 +125,8 @@ __device__ __forceinline__ void store_es(EdgeState *p, const EdgeState &r) {
     reinterpret_cast<uint4 *>(p)[0] = make_uint4(r.base, r.rpos, r.en, r.sg);
     reinterpret_cast<uint4 *>(p)[1] = make_uint4(__float_as_uint(r.v0), r.nmoff,
                                                  (uint32_t)r.len | ((uint32_t)r.sph << 16),
-                                                 (uint32_t)r.nlen | ((uint32_t)r.nlanes << 16));
+                                                 (uint32_t)r.nlen | ((uint32_t)r.nlanes << 16) |
+                                                     ((uint32_t)r.vt << 24));
 }
 
 // Vehicle slots.  x and v are double-buffered by step parity: step k reads
@@ -149,7 +157,7 @@ struct __align__(16) CrossRec {
     uint32_t nbase, nen, nsg;         // on the next edge: lane row, the edge after, its signal's green
     float x, vn, nv0;                 // position and speed now, next edge's speed limit
     uint16_t len, nlen, nsph;         // current / next edge length, next signal phases | phase << 8
-    uint8_t lane, tln;                // lane asked for, target lane on the next edge
+    uint8_t lane, tln;                // lane asked for | vehicle type << 2, target lane on the next edge
 };
 
 // What step_p2 needs of a departure request (packed by step_p1 for the queue
@@ -161,6 +169,7 @@ struct __align__(16) DepRec {
     float v0;                         // speed limit of the origin edge
     uint16_t len, nsph;               // origin edge length, signal phases | phase << 8
     uint8_t lane, tlc;                // lane asked for, target lane for the movement after the origin edge
+    uint8_t vt;                       // vehicle type
 };
 
 // What step_p2 needs of a lane-change intender (packed by step_p1).
@@ -186,6 +195,9 @@ struct Dev {
     const uint32_t *roff;      // route start of vehicle id (n + 1 entries)
     const RouteRec *rrec;      // per route position
     const uint64_t *hkey;      // lane-change draw key: scenario seed ^ scenario-local id * C1
+    const TypeRec *types;      // vehicle types (typed != 0)
+    const uint8_t *trip_vt;    // vehicle type by id (typed != 0)
+    uint32_t typed;            // 0: every vehicle has the run parameters and no top speed of its own
     uint32_t hkey_from_id;     // 1: one scenario, whose key is m.seed ^ id * C1 (no load needed)
     uint32_t *dep_act, *arr;
     uint8_t *status;

@@ -790,6 +790,52 @@ __global__ void weights_to_bf16(const float *W, int out, int in, __nv_bfloat16 *
     }
 }
 
+// Shuffled passes over the training pool without storing a permutation: row
+// p of pass q is perm_q(p), a bijection of [0, n) built from a four-round
+// balanced Feistel network on [0, 4^h) (4^h >= n, round function SplitMix64
+// of the seed, the pass and the round) with cycle walking back into [0, n)
+// (Black and Rogaway, "Ciphers with arbitrary finite domains", 2002).  A
+// walk longer than 4096 steps (probability below (3/4)^4096) sets an error
+// bit instead of looping on.
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;  // SplitMix64 output function (Steele, Lea, Flood 2014)
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t feistel(uint64_t x, uint32_t h, uint64_t key) {
+    const uint64_t mask = (1ull << h) - 1ull;
+    uint64_t L = x >> h, R = x & mask;
+#pragma unroll
+    for (uint32_t r = 0; r < 4; r++) {
+        const uint64_t f = mix64(key ^ (0x9E3779B97F4A7C15ull * (r + 1)) ^ R) & mask;
+        const uint64_t t = L ^ f;
+        L = R;
+        R = t;
+    }
+    return (L << h) | R;
+}
+
+// batch rows j < nb: pool row perm_pass(pos % n) for pos = pos0 + j
+__global__ void gather_batch(const float *PX, const float *Pt, uint64_t n, int nf, uint32_t h, uint64_t seed,
+                             uint64_t pos0, uint32_t nb, float *Xf, float *t, uint32_t *err) {
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < nb; j += gridDim.x * blockDim.x) {
+        const uint64_t pos = pos0 + j, pass = pos / n;
+        const uint64_t key = mix64(seed ^ (pass * 0xD1B54A32D192ED03ull));
+        uint64_t r = pos % n;
+        uint32_t walk = 0;
+        do {
+            r = feistel(r, h, key);
+        } while (r >= n && ++walk < 4096u);
+        if (r >= n) {
+            atomicOr(err, 64u);
+            r = pos % n;
+        }
+        for (int c = 0; c < nf; c++) Xf[(size_t)j * nf + c] = PX[r * nf + c];
+        t[j] = Pt[r];
+    }
+}
+
 // ------------------------------------------------------------- host side
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -873,6 +919,12 @@ struct lpsim_mlp {
     CUtensorMap mX0, mW[3], mH[3], mWT[3], mdZ[3], mdZT[3], mHT[3], mX0T;
     int adam_t = 0;
     uint64_t launches = 0;
+    // training pool: samples kept on the device (grown by doubling), and the
+    // per-step batch losses of a training call
+    float *pool_X = nullptr, *pool_t = nullptr;
+    uint64_t pool_n = 0, pool_cap = 0;
+    float *loss_hist = nullptr;
+    uint32_t loss_cap = 0;
 
     void *alloc(size_t bytes) {
         void *p = nullptr;
@@ -883,6 +935,9 @@ struct lpsim_mlp {
     ~lpsim_mlp() {
         if (stream) cudaStreamSynchronize(stream);
         for (void *b : blocks) cudaFree(b);
+        cudaFree(pool_X);
+        cudaFree(pool_t);
+        cudaFree(loss_hist);
         if (own_stream) cudaStreamDestroy(stream);
     }
 };
@@ -903,6 +958,7 @@ int mlp_check_err(lpsim_mlp *m) {
     uint32_t e = 0;
     CU(cudaMemcpyAsync(&e, m->err, 4, cudaMemcpyDeviceToHost, m->stream));
     CU(cudaStreamSynchronize(m->stream));
+    if (e & 64u) return fail(LPSIM_E_TIMEOUT, "training-pool permutation walk exceeded its bound");
     if (e) return fail(LPSIM_E_TIMEOUT, "tensor-core GEMM wait gave up (code " + std::to_string(e) + ")");
     return LPSIM_OK;
 }
@@ -1207,42 +1263,91 @@ int lpsim_mlp_grad(lpsim_mlp *m, uint64_t n, const float *X, const float *t, flo
     return LPSIM_OK;
 }
 
+int lpsim_mlp_pool_clear(lpsim_mlp *m) {
+    if (!m) return fail(LPSIM_E_INVALID_ARG, "NULL argument");
+    m->pool_n = 0;
+    return LPSIM_OK;
+}
+
+uint64_t lpsim_mlp_pool_size(const lpsim_mlp *m) { return m ? m->pool_n : 0; }
+
+int lpsim_mlp_pool_add(lpsim_mlp *m, uint64_t n, const float *X, const float *t) {
+    if (!m || (n && (!X || !t))) return fail(LPSIM_E_INVALID_ARG, "NULL argument");
+    if (n == 0) return LPSIM_OK;
+    const uint64_t need = m->pool_n + n;
+    if (need >= (1ull << 40)) return fail(LPSIM_E_INVALID_ARG, "training pool too large");
+    if (need > m->pool_cap) {
+        // grow by doubling; the rows so far move to the new buffers
+        const uint64_t cap = std::max<uint64_t>(need, std::max<uint64_t>(2 * m->pool_cap, 1u << 16));
+        float *nx = nullptr, *nt = nullptr;
+        if (cudaMalloc(&nx, cap * m->nf * 4) != cudaSuccess || cudaMalloc(&nt, cap * 4) != cudaSuccess) {
+            cudaFree(nx);
+            return fail(LPSIM_E_OOM, "device allocation of the training pool failed");
+        }
+        if (m->pool_n) {
+            CU(cudaMemcpyAsync(nx, m->pool_X, m->pool_n * m->nf * 4, cudaMemcpyDeviceToDevice, m->stream));
+            CU(cudaMemcpyAsync(nt, m->pool_t, m->pool_n * 4, cudaMemcpyDeviceToDevice, m->stream));
+        }
+        CU(cudaStreamSynchronize(m->stream));
+        cudaFree(m->pool_X);
+        cudaFree(m->pool_t);
+        m->pool_X = nx;
+        m->pool_t = nt;
+        m->pool_cap = cap;
+    }
+    CU(cudaMemcpyAsync(m->pool_X + m->pool_n * m->nf, X, n * m->nf * 4, cudaMemcpyHostToDevice, m->stream));
+    CU(cudaMemcpyAsync(m->pool_t + m->pool_n, t, n * 4, cudaMemcpyHostToDevice, m->stream));
+    CU(cudaStreamSynchronize(m->stream));
+    m->pool_n = need;
+    return LPSIM_OK;
+}
+
+int lpsim_mlp_train_pool(lpsim_mlp *m, uint32_t steps, float lr, uint64_t shuffle_seed, float *losses) {
+    if (!m) return fail(LPSIM_E_INVALID_ARG, "NULL argument");
+    const uint64_t n = m->pool_n;
+    if (n == 0) return fail(LPSIM_E_INVALID_ARG, "no samples in the training pool");
+    if (steps > m->loss_cap) {
+        cudaFree(m->loss_hist);
+        m->loss_hist = nullptr;
+        m->loss_cap = 0;
+        if (cudaMalloc(&m->loss_hist, (size_t)steps * 4) != cudaSuccess)
+            return fail(LPSIM_E_OOM, "device allocation of the loss record failed");
+        m->loss_cap = steps;
+    }
+    uint32_t h = 1;
+    while ((1ull << (2 * h)) < n) h++;
+    const uint32_t nb = (uint32_t)std::min<uint64_t>(m->B, n);
+    cudaStream_t st = m->stream;
+    CU(cudaMemsetAsync(m->t, 0, m->B * 4, st));
+    for (uint32_t s = 0; s < steps; s++) {
+        // the next minibatch of the shuffled passes, gathered on the device
+        gather_batch<<<(nb + 255) / 256, 256, 0, st>>>(m->pool_X, m->pool_t, n, m->nf, h, shuffle_seed,
+                                                       (uint64_t)s * nb, nb, m->Xf, m->t, m->err);
+        pack_inputs<<<dim3(m->B / 32, 2), dim3(32, 8), 0, st>>>(m->Xf, (int)nb, m->nf, m->B, m->X0, m->X0T);
+        m->launches += 2;
+        TRY(forward_batch(m));
+        CU(cudaMemsetAsync(m->loss_acc, 0, 4, st));
+        TRY(backward_batch(m, (int)nb));
+        TRY(adam_step(m, lr));
+        CU(cudaMemcpyAsync(m->loss_hist + s, m->loss_acc, 4, cudaMemcpyDeviceToDevice, st));
+    }
+    CU(cudaGetLastError());
+    if (losses && steps) {
+        CU(cudaMemcpyAsync(losses, m->loss_hist, (size_t)steps * 4, cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+        for (uint32_t s = 0; s < steps; s++) losses[s] /= (float)nb;
+    }
+    CU(cudaStreamSynchronize(st));
+    return mlp_check_err(m);
+}
+
 int lpsim_mlp_train(lpsim_mlp *m, uint64_t n, const float *X, const float *t, uint32_t steps, float lr,
                     uint64_t shuffle_seed, float *losses) {
     if (!m || !X || !t) return fail(LPSIM_E_INVALID_ARG, "NULL argument");
     if (n == 0) return fail(LPSIM_E_INVALID_ARG, "no samples");
-    std::mt19937_64 gen(shuffle_seed);
-    std::vector<uint64_t> idx(n);
-    for (uint64_t i = 0; i < n; i++) idx[i] = i;
-    std::vector<float> bx((size_t)m->B * m->nf), bt(m->B);
-    uint64_t pos = n;
-    for (uint32_t s = 0; s < steps; s++) {
-        // next minibatch of a shuffled pass over the samples
-        const uint64_t nb = std::min<uint64_t>(m->B, n);
-        for (uint64_t j = 0; j < nb; j++) {
-            if (pos >= n) {
-                std::shuffle(idx.begin(), idx.end(), gen);
-                pos = 0;
-            }
-            const uint64_t r = idx[pos++];
-            std::memcpy(&bx[j * m->nf], X + r * m->nf, m->nf * 4);
-            bt[j] = t[r];
-        }
-        CU(cudaStreamSynchronize(m->stream));  // host staging buffers are reused
-        TRY(pack_batch(m, bx.data(), bt.data(), nb));
-        TRY(forward_batch(m));
-        CU(cudaMemsetAsync(m->loss_acc, 0, 4, m->stream));
-        TRY(backward_batch(m, (int)nb));
-        TRY(adam_step(m, lr));
-        if (losses) {
-            float l = 0.0f;
-            CU(cudaMemcpyAsync(&l, m->loss_acc, 4, cudaMemcpyDeviceToHost, m->stream));
-            CU(cudaStreamSynchronize(m->stream));
-            losses[s] = l / (float)nb;
-        }
-    }
-    CU(cudaStreamSynchronize(m->stream));
-    return mlp_check_err(m);
+    TRY(lpsim_mlp_pool_clear(m));
+    TRY(lpsim_mlp_pool_add(m, n, X, t));
+    return lpsim_mlp_train_pool(m, steps, lr, shuffle_seed, losses);
 }
 
 int lpsim_mlp_apply_grads(lpsim_mlp *m, const float *const *grads, float lr) {

@@ -605,7 +605,7 @@ namespace {
 // lane-change seed of each scenario (default: the context's seed).
 int load_demand_impl(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, const uint64_t *route_off,
                      const uint32_t *route_edges, uint32_t *out_vid, const uint32_t *scen, uint32_t n_scen,
-                     const uint64_t *seeds) {
+                     const uint64_t *seeds, const uint8_t *vtype = nullptr) {
     if (!c) return fail(LPSIM_E_INVALID_ARG, "ctx is NULL");
     if (c->loaded) return fail(LPSIM_E_STATE, "demand already loaded");
     // n == 0 is a valid (empty) demand: every step finds nothing to move and
@@ -632,6 +632,12 @@ int load_demand_impl(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, cons
     }
     const uint64_t total = route_off[n];
     if (total >= 0xFFFFFFF0ull) return fail(LPSIM_E_INVALID_ARG, "total route length must stay below 2^32");
+    if (vtype) {
+        const uint32_t nt = (uint32_t)std::max<size_t>(c->types.size(), 1);
+        for (uint64_t j = 0; j < n; j++)
+            if (vtype[j] >= nt)
+                return fail(LPSIM_E_INVALID_ARG, "trip " + std::to_string(j) + ": vehicle type out of range");
+    }
     {
         std::mutex mu;
         uint64_t bad = n;
@@ -686,14 +692,17 @@ int load_demand_impl(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, cons
         }
     }
     // per id (gathers spread over the host's threads): departure step, route
-    // length, first edge; the route offsets are their prefix sum
+    // length, first edge, vehicle type; the route offsets are their prefix sum
     std::vector<uint32_t> first(n);
+    const bool typed = !c->types.empty();
+    std::vector<uint8_t> vt(typed ? n : 0);
     parallel_pieces(n, [&](uint64_t i0, uint64_t i1, uint64_t) {
         for (uint64_t id = i0; id < i1; id++) {
             const uint32_t j = order[id];
             dep[id] = depart_step[j];
             roff[id + 1] = (uint32_t)(route_off[j + 1] - route_off[j]);
             first[id] = route_edges[route_off[j]];
+            if (typed) vt[id] = vtype ? vtype[j] : (uint8_t)0;
             if (out_vid) out_vid[j] = (uint32_t)id;
         }
     });
@@ -788,6 +797,22 @@ int load_demand_impl(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, cons
         TRY(dnew(c, c->w.perm[i], cap));
     }
     if (scen) TRY(upload(c, dhkey, hkey.data(), n * 8));
+    if (typed) {
+        std::vector<TypeRec> tr(kMaxTypes);
+        for (size_t t = 0; t < c->types.size(); t++) {
+            const lpsim_vehicle_type &y = c->types[t];
+            tr[t] = TypeRec{y.a, y.s0, y.T, (float)(2.0 * std::sqrt((double)y.a * (double)y.b)), y.vmax, {0, 0, 0}};
+        }
+        TypeRec *dtr = nullptr;
+        uint8_t *dvt = nullptr;
+        TRY(dnew(c, dtr, kMaxTypes));
+        TRY(dnew(c, dvt, n));
+        TRY(upload(c, dtr, tr.data(), kMaxTypes * sizeof(TypeRec)));
+        TRY(upload(c, dvt, vt.data(), n));
+        d.types = dtr;
+        d.trip_vt = dvt;
+        d.typed = 1;
+    }
     TRY(upload(c, droute, route.data(), route.size() * 4));
     TRY(upload(c, droff, roff.data(), (n + 1) * 4));
     TRY(upload(c, oe, org_edge.data(), norg * 4ull));
@@ -904,6 +929,28 @@ int lpsim_load_demand(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, con
     if (c && c->scen_edge_off.size() > 2)
         return fail(LPSIM_E_STATE, "a batched context takes lpsim_load_demand_batch");
     return load_demand_impl(c, n, depart_step, route_off, route_edges, out_vid, nullptr, 1, nullptr);
+}
+
+int lpsim_set_vehicle_types(lpsim_ctx *c, uint32_t n_types, const lpsim_vehicle_type *types) {
+    if (!c || !types) return fail(LPSIM_E_INVALID_ARG, "NULL argument");
+    if (c->loaded) return fail(LPSIM_E_STATE, "vehicle types are set before the trips are loaded");
+    if (n_types == 0 || n_types > LPSIM_MAX_VEHICLE_TYPES)
+        return fail(LPSIM_E_INVALID_ARG, "n_types must be 1.." + std::to_string(LPSIM_MAX_VEHICLE_TYPES));
+    for (uint32_t t = 0; t < n_types; t++) {
+        const lpsim_vehicle_type &y = types[t];
+        if (!(y.a > 0.0f) || !(y.b > 0.0f) || !(y.s0 >= 0.0f) || !std::isfinite(y.T) || !(y.vmax > 0.0f) ||
+            !(y.vmax <= 254.0f))
+            return fail(LPSIM_E_INVALID_ARG, "vehicle type " + std::to_string(t) + ": parameter out of range");
+    }
+    c->types.assign(types, types + n_types);
+    return LPSIM_OK;
+}
+
+int lpsim_load_demand_typed(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, const uint64_t *route_off,
+                            const uint32_t *route_edges, const uint8_t *vtype, uint32_t *out_vid) {
+    if (c && c->scen_edge_off.size() > 2)
+        return fail(LPSIM_E_STATE, "a batched context takes lpsim_load_demand_batch");
+    return load_demand_impl(c, n, depart_step, route_off, route_edges, out_vid, nullptr, 1, nullptr, vtype);
 }
 
 int lpsim_load_demand_batch(lpsim_ctx *c, uint32_t n_scen, const uint64_t *n_trips, const uint32_t *const *depart_step,

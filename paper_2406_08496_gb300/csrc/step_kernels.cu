@@ -111,14 +111,19 @@ __device__ __forceinline__ uint32_t first_occupied_wide(const uint8_t *row, uint
     return kNone;
 }
 
-__device__ __forceinline__ float idm_speed(const Model &m, float v, float vf, float s, float v0) {
+// car-following parameters of one vehicle (its type's, or the run's)
+struct CarParams {
+    float a, s0, T, two_sqrt_ab, vmax;
+};
+
+__device__ __forceinline__ float idm_speed(const CarParams &y, float dt, float v, float vf, float s, float v0) {
     float dv = v - vf;
-    float z = v * m.T + (v * dv) / m.two_sqrt_ab;
-    float s_star = m.s0 + fmax0(z);
+    float z = v * y.T + (v * dv) / y.two_sqrt_ab;
+    float s_star = y.s0 + fmax0(z);
     float r = v / v0;
     float q = s_star / s;
-    float acc = m.a * ((1.0f - (r * r) * (r * r)) - q * q);
-    return fmax0(v + acc * m.dt);
+    float acc = y.a * ((1.0f - (r * r) * (r * r)) - q * q);
+    return fmax0(v + acc * dt);
 }
 
 // Write a next-map cell.  With the checking flag the cell is read first and
@@ -315,6 +320,7 @@ __device__ __forceinline__ void p1_origin(const Dev &d, const StepView &w, const
         const RouteRec rr = d.rrec[hd.r0];
         const uint32_t nxt = hd.r0 + 1 < hd.r1 ? d.route[hd.r0 + 1] : kNone;
         const uint32_t so = d.slot_off[e0];
+        const uint8_t vt = d.typed ? d.trip_vt[hd.h] : (uint8_t)0;
         const uint32_t l = pick_entry_lane(entry_cells(Mc, er), er.lanes, rr.tl);
         if (l != kNone) {
             atomicMin(&claim[so + l], hd.h);
@@ -336,6 +342,7 @@ __device__ __forceinline__ void p1_origin(const Dev &d, const StepView &w, const
             dr.nsph = (uint16_t)(rr.nphase | (rr.arank << 8));
             dr.lane = (uint8_t)l;
             dr.tlc = rr.tl;
+            dr.vt = vt;
             stage_put(sk.dr, kStageDep, sk.n + 2, d.dep_rec[par], &d.counts[4 + par], dr);
         }
     }
@@ -363,7 +370,6 @@ __device__ __forceinline__ bool p1_slot(const Dev &d, const StepView &w, const P
     const EdgeState es = load_es(d.s.es + s);
     const uint32_t base = es.base;
     const uint32_t len = es.len;
-    const float v0 = es.v0;
     const uint32_t en = es.en;
     const uint32_t G = es.sg;
     const uint32_t ph = es.sph;
@@ -393,12 +399,21 @@ __device__ __forceinline__ bool p1_slot(const Dev &d, const StepView &w, const P
     d.s.pcell[s] = base + c;
     if (sample) atomicAdd(&d.bin_occ[(size_t)(k / m.bin_steps) * d.n_edges + d.route[rpos]], 1u);
 
+    // the vehicle's car-following parameters: its type's (recorded in the
+    // edge-state record), or the run's; its free-flow speed is the lower of
+    // the edge limit and its top speed
+    CarParams y{m.a, m.s0, m.T, m.two_sqrt_ab, 254.0f};
+    if (d.typed) {
+        const TypeRec tr = d.types[es.vt];
+        y = CarParams{tr.a, tr.s0, tr.T, tr.two_sqrt_ab, tr.vmax};
+    }
+    const float v0 = es.v0 < y.vmax ? es.v0 : y.vmax;
     // leader: nearest occupied cell ahead in the own lane of the own edge.
     // Cells beyond both d_front and the farthest reach of this step
     // cannot change the result, so the scan stops there.
     const float d_front = (2.0f * m.dt) * v;
-    const float vmax_step = fmaxf(v0, v + m.a * m.dt);
-    const float reach = fmaxf(d_front, vmax_step * m.dt + m.s0);
+    const float vmax_step = fmaxf(v0, v + y.a * m.dt);
+    const float reach = fmaxf(d_front, vmax_step * m.dt + y.s0);
     const float L = (float)len;
     // in the same round trip as the scan: the next edge's records for a
     // vehicle that may reach the stop line, the lane-change key for one
@@ -443,12 +458,12 @@ __device__ __forceinline__ bool p1_slot(const Dev &d, const StepView &w, const P
 
     float vn;
     if (has_f && ((float)cf - x) <= d_front)
-        vn = idm_speed(m, v, (float)Mc[base + cf], (float)cf - x, v0);
+        vn = idm_speed(y, m.dt, v, (float)Mc[base + cf], (float)cf - x, v0);
     else
         vn = v0;
     float xn = x + vn * m.dt;
     if (has_f) {
-        const float lim = (float)cf - m.s0;
+        const float lim = (float)cf - y.s0;
         if (xn > lim) {
             xn = x > lim ? x : lim;
             vn = 0.0f;
@@ -490,7 +505,7 @@ __device__ __forceinline__ bool p1_slot(const Dev &d, const StepView &w, const P
                 cr.len = (uint16_t)len;
                 cr.nlen = es.nlen;
                 cr.nsph = (uint16_t)(rr.nphase | (rr.arank << 8));
-                cr.lane = (uint8_t)l;
+                cr.lane = (uint8_t)(l | ((uint32_t)es.vt << 2));  // lane 0..3, the type above it
                 cr.tln = rr.tl;
                 stage_put(sk.cr, kStageCross, sk.n, d.cross_list[par], &d.counts[par], cr);
                 cross = true;
@@ -629,10 +644,10 @@ __device__ __forceinline__ void p2_cross(const Dev &d, const StepView &w, const 
         ne.sph = cr.nsph;
         ne.nlen = nn.len;
         ne.nlanes = nn.lanes;
-        ne.pad = 0;
+        ne.vt = (uint8_t)(cr.lane >> 2);
         store_es(d.s.es + s, ne);
         d.s.tent[s] = k + 1;
-        d.s.lane[s] = cr.lane;
+        d.s.lane[s] = (uint8_t)(cr.lane & 3u);
         d.s.tlc[s] = cr.tln;
         d.s.cprev[s] = cr.cslot;
         xw[s] = 0.0f;
@@ -681,7 +696,7 @@ __device__ __forceinline__ void p2_dep(const Dev &d, const StepView &w, const De
     ne.sph = dr.nsph;
     ne.nlen = nn.len;
     ne.nlanes = nn.lanes;
-    ne.pad = 0;
+    ne.vt = dr.vt;
     store_es(d.s.es + s, ne);
     d.s.tent[s] = k + 1;
     d.s.id[s] = dr.h;

@@ -40,9 +40,14 @@ def fmax0(t):
 
 
 class BruteForce:
-    def __init__(self, net: dict, params: dict):
+    def __init__(self, net: dict, params: dict, vehicle_types: list | None = None):
         p = {k: F(v) if isinstance(v, float) else v for k, v in params.items()}
         self.p = p
+        # vehicle types: each its own IDM parameters and top speed; without
+        # them one type with the run parameters and no top speed of its own
+        tys = vehicle_types or [dict(a=p["a"], b=p["b"], s0=p["s0"], T=p["T"], vmax=254.0)]
+        self.types = [dict(a=F(t["a"]), s0=F(t["s0"]), T=F(t["T"]), vmax=F(t["vmax"]),
+                           tsab=F(2.0 * math.sqrt(float(F(t["a"])) * float(F(t["b"]))))) for t in tys]
         self.src = [int(a) for a in net["edge_src"]]
         self.dst = [int(a) for a in net["edge_dst"]]
         self.ncell = [max(1, int(math.ceil(float(F(a))))) for a in net["edge_len"]]
@@ -70,7 +75,7 @@ class BruteForce:
         self.two_sqrt_ab = F(2.0 * math.sqrt(float(p["a"]) * float(p["b"])))
         self.k = 0
 
-    def load(self, depart_step, routes):
+    def load(self, depart_step, routes, vtypes=None):
         n = len(depart_step)
         order = sorted(range(n), key=lambda j: int(depart_step[j]))  # stable
         self.vid = [0] * n
@@ -78,6 +83,7 @@ class BruteForce:
         for i, j in enumerate(order):
             self.vid[j] = i
             self.veh.append(dict(id=i, dep=int(depart_step[j]), route=[int(e) for e in routes[j]],
+                                 ty=self.types[int(vtypes[j]) if vtypes is not None else 0],
                                  status=WAITING, e=None, r=0, lane=0, x=F(0), v=F(0), t_enter=0,
                                  dep_act=0xFFFFFFFF, arr=0xFFFFFFFF))
 
@@ -92,14 +98,14 @@ class BruteForce:
     def tl_for(self, edge, nxt):
         return (self.orank[nxt] * self.lanes[edge]) // self.nout[self.dst[edge]]
 
-    def idm(self, v, vf, s, v0):
+    def idm(self, ty, v, vf, s, v0):
         p = self.p
         dv = F(v - vf)
-        z = F(F(v * p["T"]) + F(F(v * dv) / self.two_sqrt_ab))
-        s_star = F(p["s0"] + fmax0(z))
+        z = F(F(v * ty["T"]) + F(F(v * dv) / ty["tsab"]))
+        s_star = F(ty["s0"] + fmax0(z))
         r = F(v / v0)
         q = F(s_star / s)
-        acc = F(p["a"] * F(F(F(1.0) - F(F(r * r) * F(r * r))) - F(q * q)))
+        acc = F(ty["a"] * F(F(F(1.0) - F(F(r * r) * F(r * r))) - F(q * q)))
         return fmax0(F(v + F(acc * p["dt"])))
 
     def cell(self, w):
@@ -139,14 +145,16 @@ class BruteForce:
             c = self.cell(w)
             ahead = [cc for (ee, ll, cc) in occ if ee == e and ll == ln and cc > c]
             cf = min(ahead) if ahead else None
+            ty = w["ty"]
+            vfree = min(self.v0[e], ty["vmax"])  # the edge limit, or the type's top speed if lower
             dfront = F(F(F(2.0) * p["dt"]) * v)
             if cf is not None and F(F(cf) - x) <= dfront:
-                vn = self.idm(v, F(speed_byte(occ[(e, ln, cf)]["v"])), F(F(cf) - x), self.v0[e])
+                vn = self.idm(ty, v, F(speed_byte(occ[(e, ln, cf)]["v"])), F(F(cf) - x), vfree)
             else:
-                vn = self.v0[e]
+                vn = vfree
             xn = F(x + F(vn * p["dt"]))
             if cf is not None:
-                lim = F(F(cf) - p["s0"])
+                lim = F(F(cf) - ty["s0"])
                 if xn > lim:
                     xn = x if x > lim else lim
                     vn = F(0)

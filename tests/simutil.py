@@ -35,15 +35,17 @@ def assert_outputs_equal(o, g, n_bins: int = 0, where: str = "") -> None:
     assert np.array_equal(o.lane_map(), g.lane_map()), where + " lane maps differ"
 
 
-def lockstep(net: dict, dem: dict, params: dict, steps: int, check_every: int = 1, gpu_params: dict | None = None):
+def lockstep(net: dict, dem: dict, params: dict, steps: int, check_every: int = 1, gpu_params: dict | None = None,
+             vehicle_types: list | None = None):
     """Run oracle and GPU for `steps` steps, comparing state every
-    `check_every` steps and all outputs at the end."""
+    `check_every` steps and all outputs at the end (vehicle_types: the
+    types the demand's "vtype" array names, if any)."""
     from paper_2406_08496_gb300 import Simulation
-    o = O.Oracle(net, params)
+    o = O.Oracle(net, params, vehicle_types=vehicle_types)
     vo = o.load_demand(dem)
     gp = dict(params, **(gpu_params or {}))
     gp["flags"] = gp.get("flags", 0) | 2  # LPSIM_F_CHECK_CELLS: every lane-map write must find an empty cell
-    g = Simulation(net, gp)
+    g = Simulation(net, gp, vehicle_types=vehicle_types)
     vg = g.load_demand(dem)
     assert np.array_equal(vo, vg)
     done = 0

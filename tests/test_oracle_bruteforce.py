@@ -37,13 +37,23 @@ def scenario(seed):
     return net, trips, params
 
 
-def compare(seed, steps=70):
+# vehicle types of the typed scenarios: a car, a truck (slower to start, longer
+# standstill gap, top speed 12 m/s) and a bike (top speed 4.5 m/s)
+TYPES = [dict(a=1.0, b=1.5, s0=2.0, T=1.5, vmax=254.0), dict(a=0.6, b=1.2, s0=4.0, T=2.0, vmax=12.0),
+         dict(a=0.8, b=1.0, s0=1.0, T=1.0, vmax=4.5)]
+
+
+def compare(seed, steps=70, typed=False):
     net, trips, params = scenario(seed)
     dem = make_demand(trips)
-    o = O.Oracle(net, params)
+    types = None
+    if typed:
+        types = TYPES
+        dem["vtype"] = np.random.default_rng(seed + 7).integers(0, len(TYPES), len(trips)).astype(np.uint8)
+    o = O.Oracle(net, params, vehicle_types=types)
     vid = o.load_demand(dem)
-    bf = BruteForce(net, dict(O.DEFAULT_PARAMS, **params))
-    bf.load(dem["depart_step"], routes_of(dem))
+    bf = BruteForce(net, dict(O.DEFAULT_PARAMS, **params), vehicle_types=types)
+    bf.load(dem["depart_step"], routes_of(dem), dem.get("vtype"))
     assert bf.vid == vid.tolist()
     for k in range(steps):
         a = o.state()
@@ -68,6 +78,14 @@ def test_bruteforce_tiny(block):
         changes += c["lane_changes"]
         crossings += c["arrived"]
     assert crossings > 0
+
+
+@pytest.mark.parametrize("block", range(2))
+def test_bruteforce_tiny_vehicle_types(block):
+    """The same family with each vehicle a car, a truck or a bike (Algorithm 1
+    State: vehicle type; multimodal traffic, Sec. 5)."""
+    for seed in range(1000 + block * 40, 1000 + block * 40 + 40):
+        compare(seed, typed=True)
 
 
 def test_bruteforce_exercises_lane_changes_and_conflicts():

@@ -545,3 +545,81 @@ def test_ring_of_one_cell_edges_gridlocks():
         assert np.array_equal(o.lane_map(), m1)
     ls = o.link_stats()
     assert np.array_equal(ls["entries"], np.ones(4, np.uint64)) and not ls["exits"].any()
+
+
+# ----------------------------------------------------------------- vehicle types
+
+TRUCK = dict(a=0.6, b=1.2, s0=4.0, T=2.0, vmax=10.0)  # top speed 10 m/s: 5 m per step, exactly
+CAR = dict(a=1.0, b=1.5, s0=2.0, T=1.5, vmax=254.0)
+
+
+def test_type_top_speed_free_flow_closed_form():
+    """A lone vehicle's free-flow speed is the lower of the edge limit and its
+    type's top speed (Algorithm 1: v <- v_free; vehicle type V): on 14 m/s
+    edges a car covers 7 m per step and a 10 m/s truck 5 m, so they arrive
+    after k_d + 1 + sum ceil(len / 7) and k_d + 1 + sum ceil(len / 5) steps;
+    on a 6 m/s edge both are held to the limit (3 m per step)."""
+    net = make_net(4, [(0, 1, 100.0, 1, 14.0), (1, 2, 37.0, 2, 6.0), (2, 3, 143.0, 1, 14.0)])
+    o = O.Oracle(net, vehicle_types=[CAR, TRUCK])
+    dem = make_demand([(2, [0, 1, 2]), (2, [0, 1, 2])])
+    dem["vtype"] = np.array([0, 1], np.uint8)
+    vid = o.load_demand(dem)
+    o.step(400)
+    tr = o.trips()
+    car, truck = int(vid[0]), int(vid[1])
+    assert tr["depart"][car] == 3  # ids by input order: the car enters first
+    assert tr["arrive"][car] == 3 + math.ceil(100 / 7) + math.ceil(37 / 3) + math.ceil(143 / 7)
+    # the truck enters two steps later (one departure every two steps from one lane)
+    assert tr["depart"][truck] == 5
+    assert tr["arrive"][truck] == 5 + math.ceil(100 / 5) + math.ceil(37 / 3) + math.ceil(143 / 5)
+
+
+def test_type_standstill_gap():
+    """Behind a vehicle stopped at a red stop line, a follower stops at
+    c_f - s0 of its own type: 2 m for a car, 4 m for a truck."""
+    net = make_net(4, [(0, 1, 200.0, 1, 14.0), (1, 2, 50.0, 1, 14.0), (3, 1, 30.0, 1, 14.0)],
+                   green={1: 10_000}, approach_rank=[1, 0, 0])
+    for ty, gap in ((0, 2.0), (1, 4.0)):
+        o = O.Oracle(net, vehicle_types=[CAR, TRUCK])
+        dem = make_demand([(0, [0, 1]), (10, [0, 1])])
+        dem["vtype"] = np.array([0, ty], np.uint8)
+        o.load_demand(dem)
+        o.step(200)
+        st = o.state()
+        assert st["x"][0] == 199.0 and st["x"][1] == 199.0 - gap and st["v"][1] == 0.0
+
+
+BIKE = dict(a=0.8, b=1.0, s0=1.0, T=1.0, vmax=4.5)
+
+
+def test_type_idm_matches_double_closed_form():
+    """A truck departing right behind a car on a long 10 m/s single-lane edge
+    closes in on it: whenever the car is within d_front and the no-crash
+    clamp does not bind, the truck's new speed is the IDM speed of the
+    truck's own parameters (a, b, s0, T; free-flow speed min(edge limit,
+    truck top speed)), within FP32 rounding of Treiber's formula in double
+    precision."""
+    net = make_net(3, [(0, 1, 1500.0, 1, 10.0), (1, 2, 50.0, 1, 10.0)])
+    o = O.Oracle(net, vehicle_types=[CAR, TRUCK, BIKE])
+    dem = make_demand([(0, [0, 1]), (0, [0, 1])])
+    dem["vtype"] = np.array([0, 1], np.uint8)
+    o.load_demand(dem)
+    positive = 0
+    for _ in range(600):
+        st = o.state()
+        o.step(1)
+        nx = o.state()
+        if not (st["status"][0] == 1 and st["status"][1] == 1 and st["edge"][0] == 0 and st["edge"][1] == 0):
+            continue
+        x1, v1 = float(st["x"][1]), float(st["v"][1])
+        cf = int(st["x"][0])
+        s = cf - x1
+        vf = float(min(int(st["v"][0]), 254))  # the leader's speed byte
+        if not (0 < s <= 2 * 0.5 * v1):
+            continue
+        want, _ = idm_double(v1, vf, s, 10.0, TRUCK["a"], TRUCK["b"], TRUCK["s0"], TRUCK["T"], 0.5)
+        if x1 + want * 0.5 > cf - TRUCK["s0"]:
+            continue  # the clamp binds
+        assert abs(float(nx["v"][1]) - want) <= 1e-5 * max(1.0, want), (v1, vf, s, nx["v"][1], want)
+        positive += want > 0
+    assert positive > 0

@@ -68,6 +68,43 @@ def test_tiny_scenarios():
         lockstep(net, make_demand(trips), params, 70, check_every=1)
 
 
+TYPES = [dict(a=1.0, b=1.5, s0=2.0, T=1.5, vmax=254.0), dict(a=0.6, b=1.2, s0=4.0, T=2.0, vmax=12.0),
+         dict(a=0.8, b=1.0, s0=1.0, T=1.0, vmax=4.5)]
+
+
+def _typed(dem, seed, weights=(0.7, 0.2, 0.1)):
+    out = dict(dem)
+    rng = np.random.default_rng(seed)
+    out["vtype"] = rng.choice(len(TYPES), size=len(dem["depart_step"]), p=weights).astype(np.uint8)
+    return out
+
+
+def test_vehicle_types_grid_day(grid_day):
+    """Cars, trucks and bikes (Algorithm 1 State: vehicle type; multimodal
+    traffic, Sec. 5) on the 8x8 grid day, every 10 steps bit for bit."""
+    net, dem = grid_day
+    lockstep(net, _typed(dem, 3), dict(bin_steps=300, n_bins=12), 3600, check_every=10, vehicle_types=TYPES)
+
+
+def test_vehicle_types_small_regional_with_lane_changes():
+    net = W.planar_network(40, 40, seed=21)
+    dem = W.route(net, W.gravity_demand(net, 12000, 22, zones_x=6, zones_y=6, access_per_zone=3,
+                                        beta_m=2500.0, peaks_h=(0.1, 0.25), peak_sigma_h=0.1))
+    o, g = lockstep(net, _typed(dem, 4), dict(bin_steps=450, n_bins=8, seed=99), 3000, check_every=100,
+                    vehicle_types=TYPES)
+    assert o.counters()["lane_changes"] > 100
+
+
+def test_vehicle_types_tiny_scenarios():
+    from test_oracle_bruteforce import TYPES as BF_TYPES
+    from test_oracle_bruteforce import scenario
+    for seed in range(1000, 1060):
+        net, trips, params = scenario(seed)
+        dem = make_demand(trips)
+        dem["vtype"] = np.random.default_rng(seed + 7).integers(0, len(BF_TYPES), len(trips)).astype(np.uint8)
+        lockstep(net, dem, params, 70, check_every=1, vehicle_types=BF_TYPES)
+
+
 def test_edge_cases():
     # one-cell edges, 4 lanes, single-edge routes, far-future departure, a
     # queue of 30 vehicles released at once onto a one-lane edge

@@ -300,3 +300,33 @@ def test_gelu_within_its_error_bound():
     tol_dg = 6e-7 + 2e-7 * np.abs(z64)
     assert np.all(np.abs(g - ref_g) <= tol_g), float(np.max(np.abs(g - ref_g) / tol_g))
     assert np.all(np.abs(dg - ref_dg) <= tol_dg), float(np.max(np.abs(dg - ref_dg) / tol_dg))
+
+
+def test_training_pool_parts_equal_one_upload():
+    """Samples appended to the device pool in parts train exactly like the
+    same samples given at once (same rows in the same order, same shuffled
+    passes for the same seed): parameters equal up to the FP32 noise of the
+    split-K gradient sums; the losses fall."""
+    from paper_2406_08496_gb300 import Surrogate
+    rng = np.random.default_rng(21)
+    X = rng.uniform(-1, 1, (5000, 9)).astype(np.float32)
+    t = (np.sin(2 * X[:, 0]) + X[:, 1] * X[:, 2]).astype(np.float32)
+    p = _params(22)
+    a = Surrogate(batch=1024, seed=0)
+    a.set_params(p)
+    la = a.train(X, t, steps=40, lr=1e-3, seed=5)
+    b = Surrogate(batch=1024, seed=0)
+    b.set_params(p)
+    for part in np.array_split(np.arange(5000), 3):
+        b.pool_add(X[part], t[part])
+    assert b.pool_size() == 5000
+    lb = b.train_pool(40, lr=1e-3, seed=5)
+    assert la[-5:].mean() < 0.5 * la[:5].mean()
+    np.testing.assert_allclose(la, lb, rtol=1e-3, atol=1e-6)
+    pa, pb = a.get_params(), b.get_params()
+    for k in pa:
+        assert np.max(np.abs(pa[k] - pb[k])) <= 1e-4 * (np.max(np.abs(pa[k])) + 1e-3), k
+    b.pool_clear()
+    assert b.pool_size() == 0
+    a.close()
+    b.close()
