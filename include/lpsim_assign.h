@@ -64,9 +64,9 @@ int lpsim_assign_shortest_paths(lpsim_assign *a, const float *tt, uint32_t n_bin
  * labels).  Same candidate routes and t_sp, bit for bit, as the host
  * searches: link times are whole milliseconds, so every arrival is an exact
  * sum, and both keep the earliest arrival with ties to the lower entering
- * edge id.  The graph, trip table and search workspaces (some 24 bytes per
- * node per concurrent tree, at most 16 GiB) stay on the device between calls
- * and are released by lpsim_assign_destroy.  Errors as the host call, plus
+ * edge id.  The graph, trip table and search workspaces (32 bytes per node
+ * per concurrent tree, up to 32 trees per SM within 48 GiB) stay on the
+ * device between calls and are released by lpsim_assign_destroy.  Errors as the host call, plus
  * LPSIM_E_CUDA, LPSIM_E_OOM and LPSIM_E_STATE (another device current). */
 int lpsim_assign_shortest_paths_gpu(lpsim_assign *a, const float *tt, uint32_t n_bins, uint32_t bin_steps,
                                     uint32_t period_steps, float *t_sp);
@@ -105,6 +105,12 @@ int lpsim_assign_get_routes(const lpsim_assign *a, uint64_t *route_off, uint32_t
 /* Inflow per (edge, bin) of the current routes propagated with link times tt
  * (departure at the planned step, each link entered at the running time). */
 int lpsim_assign_load(const lpsim_assign *a, const float *tt, uint32_t n_bins, uint32_t bin_steps, uint32_t *inflow);
+
+/* lpsim_assign_load with the walk on the GPU (one thread per trip, the
+ * routes uploaded for the call): the same counts.  The device state is the
+ * one lpsim_assign_shortest_paths_gpu sets up.  Errors as that call. */
+int lpsim_assign_load_gpu(const lpsim_assign *a, const float *tt, uint32_t n_bins, uint32_t bin_steps,
+                          uint32_t *inflow);
 
 /* Surrogate inputs per (edge, bin), edge-major, LPSIM_SURROGATE_FEATURES
  * floats each, from the inflow counts of the assignment to score, occupancy

@@ -36,6 +36,7 @@ def _lib():
         lib.lpsim_assign_route_length.restype = ctypes.c_uint64
         lib.lpsim_assign_get_routes.argtypes = [P, P, P, ctypes.c_uint64]
         lib.lpsim_assign_load.argtypes = [P, P, ctypes.c_uint32, ctypes.c_uint32, P]
+        lib.lpsim_assign_load_gpu.argtypes = [P, P, ctypes.c_uint32, ctypes.c_uint32, P]
         lib.lpsim_assign_features.argtypes = [P, ctypes.c_uint32, P, P, P, P, P, ctypes.c_uint32]
         lib.lpsim_assign_link_times.argtypes = [P, ctypes.c_uint32, P, P, P, P]
         lib.lpsim_assign_times_from_ratio.argtypes = [P, ctypes.c_uint32, P, P]
@@ -121,6 +122,13 @@ class Assignment:
         tt = np.ascontiguousarray(tt, dtype=np.float32)
         inflow = np.empty(tt.shape, np.uint32)
         _check(self.lib, self.lib.lpsim_assign_load(self.h, _p(tt), tt.shape[1], bin_steps, _p(inflow)))
+        return inflow
+
+    def load_gpu(self, tt: np.ndarray, bin_steps: int) -> np.ndarray:
+        """The same inflow counts, the routes walked on the GPU."""
+        tt = np.ascontiguousarray(tt, dtype=np.float32)
+        inflow = np.empty(tt.shape, np.uint32)
+        _check(self.lib, self.lib.lpsim_assign_load_gpu(self.h, _p(tt), tt.shape[1], bin_steps, _p(inflow)))
         return inflow
 
     def features(self, inflow: np.ndarray, occ: np.ndarray, prev_log_ratio: np.ndarray,
@@ -242,7 +250,7 @@ def msa(net: dict, dem: dict, mode: str = "plain", iterations: int = 10, fractio
                 break
             rec["rerouted"] = move(it)
         else:
-            inflow = A.load(tt_last, bin_steps)
+            inflow = A.load_gpu(tt_last, bin_steps) if paths == "gpu" else A.load(tt_last, bin_steps)
             X = A.features(inflow, occ_last, lr_last, in_last)
             y = mlp.forward(X)
             tt_pred = A.times_from_ratio(y, n_bins)

@@ -11,7 +11,8 @@
 //
 // Here every tree is searched by one warp, thousands of warps at a time (a
 // tree's frontier is a wave of a few hundred nodes; many trees in flight
-// hide the memory latency each relaxation pays):
+// hide the memory latency each relaxation pays: on the 2.82M-trip day, 16
+// trees per SM took 2.7 s per pass, 32 took 1.85 s, 64 took 1.78 s):
 //   * label-correcting search in rounds over time buckets (near-far): the
 //     near set's nodes relax their out-edges with the arrival function of
 //     the bin holding their arrival time (FIFO by construction, see TD); a
@@ -63,9 +64,15 @@ int fail(int code, const std::string &m) { return lpsim_fail(code, m); }
 
 constexpr uint64_t kUnreached = ~0ull;
 constexpr uint32_t kNoEdge = 0xFFFFFFFFu;
+#ifndef LPSIM_ASSIGN_WARPS_PER_SM
+#define LPSIM_ASSIGN_WARPS_PER_SM 32
+#endif
+#ifndef LPSIM_ASSIGN_WORKSPACE_GIB
+#define LPSIM_ASSIGN_WORKSPACE_GIB 48
+#endif
 constexpr int kWarpsPerBlock = 4;
-constexpr int kBlocksPerSm = 4;                      // 16 warps (trees) per SM
-constexpr uint64_t kWorkspaceBudget = 16ull << 30;   // bytes of per-warp workspaces at most
+constexpr int kBlocksPerSm = LPSIM_ASSIGN_WARPS_PER_SM / kWarpsPerBlock;   // trees searched at once per SM / 4
+constexpr uint64_t kWorkspaceBudget = (uint64_t)LPSIM_ASSIGN_WORKSPACE_GIB << 30;  // per-warp workspaces at most
 #ifndef LPSIM_ASSIGN_DELTA_MS
 #define LPSIM_ASSIGN_DELTA_MS 60000
 #endif
@@ -323,6 +330,25 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) td_trees(TreeArgs A) {
     if (lane == 0) A.stamp[gw] = stamp;
 }
 
+// Inflow per (edge, bin) of the routes: each trip walks its route from its
+// planned departure with the arrival rule of the table, counting one entry
+// in the bin of every link entry time (the host's lpsim_assign_load, on the
+// device: integer counts, so the order of the atomics does not matter).
+__global__ void load_routes(const unsigned long long *roff, const uint32_t *redge, const uint32_t *dep_ms,
+                            uint64_t n, const uint2 *cms, uint32_t n_edges, uint32_t n_bins, uint32_t bin_ms,
+                            uint32_t *inflow) {
+    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < n; j += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t t = dep_ms[j];
+        const unsigned long long q1 = roff[j + 1];
+        for (unsigned long long q = roff[j]; q < q1; q++) {
+            const uint32_t e = redge[q];
+            const uint64_t b = t / bin_ms;
+            if (b < n_bins) atomicAdd(&inflow[(size_t)e * n_bins + b], 1u);
+            t = arrive(cms[(size_t)(b < n_bins ? b : n_bins - 1) * n_edges + e], t);
+        }
+    }
+}
+
 }  // namespace
 
 // Device copy of the graph, the trip table and the search workspaces.
@@ -336,6 +362,12 @@ struct AssignGpu {
     uint32_t period_steps = 0;  // grouping held in A.groups / A.order
     std::vector<uint64_t> order, gstart;
     unsigned long long cap = 0;
+    // routes and inflow of lpsim_assign_load_gpu
+    unsigned long long *roff = nullptr;
+    uint32_t *redge = nullptr;
+    uint64_t redge_cap = 0;
+    uint32_t *inflow = nullptr;
+    size_t inflow_cells = 0;
 
     void *alloc(size_t bytes) {
         void *p = nullptr;
@@ -472,19 +504,12 @@ int gpu_groups(lpsim_assign *a, uint32_t period_steps) {
 
 }  // namespace
 
-extern "C" int lpsim_assign_shortest_paths_gpu(lpsim_assign *a, const float *tt, uint32_t n_bins, uint32_t bin_steps,
-                                               uint32_t period_steps, float *t_sp) {
-    if (!a || !tt || n_bins == 0 || bin_steps == 0 || period_steps == 0)
-        return fail(LPSIM_E_INVALID_ARG, "bad argument");
-    if (a->n == 0) return LPSIM_OK;
-    if (!a->gpu) TRY(gpu_setup(a));
+namespace {
+
+// the link-time table of tt in whole milliseconds (the host searches' table) on the device
+int gpu_table(lpsim_assign *a, const float *tt, uint32_t n_bins, uint32_t bin_steps) {
     AssignGpu *g = a->gpu;
-    int dev = -1;
-    CU(cudaGetDevice(&dev));
-    if (dev != g->device) return fail(LPSIM_E_STATE, "the device current at the first GPU search must be current");
-    TRY(gpu_groups(a, period_steps));
     TreeArgs &A = g->A;
-    // link times in whole milliseconds, bin-major (the host searches' table)
     const TD td(a, tt, n_bins, bin_steps);
     if (td.bin_ms > 0xFFFFFFFFull) return fail(LPSIM_E_INVALID_ARG, "bin longer than the 32-bit millisecond range");
     static_assert(sizeof(LinkTime) == sizeof(uint2), "link-time record");
@@ -500,6 +525,75 @@ extern "C" int lpsim_assign_shortest_paths_gpu(lpsim_assign *a, const float *tt,
                        cudaMemcpyHostToDevice, g->stream));
     A.n_bins = n_bins;
     A.bin_ms = (uint32_t)td.bin_ms;
+    // the host table goes away with td: let the copy finish first
+    CU(cudaStreamSynchronize(g->stream));
+    return LPSIM_OK;
+}
+
+}  // namespace
+
+extern "C" int lpsim_assign_load_gpu(const lpsim_assign *ac, const float *tt, uint32_t n_bins, uint32_t bin_steps,
+                                     uint32_t *inflow) {
+    lpsim_assign *a = const_cast<lpsim_assign *>(ac);
+    if (!a || !tt || !inflow || n_bins == 0 || bin_steps == 0) return fail(LPSIM_E_INVALID_ARG, "bad argument");
+    if (!a->gpu) TRY(gpu_setup(a));
+    AssignGpu *g = a->gpu;
+    int dev = -1;
+    CU(cudaGetDevice(&dev));
+    if (dev != g->device) return fail(LPSIM_E_STATE, "the device current at the first GPU call must be current");
+    TRY(gpu_table(a, tt, n_bins, bin_steps));
+    // the current routes, flattened (offsets on the host's threads)
+    std::vector<unsigned long long> off(a->n + 1);
+    off[0] = 0;
+    for (uint64_t j = 0; j < a->n; j++) off[j + 1] = off[j] + a->route[j].size();
+    const uint64_t total = off[a->n];
+    std::vector<uint32_t> edges(std::max<uint64_t>(total, 1));
+    lpsim::parallel_pieces(a->n, [&](uint64_t j0, uint64_t j1, uint64_t) {
+        for (uint64_t j = j0; j < j1; j++)
+            std::memcpy(edges.data() + off[j], a->route[j].data(), a->route[j].size() * 4);
+    });
+    if (!g->roff) {
+        g->roff = static_cast<unsigned long long *>(g->alloc((a->n + 1) * 8));
+        if (!g->roff) return fail(LPSIM_E_OOM, "device allocation of the route offsets failed");
+    }
+    if (total > g->redge_cap) {
+        if (g->redge) g->release(g->redge);
+        g->redge_cap = total + total / 4;
+        g->redge = static_cast<uint32_t *>(g->alloc(g->redge_cap * 4));
+        if (!g->redge) return fail(LPSIM_E_OOM, "device allocation of the routes failed");
+    }
+    const size_t cells = (size_t)a->n_edges * n_bins;
+    if (cells > g->inflow_cells) {
+        if (g->inflow) g->release(g->inflow);
+        g->inflow = static_cast<uint32_t *>(g->alloc(cells * 4));
+        if (!g->inflow) return fail(LPSIM_E_OOM, "device allocation of the inflow table failed");
+        g->inflow_cells = cells;
+    }
+    CU(cudaMemcpyAsync(g->roff, off.data(), (a->n + 1) * 8, cudaMemcpyHostToDevice, g->stream));
+    if (total) CU(cudaMemcpyAsync(g->redge, edges.data(), total * 4, cudaMemcpyHostToDevice, g->stream));
+    CU(cudaMemsetAsync(g->inflow, 0, cells * 4, g->stream));
+    load_routes<<<(unsigned)std::min<uint64_t>((a->n + 255) / 256, 65535), 256, 0, g->stream>>>(
+        g->roff, g->redge, g->A.dep_ms, a->n, g->A.cms, a->n_edges, n_bins, g->A.bin_ms, g->inflow);
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(inflow, g->inflow, cells * 4, cudaMemcpyDeviceToHost, g->stream));
+    CU(cudaStreamSynchronize(g->stream));
+    return LPSIM_OK;
+}
+
+extern "C" int lpsim_assign_shortest_paths_gpu(lpsim_assign *a, const float *tt, uint32_t n_bins, uint32_t bin_steps,
+                                               uint32_t period_steps, float *t_sp) {
+    if (!a || !tt || n_bins == 0 || bin_steps == 0 || period_steps == 0)
+        return fail(LPSIM_E_INVALID_ARG, "bad argument");
+    if (a->n == 0) return LPSIM_OK;
+    if (!a->gpu) TRY(gpu_setup(a));
+    AssignGpu *g = a->gpu;
+    int dev = -1;
+    CU(cudaGetDevice(&dev));
+    if (dev != g->device) return fail(LPSIM_E_STATE, "the device current at the first GPU search must be current");
+    TRY(gpu_groups(a, period_steps));
+    TreeArgs &A = g->A;
+    // link times in whole milliseconds, bin-major (the host searches' table)
+    TRY(gpu_table(a, tt, n_bins, bin_steps));
     // path buffer: room for the current routes' length and half as much again
     if (!g->cap) {
         uint64_t total = 0;

@@ -64,6 +64,24 @@ def test_gpu_paths_equal_host_paths(scale, period_steps, seed):
     gpu.close()
 
 
+@pytest.mark.parametrize("scale", ["tiny", "small"])
+def test_gpu_load_equals_host_load(scale):
+    """Inflow per (edge, bin) of the current routes walked on the GPU equals
+    the host walk, count for count, before and after a re-routing."""
+    from paper_2406_08496_gb300.assignment import Assignment
+    net, dem = W.assignment_case(scale=scale)
+    tt = _tables(net, 96, 7)
+    A = Assignment(net, dem, seed=2)
+    assert np.array_equal(A.load(tt, 1800), A.load_gpu(tt, 1800))
+    A.shortest_paths_gpu(tt, 1800, 3600)
+    A.reroute(0.3, 1)
+    tt2 = _tables(net, 96, 8)
+    ref = A.load(tt2, 1800)
+    assert ref.sum() > 0
+    assert np.array_equal(ref, A.load_gpu(tt2, 1800))
+    A.close()
+
+
 def test_gpu_paths_match_brute_force():
     """On a five-edge diamond, every trip's GPU route is an earliest-arrival
     path among all simple paths, from the middle of its period, and its time
