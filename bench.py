@@ -39,7 +39,20 @@ sys.path.insert(0, ROOT)
 
 BYTES_PER_VEH_STEP_P1 = 64  # 24 state read + 8 state write + 16 edge record + 16 lane-map window
 DAY_STEPS = 172_800
-SAMPLE_WINDOW = (7 * 7200 + 3600, 7 * 7200 + 3600 + 600)  # trips departing 07:30-07:35
+# bounded CPU sample: the trips departing in a few minutes from 07:30 (five
+# for the regional day, two for the 9.01M-trip day, about 10-30 s of oracle work)
+SAMPLE_START = 7 * 7200 + 3600
+SAMPLE_STEPS_BY_WORKLOAD = {"large": 240}
+
+
+def sample_window(workload: str) -> tuple[int, int]:
+    return SAMPLE_START, SAMPLE_START + SAMPLE_STEPS_BY_WORKLOAD.get(workload, 600)
+
+
+def sample_label(workload: str) -> str:
+    k0, k1 = sample_window(workload)
+    clock = lambda k: f"{int(k * 0.5) // 3600:02d}:{int(k * 0.5) // 60 % 60:02d}"
+    return f"{clock(k0)}-{clock(k1)}"
 SAMPLE_STEPS = 1200
 
 
@@ -50,7 +63,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="regional",
-                    choices=["regional", "grid", "large", "batch64", "assignment", "surrogate"])
+                    choices=["regional", "grid", "large", "batch64", "assignment", "paths", "surrogate"])
+    ap.add_argument("--repeats", type=int, default=1,
+                    help="assignment workload: alternate the two arms this many times and report the spread")
     ap.add_argument("--iterations", type=int, default=40,
                     help="assignment workload: MSA iterations at most per arm (each stops at the 1%% gap)")
     ap.add_argument("--assignment-scale", default="paper", choices=["paper", "small", "tiny"],
@@ -83,11 +98,11 @@ def load_workload(name: str):
     return net, dem, label
 
 
-def sample_workload(net, dem):
+def sample_workload(net, dem, workload: str = "regional"):
     """Bounded CPU sample of the same workload: the trips departing in a
-    five-minute window of the morning peak, simulated for 10 minutes."""
+    few-minute window of the morning peak, simulated for 10 minutes."""
     import workloads as W
-    k0, k1 = SAMPLE_WINDOW
+    k0, k1 = sample_window(workload)
     keep = (dem["depart_step"] >= k0) & (dem["depart_step"] < k1)
     sub = W.subset_trips(dem, keep)
     sub["depart_step"] = (sub["depart_step"] - k0).astype(np.uint32)
@@ -214,7 +229,7 @@ def reference_arm(args, rank, world):
     if rank != 0:
         return
     net, dem, label = load_workload(args.workload)
-    sub = sample_workload(net, dem)
+    sub = sample_workload(net, dem, args.workload)
     params = dict(bin_steps=1800, n_bins=0)
     for _ in range(args.warmup):
         run_oracle_sample(net, sub, params)
@@ -224,7 +239,7 @@ def reference_arm(args, rank, world):
         vs_tot += vs
         t_tot += dt
     value = vs_tot / t_tot
-    sample = (f"{len(sub['depart_step'])} trips departing 07:30-07:35 of the {label} workload, "
+    sample = (f"{len(sub['depart_step'])} trips departing {sample_label(args.workload)} of the {label} workload, "
               f"{SAMPLE_STEPS} steps from 07:30, full network")
     line = {"impl": "reference", "metric": "veh-steps/s", "value": value, "unit": "veh-steps/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_tot / args.steps * 1e3,
@@ -298,9 +313,14 @@ def assignment_arm(args, L, torch):
     net, dem = W.assignment_case(scale=args.assignment_scale)
     iters = args.iterations
     res = {}
+    runs = {"plain": [], "surrogate": []}
+    for rep in range(max(1, args.repeats)):
+        for mode in ("plain", "surrogate"):
+            r = msa(net, dem, mode, iterations=iters, target_gap=0.01, paths=args.paths,
+                    surrogate_batch=131072 if args.assignment_scale == "paper" else 8192)
+            runs[mode].append(r)
     for mode in ("plain", "surrogate"):
-        r = msa(net, dem, mode, iterations=iters, target_gap=0.01, paths=args.paths,
-                surrogate_batch=131072 if args.assignment_scale == "paper" else 8192)
+        r = runs[mode][-1]
         hist = [(h["wall_s"], h["gap"]) for h in r["history"] if h["gap"] is not None]
 
         def hit(th):
@@ -316,17 +336,54 @@ def assignment_arm(args, L, torch):
                                       if any("train_s" in h for h in sims) else None),
                      "surrogate_iter_s_mean": (float(np.mean([h["iter_s"] for h in r["history"]
                                                               if h["kind"] == "surrogate"]))
-                                               if any(h["kind"] == "surrogate" for h in r["history"]) else None)}
+                                               if any(h["kind"] == "surrogate" for h in r["history"]) else None),
+                     "time_to_1pct_gap_s_runs": [x["time_to_target_s"] for x in runs[mode]]}
     trips = int(len(dem["depart_step"]))
     label = {"paper": "assignment-224k-nodes-2.82M-trips", "small": "assignment-27k-nodes-340k-trips",
              "tiny": "assignment-3k-nodes-30k-trips"}[args.assignment_scale]
-    out = {"metric": "time-to-1%-gap", "value": res["surrogate"]["time_to_1pct_gap_s"], "unit": "s",
+    def median(v):
+        v = [x for x in v if x is not None]
+        return float(np.median(v)) if v else None
+    out = {"metric": "time-to-1%-gap", "value": median(res["surrogate"]["time_to_1pct_gap_s_runs"]), "unit": "s",
            "higher_is_better": False, "n_gpus": 1, "steps": iters, "warmup": 0, "dtype": "f32+bf16",
            "data": "synthetic", "vs_baseline": None,
            "config": {"workload": label, "nodes": net["n_nodes"], "edges": net["n_edges"], "trips": trips,
                       "reroute_fraction": 0.1, "selection": "random", "paths": args.paths,
                       "full_simulation": "every iteration (plain), every 2nd (surrogate)"},
-           "plain_time_to_1pct_gap_s": res["plain"]["time_to_1pct_gap_s"], "arms": res}
+           "plain_time_to_1pct_gap_s": median(res["plain"]["time_to_1pct_gap_s_runs"]),
+           "repeats": max(1, args.repeats), "arms": res}
+    print(json.dumps(out), flush=True)
+
+
+def paths_arm(args):
+    """Time-dependent shortest paths of every trip of the assignment case
+    (one tree per origin and 30-minute departure period) under the link
+    times of one simulation of its free-flow routes, per pass: the GPU
+    search (one warp per tree) or the host search (--paths host)."""
+    import workloads as W
+    import paper_2406_08496_gb300 as L
+    from paper_2406_08496_gb300.assignment import Assignment
+    net, dem = W.assignment_case(scale=args.assignment_scale)
+    A = Assignment(net, dem, seed=0)
+    sim = L.Simulation(net, dict(bin_steps=1800, n_bins=96))
+    sim.load_demand(A.routes())
+    sim.run(300_000)
+    ls = sim.link_stats()
+    sim.close()
+    tt, _ = A.link_times(ls["tt_sum"], ls["tt_cnt"])
+    search = A.shortest_paths_gpu if args.paths == "gpu" else A.shortest_paths
+    for _ in range(args.warmup):
+        search(tt, 1800, 3600)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        search(tt, 1800, 3600)
+    dt = (time.perf_counter() - t0) / args.steps
+    groups = len(np.unique(dem["orig"].astype(np.uint64) * 1000 + dem["depart_step"] // 3600))
+    out = {"metric": "shortest-path pass", "value": dt, "unit": "s", "higher_is_better": False, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "dtype": "u32 ms", "data": "synthetic", "vs_baseline": None,
+           "config": {"workload": f"assignment-paths-{args.assignment_scale}", "nodes": net["n_nodes"],
+                      "edges": net["n_edges"], "trips": int(len(dem["depart_step"])), "trees": int(groups),
+                      "paths": args.paths, "period_steps": 3600}}
     print(json.dumps(out), flush=True)
 
 
@@ -392,6 +449,9 @@ def main():
         return
     if args.workload == "assignment":
         assignment_arm(args, L, torch)
+        return
+    if args.workload == "paths":
+        paths_arm(args)
         return
     if args.workload == "surrogate":
         surrogate_arm(args)
@@ -546,10 +606,10 @@ def main():
             roofline["peak_window"] = peak_window
         cpu = None
         if not args.no_cpu_baseline and world == 1:
-            sub = sample_workload(net, dem)
+            sub = sample_workload(net, dem, args.workload)
             vs, dt = run_oracle_sample(net, sub, dict(bin_steps=1800, n_bins=0))
             cpu = {"value": vs / dt, "unit": "veh-steps/s", "cores": 1, "kind": "oracle",
-                   "sample": f"{len(sub['depart_step'])} trips departing 07:30-07:35 of the same day, "
+                   "sample": f"{len(sub['depart_step'])} trips departing {sample_label(args.workload)} of the same day, "
                              f"{SAMPLE_STEPS} steps from 07:30 on the full network ({vs} veh-steps, {dt:.1f} s)",
                    "host_cpus": os.cpu_count()}
         e2e = None
