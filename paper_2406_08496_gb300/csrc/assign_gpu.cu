@@ -12,7 +12,8 @@
 // Here every tree is searched by one warp, thousands of warps at a time (a
 // tree's frontier is a wave of a few hundred nodes; many trees in flight
 // hide the memory latency each relaxation pays: on the 2.82M-trip day, 16
-// trees per SM took 2.7 s per pass, 32 took 1.85 s, 64 took 1.78 s):
+// trees per SM took 2.7 s per pass, 32 took 1.85 s, 64 took 1.78 s; the
+// out-edges of a round's near nodes spread over the lanes took 32 to 1.7 s):
 //   * label-correcting search in rounds over time buckets (near-far): the
 //     near set's nodes relax their out-edges with the arrival function of
 //     the bin holding their arrival time (FIFO by construction, see TD); a
@@ -150,7 +151,7 @@ __device__ __forceinline__ uint64_t dest_bound(const TreeArgs &A, const GroupRec
     return m;
 }
 
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) td_trees(TreeArgs A) {
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, kBlocksPerSm) td_trees(TreeArgs A) {
     const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
     const size_t gw = (size_t)blockIdx.x * kWarpsPerBlock + wib;
     uint64_t *lab = A.lab + gw * A.n_nodes;
@@ -196,15 +197,44 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) td_trees(TreeArgs A) {
                     s_far[wib] = nfar;
                 }
                 __syncwarp();
-                for (uint32_t i = lane; i < nn; i += 32) {
-                    const uint32_t u = __ldcg(fa + i);
-                    const uint64_t tu = __ldcg(reinterpret_cast<const unsigned long long *>(lab + u)) >> 32;
-                    if (tu >= ub) continue;
-                    const uint2 *crow = A.cms + (size_t)bin_of(A, tu) * A.n_edges;
-                    const uint32_t j1 = A.out_off[u + 1];
-                    for (uint32_t j = A.out_off[u]; j < j1; j++) {
+                // 32 near nodes at a time, their out-edges spread over the
+                // lanes (a warp scan of the degrees; each lane finds the node
+                // of its edge by a binary search over the scan), so a round
+                // with a few nodes of a few edges each keeps most lanes busy
+                for (uint32_t c0 = 0; c0 < nn; c0 += 32) {
+                    const uint32_t i = c0 + lane;
+                    uint32_t u = 0, j0 = 0, deg = 0;
+                    uint64_t tu = kUnreached;
+                    if (i < nn) {
+                        u = __ldcg(fa + i);
+                        tu = __ldcg(reinterpret_cast<const unsigned long long *>(lab + u)) >> 32;
+                        j0 = A.out_off[u];
+                        deg = tu < ub ? A.out_off[u + 1] - j0 : 0u;
+                    }
+                    uint32_t incl = deg;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                        if (lane >= (uint32_t)o) incl += y;
+                    }
+                    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+                    for (uint32_t b0 = 0; b0 < total; b0 += 32) {
+                        const uint32_t t = b0 + lane;
+                        // the lane whose node owns edge t: the first with incl > t
+                        uint32_t owner = 0;
+#pragma unroll
+                        for (uint32_t step = 16; step > 0; step >>= 1) {
+                            const uint32_t y = __shfl_sync(0xFFFFFFFFu, incl, (int)(owner + step - 1));
+                            if (y <= t) owner += step;
+                        }
+                        const uint32_t o_incl = __shfl_sync(0xFFFFFFFFu, incl, (int)owner);
+                        const uint32_t o_deg = __shfl_sync(0xFFFFFFFFu, deg, (int)owner);
+                        const uint32_t o_j0 = __shfl_sync(0xFFFFFFFFu, j0, (int)owner);
+                        const uint64_t o_tu = __shfl_sync(0xFFFFFFFFu, tu, (int)owner);
+                        if (t >= total) continue;
+                        const uint32_t j = o_j0 + (t - (o_incl - o_deg));
                         const uint2 ev = A.adj[j];
-                        const uint64_t at = arrive(crow[ev.x], tu);
+                        const uint64_t at = arrive(A.cms[(size_t)bin_of(A, o_tu) * A.n_edges + ev.x], o_tu);
                         if (at > 0xFFFFFFFFull || at > ub) continue;
                         const unsigned long long cand = (at << 32) | ev.x;
                         const unsigned long long old =
@@ -536,6 +566,10 @@ extern "C" int lpsim_assign_load_gpu(const lpsim_assign *ac, const float *tt, ui
                                      uint32_t *inflow) {
     lpsim_assign *a = const_cast<lpsim_assign *>(ac);
     if (!a || !tt || !inflow || n_bins == 0 || bin_steps == 0) return fail(LPSIM_E_INVALID_ARG, "bad argument");
+    if (a->n == 0) {
+        std::memset(inflow, 0, (size_t)a->n_edges * n_bins * 4);
+        return LPSIM_OK;
+    }
     if (!a->gpu) TRY(gpu_setup(a));
     AssignGpu *g = a->gpu;
     int dev = -1;
