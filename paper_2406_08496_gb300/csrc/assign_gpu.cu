@@ -13,7 +13,9 @@
 // tree's frontier is a wave of a few hundred nodes; many trees in flight
 // hide the memory latency each relaxation pays: on the 2.82M-trip day, 16
 // trees per SM took 2.7 s per pass, 32 took 1.85 s, 64 took 1.78 s; the
-// out-edges of a round's near nodes spread over the lanes took 32 to 1.7 s):
+// out-edges of a round's near nodes spread over the lanes took 32 to 1.7 s,
+// and a node's label, round stamp and far mark in one 16-byte record to
+// 1.33 s):
 //   * label-correcting search in rounds over time buckets (near-far): the
 //     near set's nodes relax their out-edges with the arrival function of
 //     the bin holding their arrival time (FIFO by construction, see TD); a
@@ -91,6 +93,15 @@ struct GroupRec {
     uint32_t count;  // trips
 };
 
+// a node's search state in one 16-byte record, so the atomics of one
+// relaxation (the label's minimum, then the round stamp or the far mark)
+// touch one 32-byte sector
+struct __align__(16) NodeRec {
+    unsigned long long lab;  // (arrival ms << 32) | entering edge, or all ones while unreached
+    uint32_t inq;            // round stamp of the last push onto a near set
+    uint32_t fmark;          // tree mark while the node is in the far pile
+};
+
 struct TreeArgs {
     uint32_t n_nodes, n_edges, n_bins, bin_ms;
     const uint32_t *out_off;  // n_nodes + 1
@@ -110,12 +121,10 @@ struct TreeArgs {
     unsigned long long cap;   // entries of edges
     unsigned long long *cursor;
     // per-warp workspaces
-    uint64_t *lab;            // n_warps x n_nodes
-    uint32_t *inq;            // n_warps x n_nodes: round stamp of the last push
+    NodeRec *node;            // n_warps x n_nodes: label, round stamp of the last push, far-pile mark
     uint32_t *touched;        // n_warps x n_nodes
     uint32_t *fa, *fb;        // n_warps x n_nodes: near sets (this round, next round)
     uint32_t *far;            // n_warps x n_nodes: far pile (labels at or above the threshold)
-    uint32_t *fmark;          // n_warps x n_nodes: tree mark of the nodes in the far pile
     uint32_t *stamp;          // per warp: last round stamp used
     uint64_t delta_ms;        // bucket width of the thresholds
     uint32_t *next_group;
@@ -135,11 +144,11 @@ __device__ __forceinline__ uint64_t arrive(const uint2 lt, uint64_t t) {
 
 // Latest current arrival over the group's destinations (its trips'), or
 // kUnreached while any is unreached; every lane gets the result.
-__device__ __forceinline__ uint64_t dest_bound(const TreeArgs &A, const GroupRec &G, const uint64_t *lab,
+__device__ __forceinline__ uint64_t dest_bound(const TreeArgs &A, const GroupRec &G, const NodeRec *nd,
                                                uint32_t lane) {
     uint64_t m = 0;
     for (uint32_t q = lane; q < G.count; q += 32) {
-        const uint64_t l = __ldcg(reinterpret_cast<const unsigned long long *>(lab + A.dest[A.order[G.first + q]]));
+        const uint64_t l = __ldcg(&nd[A.dest[A.order[G.first + q]]].lab);
         const uint64_t t = l == kUnreached ? kUnreached : (l >> 32);
         m = t > m ? t : m;
     }
@@ -154,9 +163,7 @@ __device__ __forceinline__ uint64_t dest_bound(const TreeArgs &A, const GroupRec
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBlocksPerSm) td_trees(TreeArgs A) {
     const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
     const size_t gw = (size_t)blockIdx.x * kWarpsPerBlock + wib;
-    uint64_t *lab = A.lab + gw * A.n_nodes;
-    uint32_t *inq = A.inq + gw * A.n_nodes;
-    uint32_t *fmark = A.fmark + gw * A.n_nodes;
+    NodeRec *nd = A.node + gw * A.n_nodes;
     uint32_t *touched = A.touched + gw * A.n_nodes;
     uint32_t *fa = A.fa + gw * A.n_nodes, *fb = A.fb + gw * A.n_nodes;
     uint32_t *far = A.far + gw * A.n_nodes;
@@ -173,7 +180,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBlocksPerSm) td_trees(Tr
         const GroupRec G = A.groups[g];
         const uint32_t tmark = ++stamp;  // this tree's mark of the nodes in its far pile
         if (lane == 0) {
-            __stcg(reinterpret_cast<unsigned long long *>(lab + G.src), ((uint64_t)G.t0 << 32) | kNoEdge);
+            __stcg(&nd[G.src].lab, (unsigned long long)(((uint64_t)G.t0 << 32) | kNoEdge));
             __stcg(touched, G.src);
             __stcg(fa, G.src);
         }
@@ -207,7 +214,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBlocksPerSm) td_trees(Tr
                     uint64_t tu = kUnreached;
                     if (i < nn) {
                         u = __ldcg(fa + i);
-                        tu = __ldcg(reinterpret_cast<const unsigned long long *>(lab + u)) >> 32;
+                        tu = __ldcg(&nd[u].lab) >> 32;
                         j0 = A.out_off[u];
                         deg = tu < ub ? A.out_off[u + 1] - j0 : 0u;
                     }
@@ -237,14 +244,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBlocksPerSm) td_trees(Tr
                         const uint64_t at = arrive(A.cms[(size_t)bin_of(A, o_tu) * A.n_edges + ev.x], o_tu);
                         if (at > 0xFFFFFFFFull || at > ub) continue;
                         const unsigned long long cand = (at << 32) | ev.x;
-                        const unsigned long long old =
-                            atomicMin(reinterpret_cast<unsigned long long *>(lab + ev.y), cand);
+                        const unsigned long long old = atomicMin(&nd[ev.y].lab, cand);
                         if (cand < old) {
                             if (old == kUnreached) __stcg(touched + atomicAdd(&s_touched[wib], 1u), ev.y);
                             if (at < theta) {
-                                if (atomicExch(inq + ev.y, stamp) != stamp)
+                                if (atomicExch(&nd[ev.y].inq, stamp) != stamp)
                                     __stcg(fb + atomicAdd(&s_next[wib], 1u), ev.y);
-                            } else if (atomicExch(fmark + ev.y, tmark) != tmark) {
+                            } else if (atomicExch(&nd[ev.y].fmark, tmark) != tmark) {
                                 __stcg(far + atomicAdd(&s_far[wib], 1u), ev.y);
                             }
                         }
@@ -262,7 +268,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBlocksPerSm) td_trees(Tr
                 continue;
             }
             // the near set is empty: every label below theta is final
-            ub = dest_bound(A, G, lab, lane);
+            ub = dest_bound(A, G, nd, lane);
             if (ub < theta || nfar == 0) break;  // every destination settled (or nothing left)
             // next threshold: move the far nodes below it to the near set, keep
             // the rest (the far list holds each node once: its mark)
@@ -276,7 +282,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBlocksPerSm) td_trees(Tr
                     uint64_t tv = kUnreached;
                     if (i < nfar) {
                         v = __ldcg(far + i);
-                        tv = __ldcg(reinterpret_cast<const unsigned long long *>(lab + v)) >> 32;
+                        tv = __ldcg(&nd[v].lab) >> 32;
                     }
                     const bool drop = i < nfar && tv < theta;            // settled in an earlier bucket
                     const bool move = i < nfar && tv >= theta && tv < next;
@@ -284,7 +290,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBlocksPerSm) td_trees(Tr
                     const uint32_t mk = __ballot_sync(0xFFFFFFFFu, keep), mm = __ballot_sync(0xFFFFFFFFu, move);
                     const uint32_t below = (1u << lane) - 1u;
                     __syncwarp();  // every lane has read its entry before any is overwritten
-                    if (drop || move) __stcg(fmark + v, 0u);
+                    if (drop || move) __stcg(&nd[v].fmark, 0u);
                     if (keep) __stcg(far + kept + __popc(mk & below), v);
                     if (move) __stcg(fa + nn + __popc(mm & below), v);
                     kept += __popc(mk);
@@ -307,13 +313,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBlocksPerSm) td_trees(Tr
         }
         if (!bounded && lane == 0) atomicOr(A.err, kErrBound);
         // far marks of the nodes still in the far pile (the others were cleared)
-        for (uint32_t i = lane; i < nfar; i += 32) __stcg(fmark + __ldcg(far + i), 0u);
+        for (uint32_t i = lane; i < nfar; i += 32) __stcg(&nd[__ldcg(far + i)].fmark, 0u);
         // paths of the group's trips, in travel order, timed from each trip's departure
         for (uint32_t q = lane; q < G.count; q += 32) {
             const uint32_t j = A.order[G.first + q];
             const uint32_t d = A.dest[j];
             A.path_len[j] = 0;
-            const uint64_t ld = __ldcg(reinterpret_cast<const unsigned long long *>(lab + d));
+            const uint64_t ld = __ldcg(&nd[d].lab);
             if (ld == kUnreached || d == G.src || !bounded) {
                 atomicOr(A.err, kErrUnreachable);
                 continue;
@@ -321,7 +327,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBlocksPerSm) td_trees(Tr
             uint32_t L = 0;
             bool ok = true;
             for (uint32_t v = d; v != G.src;) {
-                const uint32_t e = (uint32_t)__ldcg(reinterpret_cast<const unsigned long long *>(lab + v));
+                const uint32_t e = (uint32_t)__ldcg(&nd[v].lab);
                 if (++L > A.n_nodes || e >= A.n_edges) {
                     ok = false;
                     break;
@@ -339,7 +345,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBlocksPerSm) td_trees(Tr
             }
             uint32_t pos = L;
             for (uint32_t v = d; v != G.src && pos > 0;) {
-                const uint32_t e = (uint32_t)__ldcg(reinterpret_cast<const unsigned long long *>(lab + v));
+                const uint32_t e = (uint32_t)__ldcg(&nd[v].lab);
                 A.edges[off + --pos] = e;  // e < n_edges: the counting walk checked this chain
                 v = A.src[e];
             }
@@ -353,11 +359,17 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBlocksPerSm) td_trees(Tr
         // clear the labels this tree set
         __syncwarp();
         for (uint32_t i = lane; i < nt; i += 32)
-            __stcg(reinterpret_cast<unsigned long long *>(lab + __ldcg(touched + i)), (unsigned long long)kUnreached);
+            __stcg(&nd[__ldcg(touched + i)].lab, (unsigned long long)kUnreached);
         __threadfence_block();
         __syncwarp();
     }
     if (lane == 0) A.stamp[gw] = stamp;
+}
+
+// every node unreached, with no round stamp and no far mark
+__global__ void init_nodes(NodeRec *nd, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        nd[i] = NodeRec{(unsigned long long)kUnreached, 0u, 0u};
 }
 
 // Inflow per (edge, bin) of the routes: each trip walks its route from its
@@ -477,26 +489,23 @@ int gpu_setup(lpsim_assign *a) {
     A.err = static_cast<uint32_t *>(g->alloc(4));
     if (!A.path_off || !A.path_len || !A.tsp || !A.cursor || !A.next_group || !A.err)
         return fail(LPSIM_E_OOM, "device allocation failed");
-    // workspaces: as many warps as fit the budget, at most 16 per SM
-    const uint64_t per_warp = (uint64_t)a->n_nodes * (8 + 6 * 4);
+    // workspaces: as many warps as fit the budget, at most kBlocksPerSm * kWarpsPerBlock per SM
+    const uint64_t per_warp = (uint64_t)a->n_nodes * (sizeof(NodeRec) + 4 * 4);
     uint64_t warps = std::min<uint64_t>((uint64_t)g->n_sm * kBlocksPerSm * kWarpsPerBlock,
                                         std::max<uint64_t>(kWorkspaceBudget / std::max<uint64_t>(per_warp, 1), 1));
     warps = std::max<uint64_t>(kWarpsPerBlock, warps / kWarpsPerBlock * kWarpsPerBlock);
     g->n_warps = (uint32_t)warps;
     const size_t nn = (size_t)warps * a->n_nodes;
-    A.lab = static_cast<uint64_t *>(g->alloc(nn * 8));
-    A.inq = static_cast<uint32_t *>(g->alloc(nn * 4));
+    A.node = static_cast<NodeRec *>(g->alloc(nn * sizeof(NodeRec)));
     A.touched = static_cast<uint32_t *>(g->alloc(nn * 4));
     A.fa = static_cast<uint32_t *>(g->alloc(nn * 4));
     A.fb = static_cast<uint32_t *>(g->alloc(nn * 4));
     A.far = static_cast<uint32_t *>(g->alloc(nn * 4));
-    A.fmark = static_cast<uint32_t *>(g->alloc(nn * 4));
     A.stamp = static_cast<uint32_t *>(g->alloc(warps * 4));
-    if (!A.lab || !A.inq || !A.touched || !A.fa || !A.fb || !A.far || !A.fmark || !A.stamp)
+    if (!A.node || !A.touched || !A.fa || !A.fb || !A.far || !A.stamp)
         return fail(LPSIM_E_OOM, "device allocation of the search workspaces failed");
-    CU(cudaMemsetAsync(A.lab, 0xFF, nn * 8, g->stream));
-    CU(cudaMemsetAsync(A.inq, 0, nn * 4, g->stream));
-    CU(cudaMemsetAsync(A.fmark, 0, nn * 4, g->stream));
+    init_nodes<<<g->n_sm * 4, 256, 0, g->stream>>>(A.node, nn);
+    CU(cudaGetLastError());
     A.delta_ms = kDeltaMs;
     CU(cudaMemsetAsync(A.stamp, 0, warps * 4, g->stream));
     CU(cudaStreamSynchronize(g->stream));
