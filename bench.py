@@ -301,6 +301,14 @@ def batch_arm(args, L, torch, rank, world, local, dist=None):
     print(json.dumps(out), flush=True)
 
 
+def surrogate_rows(torch) -> int:
+    """Rows per surrogate batch at the large scales: eight 128-row tiles per
+    SM (155,648 on 152 SMs), so the fused forward's persistent CTAs each run
+    four pairs of tiles and none idles while others finish a last tile."""
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    return 128 * 8 * n_sm
+
+
 def assignment_arm(args, L, torch):
     """Plain and surrogate-assisted MSA on the regional day (the 224k-node
     network and its 2.82M trips; --assignment-scale picks a reduced case),
@@ -317,7 +325,7 @@ def assignment_arm(args, L, torch):
     for rep in range(max(1, args.repeats)):
         for mode in ("plain", "surrogate"):
             r = msa(net, dem, mode, iterations=iters, target_gap=0.01, paths=args.paths,
-                    surrogate_batch=131072 if args.assignment_scale == "paper" else 8192)
+                    surrogate_batch=surrogate_rows(torch) if args.assignment_scale == "paper" else 8192)
             runs[mode].append(r)
     for mode in ("plain", "surrogate"):
         r = runs[mode][-1]
@@ -396,7 +404,8 @@ def surrogate_arm(args):
     import paper_2406_08496_gb300 as L
     with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
         peaks = json.load(f)
-    rows = 131072
+    import torch
+    rows = surrogate_rows(torch)
     s = L.Surrogate(n_features=11, batch=rows, seed=0)
     t = s.time(max(args.steps, 10))
     # the method's own multiply-adds per row: 11 real inputs (the zero

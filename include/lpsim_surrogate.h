@@ -91,8 +91,9 @@ int lpsim_mlp_time(lpsim_mlp *m, uint32_t iters, double *fwd_ms, double *train_m
 
 /* Diagnostics: GELU(z) and GELU'(z) of n inputs (host arrays) as the
  * tensor-core epilogues compute them -- z Phi(z) and Phi(z) + z phi(z) with
- * the standard normal CDF from Abramowitz and Stegun 26.2.17 (|error| <
- * 7.5e-8) -- so that tests can hold them to their error bound. */
+ * the standard normal CDF as a logistic of a fitted odd polynomial,
+ * 1 / (1 + 2^(z q(z^2))) (|error| < 6.8e-6, |z| |error| < 3.1e-6), and the
+ * exact density -- so that tests can hold them to their error bound. */
 int lpsim_mlp_gelu_eval(uint64_t n, const float *z, float *gelu, float *dgelu);
 
 void lpsim_mlp_destroy(lpsim_mlp *m);

