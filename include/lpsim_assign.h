@@ -119,6 +119,15 @@ int lpsim_assign_load_gpu(const lpsim_assign *a, const float *tt, uint32_t n_bin
 int lpsim_assign_features(const lpsim_assign *a, uint32_t n_bins, const uint32_t *inflow, const uint32_t *occ,
                           const float *prev_log_ratio, const uint32_t *prev_inflow, float *X, uint32_t n_features);
 
+/* lpsim_assign_features for the listed cells only: row r of X (n_rows x
+ * LPSIM_SURROGATE_FEATURES) holds the inputs of cell rows[r] = edge * n_bins
+ * + bin, equal bit for bit to that cell's row of the all-cells call (the
+ * arrays are the same full n_edges x n_bins inputs).  A cell index beyond
+ * n_edges x n_bins is LPSIM_E_INVALID_ARG. */
+int lpsim_assign_features_rows(const lpsim_assign *a, uint32_t n_bins, const uint32_t *inflow, const uint32_t *occ,
+                               const float *prev_log_ratio, const uint32_t *prev_inflow, uint64_t n_rows,
+                               const uint64_t *rows, float *X, uint32_t n_features);
+
 /* Link times (s) per (edge, bin) from a simulation's binned traversal sums
  * and counts; bins without a traversal take the free-flow time len / vmax.
  * log_ratio (nullable) receives log(measured / free-flow) where measured

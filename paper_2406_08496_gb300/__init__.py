@@ -38,7 +38,7 @@ EXPORTED = ["lpsim_last_error", "lpsim_version", "lpsim_set_allocator", "lpsim_l
             "lpsim_mlp_destroy",
             "lpsim_assign_create", "lpsim_assign_shortest_paths", "lpsim_assign_shortest_paths_gpu", "lpsim_assign_gap", "lpsim_assign_reroute",
             "lpsim_assign_route_excess", "lpsim_assign_reroute_worst", "lpsim_assign_route_length",
-            "lpsim_assign_get_routes", "lpsim_assign_load", "lpsim_assign_load_gpu", "lpsim_assign_features", "lpsim_assign_link_times", "lpsim_assign_times_from_ratio", "lpsim_assign_destroy"]
+            "lpsim_assign_get_routes", "lpsim_assign_load", "lpsim_assign_load_gpu", "lpsim_assign_features", "lpsim_assign_features_rows", "lpsim_assign_link_times", "lpsim_assign_times_from_ratio", "lpsim_assign_destroy"]
 
 STATUS = {0: "LPSIM_OK", -1: "LPSIM_E_INVALID_ARG", -2: "LPSIM_E_OOM", -3: "LPSIM_E_CUDA", -4: "LPSIM_E_STATE",
           -5: "LPSIM_E_TIMEOUT", -6: "LPSIM_E_GRIDLOCK", -7: "LPSIM_E_INVARIANT"}

@@ -38,6 +38,8 @@ def _lib():
         lib.lpsim_assign_load.argtypes = [P, P, ctypes.c_uint32, ctypes.c_uint32, P]
         lib.lpsim_assign_load_gpu.argtypes = [P, P, ctypes.c_uint32, ctypes.c_uint32, P]
         lib.lpsim_assign_features.argtypes = [P, ctypes.c_uint32, P, P, P, P, P, ctypes.c_uint32]
+        lib.lpsim_assign_features_rows.argtypes = [P, ctypes.c_uint32, P, P, P, P, ctypes.c_uint64, P, P,
+                                                   ctypes.c_uint32]
         lib.lpsim_assign_link_times.argtypes = [P, ctypes.c_uint32, P, P, P, P]
         lib.lpsim_assign_times_from_ratio.argtypes = [P, ctypes.c_uint32, P, P]
         lib.lpsim_assign_destroy.argtypes = [P]
@@ -132,11 +134,19 @@ class Assignment:
         return inflow
 
     def features(self, inflow: np.ndarray, occ: np.ndarray, prev_log_ratio: np.ndarray,
-                 prev_inflow: np.ndarray) -> np.ndarray:
+                 prev_inflow: np.ndarray, rows: np.ndarray | None = None) -> np.ndarray:
+        """Surrogate inputs of every (edge, bin) cell, edge-major, or of the
+        listed cells (rows: indices edge * n_bins + bin) in that order."""
         inflow = np.ascontiguousarray(inflow, dtype=np.uint32)
         occ = np.ascontiguousarray(occ, dtype=np.uint32)
         plr = np.ascontiguousarray(prev_log_ratio, dtype=np.float32)
         pin = np.ascontiguousarray(prev_inflow, dtype=np.uint32)
+        if rows is not None:
+            rows = np.ascontiguousarray(rows, dtype=np.uint64)
+            X = np.empty((len(rows), N_FEATURES), np.float32)
+            _check(self.lib, self.lib.lpsim_assign_features_rows(self.h, inflow.shape[1], _p(inflow), _p(occ), _p(plr),
+                                                                 _p(pin), len(rows), _p(rows), _p(X), N_FEATURES))
+            return X
         X = np.empty((inflow.shape[0] * inflow.shape[1], N_FEATURES), np.float32)
         _check(self.lib, self.lib.lpsim_assign_features(self.h, inflow.shape[1], _p(inflow), _p(occ), _p(plr),
                                                         _p(pin), _p(X), N_FEATURES))
@@ -179,7 +189,12 @@ def msa(net: dict, dem: dict, mode: str = "plain", iterations: int = 10, fractio
     on every simulation's link statistics so far); odd iterations skip the
     simulation, predict the link times of the current routes with the
     surrogate (inflows from loading the routes with the last simulated
-    times) and re-route under the prediction.  Every reported gap is
+    times) and re-route under the prediction.  The surrogate predicts the
+    change of each (link, bin) log travel-time ratio from the last
+    simulation (taken as 0 where that simulation did not measure the cell),
+    and it is trained on exactly the inputs a prediction sees: each
+    simulation's routes loaded under the previous simulation's link times,
+    with the previous simulation's occupancy, ratios and inflows.  Every reported gap is
     measured by a full simulation.  select: which trips move -- "random"
     (each trip with probability fraction, seeded) or "worst" (the fraction
     with the largest relative excess of their route over the shortest path
@@ -229,15 +244,20 @@ def msa(net: dict, dem: dict, mode: str = "plain", iterations: int = 10, fractio
             if rg <= target_gap and t_hit is None:
                 t_hit = now
             if mlp is not None:
-                # training pair: this simulation's (link, bin) times from its own
-                # inflows, starting from the previous simulation (itself at first)
-                ref_lr = logratio if lr_last is None else lr_last
-                ref_in = ls["inflow"] if in_last is None else in_last
-                X = A.features(ls["inflow"], ls["occ"], ref_lr, ref_in)
-                ok = (ls["tt_cnt"].reshape(-1) >= 2) & np.isfinite(logratio.reshape(-1))
+                # training pair (previous simulation -> this one; this one
+                # itself at first): the inputs a prediction from the previous
+                # simulation sees for these routes, and the change of the log
+                # ratios it should predict
                 t1 = time.perf_counter()
+                first = lr_last is None
+                ref_tt, ref_occ = (tt, ls["occ"]) if first else (tt_last, occ_last)
+                ref_lr, ref_in = (logratio, ls["inflow"]) if first else (lr_last, in_last)
+                loaded = A.load_gpu(ref_tt, bin_steps) if paths == "gpu" else A.load(ref_tt, bin_steps)
+                # samples: cells crossed at least twice (a measured ratio)
+                rows = np.flatnonzero(ls["tt_cnt"].reshape(-1) >= 2)
+                dy = logratio.reshape(-1)[rows] - np.nan_to_num(ref_lr.reshape(-1)[rows], nan=0.0)
                 # every simulation's samples join the model's device-resident pool
-                mlp.pool_add(X[ok], logratio.reshape(-1)[ok])
+                mlp.pool_add(A.features(loaded, ref_occ, ref_lr, ref_in, rows=rows), dy)
                 losses = mlp.train_pool(surrogate_steps, lr=1e-3, seed=seed + it)
                 rec["train_s"] = time.perf_counter() - t1
                 rec["surrogate_loss"] = float(losses[-20:].mean())
@@ -252,7 +272,7 @@ def msa(net: dict, dem: dict, mode: str = "plain", iterations: int = 10, fractio
         else:
             inflow = A.load_gpu(tt_last, bin_steps) if paths == "gpu" else A.load(tt_last, bin_steps)
             X = A.features(inflow, occ_last, lr_last, in_last)
-            y = mlp.forward(X)
+            y = mlp.forward(X) + np.nan_to_num(lr_last, nan=0.0).reshape(-1)
             tt_pred = A.times_from_ratio(y, n_bins)
             search(tt_pred, bin_steps, period_steps)
             if select == "worst":

@@ -361,43 +361,89 @@ int lpsim_assign_load(const lpsim_assign *a, const float *tt, uint32_t n_bins, u
     return LPSIM_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// the surrogate inputs of cell (e, b) (the layout lpsim_assign_features
+// documents); cells[] = cells of every edge, lin(b') = the edge's scaled log
+// inflow of bin b'
+template <class Lin>
+inline void feature_row(const lpsim_assign *a, uint32_t n_bins, const uint32_t *occ, const float *prev_log_ratio,
+                        const uint32_t *prev_inflow, const float *cells, uint32_t e, uint32_t b, const Lin &lin,
+                        float *x) {
+    x[0] = a->len[e] / 1000.0f;
+    x[1] = (float)a->lanes[e] / 4.0f;
+    x[2] = a->vmax[e] / 30.0f;
+    // inflow of this bin and the three before it (log1p(0) = 0 before the first)
+    for (int q = 0; q < 4; q++) x[3 + q] = (int64_t)b - q >= 0 ? lin(b - q) : 0.0f;
+    x[7] = 10.0f * (float)occ[(size_t)e * n_bins + b] / cells[e];
+    // mean occupancy density of the downstream links
+    const uint32_t v = a->dst[e];
+    float down = 0.0f;
+    uint32_t nd = 0;
+    for (uint32_t j = a->out_off[v]; j < a->out_off[v + 1]; j++) {
+        const uint32_t f = a->out_edge[j];
+        down += (float)occ[(size_t)f * n_bins + b] / cells[f];
+        nd++;
+    }
+    x[8] = nd ? 10.0f * down / (float)nd : 0.0f;
+    // the reference simulation of the same (edge, bin): its travel-time ratio and inflow
+    const size_t i = (size_t)e * n_bins + b;
+    x[9] = std::isfinite(prev_log_ratio[i]) ? prev_log_ratio[i] : 0.0f;
+    x[10] = std::log1p((float)prev_inflow[i] / (float)a->lanes[e]) / 4.0f;
+}
+
+std::vector<float> edge_cells(const lpsim_assign *a) {
+    std::vector<float> cells(a->n_edges);
+    parallel_pieces(a->n_edges, [&](uint64_t e0, uint64_t e1, uint64_t) {
+        for (uint64_t e = e0; e < e1; e++) cells[e] = std::max(1.0f, std::ceil(a->len[e])) * (float)a->lanes[e];
+    });
+    return cells;
+}
+
+}  // namespace
+
+extern "C" {
+
 int lpsim_assign_features(const lpsim_assign *a, uint32_t n_bins, const uint32_t *inflow, const uint32_t *occ,
                           const float *prev_log_ratio, const uint32_t *prev_inflow, float *X, uint32_t n_features) {
     if (!a || !inflow || !occ || !prev_log_ratio || !prev_inflow || !X || n_features != LPSIM_SURROGATE_FEATURES)
         return fail(LPSIM_E_INVALID_ARG, "bad argument");
     // cells of every edge (for the occupancy densities), once
-    std::vector<float> cells(a->n_edges);
-    parallel_pieces(a->n_edges, [&](uint64_t e0, uint64_t e1, uint64_t) {
-        for (uint64_t e = e0; e < e1; e++) cells[e] = std::max(1.0f, std::ceil(a->len[e])) * (float)a->lanes[e];
-    });
+    const std::vector<float> cells = edge_cells(a);
     parallel_pieces(a->n_edges, [&](uint64_t e0, uint64_t e1, uint64_t) {
         std::vector<float> lin(n_bins);  // the edge's scaled log inflow per bin, each computed once
         for (uint32_t e = (uint32_t)e0; e < (uint32_t)e1; e++) {
             for (uint32_t b = 0; b < n_bins; b++)
                 lin[b] = std::log1p((float)inflow[(size_t)e * n_bins + b] / (float)a->lanes[e]) / 4.0f;
-            // mean occupancy density of the downstream links
-            const uint32_t v = a->dst[e];
-            for (uint32_t b = 0; b < n_bins; b++) {
-                float *x = X + ((size_t)e * n_bins + b) * n_features;
-                x[0] = a->len[e] / 1000.0f;
-                x[1] = (float)a->lanes[e] / 4.0f;
-                x[2] = a->vmax[e] / 30.0f;
-                // inflow of this bin and the three before it (log1p(0) = 0 before the first)
-                for (int q = 0; q < 4; q++) x[3 + q] = (int64_t)b - q >= 0 ? lin[b - q] : 0.0f;
-                x[7] = 10.0f * (float)occ[(size_t)e * n_bins + b] / cells[e];
-                float down = 0.0f;
-                uint32_t nd = 0;
-                for (uint32_t j = a->out_off[v]; j < a->out_off[v + 1]; j++) {
-                    const uint32_t f = a->out_edge[j];
-                    down += (float)occ[(size_t)f * n_bins + b] / cells[f];
-                    nd++;
-                }
-                x[8] = nd ? 10.0f * down / (float)nd : 0.0f;
-                // the reference simulation of the same (edge, bin): its travel-time ratio and inflow
-                const size_t i = (size_t)e * n_bins + b;
-                x[9] = std::isfinite(prev_log_ratio[i]) ? prev_log_ratio[i] : 0.0f;
-                x[10] = std::log1p((float)prev_inflow[i] / (float)a->lanes[e]) / 4.0f;
-            }
+            for (uint32_t b = 0; b < n_bins; b++)
+                feature_row(a, n_bins, occ, prev_log_ratio, prev_inflow, cells.data(), e, b,
+                            [&](uint32_t bb) { return lin[bb]; }, X + ((size_t)e * n_bins + b) * n_features);
+        }
+    });
+    return LPSIM_OK;
+}
+
+int lpsim_assign_features_rows(const lpsim_assign *a, uint32_t n_bins, const uint32_t *inflow, const uint32_t *occ,
+                               const float *prev_log_ratio, const uint32_t *prev_inflow, uint64_t n_rows,
+                               const uint64_t *rows, float *X, uint32_t n_features) {
+    if (!a || !inflow || !occ || !prev_log_ratio || !prev_inflow || (n_rows && (!rows || !X)) || n_bins == 0 ||
+        n_features != LPSIM_SURROGATE_FEATURES)
+        return fail(LPSIM_E_INVALID_ARG, "bad argument");
+    const uint64_t n_cells = (uint64_t)a->n_edges * n_bins;
+    for (uint64_t r = 0; r < n_rows; r++)
+        if (rows[r] >= n_cells) return fail(LPSIM_E_INVALID_ARG, "row index beyond n_edges x n_bins");
+    const std::vector<float> cells = edge_cells(a);
+    parallel_pieces(n_rows, [&](uint64_t r0, uint64_t r1, uint64_t) {
+        for (uint64_t r = r0; r < r1; r++) {
+            const uint32_t e = (uint32_t)(rows[r] / n_bins), b = (uint32_t)(rows[r] % n_bins);
+            // the same scaled log inflow as the all-cells call computes per bin
+            feature_row(a, n_bins, occ, prev_log_ratio, prev_inflow, cells.data(), e, b,
+                        [&](uint32_t bb) {
+                            return std::log1p((float)inflow[(size_t)e * n_bins + bb] / (float)a->lanes[e]) / 4.0f;
+                        },
+                        X + r * n_features);
         }
     });
     return LPSIM_OK;

@@ -156,6 +156,30 @@ def test_link_times_and_features(A):
     assert abs(X[1, 9] - lr[0, 1]) < 1e-6 and X[4 + 1, 9] == 0.0  # unmeasured cells read 0
 
 
+def test_features_of_listed_cells_equal_all_cells(A):
+    """The per-cell feature call gives, bit for bit, the rows of the
+    all-cells call for the listed cells, in the listed order; an index past
+    the last cell is refused."""
+    import workloads as W
+    net = W.grid_network(5, 5)
+    dem = W.route(net, W.uniform_demand(net, 80, 4))
+    a = A.Assignment(net, dem, dt=0.5)
+    rng = np.random.default_rng(3)
+    ne, nb = net["n_edges"], 12
+    inflow = rng.integers(0, 40, (ne, nb)).astype(np.uint32)
+    occ = rng.integers(0, 20, (ne, nb)).astype(np.uint32)
+    plr = rng.normal(0.0, 0.3, (ne, nb)).astype(np.float32)
+    plr[rng.random((ne, nb)) < 0.3] = np.nan
+    pin = rng.integers(0, 40, (ne, nb)).astype(np.uint32)
+    X = a.features(inflow, occ, plr, pin)
+    rows = rng.permutation(ne * nb)[: ne * nb // 3]
+    Xr = a.features(inflow, occ, plr, pin, rows=rows)
+    assert np.array_equal(X[rows].view(np.uint32), Xr.view(np.uint32))
+    assert a.features(inflow, occ, plr, pin, rows=np.zeros(0, np.uint64)).shape == (0, 11)
+    with pytest.raises(RuntimeError):
+        a.features(inflow, occ, plr, pin, rows=np.array([ne * nb], np.uint64))
+
+
 def test_worst_first_reroute(A):
     """Per-trip excess from a simulated outcome (gap) and from predicted link
     times (route_excess); worst-first re-routing moves exactly the requested

@@ -1,6 +1,7 @@
 """The assignment loop on the GPU: plain MSA and surrogate-assisted MSA on a
-small regional case; every gap is measured by a full simulation; the
-trained surrogate predicts link times better than the method without it."""
+small regional case; every gap is measured by a full simulation; on the
+regional day the trained surrogate predicts link times better than the
+method without it (the last simulation's own times)."""
 from __future__ import annotations
 
 import numpy as np
@@ -133,53 +134,83 @@ def test_msa_surrogate_runs_and_is_judged_by_simulation(case):
     assert sims[-1]["gap"] < sims[0]["gap"]
 
 
-def test_surrogate_beats_free_flow_and_stale_times(case):
-    """Train on one simulation of the routes, then predict the link times of
-    a second simulation after 30% of the trips moved to new paths; compare
-    the errors (seconds, over measured (link, bin) cells) with the free-flow
-    times and with the first simulation's times."""
+def _surrogate_vs_stale(net, dem, fraction, n_pairs, batch):
+    """Simulate the routes n_pairs + 1 times, `fraction` of the trips moved
+    to their shortest paths between simulations; train the surrogate as the
+    assignment loop does (pairs (0 -> 0), (0 -> 1), ..., (n-2 -> n-1): the
+    change of each measured cell's log travel-time ratio from the earlier
+    simulation, from the later routes loaded under the earlier link times and
+    the earlier occupancy, ratios and inflows), predict simulation n from
+    n - 1, and return the per-vehicle link-time errors (seconds; cells
+    weighted by the vehicles that crossed them) of the prediction, of the
+    free-flow times and of simulation n - 1's own times (the input plain MSA
+    re-routes with), over every measured cell and over the cells whose
+    loaded inflow changed by 10% or more."""
     from paper_2406_08496_gb300 import Simulation, Surrogate
     from paper_2406_08496_gb300.assignment import Assignment
-    net, dem = case
-    params = dict(bin_steps=1800, n_bins=96)
+    nb = 96
     A = Assignment(net, dem, seed=1)
-
-    def simulate():
-        s = Simulation(net, params)
+    sims = []
+    for k in range(n_pairs + 1):
+        s = Simulation(net, dict(bin_steps=1800, n_bins=nb))
         s.load_demand(A.routes())
         s.run(300_000)
         ls = s.link_stats()
         s.close()
-        return ls
+        tt, lr = A.link_times(ls["tt_sum"], ls["tt_cnt"])
+        # these routes loaded under the earlier simulation's times (their own at first)
+        loaded = A.load_gpu(sims[-1]["tt"] if sims else tt, 1800)
+        sims.append(dict(ls, tt=tt, lr=lr, loaded=loaded, loaded_self=A.load_gpu(tt, 1800)))
+        if k < n_pairs:
+            A.shortest_paths_gpu(tt, 1800, 3600)
+            A.reroute(fraction, k)
+    base = [np.nan_to_num(x["lr"], nan=0.0).reshape(-1) for x in sims]
+    mlp = Surrogate(n_features=11, batch=batch, seed=3)
+    for ref, k in [(0, 0)] + [(k - 1, k) for k in range(1, n_pairs)]:
+        r, x = sims[ref], sims[k]
+        rows = np.flatnonzero(x["tt_cnt"].reshape(-1) >= 2)
+        X = A.features(x["loaded_self"] if ref == k else x["loaded"], r["occ"], r["lr"], r["inflow"], rows=rows)
+        mlp.pool_add(X, x["lr"].reshape(-1)[rows] - base[ref][rows])
+    mlp.train_pool(1500, lr=1e-3, seed=4)
+    r, x = sims[n_pairs - 1], sims[n_pairs]
+    y = mlp.forward(A.features(x["loaded"], r["occ"], r["lr"], r["inflow"])) + base[n_pairs - 1]
+    pred = A.times_from_ratio(y, nb).reshape(-1)
+    ff = np.repeat((net["edge_len"] / net["edge_vmax"])[:, None], nb, axis=1).reshape(-1)
+    w = x["tt_cnt"].reshape(-1).astype(np.float64)
+    lp, lq = x["loaded"].reshape(-1).astype(np.float64), r["loaded_self"].reshape(-1).astype(np.float64)
+    changed = np.abs(lp - lq) >= 0.1 * np.maximum(lq, 1.0)
+    out = {}
+    for name, m in (("all", w > 0), ("changed", (w > 0) & changed)):
+        err = lambda p: float(np.average(np.abs(p[m] - x["tt"].reshape(-1)[m]), weights=w[m]))
+        out[name] = dict(surrogate=err(pred), free_flow=err(ff), stale=err(r["tt"].reshape(-1)))
+    return out
 
-    # three simulations, 20% of the trips re-routed between them; train on
-    # the pairs (sim0 -> sim0) and (sim0 -> sim1), predict sim2 from sim1
-    ls, tt, lr = [], [], []
-    for k in range(3):
-        ls.append(simulate())
-        a, b = A.link_times(ls[-1]["tt_sum"], ls[-1]["tt_cnt"])
-        tt.append(a)
-        lr.append(b)
-        if k < 2:
-            A.shortest_paths(a, 1800, 3600)
-            A.reroute(0.2, k)
-    mlp = Surrogate(n_features=11, batch=2048, seed=3)
-    Xs, ts = [], []
-    for ref, k in ((0, 0), (0, 1)):
-        X = A.features(ls[k]["inflow"], ls[k]["occ"], lr[ref], ls[ref]["inflow"])
-        ok = (ls[k]["tt_cnt"].reshape(-1) >= 2) & np.isfinite(lr[k].reshape(-1))
-        Xs.append(X[ok])
-        ts.append(lr[k].reshape(-1)[ok])
-    mlp.train(np.concatenate(Xs), np.concatenate(ts), steps=1500, lr=1e-3, seed=4)
-    inflow = A.load(tt[1], 1800)
-    tt_pred = A.times_from_ratio(mlp.forward(A.features(inflow, ls[1]["occ"], lr[1], ls[1]["inflow"])), 96)
-    ff = np.repeat((net["edge_len"] / net["edge_vmax"])[:, None], 96, axis=1)
-    w = ls[2]["tt_cnt"].reshape(-1).astype(np.float64)
-    ok2 = w > 0
-    # per-vehicle error: cells weighted by the vehicles that crossed them
-    err = lambda p: float(np.average(np.abs(p.reshape(-1)[ok2] - tt[2].reshape(-1)[ok2]), weights=w[ok2]))
-    e_sur, e_ff, e_stale = err(tt_pred), err(ff), err(tt[1])
-    print(f"link-time error per vehicle (s): surrogate {e_sur:.3f}, free flow {e_ff:.3f}, "
-          f"previous simulation {e_stale:.3f}")
-    assert e_sur < 0.5 * e_ff
-    assert e_sur < 1.5 * e_stale
+
+def test_surrogate_pipeline_beats_free_flow(case):
+    """The loop's training and prediction path end to end on the small
+    case: the prediction is far closer to the next simulation than free flow.
+    (On this lightly loaded network link times hardly respond to the moved
+    trips -- the change of a cell's log ratio correlates about 0.1 with the
+    change of its inflow -- so the earlier simulation's own times are the
+    better guess there; the regional day below is where the surrogate has
+    something to predict.)"""
+    e = _surrogate_vs_stale(*case, fraction=0.2, n_pairs=3, batch=2048)["all"]
+    print("tiny case, link-time error per vehicle (s):", {k: round(v, 3) for k, v in e.items()})
+    assert e["surrogate"] < 0.5 * e["free_flow"]
+
+
+def test_surrogate_beats_stale_times_on_the_regional_day():
+    """The gain of the trained network over the method without it, on the
+    2.82M-trip regional day (224k nodes) with the loop's 10% re-routing:
+    its prediction of the next simulation's link times is closer than the
+    last simulation's own times (the input plain MSA re-routes with) over
+    every measured cell, and by more on the cells whose inflow the moved
+    trips changed; both far closer than free flow."""
+    net, dem = W.assignment_case(scale="paper")
+    import torch
+    batch = 128 * 8 * torch.cuda.get_device_properties(0).multi_processor_count
+    e = _surrogate_vs_stale(net, dem, fraction=0.1, n_pairs=4, batch=batch)
+    print("regional day, link-time error per vehicle (s):",
+          {k: {q: round(v, 3) for q, v in d.items()} for k, d in e.items()})
+    assert e["all"]["surrogate"] < e["all"]["stale"] < 0.5 * e["all"]["free_flow"]
+    assert e["changed"]["surrogate"] < e["changed"]["stale"]
