@@ -25,7 +25,7 @@ _LOCK = threading.Lock()
 # lane-change horizon x0; critical-gap constants).
 DEFAULT_PARAMS = dict(dt=0.5, a=1.0, b=1.5, s0=2.0, T=1.5, x0=100.0, g_a=2.0, g_b=2.0,
                       alpha_i=1.0, alpha_a=1.0, alpha_b=1.0, eps_amp=0.0, seed=12345,
-                      bin_steps=1800, n_bins=0)
+                      bin_steps=1800, n_bins=0, dlc_prob=0.0, dlc_gain=5.0)
 
 
 class OrcParams(ctypes.Structure):
@@ -33,7 +33,8 @@ class OrcParams(ctypes.Structure):
                 ("s0", ctypes.c_float), ("T", ctypes.c_float), ("x0", ctypes.c_float),
                 ("g_a", ctypes.c_float), ("g_b", ctypes.c_float), ("alpha_i", ctypes.c_float),
                 ("alpha_a", ctypes.c_float), ("alpha_b", ctypes.c_float), ("eps_amp", ctypes.c_float),
-                ("seed", ctypes.c_uint64), ("bin_steps", ctypes.c_uint32), ("n_bins", ctypes.c_uint32)]
+                ("seed", ctypes.c_uint64), ("bin_steps", ctypes.c_uint32), ("n_bins", ctypes.c_uint32),
+                ("dlc_prob", ctypes.c_float), ("dlc_gain", ctypes.c_float)]
 
 
 class OrcVehicleType(ctypes.Structure):

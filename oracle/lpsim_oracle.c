@@ -47,6 +47,17 @@
  *                 on odd k, downward only on even k; probability
  *                 m = 1 - (L_e - x)/x0 when L_e - x < x0, else 0; draw
  *                 u = top 24 bits of SplitMix64(seed ^ id*C1 ^ k*C2) / 2^24.
+ *      discretionary lane change (an extension: the paper names only the
+ *                 mandatory change; off when dlc_prob = 0): a staying vehicle
+ *                 outside the mandatory case above (no next movement, already
+ *                 in its target lane, or farther than x0 from the end) held
+ *                 below its free speed by its leader c_f (v' < v0: the IDM or
+ *                 the clamp acted) with that leader slower than its free speed
+ *                 (speed byte < v0) intends one lane up on odd k, down on even
+ *                 k (if that lane exists) when, in that lane of M_cur, the
+ *                 nearest occupied cell c_a in [floor(x), floor(x)+63] is
+ *                 absent or c_a - c_f >= dlc_gain, and u < dlc_prob (the same
+ *                 draw u); P3 then judges it like any intent.
  *      departure  the lowest-id waiting vehicle of each first edge whose
  *                 departure step has come asks for cell 0 of that edge.
  *      entry lane lanes of the entered edge ordered by distance to its own tl
@@ -234,6 +245,7 @@ int orc_create(orc_sim **out, uint32_t n_nodes, uint32_t n_edges, const uint32_t
     if (!out || !src || !dst || !len_m || !lanes || !vmax || !green_steps || !p) return -1;
     if (n_nodes == 0 || n_edges == 0) return -1;
     if (!(p->dt > 0.0f) || !(p->a > 0.0f) || !(p->b > 0.0f) || !(p->s0 >= 0.0f) || !(p->x0 > 0.0f)) return -1;
+    if (!(p->dlc_prob >= 0.0f && p->dlc_prob <= 1.0f) || !(p->dlc_gain >= 0.0f)) return -1;
     if (p->bin_steps == 0 && p->n_bins != 0) return -1;
     for (uint32_t e = 0; e < n_edges; e++) {
         if (src[e] >= n_nodes || dst[e] >= n_nodes) return -1;
@@ -445,12 +457,15 @@ static void decide(orc_sim *s, uint32_t i, uint32_t k) {
         return;
     }
     s->act[i] = ACT_STAY;
-    if (s->lanes[e] > 1 && pos < last) {
+    if (s->lanes[e] < 2) return;
+    int mandatory = 0;
+    if (pos < last) {
         uint32_t tl = target_lane(s, e, s->redge[pos + 1]);
         if (tl != ln) {
             int dir = tl > ln ? 1 : -1;
+            float xrem = L - x;
+            mandatory = xrem < p->x0;
             if ((dir > 0) == ((k & 1u) == 1u)) {
-                float xrem = L - x;
                 float m = xrem >= p->x0 ? 0.0f : 1.0f - xrem / p->x0;
                 uint64_t h = splitmix64_mix(p->seed ^ ((uint64_t)i * 0x9E3779B97F4A7C15ULL) ^
                                             ((uint64_t)k * 0xD1B54A32D192ED03ULL));
@@ -458,6 +473,20 @@ static void decide(orc_sim *s, uint32_t i, uint32_t k) {
             }
         }
     }
+    /* discretionary lane change: held up by a slower leader, a longer gap
+     * ahead in the lane of this step's direction */
+    if (mandatory || !(p->dlc_prob > 0.0f)) return;
+    if (!(has_f && vn < v0 && (float)s->Mcur[base + cf] < v0)) return;
+    int dir = (k & 1u) ? 1 : -1;
+    if (dir > 0 ? ln + 1 >= s->lanes[e] : ln == 0) return;
+    uint64_t base2 = cell_index(s, e, (uint32_t)((int)ln + dir), 0);
+    for (uint32_t q = c; q < len && q <= c + 63; q++)
+        if (s->Mcur[base2 + q] != EMPTY) {
+            if (!((float)q - (float)cf >= p->dlc_gain)) return;
+            break;
+        }
+    uint64_t h = splitmix64_mix(p->seed ^ ((uint64_t)i * 0x9E3779B97F4A7C15ULL) ^ ((uint64_t)k * 0xD1B54A32D192ED03ULL));
+    if (unit24(h) < p->dlc_prob) { s->act[i] = ACT_INTEND; s->dir[i] = (int8_t)dir; }
 }
 
 /* P3 for one lane-change intender: gap acceptance against M_cur, free target

@@ -40,6 +40,8 @@ typedef struct orc_params {
     uint64_t seed;            /* seed of the lane-change draws */
     uint32_t bin_steps;       /* steps per link-statistics bin */
     uint32_t n_bins;          /* bins kept per edge */
+    float dlc_prob;           /* discretionary lane change: probability per step when it pays (0 = none) */
+    float dlc_gain;           /* discretionary lane change: gap gain it needs, m */
 } orc_params;
 
 typedef struct orc_sim orc_sim;

@@ -173,17 +173,31 @@ class BruteForce:
                         requests.append((w["route"][w["r"] + 1], l, w["id"]))
                 continue
             kind, d = "stay", 0
+            draw = unit24(splitmix64_mix(int(p["seed"]) ^ ((w["id"] * 0x9E3779B97F4A7C15) & M64)
+                                         ^ ((k * 0xD1B54A32D192ED03) & M64)))
+            must = False  # inside the mandatory lane-change zone of its next movement
             if self.lanes[e] > 1 and not last:
                 tl = self.tl_for(e, w["route"][w["r"] + 1])
                 if tl != ln:
                     d = 1 if tl > ln else -1
+                    xrem = F(L - x)
+                    must = xrem < p["x0"]
                     if (d > 0) == (k % 2 == 1):
-                        xrem = F(L - x)
                         m = F(0) if xrem >= p["x0"] else F(F(1.0) - F(xrem / p["x0"]))
-                        h = splitmix64_mix(int(p["seed"]) ^ ((w["id"] * 0x9E3779B97F4A7C15) & M64)
-                                           ^ ((k * 0xD1B54A32D192ED03) & M64))
-                        if unit24(h) < m:
+                        if draw < m:
                             kind = "intend"
+            # discretionary change: held up by a slower leader, a longer gap in
+            # the lane of this step's direction (up on odd steps)
+            if kind == "stay" and not must and self.lanes[e] > 1 and p.get("dlc_prob", 0.0) > 0.0:
+                d = 1 if k % 2 == 1 else -1
+                ln2 = ln + d
+                blocked = (cf is not None and vn < vfree
+                           and F(speed_byte(occ[(e, ln, cf)]["v"])) < vfree)
+                if blocked and 0 <= ln2 < self.lanes[e]:
+                    lead = [cc for cc in range(c, min(c + 63, ncell - 1) + 1) if (e, ln2, cc) in occ]
+                    pays = not lead or F(F(lead[0]) - F(cf)) >= F(p["dlc_gain"])
+                    if pays and draw < F(p["dlc_prob"]):
+                        kind = "intend"
             plan[w["id"]] = (kind, xn, vn, d if kind == "intend" else 0)
         # departures: lowest waiting id per first edge, if its time has come
         heads = {}

@@ -43,13 +43,41 @@ TYPES = [dict(a=1.0, b=1.5, s0=2.0, T=1.5, vmax=254.0), dict(a=0.6, b=1.2, s0=4.
          dict(a=0.8, b=1.0, s0=1.0, T=1.0, vmax=4.5)]
 
 
-def compare(seed, steps=70, typed=False):
-    net, trips, params = scenario(seed)
+def scenario_overtaking(seed):
+    """Long multi-lane edges in a chain with a diverge, a slow vehicle
+    departing first and faster ones behind it: the case the discretionary
+    rule is for."""
+    rng = np.random.default_rng(seed)
+    topo = [(0, 1), (1, 2), (1, 3), (2, 4)]
+    lens = rng.choice([60.0, 120.0, 250.0], size=len(topo))
+    lanes = rng.integers(2, 4, size=len(topo))
+    vmax = rng.choice([13.9, 20.0], size=len(topo))
+    edges = [(a, b, float(l), int(n), float(v)) for (a, b), l, n, v in zip(topo, lens, lanes, vmax)]
+    net = make_net(5, edges, green={1: int(rng.choice([0, 20]))})
+    routes = [[0, 1, 3], [0, 2], [0, 1], [0]]
+    nveh = int(rng.integers(3, 8))
+    trips = [(int(2 * q + rng.integers(0, 3)), routes[int(rng.integers(len(routes)))]) for q in range(nveh)]
+    params = dict(x0=float(rng.choice([100.0, 30.0])), seed=int(rng.integers(1, 1 << 40)),
+                  eps_amp=float(rng.choice([0.0, 1.5])), bin_steps=0, n_bins=0)
+    vt = np.concatenate([[2], rng.integers(0, len(TYPES), nveh - 1)]).astype(np.uint8)  # a bike first
+    return net, trips, params, vt
+
+
+def compare(seed, steps=70, typed=False, dlc=False, overtaking=False):
+    if overtaking:
+        net, trips, params, vt = scenario_overtaking(seed)
+    else:
+        net, trips, params = scenario(seed)
+    if dlc:
+        # discretionary lane changes (an extension of the paper's mandatory rule)
+        rng = np.random.default_rng(seed + 11)
+        params.update(dlc_prob=float(rng.choice([0.3, 1.0])), dlc_gain=float(rng.choice([0.0, 3.0, 8.0])))
     dem = make_demand(trips)
     types = None
-    if typed:
+    if typed or overtaking:
         types = TYPES
-        dem["vtype"] = np.random.default_rng(seed + 7).integers(0, len(TYPES), len(trips)).astype(np.uint8)
+        dem["vtype"] = (vt if overtaking else
+                        np.random.default_rng(seed + 7).integers(0, len(TYPES), len(trips)).astype(np.uint8))
     o = O.Oracle(net, params, vehicle_types=types)
     vid = o.load_demand(dem)
     bf = BruteForce(net, dict(O.DEFAULT_PARAMS, **params), vehicle_types=types)
@@ -86,6 +114,20 @@ def test_bruteforce_tiny_vehicle_types(block):
     State: vehicle type; multimodal traffic, Sec. 5)."""
     for seed in range(1000 + block * 40, 1000 + block * 40 + 40):
         compare(seed, typed=True)
+
+
+@pytest.mark.parametrize("block", range(2))
+def test_bruteforce_tiny_discretionary_lane_changes(block):
+    """Discretionary lane changes on, in the typed family and in a family of
+    long multi-lane edges with a bike departing ahead of cars and trucks:
+    trajectories agree bit for bit, and the rule fires (more lane changes
+    than the same overtaking scenarios with it off)."""
+    on = off = 0
+    for seed in range(2000 + block * 40, 2000 + block * 40 + 40):
+        compare(seed, typed=True, dlc=True)
+        on += compare(seed, steps=120, dlc=True, overtaking=True)["lane_changes"]
+        off += compare(seed, steps=120, overtaking=True)["lane_changes"]
+    assert on > off
 
 
 def test_bruteforce_exercises_lane_changes_and_conflicts():

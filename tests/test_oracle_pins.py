@@ -623,3 +623,32 @@ def test_type_idm_matches_double_closed_form():
         assert abs(float(nx["v"][1]) - want) <= 1e-5 * max(1.0, want), (v1, vf, s, nx["v"][1], want)
         positive += want > 0
     assert positive > 0
+
+
+def test_discretionary_lane_change_lets_a_car_pass_a_bike():
+    """Discretionary lane change (an extension: the paper defines only the
+    mandatory change): on a 1 km two-lane edge a bike (top speed 4.5 m/s)
+    departs first and a car follows in the same lane.  With the rule off the
+    car cannot pass (no mandatory change on its last edge) and arrives after
+    the bike; with it on, the first odd step at which the bike holds it below
+    its free speed (the bike slower than that speed, an empty lane above)
+    moves it up one lane, and it arrives first."""
+    types = [dict(a=1.0, b=1.5, s0=2.0, T=1.5, vmax=254.0), dict(a=0.8, b=1.0, s0=1.0, T=1.0, vmax=4.5)]
+    net = make_net(2, [(0, 1, 1000.0, 2, 20.0)])
+    dem = make_demand([(0, [0]), (4, [0])])
+    dem["vtype"] = np.array([1, 0], np.uint8)
+    arrive, lanes_seen = {}, {}
+    for dlc in (0.0, 1.0):
+        o = O.Oracle(net, dict(bin_steps=0, n_bins=0, dlc_prob=dlc, dlc_gain=5.0), vehicle_types=types)
+        o.load_demand(dem)
+        seen = set()
+        for _ in range(600):
+            o.step(1)
+            st = o.state()
+            if st["status"][1] == 1:
+                seen.add(int(st["lane"][1]))
+        arrive[dlc] = o.trips()["arrive"].tolist()
+        lanes_seen[dlc] = seen
+    bike, car = 0, 1
+    assert arrive[0.0][car] > arrive[0.0][bike] and lanes_seen[0.0] == {0}
+    assert arrive[1.0][car] < arrive[1.0][bike] and lanes_seen[1.0] == {0, 1}
