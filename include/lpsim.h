@@ -96,6 +96,12 @@ typedef struct lpsim_params {
     uint32_t light_trips; /* a chunk runs in the single-block light-load kernel when at most this many
                              trips can be on the network or waiting during it (0 = 1536); a speed
                              setting only, results are the same for every value */
+    float dlc_prob;       /* discretionary lane change (an extension; the paper defines only the
+                             mandatory change): per-step probability, in [0, 1], that a vehicle
+                             outside the mandatory zone, held below its free speed by a slower
+                             leader, intends one lane up (odd steps) or down (even steps); 0 = off */
+    float dlc_gain;       /* the lead gap in that lane must be absent or longer than the own lane's
+                             by at least this many metres (>= 0) */
 } lpsim_params;
 
 /* Road network.  Edge e runs edge_src[e] -> edge_dst[e], is edge_len_m[e]

@@ -23,7 +23,7 @@ __all__ = ["Simulation", "LpsimError", "DEFAULT_PARAMS", "build", "load_library"
 DEFAULT_PARAMS = dict(dt=0.5, a=1.0, b=1.5, s0=2.0, T=1.5, x0=100.0, g_a=2.0, g_b=2.0,
                       alpha_i=1.0, alpha_a=1.0, alpha_b=1.0, eps_amp=0.0, seed=12345,
                       bin_steps=1800, n_bins=0, sort_period=256, block_size=256, blocks_per_sm=4,
-                      chunk_steps=1536, gridlock_steps=0, flags=0, light_trips=0)
+                      chunk_steps=1536, gridlock_steps=0, flags=0, light_trips=0, dlc_prob=0.0, dlc_gain=5.0)
 FLAG_NO_SORT = 1
 
 EXPORTED = ["lpsim_last_error", "lpsim_version", "lpsim_set_allocator", "lpsim_load_network",
@@ -50,7 +50,8 @@ class Params(ctypes.Structure):
                [("seed", ctypes.c_uint64)] + \
                [(n, ctypes.c_uint32) for n in ("bin_steps", "n_bins", "sort_period", "block_size",
                                                "blocks_per_sm", "chunk_steps", "gridlock_steps", "flags",
-                                               "light_trips")]
+                                               "light_trips")] + \
+               [(n, ctypes.c_float) for n in ("dlc_prob", "dlc_gain")]
 
 
 class Network(ctypes.Structure):

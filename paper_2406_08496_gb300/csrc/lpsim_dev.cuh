@@ -55,6 +55,7 @@ struct Model {
     float dt, a, s0, T, two_sqrt_ab, x0, g_a, g_b, alpha_i, alpha_a, alpha_b, eps_amp;
     uint64_t seed;
     uint32_t bin_steps, n_bins;
+    float dlc_prob, dlc_gain;  // discretionary lane change (dlc_prob = 0: off)
 };
 
 // Vehicle type: its car-following parameters and top speed (free-flow speed

@@ -75,7 +75,8 @@ int check_params(const lpsim_params *p) {
     if (!p) return fail(LPSIM_E_INVALID_ARG, "params is NULL");
     if (!(p->dt > 0.0f) || !(p->a > 0.0f) || !(p->b > 0.0f) || !(p->s0 >= 0.0f) || !(p->x0 > 0.0f) ||
         !std::isfinite(p->T) || !std::isfinite(p->g_a) || !std::isfinite(p->g_b) || !std::isfinite(p->alpha_i) ||
-        !std::isfinite(p->alpha_a) || !std::isfinite(p->alpha_b) || !(p->eps_amp >= 0.0f))
+        !std::isfinite(p->alpha_a) || !std::isfinite(p->alpha_b) || !(p->eps_amp >= 0.0f) ||
+        !(p->dlc_prob >= 0.0f && p->dlc_prob <= 1.0f) || !(p->dlc_gain >= 0.0f) || !std::isfinite(p->dlc_gain))
         return fail(LPSIM_E_INVALID_ARG, "model parameter out of range");
     if (p->bin_steps == 0 && p->n_bins != 0) return fail(LPSIM_E_INVALID_ARG, "n_bins without bin_steps");
     if (p->block_size && p->block_size != 128 && p->block_size != 256 && p->block_size != 512)
@@ -476,6 +477,8 @@ int load_network_impl(lpsim_ctx **out, const lpsim_network *net, const lpsim_par
     d.m.seed = p->seed;
     d.m.bin_steps = p->bin_steps;
     d.m.n_bins = p->n_bins;
+    d.m.dlc_prob = p->dlc_prob;
+    d.m.dlc_gain = p->dlc_gain;
     d.n_edges = ne;
 
     EdgeRec *edge = nullptr;

@@ -524,32 +524,56 @@ __device__ __forceinline__ bool p1_slot(const Dev &d, const StepView &w, const P
     vw[s] = vn;
     const uint32_t cn = (uint32_t)xn;
     put_cell(d, Mn, base + cn, speed_byte(vn));
+    bool intend = false;
+    uint32_t up = 0;
+    uint64_t hkd = hk;
     if (may_draw) {
         const float xrem = L - x;
         const float mp = xrem >= m.x0 ? 0.0f : 1.0f - xrem / m.x0;
         // u is in [0, 1): no draw can pass when mp <= 0
         if (mp > 0.0f && unit24(splitmix64_mix(hk ^ ((uint64_t)k * 0xD1B54A32D192ED03ull))) < mp) {
-            Iw[base + cn] = 1;
-            d.s.imark[s] = base + cn;
-            IntendRec ir;
-            ir.s = s;
-            ir.base = base;
-            ir.hk = hk;
-            ir.x = x;
-            ir.xn = xn;
-            ir.vn = vn;
-            ir.len = (uint16_t)len;
-            ir.lane = (uint8_t)ln;
-            ir.up = tl > ln ? 1 : 0;
-            // An intent aiming at cell len - 1 (where a stop-line hold may land) goes to
-            // the top of the same list, growing downwards: step_p2 checks those few
-            // against the crossing request of the target lane.
-            if (cn + 1 < len)
-                stage_put(sk.ir, kStageIntend, sk.n + 1, d.intend_list[par], &d.counts[2 + par], ir);
-            else {
-                d.intend_list[par][d.cap - 1 - warp_append(&d.counts[6 + par])] = ir;
-                atomicAdd(sk.n + 3, 1u);
+            intend = true;
+            up = tl > ln ? 1u : 0u;
+        }
+    } else if (m.dlc_prob > 0.0f && has_f && vn < v0 && !(tl != kNoLane && tl != ln && (L - x) < m.x0) &&
+               (float)Mc[base + cf] < v0) {
+        // discretionary lane change (outside the mandatory zone, held below
+        // its free speed by a slower leader): one lane up on odd steps, down
+        // on even ones, when that lane's lead gap is absent or longer by
+        // dlc_gain; the same draw as the mandatory rule
+        up = par;
+        const uint32_t nl = d.edge[d.route[rpos]].lanes;
+        if (up ? ln + 1 < nl : ln > 0) {
+            const uint32_t stride = row_stride(len);
+            const uint32_t base2 = up ? base + stride : base - stride;
+            const uint32_t ca = first_occupied_wide(Mc + base2, c, min(c + 63u, len - 1));
+            if (ca == kNone || (float)ca - (float)cf >= m.dlc_gain) {
+                hkd = d.hkey_from_id ? d.m.seed ^ ((uint64_t)id * 0x9E3779B97F4A7C15ull) : d.hkey[id];
+                intend = unit24(splitmix64_mix(hkd ^ ((uint64_t)k * 0xD1B54A32D192ED03ull))) < m.dlc_prob;
             }
+        }
+    }
+    if (intend) {
+        Iw[base + cn] = 1;
+        d.s.imark[s] = base + cn;
+        IntendRec ir;
+        ir.s = s;
+        ir.base = base;
+        ir.hk = hkd;
+        ir.x = x;
+        ir.xn = xn;
+        ir.vn = vn;
+        ir.len = (uint16_t)len;
+        ir.lane = (uint8_t)ln;
+        ir.up = (uint8_t)up;
+        // An intent aiming at cell len - 1 (where a stop-line hold may land) goes to
+        // the top of the same list, growing downwards: step_p2 checks those few
+        // against the crossing request of the target lane.
+        if (cn + 1 < len)
+            stage_put(sk.ir, kStageIntend, sk.n + 1, d.intend_list[par], &d.counts[2 + par], ir);
+        else {
+            d.intend_list[par][d.cap - 1 - warp_append(&d.counts[6 + par])] = ir;
+            atomicAdd(sk.n + 3, 1u);
         }
     }
     return true;

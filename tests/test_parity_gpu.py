@@ -105,6 +105,41 @@ def test_vehicle_types_tiny_scenarios():
         lockstep(net, dem, params, 70, check_every=1, vehicle_types=BF_TYPES)
 
 
+def test_discretionary_lane_changes_small_regional():
+    """Discretionary lane changes on (an extension of the paper's mandatory
+    rule) with cars, trucks and bikes on the small planar network, with
+    random gap components: bit for bit every 100 steps, and the rule adds
+    lane changes over the same run with it off."""
+    net = W.planar_network(40, 40, seed=21)
+    dem = W.route(net, W.gravity_demand(net, 12000, 22, zones_x=6, zones_y=6, access_per_zone=3,
+                                        beta_m=2500.0, peaks_h=(0.1, 0.25), peak_sigma_h=0.1))
+    base = dict(bin_steps=450, n_bins=8, seed=99, eps_amp=1.0)
+    o, g = lockstep(net, _typed(dem, 4), dict(base, dlc_prob=0.3, dlc_gain=3.0), 3000, check_every=100,
+                    vehicle_types=TYPES)
+    o2, _ = lockstep(net, _typed(dem, 4), base, 3000, check_every=3000, vehicle_types=TYPES)
+    assert o.counters()["lane_changes"] > o2.counters()["lane_changes"] + 100
+
+
+@pytest.mark.parametrize("chunked", [False, True])
+def test_discretionary_lane_changes_tiny_overtaking(chunked):
+    """The brute force's overtaking family (long multi-lane edges, a bike
+    departing ahead of cars and trucks) with the rule on: step by step in
+    the grid-wide kernels, and in 24-step graph chunks, which these few
+    trips run in the single-block light-load kernel."""
+    from test_oracle_bruteforce import TYPES as BF_TYPES
+    from test_oracle_bruteforce import scenario_overtaking
+    for seed in range(2000, 2030):
+        net, trips, params, vt = scenario_overtaking(seed)
+        dem = make_demand(trips)
+        dem["vtype"] = vt
+        params.update(dlc_prob=1.0 if seed % 2 else 0.3, dlc_gain=float(seed % 3) * 4.0)
+        if chunked:
+            lockstep(net, dem, params, 120, check_every=24, vehicle_types=BF_TYPES,
+                     gpu_params=dict(sort_period=6, chunk_steps=24))
+        else:
+            lockstep(net, dem, params, 120, check_every=1, vehicle_types=BF_TYPES, gpu_params=dict(flags=4))
+
+
 def test_edge_cases():
     # one-cell edges, 4 lanes, single-edge routes, far-future departure, a
     # queue of 30 vehicles released at once onto a one-lane edge
