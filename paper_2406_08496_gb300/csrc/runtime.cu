@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <numeric>
 #include <string>
@@ -683,7 +684,14 @@ int load_demand_impl(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, cons
         std::stable_sort(order.begin(), order.end(),
                          [&](uint32_t a, uint32_t b) { return depart_step[a] < depart_step[b]; });
     }
-    std::vector<uint32_t> dep(n), roff(n + 1), route(total ? total : 1);
+    std::vector<uint32_t> dep(n), roff(n + 1);
+    // the routes in vehicle-id order: left uninitialised (every entry is
+    // written below, by the host's threads, which also take its first-touch
+    // page faults in parallel)
+    const uint64_t rsize = total ? total : 1;
+    std::unique_ptr<uint32_t[]> route(new (std::nothrow) uint32_t[rsize]);
+    if (!route) return fail(LPSIM_E_OOM, "host allocation of the route array failed");
+    if (!total) route[0] = 0;
     // lane-change draw keys: seed ^ (id within the scenario) * C1; a single
     // scenario's key follows from the id on the device
     std::vector<uint64_t> hkey(scen ? n : 0);
@@ -714,7 +722,7 @@ int load_demand_impl(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, cons
     parallel_pieces(n, [&](uint64_t i0, uint64_t i1, uint64_t) {
         for (uint64_t id = i0; id < i1; id++) {
             const uint32_t j = order[id];
-            std::memcpy(route.data() + roff[id], route_edges + route_off[j], (size_t)(roff[id + 1] - roff[id]) * 4);
+            std::memcpy(route.get() + roff[id], route_edges + route_off[j], (size_t)(roff[id + 1] - roff[id]) * 4);
         }
     });
     c->dep_sorted = dep;  // nondecreasing: ids are ranks by departure step
@@ -758,9 +766,9 @@ int load_demand_impl(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, cons
     RouteRec *drrec;
     dhkey = nullptr;
     if (scen) TRY(dnew(c, dhkey, n));
-    TRY(dnew(c, droute, route.size()));
+    TRY(dnew(c, droute, rsize));
     TRY(dnew(c, droff, n + 1));
-    TRY(dnew(c, drrec, route.size()));
+    TRY(dnew(c, drrec, rsize));
     TRY(dnew_mut(c, d.dep_act, n));
     TRY(dnew_mut(c, d.arr, n));
     TRY(dnew_mut(c, d.status, n));
@@ -816,7 +824,7 @@ int load_demand_impl(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, cons
         d.trip_vt = dvt;
         d.typed = 1;
     }
-    TRY(upload(c, droute, route.data(), route.size() * 4));
+    TRY(upload(c, droute, route.get(), rsize * 4));
     TRY(upload(c, droff, roff.data(), (n + 1) * 4));
     TRY(upload(c, oe, org_edge.data(), norg * 4ull));
     TRY(upload(c, oq, org_qoff.data(), norg * 4ull));
