@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="regional",
-                    choices=["regional", "grid", "large", "batch64", "assignment", "paths", "surrogate"])
+                    choices=["regional", "grid", "large", "batch64", "assignment", "paths", "surrogate", "onchip"])
     ap.add_argument("--repeats", type=int, default=1,
                     help="assignment workload: alternate the two arms this many times and report the spread")
     ap.add_argument("--iterations", type=int, default=40,
@@ -395,6 +395,52 @@ def paths_arm(args):
     print(json.dumps(out), flush=True)
 
 
+def onchip_arm(args):
+    """The lane maps on chip (the paper's shared-memory direction, Sec. 5):
+    a 4x4 grid (48 two-lane 400 m links, 38 KB of lane map) whose five maps
+    fit the light-load kernel's shared memory, 1,200 trips over 30 minutes
+    run to completion in light-load chunks, timed with the maps in shared
+    memory (LPSIM_F_SHARED_MAPS) and, alternately, in global memory; same
+    results either way (tested).  value = vehicle-steps/s with the maps on
+    chip."""
+    import paper_2406_08496_gb300 as L
+    import torch
+    import workloads as W
+    L.use_torch_allocator()
+    st = torch.cuda.Stream()
+    torch.cuda.set_stream(st)
+    net = W.grid_network(4, 4)
+    dem = W.route(net, W.uniform_demand(net, 1200, 5))
+    base = dict(bin_steps=1800, n_bins=4)
+    sims = {"shared": L.Simulation(net, dict(base, flags=8)), "global": L.Simulation(net, dict(base))}
+    for s in sims.values():
+        s.load_demand(dem)
+    res = {k: [] for k in sims}
+    veh = {}
+    for rep in range(max(args.warmup, 1) + max(args.steps, 1)):
+        for name, s in sims.items():
+            s.reset()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(st)
+            r = s.run(200_000)
+            e1.record(st)
+            torch.cuda.synchronize()
+            veh[name] = (r["veh_steps"], r["steps"])
+            if rep >= max(args.warmup, 1):
+                res[name].append(e0.elapsed_time(e1))
+    ms = {k: float(np.median(v)) for k, v in res.items()}
+    out = {"metric": "veh-steps/s", "value": veh["shared"][0] / (ms["shared"] / 1e3), "unit": "veh-steps/s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms["shared"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "grid-4x4-1200-trips-lane-maps-on-chip", "edges": int(net["n_edges"]),
+                      "trips": 1200, "sim_steps": veh["shared"][1], "step": "the demand run to completion"},
+           "global_maps": {"value": veh["global"][0] / (ms["global"] / 1e3), "ms_per_run": ms["global"]},
+           "speedup_on_chip": ms["global"] / ms["shared"],
+           "us_per_sim_step": {k: 1e3 * ms[k] / veh[k][1] for k in ms}}
+    print(json.dumps(out), flush=True)
+
+
 def surrogate_arm(args):
     """The surrogate MLP's tensor-core kernels on device-resident batches:
     the inference forward (one persistent kernel: three BF16 layers and the
@@ -464,6 +510,9 @@ def main():
         return
     if args.workload == "surrogate":
         surrogate_arm(args)
+        return
+    if args.workload == "onchip":
+        onchip_arm(args)
         return
 
     net, dem, label = load_workload(args.workload)

@@ -64,6 +64,7 @@ extern "C" {
 #define LPSIM_F_NO_SORT 1u
 #define LPSIM_F_CHECK_CELLS 2u
 #define LPSIM_F_NO_LIGHT 4u
+#define LPSIM_F_SHARED_MAPS 8u
 
 typedef struct lpsim_ctx lpsim_ctx;
 
@@ -92,6 +93,10 @@ typedef struct lpsim_params {
                              every lane-map write lands on an empty cell (LPSIM_E_INVARIANT otherwise;
                              costs a load per write); LPSIM_F_NO_LIGHT: never run a chunk in the
                              single-block light-load kernel (results are the same either way);
+                             LPSIM_F_SHARED_MAPS: the light-load kernel copies the five lane maps
+                             into its shared memory for each chunk when they fit (at most 200 KB:
+                             networks of up to ~40k lane-metres; results are the same either way;
+                             measured 2% slower on a 4x4 grid, whose maps stay in L2 anyway);
                              other bits must be 0 */
     uint32_t light_trips; /* a chunk runs in the single-block light-load kernel when at most this many
                              trips can be on the network or waiting during it (0 = 1536); a speed
@@ -142,6 +147,7 @@ typedef struct lpsim_counters {
     uint64_t k, veh_steps, arrived, active, waiting, lane_changes;
     uint64_t slots;       /* vehicle slots in use (active plus not yet compacted) */
     uint64_t launches;    /* kernel launches issued by this context */
+    uint64_t light_chunks; /* chunks run in the single-block light-load kernel */
 } lpsim_counters;
 
 /* Message of the calling thread's last failure ("" if none). */

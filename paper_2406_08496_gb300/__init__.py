@@ -72,7 +72,7 @@ class LinkStat(ctypes.Structure):
 
 class Counters(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("k", "veh_steps", "arrived", "active", "waiting", "lane_changes",
-                                               "slots", "launches")]
+                                               "slots", "launches", "light_chunks")]
 
 
 class TuneResult(ctypes.Structure):

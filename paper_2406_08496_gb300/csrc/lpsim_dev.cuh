@@ -295,8 +295,10 @@ void launch_apply_crossings(const Dev &d, int grid, cudaStream_t st);
 void launch_timing_fold(const Dev &d, uint32_t nsteps, cudaStream_t st);
 // steps [k0, k0 + nsteps) in one block (light load); olist: n_org scratch
 // entries, no: one device counter
+// shared memory the light-load kernel may take for the lane maps (five maps)
+constexpr size_t kSmallMapSmem = 200 * 1024;
 cudaError_t launch_small(const Dev &d, uint32_t k0, uint32_t nsteps, uint32_t *olist, uint32_t *no,
-                         cudaStream_t st);
+                         uint32_t map_words, cudaStream_t st);
 
 // compaction (and optional sort by lane-map cell) of the slots after step k;
 // src/dst slot sets; writes *n_slots

@@ -82,7 +82,7 @@ int check_params(const lpsim_params *p) {
     if (p->bin_steps == 0 && p->n_bins != 0) return fail(LPSIM_E_INVALID_ARG, "n_bins without bin_steps");
     if (p->block_size && p->block_size != 128 && p->block_size != 256 && p->block_size != 512)
         return fail(LPSIM_E_INVALID_ARG, "block_size must be 0, 128, 256 or 512");
-    if (p->flags & ~7u) return fail(LPSIM_E_INVALID_ARG, "unknown flag bits");
+    if (p->flags & ~15u) return fail(LPSIM_E_INVALID_ARG, "unknown flag bits");
     if (p->sort_period > 256) return fail(LPSIM_E_INVALID_ARG, "sort_period must be at most 256");
     return LPSIM_OK;
 }
@@ -243,7 +243,12 @@ bool light_chunk_ok(const lpsim_ctx *c) {
 int light_chunk(lpsim_ctx *c) {
     Dev d = c->d;
     d.s = c->sets[c->cur];
-    CU(launch_small(d, c->k, c->C, c->small_list, c->small_n, c->stream));
+    // with LPSIM_F_SHARED_MAPS the lane maps of a small network ride in the
+    // light-load kernel's shared memory for the chunk
+    const uint64_t words = (c->map_bytes + 15) / 16;
+    const uint32_t map_words =
+        ((c->p.flags & LPSIM_F_SHARED_MAPS) && words * 16 * 5 <= kSmallMapSmem) ? (uint32_t)words : 0u;
+    CU(launch_small(d, c->k, c->C, c->small_list, c->small_n, map_words, c->stream));
     launch_compact(d, c->sets[c->cur ^ 1], c->w, c->C - 1, c->sort, c->grid, c->stream);
     c->cur ^= 1;
     launch_apply_crossings(c->d, c->grid, c->stream);
@@ -1169,6 +1174,7 @@ int lpsim_get_counters(lpsim_ctx *c, lpsim_counters *out) {
     out->lane_changes = c->h_ctr[2];
     out->slots = c->h_ctr[9] & 0xFFFFFFFFull;
     out->launches = c->launches;
+    out->light_chunks = c->light_chunks;
     return LPSIM_OK;
 }
 

@@ -930,12 +930,28 @@ __global__ void __launch_bounds__(BLOCK) step_p2(Dev d, uint32_t koff, uint32_t 
 // global round trip of its own.  (Clusters of 2-8 such blocks, synchronised
 // by cluster barriers, were measured slower than the grid-wide kernels for
 // 2k-12k trips.)
+// map_words > 0: the network's five lane maps (three rotating occupancy
+// maps, two intent maps; map_words 16-byte words each) are copied into this
+// block's shared memory for the chunk and back at its end, and every phase
+// reads and writes them there (through generic addresses: the phase bodies
+// are the same code); 0: they stay in global memory.
 __global__ void __launch_bounds__(kSmallBlock, 1)
-    step_small(Dev d, uint32_t k0, uint32_t nsteps, const uint32_t *olist, const uint32_t *no_ptr) {
+    step_small(Dev d, uint32_t k0, uint32_t nsteps, const uint32_t *olist, const uint32_t *no_ptr,
+               uint32_t map_words) {
+    extern __shared__ __align__(16) uint4 s_maps[];
     span_start(d, d.tspan_light);
     const uint32_t tid = threadIdx.x;
     const uint32_t no = *no_ptr;
     uint32_t n = *d.n_slots, ev0 = *d.ev_n;
+    // the five maps in global memory, in the order (map 0, 1, 2, intent map 0, 1)
+    uint8_t *const gmaps[5] = {d.map[0], d.map[1], d.map[2], d.imap[0], d.imap[1]};
+    if (map_words) {
+        for (int a = 0; a < 5; a++) {
+            const uint4 *g = reinterpret_cast<const uint4 *>(gmaps[a]);
+            uint4 *sm = s_maps + (size_t)a * map_words;
+            for (uint32_t i = tid; i < map_words; i += kSmallBlock) sm[i] = g[i];
+        }
+    }
     __shared__ __align__(16) CrossRec s_cr[kStageCross];
     __shared__ __align__(16) IntendRec s_ir[kStageIntend];
     __shared__ __align__(16) DepRec s_dr[kStageDep];
@@ -946,7 +962,18 @@ __global__ void __launch_bounds__(kSmallBlock, 1)
     uint32_t live = 0, arrived = 0, events = 0, departed = 0, changes = 0;
     for (uint32_t t = 0; t < nsteps; t++) {
         const uint32_t k = k0 + t, par = k & 1u;
-        const StepView w = step_view(d, k, k);
+        StepView w = step_view(d, k, k);
+        if (map_words) {
+            // the same rotation over the shared-memory copies
+            uint8_t *const sm = reinterpret_cast<uint8_t *>(s_maps);
+            const size_t mb = (size_t)map_words * 16;
+            const uint32_t r3 = k % 3u;
+            w.Mc = sm + r3 * mb;
+            w.Mn = sm + (r3 == 2u ? 0u : r3 + 1u) * mb;
+            w.Mo = sm + (r3 == 0u ? 2u : r3 - 1u) * mb;
+            w.Iw = sm + (3u + par) * mb;
+            w.Io = sm + (3u + (par ^ 1u)) * mb;
+        }
         // P1
         for (uint32_t i = tid; i < no; i += kSmallBlock) p1_origin(d, w, sk, olist[i]);
         for (uint32_t s = tid; s < n; s += kSmallBlock) p1_slot(d, w, sk, s, n, live, arrived);
@@ -977,6 +1004,14 @@ __global__ void __launch_bounds__(kSmallBlock, 1)
     if (tid == 0) {
         *d.n_slots = n;
         *d.ev_n = ev0;
+    }
+    if (map_words) {
+        // the loop ended on a block barrier: every write to the maps is done
+        for (int a = 0; a < 5; a++) {
+            const uint4 *sm = s_maps + (size_t)a * map_words;
+            uint4 *g = reinterpret_cast<uint4 *>(gmaps[a]);
+            for (uint32_t i = tid; i < map_words; i += kSmallBlock) g[i] = sm[i];
+        }
     }
     warp_add64(&d.ctr[0], live);
     warp_add64(&d.ctr[1], arrived);
@@ -1111,11 +1146,19 @@ void launch_apply_crossings(const Dev &d, int grid, cudaStream_t st) { apply_cro
 void launch_timing_fold(const Dev &d, uint32_t nsteps, cudaStream_t st) { timing_fold<<<1, 1024, 0, st>>>(d, nsteps); }
 
 cudaError_t launch_small(const Dev &d, uint32_t k0, uint32_t nsteps, uint32_t *olist, uint32_t *no,
-                         cudaStream_t st) {
+                         uint32_t map_words, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(no, 0, 4, st);
     if (e != cudaSuccess) return e;
+    const size_t smem = (size_t)map_words * 16 * 5;
+    if (smem > kSmallMapSmem) return cudaErrorInvalidValue;
+    static bool attr_set = false;
+    if (smem > 48 * 1024 && !attr_set) {
+        e = cudaFuncSetAttribute(step_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmallMapSmem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
     small_origins<<<(d.n_org + 255) / 256 + 1, 256, 0, st>>>(d, k0 + nsteps, olist, no);
-    step_small<<<1, kSmallBlock, 0, st>>>(d, k0, nsteps, olist, no);
+    step_small<<<1, kSmallBlock, smem, st>>>(d, k0, nsteps, olist, no, map_words);
     return cudaGetLastError();
 }
 

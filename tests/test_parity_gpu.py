@@ -211,6 +211,36 @@ def test_idle_hours_match_oracle(grid_day, chunk_steps):
     assert_outputs_equal(o, g, n_bins=20)
 
 
+@pytest.mark.parametrize("flags", [0, 8])
+def test_lane_maps_on_chip_match_oracle(flags):
+    """A 4x4 grid (38 KB of lane map): the light-load kernel keeps all five
+    lane maps in its shared memory for each chunk (flags 8 =
+    LPSIM_F_SHARED_MAPS) or in global memory (flags 0); both match the oracle bit for bit
+    at every chunk boundary, in the outputs and with lane changes on (the
+    discretionary rule too), and the maps read back equal."""
+    import oracle as O
+    from paper_2406_08496_gb300 import Simulation
+    net = W.grid_network(4, 4)
+    dem = W.route(net, W.uniform_demand(net, 1200, 5))
+    params = dict(bin_steps=600, n_bins=8, dlc_prob=0.3, dlc_gain=3.0, eps_amp=1.0)
+    o = O.Oracle(net, params)
+    o.load_demand(dem)
+    g = Simulation(net, dict(params, flags=flags | 2))
+    g.load_demand(dem)
+    for _ in range(3):
+        o.step(1536)
+        g.step(1536)
+        assert_state_equal(o.state(), g.state(), f"step {o.counters()['k']}")
+        assert np.array_equal(o.lane_map(), g.lane_map())
+    ro, rg = o.run(20000), g.run(20000)
+    for key in ("steps", "veh_steps", "arrived", "active", "waiting", "k"):
+        assert ro[key] == rg[key], (key, ro[key], rg[key])
+    assert_outputs_equal(o, g, n_bins=8)
+    co, cg = o.counters(), g.counters()
+    assert co["lane_changes"] == cg["lane_changes"] and co["lane_changes"] > 0
+    assert g.counters()["light_chunks"] >= 3
+
+
 @pytest.mark.parametrize("flags", [0, 4])
 def test_light_load_chunks_match_oracle(grid_day, flags):
     """A quarter of the grid day's trips: at most 1,536 trips are ever due
