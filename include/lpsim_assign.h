@@ -65,7 +65,7 @@ int lpsim_assign_shortest_paths(lpsim_assign *a, const float *tt, uint32_t n_bin
  * searches: link times are whole milliseconds, so every arrival is an exact
  * sum, and both keep the earliest arrival with ties to the lower entering
  * edge id.  The graph, trip table and search workspaces (32 bytes per node
- * per concurrent tree, up to 32 trees per SM within 48 GiB) stay on the
+ * per concurrent tree, up to 40 trees per SM within 48 GiB) stay on the
  * device between calls and are released by lpsim_assign_destroy.  Errors as the host call, plus
  * LPSIM_E_CUDA, LPSIM_E_OOM and LPSIM_E_STATE (another device current). */
 int lpsim_assign_shortest_paths_gpu(lpsim_assign *a, const float *tt, uint32_t n_bins, uint32_t bin_steps,

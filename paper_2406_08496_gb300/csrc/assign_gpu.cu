@@ -14,8 +14,8 @@
 // hide the memory latency each relaxation pays: on the 2.82M-trip day, 16
 // trees per SM took 2.7 s per pass, 32 took 1.85 s, 64 took 1.78 s; the
 // out-edges of a round's near nodes spread over the lanes took 32 to 1.7 s,
-// and a node's label, round stamp and far mark in one 16-byte record to
-// 1.33 s):
+// a node's label, round stamp and far mark in one 16-byte record to
+// 1.33 s, and 40 trees per SM (48 registers, no spills) to 1.26 s):
 //   * label-correcting search in rounds over time buckets (near-far): the
 //     near set's nodes relax their out-edges with the arrival function of
 //     the bin holding their arrival time (FIFO by construction, see TD); a
@@ -68,7 +68,7 @@ int fail(int code, const std::string &m) { return lpsim_fail(code, m); }
 constexpr uint64_t kUnreached = ~0ull;
 constexpr uint32_t kNoEdge = 0xFFFFFFFFu;
 #ifndef LPSIM_ASSIGN_WARPS_PER_SM
-#define LPSIM_ASSIGN_WARPS_PER_SM 32
+#define LPSIM_ASSIGN_WARPS_PER_SM 40
 #endif
 #ifndef LPSIM_ASSIGN_WORKSPACE_GIB
 #define LPSIM_ASSIGN_WORKSPACE_GIB 48
