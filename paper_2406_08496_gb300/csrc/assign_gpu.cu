@@ -44,6 +44,8 @@
 
 #include <algorithm>
 #include <cstring>
+#include <memory>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -410,6 +412,29 @@ struct AssignGpu {
     uint64_t redge_cap = 0;
     uint32_t *inflow = nullptr;
     size_t inflow_cells = 0;
+    // host staging kept between calls (grown, never shrunk, never cleared:
+    // every call writes what it reads), so the large tables are not
+    // zero-filled and their pages not faulted in again at every call
+    std::unique_ptr<LinkTime[]> h_table;
+    size_t h_table_cap = 0;
+    std::unique_ptr<uint32_t[]> h_edges;
+    size_t h_edges_cap = 0;
+    LinkTime *table_buf(size_t n) {
+        if (n > h_table_cap) {
+            h_table.reset(new (std::nothrow) LinkTime[n]);
+            h_table_cap = h_table ? n : 0;
+        }
+        return h_table.get();
+    }
+    uint32_t *edges_buf(size_t n) {
+        n = std::max<size_t>(n, 1);
+        if (n > h_edges_cap) {
+            const size_t want = n + n / 4;
+            h_edges.reset(new (std::nothrow) uint32_t[want]);
+            h_edges_cap = h_edges ? want : 0;
+        }
+        return h_edges.get();
+    }
 
     void *alloc(size_t bytes) {
         void *p = nullptr;
@@ -549,22 +574,26 @@ namespace {
 int gpu_table(lpsim_assign *a, const float *tt, uint32_t n_bins, uint32_t bin_steps) {
     AssignGpu *g = a->gpu;
     TreeArgs &A = g->A;
-    const TD td(a, tt, n_bins, bin_steps);
-    if (td.bin_ms > 0xFFFFFFFFull) return fail(LPSIM_E_INVALID_ARG, "bin longer than the 32-bit millisecond range");
+    const uint64_t bin_ms = table_bin_ms(a, bin_steps);
+    if (bin_ms > 0xFFFFFFFFull) return fail(LPSIM_E_INVALID_ARG, "bin longer than the 32-bit millisecond range");
     static_assert(sizeof(LinkTime) == sizeof(uint2), "link-time record");
+    const size_t cells = (size_t)n_bins * a->n_edges;
+    // the previous call's upload of the staging table has finished (each call synchronises)
+    LinkTime *tbm = g->table_buf(cells);
+    if (!tbm) return fail(LPSIM_E_OOM, "host allocation of the link-time table failed");
+    fill_link_times(a, tt, n_bins, bin_ms, tbm);
     if (A.cms && A.n_bins != n_bins) {
         g->release(const_cast<uint2 *>(A.cms));
         A.cms = nullptr;
     }
     if (!A.cms) {
-        A.cms = static_cast<uint2 *>(g->alloc(td.tbm.size() * sizeof(uint2)));
+        A.cms = static_cast<uint2 *>(g->alloc(cells * sizeof(uint2)));
         if (!A.cms) return fail(LPSIM_E_OOM, "device allocation of the link-time table failed");
     }
-    CU(cudaMemcpyAsync(const_cast<uint2 *>(A.cms), td.tbm.data(), td.tbm.size() * sizeof(uint2),
-                       cudaMemcpyHostToDevice, g->stream));
+    CU(cudaMemcpyAsync(const_cast<uint2 *>(A.cms), tbm, cells * sizeof(uint2), cudaMemcpyHostToDevice, g->stream));
     A.n_bins = n_bins;
-    A.bin_ms = (uint32_t)td.bin_ms;
-    // the host table goes away with td: let the copy finish first
+    A.bin_ms = (uint32_t)bin_ms;
+    // the staging table is rewritten by the next call: let the copy finish first
     CU(cudaStreamSynchronize(g->stream));
     return LPSIM_OK;
 }
@@ -590,10 +619,10 @@ extern "C" int lpsim_assign_load_gpu(const lpsim_assign *ac, const float *tt, ui
     off[0] = 0;
     for (uint64_t j = 0; j < a->n; j++) off[j + 1] = off[j] + a->route[j].size();
     const uint64_t total = off[a->n];
-    std::vector<uint32_t> edges(std::max<uint64_t>(total, 1));
+    uint32_t *edges = g->edges_buf(total);
+    if (!edges) return fail(LPSIM_E_OOM, "host allocation of the route staging failed");
     lpsim::parallel_pieces(a->n, [&](uint64_t j0, uint64_t j1, uint64_t) {
-        for (uint64_t j = j0; j < j1; j++)
-            std::memcpy(edges.data() + off[j], a->route[j].data(), a->route[j].size() * 4);
+        for (uint64_t j = j0; j < j1; j++) std::memcpy(edges + off[j], a->route[j].data(), a->route[j].size() * 4);
     });
     if (!g->roff) {
         g->roff = static_cast<unsigned long long *>(g->alloc((a->n + 1) * 8));
@@ -613,7 +642,7 @@ extern "C" int lpsim_assign_load_gpu(const lpsim_assign *ac, const float *tt, ui
         g->inflow_cells = cells;
     }
     CU(cudaMemcpyAsync(g->roff, off.data(), (a->n + 1) * 8, cudaMemcpyHostToDevice, g->stream));
-    if (total) CU(cudaMemcpyAsync(g->redge, edges.data(), total * 4, cudaMemcpyHostToDevice, g->stream));
+    if (total) CU(cudaMemcpyAsync(g->redge, edges, total * 4, cudaMemcpyHostToDevice, g->stream));
     CU(cudaMemsetAsync(g->inflow, 0, cells * 4, g->stream));
     load_routes<<<(unsigned)std::min<uint64_t>((a->n + 255) / 256, 65535), 256, 0, g->stream>>>(
         g->roff, g->redge, g->A.dep_ms, a->n, g->A.cms, a->n_edges, n_bins, g->A.bin_ms, g->inflow);
@@ -668,14 +697,16 @@ extern "C" int lpsim_assign_shortest_paths_gpu(lpsim_assign *a, const float *tt,
     if (err & kErrUnreachable) return fail(LPSIM_E_INVALID_ARG, "a destination is unreachable from its origin");
     if (err & kErrCapacity) return fail(LPSIM_E_OOM, "path buffer still too small after resizing");
     std::vector<unsigned long long> off(a->n);
-    std::vector<uint32_t> len(a->n), edges(used);
+    std::vector<uint32_t> len(a->n);
+    uint32_t *edges = g->edges_buf(used);
+    if (!edges) return fail(LPSIM_E_OOM, "host allocation of the path staging failed");
     CU(cudaMemcpyAsync(off.data(), A.path_off, a->n * 8, cudaMemcpyDeviceToHost, g->stream));
     CU(cudaMemcpyAsync(len.data(), A.path_len, a->n * 4, cudaMemcpyDeviceToHost, g->stream));
     CU(cudaMemcpyAsync(a->tsp.data(), A.tsp, a->n * 4, cudaMemcpyDeviceToHost, g->stream));
-    if (used) CU(cudaMemcpyAsync(edges.data(), A.edges, used * 4, cudaMemcpyDeviceToHost, g->stream));
+    if (used) CU(cudaMemcpyAsync(edges, A.edges, used * 4, cudaMemcpyDeviceToHost, g->stream));
     CU(cudaStreamSynchronize(g->stream));
     lpsim::parallel_pieces(a->n, [&](uint64_t j0, uint64_t j1, uint64_t) {
-        for (uint64_t j = j0; j < j1; j++) a->cand[j].assign(edges.begin() + off[j], edges.begin() + off[j] + len[j]);
+        for (uint64_t j = j0; j < j1; j++) a->cand[j].assign(edges + off[j], edges + off[j] + len[j]);
     });
     if (t_sp) std::memcpy(t_sp, a->tsp.data(), a->n * 4);
     return LPSIM_OK;

@@ -61,6 +61,27 @@ struct LinkTime {
     uint32_t m;  // earliest arrival by entering in a later bin (ms; 0xFFFFFFFF: none)
 };
 
+// bin length (ms) of a link-time table with bins of bin_steps steps
+inline uint64_t table_bin_ms(const lpsim_assign *a, uint32_t bin_steps) {
+    return std::max<uint64_t>(1, to_ms((double)bin_steps * a->dt));
+}
+
+// The link-time table, bin-major (n_bins x n_edges): each (edge, bin)'s time in
+// ms and the earliest arrival entering a later bin, on the host's threads.
+inline void fill_link_times(const lpsim_assign *a, const float *tt, uint32_t n_bins, uint64_t bin_ms, LinkTime *tbm) {
+    const uint32_t ne = a->n_edges;
+    lpsim::parallel_pieces(ne, [&](uint64_t e0, uint64_t e1, uint64_t) {
+        for (uint64_t e = e0; e < e1; e++) {
+            uint64_t m = 0xFFFFFFFFull;
+            for (uint32_t b = n_bins; b-- > 0;) {
+                const uint32_t c = cost_ms(tt[e * n_bins + b]);
+                tbm[(size_t)b * ne + e] = LinkTime{c, (uint32_t)m};
+                m = std::min<uint64_t>(m, (uint64_t)b * bin_ms + c);
+            }
+        }
+    });
+}
+
 struct TD {
     const lpsim_assign *a;
     std::vector<LinkTime> tbm;  // n_bins x n_edges
@@ -68,19 +89,8 @@ struct TD {
     uint64_t bin_ms;
 
     TD(const lpsim_assign *a_, const float *tt, uint32_t n_bins_, uint32_t bin_steps)
-        : a(a_), tbm((size_t)n_bins_ * a_->n_edges), n_bins(n_bins_),
-          bin_ms(std::max<uint64_t>(1, to_ms((double)bin_steps * a_->dt))) {
-        const uint32_t ne = a->n_edges;
-        lpsim::parallel_pieces(ne, [&](uint64_t e0, uint64_t e1, uint64_t) {
-            for (uint64_t e = e0; e < e1; e++) {
-                uint64_t m = 0xFFFFFFFFull;
-                for (uint32_t b = n_bins; b-- > 0;) {
-                    const uint32_t c = cost_ms(tt[e * n_bins + b]);
-                    tbm[(size_t)b * ne + e] = LinkTime{c, (uint32_t)m};
-                    m = std::min<uint64_t>(m, (uint64_t)b * bin_ms + c);
-                }
-            }
-        });
+        : a(a_), tbm((size_t)n_bins_ * a_->n_edges), n_bins(n_bins_), bin_ms(table_bin_ms(a_, bin_steps)) {
+        fill_link_times(a, tt, n_bins, bin_ms, tbm.data());
     }
 
     uint32_t bin(uint64_t t) const { return (uint32_t)std::min<uint64_t>(t / bin_ms, n_bins - 1); }
