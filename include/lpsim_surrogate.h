@@ -36,7 +36,10 @@ int lpsim_mlp_create(lpsim_mlp **out, uint32_t n_features, uint32_t batch, uint6
 int lpsim_mlp_set_params(lpsim_mlp *m, const float *const *tensors);
 int lpsim_mlp_get_params(lpsim_mlp *m, float *const *tensors);
 
-/* y[i] = MLP(X[i, :]) for n rows of n_features f32 values (BF16 inside). */
+/* y[i] = MLP(X[i, :]) for n rows of n_features f32 values (BF16 inside).
+ * With more than `batch` rows the outputs gather on the device (4 bytes per
+ * row, in whole batches; allocated at the first such call and kept until
+ * lpsim_mlp_destroy, LPSIM_E_OOM if it cannot be) and cross back once. */
 int lpsim_mlp_forward(lpsim_mlp *m, uint64_t n, const float *X, float *y);
 
 /* Forward and backward of one batch (n <= batch rows): mean squared error

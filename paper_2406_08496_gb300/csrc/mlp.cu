@@ -1023,6 +1023,9 @@ struct lpsim_mlp {
     uint64_t pool_n = 0, pool_cap = 0;
     float *loss_hist = nullptr;
     uint32_t loss_cap = 0;
+    // outputs of a many-batch inference call, gathered on the device
+    float *y_all = nullptr;
+    uint64_t y_all_cap = 0;
 
     void *alloc(size_t bytes) {
         void *p = nullptr;
@@ -1036,6 +1039,7 @@ struct lpsim_mlp {
         cudaFree(pool_X);
         cudaFree(pool_t);
         cudaFree(loss_hist);
+        cudaFree(y_all);
         if (own_stream) cudaStreamDestroy(stream);
     }
 };
@@ -1092,7 +1096,7 @@ int adam_step(lpsim_mlp *m, float lr) {
 // forward of rows [0, B) already packed in X0; keep = training buffers
 // training keeps the pre-activations (for GELU') and transposed activations
 // (for the weight gradients); inference writes only the activations
-int forward_fused(lpsim_mlp *m) {
+int forward_fused(lpsim_mlp *m, float *y_out = nullptr) {
     static bool attr_set = false;
     if (!attr_set) {
         CU(cudaFuncSetAttribute(mlp_forward_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem));
@@ -1106,7 +1110,7 @@ int forward_fused(lpsim_mlp *m) {
     g.b3 = m->P[5];
     g.w4 = m->P[6];
     g.b4 = m->P[7];
-    g.y = m->y;
+    g.y = y_out ? y_out : m->y;
     g.err = m->err;
     const int grid = std::min(g.n_tiles, m->n_sm);
     mlp_forward_fused<<<grid, kFwdThreads, kFwdSmem, m->stream>>>(m->mX0, m->mW[0], m->mW[1], m->mW[2], g);
@@ -1202,14 +1206,16 @@ int backward_batch(lpsim_mlp *m, int n_real) {
     return LPSIM_OK;
 }
 
-int pack_batch(lpsim_mlp *m, const float *X_host, const float *t_host, uint64_t n) {
+// transposed: also the transposed input copy the weight gradients read (training only)
+int pack_batch(lpsim_mlp *m, const float *X_host, const float *t_host, uint64_t n, bool transposed = true) {
     cudaStream_t st = m->stream;
     CU(cudaMemcpyAsync(m->Xf, X_host, n * m->nf * 4, cudaMemcpyHostToDevice, st));
     if (t_host) {
         CU(cudaMemsetAsync(m->t, 0, m->B * 4, st));
         CU(cudaMemcpyAsync(m->t, t_host, n * 4, cudaMemcpyHostToDevice, st));
     }
-    pack_inputs<<<dim3(m->B / 32, 2), dim3(32, 8), 0, st>>>(m->Xf, (int)n, m->nf, m->B, m->X0, m->X0T);
+    pack_inputs<<<dim3(m->B / 32, 2), dim3(32, 8), 0, st>>>(m->Xf, (int)n, m->nf, m->B, m->X0,
+                                                           transposed ? m->X0T : nullptr);
     m->launches++;
     CU(cudaGetLastError());
     return LPSIM_OK;
@@ -1331,12 +1337,35 @@ int lpsim_mlp_get_params(lpsim_mlp *m, float *const *tensors) {
 
 int lpsim_mlp_forward(lpsim_mlp *m, uint64_t n, const float *X, float *y) {
     if (!m || !X || !y) return fail(LPSIM_E_INVALID_ARG, "NULL argument");
-    for (uint64_t r0 = 0; r0 < n; r0 += m->B) {
-        const uint64_t nb = std::min<uint64_t>(m->B, n - r0);
-        TRY(pack_batch(m, X + r0 * m->nf, nullptr, nb));
-        TRY(forward_batch(m, false));
-        CU(cudaMemcpyAsync(y + r0, m->y, nb * 4, cudaMemcpyDeviceToHost, m->stream));
+    const uint64_t B = (uint64_t)m->B;
+    if (n > B) {
+        // many batches: each batch's outputs land in one device array (every
+        // tile of a batch writes its 128 rows, so it is sized in whole
+        // batches) that crosses back once, not one small copy per batch
+        const uint64_t rows = (n + B - 1) / B * B;
+        if (rows > m->y_all_cap) {
+            CU(cudaStreamSynchronize(m->stream));
+            cudaFree(m->y_all);
+            m->y_all = nullptr;
+            m->y_all_cap = 0;
+            if (cudaMalloc(&m->y_all, rows * 4) != cudaSuccess) {
+                m->y_all = nullptr;
+                return fail(LPSIM_E_OOM, "device allocation of the outputs failed");
+            }
+            m->y_all_cap = rows;
+        }
     }
+    for (uint64_t r0 = 0; r0 < n; r0 += B) {
+        const uint64_t nb = std::min<uint64_t>(B, n - r0);
+        TRY(pack_batch(m, X + r0 * m->nf, nullptr, nb, false));
+        if (n > B) {
+            TRY(forward_fused(m, m->y_all + r0));
+        } else {
+            TRY(forward_batch(m, false));
+            CU(cudaMemcpyAsync(y + r0, m->y, nb * 4, cudaMemcpyDeviceToHost, m->stream));
+        }
+    }
+    if (n > B) CU(cudaMemcpyAsync(y, m->y_all, n * 4, cudaMemcpyDeviceToHost, m->stream));
     CU(cudaStreamSynchronize(m->stream));
     return mlp_check_err(m);
 }
