@@ -64,6 +64,24 @@ int dnew(lpsim_ctx *c, T *&out, size_t count) {
         if (rc_ != LPSIM_OK) return rc_; \
     } while (0)
 
+// A device block held for the length of one call and given back, after the
+// stream has finished with it, on every exit path.
+struct Scratch {
+    lpsim_ctx *c;
+    void *p;
+    Scratch(lpsim_ctx *ctx, size_t bytes) : c(ctx), p(ctx->dalloc(bytes)) {}
+    Scratch(const Scratch &) = delete;
+    Scratch &operator=(const Scratch &) = delete;
+    ~Scratch() {
+        if (!p) return;
+        cudaStreamSynchronize(c->stream);
+        auto it = std::find(c->blocks.begin(), c->blocks.end(), p);
+        if (it != c->blocks.end()) c->blocks.erase(it);
+        if (c->release) c->release(p, c->alloc_user);
+        else cudaFree(p);
+    }
+};
+
 // a device buffer whose contents change while stepping
 template <class T>
 int dnew_mut(lpsim_ctx *c, T *&out, size_t count) {
@@ -1059,19 +1077,9 @@ int lpsim_link_stats(lpsim_ctx *c, lpsim_link_stat *out, uint64_t n_edges, uint3
     size_t nb = (size_t)c->n_edges * c->p.n_bins * 4;
     if (nb) {
         // device arrays are bin-major: transpose into edge-major scratch first
-        uint32_t *tmp = static_cast<uint32_t *>(c->dalloc(nb));
-        if (!tmp) return fail(LPSIM_E_OOM, "device scratch allocation failed");
-        struct Giveback {
-            lpsim_ctx *c;
-            void *p;
-            ~Giveback() {
-                cudaStreamSynchronize(c->stream);
-                auto it = std::find(c->blocks.begin(), c->blocks.end(), p);
-                if (it != c->blocks.end()) c->blocks.erase(it);
-                if (c->release) c->release(p, c->alloc_user);
-                else cudaFree(p);
-            }
-        } giveback{c, tmp};
+        Scratch scratch(c, nb);
+        if (!scratch.p) return fail(LPSIM_E_OOM, "device scratch allocation failed");
+        uint32_t *tmp = static_cast<uint32_t *>(scratch.p);
         struct {
             uint32_t *host;
             const uint32_t *dev;
@@ -1110,19 +1118,9 @@ int lpsim_get_state(lpsim_ctx *c, uint64_t n, float *x, float *v, uint32_t *edge
     if (n != c->n_trips) return fail(LPSIM_E_INVALID_ARG, "n does not match the trips loaded");
     // scratch: x, v, edge, ridx (4 B each) and lane (1 B) per vehicle; given
     // back on every exit path (after the stream has finished with it)
-    uint8_t *tmp = static_cast<uint8_t *>(c->dalloc(n * 17 + 64));
-    if (!tmp) return fail(LPSIM_E_OOM, "device scratch allocation failed");
-    struct Giveback {
-        lpsim_ctx *c;
-        void *p;
-        ~Giveback() {
-            cudaStreamSynchronize(c->stream);
-            auto it = std::find(c->blocks.begin(), c->blocks.end(), p);
-            if (it != c->blocks.end()) c->blocks.erase(it);
-            if (c->release) c->release(p, c->alloc_user);
-            else cudaFree(p);
-        }
-    } giveback{c, tmp};
+    Scratch scratch(c, n * 17 + 64);
+    if (!scratch.p) return fail(LPSIM_E_OOM, "device scratch allocation failed");
+    uint8_t *tmp = static_cast<uint8_t *>(scratch.p);
     float *dx = reinterpret_cast<float *>(tmp);
     float *dv = dx + n;
     uint32_t *de = reinterpret_cast<uint32_t *>(dv + n);
