@@ -140,6 +140,21 @@ def test_discretionary_lane_changes_tiny_overtaking(chunked):
             lockstep(net, dem, params, 120, check_every=1, vehicle_types=BF_TYPES, gpu_params=dict(flags=4))
 
 
+def test_busy_lanes_tiny():
+    """The brute force's busy family (10-17 vehicles on long multi-lane edges
+    with a diverge), the mandatory rule alone and with the discretionary one,
+    every step."""
+    from test_oracle_bruteforce import TYPES as BF_TYPES
+    from test_oracle_bruteforce import scenario_overtaking
+    for seed in range(3000, 3020):
+        for dlc in (0.0, 1.0):
+            net, trips, params, vt = scenario_overtaking(seed, busy=True)
+            dem = make_demand(trips)
+            dem["vtype"] = vt
+            params.update(dlc_prob=dlc, dlc_gain=3.0)
+            lockstep(net, dem, params, 150, check_every=1, vehicle_types=BF_TYPES, gpu_params=dict(flags=4))
+
+
 def test_edge_cases():
     # one-cell edges, 4 lanes, single-edge routes, far-future departure, a
     # queue of 30 vehicles released at once onto a one-lane edge
