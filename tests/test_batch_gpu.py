@@ -53,10 +53,14 @@ def _compare_scenario(g, vids_b, off, s, o, vid_o, n_bins):
     assert np.array_equal(g.lane_map()[c0:c1], o.lane_map()), s
 
 
-@pytest.mark.parametrize("gpu_params", [{}, dict(block_size=128, blocks_per_sm=2, sort_period=32)])
-def test_batch_equals_each_scenario_alone(scenarios, gpu_params):
+@pytest.mark.parametrize("gpu_params,extra", [({}, {}), (dict(block_size=128, blocks_per_sm=2, sort_period=32), {}),
+                                               ({}, dict(dlc_prob=0.3, dlc_gain=3.0, eps_amp=1.0))])
+def test_batch_equals_each_scenario_alone(scenarios, gpu_params, extra):
+    """Each scenario of a batch bit for bit equal to the oracle's run of it
+    alone: in two launch configurations, and with the discretionary lane
+    change on (its draws keyed by the scenario's own seed and ids)."""
     from paper_2406_08496_gb300 import BatchSimulation
-    params = dict(bin_steps=300, n_bins=8, x0=80.0)
+    params = dict(bin_steps=300, n_bins=8, x0=80.0, **extra)
     nets = [n for n, _, _ in scenarios]
     dems = [d for _, d, _ in scenarios]
     seeds = [s for _, _, s in scenarios]
