@@ -63,7 +63,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="regional",
-                    choices=["regional", "grid", "large", "batch64", "assignment", "paths", "surrogate", "onchip"])
+                    choices=["regional", "regional-small", "grid", "large", "batch64", "assignment", "paths", "surrogate",
+                             "onchip"])
     ap.add_argument("--repeats", type=int, default=1,
                     help="assignment workload: alternate the two arms this many times and report the spread")
     ap.add_argument("--iterations", type=int, default=40,
@@ -92,6 +93,11 @@ def load_workload(name: str):
     elif name == "large":
         net, dem = W.regional_day(seed=3, n_trips=9_010_000, scale="large")
         label = "regional-1M-nodes-9.01M-trips-24h"
+    elif name == "regional-small":
+        # the regional generator at reduced scale (the small case for full
+        # profiler captures: a few hundred MB on the device)
+        net, dem = W.assignment_case(scale="small")
+        label = "regional-27k-nodes-340k-trips-24h"
     else:
         net, dem = W.grid_day(seed=1)
         label = "grid-8x8-2000-trips"
