@@ -184,7 +184,9 @@ int lpsim_load_network(lpsim_ctx **out, const lpsim_network *net, const lpsim_pa
  * route), an edge id is out of range or consecutive route edges do not
  * meet; the message names the lowest failing trip, offset errors before edge
  * errors (the checks run on the host's threads); LPSIM_E_STATE on a second
- * call. */
+ * call.  The routes are reordered on the host in a staging buffer of 4 bytes
+ * per route entry that the process keeps for later loads (one load uses it at
+ * a time; it grows to the largest demand loaded and is released at exit). */
 int lpsim_load_demand(lpsim_ctx *ctx, uint64_t n_trips, const uint32_t *depart_step, const uint64_t *route_off,
                       const uint32_t *route_edges, uint32_t *out_vehicle_id);
 

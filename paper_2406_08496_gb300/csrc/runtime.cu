@@ -630,6 +630,60 @@ namespace {
 // Trips of one simulation or of a batch of scenarios.  scen (nullable): the
 // scenario of each input trip, non-decreasing; seeds (nullable): the
 // lane-change seed of each scenario (default: the context's seed).
+// Host staging of the id-ordered routes, kept for the process between demand
+// loads: a fresh buffer's pages fault in at first touch (about 50 ms for the
+// 1.4 GB of the 2.82M-trip day), and the assignment loop loads a demand per
+// simulation.  One load holds it at a time (others allocate their own); it
+// grows to the largest demand seen and is never shrunk.
+struct RouteStaging {
+    std::mutex mu;
+    std::unique_ptr<uint32_t[]> buf;
+    uint64_t cap = 0;
+    bool busy = false;
+};
+
+RouteStaging &route_staging() {
+    static RouteStaging s;
+    return s;
+}
+
+// the staging for one load: the process's buffer when free, else a private one
+struct RouteBuffer {
+    uint32_t *p = nullptr;
+    bool pooled = false;
+    std::unique_ptr<uint32_t[]> own;
+    explicit RouteBuffer(uint64_t n) {
+        RouteStaging &st = route_staging();
+        {
+            std::lock_guard<std::mutex> g(st.mu);
+            if (!st.busy) {
+                if (st.cap < n) {
+                    st.buf.reset();
+                    st.buf.reset(new (std::nothrow) uint32_t[n]);
+                    st.cap = st.buf ? n : 0;
+                }
+                if (st.buf) {
+                    st.busy = true;
+                    pooled = true;
+                    p = st.buf.get();
+                }
+            }
+        }
+        if (!pooled) {
+            own.reset(new (std::nothrow) uint32_t[n]);
+            p = own.get();
+        }
+    }
+    RouteBuffer(const RouteBuffer &) = delete;
+    RouteBuffer &operator=(const RouteBuffer &) = delete;
+    ~RouteBuffer() {
+        if (!pooled) return;
+        RouteStaging &st = route_staging();
+        std::lock_guard<std::mutex> g(st.mu);
+        st.busy = false;
+    }
+};
+
 int load_demand_impl(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, const uint64_t *route_off,
                      const uint32_t *route_edges, uint32_t *out_vid, const uint32_t *scen, uint32_t n_scen,
                      const uint64_t *seeds, const uint8_t *vtype = nullptr) {
@@ -669,15 +723,28 @@ int load_demand_impl(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, cons
         std::mutex mu;
         uint64_t bad = n;
         int kind = 0;
-        const uint32_t *src = c->src.data(), *dst = c->dst.data();
         const uint32_t ne = c->n_edges;
+        // each edge's (tail, head) in one record: one random read per route entry
+        std::vector<uint2> ends(ne);
+        parallel_pieces(ne, [&](uint64_t e0, uint64_t e1, uint64_t) {
+            for (uint64_t e = e0; e < e1; e++) ends[e] = make_uint2(c->src[e], c->dst[e]);
+        });
         parallel_pieces(n, [&](uint64_t j0, uint64_t j1, uint64_t) {
             for (uint64_t j = j0; j < j1; j++) {
                 int k = 0;
-                for (uint64_t q = route_off[j]; q < route_off[j + 1] && !k; q++) {
+                uint32_t head = 0;  // head node of the previous edge of the route
+                for (uint64_t q = route_off[j]; q < route_off[j + 1]; q++) {
                     const uint32_t e = route_edges[q];
-                    if (e >= ne) k = 1;
-                    else if (q > route_off[j] && dst[route_edges[q - 1]] != src[e]) k = 2;
+                    if (e >= ne) {
+                        k = 1;
+                        break;
+                    }
+                    const uint2 te = ends[e];
+                    if (q > route_off[j] && head != te.x) {
+                        k = 2;
+                        break;
+                    }
+                    head = te.y;
                 }
                 if (k) {
                     std::lock_guard<std::mutex> g(mu);
@@ -708,11 +775,11 @@ int load_demand_impl(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, cons
                          [&](uint32_t a, uint32_t b) { return depart_step[a] < depart_step[b]; });
     }
     std::vector<uint32_t> dep(n), roff(n + 1);
-    // the routes in vehicle-id order: left uninitialised (every entry is
-    // written below, by the host's threads, which also take its first-touch
-    // page faults in parallel)
+    // the routes in vehicle-id order, in the process's staging buffer (never
+    // cleared: every entry is written below, by the host's threads)
     const uint64_t rsize = total ? total : 1;
-    std::unique_ptr<uint32_t[]> route(new (std::nothrow) uint32_t[rsize]);
+    RouteBuffer rbuf(rsize);
+    uint32_t *const route = rbuf.p;
     if (!route) return fail(LPSIM_E_OOM, "host allocation of the route array failed");
     if (!total) route[0] = 0;
     // lane-change draw keys: seed ^ (id within the scenario) * C1; a single
@@ -745,7 +812,7 @@ int load_demand_impl(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, cons
     parallel_pieces(n, [&](uint64_t i0, uint64_t i1, uint64_t) {
         for (uint64_t id = i0; id < i1; id++) {
             const uint32_t j = order[id];
-            std::memcpy(route.get() + roff[id], route_edges + route_off[j], (size_t)(roff[id + 1] - roff[id]) * 4);
+            std::memcpy(route + roff[id], route_edges + route_off[j], (size_t)(roff[id + 1] - roff[id]) * 4);
         }
     });
     c->dep_sorted = dep;  // nondecreasing: ids are ranks by departure step
@@ -847,7 +914,7 @@ int load_demand_impl(lpsim_ctx *c, uint64_t n, const uint32_t *depart_step, cons
         d.trip_vt = dvt;
         d.typed = 1;
     }
-    TRY(upload(c, droute, route.get(), rsize * 4));
+    TRY(upload(c, droute, route, rsize * 4));
     TRY(upload(c, droff, roff.data(), (n + 1) * 4));
     TRY(upload(c, oe, org_edge.data(), norg * 4ull));
     TRY(upload(c, oq, org_qoff.data(), norg * 4ull));
